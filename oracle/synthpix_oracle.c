@@ -1,0 +1,394 @@
+/*
+ * FP64 CPU oracle for PIV image-pair rendering (SynthPix, arXiv 2512.09664).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is a plain, slow, step-by-step
+ * restatement of the rendering method, used to check the CUDA library.
+ * It shares no code, header or constant table with the CUDA path and must
+ * never be linked into it.  Only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark load it.
+ *
+ * The method (paper Section 2):
+ *   - particles sampled uniformly over the image domain, parameters drawn
+ *     uniformly from configured intervals            ("Sampling the particles",
+ *                                                       text after Eq. 1)
+ *   - image-2 positions from the displacement map (x, y) -> (x+u, y+v)
+ *                                                     ("Sampling the particles")
+ *   - single-particle image: the Gaussian of Eq. 1 (rho = 0, sigma_x = sigma_y)
+ *   - contributions summed (superposition)          ("aggregation of the
+ *                                                       particle contributions")
+ *   - each particle rendered on a patch of 3 max(d)+1 px ("Efficient rasterization")
+ *   - illumination non-uniformity, noise and blur named among the imaging
+ *     parameters (Abstract) with no formula given.
+ *
+ * Readings taken where the paper is silent:
+ *   R1  sigma = d / 4 (e^-2 diameter), so the integrated particle image is
+ *       pi d^2 / 8 * I0.
+ *   R2  pixel (i, j) covers [j, j+1) x [i, i+1), x = column, y = row (down);
+ *       the particle image is integrated over the pixel (100% fill factor,
+ *       Remark "camera-model"), giving separable erf differences.
+ *   R3  out-of-plane gain exp(-z^2 / (2 s^2)) (Gaussian laser sheet), z fixed
+ *       between frames; the Remark "out-of-focus" form is deferred by the paper.
+ *   R4  flow grid nodes at cell centres, bilinear interpolation in lerp form,
+ *       indices clamped to the grid (border); displacement integrated with RK4
+ *       (or Euler) in n substeps over dt.  Euler with n = 1 and dt = 1 is the
+ *       paper's x + u(x).
+ *   R5  window: per particle j in [floor(x - 1.5 d), floor(x + 1.5 d)] (the
+ *       3 d + 1 patch), clipped to the image.
+ *   R6  epilogue per frame: A = L * S + sigma_n * n, L a separable sin^2
+ *       bump between illum_min and illum_max, n standard normal (Box-Muller on
+ *       Philox words); separable normalised Gaussian blur, radius ceil(3 sigma_b),
+ *       replicate border, horizontal pass first; quantisation
+ *       clamp(rint(B * M), 0, M), M = 2^bits - 1, round-half-even, decided in
+ *       FP32 like the GPU's FP32 epilogue.
+ *   R7  random numbers: Philox4x32-10 (Salmon et al., SC'11) keyed by the seed,
+ *       counter (index, stream tag, pair id): tag 0 -> (x, y, d, I) words,
+ *       tag 1 -> (z, d2) words, tag 0x100 + f -> noise words of frame f.
+ *
+ * Precision: FP64 everywhere except the quantisation decision (R6).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_PI 3.14159265358979323846
+
+typedef struct {
+    int32_t height, width;      /* image size in pixels */
+    int32_t flow_h, flow_w;     /* flow grid size in nodes */
+    int64_t n_particles;        /* particles seeded in frame 1 */
+    uint64_t seed, pair_id;     /* Philox key and counter words */
+    int32_t d_dist;             /* 0 uniform diameter, 1 clipped normal */
+    int32_t integrator;         /* 0 RK4, 1 Euler */
+    int32_t n_substeps;         /* >= 1 */
+    int32_t quant_bits;         /* 0: no quantisation */
+    double d_min, d_max, d_mu, d_sigma;
+    double i_min, i_max, z_min, z_max, sheet_sigma;
+    double illum_min, illum_max, noise_sigma, blur_sigma;
+    double dt;
+} oracle_pair;
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10: Salmon, Moraes, Dror, Shaw, "Parallel Random Numbers: As  */
+/* Easy as 1, 2, 3", SC'11.  Round: two 32x32->64 products of counter words */
+/* 0 and 2 with the multipliers, outputs mixed with the other counter words */
+/* and the key; the key is bumped by the Weyl constants between rounds.     */
+/* ------------------------------------------------------------------------ */
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Words of stream `tag` at index `idx` for this pair (R7). */
+void oracle_stream_words(uint64_t seed, uint64_t pair_id, uint32_t idx, uint32_t tag, uint32_t w[4])
+{
+    uint32_t ctr[4] = { idx, tag, (uint32_t)pair_id, (uint32_t)(pair_id >> 32) };
+    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    oracle_philox4x32_10(ctr, key, w);
+}
+
+/* uniform in [0, 1) from the top 24 bits */
+static double u24(uint32_t w) { return (double)(w >> 8) * (1.0 / 16777216.0); }
+/* uniform in (0, 1] from the top 24 bits (safe for log) */
+static double uo24(uint32_t w) { return (double)((w >> 8) + 1u) * (1.0 / 16777216.0); }
+
+/* Box-Muller normal; second = 0 takes the cosine branch, 1 the sine branch */
+static double box_muller(uint32_t wa, uint32_t wb, int second)
+{
+    double r = sqrt(-2.0 * log(uo24(wa)));
+    double th = 2.0 * ORACLE_PI * u24(wb);
+    return second ? r * sin(th) : r * cos(th);
+}
+
+/* ------------------------------------------------------------------------ */
+/* particle attributes (paper Section 2, text after Eq. 1; R1, R3, R7)      */
+/* ------------------------------------------------------------------------ */
+typedef struct { double x0, y0, d, intensity, z, ieff; } oracle_attr;
+
+static void particle_attr(const oracle_pair *p, uint32_t i, oracle_attr *a)
+{
+    uint32_t w0[4], w1[4];
+    oracle_stream_words(p->seed, p->pair_id, i, 0u, w0);
+    oracle_stream_words(p->seed, p->pair_id, i, 1u, w1);
+    a->x0 = u24(w0[0]) * (double)p->width;
+    a->y0 = u24(w0[1]) * (double)p->height;
+    if (p->d_dist == 0) {
+        a->d = p->d_min + u24(w0[2]) * (p->d_max - p->d_min);
+    } else {
+        double n = box_muller(w0[2], w1[1], 0);
+        double d = p->d_mu + p->d_sigma * n;
+        a->d = d < p->d_min ? p->d_min : (d > p->d_max ? p->d_max : d);
+    }
+    a->intensity = p->i_min + u24(w0[3]) * (p->i_max - p->i_min);
+    a->z = p->z_min + u24(w1[0]) * (p->z_max - p->z_min);
+    double gain = 1.0;
+    if (p->sheet_sigma > 0.0)
+        gain = exp(-(a->z * a->z) / (2.0 * p->sheet_sigma * p->sheet_sigma));
+    a->ieff = a->intensity * gain;
+}
+
+/* ------------------------------------------------------------------------ */
+/* bilinear velocity on the cell-centred grid, border clamp (R4)            */
+/* ------------------------------------------------------------------------ */
+static long clampl(long v, long lo, long hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+void oracle_velocity(const float *flow, int32_t gh, int32_t gw, int32_t height, int32_t width,
+                     double x, double y, double *u, double *v)
+{
+    double gx = x * (double)gw / (double)width - 0.5;
+    double gy = y * (double)gh / (double)height - 0.5;
+    double fl = floor(gx), fk = floor(gy);
+    double tx = gx - fl, ty = gy - fk;
+    long l0 = clampl((long)fl, 0, gw - 1), l1 = clampl((long)fl + 1, 0, gw - 1);
+    long k0 = clampl((long)fk, 0, gh - 1), k1 = clampl((long)fk + 1, 0, gh - 1);
+    double out[2];
+    for (int c = 0; c < 2; ++c) {
+        double a = flow[(k0 * gw + l0) * 2 + c], b = flow[(k0 * gw + l1) * 2 + c];
+        double e = flow[(k1 * gw + l0) * 2 + c], f = flow[(k1 * gw + l1) * 2 + c];
+        double top = a + tx * (b - a);
+        double bot = e + tx * (f - e);
+        out[c] = top + ty * (bot - top);
+    }
+    *u = out[0];
+    *v = out[1];
+}
+
+/* Position after dt (paper: displacement map; R4: RK4 / Euler substeps). */
+void oracle_advect(const oracle_pair *p, const float *flow, double x, double y,
+                   double *xo, double *yo)
+{
+    int n = p->n_substeps;
+    double h = p->dt / (double)n;
+    for (int s = 0; s < n; ++s) {
+        double u1, v1;
+        oracle_velocity(flow, p->flow_h, p->flow_w, p->height, p->width, x, y, &u1, &v1);
+        if (p->integrator == 1) {
+            x += h * u1;
+            y += h * v1;
+            continue;
+        }
+        double u2, v2, u3, v3, u4, v4;
+        oracle_velocity(flow, p->flow_h, p->flow_w, p->height, p->width,
+                        x + 0.5 * h * u1, y + 0.5 * h * v1, &u2, &v2);
+        oracle_velocity(flow, p->flow_h, p->flow_w, p->height, p->width,
+                        x + 0.5 * h * u2, y + 0.5 * h * v2, &u3, &v3);
+        oracle_velocity(flow, p->flow_h, p->flow_w, p->height, p->width,
+                        x + h * u3, y + h * v3, &u4, &v4);
+        x += h / 6.0 * (u1 + 2.0 * u2 + 2.0 * u3 + u4);
+        y += h / 6.0 * (v1 + 2.0 * v2 + 2.0 * v3 + v4);
+    }
+    *xo = x;
+    *yo = y;
+}
+
+/*
+ * Per-particle table, 8 doubles per particle:
+ *   x0, y0 (frame 1), d, I, z, Ieff, x1, y1 (frame 2).
+ */
+int oracle_particles(const oracle_pair *p, const float *flow, double *out)
+{
+    for (int64_t i = 0; i < p->n_particles; ++i) {
+        oracle_attr a;
+        particle_attr(p, (uint32_t)i, &a);
+        double x1, y1;
+        oracle_advect(p, flow, a.x0, a.y0, &x1, &y1);
+        double *o = out + 8 * i;
+        o[0] = a.x0; o[1] = a.y0; o[2] = a.d; o[3] = a.intensity;
+        o[4] = a.z; o[5] = a.ieff; o[6] = x1; o[7] = y1;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* pixel integration of Eq. 1 (rho = 0): separable erf differences (R2)     */
+/* ------------------------------------------------------------------------ */
+
+/* Mass of a unit 1-D Gaussian (centre c, std sigma) over [j, j + 1). */
+double oracle_pixel_mass(double c, double sigma, int64_t j)
+{
+    const double s2 = 1.4142135623730950488;
+    double a = ((double)j - c) / sigma;
+    double b = ((double)j + 1.0 - c) / sigma;
+    /* Phi(t) = erfc(-t / sqrt 2) / 2; the tails use erfc differences */
+    if (a >= 0.0)
+        return 0.5 * (erfc(a / s2) - erfc(b / s2));
+    if (b <= 0.0)
+        return 0.5 * (erfc(-b / s2) - erfc(-a / s2));
+    return 1.0 - 0.5 * erfc(-a / s2) - 0.5 * erfc(b / s2);
+}
+
+/*
+ * Accumulate particles into one frame S[H][W] (not cleared here).
+ * parts: n rows of (x, y, d, Ieff).  mode 0: windowed pixel-integrated
+ * (the method); mode 1: pixel-integrated over every pixel (brute force, no
+ * window); mode 2: Eq. 1 point-sampled at pixel centres inside the window.
+ */
+int oracle_splat(int32_t height, int32_t width, const double *parts, int64_t n, int32_t mode,
+                 double *S)
+{
+    double *ex = (double *)malloc(sizeof(double) * (size_t)width);
+    if (!ex) return -1;
+    for (int64_t k = 0; k < n; ++k) {
+        double x = parts[4 * k], y = parts[4 * k + 1], d = parts[4 * k + 2], ieff = parts[4 * k + 3];
+        double sigma = d / 4.0;
+        double amp = ieff * 2.0 * ORACLE_PI * sigma * sigma;
+        long j0 = (long)floor(x - 1.5 * d), j1 = (long)floor(x + 1.5 * d);
+        long i0 = (long)floor(y - 1.5 * d), i1 = (long)floor(y + 1.5 * d);
+        if (mode == 1) {
+            j0 = 0; j1 = width - 1; i0 = 0; i1 = height - 1;
+        }
+        if (j0 < 0) j0 = 0;
+        if (i0 < 0) i0 = 0;
+        if (j1 > width - 1) j1 = width - 1;
+        if (i1 > height - 1) i1 = height - 1;
+        if (j0 > j1 || i0 > i1) continue;
+        if (mode == 2) {
+            for (long i = i0; i <= i1; ++i)
+                for (long j = j0; j <= j1; ++j) {
+                    double dx = (double)j + 0.5 - x, dy = (double)i + 0.5 - y;
+                    S[i * width + j] += ieff * exp(-(dx * dx + dy * dy) / (2.0 * sigma * sigma));
+                }
+            continue;
+        }
+        for (long j = j0; j <= j1; ++j) ex[j] = oracle_pixel_mass(x, sigma, j);
+        for (long i = i0; i <= i1; ++i) {
+            double ey = oracle_pixel_mass(y, sigma, i);
+            for (long j = j0; j <= j1; ++j) S[i * width + j] += amp * ex[j] * ey;
+        }
+    }
+    free(ex);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* epilogue (R6)                                                            */
+/* ------------------------------------------------------------------------ */
+
+/* Standard normal noise sample of pixel `pix` (row-major) in frame `frame`. */
+double oracle_noise(uint64_t seed, uint64_t pair_id, int32_t frame, int64_t pix)
+{
+    uint32_t w[4];
+    oracle_stream_words(seed, pair_id, (uint32_t)(pix >> 2), 0x100u + (uint32_t)frame, w);
+    switch (pix & 3) {
+    case 0: return box_muller(w[0], w[1], 0);
+    case 1: return box_muller(w[0], w[1], 1);
+    case 2: return box_muller(w[2], w[3], 0);
+    default: return box_muller(w[2], w[3], 1);
+    }
+}
+
+double oracle_illumination(const oracle_pair *p, int64_t i, int64_t j)
+{
+    double sx = sin(ORACLE_PI * ((double)j + 0.5) / (double)p->width);
+    double sy = sin(ORACLE_PI * ((double)i + 0.5) / (double)p->height);
+    return p->illum_min + (p->illum_max - p->illum_min) * (sx * sx) * (sy * sy);
+}
+
+int32_t oracle_blur_radius(double blur_sigma)
+{
+    if (!(blur_sigma > 0.0)) return 0;
+    return (int32_t)ceil(3.0 * blur_sigma);
+}
+
+/* frame: 0 or 1.  S, B: [H][W] FP64.  Q: [H][W] codes or NULL. */
+int oracle_epilogue(const oracle_pair *p, int32_t frame, const double *S, double *B, uint32_t *Q)
+{
+    const long H = p->height, W = p->width;
+    double *A = (double *)malloc(sizeof(double) * (size_t)(H * W));
+    if (!A) return -1;
+    for (long i = 0; i < H; ++i)
+        for (long j = 0; j < W; ++j) {
+            double val = oracle_illumination(p, i, j) * S[i * W + j];
+            if (p->noise_sigma != 0.0)
+                val += p->noise_sigma * oracle_noise(p->seed, p->pair_id, frame, i * W + j);
+            A[i * W + j] = val;
+        }
+    int32_t R = oracle_blur_radius(p->blur_sigma);
+    if (R > 0) {
+        double *w = (double *)malloc(sizeof(double) * (size_t)(2 * R + 1));
+        double *T = (double *)malloc(sizeof(double) * (size_t)(H * W));
+        if (!w || !T) { free(A); free(w); free(T); return -1; }
+        double sum = 0.0;
+        for (int k = -R; k <= R; ++k) {
+            w[k + R] = exp(-(double)(k * k) / (2.0 * p->blur_sigma * p->blur_sigma));
+            sum += w[k + R];
+        }
+        for (int k = 0; k <= 2 * R; ++k) w[k] /= sum;
+        for (long i = 0; i < H; ++i)           /* horizontal pass */
+            for (long j = 0; j < W; ++j) {
+                double acc = 0.0;
+                for (int k = -R; k <= R; ++k)
+                    acc += w[k + R] * A[i * W + clampl(j + k, 0, W - 1)];
+                T[i * W + j] = acc;
+            }
+        for (long i = 0; i < H; ++i)           /* vertical pass */
+            for (long j = 0; j < W; ++j) {
+                double acc = 0.0;
+                for (int k = -R; k <= R; ++k)
+                    acc += w[k + R] * T[clampl(i + k, 0, H - 1) * W + j];
+                B[i * W + j] = acc;
+            }
+        free(w);
+        free(T);
+    } else {
+        memcpy(B, A, sizeof(double) * (size_t)(H * W));
+    }
+    free(A);
+    if (Q && p->quant_bits > 0) {
+        float M = (float)((1u << p->quant_bits) - 1u);
+        for (long k = 0; k < H * W; ++k) {
+            float q = rintf((float)B[k] * M);
+            Q[k] = q < 0.0f ? 0u : (q > M ? (uint32_t)M : (uint32_t)q);
+        }
+    }
+    return 0;
+}
+
+/*
+ * Render one pair.  S (nullable) receives the splatted frames before the
+ * epilogue, B the frames after it, Q (nullable) the quantised codes, parts
+ * (nullable) the particle table of oracle_particles.  Frame f occupies
+ * [f*H*W, (f+1)*H*W) of each output.
+ */
+int oracle_render_pair(const oracle_pair *p, const float *flow, double *S, double *B, uint32_t *Q,
+                       double *parts, int32_t splat_mode)
+{
+    const int64_t HW = (int64_t)p->height * p->width;
+    const int64_t n = p->n_particles;
+    double *tab = (double *)malloc(sizeof(double) * (size_t)(8 * (n > 0 ? n : 1)));
+    double *xy = (double *)malloc(sizeof(double) * (size_t)(4 * (n > 0 ? n : 1)));
+    double *s = S ? S : (double *)malloc(sizeof(double) * (size_t)(2 * HW));
+    if (!tab || !xy || !s) { free(tab); free(xy); if (!S) free(s); return -1; }
+    oracle_particles(p, flow, tab);
+    memset(s, 0, sizeof(double) * (size_t)(2 * HW));
+    for (int f = 0; f < 2; ++f) {
+        for (int64_t i = 0; i < n; ++i) {
+            xy[4 * i] = tab[8 * i + (f ? 6 : 0)];
+            xy[4 * i + 1] = tab[8 * i + (f ? 7 : 1)];
+            xy[4 * i + 2] = tab[8 * i + 2];
+            xy[4 * i + 3] = tab[8 * i + 5];
+        }
+        oracle_splat(p->height, p->width, xy, n, splat_mode, s + f * HW);
+        oracle_epilogue(p, f, s + f * HW, B + f * HW, Q ? Q + f * HW : NULL);
+    }
+    if (parts) memcpy(parts, tab, sizeof(double) * (size_t)(8 * n));
+    free(tab);
+    free(xy);
+    if (!S) free(s);
+    return 0;
+}
