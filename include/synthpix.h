@@ -1,0 +1,160 @@
+/*
+ * synthpix.h — C ABI of the B300 (sm_103a) PIV image-pair renderer.
+ *
+ * The library renders synthetic Particle Image Velocimetry image pairs from a
+ * prescribed flow field, the method of SynthPix (arXiv 2512.09664, Section 2):
+ * particles are seeded over the image, moved by the flow for the second
+ * frame, each drawn as the Gaussian particle image of Eq. 1, summed, and the
+ * frames finished with illumination non-uniformity, noise, blur and
+ * quantisation (the imaging parameters listed in the Abstract and in
+ * Section 2 "Configuration file").
+ *
+ * Conventions used by every entry point
+ *  - Pixel (i, j) covers [j, j+1) x [i, i+1); x is the column, y the row
+ *    (downwards).  Frames are row-major [H][W].
+ *  - Flow grids are float32 [flow_h][flow_w][2] holding (u, v) in pixels per
+ *    frame, nodes at cell centres ((l + 1/2) W / flow_w, (k + 1/2) H / flow_h),
+ *    interpolated bilinearly with indices clamped to the grid.
+ *  - sigma = d / 4 for a particle of diameter d; the particle image is
+ *    integrated over each pixel (separable erf differences) on the window
+ *    [floor(x - 1.5 d), floor(x + 1.5 d)]^2, the 3 d + 1 patch of Section 2
+ *    "Efficient rasterization".
+ *  - Random numbers: Philox4x32-10 keyed by the batch seed; the output of a
+ *    pair depends only on (seed, pair_id, its descriptor, its flow grid).
+ *  - All device pointers are owned by the caller.  The library allocates no
+ *    device memory and keeps no per-call state; it only reads the caller's
+ *    inputs and writes the caller's outputs and workspace.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *    default stream).  They never synchronise the device and never trap; on
+ *    error they return a negative status before launching anything, and
+ *    synthpix_last_error() describes it.
+ */
+#ifndef SYNTHPIX_H
+#define SYNTHPIX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SYNTHPIX_ABI_VERSION 1
+
+/* ---- status codes ------------------------------------------------------ */
+#define SYNTHPIX_OK            0
+#define SYNTHPIX_EINVAL       -1  /* a descriptor or argument is out of range      */
+#define SYNTHPIX_EWORKSPACE   -2  /* workspace pointer NULL / too small / unaligned */
+#define SYNTHPIX_ECUDA        -3  /* a CUDA call or launch failed                   */
+#define SYNTHPIX_EUNSUPPORTED -4  /* valid but not supported (reserved fields set)  */
+
+/* ---- element types (out_dtype, inter_dtype) ----------------------------- */
+#define SYNTHPIX_F32  0
+#define SYNTHPIX_F16  1
+#define SYNTHPIX_BF16 2
+#define SYNTHPIX_U8   3
+#define SYNTHPIX_U16  4
+
+/* ---- integrators -------------------------------------------------------- */
+#define SYNTHPIX_RK4   0
+#define SYNTHPIX_EULER 1
+
+/*
+ * Per-pair acquisition parameters (Abstract: seeding density, particle image
+ * size, illumination non-uniformity, noise, blur, timing; Section 2 "Sampling
+ * the particles": parameters drawn uniformly from configured intervals).
+ * 128 bytes, naturally aligned; reserved fields must be zero.
+ */
+typedef struct synthpix_pair_desc {
+    int32_t  height, width;      /* frame size in pixels, 1..32768                   */
+    int64_t  image_offset;       /* element offset of frame 1 in the output buffer;
+                                    frame 2 follows at image_offset + height*width   */
+    int64_t  flow_offset;        /* float offset of this pair's flow grid in `flows`;
+                                    pairs may share a grid (F flows for B pairs)     */
+    int32_t  flow_h, flow_w;     /* flow grid nodes, 1..32768                         */
+    uint64_t pair_id;            /* Philox counter words of this pair                 */
+    uint32_t n_particles;        /* particles of frame 1: floor(ppp * H * W)          */
+    int32_t  d_dist;             /* 0: d ~ U[d_min, d_max]; 1: N(d_mu, d_sigma)
+                                    clipped to [d_min, d_max]                         */
+    float d_min, d_max;          /* particle diameter bounds, px; 0 < d_min <= d_max <= 32 */
+    float d_mu, d_sigma;         /* normal diameter parameters (d_dist = 1)           */
+    float i_min, i_max;          /* peak intensity I0 of Eq. 1 ~ U[i_min, i_max]       */
+    float z_min, z_max;          /* out-of-plane position ~ U[z_min, z_max]            */
+    float sheet_sigma;           /* Gaussian laser sheet: I = I0 exp(-z^2/(2 s^2));
+                                    <= 0 disables the attenuation                     */
+    float illum_min, illum_max;  /* illumination field L in [illum_min, illum_max]:
+                                    L = min + (max-min) sin^2(pi (j+.5)/W) sin^2(pi (i+.5)/H) */
+    float noise_sigma;           /* additive Gaussian noise std (full scale 1.0)      */
+    float blur_sigma;            /* Gaussian blur std in px (radius ceil(3 sigma)), 0..8 */
+    float reserved[7];           /* must be zero                                       */
+} synthpix_pair_desc;
+
+/*
+ * Batch-wide settings.  64 bytes; reserved fields must be zero.
+ */
+typedef struct synthpix_batch_desc {
+    uint64_t seed;               /* Philox key                                         */
+    int32_t  out_dtype;          /* SYNTHPIX_F32/F16/BF16 (values of B, unclipped) or
+                                    SYNTHPIX_U8/U16 (codes clamp(rint(B*M),0,M))        */
+    int32_t  quant_bits;         /* 0 for float outputs; 1..8 for U8; 1..16 for U16;
+                                    M = 2^quant_bits - 1                               */
+    int32_t  inter_dtype;        /* storage of the splatted image between the splat and
+                                    the epilogue: SYNTHPIX_F32 keeps it in on-chip
+                                    memory (fused, no HBM intermediate); SYNTHPIX_F16 /
+                                    SYNTHPIX_BF16 write it to the workspace in 16 bits
+                                    (accumulation stays FP32 or wider)                 */
+    int32_t  integrator;         /* SYNTHPIX_RK4 or SYNTHPIX_EULER                      */
+    int32_t  n_substeps;         /* substeps over dt, 1..1024                          */
+    float    dt;                 /* time between the frames, in frames (|dt| <= 64)    */
+    int32_t  tile;               /* square screen tile edge: 0 (auto), 16, 32 or 64     */
+    int32_t  flags;              /* must be 0                                          */
+    int32_t  reserved[6];        /* must be zero                                       */
+} synthpix_batch_desc;
+
+/*
+ * Bytes of device workspace synthpix_render_pairs needs for this batch
+ * (a 256-byte aligned region the caller allocates).  Returns 0 and sets the
+ * last error if the descriptors are invalid.  Only the host arrays are read.
+ */
+size_t synthpix_workspace_bytes(const synthpix_batch_desc *batch,
+                                const synthpix_pair_desc *pairs, int32_t n_pairs);
+
+/*
+ * Render n_pairs image pairs (paper Section 2; Eq. 1 integrated per pixel).
+ *
+ *   batch      host pointer, batch settings.
+ *   pairs      host pointer, n_pairs descriptors; read during the call only.
+ *   pairs_dev  NULL, or a device copy of the same n_pairs descriptors.  With
+ *              NULL the library copies `pairs` into the workspace with
+ *              cudaMemcpyAsync on `stream` (keep `pairs` unchanged until the
+ *              stream reaches the copy if it is pinned memory).  Passing a
+ *              device copy makes the call free of host-to-device copies, as a
+ *              CUDA-graph capture needs.
+ *   n_pairs    0 .. 1<<20 (0 returns SYNTHPIX_OK and does nothing).
+ *   flows      device pointer, float32; each pair reads
+ *              flows[flow_offset .. flow_offset + flow_h*flow_w*2).
+ *   images     device pointer to the output buffer of element type
+ *              batch->out_dtype; pair b writes elements
+ *              [image_offset, image_offset + 2*H*W) once each (frame 1, then 2).
+ *   workspace  device pointer, 256-byte aligned, at least
+ *              synthpix_workspace_bytes(...) bytes; contents on entry ignored.
+ *   stream     cudaStream_t.
+ *
+ * Returns SYNTHPIX_OK or a negative status (nothing is launched on error).
+ */
+int synthpix_render_pairs(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
+                          const synthpix_pair_desc *pairs_dev, int32_t n_pairs,
+                          const float *flows, void *images,
+                          void *workspace, size_t workspace_bytes, void *stream);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char *synthpix_last_error(void);
+
+/* SYNTHPIX_ABI_VERSION of the loaded library. */
+int synthpix_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SYNTHPIX_H */

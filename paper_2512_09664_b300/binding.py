@@ -1,0 +1,214 @@
+"""Thin Python binding of ``libsynthpix.so`` (the C ABI in include/synthpix.h).
+
+Argument marshalling only: descriptors become ctypes structures, tensors
+become raw device pointers and the current torch stream is passed through.
+Every step of the rendering runs in the library's CUDA kernels; if the
+library is missing or fails to load this module raises — there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import List, Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsynthpix.so")
+
+OK, EINVAL, EWORKSPACE, ECUDA, EUNSUPPORTED = 0, -1, -2, -3, -4
+DTYPE_CODE = {"f32": 0, "f16": 1, "bf16": 2, "u8": 3, "u16": 4}
+INTEGRATOR_CODE = {"rk4": 0, "euler": 1}
+_EXPORTS = ("synthpix_workspace_bytes", "synthpix_render_pairs", "synthpix_last_error", "synthpix_version")
+
+
+class PairDesc(C.Structure):
+    _fields_ = [
+        ("height", C.c_int32), ("width", C.c_int32),
+        ("image_offset", C.c_int64), ("flow_offset", C.c_int64),
+        ("flow_h", C.c_int32), ("flow_w", C.c_int32),
+        ("pair_id", C.c_uint64),
+        ("n_particles", C.c_uint32), ("d_dist", C.c_int32),
+        ("d_min", C.c_float), ("d_max", C.c_float), ("d_mu", C.c_float), ("d_sigma", C.c_float),
+        ("i_min", C.c_float), ("i_max", C.c_float), ("z_min", C.c_float), ("z_max", C.c_float),
+        ("sheet_sigma", C.c_float), ("illum_min", C.c_float), ("illum_max", C.c_float),
+        ("noise_sigma", C.c_float), ("blur_sigma", C.c_float),
+        ("reserved", C.c_float * 7),
+    ]
+
+
+class BatchDesc(C.Structure):
+    _fields_ = [
+        ("seed", C.c_uint64), ("out_dtype", C.c_int32), ("quant_bits", C.c_int32),
+        ("inter_dtype", C.c_int32), ("integrator", C.c_int32), ("n_substeps", C.c_int32),
+        ("dt", C.c_float), ("tile", C.c_int32), ("flags", C.c_int32), ("reserved", C.c_int32 * 6),
+    ]
+
+
+assert C.sizeof(PairDesc) == 128 and C.sizeof(BatchDesc) == 64
+
+_lib = None
+
+
+class SynthpixError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"synthpix error {code}: {msg}")
+        self.code = code
+
+
+def lib():
+    """Load the CUDA library (raises if it is absent: no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing; build it with `python -m paper_2512_09664_b300.build`")
+        L = C.CDLL(LIB_PATH)
+        vp, sz = C.c_void_p, C.c_size_t
+        L.synthpix_workspace_bytes.argtypes = [C.POINTER(BatchDesc), C.POINTER(PairDesc), C.c_int32]
+        L.synthpix_workspace_bytes.restype = sz
+        L.synthpix_render_pairs.argtypes = [C.POINTER(BatchDesc), C.POINTER(PairDesc), vp, C.c_int32,
+                                            vp, vp, vp, sz, vp]
+        L.synthpix_render_pairs.restype = C.c_int
+        L.synthpix_last_error.argtypes = []
+        L.synthpix_last_error.restype = C.c_char_p
+        L.synthpix_version.argtypes = []
+        L.synthpix_version.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> List[str]:
+    L = lib()
+    return [s for s in _EXPORTS if hasattr(L, s)]
+
+
+def last_error() -> str:
+    return lib().synthpix_last_error().decode()
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise SynthpixError(rc, last_error())
+
+
+# ----------------------------------------------------------------------------
+# descriptor marshalling
+# ----------------------------------------------------------------------------
+
+def batch_desc(seed: int, out_dtype="f32", quant_bits=0, inter_dtype="f32", integrator="rk4",
+               n_substeps=4, dt=1.0, tile=0) -> BatchDesc:
+    b = BatchDesc()
+    b.seed = seed
+    b.out_dtype = DTYPE_CODE[out_dtype]
+    b.quant_bits = quant_bits
+    b.inter_dtype = DTYPE_CODE[inter_dtype]
+    b.integrator = INTEGRATOR_CODE[integrator]
+    b.n_substeps = n_substeps
+    b.dt = float(np.float32(dt))
+    b.tile = tile
+    return b
+
+
+def pair_desc(spec, image_offset: int, flow_offset: int, flow_shape) -> PairDesc:
+    p = PairDesc()
+    p.height, p.width = spec.height, spec.width
+    p.image_offset, p.flow_offset = image_offset, flow_offset
+    p.flow_h, p.flow_w = int(flow_shape[0]), int(flow_shape[1])
+    p.pair_id = spec.pair_id
+    p.n_particles = spec.n_particles
+    p.d_dist = spec.d_dist
+    for k in ("d_min", "d_max", "d_mu", "d_sigma", "i_min", "i_max", "z_min", "z_max", "sheet_sigma",
+              "illum_min", "illum_max", "noise_sigma", "blur_sigma"):
+        setattr(p, k, float(getattr(spec, k)))
+    return p
+
+
+def torch_dtype(name: str):
+    import torch
+    return {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16, "u8": torch.uint8,
+            "u16": torch.uint16}[name]
+
+
+@dataclass
+class Packed:
+    """A workload laid out for the library: descriptors, flat flows, offsets."""
+
+    batch: BatchDesc
+    pairs: C.Array
+    n_pairs: int
+    flows_host: np.ndarray       # flat float32
+    image_offsets: List[int]
+    image_elems: int
+    out_dtype: str
+    shapes: List[tuple]
+
+
+def pack(wl, tile: int = 0, out_dtype: Optional[str] = None, inter_dtype: Optional[str] = None) -> Packed:
+    out_dtype = out_dtype or wl.out_dtype
+    flat, flow_off = [], []
+    off = 0
+    for f in wl.flows:
+        flow_off.append(off)
+        flat.append(np.ascontiguousarray(f, dtype=np.float32).reshape(-1))
+        off += f.size
+    arr = (PairDesc * max(wl.n_pairs, 1))()
+    img_off, io = [], 0
+    for b, spec in enumerate(wl.pairs):
+        img_off.append(io)
+        arr[b] = pair_desc(spec, io, flow_off[spec.flow_index], wl.flows[spec.flow_index].shape[:2])
+        io += 2 * spec.height * spec.width
+    bd = batch_desc(wl.seed, out_dtype, wl.quant_bits if out_dtype in ("u8", "u16") else 0,
+                    inter_dtype or wl.inter_dtype, wl.integrator, wl.n_substeps, wl.dt, tile)
+    flows = np.concatenate(flat) if flat else np.zeros(2, np.float32)
+    return Packed(bd, arr, wl.n_pairs, flows, img_off, io, out_dtype,
+                  [(p.height, p.width) for p in wl.pairs])
+
+
+def workspace_bytes(pk: Packed) -> int:
+    n = lib().synthpix_workspace_bytes(C.byref(pk.batch), pk.pairs, pk.n_pairs)
+    if n == 0 and pk.n_pairs > 0:
+        raise SynthpixError(EINVAL, last_error())
+    return n
+
+
+def render_pairs(pk: Packed, flows_dev, images_dev, workspace_dev, pairs_dev=None, stream=None) -> None:
+    """synthpix_render_pairs on torch tensors (device pointers) and the current stream."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    rc = lib().synthpix_render_pairs(
+        C.byref(pk.batch), pk.pairs, C.c_void_p(pairs_dev.data_ptr()) if pairs_dev is not None else None,
+        pk.n_pairs, C.c_void_p(flows_dev.data_ptr()), C.c_void_p(images_dev.data_ptr()),
+        C.c_void_p(workspace_dev.data_ptr()), workspace_dev.numel() * workspace_dev.element_size(),
+        C.c_void_p(st.cuda_stream))
+    _check(rc)
+
+
+class Renderer:
+    """Device buffers for repeated rendering of one packed workload."""
+
+    def __init__(self, wl, device="cuda", tile: int = 0, out_dtype=None, inter_dtype=None,
+                 device_descriptors: bool = True):
+        import torch
+        self.pk = pack(wl, tile=tile, out_dtype=out_dtype, inter_dtype=inter_dtype)
+        self.device = torch.device(device)
+        self.flows = torch.from_numpy(self.pk.flows_host).to(self.device)
+        ws = workspace_bytes(self.pk)
+        self.workspace = torch.empty(max(ws, 256), dtype=torch.uint8, device=self.device)
+        self.images = torch.empty(max(self.pk.image_elems, 1), dtype=torch_dtype(self.pk.out_dtype),
+                                  device=self.device)
+        self.pairs_dev = None
+        if device_descriptors and self.pk.n_pairs > 0:
+            raw = np.frombuffer(C.string_at(C.addressof(self.pk.pairs), 128 * self.pk.n_pairs), dtype=np.uint8)
+            self.pairs_dev = torch.from_numpy(raw.copy()).to(self.device)
+
+    def render(self, stream=None):
+        render_pairs(self.pk, self.flows, self.images, self.workspace, self.pairs_dev, stream)
+        return self.images
+
+    def frames(self, b: int):
+        """[2, H, W] view of pair b in the output buffer."""
+        h, w = self.pk.shapes[b]
+        o = self.pk.image_offsets[b]
+        return self.images[o:o + 2 * h * w].view(2, h, w)

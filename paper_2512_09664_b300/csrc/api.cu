@@ -1,0 +1,235 @@
+// Host entry points of the C ABI declared in include/synthpix.h: argument
+// validation, workspace layout and the launch sequence.  Nothing here touches
+// the device before every argument has been checked.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+bool finite(float v) { return std::isfinite(v); }
+
+struct Plan {
+    spx::Layout L;
+    int32_t tile;
+    int32_t fused;
+    int32_t max_halo;
+    float max_d;
+};
+
+int check_batch(const synthpix_batch_desc *b) {
+    if (!b) return fail(SYNTHPIX_EINVAL, "batch descriptor is NULL");
+    if (b->out_dtype < SYNTHPIX_F32 || b->out_dtype > SYNTHPIX_U16)
+        return fail(SYNTHPIX_EINVAL, "out_dtype %d is not one of F32/F16/BF16/U8/U16", b->out_dtype);
+    if (b->out_dtype == SYNTHPIX_U8 && (b->quant_bits < 1 || b->quant_bits > 8))
+        return fail(SYNTHPIX_EINVAL, "U8 output needs quant_bits in 1..8 (got %d)", b->quant_bits);
+    if (b->out_dtype == SYNTHPIX_U16 && (b->quant_bits < 1 || b->quant_bits > 16))
+        return fail(SYNTHPIX_EINVAL, "U16 output needs quant_bits in 1..16 (got %d)", b->quant_bits);
+    if (b->out_dtype <= SYNTHPIX_BF16 && b->quant_bits != 0)
+        return fail(SYNTHPIX_EINVAL, "float outputs need quant_bits = 0 (got %d)", b->quant_bits);
+    if (b->inter_dtype < SYNTHPIX_F32 || b->inter_dtype > SYNTHPIX_BF16)
+        return fail(SYNTHPIX_EINVAL, "inter_dtype %d is not one of F32/F16/BF16", b->inter_dtype);
+    if (b->inter_dtype != SYNTHPIX_F32)
+        return fail(SYNTHPIX_EUNSUPPORTED, "16-bit intermediate storage is not available in this build");
+    if (b->integrator != SYNTHPIX_RK4 && b->integrator != SYNTHPIX_EULER)
+        return fail(SYNTHPIX_EINVAL, "integrator %d is not RK4 (0) or Euler (1)", b->integrator);
+    if (b->n_substeps < 1 || b->n_substeps > 1024)
+        return fail(SYNTHPIX_EINVAL, "n_substeps %d outside 1..1024", b->n_substeps);
+    if (!finite(b->dt) || std::fabs(b->dt) > 64.0f) return fail(SYNTHPIX_EINVAL, "dt must be finite with |dt| <= 64");
+    if (b->tile != 0 && b->tile != 16 && b->tile != 32 && b->tile != 64)
+        return fail(SYNTHPIX_EINVAL, "tile %d is not 0, 16, 32 or 64", b->tile);
+    if (b->flags != 0) return fail(SYNTHPIX_EUNSUPPORTED, "flags must be 0 (got 0x%x)", b->flags);
+    for (int k = 0; k < 6; ++k)
+        if (b->reserved[k] != 0) return fail(SYNTHPIX_EUNSUPPORTED, "batch reserved[%d] is not zero", k);
+    return SYNTHPIX_OK;
+}
+
+int check_pair(const synthpix_pair_desc &d, int b) {
+    if (d.height < 1 || d.height > 32768 || d.width < 1 || d.width > 32768)
+        return fail(SYNTHPIX_EINVAL, "pair %d: frame %dx%d outside 1..32768", b, d.height, d.width);
+    if (d.flow_h < 1 || d.flow_h > 32768 || d.flow_w < 1 || d.flow_w > 32768)
+        return fail(SYNTHPIX_EINVAL, "pair %d: flow grid %dx%d outside 1..32768", b, d.flow_h, d.flow_w);
+    if (d.flow_offset < 0 || (d.flow_offset & 1))
+        return fail(SYNTHPIX_EINVAL, "pair %d: flow_offset must be even and >= 0", b);
+    if (d.image_offset < 0 || d.image_offset > (int64_t(1) << 60))
+        return fail(SYNTHPIX_EINVAL, "pair %d: image_offset out of range", b);
+    if (d.d_dist != 0 && d.d_dist != 1) return fail(SYNTHPIX_EINVAL, "pair %d: d_dist must be 0 or 1", b);
+    const float fs[] = {d.d_min, d.d_max, d.d_mu, d.d_sigma, d.i_min, d.i_max, d.z_min, d.z_max,
+                        d.sheet_sigma, d.illum_min, d.illum_max, d.noise_sigma, d.blur_sigma};
+    for (float v : fs)
+        if (!finite(v)) return fail(SYNTHPIX_EINVAL, "pair %d: non-finite parameter", b);
+    if (!(d.d_min > 0.0f) || d.d_max < d.d_min || d.d_max > 32.0f)
+        return fail(SYNTHPIX_EINVAL, "pair %d: need 0 < d_min <= d_max <= 32", b);
+    if (d.d_sigma < 0.0f) return fail(SYNTHPIX_EINVAL, "pair %d: d_sigma < 0", b);
+    if (d.i_min < 0.0f || d.i_max < d.i_min || d.i_max > 1e6f)
+        return fail(SYNTHPIX_EINVAL, "pair %d: need 0 <= i_min <= i_max <= 1e6", b);
+    if (d.z_max < d.z_min) return fail(SYNTHPIX_EINVAL, "pair %d: z_max < z_min", b);
+    if (d.illum_max < d.illum_min || std::fabs(d.illum_min) > 1e6f || std::fabs(d.illum_max) > 1e6f)
+        return fail(SYNTHPIX_EINVAL, "pair %d: need illum_min <= illum_max within +-1e6", b);
+    if (d.noise_sigma < 0.0f || d.noise_sigma > 1e6f) return fail(SYNTHPIX_EINVAL, "pair %d: noise_sigma < 0", b);
+    if (d.blur_sigma < 0.0f || d.blur_sigma > 8.0f) return fail(SYNTHPIX_EINVAL, "pair %d: blur_sigma outside 0..8", b);
+    for (int k = 0; k < 7; ++k)
+        if (d.reserved[k] != 0.0f) return fail(SYNTHPIX_EUNSUPPORTED, "pair %d: reserved[%d] is not zero", b, k);
+    return SYNTHPIX_OK;
+}
+
+int make_plan(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs, int32_t n_pairs, Plan &P) {
+    int rc = check_batch(batch);
+    if (rc) return rc;
+    if (n_pairs < 0 || n_pairs > (1 << 20)) return fail(SYNTHPIX_EINVAL, "n_pairs %d outside 0..2^20", n_pairs);
+    if (n_pairs > 0 && !pairs) return fail(SYNTHPIX_EINVAL, "pairs is NULL");
+    P.tile = batch->tile ? batch->tile : 32;
+    P.fused = batch->inter_dtype == SYNTHPIX_F32 ? 1 : 0;
+    P.max_halo = 0;
+    P.max_d = 0.0f;
+    spx::Layout &L = P.L;
+    L.n_part = L.n_tiles = L.n_list = L.n_inter = 0;
+    for (int32_t b = 0; b < n_pairs; ++b) {
+        rc = check_pair(pairs[b], b);
+        if (rc) return rc;
+        const spx::PairGeom g = spx::pair_geom(pairs[b], P.tile, P.fused != 0);
+        L.n_part += pairs[b].n_particles;
+        L.n_tiles += 2LL * g.ntiles;
+        L.n_list += 2LL * g.list_cap;
+        if (!P.fused) L.n_inter += 2LL * pairs[b].height * pairs[b].width;
+        if (g.halo > P.max_halo) P.max_halo = g.halo;
+        if (pairs[b].d_max > P.max_d) P.max_d = pairs[b].d_max;
+    }
+    if (L.n_tiles > 0x7FFFFFFFLL) return fail(SYNTHPIX_EINVAL, "batch has more than 2^31-1 tiles");
+    if (L.n_list > (int64_t(1) << 40)) return fail(SYNTHPIX_EINVAL, "batch bin lists too large");
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = spx::align256(o + bytes);
+        return at;
+    };
+    L.plan = take((size_t)n_pairs * sizeof(spx::PairPlan));
+    L.desc = take((size_t)n_pairs * sizeof(synthpix_pair_desc));
+    L.check = take(256);
+    L.blur = take((size_t)n_pairs * spx::kBlurStride * sizeof(float));
+    L.count = take((size_t)L.n_tiles * 4);
+    L.off = take((size_t)L.n_tiles * 4);
+    L.cursor = take((size_t)L.n_tiles * 4);
+    L.pos = take((size_t)L.n_part * 32);
+    L.sa = take((size_t)L.n_part * 8);
+    L.list = take((size_t)L.n_list * 4);
+    L.inter = take((size_t)L.n_inter * 2);
+    L.total = o;
+    return SYNTHPIX_OK;
+}
+
+size_t elem_size(int32_t dt) {
+    switch (dt) {
+    case SYNTHPIX_F32: return 4;
+    case SYNTHPIX_U8: return 1;
+    default: return 2;
+    }
+}
+
+}  // namespace
+
+static_assert(sizeof(synthpix_pair_desc) == 128, "pair descriptor ABI");
+static_assert(sizeof(synthpix_batch_desc) == 64, "batch descriptor ABI");
+
+extern "C" {
+
+const char *synthpix_last_error(void) { return g_err; }
+
+int synthpix_version(void) { return SYNTHPIX_ABI_VERSION; }
+
+size_t synthpix_workspace_bytes(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
+                                int32_t n_pairs) {
+    Plan P;
+    if (make_plan(batch, pairs, n_pairs, P) != SYNTHPIX_OK) return 0;
+    g_err[0] = 0;
+    return P.L.total;
+}
+
+int synthpix_render_pairs(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
+                          const synthpix_pair_desc *pairs_dev, int32_t n_pairs, const float *flows, void *images,
+                          void *workspace, size_t workspace_bytes, void *stream) {
+    Plan P;
+    int rc = make_plan(batch, pairs, n_pairs, P);
+    if (rc) return rc;
+    if (n_pairs == 0) {
+        g_err[0] = 0;
+        return SYNTHPIX_OK;
+    }
+    if (!flows || ((uintptr_t)flows & 7)) return fail(SYNTHPIX_EINVAL, "flows is NULL or not 8-byte aligned");
+    if (!images || ((uintptr_t)images % elem_size(batch->out_dtype)))
+        return fail(SYNTHPIX_EINVAL, "images is NULL or misaligned for its element type");
+    if (!workspace || ((uintptr_t)workspace & 255))
+        return fail(SYNTHPIX_EWORKSPACE, "workspace is NULL or not 256-byte aligned");
+    if (workspace_bytes < P.L.total)
+        return fail(SYNTHPIX_EWORKSPACE, "workspace has %zu bytes, %zu needed", workspace_bytes, P.L.total);
+    if (pairs_dev && ((uintptr_t)pairs_dev & 7)) return fail(SYNTHPIX_EINVAL, "pairs_dev is not 8-byte aligned");
+
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    unsigned char *ws = static_cast<unsigned char *>(workspace);
+    const spx::Layout &L = P.L;
+    const synthpix_pair_desc *descs = pairs_dev;
+    cudaError_t e;
+    if (!descs) {
+        e = cudaMemcpyAsync(ws + L.desc, pairs, (size_t)n_pairs * sizeof(synthpix_pair_desc),
+                            cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return fail(SYNTHPIX_ECUDA, "descriptor copy: %s", cudaGetErrorString(e));
+        descs = reinterpret_cast<const synthpix_pair_desc *>(ws + L.desc);
+    }
+    spx::PairPlan *plan = reinterpret_cast<spx::PairPlan *>(ws + L.plan);
+    int32_t *check = reinterpret_cast<int32_t *>(ws + L.check);
+    float *blur_w = reinterpret_cast<float *>(ws + L.blur);
+    e = spx::launch_plan(descs, n_pairs, P.tile, P.fused, plan, L, check, blur_w, st);
+    if (e != cudaSuccess) return fail(SYNTHPIX_ECUDA, "plan launch: %s", cudaGetErrorString(e));
+    e = cudaMemsetAsync(ws + L.count, 0, (size_t)L.n_tiles * 4, st);
+    if (e != cudaSuccess) return fail(SYNTHPIX_ECUDA, "count reset: %s", cudaGetErrorString(e));
+
+    spx::KernelArgs a;
+    a.descs = descs;
+    a.plan = plan;
+    a.check = check;
+    a.n_pairs = n_pairs;
+    a.tile = P.tile;
+    a.n_part = L.n_part;
+    a.n_tiles = L.n_tiles;
+    a.seed = batch->seed;
+    a.dt = batch->dt;
+    a.n_substeps = batch->n_substeps;
+    a.integrator = batch->integrator;
+    a.quant_bits = batch->quant_bits;
+    a.flows = flows;
+    a.images = images;
+    a.pos0 = reinterpret_cast<float4 *>(ws + L.pos);
+    a.pos1 = a.pos0 + L.n_part;
+    a.sa = reinterpret_cast<float2 *>(ws + L.sa);
+    a.count = reinterpret_cast<uint32_t *>(ws + L.count);
+    a.off = reinterpret_cast<uint32_t *>(ws + L.off);
+    a.cursor = reinterpret_cast<uint32_t *>(ws + L.cursor);
+    a.list = reinterpret_cast<uint32_t *>(ws + L.list);
+    a.blur_w = blur_w;
+    a.smem_edge = P.tile + 2 * P.max_halo;
+    const int wmax = std::min(spx::window_max(P.max_d), a.smem_edge);
+    a.warp_scratch = 4 * (wmax + 2);
+    if (spx::splat_smem_bytes(a.smem_edge, a.tile, a.warp_scratch) > 227 * 1024)
+        return fail(SYNTHPIX_EUNSUPPORTED, "tile %d with blur radius %d needs too much shared memory", P.tile,
+                    P.max_halo);
+    e = spx::launch_render(a, batch->out_dtype, st);
+    if (e != cudaSuccess) return fail(SYNTHPIX_ECUDA, "render launch: %s", cudaGetErrorString(e));
+    g_err[0] = 0;
+    return SYNTHPIX_OK;
+}
+
+}  // extern "C"

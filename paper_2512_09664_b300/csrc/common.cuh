@@ -1,0 +1,124 @@
+// Shared declarations of the sm_103a PIV renderer: per-pair plan, workspace
+// layout, Philox4x32-10 and the split (integer + fraction) particle position.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "synthpix.h"
+
+namespace spx {
+
+constexpr int kMaxBlurRadius = 24;  // ceil(3 * 8)
+constexpr int kBlurStride = 32;     // floats per pair in the blur-tap table
+
+// Derived per-pair geometry (device table built by k_plan, mirrored on the host).
+struct PairPlan {
+    int64_t part_base;   // first global particle index of the pair
+    int64_t list_base;   // first bin-list slot of the frame-1 segment
+    int64_t list_cap;    // slots of one frame segment (frame 2 at list_base + list_cap)
+    int64_t inter_base;  // first element of the pair's 16-bit intermediate frames
+    int32_t tile_base;   // first global tile id of frame 1 (frame 2 at + ntiles)
+    int32_t tiles_x, tiles_y, ntiles;
+    int32_t blur_r;      // ceil(3 * blur_sigma), 0 without blur
+    int32_t halo;        // pixels a tile's bins extend beyond the tile (blur_r or 0)
+    int32_t pad[2];
+};
+static_assert(sizeof(PairPlan) == 64, "PairPlan layout");
+
+// Screen tile edge and per-pair quantities shared by host and device.
+struct PairGeom {
+    int32_t tiles_x, tiles_y, ntiles, blur_r, halo, span;
+    int64_t list_cap;
+};
+
+__host__ __device__ inline int32_t blur_radius_of(float blur_sigma) {
+    if (!(blur_sigma > 0.0f)) return 0;
+    return (int32_t)ceil(3.0 * (double)blur_sigma);  // exact product of an FP32 value
+}
+
+// Upper bound of the pixels along one axis of a particle window [floor(x-1.5d), floor(x+1.5d)].
+__host__ __device__ inline int32_t window_max(float d_max) { return (int32_t)floor(3.0 * (double)d_max) + 5; }
+
+__host__ __device__ inline PairGeom pair_geom(const synthpix_pair_desc &d, int tile, bool fused) {
+    PairGeom g;
+    g.tiles_x = (d.width + tile - 1) / tile;
+    g.tiles_y = (d.height + tile - 1) / tile;
+    g.ntiles = g.tiles_x * g.tiles_y;
+    g.blur_r = blur_radius_of(d.blur_sigma);
+    g.halo = fused ? g.blur_r : 0;
+    // pixels of a clipped particle window: <= floor(3 d_max) + 2, plus margin
+    // for FP32 rounding of d and x +- 1.5 d; widened by the halo on both sides
+    int32_t ext = window_max(d.d_max) + 2 * g.halo;
+    g.span = (ext - 1) / tile + 2;
+    int32_t sx = g.span < g.tiles_x ? g.span : g.tiles_x;
+    int32_t sy = g.span < g.tiles_y ? g.span : g.tiles_y;
+    g.list_cap = (int64_t)d.n_particles * (int64_t)sx * (int64_t)sy;
+    return g;
+}
+
+// Workspace layout (byte offsets, 256-aligned), computed on the host.
+struct Layout {
+    size_t plan, desc, check, blur, count, off, cursor, pos, sa, list, inter, total;
+    int64_t n_part, n_tiles, n_list, n_inter;
+};
+
+__host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64 multiplies of counter words 0 and 2, mixing the high halves with
+// the other counter words and the key, the key advanced by the Weyl
+// increments between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// Stream layout: counter = (index, tag, pair_id lo, pair_id hi), key = seed.
+constexpr uint32_t kTagAttrA = 0u;      // (x, y, d, I)
+constexpr uint32_t kTagAttrB = 1u;      // (z, d2, -, -)
+constexpr uint32_t kTagNoise = 0x100u;  // + frame; index = pixel / 4
+
+__device__ __forceinline__ uint4 stream_words(uint64_t seed, uint64_t pair_id, uint32_t idx, uint32_t tag) {
+    return philox4x32_10(make_uint4(idx, tag, (uint32_t)pair_id, (uint32_t)(pair_id >> 32)),
+                         make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+
+__device__ __forceinline__ float u24f(uint32_t w) { return (float)(w >> 8) * (1.0f / 16777216.0f); }
+__device__ __forceinline__ float uo24f(uint32_t w) { return (float)((w >> 8) + 1u) * (1.0f / 16777216.0f); }
+
+// ---------------------------------------------------------------------------
+// Split particle coordinate: value = i + f with integer i and FP32 f (|f| <= ~1
+// after renormalisation), keeping ~2^-24 px absolute resolution anywhere in
+// a 32768 px frame (a plain FP32 coordinate has 2^-9 px at 16384).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void split_add(int32_t &i, float &f, float d) {
+    // TwoSum with non-contractible intrinsics (an FMA fused into f + d would
+    // break the exact error term)
+    const float s = __fadd_rn(f, d);
+    const float bb = __fsub_rn(s, f);
+    const float e = __fadd_rn(__fsub_rn(f, __fsub_rn(s, bb)), __fsub_rn(d, bb));
+    const float n = floorf(s);
+    float r = __fadd_rn(__fsub_rn(s, n), e);  // s - n is exact
+    int32_t ni = (int32_t)fminf(fmaxf(n, -1.0e9f), 1.0e9f);
+    if (r >= 1.0f) { r = __fsub_rn(r, 1.0f); ni += 1; }
+    else if (r < 0.0f) { r = __fadd_rn(r, 1.0f); ni -= 1; }
+    long long t = (long long)i + ni;
+    i = (int32_t)(t > 1000000000LL ? 1000000000LL : (t < -1000000000LL ? -1000000000LL : t));
+    f = r;
+}
+
+}  // namespace spx

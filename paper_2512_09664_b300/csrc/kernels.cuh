@@ -1,0 +1,38 @@
+// Launch interface between the host entry points (api.cu) and the kernels.
+#pragma once
+
+#include "common.cuh"
+
+namespace spx {
+
+// Everything one render launch sequence reads or writes (passed by value).
+struct KernelArgs {
+    const synthpix_pair_desc *descs;  // device copy of the descriptors
+    const PairPlan *plan;             // device plan (k_plan)
+    const int32_t *check;             // 1 when the device plan matches the host's
+    int32_t n_pairs;
+    int32_t tile;
+    int64_t n_part;                   // particles of all pairs
+    int64_t n_tiles;                  // (pair, frame, tile) items
+    uint64_t seed;
+    float dt;
+    int32_t n_substeps;
+    int32_t integrator;
+    int32_t quant_bits;
+    const float *flows;
+    void *images;
+    float4 *pos0, *pos1;              // split positions of frames 1 and 2
+    float2 *sa;                       // (sigma, Ieff * 2 pi sigma^2)
+    uint32_t *count, *off, *cursor;   // per (pair, frame, tile)
+    uint32_t *list;                   // bin lists
+    int32_t smem_edge;                // capacity edge of the on-chip tile (tile + 2 max radius)
+    int32_t warp_scratch;             // floats of per-warp window scratch
+    const float *blur_w;              // [n_pairs][kBlurStride] normalised taps w[|k|]
+};
+
+cudaError_t launch_plan(const synthpix_pair_desc *descs, int32_t n_pairs, int32_t tile, int32_t fused,
+                        PairPlan *plan, const Layout &L, int32_t *check, float *blur_w, cudaStream_t st);
+cudaError_t launch_render(const KernelArgs &a, int32_t out_dtype, cudaStream_t st);
+size_t splat_smem_bytes(int edge, int tile, int warp_scratch);
+
+}  // namespace spx

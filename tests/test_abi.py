@@ -1,0 +1,108 @@
+"""The C ABI without a GPU: the library loads, exports what include/synthpix.h
+declares, and rejects bad arguments with the documented status codes before
+touching the device (these calls never reach CUDA)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2512_09664_b300 import binding as B
+from paper_2512_09664_b300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "synthpix.h")).read()
+    return sorted(set(re.findall(r"\b(synthpix_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = B.lib()
+    for name in _declared():
+        assert hasattr(L, name), name
+    assert L.synthpix_version() == 1
+
+
+def test_descriptor_sizes_match_header():
+    assert C.sizeof(B.PairDesc) == 128 and C.sizeof(B.BatchDesc) == 64
+
+
+def _packed():
+    return B.pack(W.batch_512_u8(n_pairs=2))
+
+
+FAKE = C.c_void_p(0x7F0000000000)  # never dereferenced: validation fails first
+
+
+def _render(pk, ws_bytes=1 << 30, ws=FAKE, flows=FAKE, images=FAKE):
+    return B.lib().synthpix_render_pairs(C.byref(pk.batch), pk.pairs, None, pk.n_pairs, flows, images,
+                                         ws, ws_bytes, None)
+
+
+@pytest.mark.parametrize("field,value", [
+    ("out_dtype", 9), ("quant_bits", 0), ("integrator", 3), ("n_substeps", 0), ("n_substeps", 5000),
+    ("dt", float("nan")), ("tile", 48)])
+def test_bad_batch_fields_are_rejected(field, value):
+    pk = _packed()
+    setattr(pk.batch, field, value)
+    assert _render(pk) == B.EINVAL
+    assert B.last_error()
+    assert B.lib().synthpix_workspace_bytes(C.byref(pk.batch), pk.pairs, pk.n_pairs) == 0
+
+
+@pytest.mark.parametrize("field,value", [
+    ("height", 0), ("width", 40000), ("flow_h", 0), ("flow_offset", -2), ("flow_offset", 3),
+    ("d_min", 0.0), ("d_max", 40.0), ("d_dist", 2), ("i_min", 2.0), ("blur_sigma", 9.0),
+    ("noise_sigma", -1.0), ("z_min", 5.0), ("sheet_sigma", float("inf"))])
+def test_bad_pair_fields_are_rejected(field, value):
+    pk = _packed()
+    setattr(pk.pairs[1], field, value)
+    assert _render(pk) == B.EINVAL
+    assert "pair 1" in B.last_error()
+
+
+def test_reserved_fields_and_flags_unsupported():
+    pk = _packed()
+    pk.pairs[0].reserved[3] = 1.0
+    assert _render(pk) == B.EUNSUPPORTED
+    pk = _packed()
+    pk.batch.flags = 4
+    assert _render(pk) == B.EUNSUPPORTED
+    pk = _packed()
+    pk.batch.reserved[0] = 1
+    assert _render(pk) == B.EUNSUPPORTED
+
+
+def test_workspace_checks():
+    pk = _packed()
+    need = B.workspace_bytes(pk)
+    assert need > 0
+    assert _render(pk, ws_bytes=need - 1) == B.EWORKSPACE
+    assert _render(pk, ws=None) == B.EWORKSPACE
+    assert _render(pk, ws=C.c_void_p(0x7F0000000010)) == B.EWORKSPACE  # not 256-aligned
+
+
+def test_null_and_misaligned_buffers():
+    pk = _packed()
+    assert _render(pk, flows=None) == B.EINVAL
+    assert _render(pk, flows=C.c_void_p(0x7F0000000004)) == B.EINVAL
+    assert _render(pk, images=None) == B.EINVAL
+    assert B.lib().synthpix_render_pairs(None, pk.pairs, None, 2, FAKE, FAKE, FAKE, 1 << 30, None) == B.EINVAL
+    assert B.lib().synthpix_render_pairs(C.byref(pk.batch), None, None, 2, FAKE, FAKE, FAKE, 1 << 30,
+                                         None) == B.EINVAL
+    assert B.lib().synthpix_render_pairs(C.byref(pk.batch), pk.pairs, None, -1, FAKE, FAKE, FAKE, 1 << 30,
+                                         None) == B.EINVAL
+
+
+def test_zero_pairs_is_a_no_op():
+    pk = _packed()
+    assert B.lib().synthpix_render_pairs(C.byref(pk.batch), pk.pairs, None, 0, None, None, None, 0,
+                                         None) == B.OK
+
+
+def test_workspace_grows_with_particles_and_tiles():
+    small = B.workspace_bytes(B.pack(W.batch_512_u8(n_pairs=1)))
+    big = B.workspace_bytes(B.pack(W.batch_512_u8(n_pairs=2)))
+    assert big > small

@@ -1,0 +1,171 @@
+"""CUDA path vs the FP64 oracle, element by element, on seeded synthetic inputs.
+
+Sizes are chosen so the oracle finishes in seconds while the GPU path spans
+several tiles and a ragged tail; the full-size workloads are covered in
+test_gpu_fullsize.py.  All calls go through the C ABI.
+"""
+import numpy as np
+import pytest
+
+from paper_2512_09664_b300 import workloads as W
+
+from parity import compare, gpu_render, oracle_render
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("CUDA device required")
+
+
+def _small(H, Wd, n, **kw):
+    return W.PairSpec(height=H, width=Wd, n_particles=n, pair_id=kw.pop("pair_id", 0), **kw)
+
+
+def _wl(pairs, flows, seed=7, **kw):
+    return W.Workload(name="t", seed=seed, pairs=pairs, flows=flows, **kw)
+
+
+def test_single_pair_256_lamb_oseen_f32():
+    wl = W.single_pair_256()
+    st = compare(wl, gpu_render(wl), oracle_render(wl))
+    print("single_pair_256", st)
+
+
+@pytest.mark.parametrize("tile", [16, 32, 64])
+def test_batch_512_u8_epilogue(tile):
+    wl = W.batch_512_u8(n_pairs=2)
+    st = compare(wl, gpu_render(wl, tile=tile), oracle_render(wl))
+    print("batch_512_u8", tile, st)
+
+
+def test_batch_512_float_error_budget():
+    # the same pairs with float output: the error of B itself, which decides
+    # the quantised codes; it must sit far below the 1e-6 boundary band
+    wl = W.batch_512_u8(n_pairs=2)
+    wl.out_dtype, wl.quant_bits = "f32", 0
+    ref = oracle_render(wl)
+    st = compare(wl, gpu_render(wl), ref)
+    print("float error of the u8 workload", st)
+    assert st["max_abs"] < 2e-6
+
+
+def test_ragged_non_square_12bit():
+    flows = [W.fourier_flow(37, 53, 37, 53, rms=2.0, seed=11)]
+    p = _small(37, 53, 98, d_min=1.0, d_max=5.0, illum_min=0.7, illum_max=1.0, noise_sigma=0.02,
+               blur_sigma=0.7)
+    wl = _wl([p], flows, out_dtype="u16", quant_bits=12)
+    for tile in (16, 32):
+        compare(wl, gpu_render(wl, tile=tile), oracle_render(wl))
+
+
+def test_uneven_batch_mixed_sizes():
+    wl = W.uneven_batch(n_pairs=10, sizes=(48, 96, 160, 256))
+    st = compare(wl, gpu_render(wl), oracle_render(wl))
+    print("uneven", st)
+
+
+def test_flow_grid_coarser_than_image_and_euler():
+    flows = [W.fourier_flow(17, 23, 64, 80, rms=2.5, seed=2)]
+    p = _small(64, 80, 300, d_min=1.0, d_max=4.0, flow_index=0)
+    for integ, n in (("euler", 1), ("euler", 3), ("rk4", 2)):
+        wl = _wl([p], flows, integrator=integ, n_substeps=n, dt=1.5)
+        compare(wl, gpu_render(wl), oracle_render(wl))
+
+
+def test_shared_flow_f1_and_pair_ids():
+    # F = 1: three pairs read the same flow grid; pair ids decorrelate them
+    flows = [W.fourier_flow(128, 128, 128, 128, rms=3.0, seed=1000)]
+    pairs = [_small(128, 128, 800, pair_id=b, flow_index=0, d_min=1.0, d_max=4.0, illum_min=0.7,
+                    illum_max=1.0, noise_sigma=0.02, blur_sigma=0.7) for b in range(3)]
+    wl = _wl(pairs, flows, out_dtype="u8", quant_bits=8)
+    g = gpu_render(wl)
+    compare(wl, g, oracle_render(wl))
+    assert not np.array_equal(g[0], g[1])
+
+
+def test_large_tracers_and_wide_blur():
+    flows = [W.fourier_flow(72, 96, 72, 96, rms=4.0, seed=9)]
+    p = _small(72, 96, 60, d_min=4.0, d_max=10.0, illum_min=0.7, illum_max=1.0, noise_sigma=0.02,
+               blur_sigma=2.0)
+    wl = _wl([p], flows, out_dtype="u16", quant_bits=16)
+    compare(wl, gpu_render(wl, tile=32), oracle_render(wl))
+
+
+def test_clipped_normal_diameter_and_sheet():
+    flows = [W.lamb_oseen_flow(96, 96, 96, 96, gamma=150.0, core=12.0)]
+    p = _small(96, 96, 400, d_dist=1, d_min=1.0, d_max=4.0, d_mu=2.5, d_sigma=0.6, z_min=-1.0, z_max=1.0,
+               sheet_sigma=0.5)
+    wl = _wl([p], flows)
+    compare(wl, gpu_render(wl), oracle_render(wl))
+
+
+def test_float16_and_bfloat16_outputs():
+    wl = W.batch_512_u8(n_pairs=1)
+    wl.pairs[0] = W.PairSpec(**{**wl.pairs[0].__dict__, "height": 96, "width": 112, "n_particles": 500})
+    wl.flows = [W.fourier_flow(96, 112, 96, 112, rms=3.0, seed=1)]
+    ref = None
+    for od in ("f16", "bf16"):
+        wl.out_dtype, wl.quant_bits = od, 0
+        ref = ref or oracle_render(wl)
+        compare(wl, gpu_render(wl), ref, out_dtype=od)
+
+
+# ----------------------------------------------------------------------------
+# degenerate cases
+# ----------------------------------------------------------------------------
+
+def test_no_particles_gives_noise_only_frames():
+    flows = [W.zero_flow(40, 40)]
+    p = _small(40, 40, 0, noise_sigma=0.05, blur_sigma=0.7, illum_min=0.5, illum_max=1.0)
+    wl = _wl([p], flows)
+    compare(wl, gpu_render(wl), oracle_render(wl))
+
+
+def test_one_pixel_high_and_one_pixel_wide_frames():
+    for H, Wd in ((1, 300), (300, 1), (1, 1)):
+        flows = [W.fourier_flow(H, Wd, H, Wd, rms=1.0, seed=4) if H * Wd > 1 else W.uniform_flow(1, 1, 0.3, 0.2)]
+        p = _small(H, Wd, max(3, H * Wd // 20), d_min=1.0, d_max=4.0, blur_sigma=0.7, noise_sigma=0.01)
+        wl = _wl([p], flows)
+        compare(wl, gpu_render(wl, tile=16), oracle_render(wl))
+
+
+def test_particles_leaving_the_frame():
+    flows = [W.uniform_flow(48, 48, 40.0, -35.0)]
+    p = _small(48, 48, 200, d_min=1.0, d_max=4.0)
+    wl = _wl([p], flows, dt=1.0)
+    g = gpu_render(wl)
+    compare(wl, g, oracle_render(wl))
+    assert g[0][1].sum() < g[0][0].sum()
+
+
+def test_zero_flow_frames_identical_and_tile_invariance():
+    flows = [W.zero_flow(100, 70)]
+    p = _small(100, 70, 300, d_min=1.0, d_max=4.0, blur_sigma=0.7, illum_min=0.7, illum_max=1.0)
+    wl = _wl([p], flows)
+    outs = [gpu_render(wl, tile=t)[0] for t in (16, 32, 64)]
+    assert np.array_equal(outs[0][0], outs[0][1])
+    # fixed-point accumulation: the sum does not depend on the binning
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
+
+
+def test_pair_independent_of_batch_position():
+    wl = W.uneven_batch(n_pairs=6, sizes=(64, 96))
+    alone = gpu_render(wl.subset([3]))[0]
+    batched = gpu_render(wl)[3]
+    assert np.array_equal(alone, batched)
+
+
+def test_integer_translation_exact_shift_on_gpu():
+    H, Wd, a, b = 64, 72, 3, -2
+    flows = [W.uniform_flow(H, Wd, a, b)]
+    p = _small(H, Wd, 400, d_min=1.0, d_max=4.0)
+    wl = _wl([p], flows)
+    g = gpu_render(wl)[0]
+    m = abs(a) + 7, abs(b) + 7
+    s2 = g[1][m[1]:H - m[1], m[0]:Wd - m[0]]
+    s1 = g[0][m[1] - b:H - m[1] - b, m[0] - a:Wd - m[0] - a]
+    assert np.array_equal(s1, s2)
