@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the B300 PIV image-pair renderer.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+A step renders one batch of the workload the paper's throughput study uses
+(Section 3.1: 512x512 pairs; batch 64 as in the ablation defaults of
+Section 3.3) with every stage of the method: 64 pairs 512x512, ppp 0.05,
+d ~ U[1, 4], a distinct Fourier-mode flow per pair (rms 3 px/frame),
+illumination 0.7-1.0, noise 0.02, blur 0.7, 8-bit output.  Inputs are
+synthetic and seeded; the timed region starts with them resident in HBM.
+
+Timing: W untimed warm-up steps, then K steps, each preceded by an L2 flush
+(a 256 MiB write) outside its events; per-step device time from CUDA events
+recorded by the library on its stream at the start and end of the launch
+sequence.  One JSON line is printed by rank 0.
+
+`--impl reference` times the FP64 CPU oracle (the correctness reference) on
+the host cores on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "PIV image pairs/s at 512², ppp 0.05 (batched/FP16 vs plain FP32); % roofline"
+UNIT = "pairs/s"
+N_PAIRS = 64
+HBM_PEAK_FALLBACK = 6400.0  # GB/s, used only when MEASURED_PEAKS.json is absent
+SM_COUNT = 148
+FP32_LANES_PER_SM = 128
+
+# ncu DRAM traffic of k_splat_fused per launch (bytes), with the sha256 of the
+# kernel source it was taken on; reported only while the source is unchanged.
+SPLAT_TRAFFIC = {"sha256": None, "bytes_per_launch": None, "capture": None}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def workload(rank: int = 0):
+    from paper_2512_09664_b300 import workloads as W
+    wl = W.batch_512_u8(n_pairs=N_PAIRS, seed=1)
+    if rank:  # weak scaling: every rank renders its own 64 pairs
+        for p in wl.pairs:
+            p.pair_id += rank * N_PAIRS
+    return wl
+
+
+def workload_config(wl, extra=None):
+    cfg = {"workload": "batch64_512_u8: 64 pairs 512x512, ppp 0.05 (13107 particles/frame), d~U[1,4] px, "
+                       "I~U[0.8,1], z~U[-1,1] sheet 0.5, Fourier flow rms 3 px/frame (one grid per pair), "
+                       "RK4 x4 dt 1, illum 0.7-1.0, noise 0.02, blur 0.7, 8-bit",
+           "pairs_per_step": wl.n_pairs, "height": 512, "width": 512, "ppp": 0.05,
+           "l2": "flushed between steps (256 MiB write outside the timed events)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": HBM_PEAK_FALLBACK, "sm_max_mhz": 2032.0}, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# algorithmic work of the method (per pair), the roofline numerators
+# ----------------------------------------------------------------------------
+
+def algorithmic(wl):
+    """Bytes and FP32 lane-operations the method needs, summed over the batch.
+
+    bytes: both output frames written once + the FP32 flow grid read once.
+    lane-ops (minimum arithmetic of the method, an FMA counted once):
+      per particle and frame: (6 E[d] + 4) window edges x 12 (one Phi value:
+      a degree-8 polynomial, the exp, scaling) + E[(3d + 1)^2] pixels x 2
+      (product and accumulation);
+      per output pixel: illumination 1, noise 13 (a quarter of a 10-round
+      Philox call at 4 ops per round plus half a Box-Muller pair),
+      blur 2 (2R + 1), quantisation 2.
+    """
+    nbytes, ops = 0, 0.0
+    osize = {"u8": 1, "u16": 2, "f16": 2, "bf16": 2, "f32": 4}[wl.out_dtype]
+    for p in wl.pairs:
+        g = wl.flows[p.flow_index]
+        nbytes += 2 * p.height * p.width * osize
+        lo, hi = float(p.d_min), float(p.d_max)
+        ed, ed2 = (lo + hi) / 2, (lo * lo + lo * hi + hi * hi) / 3
+        edges = 6 * ed + 4
+        pixels = 9 * ed2 + 6 * ed + 1
+        ops += 2 * p.n_particles * (12 * edges + 2 * pixels)
+        R = math.ceil(3 * float(p.blur_sigma)) if p.blur_sigma > 0 else 0
+        per_px = 1 + (13 if p.noise_sigma > 0 else 0) + (2 * (2 * R + 1) if R else 0) + 2
+        ops += 2 * p.height * p.width * per_px
+    flow_bytes = sum(f.size * 4 for f in wl.flows)
+    return nbytes + flow_bytes, ops
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait(timeout=5)
+            self.fh.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows]
+        mx = max(float(r[2]) for r in rows)
+        load = [s for s in sm if s > 0.5 * mx] or sm
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3] not in ("", "[N/A]"))}
+
+
+# ----------------------------------------------------------------------------
+# CPU arms (oracle)
+# ----------------------------------------------------------------------------
+
+def oracle_sample(wl, n_pairs: int, start: int, threads: int):
+    import oracle
+    idx = [(start + k) % wl.n_pairs for k in range(n_pairs)]
+    t0 = time.perf_counter()
+    oracle.render_workload(wl, pairs=idx, threads=threads)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(wl, seconds: float):
+    cores = os.cpu_count() or 1
+    threads = min(cores, wl.n_pairs)
+    done, elapsed, start = 0, 0.0, 0
+    while elapsed < seconds:
+        elapsed += oracle_sample(wl, threads, start, threads)
+        done += threads
+        start += threads
+    return {"value": done / elapsed, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{done} pairs of the same workload (FP64 C oracle, {threads} host threads, "
+                      f"{elapsed:.1f} s)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    wl = workload()
+    cores = os.cpu_count() or 1
+    threads = min(cores, wl.n_pairs)
+    for w in range(args.warmup):
+        oracle_sample(wl, threads, w * threads, threads)
+    total = 0.0
+    for k in range(args.steps):
+        total += oracle_sample(wl, threads, k * threads, threads)
+    value = args.steps * threads / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": workload_config(wl, {"step": f"{threads} pairs of the workload per step"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{threads} pairs per step, {args.steps} steps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+
+def splat_source_hash():
+    with open(os.path.join(ROOT, "paper_2512_09664_b300", "csrc", "kernels.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def run_ours(args, rank, world, dist):
+    import torch
+
+    from paper_2512_09664_b300.binding import STAGES, Renderer
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    wl = workload(rank)
+    r = Renderer(wl, device=dev, tile=args.tile)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def new_events():
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        for e in evs:
+            e.record(stream)  # creates the CUDA event
+        return evs
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        r.render()
+    torch.cuda.synchronize()
+    events = [new_events() for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            r.render_staged(events[k])
+        torch.cuda.synchronize()
+        barrier()
+    clocks = clk.summary()
+    step_ms = [ev[0].elapsed_time(ev[5]) for ev in events]
+    stage_ms = {name: sum(ev[i].elapsed_time(ev[i + 1]) for ev in events) / args.steps
+                for i, name in enumerate(STAGES)}
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * wl.n_pairs * args.steps / (total_ms / 1e3)
+    ms_per_step = total_ms / args.steps
+
+    # end to end through the same C ABI: pinned host flows in, images out
+    flows_host = torch.from_numpy(r.pk.flows_host).pin_memory()
+    img_host = torch.empty(r.images.shape, dtype=r.images.dtype).pin_memory()
+    e2e_steps = max(3, min(args.steps, 30))
+    for _ in range(2):
+        r.flows.copy_(flows_host, non_blocking=True)
+        r.render()
+        img_host.copy_(r.images, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        r.flows.copy_(flows_host, non_blocking=True)
+        r.render()
+        img_host.copy_(r.images, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    h2d = flows_host.numel() * flows_host.element_size()
+    d2h = img_host.numel() * img_host.element_size()
+
+    # plain FP32 per-pair path: one launch sequence per pair, FP32 output
+    from paper_2512_09664_b300 import workloads as W
+    plain = [Renderer(wl.subset([b]), device=dev, tile=args.tile, out_dtype="f32") for b in range(wl.n_pairs)]
+    for p in plain:
+        p.render()
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    p0.record(stream)
+    for _ in range(reps):
+        for p in plain:
+            p.render()
+    p1.record(stream)
+    torch.cuda.synchronize()
+    plain_pairs_s = reps * wl.n_pairs / (p0.elapsed_time(p1) / 1e3)
+    del plain
+
+    peaks, peak_kind = measured_peaks()
+    alg_bytes, alg_ops = algorithmic(wl)
+    splat_ms = stage_ms["splat_epilogue"]
+    sm_mhz = float(peaks.get("sm_max_mhz", 2032.0))
+    alu_peak = SM_COUNT * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12  # T lane-op/s
+    # the epilogue and splat work run in the splat kernel; seeding/advection
+    # arithmetic is not counted there
+    achieved = alg_ops / (splat_ms / 1e3) / 1e12
+    traffic = None
+    if SPLAT_TRAFFIC["sha256"] == splat_source_hash():
+        traffic = SPLAT_TRAFFIC["bytes_per_launch"]
+    hbm_peak = float(peaks["hbm_gbs"])
+    step_gbs = alg_bytes / (ms_per_step / 1e3) / 1e9
+    launches_per_step = 5  # k_plan, k_seed_advect, k_scan, k_scatter, k_splat_fused
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(wl, {"tile": r.pk.batch.tile or 32, "parallelism": f"replicas x{world}"}),
+        "mpx_per_s": value * 2 * 512 * 512 / 1e6,
+        "stage_ms": stage_ms,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tlane-op/s",
+                     "frac": achieved / alu_peak, "traffic": traffic, "kernel": "k_splat_fused",
+                     "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_mhz:.0f} MHz"},
+        "step_roofline_hbm": {"achieved_gbs": step_gbs, "peak_gbs": hbm_peak, "frac": step_gbs / hbm_peak,
+                              "peak_source": peak_kind, "algorithmic_bytes_per_step": alg_bytes},
+        "plain_fp32_per_pair": {"value": plain_pairs_s, "unit": UNIT, "speedup": value / world / plain_pairs_s},
+        "e2e": {"value": world * wl.n_pairs / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        tdist.init_process_group("nccl")
+        dist = tdist
+    run_ours(args, rank, world, dist)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -147,6 +147,23 @@ int synthpix_render_pairs(const synthpix_batch_desc *batch, const synthpix_pair_
                           const float *flows, void *images,
                           void *workspace, size_t workspace_bytes, void *stream);
 
+/*
+ * synthpix_render_pairs plus per-stage timing: stage_events holds 6 CUDA
+ * events (cudaEvent_t, created by the caller; NULL entries are skipped) that
+ * are recorded on `stream` at the stage boundaries, so the caller can time
+ * each kernel with cudaEventElapsedTime after synchronising:
+ *   [0] before the plan kernel, [1] after the plan and the bin reset,
+ *   [2] after seeding + advection, [3] after the bin scan,
+ *   [4] after the bin scatter, [5] after the splat + epilogue kernel.
+ * The paper has no counterpart; it exists for measurement.  Same arguments,
+ * errors and asynchrony as synthpix_render_pairs; no synchronisation.
+ */
+int synthpix_render_pairs_staged(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
+                                 const synthpix_pair_desc *pairs_dev, int32_t n_pairs,
+                                 const float *flows, void *images,
+                                 void *workspace, size_t workspace_bytes, void *stream,
+                                 void *const *stage_events);
+
 /* Message of the last failing call on this host thread ("" if none). */
 const char *synthpix_last_error(void);
 

@@ -21,7 +21,9 @@ LIB_PATH = os.path.join(_PKG, "libsynthpix.so")
 OK, EINVAL, EWORKSPACE, ECUDA, EUNSUPPORTED = 0, -1, -2, -3, -4
 DTYPE_CODE = {"f32": 0, "f16": 1, "bf16": 2, "u8": 3, "u16": 4}
 INTEGRATOR_CODE = {"rk4": 0, "euler": 1}
-_EXPORTS = ("synthpix_workspace_bytes", "synthpix_render_pairs", "synthpix_last_error", "synthpix_version")
+_EXPORTS = ("synthpix_workspace_bytes", "synthpix_render_pairs", "synthpix_render_pairs_staged",
+            "synthpix_last_error", "synthpix_version")
+STAGES = ("plan", "seed_advect", "bin_scan", "bin_scatter", "splat_epilogue")
 
 
 class PairDesc(C.Structure):
@@ -71,6 +73,9 @@ def lib():
         L.synthpix_render_pairs.argtypes = [C.POINTER(BatchDesc), C.POINTER(PairDesc), vp, C.c_int32,
                                             vp, vp, vp, sz, vp]
         L.synthpix_render_pairs.restype = C.c_int
+        L.synthpix_render_pairs_staged.argtypes = [C.POINTER(BatchDesc), C.POINTER(PairDesc), vp, C.c_int32,
+                                                   vp, vp, vp, sz, vp, C.POINTER(C.c_void_p)]
+        L.synthpix_render_pairs_staged.restype = C.c_int
         L.synthpix_last_error.argtypes = []
         L.synthpix_last_error.restype = C.c_char_p
         L.synthpix_version.argtypes = []
@@ -185,6 +190,20 @@ def render_pairs(pk: Packed, flows_dev, images_dev, workspace_dev, pairs_dev=Non
     _check(rc)
 
 
+def render_pairs_staged(pk: Packed, flows_dev, images_dev, workspace_dev, events, pairs_dev=None,
+                        stream=None) -> None:
+    """render_pairs recording 6 torch.cuda.Events (already created) at the stage boundaries."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    arr = (C.c_void_p * 6)(*[C.c_void_p(e.cuda_event) if e is not None else None for e in events])
+    rc = lib().synthpix_render_pairs_staged(
+        C.byref(pk.batch), pk.pairs, C.c_void_p(pairs_dev.data_ptr()) if pairs_dev is not None else None,
+        pk.n_pairs, C.c_void_p(flows_dev.data_ptr()), C.c_void_p(images_dev.data_ptr()),
+        C.c_void_p(workspace_dev.data_ptr()), workspace_dev.numel() * workspace_dev.element_size(),
+        C.c_void_p(st.cuda_stream), arr)
+    _check(rc)
+
+
 class Renderer:
     """Device buffers for repeated rendering of one packed workload."""
 
@@ -205,6 +224,10 @@ class Renderer:
 
     def render(self, stream=None):
         render_pairs(self.pk, self.flows, self.images, self.workspace, self.pairs_dev, stream)
+        return self.images
+
+    def render_staged(self, events, stream=None):
+        render_pairs_staged(self.pk, self.flows, self.images, self.workspace, events, self.pairs_dev, stream)
         return self.images
 
     def frames(self, b: int):

@@ -159,9 +159,11 @@ size_t synthpix_workspace_bytes(const synthpix_batch_desc *batch, const synthpix
     return P.L.total;
 }
 
-int synthpix_render_pairs(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
-                          const synthpix_pair_desc *pairs_dev, int32_t n_pairs, const float *flows, void *images,
-                          void *workspace, size_t workspace_bytes, void *stream) {
+}  // extern "C"
+
+static int render_impl(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
+                       const synthpix_pair_desc *pairs_dev, int32_t n_pairs, const float *flows, void *images,
+                       void *workspace, size_t workspace_bytes, void *stream, cudaEvent_t const *ev) {
     Plan P;
     int rc = make_plan(batch, pairs, n_pairs, P);
     if (rc) return rc;
@@ -192,10 +194,12 @@ int synthpix_render_pairs(const synthpix_batch_desc *batch, const synthpix_pair_
     spx::PairPlan *plan = reinterpret_cast<spx::PairPlan *>(ws + L.plan);
     int32_t *check = reinterpret_cast<int32_t *>(ws + L.check);
     float *blur_w = reinterpret_cast<float *>(ws + L.blur);
+    if (ev && ev[0]) cudaEventRecord(ev[0], st);
     e = spx::launch_plan(descs, n_pairs, P.tile, P.fused, plan, L, check, blur_w, st);
     if (e != cudaSuccess) return fail(SYNTHPIX_ECUDA, "plan launch: %s", cudaGetErrorString(e));
     e = cudaMemsetAsync(ws + L.count, 0, (size_t)L.n_tiles * 4, st);
     if (e != cudaSuccess) return fail(SYNTHPIX_ECUDA, "count reset: %s", cudaGetErrorString(e));
+    if (ev && ev[1]) cudaEventRecord(ev[1], st);
 
     spx::KernelArgs a;
     a.descs = descs;
@@ -226,10 +230,26 @@ int synthpix_render_pairs(const synthpix_batch_desc *batch, const synthpix_pair_
     if (spx::splat_smem_bytes(a.smem_edge, a.tile, a.warp_scratch) > 227 * 1024)
         return fail(SYNTHPIX_EUNSUPPORTED, "tile %d with blur radius %d needs too much shared memory", P.tile,
                     P.max_halo);
-    e = spx::launch_render(a, batch->out_dtype, st);
+    e = spx::launch_render(a, batch->out_dtype, st, ev);
     if (e != cudaSuccess) return fail(SYNTHPIX_ECUDA, "render launch: %s", cudaGetErrorString(e));
     g_err[0] = 0;
     return SYNTHPIX_OK;
+}
+
+extern "C" {
+
+int synthpix_render_pairs(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
+                          const synthpix_pair_desc *pairs_dev, int32_t n_pairs, const float *flows, void *images,
+                          void *workspace, size_t workspace_bytes, void *stream) {
+    return render_impl(batch, pairs, pairs_dev, n_pairs, flows, images, workspace, workspace_bytes, stream, nullptr);
+}
+
+int synthpix_render_pairs_staged(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
+                                 const synthpix_pair_desc *pairs_dev, int32_t n_pairs, const float *flows,
+                                 void *images, void *workspace, size_t workspace_bytes, void *stream,
+                                 void *const *stage_events) {
+    return render_impl(batch, pairs, pairs_dev, n_pairs, flows, images, workspace, workspace_bytes, stream,
+                       reinterpret_cast<cudaEvent_t const *>(stage_events));
 }
 
 }  // extern "C"

@@ -669,14 +669,23 @@ cudaError_t launch_plan(const synthpix_pair_desc *descs, int32_t n_pairs, int32_
     return cudaGetLastError();
 }
 
-cudaError_t launch_render(const KernelArgs &a, int32_t out_dtype, cudaStream_t st) {
+cudaError_t launch_render(const KernelArgs &a, int32_t out_dtype, cudaStream_t st, cudaEvent_t const *ev) {
+    auto mark = [&](int k) {
+        if (ev && ev[k]) cudaEventRecord(ev[k], st);
+    };
     if (a.n_part > 0) {
         const unsigned nb = (unsigned)((a.n_part + 255) / 256);
         k_seed_advect<<<nb, 256, 0, st>>>(a);
+        mark(2);
         k_scan<<<2 * a.n_pairs, 1024, 0, st>>>(a);
+        mark(3);
         k_scatter<<<nb, 256, 0, st>>>(a);
+        mark(4);
     } else {
+        mark(2);
         k_scan<<<2 * a.n_pairs, 1024, 0, st>>>(a);
+        mark(3);
+        mark(4);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -696,6 +705,7 @@ cudaError_t launch_render(const KernelArgs &a, int32_t out_dtype, cudaStream_t s
     default: SPX_LAUNCH(uint16_t); break;
     }
 #undef SPX_LAUNCH
+    mark(5);
     return cudaGetLastError();
 }
 

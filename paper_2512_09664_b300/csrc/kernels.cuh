@@ -32,7 +32,9 @@ struct KernelArgs {
 
 cudaError_t launch_plan(const synthpix_pair_desc *descs, int32_t n_pairs, int32_t tile, int32_t fused,
                         PairPlan *plan, const Layout &L, int32_t *check, float *blur_w, cudaStream_t st);
-cudaError_t launch_render(const KernelArgs &a, int32_t out_dtype, cudaStream_t st);
+// ev: NULL or kStageEvents events recorded at the stage boundaries.
+cudaError_t launch_render(const KernelArgs &a, int32_t out_dtype, cudaStream_t st, cudaEvent_t const *ev);
+constexpr int kStageEvents = 6;
 size_t splat_smem_bytes(int edge, int tile, int warp_scratch);
 
 }  // namespace spx
