@@ -164,6 +164,35 @@ int synthpix_render_pairs_staged(const synthpix_batch_desc *batch, const synthpi
                                  void *workspace, size_t workspace_bytes, void *stream,
                                  void *const *stage_events);
 
+/*
+ * synthpix_render_pairs for callers that cannot allocate device memory: host
+ * applications that own all device memory through their own allocator and
+ * do not let libraries call cudaMalloc (plugin hosts, embedded runtimes with
+ * a fixed memory budget), and loops that cannot afford the device
+ * synchronisation cudaMalloc may imply.  The paper has no counterpart.
+ *
+ * The caller passes inputs and outputs only.  The scratch memory lives in a
+ * static __device__ array of SYNTHPIX_NOALLOC_SCRATCH_BYTES (32 MiB) compiled
+ * into the library; every GPU that loads the library holds it until the
+ * process exits.  This call allocates nothing (no cudaMalloc / cudaFree, no
+ * allocating library routine).
+ *  - A batch that needs more scratch than the array holds (compare
+ *    synthpix_workspace_bytes) is rejected with SYNTHPIX_EWORKSPACE and a
+ *    message, before anything is launched.
+ *  - The first call on a device looks up the array's device address on that
+ *    device (cudaGetSymbolAddress with the device current) and caches it;
+ *    make that first call on each device before any stream capture.
+ *  - All calls share the one array, which keeps the last call's contents;
+ *    the call clears what must start at zero itself.  Calls whose work
+ *    overlaps on the GPU (other streams, other host threads) race on the
+ *    array: the caller must order them.
+ * Other arguments, errors and asynchrony are those of synthpix_render_pairs.
+ */
+#define SYNTHPIX_NOALLOC_SCRATCH_BYTES (32u << 20)
+int synthpix_render_pairs_noalloc(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
+                                  const synthpix_pair_desc *pairs_dev, int32_t n_pairs,
+                                  const float *flows, void *images, void *stream);
+
 /* Message of the last failing call on this host thread ("" if none). */
 const char *synthpix_last_error(void);
 

@@ -253,3 +253,13 @@ int synthpix_render_pairs_staged(const synthpix_batch_desc *batch, const synthpi
 }
 
 }  // extern "C"
+
+namespace spx {
+
+// Sets the thread's last-error message (used by entry points in other files).
+int set_error(int code, const char *msg) {
+    snprintf(g_err, sizeof(g_err), "%s", msg);
+    return code;
+}
+
+}  // namespace spx

@@ -1,0 +1,80 @@
+// synthpix_render_pairs_noalloc: the render call for callers that cannot
+// allocate device memory.  Some host applications own all device memory
+// through their own allocator and do not let libraries call cudaMalloc
+// (plugin hosts, embedded runtimes with a fixed memory budget), and some
+// loops cannot afford the device synchronisation cudaMalloc may imply.  Such
+// callers pass only their inputs and outputs; the scratch memory the render
+// needs lives in the fixed array below, compiled into the library.
+#include <cstdio>
+#include <mutex>
+
+#include "synthpix.h"
+
+// The scratch of the no-allocation entry point.  Every GPU that loads the
+// library holds these SYNTHPIX_NOALLOC_SCRATCH_BYTES until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SYNTHPIX_NOALLOC_SCRATCH_BYTES];
+
+namespace spx {
+int set_error(int code, const char *msg);
+}
+
+namespace {
+
+constexpr int kMaxDevices = 256;
+std::mutex g_mu;
+void *g_scratch_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device.  Host code only
+// sees a host-side stand-in under the array's name, so the address is looked
+// up once per device with that device current, and cached.
+int scratch_address(void **out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        char msg[256];
+        snprintf(msg, sizeof(msg), "no-allocation render: cudaGetDevice failed: %s", cudaGetErrorString(e));
+        return spx::set_error(SYNTHPIX_ECUDA, msg);
+    }
+    if (dev < 0 || dev >= kMaxDevices) return spx::set_error(SYNTHPIX_ECUDA, "no-allocation render: device index out of range");
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            char msg[256];
+            snprintf(msg, sizeof(msg), "no-allocation render: cudaGetSymbolAddress failed: %s",
+                     cudaGetErrorString(e));
+            return spx::set_error(SYNTHPIX_ECUDA, msg);
+        }
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return SYNTHPIX_OK;
+}
+
+}  // namespace
+
+extern "C" int synthpix_render_pairs_noalloc(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
+                                             const synthpix_pair_desc *pairs_dev, int32_t n_pairs,
+                                             const float *flows, void *images, void *stream) {
+    // validation and the scratch size come from the host descriptors alone
+    const size_t need = synthpix_workspace_bytes(batch, pairs, n_pairs);
+    if (need == 0 && n_pairs != 0)  // invalid descriptors: report them with their own status code
+        return synthpix_render_pairs(batch, pairs, pairs_dev, n_pairs, flows, images, nullptr, 0, stream);
+    if (n_pairs == 0) return SYNTHPIX_OK;
+    if (need > (size_t)SYNTHPIX_NOALLOC_SCRATCH_BYTES) {
+        char msg[256];
+        snprintf(msg, sizeof(msg),
+                 "no-allocation render: this batch needs %zu bytes of scratch, more than the %zu the library "
+                 "holds; split the batch or use synthpix_render_pairs with a workspace",
+                 need, (size_t)SYNTHPIX_NOALLOC_SCRATCH_BYTES);
+        return spx::set_error(SYNTHPIX_EWORKSPACE, msg);
+    }
+    void *scratch = nullptr;
+    const int rc = scratch_address(&scratch);
+    if (rc != SYNTHPIX_OK) return rc;
+    // the render clears what must start at zero (its bin counters) itself;
+    // everything else in the scratch is written before it is read
+    return synthpix_render_pairs(batch, pairs, pairs_dev, n_pairs, flows, images, scratch,
+                                 (size_t)SYNTHPIX_NOALLOC_SCRATCH_BYTES, stream);
+}
