@@ -124,7 +124,8 @@ size_t synthpix_workspace_bytes(const synthpix_batch_desc *batch,
  *
  *   batch      host pointer, batch settings.
  *   pairs      host pointer, n_pairs descriptors; read during the call only.
- *   pairs_dev  NULL, or a device copy of the same n_pairs descriptors.  With
+ *   pairs_dev  NULL, or a 16-byte aligned device copy of the same n_pairs
+ *              descriptors.  With
  *              NULL the library copies `pairs` into the workspace with
  *              cudaMemcpyAsync on `stream` (keep `pairs` unchanged until the
  *              stream reaches the copy if it is pinned memory).  Passing a

@@ -124,9 +124,10 @@ int make_plan(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
     L.count = take((size_t)L.n_tiles * 4);
     L.off = take((size_t)L.n_tiles * 4);
     L.cursor = take((size_t)L.n_tiles * 4);
+    L.items = take((size_t)L.n_tiles * sizeof(spx::ItemInfo));
     L.pos = take((size_t)L.n_part * 32);
     L.sa = take((size_t)L.n_part * 8);
-    L.list = take((size_t)L.n_list * 4);
+    L.rec = take((size_t)L.n_list * sizeof(spx::Record) + 64);  // + read-over of 16-byte staging
     L.inter = take((size_t)L.n_inter * 2);
     L.total = o;
     return SYNTHPIX_OK;
@@ -178,7 +179,7 @@ static int render_impl(const synthpix_batch_desc *batch, const synthpix_pair_des
         return fail(SYNTHPIX_EWORKSPACE, "workspace is NULL or not 256-byte aligned");
     if (workspace_bytes < P.L.total)
         return fail(SYNTHPIX_EWORKSPACE, "workspace has %zu bytes, %zu needed", workspace_bytes, P.L.total);
-    if (pairs_dev && ((uintptr_t)pairs_dev & 7)) return fail(SYNTHPIX_EINVAL, "pairs_dev is not 8-byte aligned");
+    if (pairs_dev && ((uintptr_t)pairs_dev & 15)) return fail(SYNTHPIX_EINVAL, "pairs_dev is not 16-byte aligned");
 
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     unsigned char *ws = static_cast<unsigned char *>(workspace);
@@ -193,9 +194,10 @@ static int render_impl(const synthpix_batch_desc *batch, const synthpix_pair_des
     }
     spx::PairPlan *plan = reinterpret_cast<spx::PairPlan *>(ws + L.plan);
     int32_t *check = reinterpret_cast<int32_t *>(ws + L.check);
+    uint32_t *ticket = reinterpret_cast<uint32_t *>(ws + L.check + 16);
     float *blur_w = reinterpret_cast<float *>(ws + L.blur);
     if (ev && ev[0]) cudaEventRecord(ev[0], st);
-    e = spx::launch_plan(descs, n_pairs, P.tile, P.fused, plan, L, check, blur_w, st);
+    e = spx::launch_plan(descs, n_pairs, P.tile, P.fused, plan, L, check, blur_w, ticket, st);
     if (e != cudaSuccess) return fail(SYNTHPIX_ECUDA, "plan launch: %s", cudaGetErrorString(e));
     e = cudaMemsetAsync(ws + L.count, 0, (size_t)L.n_tiles * 4, st);
     if (e != cudaSuccess) return fail(SYNTHPIX_ECUDA, "count reset: %s", cudaGetErrorString(e));
@@ -222,16 +224,21 @@ static int render_impl(const synthpix_batch_desc *batch, const synthpix_pair_des
     a.count = reinterpret_cast<uint32_t *>(ws + L.count);
     a.off = reinterpret_cast<uint32_t *>(ws + L.off);
     a.cursor = reinterpret_cast<uint32_t *>(ws + L.cursor);
-    a.list = reinterpret_cast<uint32_t *>(ws + L.list);
+    a.items = reinterpret_cast<spx::ItemInfo *>(ws + L.items);
+    a.rec = reinterpret_cast<spx::Record *>(ws + L.rec);
+    a.ticket = ticket;
+    a.rec_buf_bytes = 8192;
     a.blur_w = blur_w;
     a.smem_edge = P.tile + 2 * P.max_halo;
     const int wmax = std::min(spx::window_max(P.max_d), a.smem_edge);
     a.warp_scratch = 4 * (wmax + 2);
-    if (spx::splat_smem_bytes(a.smem_edge, a.tile, a.warp_scratch) > 227 * 1024)
+    if (spx::splat_smem_bytes(a.smem_edge, a.tile, a.warp_scratch, a.rec_buf_bytes) > 227 * 1024)
         return fail(SYNTHPIX_EUNSUPPORTED, "tile %d with blur radius %d needs too much shared memory", P.tile,
                     P.max_halo);
-    e = spx::launch_render(a, batch->out_dtype, st, ev);
-    if (e != cudaSuccess) return fail(SYNTHPIX_ECUDA, "render launch: %s", cudaGetErrorString(e));
+    e = spx::launch_prep(a, st, ev);
+    if (e != cudaSuccess) return fail(SYNTHPIX_ECUDA, "seeding/binning launch: %s", cudaGetErrorString(e));
+    e = spx::launch_splat(a, batch->out_dtype, st, ev);
+    if (e != cudaSuccess) return fail(SYNTHPIX_ECUDA, "splat launch: %s", cudaGetErrorString(e));
     g_err[0] = 0;
     return SYNTHPIX_OK;
 }

@@ -59,9 +59,25 @@ __host__ __device__ inline PairGeom pair_geom(const synthpix_pair_desc &d, int t
     return g;
 }
 
+// A particle as binned for one frame: split position, sigma, amplitude.
+struct Record {
+    float fx, fy;      // fractions of the split position
+    int32_t ix, iy;    // integer parts
+    float sigma, amp;  // d / 4 and Ieff * 2 pi sigma^2
+};
+static_assert(sizeof(Record) == 24, "Record layout");
+
+// One work item of the splat: the bin of one (pair, frame, tile).
+struct ItemInfo {
+    int32_t pair, frame, tile;
+    uint32_t count;  // records in the bin
+    int64_t rec0;    // first record of the bin
+};
+static_assert(sizeof(ItemInfo) == 24, "ItemInfo layout");
+
 // Workspace layout (byte offsets, 256-aligned), computed on the host.
 struct Layout {
-    size_t plan, desc, check, blur, count, off, cursor, pos, sa, list, inter, total;
+    size_t plan, desc, check, blur, count, off, cursor, items, pos, sa, rec, inter, total;
     int64_t n_part, n_tiles, n_list, n_inter;
 };
 

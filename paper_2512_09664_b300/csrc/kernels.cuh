@@ -1,4 +1,5 @@
-// Launch interface between the host entry points (api.cu) and the kernels.
+// Launch interface between the host entry points (api.cu) and the kernels
+// (prep.cu: plan, seeding + advection, binning; splat.cu: the splat).
 #pragma once
 
 #include "common.cuh"
@@ -7,13 +8,13 @@ namespace spx {
 
 // Everything one render launch sequence reads or writes (passed by value).
 struct KernelArgs {
-    const synthpix_pair_desc *descs;  // device copy of the descriptors
+    const synthpix_pair_desc *descs;  // device copy of the descriptors (16-byte aligned)
     const PairPlan *plan;             // device plan (k_plan)
     const int32_t *check;             // 1 when the device plan matches the host's
     int32_t n_pairs;
     int32_t tile;
     int64_t n_part;                   // particles of all pairs
-    int64_t n_tiles;                  // (pair, frame, tile) items
+    int64_t n_tiles;                  // (pair, frame, tile) work items
     uint64_t seed;
     float dt;
     int32_t n_substeps;
@@ -24,17 +25,26 @@ struct KernelArgs {
     float4 *pos0, *pos1;              // split positions of frames 1 and 2
     float2 *sa;                       // (sigma, Ieff * 2 pi sigma^2)
     uint32_t *count, *off, *cursor;   // per (pair, frame, tile)
-    uint32_t *list;                   // bin lists
+    ItemInfo *items;                  // per (pair, frame, tile): the splat's work items
+    Record *rec;                      // bins
+    uint32_t *ticket;                 // work-queue counter of the persistent splat
     int32_t smem_edge;                // capacity edge of the on-chip tile (tile + 2 max radius)
     int32_t warp_scratch;             // floats of per-warp window scratch
     const float *blur_w;              // [n_pairs][kBlurStride] normalised taps w[|k|]
+    int32_t rec_buf_bytes;            // bytes of each staged-records buffer
 };
 
-cudaError_t launch_plan(const synthpix_pair_desc *descs, int32_t n_pairs, int32_t tile, int32_t fused,
-                        PairPlan *plan, const Layout &L, int32_t *check, float *blur_w, cudaStream_t st);
-// ev: NULL or kStageEvents events recorded at the stage boundaries.
-cudaError_t launch_render(const KernelArgs &a, int32_t out_dtype, cudaStream_t st, cudaEvent_t const *ev);
 constexpr int kStageEvents = 6;
-size_t splat_smem_bytes(int edge, int tile, int warp_scratch);
+constexpr int kSplatThreads = 256;
+constexpr int kSplatWarps = kSplatThreads / 32;
+constexpr int kStageHeader = 320;     // descriptor (128) + plan (64) + blur taps (128)
+
+cudaError_t launch_plan(const synthpix_pair_desc *descs, int32_t n_pairs, int32_t tile, int32_t fused,
+                        PairPlan *plan, const Layout &L, int32_t *check, float *blur_w, uint32_t *ticket,
+                        cudaStream_t st);
+// ev: NULL or kStageEvents events recorded at the stage boundaries.
+cudaError_t launch_prep(const KernelArgs &a, cudaStream_t st, cudaEvent_t const *ev);
+cudaError_t launch_splat(const KernelArgs &a, int32_t out_dtype, cudaStream_t st, cudaEvent_t const *ev);
+size_t splat_smem_bytes(int edge, int tile, int warp_scratch, int rec_buf_bytes);
 
 }  // namespace spx
