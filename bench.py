@@ -42,8 +42,9 @@ HBM_PEAK_FALLBACK = 6400.0  # GB/s, used only when MEASURED_PEAKS.json is absent
 SM_COUNT = 148
 FP32_LANES_PER_SM = 128
 
-# ncu DRAM traffic of k_splat_fused per launch (bytes), with the sha256 of the
-# kernel source it was taken on; reported only while the source is unchanged.
+# ncu DRAM traffic of k_splat per launch (bytes), with the sha256 of the
+# kernel source (splat.cu) it was taken on; reported only while the source is
+# unchanged.
 SPLAT_TRAFFIC = {"sha256": None, "bytes_per_launch": None, "capture": None}
 
 
@@ -53,7 +54,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--tile", type=int, default=0, help="0: autotune")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
@@ -225,7 +226,7 @@ def run_reference(args, rank, world):
 # ----------------------------------------------------------------------------
 
 def splat_source_hash():
-    with open(os.path.join(ROOT, "paper_2512_09664_b300", "csrc", "kernels.cu"), "rb") as f:
+    with open(os.path.join(ROOT, "paper_2512_09664_b300", "csrc", "splat.cu"), "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()
 
 
@@ -238,6 +239,8 @@ def run_ours(args, rank, world, dist):
     wl = workload(rank)
     r = Renderer(wl, device=dev, tile=args.tile)
     stream = torch.cuda.current_stream()
+    if args.tile == 0:
+        r.autotune(reps=2)
 
     def barrier():
         if dist is not None:
@@ -275,6 +278,41 @@ def run_ours(args, rank, world, dist):
         total_ms = float(t.item())
     value = world * wl.n_pairs * args.steps / (total_ms / 1e3)
     ms_per_step = total_ms / args.steps
+
+    # the same step replayed from a captured CUDA graph (no host launch cost)
+    r.capture()
+    for _ in range(2):
+        r.replay()
+    torch.cuda.synchronize()
+    g_ms = 0.0
+    for k in range(min(args.steps, 50)):
+        flush.fill_(k & 0xFF)
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        r.replay()
+        g1.record(stream)
+        g1.synchronize()
+        g_ms += g0.elapsed_time(g1)
+    graph_ms = g_ms / min(args.steps, 50)
+
+    # the batched path with FP16 intermediate frames (splat, then a separate
+    # finishing kernel reading the 16-bit frames)
+    r16 = Renderer(wl, device=dev, tile=r.pk.batch.tile, inter_dtype="f16")
+    for _ in range(3):
+        r16.render()
+    torch.cuda.synchronize()
+    f_ms = 0.0
+    nf = min(args.steps, 50)
+    for k in range(nf):
+        flush.fill_(k & 0xFF)
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        r16.render()
+        h1.record(stream)
+        h1.synchronize()
+        f_ms += h0.elapsed_time(h1)
+    f16_ms = f_ms / nf
+    del r16
 
     # end to end through the same C ABI: pinned host flows in, images out
     flows_host = torch.from_numpy(r.pk.flows_host).pin_memory()
@@ -328,20 +366,24 @@ def run_ours(args, rank, world, dist):
         traffic = SPLAT_TRAFFIC["bytes_per_launch"]
     hbm_peak = float(peaks["hbm_gbs"])
     step_gbs = alg_bytes / (ms_per_step / 1e3) / 1e9
-    launches_per_step = 5  # k_plan, k_seed_advect, k_scan, k_scatter, k_splat_fused
+    launches_per_step = 5  # k_plan, k_seed_advect, k_scan, k_scatter, k_splat
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_config(wl, {"tile": r.pk.batch.tile or 32, "parallelism": f"replicas x{world}"}),
+        "config": workload_config(wl, {"tile": r.pk.batch.tile, "tile_choice": "autotuned" if args.tile == 0
+                                       else "fixed", "path": "fused FP32 splat + epilogue (on-chip intermediate)",
+                                       "parallelism": f"replicas x{world}"}),
         "mpx_per_s": value * 2 * 512 * 512 / 1e6,
         "stage_ms": stage_ms,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tlane-op/s",
-                     "frac": achieved / alu_peak, "traffic": traffic, "kernel": "k_splat_fused",
+                     "frac": achieved / alu_peak, "traffic": traffic, "kernel": "k_splat",
                      "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_mhz:.0f} MHz"},
         "step_roofline_hbm": {"achieved_gbs": step_gbs, "peak_gbs": hbm_peak, "frac": step_gbs / hbm_peak,
                               "peak_source": peak_kind, "algorithmic_bytes_per_step": alg_bytes},
         "plain_fp32_per_pair": {"value": plain_pairs_s, "unit": UNIT, "speedup": value / world / plain_pairs_s},
+        "batched_f16_intermediate": {"value": wl.n_pairs / (f16_ms / 1e3), "unit": UNIT, "ms_per_step": f16_ms},
+        "graph_replay": {"ms_per_step": graph_ms, "value": world * wl.n_pairs / (graph_ms / 1e3), "unit": UNIT},
         "e2e": {"value": world * wl.n_pairs / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,

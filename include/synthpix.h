@@ -106,15 +106,19 @@ typedef struct synthpix_batch_desc {
     int32_t  integrator;         /* SYNTHPIX_RK4 or SYNTHPIX_EULER                      */
     int32_t  n_substeps;         /* substeps over dt, 1..1024                          */
     float    dt;                 /* time between the frames, in frames (|dt| <= 64)    */
-    int32_t  tile;               /* square screen tile edge: 0 (auto), 16, 32 or 64     */
+    int32_t  tile;               /* square screen tile edge: 16, 32 or 64, or 0 for a
+                                    default from the frame sizes (64 when the mean
+                                    frame area is >= 256x256, else 32)                 */
     int32_t  flags;              /* must be 0                                          */
     int32_t  reserved[6];        /* must be zero                                       */
 } synthpix_batch_desc;
 
 /*
  * Bytes of device workspace synthpix_render_pairs needs for this batch
- * (a 256-byte aligned region the caller allocates).  Returns 0 and sets the
- * last error if the descriptors are invalid.  Only the host arrays are read.
+ * (a 256-byte aligned region the caller allocates).  With batch->tile = 0 it
+ * is the largest over the tile edges synthpix_autotune_tile tries, so one
+ * workspace serves every choice.  Returns 0 and sets the last error if the
+ * descriptors are invalid.  Only the host arrays are read.
  */
 size_t synthpix_workspace_bytes(const synthpix_batch_desc *batch,
                                 const synthpix_pair_desc *pairs, int32_t n_pairs);
@@ -193,6 +197,23 @@ int synthpix_render_pairs_staged(const synthpix_batch_desc *batch, const synthpi
 int synthpix_render_pairs_noalloc(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
                                   const synthpix_pair_desc *pairs_dev, int32_t n_pairs,
                                   const float *flows, void *images, void *stream);
+
+/*
+ * Autotuner of the screen tile edge (a scheduling parameter; the paper has no
+ * counterpart).  Renders the batch with each candidate edge (16, 32, 64):
+ * once to warm up, then `reps` (1..1000) timed times on `stream`, timed with
+ * CUDA events, and returns the fastest edge in *best_tile and its mean time
+ * per render in *best_ms (nullable).  The images are overwritten.  The
+ * workspace must hold synthpix_workspace_bytes for batch->tile = 0.  Unlike
+ * the other entry points this call BLOCKS the host until the timings are
+ * done.  Results never depend on the tile edge (exact accumulation), only
+ * the speed does.
+ */
+int synthpix_autotune_tile(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
+                           const synthpix_pair_desc *pairs_dev, int32_t n_pairs,
+                           const float *flows, void *images,
+                           void *workspace, size_t workspace_bytes, void *stream,
+                           int32_t reps, int32_t *best_tile, float *best_ms);
 
 /* Message of the last failing call on this host thread ("" if none). */
 const char *synthpix_last_error(void);

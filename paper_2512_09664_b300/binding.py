@@ -22,7 +22,7 @@ OK, EINVAL, EWORKSPACE, ECUDA, EUNSUPPORTED = 0, -1, -2, -3, -4
 DTYPE_CODE = {"f32": 0, "f16": 1, "bf16": 2, "u8": 3, "u16": 4}
 INTEGRATOR_CODE = {"rk4": 0, "euler": 1}
 _EXPORTS = ("synthpix_workspace_bytes", "synthpix_render_pairs", "synthpix_render_pairs_staged",
-            "synthpix_last_error", "synthpix_version")
+            "synthpix_autotune_tile", "synthpix_last_error", "synthpix_version")
 STAGES = ("plan", "seed_advect", "bin_scan", "bin_scatter", "splat_epilogue")
 
 
@@ -76,6 +76,10 @@ def lib():
         L.synthpix_render_pairs_staged.argtypes = [C.POINTER(BatchDesc), C.POINTER(PairDesc), vp, C.c_int32,
                                                    vp, vp, vp, sz, vp, C.POINTER(C.c_void_p)]
         L.synthpix_render_pairs_staged.restype = C.c_int
+        L.synthpix_autotune_tile.argtypes = [C.POINTER(BatchDesc), C.POINTER(PairDesc), vp, C.c_int32,
+                                             vp, vp, vp, sz, vp, C.c_int32, C.POINTER(C.c_int32),
+                                             C.POINTER(C.c_float)]
+        L.synthpix_autotune_tile.restype = C.c_int
         L.synthpix_last_error.argtypes = []
         L.synthpix_last_error.restype = C.c_char_p
         L.synthpix_version.argtypes = []
@@ -228,6 +232,43 @@ class Renderer:
 
     def render_staged(self, events, stream=None):
         render_pairs_staged(self.pk, self.flows, self.images, self.workspace, events, self.pairs_dev, stream)
+        return self.images
+
+    def autotune(self, reps: int = 3, stream=None):
+        """Pick the tile edge with synthpix_autotune_tile; later renders use it."""
+        import torch
+        st = stream if stream is not None else torch.cuda.current_stream()
+        best, ms = C.c_int32(0), C.c_float(0.0)
+        saved = self.pk.batch.tile
+        self.pk.batch.tile = 0
+        rc = lib().synthpix_autotune_tile(
+            C.byref(self.pk.batch), self.pk.pairs,
+            C.c_void_p(self.pairs_dev.data_ptr()) if self.pairs_dev is not None else None, self.pk.n_pairs,
+            C.c_void_p(self.flows.data_ptr()), C.c_void_p(self.images.data_ptr()),
+            C.c_void_p(self.workspace.data_ptr()), self.workspace.numel(), C.c_void_p(st.cuda_stream), reps,
+            C.byref(best), C.byref(ms))
+        if rc != OK:
+            self.pk.batch.tile = saved
+            _check(rc)
+        self.pk.batch.tile = best.value
+        return best.value, ms.value
+
+    def capture(self):
+        """Capture one render into a CUDA graph (descriptors must be on the device)."""
+        import torch
+        assert self.pairs_dev is not None or self.pk.n_pairs == 0
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self.render()
+        torch.cuda.current_stream().wait_stream(side)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.render()
+        return self.graph
+
+    def replay(self):
+        self.graph.replay()
         return self.images
 
     def frames(self, b: int):

@@ -28,6 +28,7 @@ struct Plan {
     int32_t tile;
     int32_t fused;
     int32_t max_halo;
+    int32_t max_r;
     float max_d;
 };
 
@@ -43,8 +44,6 @@ int check_batch(const synthpix_batch_desc *b) {
         return fail(SYNTHPIX_EINVAL, "float outputs need quant_bits = 0 (got %d)", b->quant_bits);
     if (b->inter_dtype < SYNTHPIX_F32 || b->inter_dtype > SYNTHPIX_BF16)
         return fail(SYNTHPIX_EINVAL, "inter_dtype %d is not one of F32/F16/BF16", b->inter_dtype);
-    if (b->inter_dtype != SYNTHPIX_F32)
-        return fail(SYNTHPIX_EUNSUPPORTED, "16-bit intermediate storage is not available in this build");
     if (b->integrator != SYNTHPIX_RK4 && b->integrator != SYNTHPIX_EULER)
         return fail(SYNTHPIX_EINVAL, "integrator %d is not RK4 (0) or Euler (1)", b->integrator);
     if (b->n_substeps < 1 || b->n_substeps > 1024)
@@ -87,14 +86,33 @@ int check_pair(const synthpix_pair_desc &d, int b) {
     return SYNTHPIX_OK;
 }
 
+// Tile edge used when batch->tile is 0: 64 when the batch's mean frame area
+// is at least 256 x 256 (fewer particles rendered twice at tile borders),
+// else 32 (more work items for small frames).
+int default_tile(const synthpix_pair_desc *pairs, int32_t n_pairs) {
+    double area = 0.0;
+    for (int32_t b = 0; b < n_pairs; ++b) area += (double)pairs[b].height * pairs[b].width;
+    return (n_pairs > 0 && area / n_pairs >= 65536.0) ? 64 : 32;
+}
+
+int make_plan_tile(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs, int32_t n_pairs, int tile,
+                   Plan &P);
+
 int make_plan(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs, int32_t n_pairs, Plan &P) {
     int rc = check_batch(batch);
     if (rc) return rc;
     if (n_pairs < 0 || n_pairs > (1 << 20)) return fail(SYNTHPIX_EINVAL, "n_pairs %d outside 0..2^20", n_pairs);
     if (n_pairs > 0 && !pairs) return fail(SYNTHPIX_EINVAL, "pairs is NULL");
-    P.tile = batch->tile ? batch->tile : 32;
+    return make_plan_tile(batch, pairs, n_pairs, batch->tile ? batch->tile : default_tile(pairs, n_pairs), P);
+}
+
+int make_plan_tile(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs, int32_t n_pairs, int tile,
+                   Plan &P) {
+    int rc;
+    P.tile = tile;
     P.fused = batch->inter_dtype == SYNTHPIX_F32 ? 1 : 0;
     P.max_halo = 0;
+    P.max_r = 0;
     P.max_d = 0.0f;
     spx::Layout &L = P.L;
     L.n_part = L.n_tiles = L.n_list = L.n_inter = 0;
@@ -107,6 +125,7 @@ int make_plan(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
         L.n_list += 2LL * g.list_cap;
         if (!P.fused) L.n_inter += 2LL * pairs[b].height * pairs[b].width;
         if (g.halo > P.max_halo) P.max_halo = g.halo;
+        if (g.blur_r > P.max_r) P.max_r = g.blur_r;
         if (pairs[b].d_max > P.max_d) P.max_d = pairs[b].d_max;
     }
     if (L.n_tiles > 0x7FFFFFFFLL) return fail(SYNTHPIX_EINVAL, "batch has more than 2^31-1 tiles");
@@ -141,6 +160,8 @@ size_t elem_size(int32_t dt) {
     }
 }
 
+constexpr int kTileCandidates[3] = {16, 32, 64};
+
 }  // namespace
 
 static_assert(sizeof(synthpix_pair_desc) == 128, "pair descriptor ABI");
@@ -156,8 +177,16 @@ size_t synthpix_workspace_bytes(const synthpix_batch_desc *batch, const synthpix
                                 int32_t n_pairs) {
     Plan P;
     if (make_plan(batch, pairs, n_pairs, P) != SYNTHPIX_OK) return 0;
+    size_t need = P.L.total;
+    if (batch->tile == 0) {  // large enough for every tile the autotuner tries
+        for (int t : kTileCandidates) {
+            Plan Q;
+            if (make_plan_tile(batch, pairs, n_pairs, t, Q) != SYNTHPIX_OK) return 0;
+            if (Q.L.total > need) need = Q.L.total;
+        }
+    }
     g_err[0] = 0;
-    return P.L.total;
+    return need;
 }
 
 }  // extern "C"
@@ -229,12 +258,14 @@ static int render_impl(const synthpix_batch_desc *batch, const synthpix_pair_des
     a.ticket = ticket;
     a.rec_buf_bytes = 8192;
     a.blur_w = blur_w;
-    a.smem_edge = P.tile + 2 * P.max_halo;
+    a.inter_dtype = batch->inter_dtype;
+    a.inter = ws + L.inter;
+    a.smem_edge = P.tile + 2 * P.max_r;
     const int wmax = std::min(spx::window_max(P.max_d), a.smem_edge);
     a.warp_scratch = 4 * (wmax + 2);
     if (spx::splat_smem_bytes(a.smem_edge, a.tile, a.warp_scratch, a.rec_buf_bytes) > 227 * 1024)
         return fail(SYNTHPIX_EUNSUPPORTED, "tile %d with blur radius %d needs too much shared memory", P.tile,
-                    P.max_halo);
+                    P.max_r);
     e = spx::launch_prep(a, st, ev);
     if (e != cudaSuccess) return fail(SYNTHPIX_ECUDA, "seeding/binning launch: %s", cudaGetErrorString(e));
     e = spx::launch_splat(a, batch->out_dtype, st, ev);
@@ -249,6 +280,54 @@ int synthpix_render_pairs(const synthpix_batch_desc *batch, const synthpix_pair_
                           const synthpix_pair_desc *pairs_dev, int32_t n_pairs, const float *flows, void *images,
                           void *workspace, size_t workspace_bytes, void *stream) {
     return render_impl(batch, pairs, pairs_dev, n_pairs, flows, images, workspace, workspace_bytes, stream, nullptr);
+}
+
+int synthpix_autotune_tile(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
+                           const synthpix_pair_desc *pairs_dev, int32_t n_pairs, const float *flows, void *images,
+                           void *workspace, size_t workspace_bytes, void *stream, int32_t reps, int32_t *best_tile,
+                           float *best_ms) {
+    if (!batch || !best_tile) return fail(SYNTHPIX_EINVAL, "batch and best_tile must not be NULL");
+    if (reps < 1 || reps > 1000) return fail(SYNTHPIX_EINVAL, "reps %d outside 1..1000", reps);
+    Plan P;
+    int rc = make_plan(batch, pairs, n_pairs, P);
+    if (rc) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return fail(SYNTHPIX_ECUDA, "autotune: cudaEventCreate failed");
+    }
+    synthpix_batch_desc b = *batch;
+    float best = -1.0f;
+    int best_t = 0;
+    for (int t : kTileCandidates) {
+        b.tile = t;
+        rc = render_impl(&b, pairs, pairs_dev, n_pairs, flows, images, workspace, workspace_bytes, stream, nullptr);
+        if (rc) break;  // warm-up; also validates the workspace for this tile
+        cudaEventRecord(e0, st);
+        for (int k = 0; k < reps && !rc; ++k)
+            rc = render_impl(&b, pairs, pairs_dev, n_pairs, flows, images, workspace, workspace_bytes, stream,
+                             nullptr);
+        cudaEventRecord(e1, st);
+        if (rc) break;
+        float ms = 0.0f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            rc = fail(SYNTHPIX_ECUDA, "autotune: event timing failed");
+            break;
+        }
+        ms /= (float)reps;
+        if (best < 0.0f || ms < best) {
+            best = ms;
+            best_t = t;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    *best_tile = best_t;
+    if (best_ms) *best_ms = best;
+    g_err[0] = 0;
+    return SYNTHPIX_OK;
 }
 
 int synthpix_render_pairs_staged(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,

@@ -32,6 +32,8 @@ struct KernelArgs {
     int32_t warp_scratch;             // floats of per-warp window scratch
     const float *blur_w;              // [n_pairs][kBlurStride] normalised taps w[|k|]
     int32_t rec_buf_bytes;            // bytes of each staged-records buffer
+    int32_t inter_dtype;              // SYNTHPIX_F32: fused; F16 / BF16: intermediate frames
+    void *inter;                      // 16-bit intermediate frames (non-fused path)
 };
 
 constexpr int kStageEvents = 6;

@@ -389,31 +389,30 @@ struct Smem {
     int BP;
 };
 
-template <typename T>
-__device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo &it, unsigned char *buf,
-                                             uint32_t cap, const Smem &s) {
-    const synthpix_pair_desc &D = *reinterpret_cast<const synthpix_pair_desc *>(buf);
-    const PairPlan &pl = *reinterpret_cast<const PairPlan *>(buf + 128);
-    const float *wtab = reinterpret_cast<const float *>(buf + 192);
+__device__ __forceinline__ Geo make_geo(const synthpix_pair_desc &D, const PairPlan &pl, int tile_edge, int tile,
+                                        int halo) {
     Geo g;
     g.W = D.width;
     g.H = D.height;
-    const int ty = it.tile / pl.tiles_x, tx = it.tile - ty * pl.tiles_x;
+    const int ty = tile / pl.tiles_x, tx = tile - ty * pl.tiles_x;
     g.R = pl.blur_r;
-    g.x0 = tx * a.tile;
-    g.x1 = min(g.x0 + a.tile, g.W);
-    g.y0 = ty * a.tile;
-    g.y1 = min(g.y0 + a.tile, g.H);
-    g.ex0 = max(g.x0 - g.R, 0);
-    g.ex1 = min(g.x1 + g.R, g.W);
-    g.ey0 = max(g.y0 - g.R, 0);
-    g.ey1 = min(g.y1 + g.R, g.H);
+    g.x0 = tx * tile_edge;
+    g.x1 = min(g.x0 + tile_edge, g.W);
+    g.y0 = ty * tile_edge;
+    g.y1 = min(g.y0 + tile_edge, g.H);
+    g.ex0 = max(g.x0 - halo, 0);
+    g.ex1 = min(g.x1 + halo, g.W);
+    g.ey0 = max(g.y0 - halo, 0);
+    g.ey1 = min(g.y1 + halo, g.H);
     g.EW = g.ex1 - g.ex0;
     g.EH = g.ey1 - g.ey0;
     g.FW = (g.x1 - g.x0) + 2 * g.R;
     g.FH = (g.y1 - g.y0) + 2 * g.R;
+    return g;
+}
 
-    // separable illumination factors of the clipped halo rectangle
+// separable illumination factors sin^2 of the clipped halo rectangle
+__device__ __forceinline__ bool illum_factors(const Geo &g, const synthpix_pair_desc &D, const Smem &s) {
     const bool illum = D.illum_min != 1.0f || D.illum_max != 1.0f;
     if (illum) {
         for (int k = threadIdx.x; k < g.EW + g.EH; k += blockDim.x) {
@@ -426,6 +425,102 @@ __device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo
             }
         }
     }
+    return illum;
+}
+
+// The finishing steps of one tile of one frame: A = L * S + sigma_n * n over
+// the clipped halo rectangle, border replication, separable blur, store.
+// src(idx, r, c) gives S at row r, column c of the clipped halo rectangle
+// (idx = r * EW + c).  The illumination factors must be in s.sx2 / s.sy2 and
+// visible (a barrier after illum_factors).
+template <typename T, typename Src>
+__device__ __forceinline__ void finish_tile(const KernelArgs &a, const Geo &g, const synthpix_pair_desc &D,
+                                            const float *wtab, int frame, bool illum, const Smem &s, Src src) {
+    const float dl = D.illum_max - D.illum_min;
+    const int fx0 = g.x0 - g.R, fy0 = g.y0 - g.R;
+    if (D.noise_sigma != 0.0f) {
+        const int64_t HW = (int64_t)g.H * g.W;
+        const int nq = (g.EW + 6) / 4 + 1;
+        const float inq = 1.0f / (float)nq;
+        const uint32_t tag = kTagNoise + (uint32_t)frame;
+        for (int item = threadIdx.x; item < g.EH * nq; item += blockDim.x) {
+            const int r = small_div(item, inq), qi = item - r * nq;
+            const int64_t rowlin = (int64_t)(g.ey0 + r) * g.W;
+            const int64_t q = ((rowlin + g.ex0) >> 2) + qi;
+            if (4 * q > rowlin + g.ex1 - 1) continue;
+            const uint4 w = stream_words(a.seed, D.pair_id, (uint32_t)q, tag);
+            float nv[4];
+            box_muller(w.x, w.y, nv[0], nv[1]);
+            box_muller(w.z, w.w, nv[2], nv[3]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int64_t pix = 4 * q + k;
+                const int64_t col = pix - rowlin;
+                if (pix < HW && col >= g.ex0 && col < g.ex1) {
+                    const int c = (int)(col - g.ex0);
+                    const float S = src(r * g.EW + c, r, c);
+                    const float L = illum ? fmaf(dl, s.sx2[c] * s.sy2[r], D.illum_min) : 1.0f;
+                    s.A[(g.ey0 + r - fy0) * g.FW + (g.ex0 + c - fx0)] = fmaf(L, S, D.noise_sigma * nv[k]);
+                }
+            }
+        }
+    } else {
+        const float iew = 1.0f / (float)g.EW;
+        for (int idx = threadIdx.x; idx < g.EH * g.EW; idx += blockDim.x) {
+            const int r = small_div(idx, iew), c = idx - r * g.EW;
+            const float S = src(idx, r, c);
+            const float L = illum ? fmaf(dl, s.sx2[c] * s.sy2[r], D.illum_min) : 1.0f;
+            s.A[(g.ey0 + r - fy0) * g.FW + (g.ex0 + c - fx0)] = L * S;
+        }
+    }
+    __syncthreads();
+    // replicate the border into the halo outside the frame
+    if (g.R > 0 && (fx0 < 0 || fy0 < 0 || g.x1 + g.R > g.W || g.y1 + g.R > g.H)) {
+        const float ifw = 1.0f / (float)g.FW;
+        for (int k = threadIdx.x; k < g.FH * g.FW; k += blockDim.x) {
+            const int r = small_div(k, ifw), c = k - r * g.FW;
+            const int gi = fy0 + r, gj = fx0 + c;
+            if (gi < 0 || gi >= g.H || gj < 0 || gj >= g.W) {
+                const int ci = min(max(gi, 0), g.H - 1) - fy0, cj = min(max(gj, 0), g.W - 1) - fx0;
+                s.A[k] = s.A[ci * g.FW + cj];
+            }
+        }
+    }
+    __syncthreads();
+    const int64_t HW = (int64_t)g.H * g.W;
+    T *out = reinterpret_cast<T *>(a.images) + D.image_offset + (int64_t)frame * HW;
+    const float M = a.quant_bits > 0 ? (float)((1u << a.quant_bits) - 1u) : 0.0f;
+    switch (g.R) {
+    case 0: store_unblurred<T>(g, s.A, out, M); break;
+    case 1: blur_store<T, 1>(g, s.A, s.Bh, s.BP, wtab, out, M); break;
+    case 2: blur_store<T, 2>(g, s.A, s.Bh, s.BP, wtab, out, M); break;
+    case 3: blur_store<T, 3>(g, s.A, s.Bh, s.BP, wtab, out, M); break;
+    case 4: blur_store<T, 4>(g, s.A, s.Bh, s.BP, wtab, out, M); break;
+    case 5: blur_store<T, 5>(g, s.A, s.Bh, s.BP, wtab, out, M); break;
+    case 6: blur_store<T, 6>(g, s.A, s.Bh, s.BP, wtab, out, M); break;
+    default: blur_store_any<T>(g, s.A, s.Bh, s.BP, wtab, out, M); break;
+    }
+}
+
+template <typename I>
+__device__ __forceinline__ I to_inter(float v);
+template <>
+__device__ __forceinline__ __half to_inter<__half>(float v) { return __float2half_rn(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_inter<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+// One work item of k_splat.  Fused (inter_dtype F32): splat the tile plus
+// its blur halo and finish it on chip.  Otherwise splat the tile alone and
+// store S in 16 bits to the intermediate frames; k_finish does the rest.
+template <typename T>
+__device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo &it, unsigned char *buf,
+                                             uint32_t cap, const Smem &s) {
+    const synthpix_pair_desc &D = *reinterpret_cast<const synthpix_pair_desc *>(buf);
+    const PairPlan &pl = *reinterpret_cast<const PairPlan *>(buf + 128);
+    const float *wtab = reinterpret_cast<const float *>(buf + 192);
+    const Geo g = make_geo(D, pl, a.tile, it.tile, pl.halo);
+    const bool fused = a.inter_dtype == SYNTHPIX_F32;
+    const bool illum = fused ? illum_factors(g, D, s) : false;
 
     // splat, chunk by chunk of staged records
     const float imax = D.i_max > 0.0f ? D.i_max : 1.0f;
@@ -447,80 +542,33 @@ __device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo
     }
     if (it.count == 0) __syncthreads();  // illumination factors
 
-    // pass 1: A = L * S + sigma_n * n over the clipped halo rectangle, stored in
-    // full-rectangle coordinates (origin (x0 - R, y0 - R), pitch FW)
     const float unit = imax * (1.0f / 1024.0f);
-    const float dl = D.illum_max - D.illum_min;
-    const int fx0 = g.x0 - g.R, fy0 = g.y0 - g.R;
-    if (D.noise_sigma != 0.0f) {
+    int32_t *hi = s.hi, *lo = s.lo;
+    auto fixed_src = [hi, lo, unit](int idx, int, int) {
+        return fmaf((float)lo[idx], 1.0f / 4194304.0f, (float)hi[idx]) * unit;
+    };
+    if (!fused) {
+        // halo 0: the clipped rectangle is the tile
         const int64_t HW = (int64_t)g.H * g.W;
-        const int nq = (g.EW + 6) / 4 + 1;
-        const float inq = 1.0f / (float)nq;
-        const uint32_t tag = kTagNoise + (uint32_t)it.frame;
-        for (int item = threadIdx.x; item < g.EH * nq; item += blockDim.x) {
-            const int r = small_div(item, inq), qi = item - r * nq;
-            const int64_t rowlin = (int64_t)(g.ey0 + r) * g.W;
-            const int64_t q = ((rowlin + g.ex0) >> 2) + qi;
-            if (4 * q > rowlin + g.ex1 - 1) continue;
-            const uint4 w = stream_words(a.seed, D.pair_id, (uint32_t)q, tag);
-            float nv[4];
-            box_muller(w.x, w.y, nv[0], nv[1]);
-            box_muller(w.z, w.w, nv[2], nv[3]);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int64_t pix = 4 * q + k;
-                const int64_t col = pix - rowlin;
-                if (pix < HW && col >= g.ex0 && col < g.ex1) {
-                    const int c = (int)(col - g.ex0);
-                    const int idx = r * g.EW + c;
-                    const float S = fmaf((float)s.lo[idx], 1.0f / 4194304.0f, (float)s.hi[idx]) * unit;
-                    const float L = illum ? fmaf(dl, s.sx2[c] * s.sy2[r], D.illum_min) : 1.0f;
-                    s.A[(g.ey0 + r - fy0) * g.FW + (g.ex0 + c - fx0)] = fmaf(L, S, D.noise_sigma * nv[k]);
-                }
-            }
-        }
-    } else {
+        const int64_t base = pl.inter_base + (int64_t)it.frame * HW;
         const float iew = 1.0f / (float)g.EW;
         for (int idx = threadIdx.x; idx < g.EH * g.EW; idx += blockDim.x) {
             const int r = small_div(idx, iew), c = idx - r * g.EW;
-            const float S = fmaf((float)s.lo[idx], 1.0f / 4194304.0f, (float)s.hi[idx]) * unit;
-            const float L = illum ? fmaf(dl, s.sx2[c] * s.sy2[r], D.illum_min) : 1.0f;
-            s.A[(g.ey0 + r - fy0) * g.FW + (g.ex0 + c - fx0)] = L * S;
+            const float S = fixed_src(idx, r, c);
+            const int64_t o = base + (int64_t)(g.ey0 + r) * g.W + (g.ex0 + c);
+            if (a.inter_dtype == SYNTHPIX_F16) reinterpret_cast<__half *>(a.inter)[o] = to_inter<__half>(S);
+            else reinterpret_cast<__nv_bfloat16 *>(a.inter)[o] = to_inter<__nv_bfloat16>(S);
+            hi[idx] = 0;
+            lo[idx] = 0;
         }
+        return;  // the caller's loop ends with a barrier
     }
-    __syncthreads();
-    // pass 2: replicate the border into the halo outside the frame; clear the
-    // accumulator region for the next item
-    if (g.R > 0 && (fx0 < 0 || fy0 < 0 || g.x1 + g.R > g.W || g.y1 + g.R > g.H)) {
-        const float ifw = 1.0f / (float)g.FW;
-        for (int k = threadIdx.x; k < g.FH * g.FW; k += blockDim.x) {
-            const int r = small_div(k, ifw), c = k - r * g.FW;
-            const int gi = fy0 + r, gj = fx0 + c;
-            if (gi < 0 || gi >= g.H || gj < 0 || gj >= g.W) {
-                const int ci = min(max(gi, 0), g.H - 1) - fy0, cj = min(max(gj, 0), g.W - 1) - fx0;
-                s.A[k] = s.A[ci * g.FW + cj];
-            }
-        }
-    }
+    finish_tile<T>(a, g, D, wtab, it.frame, illum, s, fixed_src);
+    // clear the accumulator region for the next item (pass 1 is done reading it:
+    // finish_tile passed two barriers since)
     for (int k = threadIdx.x; k < g.EH * g.EW; k += blockDim.x) {
         s.hi[k] = 0;
         s.lo[k] = 0;
-    }
-    __syncthreads();
-
-    // blur and store
-    const int64_t HW = (int64_t)g.H * g.W;
-    T *out = reinterpret_cast<T *>(a.images) + D.image_offset + (int64_t)it.frame * HW;
-    const float M = a.quant_bits > 0 ? (float)((1u << a.quant_bits) - 1u) : 0.0f;
-    switch (g.R) {
-    case 0: store_unblurred<T>(g, s.A, out, M); break;
-    case 1: blur_store<T, 1>(g, s.A, s.Bh, s.BP, wtab, out, M); break;
-    case 2: blur_store<T, 2>(g, s.A, s.Bh, s.BP, wtab, out, M); break;
-    case 3: blur_store<T, 3>(g, s.A, s.Bh, s.BP, wtab, out, M); break;
-    case 4: blur_store<T, 4>(g, s.A, s.Bh, s.BP, wtab, out, M); break;
-    case 5: blur_store<T, 5>(g, s.A, s.Bh, s.BP, wtab, out, M); break;
-    case 6: blur_store<T, 6>(g, s.A, s.Bh, s.BP, wtab, out, M); break;
-    default: blur_store_any<T>(g, s.A, s.Bh, s.BP, wtab, out, M); break;
     }
 }
 
@@ -616,6 +664,61 @@ __global__ void __launch_bounds__(kSplatThreads) k_splat(KernelArgs a) {
     cp_async_wait_all();
 }
 
+// ---------------------------------------------------------------------------
+// k_finish: the epilogue of the 16-bit intermediate path, one CTA per item
+// (pair, frame, tile).  S of the tile and its blur halo is read from the
+// intermediate frames written by k_splat; every output pixel written once.
+// ---------------------------------------------------------------------------
+struct FinishLayout {
+    size_t A, Bh, sx2, sy2, total;
+};
+
+__host__ __device__ inline FinishLayout finish_layout(int E, int tile) {
+    FinishLayout L;
+    const int BP = (tile + 3) & ~3;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = (o + bytes + 15) & ~(size_t)15;
+        return at;
+    };
+    L.A = take((size_t)E * E * 4);
+    L.Bh = take((size_t)E * BP * 4);
+    L.sx2 = take((size_t)E * 4);
+    L.sy2 = take((size_t)E * 4);
+    L.total = o;
+    return L;
+}
+
+template <typename T, typename I>
+__global__ void __launch_bounds__(kSplatThreads) k_finish(KernelArgs a) {
+    if (*a.check != 1) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ float wtab[kBlurStride];
+    const FinishLayout FL = finish_layout(a.smem_edge, a.tile);
+    Smem s;
+    s.hi = s.lo = nullptr;
+    s.A = reinterpret_cast<float *>(smem + FL.A);
+    s.Bh = reinterpret_cast<float *>(smem + FL.Bh);
+    s.sx2 = reinterpret_cast<float *>(smem + FL.sx2);
+    s.sy2 = reinterpret_cast<float *>(smem + FL.sy2);
+    s.scr = nullptr;
+    s.BP = (a.tile + 3) & ~3;
+    const ItemInfo it = a.items[blockIdx.x];
+    const synthpix_pair_desc &D = a.descs[it.pair];
+    const PairPlan pl = a.plan[it.pair];
+    if (threadIdx.x < kBlurStride) wtab[threadIdx.x] = a.blur_w[(int64_t)it.pair * kBlurStride + threadIdx.x];
+    const Geo g = make_geo(D, pl, a.tile, it.tile, pl.blur_r);
+    const bool illum = illum_factors(g, D, s);
+    __syncthreads();
+    const I *S16 = reinterpret_cast<const I *>(a.inter) + pl.inter_base + (int64_t)it.frame * g.H * g.W;
+    const int W = g.W, ex0 = g.ex0, ey0 = g.ey0;
+    auto src = [S16, W, ex0, ey0](int, int r, int c) {
+        return (float)S16[(int64_t)(ey0 + r) * W + (ex0 + c)];
+    };
+    finish_tile<T>(a, g, D, wtab, it.frame, illum, s, src);
+}
+
 size_t splat_smem_bytes(int edge, int tile, int warp_scratch, int rec_buf_bytes) {
     return smem_layout(edge, tile, warp_scratch, rec_buf_bytes).total;
 }
@@ -645,6 +748,31 @@ cudaError_t launch_splat(const KernelArgs &a, int32_t out_dtype, cudaStream_t st
     default: SPX_LAUNCH(uint16_t); break;
     }
 #undef SPX_LAUNCH
+    if (a.inter_dtype != SYNTHPIX_F32) {
+        const size_t fsm = finish_layout(a.smem_edge, a.tile).total;
+        const unsigned grid = (unsigned)a.n_tiles;
+#define SPX_FINISH(T, I)                                                                                     \
+    do {                                                                                                     \
+        e = cudaFuncSetAttribute(k_finish<T, I>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);     \
+        if (e != cudaSuccess) return e;                                                                      \
+        k_finish<T, I><<<grid, kSplatThreads, fsm, st>>>(a);                                                 \
+    } while (0)
+#define SPX_FINISH_I(I)                                                                                      \
+    switch (out_dtype) {                                                                                     \
+    case SYNTHPIX_F32: SPX_FINISH(float, I); break;                                                          \
+    case SYNTHPIX_F16: SPX_FINISH(__half, I); break;                                                         \
+    case SYNTHPIX_BF16: SPX_FINISH(__nv_bfloat16, I); break;                                                 \
+    case SYNTHPIX_U8: SPX_FINISH(uint8_t, I); break;                                                         \
+    default: SPX_FINISH(uint16_t, I); break;                                                                 \
+    }
+        if (a.inter_dtype == SYNTHPIX_F16) {
+            SPX_FINISH_I(__half)
+        } else {
+            SPX_FINISH_I(__nv_bfloat16)
+        }
+#undef SPX_FINISH_I
+#undef SPX_FINISH
+    }
     if (ev && ev[5]) cudaEventRecord(ev[5], st);
     return cudaGetLastError();
 }

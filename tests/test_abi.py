@@ -77,6 +77,7 @@ def test_reserved_fields_and_flags_unsupported():
 
 def test_workspace_checks():
     pk = _packed()
+    pk.batch.tile = 32  # a fixed tile: workspace_bytes is then exactly what the render needs
     need = B.workspace_bytes(pk)
     assert need > 0
     assert _render(pk, ws_bytes=need - 1) == B.EWORKSPACE
@@ -100,6 +101,14 @@ def test_zero_pairs_is_a_no_op():
     pk = _packed()
     assert B.lib().synthpix_render_pairs(C.byref(pk.batch), pk.pairs, None, 0, None, None, None, 0,
                                          None) == B.OK
+
+
+def test_auto_tile_workspace_covers_every_candidate():
+    pk = _packed()
+    auto = B.workspace_bytes(pk)
+    for t in (16, 32, 64):
+        pk.batch.tile = t
+        assert B.workspace_bytes(pk) <= auto
 
 
 def test_workspace_grows_with_particles_and_tiles():
