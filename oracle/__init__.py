@@ -83,6 +83,10 @@ def lib():
         L.oracle_epilogue.restype = C.c_int
         L.oracle_render_pair.argtypes = [C.POINTER(OraclePair), fp, dp, dp, up, dp, C.c_int32]
         L.oracle_render_pair.restype = C.c_int
+        L.oracle_render_from.argtypes = [C.POINTER(OraclePair), fp, dp, dp]
+        L.oracle_render_from.restype = C.c_int
+        L.oracle_backward.argtypes = [C.POINTER(OraclePair), fp, dp, dp, dp, dp]
+        L.oracle_backward.restype = C.c_int
         _lib = L
     return _lib
 
@@ -209,6 +213,30 @@ def render_pair(pair: OraclePair, flow: np.ndarray, splat_mode: int = 0, want_pa
     if rc != 0:
         raise MemoryError("oracle_render_pair failed")
     return {"S": S, "B": B, "Q": Q, "parts": parts}
+
+
+def render_from(pair: OraclePair, flow: np.ndarray, parts_in=None) -> np.ndarray:
+    """[2, H, W] = L * S for particles (x0, y0, d) given as [N, 3] (None: seeded)."""
+    flow = np.ascontiguousarray(flow, dtype=np.float32)
+    pin = None if parts_in is None else np.ascontiguousarray(parts_in, dtype=np.float64).reshape(-1, 3)
+    B = np.zeros((2, pair.height, pair.width), dtype=np.float64)
+    if lib().oracle_render_from(C.byref(pair), _ptr(flow, C.c_float), _ptr(pin, C.c_double),
+                                _ptr(B, C.c_double)) != 0:
+        raise MemoryError("oracle_render_from failed")
+    return B
+
+
+def backward(pair: OraclePair, flow: np.ndarray, G: np.ndarray, parts_in=None):
+    """Gradients of sum(G * render_from(...)): (grad_flow [gh, gw, 2], grad_parts [N, 3])."""
+    flow = np.ascontiguousarray(flow, dtype=np.float32)
+    pin = None if parts_in is None else np.ascontiguousarray(parts_in, dtype=np.float64).reshape(-1, 3)
+    Gd = np.ascontiguousarray(G, dtype=np.float64)
+    gf = np.zeros(flow.shape, dtype=np.float64)
+    gp = np.zeros((max(pair.n_particles, 0), 3), dtype=np.float64)
+    if lib().oracle_backward(C.byref(pair), _ptr(flow, C.c_float), _ptr(pin, C.c_double), _ptr(Gd, C.c_double),
+                             _ptr(gf, C.c_double), _ptr(gp, C.c_double)) != 0:
+        raise MemoryError("oracle_backward failed")
+    return gf, gp
 
 
 def render_workload(wl, pairs=None, threads: int | None = None, want_particles=False):

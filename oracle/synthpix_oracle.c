@@ -392,3 +392,222 @@ int oracle_render_pair(const oracle_pair *p, const float *flow, double *S, doubl
     if (!S) free(s);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* forward with given particles, and its adjoint (gradients)                */
+/* ------------------------------------------------------------------------ */
+/*
+ * The differentiable form of the render: frames S_f = splat of the particles
+ * at their frame-f positions, B_f = L * S_f (no noise, no blur).  parts_in
+ * holds (x0, y0, d) per particle, or is NULL for the seeded values; the
+ * intensities always come from the seeded streams.
+ */
+static void particle_inputs(const oracle_pair *p, const double *parts_in, int64_t i, double *x0, double *y0,
+                            double *d, double *ieff)
+{
+    oracle_attr a;
+    particle_attr(p, (uint32_t)i, &a);
+    *x0 = parts_in ? parts_in[3 * i] : a.x0;
+    *y0 = parts_in ? parts_in[3 * i + 1] : a.y0;
+    *d = parts_in ? parts_in[3 * i + 2] : a.d;
+    *ieff = a.ieff;
+}
+
+/* B[2][H][W] = L * S of both frames. */
+int oracle_render_from(const oracle_pair *p, const float *flow, const double *parts_in, double *B)
+{
+    const int64_t HW = (int64_t)p->height * p->width, n = p->n_particles;
+    double *xy = (double *)malloc(sizeof(double) * (size_t)(8 * (n > 0 ? n : 1)));
+    if (!xy) return -1;
+    for (int64_t i = 0; i < n; ++i) {
+        double x0, y0, d, ie, x1, y1;
+        particle_inputs(p, parts_in, i, &x0, &y0, &d, &ie);
+        oracle_advect(p, flow, x0, y0, &x1, &y1);
+        double *r = xy + 8 * i;
+        r[0] = x0; r[1] = y0; r[2] = d; r[3] = ie; r[4] = x1; r[5] = y1; r[6] = d; r[7] = ie;
+    }
+    memset(B, 0, sizeof(double) * (size_t)(2 * HW));
+    for (int f = 0; f < 2; ++f) {
+        double *tmp = (double *)malloc(sizeof(double) * (size_t)(4 * (n > 0 ? n : 1)));
+        if (!tmp) { free(xy); return -1; }
+        for (int64_t i = 0; i < n; ++i) {
+            tmp[4 * i] = xy[8 * i + (f ? 4 : 0)];
+            tmp[4 * i + 1] = xy[8 * i + (f ? 5 : 1)];
+            tmp[4 * i + 2] = xy[8 * i + 2];
+            tmp[4 * i + 3] = xy[8 * i + 3];
+        }
+        oracle_splat(p->height, p->width, tmp, n, 0, B + f * HW);
+        free(tmp);
+        for (int64_t i = 0; i < p->height; ++i)
+            for (int64_t j = 0; j < p->width; ++j) B[f * HW + i * p->width + j] *= oracle_illumination(p, i, j);
+    }
+    free(xy);
+    return 0;
+}
+
+static double gauss_pdf(double t) { return exp(-0.5 * t * t) / 2.50662827463100050242; }
+
+/* Velocity, its Jacobian dU/dp (J[0] = du/dx, J[1] = du/dy, J[2] = dv/dx,
+ * J[3] = dv/dy) and the four (node, weight) pairs of the bilinear stencil. */
+static void velocity_jac(const float *flow, int32_t gh, int32_t gw, int32_t height, int32_t width, double x,
+                         double y, double *u, double *v, double J[4], long node[4], double wgt[4])
+{
+    double gx = x * (double)gw / (double)width - 0.5;
+    double gy = y * (double)gh / (double)height - 0.5;
+    double fl = floor(gx), fk = floor(gy);
+    double tx = gx - fl, ty = gy - fk;
+    long l0 = clampl((long)fl, 0, gw - 1), l1 = clampl((long)fl + 1, 0, gw - 1);
+    long k0 = clampl((long)fk, 0, gh - 1), k1 = clampl((long)fk + 1, 0, gh - 1);
+    double out[2];
+    for (int c = 0; c < 2; ++c) {
+        double a = flow[(k0 * gw + l0) * 2 + c], b = flow[(k0 * gw + l1) * 2 + c];
+        double e = flow[(k1 * gw + l0) * 2 + c], f = flow[(k1 * gw + l1) * 2 + c];
+        double top = a + tx * (b - a), bot = e + tx * (f - e);
+        out[c] = top + ty * (bot - top);
+        J[2 * c] = ((1.0 - ty) * (b - a) + ty * (f - e)) * (double)gw / (double)width;
+        J[2 * c + 1] = (bot - top) * (double)gh / (double)height;
+    }
+    *u = out[0];
+    *v = out[1];
+    node[0] = k0 * gw + l0; wgt[0] = (1.0 - tx) * (1.0 - ty);
+    node[1] = k0 * gw + l1; wgt[1] = tx * (1.0 - ty);
+    node[2] = k1 * gw + l0; wgt[2] = (1.0 - tx) * ty;
+    node[3] = k1 * gw + l1; wgt[3] = tx * ty;
+}
+
+/* Adds w * lam (per velocity component) to the stencil's nodes. */
+static void scatter_flow(double *grad_flow, const long node[4], const double wgt[4], double lx, double ly)
+{
+    for (int n = 0; n < 4; ++n) {
+        grad_flow[node[n] * 2] += wgt[n] * lx;
+        grad_flow[node[n] * 2 + 1] += wgt[n] * ly;
+    }
+}
+
+/* Reverse sweep of the advection: given dL/d(frame-2 position), returns
+ * dL/d(start position) and adds dL/dflow (RK4 or Euler, as the forward). */
+static void advect_adjoint(const oracle_pair *p, const float *flow, double x0, double y0, double lx, double ly,
+                           double *gx0, double *gy0, double *grad_flow)
+{
+    const int n = p->n_substeps;
+    const double h = p->dt / (double)n;
+    double *xs = (double *)malloc(sizeof(double) * (size_t)(2 * (n + 1)));
+    double x = x0, y = y0;
+    for (int s = 0; s < n; ++s) {  /* forward, keeping the substep starts */
+        xs[2 * s] = x;
+        xs[2 * s + 1] = y;
+        oracle_pair one = *p;
+        one.n_substeps = 1;
+        one.dt = h;
+        oracle_advect(&one, flow, x, y, &x, &y);
+    }
+    for (int s = n - 1; s >= 0; --s) {
+        const double px = xs[2 * s], py = xs[2 * s + 1];
+        double u1, v1, J1[4], w1[4];
+        long n1[4];
+        velocity_jac(flow, p->flow_h, p->flow_w, p->height, p->width, px, py, &u1, &v1, J1, n1, w1);
+        if (p->integrator == 1) {
+            scatter_flow(grad_flow, n1, w1, h * lx, h * ly);
+            const double ax = lx + h * (J1[0] * lx + J1[2] * ly);
+            const double ay = ly + h * (J1[1] * lx + J1[3] * ly);
+            lx = ax;
+            ly = ay;
+            continue;
+        }
+        double u2, v2, J2[4], w2[4], u3, v3, J3[4], w3[4], u4, v4, J4[4], w4[4];
+        long n2[4], n3[4], n4[4];
+        velocity_jac(flow, p->flow_h, p->flow_w, p->height, p->width, px + 0.5 * h * u1, py + 0.5 * h * v1, &u2,
+                     &v2, J2, n2, w2);
+        velocity_jac(flow, p->flow_h, p->flow_w, p->height, p->width, px + 0.5 * h * u2, py + 0.5 * h * v2, &u3,
+                     &v3, J3, n3, w3);
+        velocity_jac(flow, p->flow_h, p->flow_w, p->height, p->width, px + h * u3, py + h * v3, &u4, &v4, J4, n4,
+                     w4);
+        /* p+ = p + h/6 (k1 + 2 k2 + 2 k3 + k4), k_m = U(q_m) */
+        const double k4x = h / 6.0 * lx, k4y = h / 6.0 * ly;
+        const double k3x = h / 3.0 * lx + h * (J4[0] * k4x + J4[2] * k4y);
+        const double k3y = h / 3.0 * ly + h * (J4[1] * k4x + J4[3] * k4y);
+        const double k2x = h / 3.0 * lx + 0.5 * h * (J3[0] * k3x + J3[2] * k3y);
+        const double k2y = h / 3.0 * ly + 0.5 * h * (J3[1] * k3x + J3[3] * k3y);
+        const double k1x = h / 6.0 * lx + 0.5 * h * (J2[0] * k2x + J2[2] * k2y);
+        const double k1y = h / 6.0 * ly + 0.5 * h * (J2[1] * k2x + J2[3] * k2y);
+        scatter_flow(grad_flow, n1, w1, k1x, k1y);
+        scatter_flow(grad_flow, n2, w2, k2x, k2y);
+        scatter_flow(grad_flow, n3, w3, k3x, k3y);
+        scatter_flow(grad_flow, n4, w4, k4x, k4y);
+        const double ax = lx + (J1[0] * k1x + J1[2] * k1y) + (J2[0] * k2x + J2[2] * k2y) +
+                          (J3[0] * k3x + J3[2] * k3y) + (J4[0] * k4x + J4[2] * k4y);
+        const double ay = ly + (J1[1] * k1x + J1[3] * k1y) + (J2[1] * k2x + J2[3] * k2y) +
+                          (J3[1] * k3x + J3[3] * k3y) + (J4[1] * k4x + J4[3] * k4y);
+        lx = ax;
+        ly = ay;
+    }
+    free(xs);
+    *gx0 = lx;
+    *gy0 = ly;
+}
+
+/* Per-axis pixel mass and its derivatives w.r.t. the centre and sigma. */
+static void mass_derivs(double c, double sigma, int64_t j, double *m, double *dm_dc, double *dm_ds)
+{
+    const double a = ((double)j - c) / sigma, b = ((double)j + 1.0 - c) / sigma;
+    *m = oracle_pixel_mass(c, sigma, j);
+    *dm_dc = (gauss_pdf(a) - gauss_pdf(b)) / sigma;
+    *dm_ds = (a * gauss_pdf(a) - b * gauss_pdf(b)) / sigma;
+}
+
+/* Gradient of one frame's splat against G at (x, y): (dL/dx, dL/dy, dL/dsigma). */
+static void splat_adjoint(const oracle_pair *p, const double *G, double x, double y, double d, double ieff,
+                          double g[3])
+{
+    const double sigma = d / 4.0, amp = ieff * 2.0 * ORACLE_PI * sigma * sigma;
+    long j0 = (long)floor(x - 1.5 * d), j1 = (long)floor(x + 1.5 * d);
+    long i0 = (long)floor(y - 1.5 * d), i1 = (long)floor(y + 1.5 * d);
+    if (j0 < 0) j0 = 0;
+    if (i0 < 0) i0 = 0;
+    if (j1 > p->width - 1) j1 = p->width - 1;
+    if (i1 > p->height - 1) i1 = p->height - 1;
+    g[0] = g[1] = g[2] = 0.0;
+    for (long i = i0; i <= i1; ++i) {
+        double ey, dey, dsy;
+        mass_derivs(y, sigma, i, &ey, &dey, &dsy);
+        for (long j = j0; j <= j1; ++j) {
+            double ex, dex, dsx;
+            mass_derivs(x, sigma, j, &ex, &dex, &dsx);
+            const double gl = G[i * p->width + j] * oracle_illumination(p, i, j);
+            g[0] += gl * amp * dex * ey;
+            g[1] += gl * amp * ex * dey;
+            g[2] += gl * (amp * (dsx * ey + ex * dsy) + 2.0 * amp / sigma * ex * ey);
+        }
+    }
+}
+
+/*
+ * Gradients of L = sum_f sum_ij G[f][i][j] * B_f(i, j) (B from
+ * oracle_render_from): grad_flow [flow_h][flow_w][2] is added to, grad_parts
+ * [N][3] = (dL/dx0, dL/dy0, dL/dd) is overwritten (either may be NULL).
+ */
+int oracle_backward(const oracle_pair *p, const float *flow, const double *parts_in, const double *G,
+                    double *grad_flow, double *grad_parts)
+{
+    const int64_t HW = (int64_t)p->height * p->width;
+    double *gf = grad_flow;
+    if (!gf) {
+        gf = (double *)calloc((size_t)(2 * p->flow_h * p->flow_w), sizeof(double));
+        if (!gf) return -1;
+    }
+    for (int64_t i = 0; i < p->n_particles; ++i) {
+        double x0, y0, d, ie, x1, y1, g1[3], g2[3], ax, ay;
+        particle_inputs(p, parts_in, i, &x0, &y0, &d, &ie);
+        oracle_advect(p, flow, x0, y0, &x1, &y1);
+        splat_adjoint(p, G, x0, y0, d, ie, g1);
+        splat_adjoint(p, G + HW, x1, y1, d, ie, g2);
+        advect_adjoint(p, flow, x0, y0, g2[0], g2[1], &ax, &ay, gf);
+        if (grad_parts) {
+            grad_parts[3 * i] = g1[0] + ax;
+            grad_parts[3 * i + 1] = g1[1] + ay;
+            grad_parts[3 * i + 2] = (g1[2] + g2[2]) / 4.0; /* sigma = d / 4 */
+        }
+    }
+    if (!grad_flow) free(gf);
+    return 0;
+}
