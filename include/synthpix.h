@@ -153,6 +153,50 @@ int synthpix_render_pairs(const synthpix_batch_desc *batch, const synthpix_pair_
                           void *workspace, size_t workspace_bytes, void *stream);
 
 /*
+ * synthpix_render_pairs with given particles instead of the seeded ones:
+ * particles_in is a device array [sum of n_particles][3] of FP32 (x0, y0, d)
+ * (frame-1 position in pixels and diameter), pairs in order; NULL means the
+ * seeded values (then identical to synthpix_render_pairs).  Intensities and
+ * out-of-plane positions still come from the seeded streams.  Used for
+ * differentiation (finite differences, optimisation over positions).
+ */
+int synthpix_render_pairs_from(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
+                               const synthpix_pair_desc *pairs_dev, int32_t n_pairs,
+                               const float *particles_in, const float *flows, void *images,
+                               void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * The seeded particles: writes particles_out [sum of n_particles][3] (FP32
+ * x0, y0, d of each particle; device pointer), the values
+ * synthpix_render_pairs draws (Section 2, "Sampling the particles").  flows
+ * and images are not needed.  Same workspace as synthpix_render_pairs.
+ */
+int synthpix_seed_particles(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
+                            const synthpix_pair_desc *pairs_dev, int32_t n_pairs, float *particles_out,
+                            void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * Adjoint of the render (not in the paper; its differentiable use): given
+ * grad_images = dL/d(images) (FP32, same packing as the images), computes
+ *   grad_flows      dL/d(flows), ADDED to the caller's array (same layout as
+ *                   flows; several pairs sharing a grid sum into it), or NULL;
+ *   grad_particles  [sum of n_particles][3] dL/d(x0, y0, d), overwritten, or NULL;
+ * for the frames B = L * S + noise (the splat of Eq. 1 integrated per pixel,
+ * times the illumination field).  Requires out_dtype F32 (quantisation has no
+ * gradient), blur_sigma = 0 for every pair, and at most 64 substeps
+ * (SYNTHPIX_EUNSUPPORTED otherwise).  particles_in as in
+ * synthpix_render_pairs_from.  Positions and bins are recomputed, not taken
+ * from a forward call.  The splat gradient is a per-particle reduction over
+ * its window; flow gradients are accumulated with atomics, so their last bits
+ * may vary from run to run.  Same workspace as synthpix_render_pairs.
+ */
+int synthpix_render_backward(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
+                             const synthpix_pair_desc *pairs_dev, int32_t n_pairs,
+                             const float *particles_in, const float *flows,
+                             const float *grad_images, float *grad_flows, float *grad_particles,
+                             void *workspace, size_t workspace_bytes, void *stream);
+
+/*
  * synthpix_render_pairs plus per-stage timing: stage_events holds 6 CUDA
  * events (cudaEvent_t, created by the caller; NULL entries are skipped) that
  * are recorded on `stream` at the stage boundaries, so the caller can time

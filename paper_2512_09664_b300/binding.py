@@ -22,6 +22,7 @@ OK, EINVAL, EWORKSPACE, ECUDA, EUNSUPPORTED = 0, -1, -2, -3, -4
 DTYPE_CODE = {"f32": 0, "f16": 1, "bf16": 2, "u8": 3, "u16": 4}
 INTEGRATOR_CODE = {"rk4": 0, "euler": 1}
 _EXPORTS = ("synthpix_workspace_bytes", "synthpix_render_pairs", "synthpix_render_pairs_staged",
+            "synthpix_render_pairs_from", "synthpix_seed_particles", "synthpix_render_backward",
             "synthpix_autotune_tile", "synthpix_last_error", "synthpix_version")
 STAGES = ("plan", "seed_advect", "bin_scan", "bin_scatter", "splat_epilogue")
 
@@ -76,6 +77,15 @@ def lib():
         L.synthpix_render_pairs_staged.argtypes = [C.POINTER(BatchDesc), C.POINTER(PairDesc), vp, C.c_int32,
                                                    vp, vp, vp, sz, vp, C.POINTER(C.c_void_p)]
         L.synthpix_render_pairs_staged.restype = C.c_int
+        L.synthpix_render_pairs_from.argtypes = [C.POINTER(BatchDesc), C.POINTER(PairDesc), vp, C.c_int32,
+                                                 vp, vp, vp, vp, sz, vp]
+        L.synthpix_render_pairs_from.restype = C.c_int
+        L.synthpix_seed_particles.argtypes = [C.POINTER(BatchDesc), C.POINTER(PairDesc), vp, C.c_int32, vp, vp,
+                                              sz, vp]
+        L.synthpix_seed_particles.restype = C.c_int
+        L.synthpix_render_backward.argtypes = [C.POINTER(BatchDesc), C.POINTER(PairDesc), vp, C.c_int32,
+                                               vp, vp, vp, vp, vp, vp, sz, vp]
+        L.synthpix_render_backward.restype = C.c_int
         L.synthpix_autotune_tile.argtypes = [C.POINTER(BatchDesc), C.POINTER(PairDesc), vp, C.c_int32,
                                              vp, vp, vp, sz, vp, C.c_int32, C.POINTER(C.c_int32),
                                              C.POINTER(C.c_float)]
@@ -271,8 +281,87 @@ class Renderer:
         self.graph.replay()
         return self.images
 
+    # --- differentiable use -------------------------------------------------
+    def _ptrs(self, stream):
+        import torch
+        st = stream if stream is not None else torch.cuda.current_stream()
+        pd = C.c_void_p(self.pairs_dev.data_ptr()) if self.pairs_dev is not None else None
+        return pd, C.c_void_p(self.workspace.data_ptr()), self.workspace.numel(), C.c_void_p(st.cuda_stream)
+
+    @staticmethod
+    def _vp(t):
+        return C.c_void_p(t.data_ptr()) if t is not None else None
+
+    def seed_particles(self, stream=None):
+        """[sum N, 3] float32 device tensor of the seeded (x0, y0, d)."""
+        import torch
+        n = sum(p.n_particles for p in self.pk.pairs[:self.pk.n_pairs])
+        out = torch.empty((max(n, 1), 3), dtype=torch.float32, device=self.device)
+        pd, ws, wsn, st = self._ptrs(stream)
+        _check(lib().synthpix_seed_particles(C.byref(self.pk.batch), self.pk.pairs, pd, self.pk.n_pairs,
+                                             self._vp(out), ws, wsn, st))
+        return out[:n]
+
+    def render_from(self, flows=None, particles=None, stream=None):
+        """Render with the given flow tensor (default: the packed flows) and particles (or seeded)."""
+        flows = self.flows if flows is None else flows
+        pd, ws, wsn, st = self._ptrs(stream)
+        _check(lib().synthpix_render_pairs_from(C.byref(self.pk.batch), self.pk.pairs, pd, self.pk.n_pairs,
+                                                self._vp(particles), self._vp(flows), self._vp(self.images),
+                                                ws, wsn, st))
+        return self.images
+
+    def backward(self, grad_images, flows=None, particles=None, grad_flows=None, grad_particles=None, stream=None):
+        """synthpix_render_backward: grad_flows is accumulated, grad_particles overwritten."""
+        flows = self.flows if flows is None else flows
+        pd, ws, wsn, st = self._ptrs(stream)
+        _check(lib().synthpix_render_backward(C.byref(self.pk.batch), self.pk.pairs, pd, self.pk.n_pairs,
+                                              self._vp(particles), self._vp(flows), self._vp(grad_images),
+                                              self._vp(grad_flows), self._vp(grad_particles), ws, wsn, st))
+
     def frames(self, b: int):
         """[2, H, W] view of pair b in the output buffer."""
         h, w = self.pk.shapes[b]
         o = self.pk.image_offsets[b]
         return self.images[o:o + 2 * h * w].view(2, h, w)
+
+
+def _render_fn():
+    import torch
+
+    class RenderFunction(torch.autograd.Function):
+        """images = render(flows, particles); differentiable in both (float output)."""
+
+        @staticmethod
+        def forward(ctx, flows, particles, renderer):
+            renderer.render_from(flows, particles)
+            ctx.renderer = renderer
+            ctx.save_for_backward(flows, particles)
+            return renderer.images.clone()
+
+        @staticmethod
+        def backward(ctx, grad):
+            flows, particles = ctx.saved_tensors
+            r = ctx.renderer
+            gf = torch.zeros_like(flows) if ctx.needs_input_grad[0] else None
+            gp = torch.empty_like(particles) if (particles is not None and ctx.needs_input_grad[1]) else None
+            r.backward(grad.contiguous().float(), flows, particles, gf, gp)
+            return gf, gp, None
+
+    return RenderFunction
+
+
+_RENDER_FN = None
+
+
+def render(renderer: "Renderer", flows, particles=None):
+    """Differentiable render through the C ABI (torch.autograd.Function).
+
+    flows: flat float32 device tensor laid out like ``renderer.flows``;
+    particles: None (seeded) or a [sum N, 3] float32 device tensor (x0, y0, d).
+    Returns the flat image buffer (FP32 output workloads).
+    """
+    global _RENDER_FN
+    if _RENDER_FN is None:
+        _RENDER_FN = _render_fn()
+    return _RENDER_FN.apply(flows, particles, renderer)

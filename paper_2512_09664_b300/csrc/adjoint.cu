@@ -1,0 +1,212 @@
+// The adjoint of the differentiable render (frames B_f = L * S_f with float
+// output, no blur; noise is additive and does not depend on the inputs): the
+// gradient of a loss with dL/dB given, with respect to the flow grids, the
+// frame-1 particle positions and the particle diameters.
+//
+//   k_adj_splat   one warp per (particle, frame): gathers
+//                 sum_ij dL/dB(i,j) L(i,j) dS(i,j)/d(x, y, sigma) over the
+//                 particle's window (a per-particle reduction, no pixel atomics)
+//   k_adj_advect  one thread per particle: recomputes the RK4 / Euler
+//                 substeps and sweeps them backwards with the bilinear
+//                 Jacobians, adding dL/dflow at each stage's four stencil nodes
+#include "common.cuh"
+#include "kernels.cuh"
+#include "particle.cuh"
+
+namespace spx {
+
+__device__ __forceinline__ float gauss_pdf(float t) { return 0.39894228040143267794f * expf(-0.5f * t * t); }
+
+// Pixel mass of column j for a particle at i + f (split), and its derivatives
+// with respect to the centre and to sigma:
+//   m = Phi(b) - Phi(a), dm/dc = (pdf(a) - pdf(b)) / sigma,
+//   dm/dsigma = (a pdf(a) - b pdf(b)) / sigma,  a = (j - c)/sigma, b = (j + 1 - c)/sigma.
+__device__ __forceinline__ void axis_terms(int32_t ic, float fc, int32_t j, float inv, float &m, float &dm,
+                                           float &ds) {
+    const float da = (float)(j - ic) - fc, db = (float)(j + 1 - ic) - fc;
+    const float ta = da * inv, tb = db * inv;
+    m = pixel_mass(edge_value(ta), edge_value(tb), da > 0.0f, db > 0.0f);
+    const float pa = gauss_pdf(ta), pb = gauss_pdf(tb);
+    dm = (pa - pb) * inv;
+    ds = (ta * pa - tb * pb) * inv;
+}
+
+__global__ void __launch_bounds__(256) k_adj_splat(KernelArgs a) {
+    if (*a.check != 1) return;
+    extern __shared__ float scr[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t wg = (int64_t)blockIdx.x * 8 + warp;
+    if (wg >= 2 * a.n_part) return;  // whole warp
+    const int64_t g = wg >> 1;
+    const int f = (int)(wg & 1);
+    const int b = upper_find(a.n_pairs, g, [&](int m) { return a.plan[m].part_base; });
+    const synthpix_pair_desc &D = a.descs[b];
+    const int32_t H = D.height, W = D.width;
+    const float4 p = f ? a.pos1[g] : a.pos0[g];
+    const float2 q = a.sa[g];
+    const int32_t ix = __float_as_int(p.z), iy = __float_as_int(p.w);
+    const float sig = q.x, amp = q.y;
+    const Window w = particle_window(ix, p.x, iy, p.y, 6.0f * sig, W, H);
+    if (w.j0 > w.j1 || w.i0 > w.i1) {
+        if (lane == 0) a.grad_frames[2 * g + f] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    const int nx = w.j1 - w.j0 + 1, ny = w.i1 - w.i0 + 1;
+    const int wq = a.warp_scratch;  // floats per array
+    float *ex = scr + warp * 8 * wq, *dex = ex + wq, *dsx = dex + wq, *lx = dsx + wq;
+    float *ey = lx + wq, *dey = ey + wq, *dsy = dey + wq, *ly = dsy + wq;
+    const float inv = __frcp_rn(sig);
+    const bool illum = D.illum_min != 1.0f || D.illum_max != 1.0f;
+    for (int e = lane; e < nx; e += 32) {
+        axis_terms(ix, p.x, w.j0 + e, inv, ex[e], dex[e], dsx[e]);
+        const float sv = sinpif(((float)(w.j0 + e) + 0.5f) / (float)W);
+        lx[e] = sv * sv;
+    }
+    for (int e = lane; e < ny; e += 32) {
+        axis_terms(iy, p.y, w.i0 + e, inv, ey[e], dey[e], dsy[e]);
+        const float sv = sinpif(((float)(w.i0 + e) + 0.5f) / (float)H);
+        ly[e] = sv * sv;
+    }
+    __syncwarp();
+    const float *G = a.grad_images + D.image_offset + (int64_t)f * H * W;
+    const float dl = D.illum_max - D.illum_min;
+    const float invx = 1.0f / (float)nx;
+    float sx = 0.f, sy = 0.f, ss = 0.f, sm = 0.f;
+    for (int m = lane; m < nx * ny; m += 32) {
+        const int r = min((int)(((float)m + 0.5f) * invx), ny - 1);
+        const int c = m - r * nx;
+        if ((unsigned)c >= (unsigned)nx) continue;
+        float gv = G[(int64_t)(w.i0 + r) * W + (w.j0 + c)];
+        if (illum) gv *= fmaf(dl, lx[c] * ly[r], D.illum_min);
+        sx = fmaf(gv * dex[c], ey[r], sx);
+        sy = fmaf(gv * ex[c], dey[r], sy);
+        ss = fmaf(gv, fmaf(dsx[c], ey[r], ex[c] * dsy[r]), ss);
+        sm = fmaf(gv * ex[c], ey[r], sm);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        sm += __shfl_xor_sync(0xffffffffu, sm, o);
+    }
+    // S = amp Ex Ey with amp = Ieff 2 pi sigma^2: d amp / d sigma = 2 amp / sigma
+    if (lane == 0) a.grad_frames[2 * g + f] = make_float4(amp * sx, amp * sy, amp * ss + 2.0f * amp * inv * sm, 0.f);
+}
+
+// Velocity at i + f (split) with its Jacobian (J = du/dx, du/dy, dv/dx, dv/dy)
+// and the four stencil nodes (flat index k * gw + l) with their weights.
+__device__ __forceinline__ float2 velocity_jac(const Flow &F, int32_t ix, float fx, int32_t iy, float fy, float J[4],
+                                               int node[4], float wgt[4]) {
+    int32_t l, k;
+    float tx, ty;
+    grid_coord(ix, fx, F.gw, F.W, l, tx);
+    grid_coord(iy, fy, F.gh, F.H, k, ty);
+    const int32_t l0 = min(max(l, 0), F.gw - 1), l1 = min(max(l + 1, 0), F.gw - 1);
+    const int32_t k0 = min(max(k, 0), F.gh - 1), k1 = min(max(k + 1, 0), F.gh - 1);
+    const float2 A = __ldg(F.f + (size_t)k0 * F.gw + l0), B = __ldg(F.f + (size_t)k0 * F.gw + l1);
+    const float2 C = __ldg(F.f + (size_t)k1 * F.gw + l0), D = __ldg(F.f + (size_t)k1 * F.gw + l1);
+    const float tu = fmaf(tx, B.x - A.x, A.x), tv = fmaf(tx, B.y - A.y, A.y);
+    const float bu = fmaf(tx, D.x - C.x, C.x), bv = fmaf(tx, D.y - C.y, C.y);
+    const float sxg = (float)F.gw / (float)F.W, syg = (float)F.gh / (float)F.H;
+    J[0] = ((1.0f - ty) * (B.x - A.x) + ty * (D.x - C.x)) * sxg;
+    J[1] = (bu - tu) * syg;
+    J[2] = ((1.0f - ty) * (B.y - A.y) + ty * (D.y - C.y)) * sxg;
+    J[3] = (bv - tv) * syg;
+    node[0] = k0 * F.gw + l0; wgt[0] = (1.0f - tx) * (1.0f - ty);
+    node[1] = k0 * F.gw + l1; wgt[1] = tx * (1.0f - ty);
+    node[2] = k1 * F.gw + l0; wgt[2] = (1.0f - tx) * ty;
+    node[3] = k1 * F.gw + l1; wgt[3] = tx * ty;
+    return make_float2(fmaf(ty, bu - tu, tu), fmaf(ty, bv - tv, tv));
+}
+
+__device__ __forceinline__ void scatter_flow(float *gf, const int node[4], const float wgt[4], float lx, float ly) {
+    if (!gf) return;
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+        atomicAdd(gf + 2 * node[n], wgt[n] * lx);
+        atomicAdd(gf + 2 * node[n] + 1, wgt[n] * ly);
+    }
+}
+
+__global__ void __launch_bounds__(128) k_adj_advect(KernelArgs a) {
+    if (*a.check != 1) return;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= a.n_part) return;
+    const int b = upper_find(a.n_pairs, g, [&](int m) { return a.plan[m].part_base; });
+    const PairPlan pl = a.plan[b];
+    const synthpix_pair_desc &D = a.descs[b];
+    const uint32_t i = (uint32_t)(g - pl.part_base);
+    const float4 g1 = a.grad_frames[2 * g], g2 = a.grad_frames[2 * g + 1];
+    const Seeded P = seed_particle(a, D, i, g);
+    const Flow F = pair_flow(a, D);
+    float *gf = a.grad_flows ? a.grad_flows + D.flow_offset : nullptr;
+    const int n = a.n_substeps;
+    const float h = a.dt / (float)n;
+    const float hh = 0.5f * h, h6 = h / 6.0f;
+    // forward, keeping the start of every substep (n <= kMaxAdjointSubsteps)
+    int32_t si[kMaxAdjointSubsteps], sj[kMaxAdjointSubsteps];
+    float sfx[kMaxAdjointSubsteps], sfy[kMaxAdjointSubsteps];
+    int32_t jx = P.ix, jy = P.iy;
+    float fx = P.fx, fy = P.fy;
+    for (int s = 0; s < n; ++s) {
+        si[s] = jx; sj[s] = jy; sfx[s] = fx; sfy[s] = fy;
+        advect_split(F, h, 1, a.integrator, jx, fx, jy, fy);
+    }
+    float lx = g2.x, ly = g2.y;  // dL / d(frame-2 position)
+    for (int s = n - 1; s >= 0; --s) {
+        const int32_t px = si[s], py = sj[s];
+        const float ux = sfx[s], uy = sfy[s];
+        float J1[4], w1[4];
+        int n1[4];
+        const float2 k1 = velocity_jac(F, px, ux, py, uy, J1, n1, w1);
+        if (a.integrator == SYNTHPIX_EULER) {
+            scatter_flow(gf, n1, w1, h * lx, h * ly);
+            const float ax = lx + h * (J1[0] * lx + J1[2] * ly);
+            const float ay = ly + h * (J1[1] * lx + J1[3] * ly);
+            lx = ax;
+            ly = ay;
+            continue;
+        }
+        float J2[4], w2[4], J3[4], w3[4], J4[4], w4[4];
+        int n2[4], n3[4], n4[4];
+        const float2 k2 = velocity_jac(F, px, fmaf(hh, k1.x, ux), py, fmaf(hh, k1.y, uy), J2, n2, w2);
+        const float2 k3 = velocity_jac(F, px, fmaf(hh, k2.x, ux), py, fmaf(hh, k2.y, uy), J3, n3, w3);
+        velocity_jac(F, px, fmaf(h, k3.x, ux), py, fmaf(h, k3.y, uy), J4, n4, w4);
+        // p+ = p + h/6 (k1 + 2 k2 + 2 k3 + k4), k_m = U(q_m): adjoints of the stages
+        const float k4x = h6 * lx, k4y = h6 * ly;
+        const float k3x = 2.0f * h6 * lx + h * (J4[0] * k4x + J4[2] * k4y);
+        const float k3y = 2.0f * h6 * ly + h * (J4[1] * k4x + J4[3] * k4y);
+        const float k2x = 2.0f * h6 * lx + hh * (J3[0] * k3x + J3[2] * k3y);
+        const float k2y = 2.0f * h6 * ly + hh * (J3[1] * k3x + J3[3] * k3y);
+        const float k1x = h6 * lx + hh * (J2[0] * k2x + J2[2] * k2y);
+        const float k1y = h6 * ly + hh * (J2[1] * k2x + J2[3] * k2y);
+        scatter_flow(gf, n1, w1, k1x, k1y);
+        scatter_flow(gf, n2, w2, k2x, k2y);
+        scatter_flow(gf, n3, w3, k3x, k3y);
+        scatter_flow(gf, n4, w4, k4x, k4y);
+        const float ax = lx + (J1[0] * k1x + J1[2] * k1y) + (J2[0] * k2x + J2[2] * k2y) + (J3[0] * k3x + J3[2] * k3y) +
+                         (J4[0] * k4x + J4[2] * k4y);
+        const float ay = ly + (J1[1] * k1x + J1[3] * k1y) + (J2[1] * k2x + J2[3] * k2y) + (J3[1] * k3x + J3[3] * k3y) +
+                         (J4[1] * k4x + J4[3] * k4y);
+        lx = ax;
+        ly = ay;
+    }
+    if (a.grad_particles) {
+        a.grad_particles[3 * g] = g1.x + lx;
+        a.grad_particles[3 * g + 1] = g1.y + ly;
+        a.grad_particles[3 * g + 2] = 0.25f * (g1.z + g2.z);  // sigma = d / 4
+    }
+}
+
+cudaError_t launch_adjoint(const KernelArgs &a, cudaStream_t st) {
+    if (a.n_part == 0) return cudaGetLastError();
+    const size_t smem = (size_t)8 * 8 * a.warp_scratch * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_adj_splat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_adj_splat<<<(unsigned)((2 * a.n_part + 7) / 8), 256, smem, st>>>(a);
+    k_adj_advect<<<(unsigned)((a.n_part + 127) / 128), 128, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace spx

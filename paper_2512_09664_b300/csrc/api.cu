@@ -148,6 +148,7 @@ int make_plan_tile(const synthpix_batch_desc *batch, const synthpix_pair_desc *p
     L.sa = take((size_t)L.n_part * 8);
     L.rec = take((size_t)L.n_list * sizeof(spx::Record) + 64);  // + read-over of 16-byte staging
     L.inter = take((size_t)L.n_inter * 2);
+    L.gfr = take((size_t)L.n_part * 2 * sizeof(float4));
     L.total = o;
     return SYNTHPIX_OK;
 }
@@ -191,9 +192,20 @@ size_t synthpix_workspace_bytes(const synthpix_batch_desc *batch, const synthpix
 
 }  // extern "C"
 
-static int render_impl(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
-                       const synthpix_pair_desc *pairs_dev, int32_t n_pairs, const float *flows, void *images,
-                       void *workspace, size_t workspace_bytes, void *stream, cudaEvent_t const *ev) {
+enum class Mode { Render, Seed, Backward };
+
+// Optional arguments of the seeding and adjoint entry points.
+struct Extra {
+    const float *particles_in = nullptr;
+    float *particles_out = nullptr;
+    const float *grad_images = nullptr;
+    float *grad_flows = nullptr;
+    float *grad_particles = nullptr;
+};
+
+static int run(Mode mode, const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
+               const synthpix_pair_desc *pairs_dev, int32_t n_pairs, const float *flows, void *images,
+               void *workspace, size_t workspace_bytes, void *stream, cudaEvent_t const *ev, const Extra &x) {
     Plan P;
     int rc = make_plan(batch, pairs, n_pairs, P);
     if (rc) return rc;
@@ -201,9 +213,27 @@ static int render_impl(const synthpix_batch_desc *batch, const synthpix_pair_des
         g_err[0] = 0;
         return SYNTHPIX_OK;
     }
-    if (!flows || ((uintptr_t)flows & 7)) return fail(SYNTHPIX_EINVAL, "flows is NULL or not 8-byte aligned");
-    if (!images || ((uintptr_t)images % elem_size(batch->out_dtype)))
+    if (mode != Mode::Seed && (!flows || ((uintptr_t)flows & 7)))
+        return fail(SYNTHPIX_EINVAL, "flows is NULL or not 8-byte aligned");
+    if (mode == Mode::Render && (!images || ((uintptr_t)images % elem_size(batch->out_dtype))))
         return fail(SYNTHPIX_EINVAL, "images is NULL or misaligned for its element type");
+    if (mode == Mode::Seed && (!x.particles_out || ((uintptr_t)x.particles_out & 3)))
+        return fail(SYNTHPIX_EINVAL, "particles_out is NULL or not 4-byte aligned");
+    if (x.particles_in && ((uintptr_t)x.particles_in & 3))
+        return fail(SYNTHPIX_EINVAL, "particles_in is not 4-byte aligned");
+    if (mode == Mode::Backward) {
+        if (!x.grad_images || ((uintptr_t)x.grad_images & 3))
+            return fail(SYNTHPIX_EINVAL, "grad_images is NULL or not 4-byte aligned");
+        if ((x.grad_flows && ((uintptr_t)x.grad_flows & 3)) || (x.grad_particles && ((uintptr_t)x.grad_particles & 3)))
+            return fail(SYNTHPIX_EINVAL, "gradient outputs must be 4-byte aligned");
+        if (batch->out_dtype != SYNTHPIX_F32)
+            return fail(SYNTHPIX_EUNSUPPORTED, "the adjoint needs out_dtype F32 (quantisation has no gradient)");
+        if (batch->n_substeps > spx::kMaxAdjointSubsteps)
+            return fail(SYNTHPIX_EUNSUPPORTED, "the adjoint supports at most %d substeps", spx::kMaxAdjointSubsteps);
+        for (int32_t b = 0; b < n_pairs; ++b)
+            if (pairs[b].blur_sigma != 0.0f)
+                return fail(SYNTHPIX_EUNSUPPORTED, "pair %d: the adjoint does not support blur", b);
+    }
     if (!workspace || ((uintptr_t)workspace & 255))
         return fail(SYNTHPIX_EWORKSPACE, "workspace is NULL or not 256-byte aligned");
     if (workspace_bytes < P.L.total)
@@ -228,8 +258,10 @@ static int render_impl(const synthpix_batch_desc *batch, const synthpix_pair_des
     if (ev && ev[0]) cudaEventRecord(ev[0], st);
     e = spx::launch_plan(descs, n_pairs, P.tile, P.fused, plan, L, check, blur_w, ticket, st);
     if (e != cudaSuccess) return fail(SYNTHPIX_ECUDA, "plan launch: %s", cudaGetErrorString(e));
-    e = cudaMemsetAsync(ws + L.count, 0, (size_t)L.n_tiles * 4, st);
-    if (e != cudaSuccess) return fail(SYNTHPIX_ECUDA, "count reset: %s", cudaGetErrorString(e));
+    if (mode == Mode::Render) {
+        e = cudaMemsetAsync(ws + L.count, 0, (size_t)L.n_tiles * 4, st);
+        if (e != cudaSuccess) return fail(SYNTHPIX_ECUDA, "count reset: %s", cudaGetErrorString(e));
+    }
     if (ev && ev[1]) cudaEventRecord(ev[1], st);
 
     spx::KernelArgs a;
@@ -250,7 +282,7 @@ static int render_impl(const synthpix_batch_desc *batch, const synthpix_pair_des
     a.pos0 = reinterpret_cast<float4 *>(ws + L.pos);
     a.pos1 = a.pos0 + L.n_part;
     a.sa = reinterpret_cast<float2 *>(ws + L.sa);
-    a.count = reinterpret_cast<uint32_t *>(ws + L.count);
+    a.count = mode == Mode::Render ? reinterpret_cast<uint32_t *>(ws + L.count) : nullptr;
     a.off = reinterpret_cast<uint32_t *>(ws + L.off);
     a.cursor = reinterpret_cast<uint32_t *>(ws + L.cursor);
     a.items = reinterpret_cast<spx::ItemInfo *>(ws + L.items);
@@ -260,18 +292,41 @@ static int render_impl(const synthpix_batch_desc *batch, const synthpix_pair_des
     a.blur_w = blur_w;
     a.inter_dtype = batch->inter_dtype;
     a.inter = ws + L.inter;
+    a.particles_in = x.particles_in;
+    a.particles_out = mode == Mode::Seed ? x.particles_out : nullptr;
+    a.grad_images = x.grad_images;
+    a.grad_flows = x.grad_flows;
+    a.grad_particles = x.grad_particles;
+    a.grad_frames = reinterpret_cast<float4 *>(ws + L.gfr);
     a.smem_edge = P.tile + 2 * P.max_r;
     const int wmax = std::min(spx::window_max(P.max_d), a.smem_edge);
     a.warp_scratch = 4 * (wmax + 2);
-    if (spx::splat_smem_bytes(a.smem_edge, a.tile, a.warp_scratch, a.rec_buf_bytes) > 227 * 1024)
-        return fail(SYNTHPIX_EUNSUPPORTED, "tile %d with blur radius %d needs too much shared memory", P.tile,
-                    P.max_r);
-    e = spx::launch_prep(a, st, ev);
-    if (e != cudaSuccess) return fail(SYNTHPIX_ECUDA, "seeding/binning launch: %s", cudaGetErrorString(e));
-    e = spx::launch_splat(a, batch->out_dtype, st, ev);
-    if (e != cudaSuccess) return fail(SYNTHPIX_ECUDA, "splat launch: %s", cudaGetErrorString(e));
+    if (mode == Mode::Seed) {
+        e = spx::launch_seed_only(a, st);
+        if (e != cudaSuccess) return fail(SYNTHPIX_ECUDA, "seeding launch: %s", cudaGetErrorString(e));
+    } else if (mode == Mode::Backward) {
+        a.warp_scratch = spx::window_max(P.max_d) + 2;  // floats per scratch array of the adjoint splat
+        e = spx::launch_seed_only(a, st);                // positions of both frames
+        if (e == cudaSuccess) e = spx::launch_adjoint(a, st);
+        if (e != cudaSuccess) return fail(SYNTHPIX_ECUDA, "adjoint launch: %s", cudaGetErrorString(e));
+    } else {
+        if (spx::splat_smem_bytes(a.smem_edge, a.tile, a.warp_scratch, a.rec_buf_bytes) > 227 * 1024)
+            return fail(SYNTHPIX_EUNSUPPORTED, "tile %d with blur radius %d needs too much shared memory", P.tile,
+                        P.max_r);
+        e = spx::launch_prep(a, st, ev);
+        if (e != cudaSuccess) return fail(SYNTHPIX_ECUDA, "seeding/binning launch: %s", cudaGetErrorString(e));
+        e = spx::launch_splat(a, batch->out_dtype, st, ev);
+        if (e != cudaSuccess) return fail(SYNTHPIX_ECUDA, "splat launch: %s", cudaGetErrorString(e));
+    }
     g_err[0] = 0;
     return SYNTHPIX_OK;
+}
+
+static int render_impl(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
+                       const synthpix_pair_desc *pairs_dev, int32_t n_pairs, const float *flows, void *images,
+                       void *workspace, size_t workspace_bytes, void *stream, cudaEvent_t const *ev) {
+    return run(Mode::Render, batch, pairs, pairs_dev, n_pairs, flows, images, workspace, workspace_bytes, stream, ev,
+               Extra());
 }
 
 extern "C" {
@@ -328,6 +383,38 @@ int synthpix_autotune_tile(const synthpix_batch_desc *batch, const synthpix_pair
     if (best_ms) *best_ms = best;
     g_err[0] = 0;
     return SYNTHPIX_OK;
+}
+
+int synthpix_render_pairs_from(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
+                               const synthpix_pair_desc *pairs_dev, int32_t n_pairs, const float *particles_in,
+                               const float *flows, void *images, void *workspace, size_t workspace_bytes,
+                               void *stream) {
+    Extra x;
+    x.particles_in = particles_in;
+    return run(Mode::Render, batch, pairs, pairs_dev, n_pairs, flows, images, workspace, workspace_bytes, stream,
+               nullptr, x);
+}
+
+int synthpix_seed_particles(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
+                            const synthpix_pair_desc *pairs_dev, int32_t n_pairs, float *particles_out,
+                            void *workspace, size_t workspace_bytes, void *stream) {
+    Extra x;
+    x.particles_out = particles_out;
+    return run(Mode::Seed, batch, pairs, pairs_dev, n_pairs, nullptr, nullptr, workspace, workspace_bytes, stream,
+               nullptr, x);
+}
+
+int synthpix_render_backward(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
+                             const synthpix_pair_desc *pairs_dev, int32_t n_pairs, const float *particles_in,
+                             const float *flows, const float *grad_images, float *grad_flows, float *grad_particles,
+                             void *workspace, size_t workspace_bytes, void *stream) {
+    Extra x;
+    x.particles_in = particles_in;
+    x.grad_images = grad_images;
+    x.grad_flows = grad_flows;
+    x.grad_particles = grad_particles;
+    return run(Mode::Backward, batch, pairs, pairs_dev, n_pairs, flows, nullptr, workspace, workspace_bytes, stream,
+               nullptr, x);
 }
 
 int synthpix_render_pairs_staged(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,

@@ -1,0 +1,190 @@
+// Device functions shared by the forward kernels (prep.cu) and the adjoint
+// (adjoint.cu): particle attributes from the Philox streams, the bilinear
+// flow and the RK4 / Euler advection on split coordinates.
+#pragma once
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace spx {
+
+// Largest b with base(b) <= key (bases non-decreasing, base(0) = 0).
+template <typename F>
+__device__ __forceinline__ int upper_find(int n, int64_t key, F base) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (base(mid) <= key) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+struct Flow {
+    const float2 *f;
+    int32_t gh, gw, H, W;
+};
+
+// Grid coordinate of an image coordinate i + f along one axis:
+// g = (i + f) * gn / n - 1/2 = cell + frac, computed without rounding the
+// integer part (integer division when the grid and image sizes differ).
+__device__ __forceinline__ void grid_coord(int32_t i, float f, int32_t gn, int32_t n, int32_t &cell, float &t) {
+    float g;
+    int32_t base;
+    if (gn == n) {
+        base = i;
+        g = f - 0.5f;
+    } else {
+        const long long num = (long long)i * gn;
+        long long q = num / n;
+        long long r = num - q * n;
+        if (r < 0) { r += n; q -= 1; }
+        base = (int32_t)q;
+        g = fmaf(f, (float)gn, (float)r) / (float)n - 0.5f;
+    }
+    const float fl = floorf(g);
+    cell = base + (int32_t)fl;
+    t = g - fl;
+}
+
+// Bilinear velocity on the cell-centred grid, indices clamped (border).
+__device__ __forceinline__ float2 velocity(const Flow &F, int32_t ix, float fx, int32_t iy, float fy) {
+    int32_t l, k;
+    float tx, ty;
+    grid_coord(ix, fx, F.gw, F.W, l, tx);
+    grid_coord(iy, fy, F.gh, F.H, k, ty);
+    const int32_t l0 = min(max(l, 0), F.gw - 1), l1 = min(max(l + 1, 0), F.gw - 1);
+    const int32_t k0 = min(max(k, 0), F.gh - 1), k1 = min(max(k + 1, 0), F.gh - 1);
+    const float2 a = __ldg(F.f + (size_t)k0 * F.gw + l0);
+    const float2 b = __ldg(F.f + (size_t)k0 * F.gw + l1);
+    const float2 c = __ldg(F.f + (size_t)k1 * F.gw + l0);
+    const float2 d = __ldg(F.f + (size_t)k1 * F.gw + l1);
+    const float tu = fmaf(tx, b.x - a.x, a.x), tv = fmaf(tx, b.y - a.y, a.y);
+    const float bu = fmaf(tx, d.x - c.x, c.x), bv = fmaf(tx, d.y - c.y, c.y);
+    return make_float2(fmaf(ty, bu - tu, tu), fmaf(ty, bv - tv, tv));
+}
+
+// Clipped pixel window [j0, j1] x [i0, i1] of a particle (empty: j0 > j1).
+struct Window {
+    int32_t j0, j1, i0, i1;
+};
+
+__device__ __forceinline__ Window particle_window(int32_t ix, float fx, int32_t iy, float fy, float r15,
+                                                  int32_t W, int32_t H) {
+    Window w;
+    w.j0 = max(ix + (int32_t)floorf(fx - r15), 0);
+    w.j1 = min(ix + (int32_t)floorf(fx + r15), W - 1);
+    w.i0 = max(iy + (int32_t)floorf(fy - r15), 0);
+    w.i1 = min(iy + (int32_t)floorf(fy + r15), H - 1);
+    return w;
+}
+
+// Tiles whose halo-widened rectangle meets the window.
+__device__ __forceinline__ void window_tiles(const Window &w, int32_t halo, int32_t tile, int32_t W, int32_t H,
+                                             int32_t &tx0, int32_t &tx1, int32_t &ty0, int32_t &ty1) {
+    tx0 = max(w.j0 - halo, 0) / tile;
+    tx1 = min(w.j1 + halo, W - 1) / tile;
+    ty0 = max(w.i0 - halo, 0) / tile;
+    ty1 = min(w.i1 + halo, H - 1) / tile;
+}
+
+
+// ---------------------------------------------------------------------------
+// pixel integration of Eq. 1 (separable erf differences)
+// ---------------------------------------------------------------------------
+// Lower-tail mass Phi(t) for t <= 0, minus the upper-tail mass 1 - Phi(t)
+// for t > 0 (both from erfc, so tails keep their relative accuracy).
+__device__ __forceinline__ float edge_value(float t) {
+    const float q = 0.5f * erfcf(fabsf(t) * 0.70710678118654752440f);
+    return t > 0.0f ? -q : q;
+}
+
+// Mass of the unit Gaussian between two pixel edges from their edge values:
+// Phi(b) - Phi(a) = sb - sa, plus 1 when a <= 0 < b.
+__device__ __forceinline__ float pixel_mass(float sa, float sb, bool a_pos, bool b_pos) {
+    if (b_pos && !a_pos) return (1.0f - sa) + sb;
+    return fmaxf(sb - sa, 0.0f);
+}
+
+// A particle of frame 1: split position, sigma = d / 4, amplitude Ieff 2 pi sigma^2.
+struct Seeded {
+    int32_t ix, iy;
+    float fx, fy;
+    float sigma, amp;
+};
+
+// Attributes of particle i of a pair (Section 2, "Sampling the particles":
+// uniform position over the image, parameters from their intervals; the
+// clipped-normal diameter via Box-Muller).  With a.particles_in, position and
+// diameter are taken from it (FP32 x0, y0, d of global particle g) instead.
+__device__ __forceinline__ Seeded seed_particle(const KernelArgs &a, const synthpix_pair_desc &D, uint32_t i,
+                                                int64_t g) {
+    Seeded P;
+    const int32_t H = D.height, W = D.width;
+    const uint4 wa = stream_words(a.seed, D.pair_id, i, kTagAttrA);
+    const uint4 wb = stream_words(a.seed, D.pair_id, i, kTagAttrB);
+    float d;
+    if (a.particles_in) {
+        const float x0 = a.particles_in[3 * g], y0 = a.particles_in[3 * g + 1];
+        const float fl = floorf(x0), fk = floorf(y0);
+        P.ix = (int32_t)fminf(fmaxf(fl, -1.0e9f), 1.0e9f);
+        P.iy = (int32_t)fminf(fmaxf(fk, -1.0e9f), 1.0e9f);
+        P.fx = x0 - fl;  // exact
+        P.fy = y0 - fk;
+        d = a.particles_in[3 * g + 2];
+    } else {
+        const unsigned long long px = (unsigned long long)(wa.x >> 8) * (uint32_t)W;
+        const unsigned long long py = (unsigned long long)(wa.y >> 8) * (uint32_t)H;
+        P.ix = (int32_t)(px >> 24);
+        P.iy = (int32_t)(py >> 24);
+        P.fx = (float)(uint32_t)(px & 0xFFFFFFu) * (1.0f / 16777216.0f);  // exact
+        P.fy = (float)(uint32_t)(py & 0xFFFFFFu) * (1.0f / 16777216.0f);
+        if (D.d_dist == 0) {
+            d = fminf(fmaf(u24f(wa.z), D.d_max - D.d_min, D.d_min), D.d_max);
+        } else {
+            float s, c;
+            sincospif(2.0f * u24f(wb.y), &s, &c);
+            const float r = sqrtf(-2.0f * logf(uo24f(wa.z)));
+            d = fminf(fmaxf(fmaf(D.d_sigma, r * c, D.d_mu), D.d_min), D.d_max);
+        }
+    }
+    const float I0 = fmaf(u24f(wa.w), D.i_max - D.i_min, D.i_min);
+    const float z = fmaf(u24f(wb.x), D.z_max - D.z_min, D.z_min);
+    float gain = 1.0f;
+    if (D.sheet_sigma > 0.0f) gain = expf(-(z * z) / (2.0f * D.sheet_sigma * D.sheet_sigma));
+    P.sigma = 0.25f * d;
+    P.amp = (I0 * gain) * (6.28318530717958647692f * P.sigma * P.sigma);  // Ieff * 2 pi sigma^2
+    return P;
+}
+
+__device__ __forceinline__ Flow pair_flow(const KernelArgs &a, const synthpix_pair_desc &D) {
+    Flow F;
+    F.f = reinterpret_cast<const float2 *>(a.flows + D.flow_offset);
+    F.gh = D.flow_h;
+    F.gw = D.flow_w;
+    F.H = D.height;
+    F.W = D.width;
+    return F;
+}
+
+// Frame-2 position: n substeps of RK4 (or Euler) over dt, on split coordinates.
+__device__ __forceinline__ void advect_split(const Flow &F, float dt, int n_substeps, int integrator, int32_t &jx,
+                                             float &gx, int32_t &jy, float &gy) {
+    const float h = dt / (float)n_substeps;
+    const float hh = 0.5f * h, h6 = h / 6.0f;
+    for (int s = 0; s < n_substeps; ++s) {
+        const float2 k1 = velocity(F, jx, gx, jy, gy);
+        if (integrator == SYNTHPIX_EULER) {
+            split_add(jx, gx, __fmul_rn(h, k1.x));
+            split_add(jy, gy, __fmul_rn(h, k1.y));
+            continue;
+        }
+        const float2 k2 = velocity(F, jx, fmaf(hh, k1.x, gx), jy, fmaf(hh, k1.y, gy));
+        const float2 k3 = velocity(F, jx, fmaf(hh, k2.x, gx), jy, fmaf(hh, k2.y, gy));
+        const float2 k4 = velocity(F, jx, fmaf(h, k3.x, gx), jy, fmaf(h, k3.y, gy));
+        split_add(jx, gx, __fmul_rn(h6, (k1.x + k4.x) + 2.0f * (k2.x + k3.x)));
+        split_add(jy, gy, __fmul_rn(h6, (k1.y + k4.y) + 2.0f * (k2.y + k3.y)));
+    }
+}
+
+}  // namespace spx

@@ -19,92 +19,13 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "particle.cuh"
 
 namespace spx {
 
 // ---------------------------------------------------------------------------
 // helpers
 // ---------------------------------------------------------------------------
-
-// Largest b with base(b) <= key (bases non-decreasing, base(0) = 0).
-template <typename F>
-__device__ __forceinline__ int upper_find(int n, int64_t key, F base) {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (base(mid) <= key) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
-struct Flow {
-    const float2 *f;
-    int32_t gh, gw, H, W;
-};
-
-// Grid coordinate of an image coordinate i + f along one axis:
-// g = (i + f) * gn / n - 1/2 = cell + frac, computed without rounding the
-// integer part (integer division when the grid and image sizes differ).
-__device__ __forceinline__ void grid_coord(int32_t i, float f, int32_t gn, int32_t n, int32_t &cell, float &t) {
-    float g;
-    int32_t base;
-    if (gn == n) {
-        base = i;
-        g = f - 0.5f;
-    } else {
-        const long long num = (long long)i * gn;
-        long long q = num / n;
-        long long r = num - q * n;
-        if (r < 0) { r += n; q -= 1; }
-        base = (int32_t)q;
-        g = fmaf(f, (float)gn, (float)r) / (float)n - 0.5f;
-    }
-    const float fl = floorf(g);
-    cell = base + (int32_t)fl;
-    t = g - fl;
-}
-
-// Bilinear velocity on the cell-centred grid, indices clamped (border).
-__device__ __forceinline__ float2 velocity(const Flow &F, int32_t ix, float fx, int32_t iy, float fy) {
-    int32_t l, k;
-    float tx, ty;
-    grid_coord(ix, fx, F.gw, F.W, l, tx);
-    grid_coord(iy, fy, F.gh, F.H, k, ty);
-    const int32_t l0 = min(max(l, 0), F.gw - 1), l1 = min(max(l + 1, 0), F.gw - 1);
-    const int32_t k0 = min(max(k, 0), F.gh - 1), k1 = min(max(k + 1, 0), F.gh - 1);
-    const float2 a = __ldg(F.f + (size_t)k0 * F.gw + l0);
-    const float2 b = __ldg(F.f + (size_t)k0 * F.gw + l1);
-    const float2 c = __ldg(F.f + (size_t)k1 * F.gw + l0);
-    const float2 d = __ldg(F.f + (size_t)k1 * F.gw + l1);
-    const float tu = fmaf(tx, b.x - a.x, a.x), tv = fmaf(tx, b.y - a.y, a.y);
-    const float bu = fmaf(tx, d.x - c.x, c.x), bv = fmaf(tx, d.y - c.y, c.y);
-    return make_float2(fmaf(ty, bu - tu, tu), fmaf(ty, bv - tv, tv));
-}
-
-// Clipped pixel window [j0, j1] x [i0, i1] of a particle (empty: j0 > j1).
-struct Window {
-    int32_t j0, j1, i0, i1;
-};
-
-__device__ __forceinline__ Window particle_window(int32_t ix, float fx, int32_t iy, float fy, float r15,
-                                                  int32_t W, int32_t H) {
-    Window w;
-    w.j0 = max(ix + (int32_t)floorf(fx - r15), 0);
-    w.j1 = min(ix + (int32_t)floorf(fx + r15), W - 1);
-    w.i0 = max(iy + (int32_t)floorf(fy - r15), 0);
-    w.i1 = min(iy + (int32_t)floorf(fy + r15), H - 1);
-    return w;
-}
-
-// Tiles whose halo-widened rectangle meets the window.
-__device__ __forceinline__ void window_tiles(const Window &w, int32_t halo, int32_t tile, int32_t W, int32_t H,
-                                             int32_t &tx0, int32_t &tx1, int32_t &ty0, int32_t &ty1) {
-    tx0 = max(w.j0 - halo, 0) / tile;
-    tx1 = min(w.j1 + halo, W - 1) / tile;
-    ty0 = max(w.i0 - halo, 0) / tile;
-    ty1 = min(w.i1 + halo, H - 1) / tile;
-}
 
 // ---------------------------------------------------------------------------
 // k_plan: per-pair prefix sums (one CTA of 1024 threads)
@@ -189,55 +110,24 @@ __global__ void __launch_bounds__(256) k_seed_advect(KernelArgs a) {
     const int32_t H = D.height, W = D.width;
     const uint32_t i = (uint32_t)(g - pl.part_base);
 
-    // attributes (Section 2: uniform position over the image, parameters from
-    // their intervals; clipped-normal diameter via Box-Muller)
-    const uint4 wa = stream_words(a.seed, D.pair_id, i, kTagAttrA);
-    const uint4 wb = stream_words(a.seed, D.pair_id, i, kTagAttrB);
-    const unsigned long long px = (unsigned long long)(wa.x >> 8) * (uint32_t)W;
-    const unsigned long long py = (unsigned long long)(wa.y >> 8) * (uint32_t)H;
-    int32_t ix = (int32_t)(px >> 24), iy = (int32_t)(py >> 24);
-    float fx = (float)(uint32_t)(px & 0xFFFFFFu) * (1.0f / 16777216.0f);  // exact
-    float fy = (float)(uint32_t)(py & 0xFFFFFFu) * (1.0f / 16777216.0f);
-    float d;
-    if (D.d_dist == 0) {
-        d = fminf(fmaf(u24f(wa.z), D.d_max - D.d_min, D.d_min), D.d_max);
-    } else {
-        float s, c;
-        sincospif(2.0f * u24f(wb.y), &s, &c);
-        const float r = sqrtf(-2.0f * logf(uo24f(wa.z)));
-        d = fminf(fmaxf(fmaf(D.d_sigma, r * c, D.d_mu), D.d_min), D.d_max);
+    const Seeded P = seed_particle(a, D, i, g);
+    a.sa[g] = make_float2(P.sigma, P.amp);
+    a.pos0[g] = make_float4(P.fx, P.fy, __int_as_float(P.ix), __int_as_float(P.iy));
+    if (a.particles_out) {
+        a.particles_out[3 * g] = (float)P.ix + P.fx;
+        a.particles_out[3 * g + 1] = (float)P.iy + P.fy;
+        a.particles_out[3 * g + 2] = 4.0f * P.sigma;
+        return;
     }
-    const float I0 = fmaf(u24f(wa.w), D.i_max - D.i_min, D.i_min);
-    const float z = fmaf(u24f(wb.x), D.z_max - D.z_min, D.z_min);
-    float gain = 1.0f;
-    if (D.sheet_sigma > 0.0f) gain = expf(-(z * z) / (2.0f * D.sheet_sigma * D.sheet_sigma));
-    const float sigma = 0.25f * d;
-    const float amp = (I0 * gain) * (6.28318530717958647692f * sigma * sigma);  // Ieff * 2 pi sigma^2
-    a.sa[g] = make_float2(sigma, amp);
-    a.pos0[g] = make_float4(fx, fy, __int_as_float(ix), __int_as_float(iy));
-
     // frame-2 position: displacement over dt through the bilinear flow
-    Flow F;
-    F.f = reinterpret_cast<const float2 *>(a.flows + D.flow_offset);
-    F.gh = D.flow_h; F.gw = D.flow_w; F.H = H; F.W = W;
-    const float h = a.dt / (float)a.n_substeps;
-    const float hh = 0.5f * h, h6 = h / 6.0f;
-    int32_t jx = ix, jy = iy;
-    float gx = fx, gy = fy;
-    for (int s = 0; s < a.n_substeps; ++s) {
-        const float2 k1 = velocity(F, jx, gx, jy, gy);
-        if (a.integrator == SYNTHPIX_EULER) {
-            split_add(jx, gx, __fmul_rn(h, k1.x));
-            split_add(jy, gy, __fmul_rn(h, k1.y));
-            continue;
-        }
-        const float2 k2 = velocity(F, jx, fmaf(hh, k1.x, gx), jy, fmaf(hh, k1.y, gy));
-        const float2 k3 = velocity(F, jx, fmaf(hh, k2.x, gx), jy, fmaf(hh, k2.y, gy));
-        const float2 k4 = velocity(F, jx, fmaf(h, k3.x, gx), jy, fmaf(h, k3.y, gy));
-        split_add(jx, gx, __fmul_rn(h6, (k1.x + k4.x) + 2.0f * (k2.x + k3.x)));
-        split_add(jy, gy, __fmul_rn(h6, (k1.y + k4.y) + 2.0f * (k2.y + k3.y)));
-    }
+    Flow F = pair_flow(a, D);
+    int32_t jx = P.ix, jy = P.iy;
+    float gx = P.fx, gy = P.fy;
+    advect_split(F, a.dt, a.n_substeps, a.integrator, jx, gx, jy, gy);
     a.pos1[g] = make_float4(gx, gy, __int_as_float(jx), __int_as_float(jy));
+    if (!a.count) return;
+    const int32_t ix = P.ix, iy = P.iy;
+    const float fx = P.fx, fy = P.fy, sigma = P.sigma;
 
     // bin counts of both frames
     const float r15 = 6.0f * sigma;  // 1.5 d
@@ -352,6 +242,15 @@ cudaError_t launch_prep(const KernelArgs &a, cudaStream_t st, cudaEvent_t const 
     mark(3);
     if (a.n_part > 0) k_scatter<<<nb, 256, 0, st>>>(a);
     mark(4);
+    return cudaGetLastError();
+}
+
+}  // namespace spx
+
+namespace spx {
+
+cudaError_t launch_seed_only(const KernelArgs &a, cudaStream_t st) {
+    if (a.n_part > 0) k_seed_advect<<<(unsigned)((a.n_part + 255) / 256), 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -15,6 +15,7 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "particle.cuh"
 
 namespace spx {
 
@@ -57,20 +58,6 @@ __device__ __forceinline__ int record_lead(int64_t first) { return (int)((first 
 // ---------------------------------------------------------------------------
 // pixel integration of Eq. 1
 // ---------------------------------------------------------------------------
-
-// Lower-tail mass Phi(t) for t <= 0, minus the upper-tail mass 1 - Phi(t)
-// for t > 0 (both from erfc, so tails keep their relative accuracy).
-__device__ __forceinline__ float edge_value(float t) {
-    const float q = 0.5f * erfcf(fabsf(t) * 0.70710678118654752440f);
-    return t > 0.0f ? -q : q;
-}
-
-// Mass of the unit Gaussian between two pixel edges from their edge values:
-// Phi(b) - Phi(a) = sb - sa, plus 1 when a <= 0 < b.
-__device__ __forceinline__ float pixel_mass(float sa, float sb, bool a_pos, bool b_pos) {
-    if (b_pos && !a_pos) return (1.0f - sa) + sb;
-    return fmaxf(sb - sa, 0.0f);
-}
 
 // ---------------------------------------------------------------------------
 // exact fixed-point accumulation
