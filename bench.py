@@ -45,7 +45,9 @@ FP32_LANES_PER_SM = 128
 # ncu DRAM traffic of k_splat per launch (bytes), with the sha256 of the
 # kernel source (splat.cu) it was taken on; reported only while the source is
 # unchanged.
-SPLAT_TRAFFIC = {"sha256": None, "bytes_per_launch": None, "capture": None}
+SPLAT_TRAFFIC = {"sha256": "1a20a745d2c83659efe7dddd18341fc58d5f9a5957b549509ec1edc75f6383bb",
+                 "bytes_per_launch": 57035264 + 7791872,
+                 "capture": "profiles/k_splat_batch64_512_u8.md"}
 
 
 def parse():
@@ -57,15 +59,18 @@ def parse():
     ap.add_argument("--tile", type=int, default=0, help="0: autotune")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--pairs", type=int, default=N_PAIRS, help="pairs per step (profiling a smaller case)")
+    ap.add_argument("--quick", action="store_true",
+                    help="timed steps only (no autotune, graph, FP16, e2e, per-pair or CPU legs): for profilers")
     return ap.parse_args()
 
 
-def workload(rank: int = 0):
+def workload(rank: int = 0, n_pairs: int = N_PAIRS):
     from paper_2512_09664_b300 import workloads as W
-    wl = W.batch_512_u8(n_pairs=N_PAIRS, seed=1)
-    if rank:  # weak scaling: every rank renders its own 64 pairs
+    wl = W.batch_512_u8(n_pairs=n_pairs, seed=1)
+    if rank:  # weak scaling: every rank renders its own pairs
         for p in wl.pairs:
-            p.pair_id += rank * N_PAIRS
+            p.pair_id += rank * n_pairs
     return wl
 
 
@@ -236,10 +241,10 @@ def run_ours(args, rank, world, dist):
     from paper_2512_09664_b300.binding import STAGES, Renderer
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    wl = workload(rank)
-    r = Renderer(wl, device=dev, tile=args.tile)
+    wl = workload(rank, args.pairs)
+    r = Renderer(wl, device=dev, tile=args.tile if args.tile else (64 if args.quick else 0))
     stream = torch.cuda.current_stream()
-    if args.tile == 0:
+    if args.tile == 0 and not args.quick:
         r.autotune(reps=2)
 
     def barrier():
@@ -278,6 +283,11 @@ def run_ours(args, rank, world, dist):
         total_ms = float(t.item())
     value = world * wl.n_pairs * args.steps / (total_ms / 1e3)
     ms_per_step = total_ms / args.steps
+    if args.quick:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": ms_per_step,
+                              "stage_ms": stage_ms, "quick": True, "pairs_per_step": wl.n_pairs}), flush=True)
+        return
 
     # the same step replayed from a captured CUDA graph (no host launch cost)
     r.capture()
