@@ -44,8 +44,8 @@ struct KernelArgs {
 };
 
 constexpr int kStageEvents = 6;
-constexpr int kSplatThreads = 256;
-constexpr int kSplatWarps = kSplatThreads / 32;
+constexpr int kSplatThreads = 256;     // k_splat below tile 64, k_finish
+constexpr int kSplatMaxThreads = 512;  // k_splat at tile 64 (more resident warps at 2 CTAs per SM)
 constexpr int kStageHeader = 320;     // descriptor (128) + plan (64) + blur taps (128)
 
 cudaError_t launch_plan(const synthpix_pair_desc *descs, int32_t n_pairs, int32_t tile, int32_t fused,

@@ -100,39 +100,48 @@ __global__ void __launch_bounds__(1024) k_plan(const synthpix_pair_desc *__restr
 // ---------------------------------------------------------------------------
 // k_seed_advect: one thread per particle
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_seed_advect(KernelArgs a) {
-    if (*a.check != 1) return;
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= a.n_part) return;
-    const int b = upper_find(a.n_pairs, g, [&](int m) { return a.plan[m].part_base; });
-    const PairPlan pl = a.plan[b];
-    const synthpix_pair_desc &D = a.descs[b];
-    const int32_t H = D.height, W = D.width;
-    const uint32_t i = (uint32_t)(g - pl.part_base);
+// One particle of k_seed_advect: attributes, frame-1 record, and what the
+// advection needs.
+struct SeedState {
+    int64_t g;
+    int b;
+    Seeded P;
+    Flow F;
+    int32_t jx, jy;
+    float gx, gy;
+};
 
-    const Seeded P = seed_particle(a, D, i, g);
-    a.sa[g] = make_float2(P.sigma, P.amp);
-    a.pos0[g] = make_float4(P.fx, P.fy, __int_as_float(P.ix), __int_as_float(P.iy));
+__device__ __forceinline__ bool seed_one(const KernelArgs &a, int64_t g, SeedState &S) {
+    S.g = g;
+    if (g >= a.n_part) return false;
+    S.b = upper_find(a.n_pairs, g, [&](int m) { return a.plan[m].part_base; });
+    const synthpix_pair_desc &D = a.descs[S.b];
+    S.P = seed_particle(a, D, (uint32_t)(g - a.plan[S.b].part_base), g);
+    a.sa[g] = make_float2(S.P.sigma, S.P.amp);
+    a.pos0[g] = make_float4(S.P.fx, S.P.fy, __int_as_float(S.P.ix), __int_as_float(S.P.iy));
     if (a.particles_out) {
-        a.particles_out[3 * g] = (float)P.ix + P.fx;
-        a.particles_out[3 * g + 1] = (float)P.iy + P.fy;
-        a.particles_out[3 * g + 2] = 4.0f * P.sigma;
-        return;
+        a.particles_out[3 * g] = (float)S.P.ix + S.P.fx;
+        a.particles_out[3 * g + 1] = (float)S.P.iy + S.P.fy;
+        a.particles_out[3 * g + 2] = 4.0f * S.P.sigma;
     }
-    // frame-2 position: displacement over dt through the bilinear flow
-    Flow F = pair_flow(a, D);
-    int32_t jx = P.ix, jy = P.iy;
-    float gx = P.fx, gy = P.fy;
-    advect_split(F, a.dt, a.n_substeps, a.integrator, jx, gx, jy, gy);
-    a.pos1[g] = make_float4(gx, gy, __int_as_float(jx), __int_as_float(jy));
-    if (!a.count) return;
-    const int32_t ix = P.ix, iy = P.iy;
-    const float fx = P.fx, fy = P.fy, sigma = P.sigma;
+    S.F = pair_flow(a, D);
+    S.jx = S.P.ix;
+    S.jy = S.P.iy;
+    S.gx = S.P.fx;
+    S.gy = S.P.fy;
+    return true;
+}
 
-    // bin counts of both frames
-    const float r15 = 6.0f * sigma;  // 1.5 d
+// Frame-2 record and bin counts of both frames.
+__device__ __forceinline__ void finish_one(const KernelArgs &a, const SeedState &S) {
+    a.pos1[S.g] = make_float4(S.gx, S.gy, __int_as_float(S.jx), __int_as_float(S.jy));
+    if (!a.count) return;
+    const PairPlan pl = a.plan[S.b];
+    const int32_t H = a.descs[S.b].height, W = a.descs[S.b].width;
+    const float r15 = 6.0f * S.P.sigma;  // 1.5 d
     for (int f = 0; f < 2; ++f) {
-        const Window w = f ? particle_window(jx, gx, jy, gy, r15, W, H) : particle_window(ix, fx, iy, fy, r15, W, H);
+        const Window w = f ? particle_window(S.jx, S.gx, S.jy, S.gy, r15, W, H)
+                           : particle_window(S.P.ix, S.P.fx, S.P.iy, S.P.fy, r15, W, H);
         if (w.j0 > w.j1 || w.i0 > w.i1) continue;
         int32_t tx0, tx1, ty0, ty1;
         window_tiles(w, pl.halo, a.tile, W, H, tx0, tx1, ty0, ty1);
@@ -140,6 +149,17 @@ __global__ void __launch_bounds__(256) k_seed_advect(KernelArgs a) {
         for (int32_t ty = ty0; ty <= ty1; ++ty)
             for (int32_t tx = tx0; tx <= tx1; ++tx) atomicAdd(cnt + ty * pl.tiles_x + tx, 1u);
     }
+}
+
+// One thread per particle.  (Two particles per thread in lockstep needs 80
+// registers and lost more occupancy than it gained in overlap.)
+__global__ void __launch_bounds__(256) k_seed_advect(KernelArgs a) {
+    if (*a.check != 1) return;
+    SeedState A;
+    if (!seed_one(a, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, A) || a.particles_out) return;
+    // frame-2 position: displacement over dt through the bilinear flow
+    advect_split(A.F, a.dt, a.n_substeps, a.integrator, A.jx, A.gx, A.jy, A.gy);
+    finish_one(a, A);
 }
 
 // ---------------------------------------------------------------------------
@@ -236,7 +256,7 @@ cudaError_t launch_prep(const KernelArgs &a, cudaStream_t st, cudaEvent_t const 
         if (ev && ev[k]) cudaEventRecord(ev[k], st);
     };
     const unsigned nb = (unsigned)((a.n_part + 255) / 256);
-    if (a.n_part > 0) k_seed_advect<<<nb, 256, 0, st>>>(a);
+    if (a.n_part > 0) k_seed_advect<<<(unsigned)((a.n_part + 255) / 256), 256, 0, st>>>(a);
     mark(2);
     k_scan<<<2 * a.n_pairs, 1024, 0, st>>>(a);
     mark(3);

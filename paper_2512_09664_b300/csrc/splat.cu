@@ -16,6 +16,7 @@
 #include "common.cuh"
 #include "kernels.cuh"
 #include "particle.cuh"
+#include "phi_table.cuh"
 
 namespace spx {
 
@@ -101,14 +102,31 @@ struct Geo {
     int32_t FW, FH;              // full halo rectangle (replicated outside the frame)
 };
 
+// Upper normal tail Q(t) = erfc(t / sqrt 2) / 2 for t >= 0 from the
+// piecewise polynomial table (staged in shared memory as [coef][piece]).
+__device__ __forceinline__ float phi_tail(float t, const float *tab) {
+    const int k = min((int)(t * kPhiWidthInv), kPhiPieces - 1);
+    const float s = t - fmaf((float)k, 1.0f / kPhiWidthInv, 0.5f / kPhiWidthInv);
+    float acc = tab[kPhiDegree * kPhiPieces + k];
+#pragma unroll
+    for (int j = kPhiDegree - 1; j >= 0; --j) acc = fmaf(acc, s, tab[j * kPhiPieces + k]);
+    return t < 8.0f ? acc : 0.0f;
+}
+
+// edge_value() evaluated from the table: Phi(t) for t <= 0, -(1 - Phi(t)) for t > 0.
+__device__ __forceinline__ float edge_value_tab(float t, const float *tab) {
+    const float q = phi_tail(fabsf(t), tab);
+    return t > 0.0f ? -q : q;
+}
+
 // Large windows (more than 30 edges): per-warp scratch in shared memory.
 __device__ __noinline__ void splat_particle_wide(const Geo &g, int32_t *hi, int32_t *lo, float px, float py,
                                                  int32_t ix, int32_t iy, float inv, float amps, int32_t j0,
-                                                 int32_t i0, int nx, int ny, float *scr, int wq) {
+                                                 int32_t i0, int nx, int ny, float *scr, int wq, const float *tab) {
     const int lane = threadIdx.x & 31;
     float *exe = scr, *eye = scr + wq, *ex = scr + 2 * wq, *ey = scr + 3 * wq;
-    for (int e = lane; e <= nx; e += 32) exe[e] = edge_value(((float)(j0 + e - ix) - px) * inv);
-    for (int e = lane; e <= ny; e += 32) eye[e] = edge_value(((float)(i0 + e - iy) - py) * inv);
+    for (int e = lane; e <= nx; e += 32) exe[e] = edge_value_tab(((float)(j0 + e - ix) - px) * inv, tab);
+    for (int e = lane; e <= ny; e += 32) eye[e] = edge_value_tab(((float)(i0 + e - iy) - py) * inv, tab);
     __syncwarp();
     for (int e = lane; e < nx; e += 32)
         ex[e] = pixel_mass(exe[e], exe[e + 1], (float)(j0 + e - ix) > px, (float)(j0 + e + 1 - ix) > px);
@@ -137,11 +155,12 @@ __device__ __forceinline__ int small_div(int a, float inv_b) { return (int)(((fl
 // lanes [0, nx] evaluate the x edges, lanes [nx+1, nx+ny+1] the y edges;
 // each lane then takes one column and every rpr-th row of the window.
 __device__ __forceinline__ void splat_records(const unsigned char *recs, uint32_t n, const Geo &g, float scale,
-                                              int32_t *hi, int32_t *lo, float *scr, int wq) {
+                                              int32_t *hi, int32_t *lo, float *scr, int wq, const float *tab) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned FULL = 0xffffffffu;
-    for (uint32_t k0 = warp; k0 < n; k0 += kSplatWarps * 32) {
-        const uint32_t k = k0 + kSplatWarps * lane;
+    const uint32_t nw = blockDim.x >> 5;
+    for (uint32_t k0 = warp; k0 < n; k0 += nw * 32) {
+        const uint32_t k = k0 + nw * lane;
         float px = 0.f, py = 0.f, inv = 0.f, amps = 0.f, invn = 0.f;
         int32_t ix = 0, iy = 0, j0 = 0, i0 = 0, nx = 0, ny = 0;
         if (k < n) {
@@ -176,7 +195,7 @@ __device__ __forceinline__ void splat_records(const unsigned char *recs, uint32_
             const int32_t bj0 = __shfl_sync(FULL, j0, src), bi0 = __shfl_sync(FULL, i0, src);
             const float binv = __shfl_sync(FULL, inv, src), bamps = __shfl_sync(FULL, amps, src);
             if (bnx + bny + 2 > 32) {
-                splat_particle_wide(g, hi, lo, bpx, bpy, bix, biy, binv, bamps, bj0, bi0, bnx, bny, scr, wq);
+                splat_particle_wide(g, hi, lo, bpx, bpy, bix, biy, binv, bamps, bj0, bi0, bnx, bny, scr, wq, tab);
                 continue;
             }
             const float binvn = __shfl_sync(FULL, invn, src);
@@ -185,7 +204,7 @@ __device__ __forceinline__ void splat_records(const unsigned char *recs, uint32_
             const int e = isx ? lane : lane - nxe;
             const float dd = isx ? (float)(bj0 + e - bix) - bpx : (float)(bi0 + e - biy) - bpy;
             const bool dpos = dd > 0.0f;
-            const float ev = lane < nxe + bny + 1 ? edge_value(dd * binv) : 0.0f;
+            const float ev = lane < nxe + bny + 1 ? edge_value_tab(dd * binv, tab) : 0.0f;
             const float evn = __shfl_down_sync(FULL, ev, 1);
             const bool dposn = __shfl_down_sync(FULL, (int)dpos, 1) != 0;
             float m = pixel_mass(ev, evn, dpos, dposn);
@@ -372,7 +391,7 @@ __device__ __forceinline__ void store_unblurred(const Geo &g, const float *A, T 
 // ---------------------------------------------------------------------------
 struct Smem {
     int32_t *hi, *lo;
-    float *A, *Bh, *sx2, *sy2, *scr;
+    float *A, *Bh, *sx2, *sy2, *scr, *phi;
     int BP;
 };
 
@@ -516,23 +535,29 @@ __device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo
     while (done < it.count) {
         const uint32_t n = min(it.count - done, cap);
         splat_records(buf + kStageHeader + record_lead(it.rec0 + done), n, g, scale, s.hi, s.lo,
-                      s.scr + (threadIdx.x >> 5) * a.warp_scratch, a.warp_scratch >> 2);
+                      s.scr + (threadIdx.x >> 5) * a.warp_scratch, a.warp_scratch >> 2, s.phi);
         done += n;
         __syncthreads();
-        carry_fixed(s.hi, s.lo, g.EH * g.EW);
-        if (done < it.count) {
+        if (done < it.count) {  // more records: carry lo before the next chunk (the last carry is in pass 1)
+            carry_fixed(s.hi, s.lo, g.EH * g.EW);
             stage_records(a, it.rec0 + done, min(it.count - done, cap), buf + kStageHeader);
             cp_async_commit();
             cp_async_wait_all();
+            __syncthreads();
         }
-        __syncthreads();
     }
     if (it.count == 0) __syncthreads();  // illumination factors
 
     const float unit = imax * (1.0f / 1024.0f);
     int32_t *hi = s.hi, *lo = s.lo;
+    // S from the fixed-point sums, carrying lo into hi on the fly; each pixel
+    // is read once, and its accumulator cleared for the next item
     auto fixed_src = [hi, lo, unit](int idx, int, int) {
-        return fmaf((float)lo[idx], 1.0f / 4194304.0f, (float)hi[idx]) * unit;
+        const int32_t l = lo[idx], c = l >> 22;
+        const float v = fmaf((float)(l - (c << 22)), 1.0f / 4194304.0f, (float)(hi[idx] + c)) * unit;
+        hi[idx] = 0;
+        lo[idx] = 0;
+        return v;
     };
     if (!fused) {
         // halo 0: the clipped rectangle is the tile
@@ -545,25 +570,17 @@ __device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo
             const int64_t o = base + (int64_t)(g.ey0 + r) * g.W + (g.ex0 + c);
             if (a.inter_dtype == SYNTHPIX_F16) reinterpret_cast<__half *>(a.inter)[o] = to_inter<__half>(S);
             else reinterpret_cast<__nv_bfloat16 *>(a.inter)[o] = to_inter<__nv_bfloat16>(S);
-            hi[idx] = 0;
-            lo[idx] = 0;
         }
         return;  // the caller's loop ends with a barrier
     }
     finish_tile<T>(a, g, D, wtab, it.frame, illum, s, fixed_src);
-    // clear the accumulator region for the next item (pass 1 is done reading it:
-    // finish_tile passed two barriers since)
-    for (int k = threadIdx.x; k < g.EH * g.EW; k += blockDim.x) {
-        s.hi[k] = 0;
-        s.lo[k] = 0;
-    }
 }
 
 // ---------------------------------------------------------------------------
 // the persistent kernel
 // ---------------------------------------------------------------------------
 struct SmemLayout {
-    size_t hi, lo, A, Bh, sx2, sy2, scr, bufs, total;
+    size_t hi, lo, A, Bh, sx2, sy2, scr, phi, bufs, total;
 };
 
 __host__ __device__ inline SmemLayout smem_layout(int E, int tile, int warp_scratch, int rec_buf_bytes) {
@@ -581,14 +598,15 @@ __host__ __device__ inline SmemLayout smem_layout(int E, int tile, int warp_scra
     L.Bh = take((size_t)E * BP * 4);
     L.sx2 = take((size_t)E * 4);
     L.sy2 = take((size_t)E * 4);
-    L.scr = take((size_t)kSplatWarps * warp_scratch * 4);
+    L.scr = take((size_t)(kSplatMaxThreads / 32) * warp_scratch * 4);
+    L.phi = take((size_t)(kPhiDegree + 1) * kPhiPieces * 4);
     L.bufs = take(2 * (size_t)rec_buf_bytes);
     L.total = o;
     return L;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kSplatThreads) k_splat(KernelArgs a) {
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_splat(KernelArgs a) {
     if (*a.check != 1) return;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ ItemInfo s_item[2];
@@ -601,6 +619,8 @@ __global__ void __launch_bounds__(kSplatThreads) k_splat(KernelArgs a) {
     s.sx2 = reinterpret_cast<float *>(smem + L.sx2);
     s.sy2 = reinterpret_cast<float *>(smem + L.sy2);
     s.scr = reinterpret_cast<float *>(smem + L.scr);
+    s.phi = reinterpret_cast<float *>(smem + L.phi);
+    for (int k = threadIdx.x; k < (kPhiDegree + 1) * kPhiPieces; k += blockDim.x) s.phi[k] = kPhiTable[k];
     s.BP = (a.tile + 3) & ~3;
     unsigned char *bufs = smem + L.bufs;
     const uint32_t cap = (uint32_t)((a.rec_buf_bytes - kStageHeader - 32) / (int)sizeof(Record));
@@ -690,6 +710,7 @@ __global__ void __launch_bounds__(kSplatThreads) k_finish(KernelArgs a) {
     s.sx2 = reinterpret_cast<float *>(smem + FL.sx2);
     s.sy2 = reinterpret_cast<float *>(smem + FL.sy2);
     s.scr = nullptr;
+    s.phi = nullptr;
     s.BP = (a.tile + 3) & ~3;
     const ItemInfo it = a.items[blockIdx.x];
     const synthpix_pair_desc &D = a.descs[it.pair];
@@ -719,13 +740,21 @@ cudaError_t launch_splat(const KernelArgs &a, int32_t out_dtype, cudaStream_t st
     if (e != cudaSuccess) return e;
 #define SPX_LAUNCH(T)                                                                                        \
     do {                                                                                                     \
-        e = cudaFuncSetAttribute(k_splat<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);        \
-        if (e != cudaSuccess) return e;                                                                      \
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_splat<T>, kSplatThreads, smem);            \
-        if (e != cudaSuccess) return e;                                                                      \
-        const int64_t want = (int64_t)nsm * (occ > 0 ? occ : 1);                                             \
-        const unsigned grid = (unsigned)(a.n_tiles < want ? a.n_tiles : want);                              \
-        k_splat<T><<<grid, kSplatThreads, smem, st>>>(a);                                                    \
+        if (a.tile >= 64) {                                                                                  \
+            e = cudaFuncSetAttribute(k_splat<T, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);\
+            if (e != cudaSuccess) return e;                                                                  \
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_splat<T, 512>, 512, smem);             \
+            if (e != cudaSuccess) return e;                                                                  \
+            const int64_t want = (int64_t)nsm * (occ > 0 ? occ : 1);                                         \
+            k_splat<T, 512><<<(unsigned)(a.n_tiles < want ? a.n_tiles : want), 512, smem, st>>>(a);          \
+        } else {                                                                                             \
+            e = cudaFuncSetAttribute(k_splat<T, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);\
+            if (e != cudaSuccess) return e;                                                                  \
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_splat<T, 256>, 256, smem);             \
+            if (e != cudaSuccess) return e;                                                                  \
+            const int64_t want = (int64_t)nsm * (occ > 0 ? occ : 1);                                         \
+            k_splat<T, 256><<<(unsigned)(a.n_tiles < want ? a.n_tiles : want), 256, smem, st>>>(a);          \
+        }                                                                                                    \
     } while (0)
     switch (out_dtype) {
     case SYNTHPIX_F32: SPX_LAUNCH(float); break;
