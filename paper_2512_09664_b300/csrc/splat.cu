@@ -346,7 +346,7 @@ __device__ __forceinline__ void blur_store(const Geo &g, const float *A, float *
             v[2] = fmaf(wr[k], a.z + b.z, v[2]);
             v[3] = fmaf(wr[k], a.w + b.w, v[3]);
         }
-        store_group<T>(out + (int64_t)(g.y0 + r) * g.W + g.x0 + c0, v, min(4, TW - c0), M);
+        store_group<T>(out + r * g.W + c0, v, min(4, TW - c0), M);
     }
 }
 
@@ -369,7 +369,7 @@ __device__ __noinline__ void blur_store_any(const Geo &g, const float *A, float 
         float acc = w[0] * col[0];
         for (int k = 1; k <= R; ++k) acc = fmaf(w[k], col[-k * BP] + col[k * BP], acc);
         float v[4] = {acc, 0.f, 0.f, 0.f};
-        store_group<T>(out + (int64_t)(g.y0 + r) * g.W + g.x0 + c, v, 1, M);
+        store_group<T>(out + r * g.W + c, v, 1, M);
     }
 }
 
@@ -382,7 +382,7 @@ __device__ __forceinline__ void store_unblurred(const Geo &g, const float *A, T 
         float v[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) v[j] = A[r * g.FW + min(c0 + j, g.FW - 1)];
-        store_group<T>(out + (int64_t)(g.y0 + r) * g.W + g.x0 + c0, v, min(4, TW - c0), M);
+        store_group<T>(out + r * g.W + c0, v, min(4, TW - c0), M);
     }
 }
 
@@ -445,28 +445,30 @@ __device__ __forceinline__ void finish_tile(const KernelArgs &a, const Geo &g, c
     const float dl = D.illum_max - D.illum_min;
     const int fx0 = g.x0 - g.R, fy0 = g.y0 - g.R;
     if (D.noise_sigma != 0.0f) {
-        const int64_t HW = (int64_t)g.H * g.W;
+        // 32-bit pixel indices: frames hold at most 32768^2 = 2^30 pixels
         const int nq = (g.EW + 6) / 4 + 1;
         const float inq = 1.0f / (float)nq;
         const uint32_t tag = kTagNoise + (uint32_t)frame;
+        const int fpitch = g.FW;
+        float *Abase = s.A + (g.ey0 - fy0) * fpitch + (g.ex0 - fx0);
         for (int item = threadIdx.x; item < g.EH * nq; item += blockDim.x) {
             const int r = small_div(item, inq), qi = item - r * nq;
-            const int64_t rowlin = (int64_t)(g.ey0 + r) * g.W;
-            const int64_t q = ((rowlin + g.ex0) >> 2) + qi;
-            if (4 * q > rowlin + g.ex1 - 1) continue;
-            const uint4 w = stream_words(a.seed, D.pair_id, (uint32_t)q, tag);
+            const int rowlin = (g.ey0 + r) * g.W;
+            const int p0 = (((rowlin + g.ex0) >> 2) + qi) << 2;
+            if (p0 > rowlin + g.ex1 - 1) continue;
+            const uint4 w = stream_words(a.seed, D.pair_id, (uint32_t)(p0 >> 2), tag);
             float nv[4];
             box_muller(w.x, w.y, nv[0], nv[1]);
             box_muller(w.z, w.w, nv[2], nv[3]);
+            const int c0 = p0 - rowlin - g.ex0;  // column of the quad's first pixel in the halo rectangle
+            const float ly = illum ? s.sy2[r] : 0.0f;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const int64_t pix = 4 * q + k;
-                const int64_t col = pix - rowlin;
-                if (pix < HW && col >= g.ex0 && col < g.ex1) {
-                    const int c = (int)(col - g.ex0);
+                const int c = c0 + k;
+                if (c >= 0 && c < g.EW) {
                     const float S = src(r * g.EW + c, r, c);
-                    const float L = illum ? fmaf(dl, s.sx2[c] * s.sy2[r], D.illum_min) : 1.0f;
-                    s.A[(g.ey0 + r - fy0) * g.FW + (g.ex0 + c - fx0)] = fmaf(L, S, D.noise_sigma * nv[k]);
+                    const float L = illum ? fmaf(dl, s.sx2[c] * ly, D.illum_min) : 1.0f;
+                    Abase[r * fpitch + c] = fmaf(L, S, D.noise_sigma * nv[k]);
                 }
             }
         }
@@ -494,7 +496,8 @@ __device__ __forceinline__ void finish_tile(const KernelArgs &a, const Geo &g, c
     }
     __syncthreads();
     const int64_t HW = (int64_t)g.H * g.W;
-    T *out = reinterpret_cast<T *>(a.images) + D.image_offset + (int64_t)frame * HW;
+    // the tile's first output pixel; stores add 32-bit row / column offsets
+    T *out = reinterpret_cast<T *>(a.images) + D.image_offset + (int64_t)frame * HW + (int64_t)g.y0 * g.W + g.x0;
     const float M = a.quant_bits > 0 ? (float)((1u << a.quant_bits) - 1u) : 0.0f;
     switch (g.R) {
     case 0: store_unblurred<T>(g, s.A, out, M); break;
