@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--pairs", type=int, default=N_PAIRS, help="pairs per step (profiling a smaller case)")
+    ap.add_argument("--workload", default="batch64_512_u8",
+                    choices=("batch64_512_u8", "uneven256", "diff32_256", "large_mixed"),
+                    help="the headline workload (default) or one of the other workloads, measured on their own")
     ap.add_argument("--quick", action="store_true",
                     help="timed steps only (no autotune, graph, FP16, e2e, per-pair or CPU legs): for profilers")
     return ap.parse_args()
@@ -405,8 +408,94 @@ def run_ours(args, rank, world, dist):
         print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------
+# the other workloads (not the headline): measured with their own comparisons
+# ----------------------------------------------------------------------------
+
+def _time_device(fn, steps, flush, stream):
+    import torch
+    tot = 0.0
+    for k in range(steps):
+        flush.fill_(k & 0xFF)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+    return tot / steps
+
+
+def run_other(args):
+    import numpy as np
+    import torch
+
+    from paper_2512_09664_b300 import workloads as W
+    from paper_2512_09664_b300.binding import Renderer
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    line = {"workload": args.workload, "steps": args.steps, "warmup": args.warmup, "unit": UNIT}
+    if args.workload == "uneven256":
+        wl = W.uneven_batch(n_pairs=256, seed=2)
+        r = Renderer(wl)
+        tile, _ = r.autotune(reps=2)
+        r.capture()
+        for _ in range(args.warmup):
+            r.replay()
+        g_ms = _time_device(r.replay, args.steps, flush, stream)
+        per = [Renderer(wl.subset([b]), tile=tile) for b in range(wl.n_pairs)]
+        for p in per:
+            p.render()
+
+        def per_pair():
+            for p in per:
+                p.render()
+        p_ms = _time_device(per_pair, max(2, args.steps // 10), flush, stream)
+        line.update({"config": wl.description, "tile": tile, "graph_persistent_ms": g_ms,
+                     "value": wl.n_pairs / (g_ms / 1e3), "per_pair_launches_ms": p_ms,
+                     "per_pair_value": wl.n_pairs / (p_ms / 1e3), "speedup": p_ms / g_ms,
+                     "mpx_per_s": wl.image_elems() / (g_ms / 1e3) / 1e6,
+                     "particles": sum(p.n_particles for p in wl.pairs)})
+    elif args.workload == "diff32_256":
+        wl = W.differentiable_batch(n_pairs=32)
+        ctrl = torch.tensor(np.stack(wl.meta["control"]), dtype=torch.float32)
+        up = torch.nn.functional.interpolate(ctrl.permute(0, 3, 1, 2), size=(256, 256), mode="bilinear",
+                                             align_corners=False).permute(0, 2, 3, 1).contiguous()
+        wl.flows = [f.numpy() for f in up]
+        r = Renderer(wl)
+        G = torch.randn(r.images.shape, device="cuda")
+        gf = torch.zeros_like(r.flows)
+        gp = torch.empty((sum(p.n_particles for p in wl.pairs), 3), device="cuda")
+        for _ in range(args.warmup):
+            r.render_from()
+            r.backward(G, grad_flows=gf, grad_particles=gp)
+        f_ms = _time_device(r.render_from, args.steps, flush, stream)
+        b_ms = _time_device(lambda: r.backward(G, grad_flows=gf, grad_particles=gp), args.steps, flush, stream)
+        line.update({"config": wl.description, "forward_ms": f_ms, "backward_ms": b_ms,
+                     "value": wl.n_pairs / ((f_ms + b_ms) / 1e3), "forward_value": wl.n_pairs / (f_ms / 1e3)})
+    else:  # large_mixed
+        wl = W.large_mixed_batch()
+        res = {}
+        for inter in ("f32", "f16", "bf16"):
+            r = Renderer(wl, inter_dtype=inter)
+            tile, _ = r.autotune(reps=1)
+            for _ in range(args.warmup):
+                r.render()
+            ms = _time_device(r.render, args.steps, flush, stream)
+            res[inter] = {"ms_per_step": ms, "value": wl.n_pairs / (ms / 1e3), "tile": tile}
+            del r
+            torch.cuda.empty_cache()
+        line.update({"config": wl.description, "paths": res, "value": res["f16"]["value"],
+                     "f16_speedup_over_f32": res["f32"]["ms_per_step"] / res["f16"]["ms_per_step"]})
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload != "batch64_512_u8":
+        run_other(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     dist = None

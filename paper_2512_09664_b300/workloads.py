@@ -173,14 +173,14 @@ def fourier_flow(gh: int, gw: int, height: int, width: int, rms: float,
     amp = kmag ** (-4.0 / 3.0)
     kx, ky = kmag * np.cos(theta), kmag * np.sin(theta)
     xs, ys = node_centres(gh, gw, height, width)
-    u = np.zeros((gh, gw))
-    v = np.zeros((gh, gw))
-    for m in range(n_modes):
-        ax = kx[m] * xs + phi[m]
-        ay = ky[m] * ys
-        term = np.outer(np.cos(ay), np.cos(ax)) - np.outer(np.sin(ay), np.sin(ax))
-        u += (amp[m] * ky[m]) * term
-        v -= (amp[m] * kx[m]) * term
+    # cos(kx x + phi + ky y) = cos(ky y) cos(kx x + phi) - sin(ky y) sin(kx x + phi),
+    # summed over the modes as two matrix products
+    ax = np.outer(xs, kx) + phi[None, :]          # [gw, M]
+    ay = np.outer(ys, ky)                         # [gh, M]
+    cx, sx, cy, sy = np.cos(ax), np.sin(ax), np.cos(ay), np.sin(ay)
+    wu, wv = amp * ky, -amp * kx
+    u = (cy * wu) @ cx.T - (sy * wu) @ sx.T
+    v = (cy * wv) @ cx.T - (sy * wv) @ sx.T
     scale = rms / math.sqrt(np.mean(u * u + v * v))
     f = np.empty((gh, gw, 2), dtype=np.float64)
     f[..., 0] = u * scale

@@ -1,0 +1,95 @@
+"""The workloads at their full sizes, in the launch configuration bench.py
+uses (autotuned tile, persistent splat), against the FP64 oracle: every pair
+of the 64-pair 512^2 batch, every pair of the 256-pair uneven batch, the
+32-pair differentiable batch (forward and gradients), and a reduced large
+mixed-precision batch (2048^2 and 1920x1080 frames) with its 16-bit error
+reported."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2512_09664_b300 import workloads as W
+
+from parity import compare, gpu_render, oracle_render
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("CUDA device required")
+
+
+def _autotuned(wl, **kw):
+    from paper_2512_09664_b300.binding import Renderer
+    r = Renderer(wl, **kw)
+    r.autotune(reps=1)
+    return r
+
+
+def test_batch64_512_u8_every_pair():
+    wl = W.batch_512_u8(n_pairs=64, seed=1)
+    r = _autotuned(wl)
+    st = compare(wl, gpu_render(wl, renderer=r), oracle_render(wl))
+    print("batch64_512_u8", st, "tile", r.pk.batch.tile)
+    assert st["mismatch"] <= st["band"]
+
+
+def test_uneven256_12bit_every_pair():
+    wl = W.uneven_batch(n_pairs=256, seed=2)
+    r = _autotuned(wl)
+    st = compare(wl, gpu_render(wl, renderer=r), oracle_render(wl))
+    print("uneven256", st, "tile", r.pk.batch.tile)
+
+
+def test_differentiable32_forward_and_gradients():
+    import torch
+
+    from paper_2512_09664_b300.binding import Renderer
+    wl = W.differentiable_batch(n_pairs=32)
+    ctrl = torch.tensor(np.stack(wl.meta["control"]), dtype=torch.float64)
+    up = torch.nn.functional.interpolate(ctrl.permute(0, 3, 1, 2), size=(256, 256), mode="bilinear",
+                                         align_corners=False).permute(0, 2, 3, 1).float()
+    wl.flows = [f.numpy() for f in up]
+    r = Renderer(wl)
+    compare(wl, gpu_render(wl, renderer=r), oracle_render(wl))
+    G = torch.randn(r.images.shape, device="cuda", generator=torch.Generator("cuda").manual_seed(5))
+    gf = torch.zeros_like(r.flows)
+    n = sum(p.n_particles for p in wl.pairs)
+    gp = torch.empty((n, 3), device="cuda")
+    r.backward(G, grad_flows=gf, grad_particles=gp)
+    torch.cuda.synchronize()
+    Gh, gfh, gph = G.cpu().numpy(), gf.cpu().numpy(), gp.cpu().numpy()
+    off_p, off_f = 0, 0
+    for b, spec in enumerate(wl.pairs):
+        io = r.pk.image_offsets[b]
+        Gb = Gh[io:io + 2 * 256 * 256].reshape(2, 256, 256).astype(np.float64)
+        rf, rp = oracle.backward(oracle.pair_from_workload(wl, b), wl.flows[b], Gb)
+        sp = gph[off_p:off_p + spec.n_particles]
+        assert np.all(np.abs(sp - rp) <= 1e-4 * np.abs(rp).max(0) + 1e-6)
+        sf = gfh[off_f:off_f + wl.flows[b].size].reshape(wl.flows[b].shape)
+        assert np.abs(sf - rf).max() <= 1e-4 * np.abs(rf).max()
+        off_p += spec.n_particles
+        off_f += wl.flows[b].size
+
+
+@pytest.mark.parametrize("inter", ["f16", "bf16", "f32"])
+def test_large_mixed_reduced_16bit_error(inter):
+    # 2 of the 2048^2 dense pairs and 2 of the 1920x1080 sparse-large pairs
+    wl = W.large_mixed_batch(n_big=2, n_hd=2, inter_dtype=inter)
+    r = _autotuned(wl)
+    g = gpu_render(wl, renderer=r)
+    ref = oracle_render(wl)
+    M = 65535.0
+    unit = {"f16": 2.0 ** -11, "bf16": 2.0 ** -8, "f32": 0.0}[inter]
+    for b, (gi, rr) in enumerate(zip(g, ref)):
+        d = np.abs(gi.astype(np.int64) - rr["Q"].astype(np.int64))
+        lim = int(np.ceil((1e-4 + unit * rr["S"].max()) * M)) + 1
+        print(f"large_mixed {inter} pair {b}: max {d.max()} LSB, rms {np.sqrt((d ** 2).mean()):.3f} LSB "
+              f"(bound {lim})")
+        assert d.max() <= lim
+    if inter == "f32":  # the fused FP32 path: exact codes away from rounding boundaries
+        st = compare(wl, g, ref)
+        print("large_mixed f32", st)
