@@ -115,7 +115,7 @@ int make_plan_tile(const synthpix_batch_desc *batch, const synthpix_pair_desc *p
     P.max_r = 0;
     P.max_d = 0.0f;
     spx::Layout &L = P.L;
-    L.n_part = L.n_tiles = L.n_list = L.n_inter = 0;
+    L.n_part = L.n_tiles = L.n_list = L.n_inter = L.n_chunks = 0;
     for (int32_t b = 0; b < n_pairs; ++b) {
         rc = check_pair(pairs[b], b);
         if (rc) return rc;
@@ -123,12 +123,14 @@ int make_plan_tile(const synthpix_batch_desc *batch, const synthpix_pair_desc *p
         L.n_part += pairs[b].n_particles;
         L.n_tiles += 2LL * g.ntiles;
         L.n_list += 2LL * g.list_cap;
+        L.n_chunks += g.chunks;
         if (!P.fused) L.n_inter += 2LL * pairs[b].height * pairs[b].width;
         if (g.halo > P.max_halo) P.max_halo = g.halo;
         if (g.blur_r > P.max_r) P.max_r = g.blur_r;
         if (pairs[b].d_max > P.max_d) P.max_d = pairs[b].d_max;
     }
     if (L.n_tiles > 0x7FFFFFFFLL) return fail(SYNTHPIX_EINVAL, "batch has more than 2^31-1 tiles");
+    if (L.n_chunks > 0x7FFFFFFFLL) return fail(SYNTHPIX_EINVAL, "batch has more than 2^40 particles");
     if (L.n_list > (int64_t(1) << 40)) return fail(SYNTHPIX_EINVAL, "batch bin lists too large");
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -272,6 +274,7 @@ static int run(Mode mode, const synthpix_batch_desc *batch, const synthpix_pair_
     a.tile = P.tile;
     a.n_part = L.n_part;
     a.n_tiles = L.n_tiles;
+    a.n_chunks = L.n_chunks;
     a.seed = batch->seed;
     a.dt = batch->dt;
     a.n_substeps = batch->n_substeps;
@@ -288,7 +291,7 @@ static int run(Mode mode, const synthpix_batch_desc *batch, const synthpix_pair_
     a.items = reinterpret_cast<spx::ItemInfo *>(ws + L.items);
     a.rec = reinterpret_cast<spx::Record *>(ws + L.rec);
     a.ticket = ticket;
-    a.rec_buf_bytes = 8192;
+    a.rec_buf_bytes = spx::kRecBufBytes;
     a.blur_w = blur_w;
     a.inter_dtype = batch->inter_dtype;
     a.inter = ws + L.inter;

@@ -12,6 +12,7 @@
 namespace spx {
 
 constexpr int kMaxBlurRadius = 24;  // ceil(3 * 8)
+constexpr int kChunk = 512;         // particles of one pair per CTA of the seeding and binning kernels
 constexpr int kBlurStride = 32;     // floats per pair in the blur-tap table
 
 // Derived per-pair geometry (device table built by k_plan, mirrored on the host).
@@ -24,7 +25,8 @@ struct PairPlan {
     int32_t tiles_x, tiles_y, ntiles;
     int32_t blur_r;      // ceil(3 * blur_sigma), 0 without blur
     int32_t halo;        // pixels a tile's bins extend beyond the tile (blur_r or 0)
-    int32_t pad[2];
+    int32_t chunk_base;  // first particle chunk (kChunk particles) of the pair
+    int32_t pad;
 };
 static_assert(sizeof(PairPlan) == 64, "PairPlan layout");
 
@@ -32,6 +34,7 @@ static_assert(sizeof(PairPlan) == 64, "PairPlan layout");
 struct PairGeom {
     int32_t tiles_x, tiles_y, ntiles, blur_r, halo, span;
     int64_t list_cap;
+    int64_t chunks;  // ceil(n_particles / kChunk)
 };
 
 __host__ __device__ inline int32_t blur_radius_of(float blur_sigma) {
@@ -56,6 +59,7 @@ __host__ __device__ inline PairGeom pair_geom(const synthpix_pair_desc &d, int t
     int32_t sx = g.span < g.tiles_x ? g.span : g.tiles_x;
     int32_t sy = g.span < g.tiles_y ? g.span : g.tiles_y;
     g.list_cap = (int64_t)d.n_particles * (int64_t)sx * (int64_t)sy;
+    g.chunks = ((int64_t)d.n_particles + kChunk - 1) / kChunk;
     return g;
 }
 
@@ -78,7 +82,7 @@ static_assert(sizeof(ItemInfo) == 24, "ItemInfo layout");
 // Workspace layout (byte offsets, 256-aligned), computed on the host.
 struct Layout {
     size_t plan, desc, check, blur, count, off, cursor, items, pos, sa, rec, inter, gfr, total;
-    int64_t n_part, n_tiles, n_list, n_inter;
+    int64_t n_part, n_tiles, n_list, n_inter, n_chunks;
 };
 
 __host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }

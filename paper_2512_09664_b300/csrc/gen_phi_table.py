@@ -1,11 +1,12 @@
 """Generate phi_table.cuh: the upper tail Q(t) = erfc(t / sqrt 2) / 2 of the
-standard normal on [0, 8) as 16 polynomial pieces of degree 8.
+standard normal on [0, 8] as 129 cubic pieces.
 
 Method: Chebyshev interpolation (Trefethen, "Approximation Theory and
-Approximation Practice", ch. 4) of Q on each interval [k/2, (k+1)/2] at 32
-Chebyshev points, truncated to degree 8 and converted to powers of
-s = t - (k/2 + 1/4); coefficients rounded to FP32.  Q is evaluated with
-scipy.special.erfc in FP64.  Beyond t = 8, Q < 6.3e-16 and is taken as 0.
+Approximation Practice", ch. 4) of Q on each interval [k/16 - 1/32, k/16 +
+1/32], k = 0..128, at 25 Chebyshev points, truncated to degree 3 and converted
+to powers of s = t - k/16; coefficients rounded to FP32.  Q is evaluated with
+scipy.special.erfc in FP64.  The kernels clamp t to 8 (Q(8) = 6.2e-16) and
+select the piece k = rint(16 t), so each piece is used on its own interval.
 
     python -m paper_2512_09664_b300.csrc.gen_phi_table   # rewrites phi_table.cuh
 
@@ -14,7 +15,7 @@ The script checks the FP32 Horner evaluation of the rounded coefficients
 on a dense grid and refuses to write a table whose absolute error exceeds
 4e-8 (0.7 FP32 ulp at Q = 1/2; the pixel masses are differences of Q values,
 so absolute accuracy is what matters).  The truncation error alone is below
-2e-12; the rest is FP32 rounding.
+1e-9; the rest is FP32 rounding.
 """
 from __future__ import annotations
 
@@ -24,9 +25,10 @@ import numpy as np
 from numpy.polynomial import chebyshev as Ch
 from scipy.special import erfc
 
-N_PIECES = 16
-WIDTH = 0.5
-DEGREE = 8
+PIECES_PER_UNIT = 16
+T_MAX = 8.0
+N_PIECES = int(T_MAX * PIECES_PER_UNIT) + 1
+DEGREE = 3
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 
@@ -35,14 +37,13 @@ def q_tail(t):
 
 
 def piece_coefficients(k: int) -> np.ndarray:
-    c = k * WIDTH + WIDTH / 2
-    half = WIDTH / 2
+    c = k / PIECES_PER_UNIT
+    half = 0.5 / PIECES_PER_UNIT
     # Chebyshev interpolant in x in [-1, 1], t = c + half x
-    cheb = Ch.chebinterpolate(lambda x: q_tail(c + half * x), 32)
+    cheb = Ch.chebinterpolate(lambda x: q_tail(c + half * x), 24)
     cheb = cheb[:DEGREE + 1]
     mono_x = Ch.cheb2poly(cheb)                      # powers of x
-    mono_s = mono_x / half ** np.arange(DEGREE + 1)  # powers of s = half x
-    return mono_s
+    return mono_x / half ** np.arange(DEGREE + 1)    # powers of s = half x
 
 
 def horner32(coef32: np.ndarray, s: np.ndarray) -> np.ndarray:
@@ -54,14 +55,16 @@ def horner32(coef32: np.ndarray, s: np.ndarray) -> np.ndarray:
 
 
 def build():
-    table = np.zeros((DEGREE + 1, N_PIECES), dtype=np.float32)
+    table = np.zeros((N_PIECES, DEGREE + 1), dtype=np.float32)
     worst = 0.0
+    half = 0.5 / PIECES_PER_UNIT
     for k in range(N_PIECES):
+        c = k / PIECES_PER_UNIT
         coef = piece_coefficients(k).astype(np.float32)
-        table[:, k] = coef
-        t = np.linspace(k * WIDTH, (k + 1) * WIDTH, 4001)
-        s = (t - (k * WIDTH + WIDTH / 2)).astype(np.float32)
-        exact = q_tail(t.astype(np.float32).astype(np.float64))
+        table[k] = coef
+        t = np.linspace(max(c - half, 0.0), min(c + half, T_MAX), 2001).astype(np.float32)
+        s = (t.astype(np.float64) - c).astype(np.float32)  # exact in the kernels (Sterbenz)
+        exact = q_tail(t.astype(np.float64))
         err = np.abs(horner32(coef, s).astype(np.float64) - exact)
         worst = max(worst, float(err.max()))
     return table, worst
@@ -71,16 +74,18 @@ def write(path=os.path.join(HERE, "phi_table.cuh")):
     table, worst = build()
     if worst > 4e-8:
         raise SystemExit(f"table error {worst:.3e} too large")
-    lines = ["// Generated by gen_phi_table.py: upper normal tail Q(t) = erfc(t / sqrt 2) / 2 on [0, 8)",
-             f"// as {N_PIECES} Chebyshev-interpolated pieces of degree {DEGREE} in s = t - (k/2 + 1/4);",
-             f"// coefficient j of piece k at kPhiTable[j * {N_PIECES} + k].  Max |error| of FP32 Horner",
+    lines = ["// Generated by gen_phi_table.py: upper normal tail Q(t) = erfc(t / sqrt 2) / 2 on [0, 8]",
+             f"// as {N_PIECES} Chebyshev-interpolated cubic pieces in s = t - k/{PIECES_PER_UNIT}, "
+             f"k = rint({PIECES_PER_UNIT} t);",
+             "// piece k = (c0, c1, c2, c3) at kPhiTable[4 k ..].  Max |error| of FP32 Horner",
              f"// on a dense grid: {worst:.2e}.",
              "#pragma once", "", "namespace spx {", "",
              f"constexpr int kPhiPieces = {N_PIECES};", f"constexpr int kPhiDegree = {DEGREE};",
-             f"constexpr float kPhiWidthInv = {1.0 / WIDTH:.1f}f;",
+             f"constexpr float kPhiPerUnit = {float(PIECES_PER_UNIT):.1f}f;",
+             f"constexpr float kPhiTMax = {T_MAX:.1f}f;",
              f"__device__ __constant__ float kPhiTable[{(DEGREE + 1) * N_PIECES}] = {{"]
-    for j in range(DEGREE + 1):
-        vals = ", ".join(f"{float(v):.9e}f" for v in table[j])
+    for k in range(N_PIECES):
+        vals = ", ".join(f"{float(v):.9e}f" for v in table[k])
         lines.append(f"    {vals},")
     lines += ["};", "", "}  // namespace spx", ""]
     with open(path, "w") as f:

@@ -15,6 +15,7 @@ struct KernelArgs {
     int32_t tile;
     int64_t n_part;                   // particles of all pairs
     int64_t n_tiles;                  // (pair, frame, tile) work items
+    int64_t n_chunks;                 // particle chunks (kChunk particles of one pair)
     uint64_t seed;
     float dt;
     int32_t n_substeps;
@@ -47,6 +48,9 @@ constexpr int kStageEvents = 6;
 constexpr int kSplatThreads = 256;     // k_splat below tile 64, k_finish
 constexpr int kSplatMaxThreads = 512;  // k_splat at tile 64 (more resident warps at 2 CTAs per SM)
 constexpr int kStageHeader = 320;     // descriptor (128) + plan (64) + blur taps (128)
+constexpr int kRecBufBytes = 8192;    // each staged-records buffer of k_splat
+constexpr int kRecCap = (kRecBufBytes - kStageHeader - 32) / 24;  // records per staged chunk
+static_assert(kRecCap <= 1015, "lo sums of one chunk must stay inside int32");
 
 cudaError_t launch_plan(const synthpix_pair_desc *descs, int32_t n_pairs, int32_t tile, int32_t fused,
                         PairPlan *plan, const Layout &L, int32_t *check, float *blur_w, uint32_t *ticket,

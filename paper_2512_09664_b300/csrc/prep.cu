@@ -33,13 +33,13 @@ namespace spx {
 __global__ void __launch_bounds__(1024) k_plan(const synthpix_pair_desc *__restrict__ descs, int32_t n_pairs,
                                                int32_t tile, int32_t fused, PairPlan *__restrict__ plan,
                                                int64_t want_part, int64_t want_tiles, int64_t want_list,
-                                               int64_t want_inter, int32_t *__restrict__ check,
+                                               int64_t want_inter, int64_t want_chunks, int32_t *__restrict__ check,
                                                float *__restrict__ blur_w, uint32_t *__restrict__ ticket) {
-    __shared__ long long s_part[1024], s_tile[1024], s_list[1024], s_inter[1024];
+    __shared__ long long s_part[1024], s_tile[1024], s_list[1024], s_inter[1024], s_chunk[1024];
     const int t = threadIdx.x;
     const int per = (n_pairs + 1023) / 1024;
     const int b0 = min(t * per, n_pairs), b1 = min(b0 + per, n_pairs);
-    long long np = 0, nt = 0, nl = 0, ni = 0;
+    long long np = 0, nt = 0, nl = 0, ni = 0, nc = 0;
     for (int b = b0; b < b1; ++b) {
         const synthpix_pair_desc d = descs[b];
         const PairGeom g = pair_geom(d, tile, fused != 0);
@@ -47,17 +47,22 @@ __global__ void __launch_bounds__(1024) k_plan(const synthpix_pair_desc *__restr
         nt += 2LL * g.ntiles;
         nl += 2LL * g.list_cap;
         ni += fused ? 0LL : 2LL * d.height * d.width;
+        nc += g.chunks;
     }
-    s_part[t] = np; s_tile[t] = nt; s_list[t] = nl; s_inter[t] = ni;
+    s_part[t] = np; s_tile[t] = nt; s_list[t] = nl; s_inter[t] = ni; s_chunk[t] = nc;
     __syncthreads();
     for (int off = 1; off < 1024; off <<= 1) {  // inclusive Hillis-Steele scan
-        long long a = 0, bq = 0, c = 0, e = 0;
-        if (t >= off) { a = s_part[t - off]; bq = s_tile[t - off]; c = s_list[t - off]; e = s_inter[t - off]; }
+        long long a = 0, bq = 0, c = 0, e = 0, h = 0;
+        if (t >= off) {
+            a = s_part[t - off]; bq = s_tile[t - off]; c = s_list[t - off]; e = s_inter[t - off];
+            h = s_chunk[t - off];
+        }
         __syncthreads();
-        s_part[t] += a; s_tile[t] += bq; s_list[t] += c; s_inter[t] += e;
+        s_part[t] += a; s_tile[t] += bq; s_list[t] += c; s_inter[t] += e; s_chunk[t] += h;
         __syncthreads();
     }
     long long bp = s_part[t] - np, bt = s_tile[t] - nt, bl = s_list[t] - nl, bi = s_inter[t] - ni;
+    long long bc = s_chunk[t] - nc;
     for (int b = b0; b < b1; ++b) {
         const synthpix_pair_desc d = descs[b];
         const PairGeom g = pair_geom(d, tile, fused != 0);
@@ -72,7 +77,8 @@ __global__ void __launch_bounds__(1024) k_plan(const synthpix_pair_desc *__restr
         p.ntiles = g.ntiles;
         p.blur_r = g.blur_r;
         p.halo = g.halo;
-        p.pad[0] = p.pad[1] = 0;
+        p.chunk_base = (int32_t)bc;
+        p.pad = 0;
         plan[b] = p;
         // normalised blur taps w[|k|], k = -R..R (FP64, stored FP32)
         if (g.blur_r > 0) {
@@ -88,78 +94,115 @@ __global__ void __launch_bounds__(1024) k_plan(const synthpix_pair_desc *__restr
         bt += 2LL * g.ntiles;
         bl += 2LL * g.list_cap;
         bi += fused ? 0LL : 2LL * d.height * d.width;
+        bc += g.chunks;
     }
     if (t == 1023) {
         *ticket = 0u;
         const bool ok = s_part[1023] == want_part && s_tile[1023] == want_tiles && s_list[1023] == want_list &&
-                        s_inter[1023] == want_inter;
+                        s_inter[1023] == want_inter && s_chunk[1023] == want_chunks;
         *check = ok ? 1 : 0;
     }
 }
 
 // ---------------------------------------------------------------------------
-// k_seed_advect: one thread per particle
+// One CTA per chunk of kChunk consecutive particles of one pair (seeding and
+// binning): the pair's descriptor and plan are read once into shared memory,
+// and per-(frame, tile) counts are aggregated in shared memory, so each CTA
+// makes one global atomic per tile it touches instead of one per particle.
 // ---------------------------------------------------------------------------
-// One particle of k_seed_advect: attributes, frame-1 record, and what the
-// advection needs.
-struct SeedState {
-    int64_t g;
-    int b;
-    Seeded P;
-    Flow F;
-    int32_t jx, jy;
-    float gx, gy;
+constexpr int kPrepThreads = 256;
+constexpr int kHistMax = 4096;  // (frame, tile) counters of a pair held on chip; larger pairs count in global
+
+struct ChunkCtx {
+    synthpix_pair_desc d;
+    PairPlan pl;
+    int32_t pair;
+    int32_t first;  // first particle of the chunk within the pair
+    int32_t n;      // particles in the chunk
 };
 
-__device__ __forceinline__ bool seed_one(const KernelArgs &a, int64_t g, SeedState &S) {
-    S.g = g;
-    if (g >= a.n_part) return false;
-    S.b = upper_find(a.n_pairs, g, [&](int m) { return a.plan[m].part_base; });
-    const synthpix_pair_desc &D = a.descs[S.b];
-    S.P = seed_particle(a, D, (uint32_t)(g - a.plan[S.b].part_base), g);
-    a.sa[g] = make_float2(S.P.sigma, S.P.amp);
-    a.pos0[g] = make_float4(S.P.fx, S.P.fy, __int_as_float(S.P.ix), __int_as_float(S.P.iy));
-    if (a.particles_out) {
-        a.particles_out[3 * g] = (float)S.P.ix + S.P.fx;
-        a.particles_out[3 * g + 1] = (float)S.P.iy + S.P.fy;
-        a.particles_out[3 * g + 2] = 4.0f * S.P.sigma;
+// The chunk of this CTA: pair (largest b with chunk_base(b) <= blockIdx.x),
+// descriptor and plan in shared memory.  Ends with a barrier.
+__device__ __forceinline__ void load_chunk(const KernelArgs &a, ChunkCtx &c) {
+    __shared__ int32_t s_pair;
+    if (threadIdx.x == 0)
+        s_pair = upper_find(a.n_pairs, (int64_t)blockIdx.x, [&](int m) { return (int64_t)a.plan[m].chunk_base; });
+    __syncthreads();
+    const int b = s_pair;
+    if (threadIdx.x < 8)
+        reinterpret_cast<int4 *>(&c.d)[threadIdx.x] = reinterpret_cast<const int4 *>(a.descs + b)[threadIdx.x];
+    else if (threadIdx.x < 12)
+        reinterpret_cast<int4 *>(&c.pl)[threadIdx.x - 8] = reinterpret_cast<const int4 *>(a.plan + b)[threadIdx.x - 8];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        c.pair = b;
+        c.first = (int32_t)(((int64_t)blockIdx.x - c.pl.chunk_base) * kChunk);
+        c.n = (int32_t)min((int64_t)kChunk, (int64_t)c.d.n_particles - c.first);
     }
-    S.F = pair_flow(a, D);
-    S.jx = S.P.ix;
-    S.jy = S.P.iy;
-    S.gx = S.P.fx;
-    S.gy = S.P.fy;
-    return true;
+    __syncthreads();
 }
 
-// Frame-2 record and bin counts of both frames.
-__device__ __forceinline__ void finish_one(const KernelArgs &a, const SeedState &S) {
-    a.pos1[S.g] = make_float4(S.gx, S.gy, __int_as_float(S.jx), __int_as_float(S.jy));
-    if (!a.count) return;
-    const PairPlan pl = a.plan[S.b];
-    const int32_t H = a.descs[S.b].height, W = a.descs[S.b].width;
-    const float r15 = 6.0f * S.P.sigma;  // 1.5 d
-    for (int f = 0; f < 2; ++f) {
-        const Window w = f ? particle_window(S.jx, S.gx, S.jy, S.gy, r15, W, H)
-                           : particle_window(S.P.ix, S.P.fx, S.P.iy, S.P.fy, r15, W, H);
-        if (w.j0 > w.j1 || w.i0 > w.i1) continue;
-        int32_t tx0, tx1, ty0, ty1;
-        window_tiles(w, pl.halo, a.tile, W, H, tx0, tx1, ty0, ty1);
-        uint32_t *cnt = a.count + pl.tile_base + (int64_t)f * pl.ntiles;
-        for (int32_t ty = ty0; ty <= ty1; ++ty)
-            for (int32_t tx = tx0; tx <= tx1; ++tx) atomicAdd(cnt + ty * pl.tiles_x + tx, 1u);
-    }
+// Bin counts of one frame's window: into the on-chip histogram, or global.
+__device__ __forceinline__ void count_window(const KernelArgs &a, const ChunkCtx &c, const Window &w, int f,
+                                             uint32_t *hist) {
+    if (w.j0 > w.j1 || w.i0 > w.i1) return;
+    int32_t tx0, tx1, ty0, ty1;
+    window_tiles(w, c.pl.halo, a.tile, c.d.width, c.d.height, tx0, tx1, ty0, ty1);
+    const int32_t k0 = f * c.pl.ntiles;
+    for (int32_t ty = ty0; ty <= ty1; ++ty)
+        for (int32_t tx = tx0; tx <= tx1; ++tx) {
+            const int32_t k = k0 + ty * c.pl.tiles_x + tx;
+            if (hist) atomicAdd(hist + k, 1u);
+            else atomicAdd(a.count + c.pl.tile_base + k, 1u);
+        }
 }
 
-// One thread per particle.  (Two particles per thread in lockstep needs 80
-// registers and lost more occupancy than it gained in overlap.)
-__global__ void __launch_bounds__(256) k_seed_advect(KernelArgs a) {
+// ---------------------------------------------------------------------------
+// k_seed_advect: Philox attributes, frame-1 position, advection to frame 2,
+// split positions and bin counts (seeding only: exports (x0, y0, d))
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kPrepThreads, 5) k_seed_advect(KernelArgs a) {
     if (*a.check != 1) return;
-    SeedState A;
-    if (!seed_one(a, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, A) || a.particles_out) return;
-    // frame-2 position: displacement over dt through the bilinear flow
-    advect_split(A.F, a.dt, a.n_substeps, a.integrator, A.jx, A.gx, A.jy, A.gy);
-    finish_one(a, A);
+    __shared__ __align__(16) ChunkCtx c;
+    __shared__ uint32_t hist[kHistMax];
+    load_chunk(a, c);
+    const int nk = 2 * c.pl.ntiles;
+    const bool counting = a.count != nullptr && !a.particles_out;
+    const bool local = counting && nk <= kHistMax;
+    if (local) {
+        for (int k = threadIdx.x; k < nk; k += kPrepThreads) hist[k] = 0u;
+        __syncthreads();
+    }
+    const Flow F = pair_flow(a, c.d);
+    for (int q = threadIdx.x; q < c.n; q += kPrepThreads) {
+        const uint32_t i = (uint32_t)(c.first + q);
+        const int64_t g = c.pl.part_base + i;
+        const Seeded P = seed_particle(a, c.d, i, g);
+        a.sa[g] = make_float2(P.sigma, P.amp);
+        a.pos0[g] = make_float4(P.fx, P.fy, __int_as_float(P.ix), __int_as_float(P.iy));
+        if (a.particles_out) {
+            a.particles_out[3 * g] = (float)P.ix + P.fx;
+            a.particles_out[3 * g + 1] = (float)P.iy + P.fy;
+            a.particles_out[3 * g + 2] = 4.0f * P.sigma;
+            continue;
+        }
+        int32_t jx = P.ix, jy = P.iy;
+        float gx = P.fx, gy = P.fy;
+        advect_split(F, a.dt, a.n_substeps, a.integrator, jx, gx, jy, gy);
+        a.pos1[g] = make_float4(gx, gy, __int_as_float(jx), __int_as_float(jy));
+        if (counting) {
+            const float r15 = 6.0f * P.sigma;  // 1.5 d
+            count_window(a, c, particle_window(P.ix, P.fx, P.iy, P.fy, r15, c.d.width, c.d.height), 0,
+                         local ? hist : nullptr);
+            count_window(a, c, particle_window(jx, gx, jy, gy, r15, c.d.width, c.d.height), 1,
+                         local ? hist : nullptr);
+        }
+    }
+    if (local) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < nk; k += kPrepThreads)
+            if (hist[k]) atomicAdd(a.count + c.pl.tile_base + k, hist[k]);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -208,36 +251,64 @@ __global__ void __launch_bounds__(1024) k_scan(KernelArgs a) {
 // ---------------------------------------------------------------------------
 // k_scatter: particle records into their tiles' bins (order within a bin is
 // free: the splat accumulates in exact fixed point, so sums are
-// order-independent)
+// order-independent).  On chip: count the chunk's records per tile, reserve
+// each tile's range with one global atomic, then place the records.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_scatter(KernelArgs a) {
-    if (*a.check != 1) return;
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= a.n_part) return;
-    const int b = upper_find(a.n_pairs, g, [&](int m) { return a.plan[m].part_base; });
-    const PairPlan pl = a.plan[b];
-    const int32_t H = a.descs[b].height, W = a.descs[b].width;
-    const float2 q = a.sa[g];
-    const float r15 = 6.0f * q.x;
-    for (int f = 0; f < 2; ++f) {
-        const float4 p = f ? a.pos1[g] : a.pos0[g];
-        const Window w = particle_window(__float_as_int(p.z), p.x, __float_as_int(p.w), p.y, r15, W, H);
-        if (w.j0 > w.j1 || w.i0 > w.i1) continue;
-        int32_t tx0, tx1, ty0, ty1;
-        window_tiles(w, pl.halo, a.tile, W, H, tx0, tx1, ty0, ty1);
-        const int64_t tb = pl.tile_base + (int64_t)f * pl.ntiles;
-        Record *seg = a.rec + pl.list_base + (int64_t)f * pl.list_cap;
-        for (int32_t ty = ty0; ty <= ty1; ++ty)
-            for (int32_t tx = tx0; tx <= tx1; ++tx) {
-                const uint32_t slot = atomicAdd(a.cursor + tb + ty * pl.tiles_x + tx, 1u);
-                if ((int64_t)slot < pl.list_cap) {
-                    float2 *r = reinterpret_cast<float2 *>(seg + slot);
-                    r[0] = make_float2(p.x, p.y);
-                    r[1] = make_float2(p.z, p.w);
-                    r[2] = q;
-                }
-            }
+template <typename Put>
+__device__ __forceinline__ void chunk_windows(const KernelArgs &a, const ChunkCtx &c, Put put) {
+    for (int q = threadIdx.x; q < c.n; q += kPrepThreads) {
+        const int64_t g = c.pl.part_base + c.first + q;
+        const float2 sa = a.sa[g];
+        const float r15 = 6.0f * sa.x;
+        for (int f = 0; f < 2; ++f) {
+            const float4 p = f ? a.pos1[g] : a.pos0[g];
+            const Window w = particle_window(__float_as_int(p.z), p.x, __float_as_int(p.w), p.y, r15, c.d.width,
+                                             c.d.height);
+            if (w.j0 > w.j1 || w.i0 > w.i1) continue;
+            int32_t tx0, tx1, ty0, ty1;
+            window_tiles(w, c.pl.halo, a.tile, c.d.width, c.d.height, tx0, tx1, ty0, ty1);
+            for (int32_t ty = ty0; ty <= ty1; ++ty)
+                for (int32_t tx = tx0; tx <= tx1; ++tx) put(f, f * c.pl.ntiles + ty * c.pl.tiles_x + tx, p, sa);
+        }
     }
+}
+
+__device__ __forceinline__ void put_record(const KernelArgs &a, const ChunkCtx &c, int f, uint32_t slot,
+                                           const float4 &p, const float2 &sa) {
+    if ((int64_t)slot < c.pl.list_cap) {
+        float2 *r = reinterpret_cast<float2 *>(a.rec + c.pl.list_base + (int64_t)f * c.pl.list_cap + slot);
+        r[0] = make_float2(p.x, p.y);
+        r[1] = make_float2(p.z, p.w);
+        r[2] = sa;
+    }
+}
+
+__global__ void __launch_bounds__(kPrepThreads) k_scatter(KernelArgs a) {
+    if (*a.check != 1) return;
+    __shared__ __align__(16) ChunkCtx c;
+    __shared__ uint32_t cnt[kHistMax], base[kHistMax];
+    load_chunk(a, c);
+    const int nk = 2 * c.pl.ntiles;
+    uint32_t *cursor = a.cursor + c.pl.tile_base;
+    if (nk > kHistMax) {
+        chunk_windows(a, c, [&](int f, int k, const float4 &p, const float2 &sa) {
+            put_record(a, c, f, atomicAdd(cursor + k, 1u), p, sa);
+        });
+        return;
+    }
+    for (int k = threadIdx.x; k < nk; k += kPrepThreads) cnt[k] = 0u;
+    __syncthreads();
+    chunk_windows(a, c, [&](int, int k, const float4 &, const float2 &) { atomicAdd(cnt + k, 1u); });
+    __syncthreads();
+    for (int k = threadIdx.x; k < nk; k += kPrepThreads) {
+        const uint32_t n = cnt[k];
+        base[k] = n ? atomicAdd(cursor + k, n) : 0u;
+        cnt[k] = 0u;
+    }
+    __syncthreads();
+    chunk_windows(a, c, [&](int f, int k, const float4 &p, const float2 &sa) {
+        put_record(a, c, f, base[k] + atomicAdd(cnt + k, 1u), p, sa);
+    });
 }
 
 // ---------------------------------------------------------------------------
@@ -246,8 +317,8 @@ __global__ void __launch_bounds__(256) k_scatter(KernelArgs a) {
 cudaError_t launch_plan(const synthpix_pair_desc *descs, int32_t n_pairs, int32_t tile, int32_t fused,
                         PairPlan *plan, const Layout &L, int32_t *check, float *blur_w, uint32_t *ticket,
                         cudaStream_t st) {
-    k_plan<<<1, 1024, 0, st>>>(descs, n_pairs, tile, fused, plan, L.n_part, L.n_tiles, L.n_list, L.n_inter, check,
-                               blur_w, ticket);
+    k_plan<<<1, 1024, 0, st>>>(descs, n_pairs, tile, fused, plan, L.n_part, L.n_tiles, L.n_list, L.n_inter,
+                               L.n_chunks, check, blur_w, ticket);
     return cudaGetLastError();
 }
 
@@ -255,12 +326,12 @@ cudaError_t launch_prep(const KernelArgs &a, cudaStream_t st, cudaEvent_t const 
     auto mark = [&](int k) {
         if (ev && ev[k]) cudaEventRecord(ev[k], st);
     };
-    const unsigned nb = (unsigned)((a.n_part + 255) / 256);
-    if (a.n_part > 0) k_seed_advect<<<(unsigned)((a.n_part + 255) / 256), 256, 0, st>>>(a);
+    const unsigned nb = (unsigned)a.n_chunks;
+    if (nb > 0) k_seed_advect<<<nb, kPrepThreads, 0, st>>>(a);
     mark(2);
     k_scan<<<2 * a.n_pairs, 1024, 0, st>>>(a);
     mark(3);
-    if (a.n_part > 0) k_scatter<<<nb, 256, 0, st>>>(a);
+    if (nb > 0) k_scatter<<<nb, kPrepThreads, 0, st>>>(a);
     mark(4);
     return cudaGetLastError();
 }
@@ -270,7 +341,7 @@ cudaError_t launch_prep(const KernelArgs &a, cudaStream_t st, cudaEvent_t const 
 namespace spx {
 
 cudaError_t launch_seed_only(const KernelArgs &a, cudaStream_t st) {
-    if (a.n_part > 0) k_seed_advect<<<(unsigned)((a.n_part + 255) / 256), 256, 0, st>>>(a);
+    if (a.n_chunks > 0) k_seed_advect<<<(unsigned)a.n_chunks, kPrepThreads, 0, st>>>(a);
     return cudaGetLastError();
 }
 

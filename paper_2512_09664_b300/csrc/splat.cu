@@ -57,16 +57,13 @@ __device__ __forceinline__ void stage_records(const KernelArgs &a, int64_t first
 __device__ __forceinline__ int record_lead(int64_t first) { return (int)((first * (int64_t)sizeof(Record)) & 15); }
 
 // ---------------------------------------------------------------------------
-// pixel integration of Eq. 1
-// ---------------------------------------------------------------------------
-
-// ---------------------------------------------------------------------------
 // exact fixed-point accumulation
 // ---------------------------------------------------------------------------
-// A contribution v in [0, i_max] is scaled to u = v * 1024 / i_max and split
-// into hi = rint(u) and lo = rint((u - hi) * 2^22), both found with the FP32
-// round-to-integer identity (x + 1.5 * 2^23 leaves rint(x) in the low
-// mantissa bits for |x| < 2^22).  The tile keeps int32 sums of hi and lo:
+// A contribution u = mx * my (pixel value * 1024 / i_max, at most 1024) is
+// split into hi = rint(u) and lo = rint((u - hi) * 2^22): hi from one FMA
+// with the FP32 round-to-integer identity (x + 1.5 * 2^23 leaves rint(x) in
+// the low mantissa bits for 0 <= x < 2^22), u - hi from a second FMA (one
+// rounding of the exact residual).  The tile keeps int32 sums of hi and lo:
 // integer addition is associative, so a pixel's value does not depend on the
 // order of its contributions, the tile size or the batch it is rendered in.
 // lo sums stay inside int32 for up to 1016 contributions; after every staged
@@ -75,13 +72,13 @@ __device__ __forceinline__ int record_lead(int64_t first) { return (int)((first 
 constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
 constexpr int32_t kMagicBits = 0x4B400000;
 
-__device__ __forceinline__ void add_fixed(int32_t *hi, int32_t *lo, int idx, float u) {
-    const float t = __fadd_rn(u, kMagic);
+__device__ __forceinline__ void add_fixed(int32_t *hi, int32_t *lo, float mx, float my) {
+    const float t = fmaf(mx, my, kMagic);
     const int32_t h = __float_as_int(t) - kMagicBits;
-    const float r = __fsub_rn(u, __fsub_rn(t, kMagic));  // exact, |r| <= 1/2
+    const float r = fmaf(mx, my, -__fsub_rn(t, kMagic));  // |r| <= 1/2
     const int32_t l = __float_as_int(fmaf(r, 4194304.0f, kMagic)) - kMagicBits;
-    atomicAdd(hi + idx, h);
-    atomicAdd(lo + idx, l);
+    atomicAdd(hi, h);
+    atomicAdd(lo, l);
 }
 
 __device__ __forceinline__ void carry_fixed(int32_t *hi, int32_t *lo, int n) {
@@ -102,36 +99,126 @@ struct Geo {
     int32_t FW, FH;              // full halo rectangle (replicated outside the frame)
 };
 
-// Upper normal tail Q(t) = erfc(t / sqrt 2) / 2 for t >= 0 from the
-// piecewise polynomial table (staged in shared memory as [coef][piece]).
-__device__ __forceinline__ float phi_tail(float t, const float *tab) {
-    const int k = min((int)(t * kPhiWidthInv), kPhiPieces - 1);
-    const float s = t - fmaf((float)k, 1.0f / kPhiWidthInv, 0.5f / kPhiWidthInv);
-    float acc = tab[kPhiDegree * kPhiPieces + k];
+// ---------------------------------------------------------------------------
+// pixel integration of Eq. 1
+// ---------------------------------------------------------------------------
+// Upper normal tail Q(a) = erfc(a / sqrt 2) / 2 for a >= 0 from the cubic
+// table (one float4 per piece, staged in shared memory).  a is clamped to
+// the table's end (Q(8) = 6e-16); the piece is k = rint(16 a), so
+// s = a - k / 16 is exact and |s| <= 1/32.
+__device__ __forceinline__ float phi_tail(float a, const float4 *tab) {
+    a = fminf(a, kPhiTMax);
+    const float kf = fmaf(a, kPhiPerUnit, kMagic);
+    const int k = __float_as_int(kf) - kMagicBits;
+    const float s = fmaf(__fsub_rn(kf, kMagic), -1.0f / kPhiPerUnit, a);
+    const float4 c = tab[k];
+    return fmaf(fmaf(fmaf(c.w, s, c.z), s, c.y), s, c.x);
+}
+
+// Edge value of a pixel edge at offset dd (edge - particle centre, pixels):
+// Phi(t) for t = dd / sigma <= 0, -(1 - Phi(t)) for t > 0 (tails keep their
+// absolute accuracy; pixel_mass adds the 1 back across the centre).
+__device__ __forceinline__ float edge_value_tab(float dd, float inv, const float4 *tab) {
+    const float q = phi_tail(fabsf(__fmul_rn(dd, inv)), tab);
+    return dd > 0.0f ? -q : q;
+}
+
+// One particle's visit of a tile, set up for the splat (same size as a
+// Record, written over the staged records it comes from).
+struct Visit {
+    float px, py;    // fractions of the split position
+    float inv;       // 1 / sigma
+    float amps;      // amplitude * 1024 / i_max
+    int32_t base;    // accumulator index of the clipped window's first pixel
+    uint32_t shape;  // bx | by << 8 (int8: window start - integer position) | nx << 16 | ny << 24
+};
+static_assert(sizeof(Visit) == sizeof(Record), "Visit layout");
+
+__device__ __forceinline__ int visit_bx(uint32_t s) { return (int)(int8_t)(s & 0xFFu); }
+__device__ __forceinline__ int visit_by(uint32_t s) { return (int)(int8_t)((s >> 8) & 0xFFu); }
+__device__ __forceinline__ int visit_nx(uint32_t s) { return (int)((s >> 16) & 0xFFu); }
+__device__ __forceinline__ int visit_ny(uint32_t s) { return (int)(s >> 24); }
+
+// Visits are sorted by (class, accumulator bank) before the splat: class c < 8
+// holds windows of at most N = 2 (c + 1) pixels a side, rendered by
+// splat_narrow<N> in units of at most kUnitRows[c] rows, one unit per lane
+// (a visit of class c is kUnits[c] units, the x edges evaluated by each); class
+// 8 holds the wider ones, rendered by a whole warp per visit.  Lanes of a
+// narrow warp take visits spread over the bank order, so their accumulator
+// addresses fall in different banks.
+constexpr int kNarrowMax = 16;
+constexpr int kWideClass = kNarrowMax / 2;
+constexpr int kBuckets = (kWideClass + 1) * 32;
+__host__ __device__ constexpr int unit_rows(int c) { return c == 0 ? 2 : (c == 2 ? 3 : 4); }
+__host__ __device__ constexpr int units_of(int c) { return (2 * (c + 1) + unit_rows(c) - 1) / unit_rows(c); }
+
+// Quotient of small non-negative integers a / b (a < 2^20, 1 <= b <= 2^10)
+// from b's reciprocal: (a + 1/2) / b is at least 1/(2b) away from an integer,
+// far more than the rounding error of the product.
+__device__ __forceinline__ int small_div(int a, float inv_b) { return (int)(((float)a + 0.5f) * inv_b); }
+
+// One visit per lane, window at most N x N: the x masses in registers, then
+// the rows (ny_max: the warp's largest ny), each with one new y edge.
+template <int N>
+__device__ __forceinline__ void splat_narrow(const Visit &v, int ny_max, int EW, int32_t *hi, int32_t *lo,
+                                             const float4 *tab) {
+    const int nx = visit_nx(v.shape), ny = visit_ny(v.shape);
+    const float fbx = (float)visit_bx(v.shape), fby = (float)visit_by(v.shape);
+    float mx[N];
+    float ea;
+    bool pa;
+    {
+        const float dd = __fsub_rn(fbx, v.px);
+        pa = dd > 0.0f;
+        ea = edge_value_tab(dd, v.inv, tab);
+    }
 #pragma unroll
-    for (int j = kPhiDegree - 1; j >= 0; --j) acc = fmaf(acc, s, tab[j * kPhiPieces + k]);
-    return t < 8.0f ? acc : 0.0f;
+    for (int e = 0; e < N; ++e) {
+        const float dd = __fsub_rn(__fadd_rn(fbx, (float)(e + 1)), v.px);
+        const bool pb = dd > 0.0f;
+        const float eb = edge_value_tab(dd, v.inv, tab);
+        mx[e] = pixel_mass(ea, eb, pa, pb);
+        ea = eb;
+        pa = pb;
+    }
+    {
+        const float dd = __fsub_rn(fby, v.py);
+        pa = dd > 0.0f;
+        ea = edge_value_tab(dd, v.inv, tab);
+    }
+    int32_t *hr = hi + v.base, *lr = lo + v.base;
+    float fr = fby;
+    for (int r = 0; r < ny_max; ++r) {
+        fr = __fadd_rn(fr, 1.0f);
+        const float dd = __fsub_rn(fr, v.py);
+        const bool pb = dd > 0.0f;
+        const float eb = edge_value_tab(dd, v.inv, tab);
+        const float my = __fmul_rn(pixel_mass(ea, eb, pa, pb), v.amps);
+        ea = eb;
+        pa = pb;
+        if (r < ny) {
+#pragma unroll
+            for (int c = 0; c < N; ++c)
+                if (c < nx) add_fixed(hr + c, lr + c, mx[c], my);
+        }
+        hr += EW;
+        lr += EW;
+    }
 }
 
-// edge_value() evaluated from the table: Phi(t) for t <= 0, -(1 - Phi(t)) for t > 0.
-__device__ __forceinline__ float edge_value_tab(float t, const float *tab) {
-    const float q = phi_tail(fabsf(t), tab);
-    return t > 0.0f ? -q : q;
-}
-
-// Large windows (more than 30 edges): per-warp scratch in shared memory.
-__device__ __noinline__ void splat_particle_wide(const Geo &g, int32_t *hi, int32_t *lo, float px, float py,
-                                                 int32_t ix, int32_t iy, float inv, float amps, int32_t j0,
-                                                 int32_t i0, int nx, int ny, float *scr, int wq, const float *tab) {
+// Windows with more than 30 edges: per-warp scratch in shared memory.
+__device__ __noinline__ void splat_particle_wide(int EW, int32_t *hi, int32_t *lo, float px, float py, float inv,
+                                                 float amps, int32_t base, int bx, int by, int nx, int ny,
+                                                 float *scr, int wq, const float4 *tab) {
     const int lane = threadIdx.x & 31;
     float *exe = scr, *eye = scr + wq, *ex = scr + 2 * wq, *ey = scr + 3 * wq;
-    for (int e = lane; e <= nx; e += 32) exe[e] = edge_value_tab(((float)(j0 + e - ix) - px) * inv, tab);
-    for (int e = lane; e <= ny; e += 32) eye[e] = edge_value_tab(((float)(i0 + e - iy) - py) * inv, tab);
+    for (int e = lane; e <= nx; e += 32) exe[e] = edge_value_tab(__fsub_rn((float)(bx + e), px), inv, tab);
+    for (int e = lane; e <= ny; e += 32) eye[e] = edge_value_tab(__fsub_rn((float)(by + e), py), inv, tab);
     __syncwarp();
     for (int e = lane; e < nx; e += 32)
-        ex[e] = pixel_mass(exe[e], exe[e + 1], (float)(j0 + e - ix) > px, (float)(j0 + e + 1 - ix) > px);
+        ex[e] = pixel_mass(exe[e], exe[e + 1], (float)(bx + e) > px, (float)(bx + e + 1) > px);
     for (int e = lane; e < ny; e += 32)
-        ey[e] = amps * pixel_mass(eye[e], eye[e + 1], (float)(i0 + e - iy) > py, (float)(i0 + e + 1 - iy) > py);
+        ey[e] = __fmul_rn(pixel_mass(eye[e], eye[e + 1], (float)(by + e) > py, (float)(by + e + 1) > py), amps);
     __syncwarp();
     const int n = nx * ny;
     const float invx = 1.0f / (float)nx;
@@ -139,88 +226,212 @@ __device__ __noinline__ void splat_particle_wide(const Geo &g, int32_t *hi, int3
         const int r = min((int)(((float)m + 0.5f) * invx), ny - 1);
         const int cc = m - r * nx;
         if ((unsigned)cc >= (unsigned)nx) continue;
-        add_fixed(hi, lo, (i0 - g.ey0 + r) * g.EW + (j0 - g.ex0 + cc), __fmul_rn(ex[cc], ey[r]));
+        const int idx = base + r * EW + cc;
+        add_fixed(hi + idx, lo + idx, ex[cc], ey[r]);
     }
     __syncwarp();
 }
 
-// Quotient of small non-negative integers a / b (a < 2^20, 1 <= b <= 2^10)
-// from b's reciprocal: (a + 1/2) / b is at least 1/(2b) away from an integer,
-// far more than the rounding error of the product.
-__device__ __forceinline__ int small_div(int a, float inv_b) { return (int)(((float)a + 0.5f) * inv_b); }
-
-// Splat n staged records.  A warp takes up to 32 records at a time (record
-// warp + 8 l for lane l), sets each one up lane-parallel (window clipped to
-// the halo rectangle, reciprocals), then renders them one after another:
-// lanes [0, nx] evaluate the x edges, lanes [nx+1, nx+ny+1] the y edges;
-// each lane then takes one column and every rpr-th row of the window.
-__device__ __forceinline__ void splat_records(const unsigned char *recs, uint32_t n, const Geo &g, float scale,
-                                              int32_t *hi, int32_t *lo, float *scr, int wq, const float *tab) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Wide visits, a warp per visit: lanes [0, nx] evaluate the x edges, lanes
+// [nx+1, nx+ny+1] the y edges; each lane then takes one column and every
+// rpr-th row of the window.  Windows with more edges than lanes go through
+// the scratch path.
+__device__ __forceinline__ void splat_coop(const Visit &v, bool valid, int EW, int32_t *hi, int32_t *lo, float *scr,
+                                           int wq, const float4 *tab) {
+    const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
-    const uint32_t nw = blockDim.x >> 5;
-    for (uint32_t k0 = warp; k0 < n; k0 += nw * 32) {
-        const uint32_t k = k0 + nw * lane;
-        float px = 0.f, py = 0.f, inv = 0.f, amps = 0.f, invn = 0.f;
-        int32_t ix = 0, iy = 0, j0 = 0, i0 = 0, nx = 0, ny = 0;
+    uint32_t todo = __ballot_sync(FULL, valid);
+    while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const float px = __shfl_sync(FULL, v.px, src), py = __shfl_sync(FULL, v.py, src);
+        const float inv = __shfl_sync(FULL, v.inv, src), amps = __shfl_sync(FULL, v.amps, src);
+        const int32_t base = __shfl_sync(FULL, v.base, src);
+        const uint32_t shape = __shfl_sync(FULL, v.shape, src);
+        const int nx = visit_nx(shape), ny = visit_ny(shape), bx = visit_bx(shape), by = visit_by(shape);
+        if (nx + ny + 2 > 32) {
+            splat_particle_wide(EW, hi, lo, px, py, inv, amps, base, bx, by, nx, ny, scr, wq, tab);
+            continue;
+        }
+        const int nxe = nx + 1;
+        const bool isx = lane < nxe;
+        const int e = isx ? lane : lane - nxe;
+        const float dd = __fsub_rn((float)((isx ? bx : by) + e), isx ? px : py);
+        const bool dpos = dd > 0.0f;
+        const float ev = lane < nxe + ny + 1 ? edge_value_tab(dd, inv, tab) : 0.0f;
+        const float evn = __shfl_down_sync(FULL, ev, 1);
+        const bool dposn = __shfl_down_sync(FULL, (int)dpos, 1) != 0;
+        float m = pixel_mass(ev, evn, dpos, dposn);
+        if (!isx) m = __fmul_rn(m, amps);
+        // lane -> (row offset lr, column lc); rpr rows per round
+        const float invn = __frcp_rn((float)nx);
+        const int rpr = small_div(32, invn);
+        const int lr = small_div(lane, invn);
+        const int lc = lane - lr * nx;
+        const float exv = __shfl_sync(FULL, m, lc);
+        const bool act = lr < rpr;
+        const int idx = base + lr * EW + lc;
+        for (int r0 = 0; r0 < ny; r0 += rpr) {
+            const int r = r0 + lr;
+            const float eyv = __shfl_sync(FULL, m, nxe + min(r, ny - 1));
+            if (act && r < ny) add_fixed(hi + idx + r0 * EW, lo + idx + r0 * EW, exv, eyv);
+        }
+    }
+}
+
+// Counters of the per-chunk visit sort (static shared memory of k_splat).
+struct SortSmem {
+    uint32_t *cnt;   // [kBuckets] visits per (class, bank) key
+    uint32_t *off;   // [kBuckets + 1] exclusive offsets
+    uint32_t *next;  // warp-slot ticket
+};
+
+// Splat n staged records (at recs) into the tile's accumulator:
+//   A. each thread sets up its records' visits (window clipped to the halo
+//      rectangle) and takes a slot in its (class, bank) bucket;
+//   B. warp 0 scans the bucket counts;
+//   C. the visits are written in key order over the staged records (out);
+//   D. warps claim slots of 32 visits, widest class first, and render them.
+template <int NT>
+__device__ __forceinline__ void splat_chunk(const unsigned char *recs, unsigned char *out, uint32_t n, const Geo &g,
+                                            float scale, int32_t *hi, int32_t *lo, const SortSmem &ss, float *scr,
+                                            int wq, const float4 *tab) {
+    constexpr int RPT = (kRecCap + NT - 1) / NT;
+    const int lane = threadIdx.x & 31;
+    const unsigned FULL = 0xffffffffu;
+    Visit v[RPT];
+    int key[RPT];
+    uint32_t slot[RPT];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+        const uint32_t k = threadIdx.x + (uint32_t)q * NT;
+        key[q] = -1;
+        slot[q] = 0;
         if (k < n) {
             const unsigned char *rp = recs + (size_t)k * sizeof(Record);
             const float2 pf = *reinterpret_cast<const float2 *>(rp);
             const int2 pi = *reinterpret_cast<const int2 *>(rp + 8);
             const float2 ps = *reinterpret_cast<const float2 *>(rp + 16);
-            px = pf.x;
-            py = pf.y;
-            ix = pi.x;
-            iy = pi.y;
             const float r15 = 6.0f * ps.x;  // 1.5 d
-            j0 = max(ix + (int32_t)floorf(px - r15), g.ex0);
-            const int32_t j1 = min(ix + (int32_t)floorf(px + r15), g.ex1 - 1);
-            i0 = max(iy + (int32_t)floorf(py - r15), g.ey0);
-            const int32_t i1 = min(iy + (int32_t)floorf(py + r15), g.ey1 - 1);
+            const int32_t j0 = max(pi.x + (int32_t)floorf(pf.x - r15), g.ex0);
+            const int32_t j1 = min(pi.x + (int32_t)floorf(pf.x + r15), g.ex1 - 1);
+            const int32_t i0 = max(pi.y + (int32_t)floorf(pf.y - r15), g.ey0);
+            const int32_t i1 = min(pi.y + (int32_t)floorf(pf.y + r15), g.ey1 - 1);
             if (j0 <= j1 && i0 <= i1) {
-                nx = j1 - j0 + 1;
-                ny = i1 - i0 + 1;
-                inv = __frcp_rn(ps.x);
-                amps = ps.y * scale;
-                invn = __frcp_rn((float)nx);
+                const int nx = j1 - j0 + 1, ny = i1 - i0 + 1;
+                v[q].px = pf.x;
+                v[q].py = pf.y;
+                v[q].inv = __frcp_rn(ps.x);
+                v[q].amps = ps.y * scale;
+                v[q].base = (i0 - g.ey0) * g.EW + (j0 - g.ex0);
+                v[q].shape = ((uint32_t)(j0 - pi.x) & 0xFFu) | (((uint32_t)(i0 - pi.y) & 0xFFu) << 8) |
+                             ((uint32_t)nx << 16) | ((uint32_t)ny << 24);
+                const int m = max(nx, ny);
+                const int cls = m > kNarrowMax ? kWideClass : (m - 1) >> 1;
+                key[q] = cls * 32 + (v[q].base & 31);
+                slot[q] = atomicAdd(ss.cnt + key[q], 1u);
             }
         }
-        uint32_t todo = __ballot_sync(FULL, nx > 0);
-        while (todo) {
-            const int src = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int bnx = __shfl_sync(FULL, nx, src), bny = __shfl_sync(FULL, ny, src);
-            const float bpx = __shfl_sync(FULL, px, src), bpy = __shfl_sync(FULL, py, src);
-            const int32_t bix = __shfl_sync(FULL, ix, src), biy = __shfl_sync(FULL, iy, src);
-            const int32_t bj0 = __shfl_sync(FULL, j0, src), bi0 = __shfl_sync(FULL, i0, src);
-            const float binv = __shfl_sync(FULL, inv, src), bamps = __shfl_sync(FULL, amps, src);
-            if (bnx + bny + 2 > 32) {
-                splat_particle_wide(g, hi, lo, bpx, bpy, bix, biy, binv, bamps, bj0, bi0, bnx, bny, scr, wq, tab);
-                continue;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        constexpr int PER = kBuckets / 32;
+        uint32_t c[PER], sum = 0;
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            c[j] = ss.cnt[lane * PER + j];
+            ss.cnt[lane * PER + j] = 0;
+            sum += c[j];
+        }
+        uint32_t incl = sum;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t t = __shfl_up_sync(FULL, incl, d);
+            if (lane >= d) incl += t;
+        }
+        uint32_t run = incl - sum;
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            ss.off[lane * PER + j] = run;
+            run += c[j];
+        }
+        if (lane == 31) ss.off[kBuckets] = incl;
+        if (lane == 0) *ss.next = 0;
+    }
+    __syncthreads();
+    float2 *o8 = reinterpret_cast<float2 *>(out);  // 16-byte aligned; a Visit is three 8-byte words
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+        if (key[q] >= 0) {
+            const uint32_t p = ss.off[key[q]] + slot[q];
+            o8[3 * p] = make_float2(v[q].px, v[q].py);
+            o8[3 * p + 1] = make_float2(v[q].inv, v[q].amps);
+            o8[3 * p + 2] = make_float2(__int_as_float(v[q].base), __uint_as_float(v[q].shape));
+        }
+    }
+    __syncthreads();
+    for (;;) {
+        uint32_t sl = 0;
+        if (lane == 0) sl = atomicAdd(ss.next, 1u);
+        sl = __shfl_sync(FULL, sl, 0);
+        int c = kWideClass;
+        uint32_t g0 = 0, G = 0, nw = 0;
+        for (; c >= 0; --c) {
+            g0 = ss.off[32 * c];
+            G = ss.off[32 * c + 32] - g0;
+            nw = (G * (c == kWideClass ? 1u : (uint32_t)units_of(c)) + 31) >> 5;
+            if (sl < nw) break;
+            sl -= nw;
+        }
+        if (c < 0) break;
+        uint32_t idx;
+        int r0 = 0;
+        if (c == kWideClass) {
+            idx = sl * 32 + lane;
+        } else {
+            // unit i = u * G + visit: rows [u R, u R + R) of the visit
+            const uint32_t i = sl + lane * nw;
+            const int u = i < G * (uint32_t)units_of(c) ? small_div((int)i, 1.0f / (float)G) : units_of(c);
+            idx = i - (uint32_t)u * G;
+            r0 = u * unit_rows(c);
+            if (u >= units_of(c)) idx = G;
+        }
+        bool valid = idx < G;
+        Visit e;
+        if (valid) {
+            const float2 a = o8[3 * (g0 + idx)], b = o8[3 * (g0 + idx) + 1], d = o8[3 * (g0 + idx) + 2];
+            e.px = a.x;
+            e.py = a.y;
+            e.inv = b.x;
+            e.amps = b.y;
+            e.base = __float_as_int(d.x);
+            e.shape = __float_as_uint(d.y);
+            if (c != kWideClass) {
+                const int rows = min(visit_ny(e.shape) - r0, unit_rows(c));
+                valid = rows > 0;
+                e.base += r0 * g.EW;
+                e.shape = (e.shape & 0x00FF00FFu) | ((uint32_t)((visit_by(e.shape) + r0) & 0xFF) << 8) |
+                          ((uint32_t)max(rows, 0) << 24);
             }
-            const float binvn = __shfl_sync(FULL, invn, src);
-            const int nxe = bnx + 1;
-            const bool isx = lane < nxe;
-            const int e = isx ? lane : lane - nxe;
-            const float dd = isx ? (float)(bj0 + e - bix) - bpx : (float)(bi0 + e - biy) - bpy;
-            const bool dpos = dd > 0.0f;
-            const float ev = lane < nxe + bny + 1 ? edge_value_tab(dd * binv, tab) : 0.0f;
-            const float evn = __shfl_down_sync(FULL, ev, 1);
-            const bool dposn = __shfl_down_sync(FULL, (int)dpos, 1) != 0;
-            float m = pixel_mass(ev, evn, dpos, dposn);
-            if (!isx) m *= bamps;
-            // lane -> (row offset lr, column lc); rpr rows per round
-            const int rpr = small_div(32, binvn);
-            const int lr = small_div(lane, binvn);
-            const int lc = lane - lr * bnx;
-            const float exv = __shfl_sync(FULL, m, lc);
-            const bool act = lr < rpr;
-            const int base = (bi0 - g.ey0 + lr) * g.EW + (bj0 - g.ex0 + lc);
-            for (int r0 = 0; r0 < bny; r0 += rpr) {
-                const int r = r0 + lr;
-                const float eyv = __shfl_sync(FULL, m, nxe + min(r, bny - 1));
-                if (act && r < bny) add_fixed(hi, lo, base + r0 * g.EW, __fmul_rn(exv, eyv));
-            }
+        } else {
+            e.px = e.py = e.inv = e.amps = 0.0f;
+            e.base = 0;
+            e.shape = 0;
+        }
+        if (c == kWideClass) {
+            splat_coop(e, valid, g.EW, hi, lo, scr, wq, tab);
+            continue;
+        }
+        const int ny_max = (int)__reduce_max_sync(FULL, (unsigned)visit_ny(e.shape));
+        switch (c) {
+        case 0: splat_narrow<2>(e, ny_max, g.EW, hi, lo, tab); break;
+        case 1: splat_narrow<4>(e, ny_max, g.EW, hi, lo, tab); break;
+        case 2: splat_narrow<6>(e, ny_max, g.EW, hi, lo, tab); break;
+        case 3: splat_narrow<8>(e, ny_max, g.EW, hi, lo, tab); break;
+        case 4: splat_narrow<10>(e, ny_max, g.EW, hi, lo, tab); break;
+        case 5: splat_narrow<12>(e, ny_max, g.EW, hi, lo, tab); break;
+        case 6: splat_narrow<14>(e, ny_max, g.EW, hi, lo, tab); break;
+        default: splat_narrow<16>(e, ny_max, g.EW, hi, lo, tab); break;
         }
     }
 }
@@ -391,7 +602,9 @@ __device__ __forceinline__ void store_unblurred(const Geo &g, const float *A, T 
 // ---------------------------------------------------------------------------
 struct Smem {
     int32_t *hi, *lo;
-    float *A, *Bh, *sx2, *sy2, *scr, *phi;
+    float *A, *Bh, *sx2, *sy2, *scr;
+    const float4 *phi;
+    SortSmem sort;
     int BP;
 };
 
@@ -521,7 +734,7 @@ __device__ __forceinline__ __nv_bfloat16 to_inter<__nv_bfloat16>(float v) { retu
 // One work item of k_splat.  Fused (inter_dtype F32): splat the tile plus
 // its blur halo and finish it on chip.  Otherwise splat the tile alone and
 // store S in 16 bits to the intermediate frames; k_finish does the rest.
-template <typename T>
+template <typename T, int NT>
 __device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo &it, unsigned char *buf,
                                              uint32_t cap, const Smem &s) {
     const synthpix_pair_desc &D = *reinterpret_cast<const synthpix_pair_desc *>(buf);
@@ -537,8 +750,8 @@ __device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo
     uint32_t done = 0;
     while (done < it.count) {
         const uint32_t n = min(it.count - done, cap);
-        splat_records(buf + kStageHeader + record_lead(it.rec0 + done), n, g, scale, s.hi, s.lo,
-                      s.scr + (threadIdx.x >> 5) * a.warp_scratch, a.warp_scratch >> 2, s.phi);
+        splat_chunk<NT>(buf + kStageHeader + record_lead(it.rec0 + done), buf + kStageHeader, n, g, scale, s.hi,
+                        s.lo, s.sort, s.scr + (threadIdx.x >> 5) * a.warp_scratch, a.warp_scratch >> 2, s.phi);
         done += n;
         __syncthreads();
         if (done < it.count) {  // more records: carry lo before the next chunk (the last carry is in pass 1)
@@ -609,10 +822,11 @@ __host__ __device__ inline SmemLayout smem_layout(int E, int tile, int warp_scra
 }
 
 template <typename T, int NT>
-__global__ void __launch_bounds__(NT) k_splat(KernelArgs a) {
+__global__ void __launch_bounds__(NT, 1024 / NT) k_splat(KernelArgs a) {
     if (*a.check != 1) return;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ ItemInfo s_item[2];
+    __shared__ uint32_t s_cnt[kBuckets], s_off[kBuckets + 1], s_next;
     const SmemLayout L = smem_layout(a.smem_edge, a.tile, a.warp_scratch, a.rec_buf_bytes);
     Smem s;
     s.hi = reinterpret_cast<int32_t *>(smem + L.hi);
@@ -622,11 +836,16 @@ __global__ void __launch_bounds__(NT) k_splat(KernelArgs a) {
     s.sx2 = reinterpret_cast<float *>(smem + L.sx2);
     s.sy2 = reinterpret_cast<float *>(smem + L.sy2);
     s.scr = reinterpret_cast<float *>(smem + L.scr);
-    s.phi = reinterpret_cast<float *>(smem + L.phi);
-    for (int k = threadIdx.x; k < (kPhiDegree + 1) * kPhiPieces; k += blockDim.x) s.phi[k] = kPhiTable[k];
+    float *phi = reinterpret_cast<float *>(smem + L.phi);
+    for (int k = threadIdx.x; k < (kPhiDegree + 1) * kPhiPieces; k += blockDim.x) phi[k] = kPhiTable[k];
+    s.phi = reinterpret_cast<const float4 *>(phi);
+    s.sort.cnt = s_cnt;
+    s.sort.off = s_off;
+    s.sort.next = &s_next;
+    for (int k = threadIdx.x; k < kBuckets; k += blockDim.x) s_cnt[k] = 0;
     s.BP = (a.tile + 3) & ~3;
     unsigned char *bufs = smem + L.bufs;
-    const uint32_t cap = (uint32_t)((a.rec_buf_bytes - kStageHeader - 32) / (int)sizeof(Record));
+    const uint32_t cap = (uint32_t)kRecCap;
     const int E2 = a.smem_edge * a.smem_edge;
     for (int k = threadIdx.x; k < E2; k += blockDim.x) {
         s.hi[k] = 0;
@@ -661,7 +880,7 @@ __global__ void __launch_bounds__(NT) k_splat(KernelArgs a) {
         cp_async_commit();
         uint32_t t2 = 0;
         if (threadIdx.x == 0) t2 = atomicAdd(a.ticket, 1u);
-        process_item<T>(a, it, bufs + cur * a.rec_buf_bytes, cap, s);
+        process_item<T, NT>(a, it, bufs + cur * a.rec_buf_bytes, cap, s);
         if (threadIdx.x == 0) {
             ItemInfo after;
             if ((int64_t)t2 < a.n_tiles) after = a.items[t2];
@@ -714,6 +933,7 @@ __global__ void __launch_bounds__(kSplatThreads) k_finish(KernelArgs a) {
     s.sy2 = reinterpret_cast<float *>(smem + FL.sy2);
     s.scr = nullptr;
     s.phi = nullptr;
+    s.sort = SortSmem{nullptr, nullptr, nullptr};
     s.BP = (a.tile + 3) & ~3;
     const ItemInfo it = a.items[blockIdx.x];
     const synthpix_pair_desc &D = a.descs[it.pair];
