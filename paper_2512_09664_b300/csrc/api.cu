@@ -276,6 +276,7 @@ static int run(Mode mode, const synthpix_batch_desc *batch, const synthpix_pair_
     a.n_tiles = L.n_tiles;
     a.n_chunks = L.n_chunks;
     a.seed = batch->seed;
+    a.keys = spx::philox_round_keys(batch->seed);
     a.dt = batch->dt;
     a.n_substeps = batch->n_substeps;
     a.integrator = batch->integrator;

@@ -93,28 +93,39 @@ __host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~(size
 // the other counter words and the key, the key advanced by the Weyl
 // increments between rounds.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        if (r) {
-            k.x += 0x9E3779B9u;
-            k.y += 0xBB67AE85u;
-        }
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
-    }
-    return c;
-}
-
 // Stream layout: counter = (index, tag, pair_id lo, pair_id hi), key = seed.
 constexpr uint32_t kTagAttrA = 0u;      // (x, y, d, I)
 constexpr uint32_t kTagAttrB = 1u;      // (z, d2, -, -)
 constexpr uint32_t kTagNoise = 0x100u;  // + frame; index = pixel / 4
 
-__device__ __forceinline__ uint4 stream_words(uint64_t seed, uint64_t pair_id, uint32_t idx, uint32_t tag) {
-    return philox4x32_10(make_uint4(idx, tag, (uint32_t)pair_id, (uint32_t)(pair_id >> 32)),
-                         make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+// The ten round keys (key + r * Weyl increments) are computed once per
+// launch: kernels read them from the launch parameters instead of advancing
+// the key in every call.
+struct PhiloxKeys {
+    uint32_t x[10], y[10];
+};
+
+__host__ __device__ inline PhiloxKeys philox_round_keys(uint64_t seed) {
+    PhiloxKeys K;
+    uint32_t kx = (uint32_t)seed, ky = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        K.x[r] = kx;
+        K.y[r] = ky;
+        kx += 0x9E3779B9u;
+        ky += 0xBB67AE85u;
+    }
+    return K;
+}
+
+__device__ __forceinline__ uint4 stream_words(const PhiloxKeys &K, uint64_t pair_id, uint32_t idx, uint32_t tag) {
+    uint4 c = make_uint4(idx, tag, (uint32_t)pair_id, (uint32_t)(pair_id >> 32));
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ K.x[r], lo1, hi0 ^ c.w ^ K.y[r], lo0);
+    }
+    return c;
 }
 
 __device__ __forceinline__ float u24f(uint32_t w) { return (float)(w >> 8) * (1.0f / 16777216.0f); }

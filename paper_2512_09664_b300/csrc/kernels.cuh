@@ -17,6 +17,7 @@ struct KernelArgs {
     int64_t n_tiles;                  // (pair, frame, tile) work items
     int64_t n_chunks;                 // particle chunks (kChunk particles of one pair)
     uint64_t seed;
+    PhiloxKeys keys;                  // round keys of seed
     float dt;
     int32_t n_substeps;
     int32_t integrator;

@@ -121,8 +121,8 @@ __device__ __forceinline__ Seeded seed_particle(const KernelArgs &a, const synth
                                                 int64_t g) {
     Seeded P;
     const int32_t H = D.height, W = D.width;
-    const uint4 wa = stream_words(a.seed, D.pair_id, i, kTagAttrA);
-    const uint4 wb = stream_words(a.seed, D.pair_id, i, kTagAttrB);
+    const uint4 wa = stream_words(a.keys, D.pair_id, i, kTagAttrA);
+    const uint4 wb = stream_words(a.keys, D.pair_id, i, kTagAttrB);
     float d;
     if (a.particles_in) {
         const float x0 = a.particles_in[3 * g], y0 = a.particles_in[3 * g + 1];

@@ -97,6 +97,7 @@ struct Geo {
     int32_t EW, EH;              // its width and height (accumulator pitch EW)
     int32_t R;                   // blur radius = halo
     int32_t FW, FH;              // full halo rectangle (replicated outside the frame)
+    int32_t AP;                  // row pitch of the finishing buffer A (FW rounded up to 4)
 };
 
 // ---------------------------------------------------------------------------
@@ -115,12 +116,22 @@ __device__ __forceinline__ float phi_tail(float a, const float4 *tab) {
     return fmaf(fmaf(fmaf(c.w, s, c.z), s, c.y), s, c.x);
 }
 
-// Edge value of a pixel edge at offset dd (edge - particle centre, pixels):
-// Phi(t) for t = dd / sigma <= 0, -(1 - Phi(t)) for t > 0 (tails keep their
-// absolute accuracy; pixel_mass adds the 1 back across the centre).
+// Edge value of a pixel edge at offset dd = edge - particle centre (pixels):
+// the lower tail Phi(t), t = dd / sigma, for dd < 0, and minus the upper tail
+// -(1 - Phi(t)) for dd >= +0, so both tails keep their absolute accuracy.
+// Q never reaches 0 on the table (Q(8) > 0), so the sign bit of the value
+// tells the side of the centre.
 __device__ __forceinline__ float edge_value_tab(float dd, float inv, const float4 *tab) {
     const float q = phi_tail(fabsf(__fmul_rn(dd, inv)), tab);
-    return dd > 0.0f ? -q : q;
+    return __int_as_float(__float_as_int(q) ^ (~__float_as_int(dd) & (int)0x80000000));
+}
+
+// Mass of the unit Gaussian between two pixel edges from their edge values:
+// Phi(b) - Phi(a) = sb - sa, plus 1 when the centre lies between them (sa on
+// the lower side, sb on the upper side).
+__device__ __forceinline__ float edge_mass(float sa, float sb) {
+    const int across = (__float_as_int(sb) & ~__float_as_int(sa)) >> 31;  // -1 or 0
+    return fmaxf(__fadd_rn(__fsub_rn(sb, sa), __int_as_float(across & 0x3F800000)), 0.0f);
 }
 
 // One particle's visit of a tile, set up for the splat (same size as a
@@ -139,64 +150,67 @@ __device__ __forceinline__ int visit_by(uint32_t s) { return (int)(int8_t)((s >>
 __device__ __forceinline__ int visit_nx(uint32_t s) { return (int)((s >> 16) & 0xFFu); }
 __device__ __forceinline__ int visit_ny(uint32_t s) { return (int)(s >> 24); }
 
-// Visits are sorted by (class, accumulator bank) before the splat: class c < 8
-// holds windows of at most N = 2 (c + 1) pixels a side, rendered by
-// splat_narrow<N> in units of at most kUnitRows[c] rows, one unit per lane
-// (a visit of class c is kUnits[c] units, the x edges evaluated by each); class
-// 8 holds the wider ones, rendered by a whole warp per visit.  Lanes of a
-// narrow warp take visits spread over the bank order, so their accumulator
+// Visits are sorted by (class, accumulator bank) before the splat.  Class
+// c < 8 holds windows of at most N = 2 (c + 1) pixels a side; each is
+// rendered by a group of U = class_lanes(c) adjacent lanes (splat_group):
+// the lanes share the N + 1 x edges and take RG = class_rows(c) rows each.
+// Class 8 holds the wider windows, rendered by a whole warp per visit.  The
+// visits of one warp are spread over the bank order, so their accumulator
 // addresses fall in different banks.
 constexpr int kNarrowMax = 16;
 constexpr int kWideClass = kNarrowMax / 2;
 constexpr int kBuckets = (kWideClass + 1) * 32;
-__host__ __device__ constexpr int unit_rows(int c) { return c == 0 ? 2 : (c == 2 ? 3 : 4); }
-__host__ __device__ constexpr int units_of(int c) { return (2 * (c + 1) + unit_rows(c) - 1) / unit_rows(c); }
+__host__ __device__ constexpr int class_lanes(int c) { return c < 2 ? 1 : (c < 4 ? 2 : 4); }
+__host__ __device__ constexpr int class_rows(int c) { return c == 0 ? 2 : (c == 2 || c == 4 || c == 5 ? 3 : 4); }
 
 // Quotient of small non-negative integers a / b (a < 2^20, 1 <= b <= 2^10)
 // from b's reciprocal: (a + 1/2) / b is at least 1/(2b) away from an integer,
 // far more than the rounding error of the product.
 __device__ __forceinline__ int small_div(int a, float inv_b) { return (int)(((float)a + 0.5f) * inv_b); }
 
-// One visit per lane, window at most N x N: the x masses in registers, then
-// the rows (ny_max: the warp's largest ny), each with one new y edge.
-template <int N>
-__device__ __forceinline__ void splat_narrow(const Visit &v, int ny_max, int EW, int32_t *hi, int32_t *lo,
-                                             const float4 *tab) {
+// One visit per group of U lanes, window at most N x N.  Lane j of the group
+// evaluates the x edges e = j + U k and the masses that start there; the
+// group exchanges them by shuffles, then lane j renders rows
+// [j RG, j RG + RG) of the window.  All lanes of the warp take part (the
+// shuffles); lanes of an empty visit add nothing.
+template <int N, int U, int RG>
+__device__ __forceinline__ void splat_group(const Visit &v, int EW, int32_t *hi, int32_t *lo, const float4 *tab) {
+    static_assert(U * RG >= N, "rows of a window");
+    constexpr int EPL = (N + U) / U;  // ceil((N + 1) / U) x edges per lane
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, j = lane & (U - 1), gbase = lane & ~(U - 1);
     const int nx = visit_nx(v.shape), ny = visit_ny(v.shape);
-    const float fbx = (float)visit_bx(v.shape), fby = (float)visit_by(v.shape);
-    float mx[N];
-    float ea;
-    bool pa;
-    {
-        const float dd = __fsub_rn(fbx, v.px);
-        pa = dd > 0.0f;
-        ea = edge_value_tab(dd, v.inv, tab);
-    }
+    const float fbx = (float)(visit_bx(v.shape) + j);
+    float ev[EPL];
 #pragma unroll
-    for (int e = 0; e < N; ++e) {
-        const float dd = __fsub_rn(__fadd_rn(fbx, (float)(e + 1)), v.px);
-        const bool pb = dd > 0.0f;
-        const float eb = edge_value_tab(dd, v.inv, tab);
-        mx[e] = pixel_mass(ea, eb, pa, pb);
-        ea = eb;
-        pa = pb;
+    for (int k = 0; k < EPL; ++k) ev[k] = edge_value_tab(__fsub_rn(__fadd_rn(fbx, (float)(U * k)), v.px), v.inv, tab);
+    float m[EPL];
+#pragma unroll
+    for (int k = 0; k < EPL; ++k) {
+        float nb;
+        if (U == 1) {
+            nb = ev[k + 1 < EPL ? k + 1 : k];
+        } else {
+            const float a = __shfl_sync(FULL, ev[k], lane + 1);                  // edge e + 1 of lanes j < U - 1
+            const float b = __shfl_sync(FULL, ev[k + 1 < EPL ? k + 1 : k], gbase);  // of lane U - 1
+            nb = j == U - 1 ? b : a;
+        }
+        m[k] = edge_mass(ev[k], nb);
     }
-    {
-        const float dd = __fsub_rn(fby, v.py);
-        pa = dd > 0.0f;
-        ea = edge_value_tab(dd, v.inv, tab);
-    }
-    int32_t *hr = hi + v.base, *lr = lo + v.base;
-    float fr = fby;
-    for (int r = 0; r < ny_max; ++r) {
-        fr = __fadd_rn(fr, 1.0f);
-        const float dd = __fsub_rn(fr, v.py);
-        const bool pb = dd > 0.0f;
-        const float eb = edge_value_tab(dd, v.inv, tab);
-        const float my = __fmul_rn(pixel_mass(ea, eb, pa, pb), v.amps);
-        ea = eb;
-        pa = pb;
-        if (r < ny) {
+    float mx[N];
+#pragma unroll
+    for (int e = 0; e < N; ++e) mx[e] = U == 1 ? m[e] : __shfl_sync(FULL, m[e / U], gbase + e % U);
+    const int r0 = j * RG;
+    const int rows = min(max(ny - r0, 0), RG);
+    const float fby = (float)(visit_by(v.shape) + r0);
+    float ey = edge_value_tab(__fsub_rn(fby, v.py), v.inv, tab);
+    int32_t *hr = hi + v.base + r0 * EW, *lr = lo + v.base + r0 * EW;
+#pragma unroll 1  // a rolled row loop keeps the class templates small enough for the instruction cache
+    for (int q = 0; q < RG; ++q) {
+        const float en = edge_value_tab(__fsub_rn(__fadd_rn(fby, (float)(q + 1)), v.py), v.inv, tab);
+        const float my = __fmul_rn(edge_mass(ey, en), v.amps);
+        ey = en;
+        if (q < rows) {
 #pragma unroll
             for (int c = 0; c < N; ++c)
                 if (c < nx) add_fixed(hr + c, lr + c, mx[c], my);
@@ -215,10 +229,8 @@ __device__ __noinline__ void splat_particle_wide(int EW, int32_t *hi, int32_t *l
     for (int e = lane; e <= nx; e += 32) exe[e] = edge_value_tab(__fsub_rn((float)(bx + e), px), inv, tab);
     for (int e = lane; e <= ny; e += 32) eye[e] = edge_value_tab(__fsub_rn((float)(by + e), py), inv, tab);
     __syncwarp();
-    for (int e = lane; e < nx; e += 32)
-        ex[e] = pixel_mass(exe[e], exe[e + 1], (float)(bx + e) > px, (float)(bx + e + 1) > px);
-    for (int e = lane; e < ny; e += 32)
-        ey[e] = __fmul_rn(pixel_mass(eye[e], eye[e + 1], (float)(by + e) > py, (float)(by + e + 1) > py), amps);
+    for (int e = lane; e < nx; e += 32) ex[e] = edge_mass(exe[e], exe[e + 1]);
+    for (int e = lane; e < ny; e += 32) ey[e] = __fmul_rn(edge_mass(eye[e], eye[e + 1]), amps);
     __syncwarp();
     const int n = nx * ny;
     const float invx = 1.0f / (float)nx;
@@ -257,11 +269,9 @@ __device__ __forceinline__ void splat_coop(const Visit &v, bool valid, int EW, i
         const bool isx = lane < nxe;
         const int e = isx ? lane : lane - nxe;
         const float dd = __fsub_rn((float)((isx ? bx : by) + e), isx ? px : py);
-        const bool dpos = dd > 0.0f;
         const float ev = lane < nxe + ny + 1 ? edge_value_tab(dd, inv, tab) : 0.0f;
         const float evn = __shfl_down_sync(FULL, ev, 1);
-        const bool dposn = __shfl_down_sync(FULL, (int)dpos, 1) != 0;
-        float m = pixel_mass(ev, evn, dpos, dposn);
+        float m = edge_mass(ev, evn);
         if (!isx) m = __fmul_rn(m, amps);
         // lane -> (row offset lr, column lc); rpr rows per round
         const float invn = __frcp_rn((float)nx);
@@ -379,24 +389,15 @@ __device__ __forceinline__ void splat_chunk(const unsigned char *recs, unsigned 
         for (; c >= 0; --c) {
             g0 = ss.off[32 * c];
             G = ss.off[32 * c + 32] - g0;
-            nw = (G * (c == kWideClass ? 1u : (uint32_t)units_of(c)) + 31) >> 5;
+            const uint32_t per = c == kWideClass ? 32u : 32u / (uint32_t)class_lanes(c);  // visits per slot
+            nw = (G + per - 1) / per;
             if (sl < nw) break;
             sl -= nw;
         }
         if (c < 0) break;
-        uint32_t idx;
-        int r0 = 0;
-        if (c == kWideClass) {
-            idx = sl * 32 + lane;
-        } else {
-            // unit i = u * G + visit: rows [u R, u R + R) of the visit
-            const uint32_t i = sl + lane * nw;
-            const int u = i < G * (uint32_t)units_of(c) ? small_div((int)i, 1.0f / (float)G) : units_of(c);
-            idx = i - (uint32_t)u * G;
-            r0 = u * unit_rows(c);
-            if (u >= units_of(c)) idx = G;
-        }
-        bool valid = idx < G;
+        // wide: visits 32 sl + lane; narrow: group q of U lanes takes visit sl + q nw (spread over the bank order)
+        const uint32_t idx = c == kWideClass ? sl * 32 + lane : sl + (uint32_t)(lane / class_lanes(c)) * nw;
+        const bool valid = idx < G;
         Visit e;
         if (valid) {
             const float2 a = o8[3 * (g0 + idx)], b = o8[3 * (g0 + idx) + 1], d = o8[3 * (g0 + idx) + 2];
@@ -406,32 +407,21 @@ __device__ __forceinline__ void splat_chunk(const unsigned char *recs, unsigned 
             e.amps = b.y;
             e.base = __float_as_int(d.x);
             e.shape = __float_as_uint(d.y);
-            if (c != kWideClass) {
-                const int rows = min(visit_ny(e.shape) - r0, unit_rows(c));
-                valid = rows > 0;
-                e.base += r0 * g.EW;
-                e.shape = (e.shape & 0x00FF00FFu) | ((uint32_t)((visit_by(e.shape) + r0) & 0xFF) << 8) |
-                          ((uint32_t)max(rows, 0) << 24);
-            }
         } else {
             e.px = e.py = e.inv = e.amps = 0.0f;
             e.base = 0;
             e.shape = 0;
         }
-        if (c == kWideClass) {
-            splat_coop(e, valid, g.EW, hi, lo, scr, wq, tab);
-            continue;
-        }
-        const int ny_max = (int)__reduce_max_sync(FULL, (unsigned)visit_ny(e.shape));
         switch (c) {
-        case 0: splat_narrow<2>(e, ny_max, g.EW, hi, lo, tab); break;
-        case 1: splat_narrow<4>(e, ny_max, g.EW, hi, lo, tab); break;
-        case 2: splat_narrow<6>(e, ny_max, g.EW, hi, lo, tab); break;
-        case 3: splat_narrow<8>(e, ny_max, g.EW, hi, lo, tab); break;
-        case 4: splat_narrow<10>(e, ny_max, g.EW, hi, lo, tab); break;
-        case 5: splat_narrow<12>(e, ny_max, g.EW, hi, lo, tab); break;
-        case 6: splat_narrow<14>(e, ny_max, g.EW, hi, lo, tab); break;
-        default: splat_narrow<16>(e, ny_max, g.EW, hi, lo, tab); break;
+        case 0: splat_group<2, class_lanes(0), class_rows(0)>(e, g.EW, hi, lo, tab); break;
+        case 1: splat_group<4, class_lanes(1), class_rows(1)>(e, g.EW, hi, lo, tab); break;
+        case 2: splat_group<6, class_lanes(2), class_rows(2)>(e, g.EW, hi, lo, tab); break;
+        case 3: splat_group<8, class_lanes(3), class_rows(3)>(e, g.EW, hi, lo, tab); break;
+        case 4: splat_group<10, class_lanes(4), class_rows(4)>(e, g.EW, hi, lo, tab); break;
+        case 5: splat_group<12, class_lanes(5), class_rows(5)>(e, g.EW, hi, lo, tab); break;
+        case 6: splat_group<14, class_lanes(6), class_rows(6)>(e, g.EW, hi, lo, tab); break;
+        case 7: splat_group<16, class_lanes(7), class_rows(7)>(e, g.EW, hi, lo, tab); break;
+        default: splat_coop(e, valid, g.EW, hi, lo, scr, wq, tab); break;
         }
     }
 }
@@ -525,12 +515,20 @@ __device__ __forceinline__ void blur_store(const Geo &g, const float *A, float *
     float wr[R + 1];
 #pragma unroll
     for (int k = 0; k <= R; ++k) wr[k] = w[k];
+    constexpr int NV = (4 + 2 * R + 3) / 4;  // float4 loads covering the 4 + 2R inputs
     for (int it = threadIdx.x; it < g.FH * G; it += blockDim.x) {
         const int r = small_div(it, iG), c0 = (it - r * G) * 4;
-        const float *row = A + r * g.FW;
-        float v[4 + 2 * R];
+        // 16-byte aligned (AP and c0 multiples of 4); inputs past FW feed only outputs past the tile
+        const float4 *row = reinterpret_cast<const float4 *>(A + r * g.AP + c0);
+        float v[4 * NV];
 #pragma unroll
-        for (int k = 0; k < 4 + 2 * R; ++k) v[k] = row[min(c0 + k, g.FW - 1)];
+        for (int q = 0; q < NV; ++q) {
+            const float4 t = row[q];
+            v[4 * q] = t.x;
+            v[4 * q + 1] = t.y;
+            v[4 * q + 2] = t.z;
+            v[4 * q + 3] = t.w;
+        }
         float4 o;
         float *op = &o.x;
 #pragma unroll
@@ -568,7 +566,7 @@ __device__ __noinline__ void blur_store_any(const Geo &g, const float *A, float 
     const int R = g.R, TW = g.x1 - g.x0, TH = g.y1 - g.y0;
     for (int it = threadIdx.x; it < g.FH * TW; it += blockDim.x) {
         const int r = it / TW, c = it - r * TW;
-        const float *row = A + r * g.FW + c + R;
+        const float *row = A + r * g.AP + c + R;
         float acc = w[0] * row[0];
         for (int k = 1; k <= R; ++k) acc = fmaf(w[k], row[-k] + row[k], acc);
         Bh[r * BP + c] = acc;
@@ -592,7 +590,7 @@ __device__ __forceinline__ void store_unblurred(const Geo &g, const float *A, T 
         const int r = it / G, c0 = (it - r * G) * 4;
         float v[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) v[j] = A[r * g.FW + min(c0 + j, g.FW - 1)];
+        for (int j = 0; j < 4; ++j) v[j] = A[r * g.AP + min(c0 + j, g.FW - 1)];
         store_group<T>(out + r * g.W + c0, v, min(4, TW - c0), M);
     }
 }
@@ -626,6 +624,7 @@ __device__ __forceinline__ Geo make_geo(const synthpix_pair_desc &D, const PairP
     g.EW = g.ex1 - g.ex0;
     g.EH = g.ey1 - g.ey0;
     g.FW = (g.x1 - g.x0) + 2 * g.R;
+    g.AP = (g.FW + 3) & ~3;
     g.FH = (g.y1 - g.y0) + 2 * g.R;
     return g;
 }
@@ -662,14 +661,14 @@ __device__ __forceinline__ void finish_tile(const KernelArgs &a, const Geo &g, c
         const int nq = (g.EW + 6) / 4 + 1;
         const float inq = 1.0f / (float)nq;
         const uint32_t tag = kTagNoise + (uint32_t)frame;
-        const int fpitch = g.FW;
+        const int fpitch = g.AP;
         float *Abase = s.A + (g.ey0 - fy0) * fpitch + (g.ex0 - fx0);
         for (int item = threadIdx.x; item < g.EH * nq; item += blockDim.x) {
             const int r = small_div(item, inq), qi = item - r * nq;
             const int rowlin = (g.ey0 + r) * g.W;
             const int p0 = (((rowlin + g.ex0) >> 2) + qi) << 2;
             if (p0 > rowlin + g.ex1 - 1) continue;
-            const uint4 w = stream_words(a.seed, D.pair_id, (uint32_t)(p0 >> 2), tag);
+            const uint4 w = stream_words(a.keys, D.pair_id, (uint32_t)(p0 >> 2), tag);
             float nv[4];
             box_muller(w.x, w.y, nv[0], nv[1]);
             box_muller(w.z, w.w, nv[2], nv[3]);
@@ -691,7 +690,7 @@ __device__ __forceinline__ void finish_tile(const KernelArgs &a, const Geo &g, c
             const int r = small_div(idx, iew), c = idx - r * g.EW;
             const float S = src(idx, r, c);
             const float L = illum ? fmaf(dl, s.sx2[c] * s.sy2[r], D.illum_min) : 1.0f;
-            s.A[(g.ey0 + r - fy0) * g.FW + (g.ex0 + c - fx0)] = L * S;
+            s.A[(g.ey0 + r - fy0) * g.AP + (g.ex0 + c - fx0)] = L * S;
         }
     }
     __syncthreads();
@@ -703,7 +702,7 @@ __device__ __forceinline__ void finish_tile(const KernelArgs &a, const Geo &g, c
             const int gi = fy0 + r, gj = fx0 + c;
             if (gi < 0 || gi >= g.H || gj < 0 || gj >= g.W) {
                 const int ci = min(max(gi, 0), g.H - 1) - fy0, cj = min(max(gj, 0), g.W - 1) - fx0;
-                s.A[k] = s.A[ci * g.FW + cj];
+                s.A[r * g.AP + c] = s.A[ci * g.AP + cj];
             }
         }
     }
@@ -810,7 +809,7 @@ __host__ __device__ inline SmemLayout smem_layout(int E, int tile, int warp_scra
     };
     L.hi = take((size_t)E * E * 4);
     L.lo = take((size_t)E * E * 4);
-    L.A = take((size_t)E * E * 4);
+    L.A = take(((size_t)E * (size_t)((E + 3) & ~3) + 16) * 4);
     L.Bh = take((size_t)E * BP * 4);
     L.sx2 = take((size_t)E * 4);
     L.sy2 = take((size_t)E * 4);
@@ -911,7 +910,7 @@ __host__ __device__ inline FinishLayout finish_layout(int E, int tile) {
         o = (o + bytes + 15) & ~(size_t)15;
         return at;
     };
-    L.A = take((size_t)E * E * 4);
+    L.A = take(((size_t)E * (size_t)((E + 3) & ~3) + 16) * 4);
     L.Bh = take((size_t)E * BP * 4);
     L.sx2 = take((size_t)E * 4);
     L.sy2 = take((size_t)E * 4);
