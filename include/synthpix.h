@@ -59,6 +59,10 @@ extern "C" {
 #define SYNTHPIX_RK4   0
 #define SYNTHPIX_EULER 1
 
+/* batch flags */
+#define SYNTHPIX_FLAG_GATHER_ADVECT 1  /* advect every particle by direct flow-grid gathers
+                                          instead of the tiled advection (same result)  */
+
 /*
  * Per-pair acquisition parameters (Abstract: seeding density, particle image
  * size, illumination non-uniformity, noise, blur, timing; Section 2 "Sampling
@@ -109,7 +113,12 @@ typedef struct synthpix_batch_desc {
     int32_t  tile;               /* square screen tile edge: 16, 32 or 64, or 0 for a
                                     default from the frame sizes (64 when the mean
                                     frame area is >= 256x256, else 32)                 */
-    int32_t  flags;              /* must be 0                                          */
+    int32_t  flags;              /* 0 or SYNTHPIX_FLAG_GATHER_ADVECT.  By default a
+                                    seeded render advects the particles tile by tile:
+                                    the flow nodes under each frame-1 tile are staged
+                                    on chip with coalesced loads.  Renders from given
+                                    particles and the adjoint always gather per
+                                    particle.  Both give the same positions.          */
     int32_t  reserved[6];        /* must be zero                                       */
 } synthpix_batch_desc;
 

@@ -19,6 +19,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libsynthpix.so")
 
 OK, EINVAL, EWORKSPACE, ECUDA, EUNSUPPORTED = 0, -1, -2, -3, -4
+FLAG_GATHER_ADVECT = 1  # advect per particle by direct flow gathers (default: tiled advection)
 DTYPE_CODE = {"f32": 0, "f16": 1, "bf16": 2, "u8": 3, "u16": 4}
 INTEGRATOR_CODE = {"rk4": 0, "euler": 1}
 _EXPORTS = ("synthpix_workspace_bytes", "synthpix_render_pairs", "synthpix_render_pairs_staged",
@@ -222,9 +223,10 @@ class Renderer:
     """Device buffers for repeated rendering of one packed workload."""
 
     def __init__(self, wl, device="cuda", tile: int = 0, out_dtype=None, inter_dtype=None,
-                 device_descriptors: bool = True):
+                 device_descriptors: bool = True, flags: int = 0):
         import torch
         self.pk = pack(wl, tile=tile, out_dtype=out_dtype, inter_dtype=inter_dtype)
+        self.pk.batch.flags = flags
         self.device = torch.device(device)
         self.flows = torch.from_numpy(self.pk.flows_host).to(self.device)
         ws = workspace_bytes(self.pk)

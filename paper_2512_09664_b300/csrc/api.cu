@@ -51,7 +51,8 @@ int check_batch(const synthpix_batch_desc *b) {
     if (!finite(b->dt) || std::fabs(b->dt) > 64.0f) return fail(SYNTHPIX_EINVAL, "dt must be finite with |dt| <= 64");
     if (b->tile != 0 && b->tile != 16 && b->tile != 32 && b->tile != 64)
         return fail(SYNTHPIX_EINVAL, "tile %d is not 0, 16, 32 or 64", b->tile);
-    if (b->flags != 0) return fail(SYNTHPIX_EUNSUPPORTED, "flags must be 0 (got 0x%x)", b->flags);
+    if (b->flags & ~SYNTHPIX_FLAG_GATHER_ADVECT)
+        return fail(SYNTHPIX_EUNSUPPORTED, "unknown flags 0x%x", b->flags);
     for (int k = 0; k < 6; ++k)
         if (b->reserved[k] != 0) return fail(SYNTHPIX_EUNSUPPORTED, "batch reserved[%d] is not zero", k);
     return SYNTHPIX_OK;
@@ -149,6 +150,7 @@ int make_plan_tile(const synthpix_batch_desc *batch, const synthpix_pair_desc *p
     L.pos = take((size_t)L.n_part * 32);
     L.sa = take((size_t)L.n_part * 8);
     L.rec = take((size_t)L.n_list * sizeof(spx::Record) + 64);  // + read-over of 16-byte staging
+    L.adv = take((size_t)(L.n_list / 2) * sizeof(spx::Record));  // frame-1 segments only
     L.inter = take((size_t)L.n_inter * 2);
     L.gfr = take((size_t)L.n_part * 2 * sizeof(float4));
     L.total = o;
@@ -291,6 +293,8 @@ static int run(Mode mode, const synthpix_batch_desc *batch, const synthpix_pair_
     a.cursor = reinterpret_cast<uint32_t *>(ws + L.cursor);
     a.items = reinterpret_cast<spx::ItemInfo *>(ws + L.items);
     a.rec = reinterpret_cast<spx::Record *>(ws + L.rec);
+    a.adv = reinterpret_cast<spx::Record *>(ws + L.adv);
+    a.tiled = (mode == Mode::Render && !x.particles_in && !(batch->flags & SYNTHPIX_FLAG_GATHER_ADVECT)) ? 1 : 0;
     a.ticket = ticket;
     a.rec_buf_bytes = spx::kRecBufBytes;
     a.blur_w = blur_w;

@@ -81,7 +81,7 @@ static_assert(sizeof(ItemInfo) == 24, "ItemInfo layout");
 
 // Workspace layout (byte offsets, 256-aligned), computed on the host.
 struct Layout {
-    size_t plan, desc, check, blur, count, off, cursor, items, pos, sa, rec, inter, gfr, total;
+    size_t plan, desc, check, blur, count, off, cursor, items, pos, sa, rec, adv, inter, gfr, total;
     int64_t n_part, n_tiles, n_list, n_inter, n_chunks;
 };
 

@@ -29,6 +29,8 @@ struct KernelArgs {
     uint32_t *count, *off, *cursor;   // per (pair, frame, tile)
     ItemInfo *items;                  // per (pair, frame, tile): the splat's work items
     Record *rec;                      // bins
+    Record *adv;                      // tiled advection: frame-2 records by frame-1 bin slot (sigma < 0: none)
+    int32_t tiled;                    // 1: frame 2 comes from the tiled advection (k_advect), not k_seed_advect
     uint32_t *ticket;                 // work-queue counter of the persistent splat
     int32_t smem_edge;                // capacity edge of the on-chip tile (tile + 2 max radius)
     int32_t warp_scratch;             // floats of per-warp window scratch

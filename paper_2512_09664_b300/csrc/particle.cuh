@@ -167,24 +167,62 @@ __device__ __forceinline__ Flow pair_flow(const KernelArgs &a, const synthpix_pa
     return F;
 }
 
-// Frame-2 position: n substeps of RK4 (or Euler) over dt, on split coordinates.
-__device__ __forceinline__ void advect_split(const Flow &F, float dt, int n_substeps, int integrator, int32_t &jx,
-                                             float &gx, int32_t &jy, float &gy) {
+// Frame-2 position: n substeps of RK4 (or Euler) over dt, on split
+// coordinates; vel(ix, fx, iy, fy) is the bilinear velocity.
+template <typename Vel>
+__device__ __forceinline__ void advect_split_with(Vel vel, float dt, int n_substeps, int integrator, int32_t &jx,
+                                                  float &gx, int32_t &jy, float &gy) {
     const float h = dt / (float)n_substeps;
     const float hh = 0.5f * h, h6 = h / 6.0f;
     for (int s = 0; s < n_substeps; ++s) {
-        const float2 k1 = velocity(F, jx, gx, jy, gy);
+        const float2 k1 = vel(jx, gx, jy, gy);
         if (integrator == SYNTHPIX_EULER) {
             split_add(jx, gx, __fmul_rn(h, k1.x));
             split_add(jy, gy, __fmul_rn(h, k1.y));
             continue;
         }
-        const float2 k2 = velocity(F, jx, fmaf(hh, k1.x, gx), jy, fmaf(hh, k1.y, gy));
-        const float2 k3 = velocity(F, jx, fmaf(hh, k2.x, gx), jy, fmaf(hh, k2.y, gy));
-        const float2 k4 = velocity(F, jx, fmaf(h, k3.x, gx), jy, fmaf(h, k3.y, gy));
+        const float2 k2 = vel(jx, fmaf(hh, k1.x, gx), jy, fmaf(hh, k1.y, gy));
+        const float2 k3 = vel(jx, fmaf(hh, k2.x, gx), jy, fmaf(hh, k2.y, gy));
+        const float2 k4 = vel(jx, fmaf(h, k3.x, gx), jy, fmaf(h, k3.y, gy));
         split_add(jx, gx, __fmul_rn(h6, (k1.x + k4.x) + 2.0f * (k2.x + k3.x)));
         split_add(jy, gy, __fmul_rn(h6, (k1.y + k4.y) + 2.0f * (k2.y + k3.y)));
     }
+}
+
+__device__ __forceinline__ void advect_split(const Flow &F, float dt, int n_substeps, int integrator, int32_t &jx,
+                                             float &gx, int32_t &jy, float &gy) {
+    advect_split_with([&](int32_t ix, float fx, int32_t iy, float fy) { return velocity(F, ix, fx, iy, fy); }, dt,
+                      n_substeps, integrator, jx, gx, jy, gy);
+}
+
+// A block of flow-grid nodes [gx0, gx0 + nw) x [gy0, gy0 + nh) staged in
+// shared memory.  The bilinear velocity reads the four corners from it when
+// all lie inside, else from global memory: the same nodes and arithmetic as
+// velocity(), so the result is identical.
+struct FlowWindow {
+    const float2 *s;
+    int32_t gx0, gy0, nw, nh;
+};
+
+__device__ __forceinline__ float2 velocity_windowed(const Flow &F, const FlowWindow &Wn, int32_t ix, float fx,
+                                                    int32_t iy, float fy) {
+    int32_t l, k;
+    float tx, ty;
+    grid_coord(ix, fx, F.gw, F.W, l, tx);
+    grid_coord(iy, fy, F.gh, F.H, k, ty);
+    const int32_t l0 = min(max(l, 0), F.gw - 1), l1 = min(max(l + 1, 0), F.gw - 1);
+    const int32_t k0 = min(max(k, 0), F.gh - 1), k1 = min(max(k + 1, 0), F.gh - 1);
+    const int32_t u0 = l0 - Wn.gx0, u1 = l1 - Wn.gx0, v0 = k0 - Wn.gy0, v1 = k1 - Wn.gy0;
+    const bool in = (unsigned)u0 < (unsigned)Wn.nw && (unsigned)u1 < (unsigned)Wn.nw &&
+                    (unsigned)v0 < (unsigned)Wn.nh && (unsigned)v1 < (unsigned)Wn.nh;
+    // per-lane generic pointers (shared window or global grid): no divergent branch
+    const float2 *r0 = in ? Wn.s + v0 * Wn.nw : F.f + (size_t)k0 * F.gw;
+    const float2 *r1 = in ? Wn.s + v1 * Wn.nw : F.f + (size_t)k1 * F.gw;
+    const int32_t c0 = in ? u0 : l0, c1 = in ? u1 : l1;
+    const float2 a = r0[c0], b = r0[c1], c = r1[c0], d = r1[c1];
+    const float tu = fmaf(tx, b.x - a.x, a.x), tv = fmaf(tx, b.y - a.y, a.y);
+    const float bu = fmaf(tx, d.x - c.x, c.x), bv = fmaf(tx, d.y - c.y, c.y);
+    return make_float2(fmaf(ty, bu - tu, tu), fmaf(ty, bv - tv, tv));
 }
 
 }  // namespace spx

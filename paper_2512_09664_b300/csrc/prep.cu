@@ -186,17 +186,18 @@ __global__ void __launch_bounds__(kPrepThreads, 5) k_seed_advect(KernelArgs a) {
             a.particles_out[3 * g + 2] = 4.0f * P.sigma;
             continue;
         }
+        const float r15 = 6.0f * P.sigma;  // 1.5 d
+        if (counting)
+            count_window(a, c, particle_window(P.ix, P.fx, P.iy, P.fy, r15, c.d.width, c.d.height), 0,
+                         local ? hist : nullptr);
+        if (a.tiled) continue;  // frame 2 from k_advect
         int32_t jx = P.ix, jy = P.iy;
         float gx = P.fx, gy = P.fy;
         advect_split(F, a.dt, a.n_substeps, a.integrator, jx, gx, jy, gy);
         a.pos1[g] = make_float4(gx, gy, __int_as_float(jx), __int_as_float(jy));
-        if (counting) {
-            const float r15 = 6.0f * P.sigma;  // 1.5 d
-            count_window(a, c, particle_window(P.ix, P.fx, P.iy, P.fy, r15, c.d.width, c.d.height), 0,
-                         local ? hist : nullptr);
+        if (counting)
             count_window(a, c, particle_window(jx, gx, jy, gy, r15, c.d.width, c.d.height), 1,
                          local ? hist : nullptr);
-        }
     }
     if (local) {
         __syncthreads();
@@ -208,11 +209,12 @@ __global__ void __launch_bounds__(kPrepThreads, 5) k_seed_advect(KernelArgs a) {
 // ---------------------------------------------------------------------------
 // k_scan: exclusive scan of the bin counts of one (pair, frame) per CTA
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_scan(KernelArgs a) {
+__global__ void __launch_bounds__(1024) k_scan(KernelArgs a, int frame) {
     if (*a.check != 1) return;
     __shared__ uint32_t s[1024];
     __shared__ uint32_t carry;
-    const int b = blockIdx.x >> 1, f = blockIdx.x & 1;
+    const int b = frame < 0 ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+    const int f = frame < 0 ? (int)(blockIdx.x & 1) : frame;
     const PairPlan pl = a.plan[b];
     const int64_t base = pl.tile_base + (int64_t)f * pl.ntiles;
     if (threadIdx.x == 0) carry = 0;
@@ -255,12 +257,12 @@ __global__ void __launch_bounds__(1024) k_scan(KernelArgs a) {
 // each tile's range with one global atomic, then place the records.
 // ---------------------------------------------------------------------------
 template <typename Put>
-__device__ __forceinline__ void chunk_windows(const KernelArgs &a, const ChunkCtx &c, Put put) {
+__device__ __forceinline__ void chunk_windows(const KernelArgs &a, const ChunkCtx &c, int nf, Put put) {
     for (int q = threadIdx.x; q < c.n; q += kPrepThreads) {
         const int64_t g = c.pl.part_base + c.first + q;
         const float2 sa = a.sa[g];
         const float r15 = 6.0f * sa.x;
-        for (int f = 0; f < 2; ++f) {
+        for (int f = 0; f < nf; ++f) {
             const float4 p = f ? a.pos1[g] : a.pos0[g];
             const Window w = particle_window(__float_as_int(p.z), p.x, __float_as_int(p.w), p.y, r15, c.d.width,
                                              c.d.height);
@@ -288,17 +290,18 @@ __global__ void __launch_bounds__(kPrepThreads) k_scatter(KernelArgs a) {
     __shared__ __align__(16) ChunkCtx c;
     __shared__ uint32_t cnt[kHistMax], base[kHistMax];
     load_chunk(a, c);
-    const int nk = 2 * c.pl.ntiles;
+    const int nf = a.tiled ? 1 : 2;  // tiled: frame 2 is placed by k_scatter2
+    const int nk = nf * c.pl.ntiles;
     uint32_t *cursor = a.cursor + c.pl.tile_base;
     if (nk > kHistMax) {
-        chunk_windows(a, c, [&](int f, int k, const float4 &p, const float2 &sa) {
+        chunk_windows(a, c, nf, [&](int f, int k, const float4 &p, const float2 &sa) {
             put_record(a, c, f, atomicAdd(cursor + k, 1u), p, sa);
         });
         return;
     }
     for (int k = threadIdx.x; k < nk; k += kPrepThreads) cnt[k] = 0u;
     __syncthreads();
-    chunk_windows(a, c, [&](int, int k, const float4 &, const float2 &) { atomicAdd(cnt + k, 1u); });
+    chunk_windows(a, c, nf, [&](int, int k, const float4 &, const float2 &) { atomicAdd(cnt + k, 1u); });
     __syncthreads();
     for (int k = threadIdx.x; k < nk; k += kPrepThreads) {
         const uint32_t n = cnt[k];
@@ -306,9 +309,210 @@ __global__ void __launch_bounds__(kPrepThreads) k_scatter(KernelArgs a) {
         cnt[k] = 0u;
     }
     __syncthreads();
-    chunk_windows(a, c, [&](int f, int k, const float4 &p, const float2 &sa) {
+    chunk_windows(a, c, nf, [&](int f, int k, const float4 &p, const float2 &sa) {
         put_record(a, c, f, base[k] + atomicAdd(cnt + k, 1u), p, sa);
     });
+}
+
+// ---------------------------------------------------------------------------
+// Tiled advection (seeded renders): one CTA per frame-1 tile.  The flow-grid
+// nodes under the tile and a margin are staged into shared memory with
+// coalesced 8-byte loads; the tile's home particles (integer position inside
+// the tile, so each particle once) are advected from it, lookups that leave
+// the window read global memory.  Frame-2 records go to adv (by frame-1 bin
+// slot) and frame-2 bin counts are aggregated on chip for tiles near the
+// home tile.  k_scatter2 places them once the frame-2 bins are scanned.
+// ---------------------------------------------------------------------------
+constexpr int kAdvThreads = 256;
+constexpr int kAdvMargin = 2;  // image pixels of flow staged beyond the tile on each side (measured best)
+constexpr int kNbr = 3;        // on-chip counters for frame-2 tiles within +-kNbr of the home tile
+constexpr int kNbrSide = 2 * kNbr + 1;
+constexpr int kAdvBatch = 2048;  // records of a bin examined per pass (home list in shared memory)
+
+__host__ __device__ inline int adv_window_nodes(int tile) { return (tile + 2 * kAdvMargin + 2) * (tile + 2 * kAdvMargin + 2); }
+
+struct TileCtx {
+    int32_t b, t, tx, ty, x0, x1, y0, y1;
+    ItemInfo it;
+    int64_t adv0;  // first adv slot of the tile's frame-1 bin
+};
+
+// The frame-1 tile of this CTA (blockIdx.x over all pairs' frame-1 tiles).
+__device__ __forceinline__ TileCtx frame1_tile(const KernelArgs &a, const PairPlan &pl, int b, int W, int H) {
+    TileCtx c;
+    c.b = b;
+    c.t = (int32_t)blockIdx.x - (pl.tile_base >> 1);
+    c.ty = c.t / pl.tiles_x;
+    c.tx = c.t - c.ty * pl.tiles_x;
+    c.x0 = c.tx * a.tile;
+    c.y0 = c.ty * a.tile;
+    c.x1 = min(c.x0 + a.tile, W);
+    c.y1 = min(c.y0 + a.tile, H);
+    c.it = a.items[pl.tile_base + c.t];
+    c.adv0 = c.it.rec0 - (pl.list_base >> 1);
+    return c;
+}
+
+__device__ __forceinline__ int frame1_pair(const KernelArgs &a) {
+    __shared__ int32_t s_b;
+    if (threadIdx.x == 0)
+        s_b = upper_find(a.n_pairs, (int64_t)blockIdx.x, [&](int m) { return (int64_t)(a.plan[m].tile_base >> 1); });
+    __syncthreads();
+    return s_b;
+}
+
+// Calls put(k, tile) for each frame-2 tile of advected record r; k = index of
+// the on-chip counter, or -1 for a tile beyond the neighbourhood.
+template <typename Put>
+__device__ __forceinline__ void frame2_tiles(const KernelArgs &a, const PairPlan &pl, const TileCtx &c, const Record &r,
+                                             int W, int H, Put put) {
+    const Window w = particle_window(r.ix, r.fx, r.iy, r.fy, 6.0f * r.sigma, W, H);
+    if (w.j0 > w.j1 || w.i0 > w.i1) return;
+    int32_t tx0, tx1, ty0, ty1;
+    window_tiles(w, pl.halo, a.tile, W, H, tx0, tx1, ty0, ty1);
+    for (int32_t ty = ty0; ty <= ty1; ++ty)
+        for (int32_t tx = tx0; tx <= tx1; ++tx) {
+            const int32_t dy = ty - c.ty + kNbr, dx = tx - c.tx + kNbr;
+            const int k = ((unsigned)dy < (unsigned)kNbrSide && (unsigned)dx < (unsigned)kNbrSide) ? dy * kNbrSide + dx : -1;
+            put(k, ty * pl.tiles_x + tx);
+        }
+}
+
+__global__ void __launch_bounds__(kAdvThreads) k_advect(KernelArgs a) {
+    if (*a.check != 1) return;
+    extern __shared__ __align__(16) float2 s_flow[];
+    __shared__ uint32_t s_nb[kNbrSide * kNbrSide];
+    __shared__ uint16_t s_home[kAdvBatch];
+    __shared__ uint32_t s_nhome;
+    const int b = frame1_pair(a);
+    const PairPlan pl = a.plan[b];
+    const synthpix_pair_desc &D = a.descs[b];
+    const int W = D.width, H = D.height;
+    const TileCtx c = frame1_tile(a, pl, b, W, H);
+    const Flow F = pair_flow(a, D);
+    // grid nodes under [x0 - M, x1 + M) x [y0 - M, y1 + M), bilinear neighbours included
+    int32_t l0, l1, k0, k1;
+    float t_;
+    grid_coord(c.x0 - kAdvMargin, 0.0f, F.gw, F.W, l0, t_);
+    grid_coord(c.x1 + kAdvMargin, 0.0f, F.gw, F.W, l1, t_);
+    grid_coord(c.y0 - kAdvMargin, 0.0f, F.gh, F.H, k0, t_);
+    grid_coord(c.y1 + kAdvMargin, 0.0f, F.gh, F.H, k1, t_);
+    FlowWindow Wn;
+    Wn.s = s_flow;
+    Wn.gx0 = min(max(l0, 0), F.gw - 1);
+    Wn.gy0 = min(max(k0, 0), F.gh - 1);
+    Wn.nw = min(max(l1 + 1, 0), F.gw - 1) - Wn.gx0 + 1;
+    Wn.nh = min(max(k1 + 1, 0), F.gh - 1) - Wn.gy0 + 1;
+    if (Wn.nw * Wn.nh > adv_window_nodes(a.tile)) Wn.nw = Wn.nh = 0;  // finer grid than fits: all lookups global
+    for (int i = threadIdx.x; i < kNbrSide * kNbrSide; i += kAdvThreads) s_nb[i] = 0u;
+    // a warp per row: consecutive lanes read consecutive nodes (coalesced 8-byte loads)
+    for (int r = threadIdx.x >> 5; r < Wn.nh; r += kAdvThreads / 32) {
+        const float2 *src = F.f + (size_t)(Wn.gy0 + r) * F.gw + Wn.gx0;
+        for (int q = threadIdx.x & 31; q < Wn.nw; q += 32) s_flow[r * Wn.nw + q] = __ldg(src + q);
+    }
+    uint32_t *cnt2 = a.count + pl.tile_base + pl.ntiles;
+    for (uint32_t base = 0; base < c.it.count; base += kAdvBatch) {
+        // compact this batch's home particles (integer position inside the tile); the others are
+        // advected by their own home tile and marked here
+        if (threadIdx.x == 0) s_nhome = 0u;
+        __syncthreads();
+        for (uint32_t k = base + threadIdx.x; k < min(c.it.count, base + kAdvBatch); k += kAdvThreads) {
+            const int2 ip = reinterpret_cast<const int2 *>(a.rec + c.it.rec0 + k)[1];
+            if (ip.x < c.x0 || ip.x >= c.x1 || ip.y < c.y0 || ip.y >= c.y1)
+                reinterpret_cast<float2 *>(a.adv + c.adv0 + k)[2] = make_float2(-1.0f, 0.0f);
+            else
+                s_home[atomicAdd(&s_nhome, 1u)] = (uint16_t)(k - base);
+        }
+        __syncthreads();
+        for (uint32_t h = threadIdx.x; h < s_nhome; h += kAdvThreads) {
+            const uint32_t k = base + s_home[h];
+            const float2 *rp = reinterpret_cast<const float2 *>(a.rec + c.it.rec0 + k);
+            const float2 p0 = rp[0], p1 = rp[1], p2 = rp[2];
+            float2 *o = reinterpret_cast<float2 *>(a.adv + c.adv0 + k);
+            Record r;
+            r.fx = p0.x;
+            r.fy = p0.y;
+            r.ix = __float_as_int(p1.x);
+            r.iy = __float_as_int(p1.y);
+            r.sigma = p2.x;
+            r.amp = p2.y;
+            advect_split_with(
+                [&](int32_t ix, float fx, int32_t iy, float fy) { return velocity_windowed(F, Wn, ix, fx, iy, fy); },
+                a.dt, a.n_substeps, a.integrator, r.ix, r.fx, r.iy, r.fy);
+            o[0] = make_float2(r.fx, r.fy);
+            o[1] = make_float2(__int_as_float(r.ix), __int_as_float(r.iy));
+            o[2] = make_float2(r.sigma, r.amp);
+            frame2_tiles(a, pl, c, r, W, H, [&](int kk, int32_t tile) {
+                if (kk >= 0) atomicAdd(s_nb + kk, 1u);
+                else atomicAdd(cnt2 + tile, 1u);
+            });
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < kNbrSide * kNbrSide; i += kAdvThreads) {
+        if (!s_nb[i]) continue;
+        const int ty = c.ty + i / kNbrSide - kNbr, tx = c.tx + i % kNbrSide - kNbr;
+        atomicAdd(cnt2 + ty * pl.tiles_x + tx, s_nb[i]);
+    }
+}
+
+// Frame-2 records of the tiled advection into their bins: count per nearby
+// tile on chip, reserve each tile's range with one global atomic, place.
+__global__ void __launch_bounds__(kAdvThreads) k_scatter2(KernelArgs a) {
+    if (*a.check != 1) return;
+    __shared__ uint32_t s_cnt[kNbrSide * kNbrSide], s_base[kNbrSide * kNbrSide];
+    const int b = frame1_pair(a);
+    const PairPlan pl = a.plan[b];
+    const int W = a.descs[b].width, H = a.descs[b].height;
+    const TileCtx c = frame1_tile(a, pl, b, W, H);
+    uint32_t *cur2 = a.cursor + pl.tile_base + pl.ntiles;
+    Record *seg = a.rec + pl.list_base + pl.list_cap;
+    for (int i = threadIdx.x; i < kNbrSide * kNbrSide; i += kAdvThreads) s_cnt[i] = 0u;
+    __syncthreads();
+    auto load = [&](uint32_t k, Record &r) {
+        const float2 *rp = reinterpret_cast<const float2 *>(a.adv + c.adv0 + k);
+        const float2 p2 = rp[2];
+        if (p2.x < 0.0f) return false;
+        const float2 p0 = rp[0], p1 = rp[1];
+        r.fx = p0.x;
+        r.fy = p0.y;
+        r.ix = __float_as_int(p1.x);
+        r.iy = __float_as_int(p1.y);
+        r.sigma = p2.x;
+        r.amp = p2.y;
+        return true;
+    };
+    auto place = [&](uint32_t slot, const Record &r) {
+        if ((int64_t)slot < pl.list_cap) {
+            float2 *o = reinterpret_cast<float2 *>(seg + slot);
+            o[0] = make_float2(r.fx, r.fy);
+            o[1] = make_float2(__int_as_float(r.ix), __int_as_float(r.iy));
+            o[2] = make_float2(r.sigma, r.amp);
+        }
+    };
+    for (uint32_t k = threadIdx.x; k < c.it.count; k += kAdvThreads) {
+        Record r;
+        if (!load(k, r)) continue;
+        frame2_tiles(a, pl, c, r, W, H, [&](int kk, int32_t tile) {
+            if (kk >= 0) atomicAdd(s_cnt + kk, 1u);
+            else place(atomicAdd(cur2 + tile, 1u), r);
+        });
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kNbrSide * kNbrSide; i += kAdvThreads) {
+        const uint32_t n = s_cnt[i];
+        const int ty = c.ty + i / kNbrSide - kNbr, tx = c.tx + i % kNbrSide - kNbr;
+        s_base[i] = n ? atomicAdd(cur2 + ty * pl.tiles_x + tx, n) : 0u;
+        s_cnt[i] = 0u;
+    }
+    __syncthreads();
+    for (uint32_t k = threadIdx.x; k < c.it.count; k += kAdvThreads) {
+        Record r;
+        if (!load(k, r)) continue;
+        frame2_tiles(a, pl, c, r, W, H, [&](int kk, int32_t) {
+            if (kk >= 0) place(s_base[kk] + atomicAdd(s_cnt + kk, 1u), r);
+        });
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -327,11 +531,28 @@ cudaError_t launch_prep(const KernelArgs &a, cudaStream_t st, cudaEvent_t const 
         if (ev && ev[k]) cudaEventRecord(ev[k], st);
     };
     const unsigned nb = (unsigned)a.n_chunks;
+    if (!a.tiled) {
+        if (nb > 0) k_seed_advect<<<nb, kPrepThreads, 0, st>>>(a);
+        mark(2);
+        k_scan<<<2 * a.n_pairs, 1024, 0, st>>>(a, -1);
+        mark(3);
+        if (nb > 0) k_scatter<<<nb, kPrepThreads, 0, st>>>(a);
+        mark(4);
+        return cudaGetLastError();
+    }
+    // seeded render: seed + frame-1 bins, tiled advection, frame-2 bins
+    const unsigned nt1 = (unsigned)(a.n_tiles / 2);
+    const size_t adv_smem = (size_t)adv_window_nodes(a.tile) * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(k_advect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adv_smem);
+    if (e != cudaSuccess) return e;
     if (nb > 0) k_seed_advect<<<nb, kPrepThreads, 0, st>>>(a);
-    mark(2);
-    k_scan<<<2 * a.n_pairs, 1024, 0, st>>>(a);
-    mark(3);
+    k_scan<<<a.n_pairs, 1024, 0, st>>>(a, 0);
     if (nb > 0) k_scatter<<<nb, kPrepThreads, 0, st>>>(a);
+    if (nt1 > 0) k_advect<<<nt1, kAdvThreads, adv_smem, st>>>(a);
+    mark(2);
+    k_scan<<<a.n_pairs, 1024, 0, st>>>(a, 1);
+    mark(3);
+    if (nt1 > 0) k_scatter2<<<nt1, kAdvThreads, 0, st>>>(a);
     mark(4);
     return cudaGetLastError();
 }

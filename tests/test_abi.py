@@ -115,3 +115,9 @@ def test_workspace_grows_with_particles_and_tiles():
     small = B.workspace_bytes(B.pack(W.batch_512_u8(n_pairs=1)))
     big = B.workspace_bytes(B.pack(W.batch_512_u8(n_pairs=2)))
     assert big > small
+
+
+def test_gather_advection_flag_accepted():
+    pk = _packed()
+    pk.batch.flags = B.FLAG_GATHER_ADVECT
+    assert B.workspace_bytes(pk) > 0
