@@ -59,46 +59,68 @@ __device__ __forceinline__ int record_lead(int64_t first) { return (int)((first 
 // ---------------------------------------------------------------------------
 // exact fixed-point accumulation
 // ---------------------------------------------------------------------------
-// A contribution u = mx * my (pixel value * 1024 / i_max, at most 1024) is
-// split into hi = rint(u) and lo = rint((u - hi) * 2^22): hi from one FMA
-// with the FP32 round-to-integer identity (x + 1.5 * 2^23 leaves rint(x) in
-// the low mantissa bits for 0 <= x < 2^22), u - hi from a second FMA (one
-// rounding of the exact residual).  The tile keeps int32 sums of hi and lo:
-// integer addition is associative, so a pixel's value does not depend on the
-// order of its contributions, the tile size or the batch it is rendered in.
-// lo sums stay inside int32 for up to 1016 contributions; after every staged
-// chunk of records (at most 1016) the multiples of 2^22 in lo are carried
-// into hi.  Resolution 2^-32 i_max; pixel sums must stay below 2^21 i_max.
+// A contribution v = mx * my * amp (at most i_max: the pixel mass of a unit
+// Gaussian is at most 1 / (sqrt(2 pi) sigma)) is rounded once to an integer
+// number of units q = i_max 2^-26 and added to the pixel's 32-bit word with
+// one shared-memory atomic.  Integer addition is associative: a pixel's
+// value does not depend on the order of its contributions, the tile size or
+// the batch it is rendered in.
+//
+// A word holds 64 i_max.  Before a chunk of visits is splatted, the visits
+// of the item so far are counted per 8 x 8 block of the accumulator; while
+// no block is met by more than 63 visits, no pixel sum can reach 2^32 units
+// and the adds go unchecked.  Otherwise the chunk takes the checked path:
+// the thread whose add wraps a word adds 1 to the pixel's carry word (worth
+// 2^32 units), so no sum is ever lost.
 constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
 constexpr int32_t kMagicBits = 0x4B400000;
+constexpr float kFixedScale = 67108864.0f;      // 2^26 units per i_max
+constexpr float kFixedUnit = 1.0f / 67108864.0f;
+constexpr float kWrapValue = 4294967296.0f;     // 2^32: the weight of a carry
+constexpr uint32_t kSafeVisits = 63;            // visits per block that cannot wrap a word
+constexpr int kBlkShift = 3;                    // 8 x 8 pixel blocks
+constexpr int kBlkSide = 16;                    // blocks per side of the counter grid (edge <= 128)
 
-__device__ __forceinline__ void add_fixed(int32_t *hi, int32_t *lo, float mx, float my) {
-    const float t = fmaf(mx, my, kMagic);
-    const int32_t h = __float_as_int(t) - kMagicBits;
-    const float r = fmaf(mx, my, -__fsub_rn(t, kMagic));  // |r| <= 1/2
-    const int32_t l = __float_as_int(fmaf(r, 4194304.0f, kMagic)) - kMagicBits;
-    atomicAdd(hi, h);
-    atomicAdd(lo, l);
-}
-
-__device__ __forceinline__ void carry_fixed(int32_t *hi, int32_t *lo, int n) {
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        const int32_t l = lo[k];
-        const int32_t c = l >> 22;  // floor(l / 2^22)
-        hi[k] += c;
-        lo[k] = l - (c << 22);
-    }
-}
-
+// Tile geometry of one work item.  The accumulator covers the halo-widened
+// rectangle clipped to the frame, from column ax0 (ex0 rounded down to a
+// multiple of 4) with a row pitch P (a multiple of 4), so quads of 4 pixels
+// are 16-byte aligned.  The finishing buffer A covers the full halo
+// rectangle [x0 - R, x1 + R) x [y0 - R, y1 + R) from column afx0 (x0 - R
+// rounded down to a multiple of 4) with pitch AP; outside the frame it holds
+// replicated border values.
 struct Geo {
     int32_t W, H;
     int32_t x0, x1, y0, y1;      // tile pixels [x0, x1) x [y0, y1)
     int32_t ex0, ex1, ey0, ey1;  // halo-widened rectangle clipped to the frame
-    int32_t EW, EH;              // its width and height (accumulator pitch EW)
-    int32_t R;                   // blur radius = halo
-    int32_t FW, FH;              // full halo rectangle (replicated outside the frame)
-    int32_t AP;                  // row pitch of the finishing buffer A (FW rounded up to 4)
+    int32_t EW, EH;              // its width and height
+    int32_t R;                   // blur radius
+    int32_t ax0, P;              // accumulator: first column, row pitch
+    int32_t fx0, fy0, FW, FH;    // full halo rectangle (may leave the frame)
+    int32_t afx0, AP;            // finishing buffer: first column, row pitch
 };
+
+// The tile's accumulator as the splat sees it.
+struct Acc {
+    uint32_t *acc;  // [rows][P] words; carry words at acc + co
+    int co;
+    int P;
+    int *wrap;      // set when a checked add wrapped a word
+};
+
+// Add one contribution to the word at w (a pixel of A).
+template <bool CHECKED>
+__device__ __forceinline__ void add_contrib(uint32_t *w, const Acc &A, float mx, float my) {
+    const uint32_t l = __float2uint_rn(__fmul_rn(mx, my));
+    if (!CHECKED) {
+        atomicAdd(w, l);
+        return;
+    }
+    const uint32_t old = atomicAdd(w, l);
+    if (old + l < old) {
+        atomicAdd(w + A.co, 1u);
+        *A.wrap = 1;
+    }
+}
 
 // ---------------------------------------------------------------------------
 // pixel integration of Eq. 1
@@ -139,7 +161,7 @@ __device__ __forceinline__ float edge_mass(float sa, float sb) {
 struct Visit {
     float px, py;    // fractions of the split position
     float inv;       // 1 / sigma
-    float amps;      // amplitude * 1024 / i_max
+    float amps;      // amplitude * 2^26 / i_max (fixed-point units)
     int32_t base;    // accumulator index of the clipped window's first pixel
     uint32_t shape;  // bx | by << 8 (int8: window start - integer position) | nx << 16 | ny << 24
 };
@@ -174,7 +196,7 @@ __device__ __forceinline__ int small_div(int a, float inv_b) { return (int)(((fl
 // [j RG, j RG + RG) of the window.  All lanes of the warp take part (the
 // shuffles); lanes of an empty visit add nothing.
 template <int N, int U, int RG>
-__device__ __forceinline__ void splat_group(const Visit &v, int EW, int32_t *hi, int32_t *lo, const float4 *tab) {
+__device__ __forceinline__ void splat_group(const Visit &v, const Acc &A, const float4 *tab) {
     static_assert(U * RG >= N, "rows of a window");
     constexpr int EPL = (N + U) / U;  // ceil((N + 1) / U) x edges per lane
     const unsigned FULL = 0xffffffffu;
@@ -204,7 +226,7 @@ __device__ __forceinline__ void splat_group(const Visit &v, int EW, int32_t *hi,
     const int rows = min(max(ny - r0, 0), RG);
     const float fby = (float)(visit_by(v.shape) + r0);
     float ey = edge_value_tab(__fsub_rn(fby, v.py), v.inv, tab);
-    int32_t *hr = hi + v.base + r0 * EW, *lr = lo + v.base + r0 * EW;
+    uint32_t *hr = A.acc + v.base + r0 * A.P;
 #pragma unroll 1  // a rolled row loop keeps the class templates small enough for the instruction cache
     for (int q = 0; q < RG; ++q) {
         const float en = edge_value_tab(__fsub_rn(__fadd_rn(fby, (float)(q + 1)), v.py), v.inv, tab);
@@ -213,15 +235,15 @@ __device__ __forceinline__ void splat_group(const Visit &v, int EW, int32_t *hi,
         if (q < rows) {
 #pragma unroll
             for (int c = 0; c < N; ++c)
-                if (c < nx) add_fixed(hr + c, lr + c, mx[c], my);
+                if (c < nx) add_contrib<false>(hr + c, A, mx[c], my);
         }
-        hr += EW;
-        lr += EW;
+        hr += A.P;
     }
 }
 
 // Windows with more than 30 edges: per-warp scratch in shared memory.
-__device__ __noinline__ void splat_particle_wide(int EW, int32_t *hi, int32_t *lo, float px, float py, float inv,
+template <bool CHECKED>
+__device__ __noinline__ void splat_particle_wide(const Acc &A, float px, float py, float inv,
                                                  float amps, int32_t base, int bx, int by, int nx, int ny,
                                                  float *scr, int wq, const float4 *tab) {
     const int lane = threadIdx.x & 31;
@@ -238,8 +260,7 @@ __device__ __noinline__ void splat_particle_wide(int EW, int32_t *hi, int32_t *l
         const int r = min((int)(((float)m + 0.5f) * invx), ny - 1);
         const int cc = m - r * nx;
         if ((unsigned)cc >= (unsigned)nx) continue;
-        const int idx = base + r * EW + cc;
-        add_fixed(hi + idx, lo + idx, ex[cc], ey[r]);
+        add_contrib<CHECKED>(A.acc + base + r * A.P + cc, A, ex[cc], ey[r]);
     }
     __syncwarp();
 }
@@ -248,7 +269,8 @@ __device__ __noinline__ void splat_particle_wide(int EW, int32_t *hi, int32_t *l
 // [nx+1, nx+ny+1] the y edges; each lane then takes one column and every
 // rpr-th row of the window.  Windows with more edges than lanes go through
 // the scratch path.
-__device__ __forceinline__ void splat_coop(const Visit &v, bool valid, int EW, int32_t *hi, int32_t *lo, float *scr,
+template <bool CHECKED>
+__device__ __forceinline__ void splat_coop(const Visit &v, bool valid, const Acc &A, float *scr,
                                            int wq, const float4 *tab) {
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
@@ -262,7 +284,7 @@ __device__ __forceinline__ void splat_coop(const Visit &v, bool valid, int EW, i
         const uint32_t shape = __shfl_sync(FULL, v.shape, src);
         const int nx = visit_nx(shape), ny = visit_ny(shape), bx = visit_bx(shape), by = visit_by(shape);
         if (nx + ny + 2 > 32) {
-            splat_particle_wide(EW, hi, lo, px, py, inv, amps, base, bx, by, nx, ny, scr, wq, tab);
+            splat_particle_wide<CHECKED>(A, px, py, inv, amps, base, bx, by, nx, ny, scr, wq, tab);
             continue;
         }
         const int nxe = nx + 1;
@@ -280,11 +302,11 @@ __device__ __forceinline__ void splat_coop(const Visit &v, bool valid, int EW, i
         const int lc = lane - lr * nx;
         const float exv = __shfl_sync(FULL, m, lc);
         const bool act = lr < rpr;
-        const int idx = base + lr * EW + lc;
+        uint32_t *dst = A.acc + base + lr * A.P + lc;
         for (int r0 = 0; r0 < ny; r0 += rpr) {
             const int r = r0 + lr;
             const float eyv = __shfl_sync(FULL, m, nxe + min(r, ny - 1));
-            if (act && r < ny) add_fixed(hi + idx + r0 * EW, lo + idx + r0 * EW, exv, eyv);
+            if (act && r < ny) add_contrib<CHECKED>(dst + r0 * A.P, A, exv, eyv);
         }
     }
 }
@@ -293,18 +315,23 @@ __device__ __forceinline__ void splat_coop(const Visit &v, bool valid, int EW, i
 struct SortSmem {
     uint32_t *cnt;   // [kBuckets] visits per (class, bank) key
     uint32_t *off;   // [kBuckets + 1] exclusive offsets
+    uint32_t *blk;   // [kBlkSide^2] visits of the item so far per 8 x 8 block
+    int *checked;    // the chunk takes the checked path
     uint32_t *next;  // warp-slot ticket
 };
 
 // Splat n staged records (at recs) into the tile's accumulator:
 //   A. each thread sets up its records' visits (window clipped to the halo
-//      rectangle) and takes a slot in its (class, bank) bucket;
-//   B. warp 0 scans the bucket counts;
+//      rectangle), takes a slot in its (class, bank) bucket and counts the
+//      visit in the 8 x 8 blocks its window meets;
+//   B. warp 0 scans the bucket counts and decides from the block counts
+//      whether the chunk's adds must be checked for wrapping;
 //   C. the visits are written in key order over the staged records (out);
-//   D. warps claim slots of 32 visits, widest class first, and render them.
+//   D. warps claim slots of 32 visits, widest class first, and render them
+//      (checked: every visit by a whole warp, with checked adds).
 template <int NT>
 __device__ __forceinline__ void splat_chunk(const unsigned char *recs, unsigned char *out, uint32_t n, const Geo &g,
-                                            float scale, int32_t *hi, int32_t *lo, const SortSmem &ss, float *scr,
+                                            float scale, const Acc &acc, const SortSmem &ss, float *scr,
                                             int wq, const float4 *tab) {
     constexpr int RPT = (kRecCap + NT - 1) / NT;
     const int lane = threadIdx.x & 31;
@@ -333,13 +360,17 @@ __device__ __forceinline__ void splat_chunk(const unsigned char *recs, unsigned 
                 v[q].py = pf.y;
                 v[q].inv = __frcp_rn(ps.x);
                 v[q].amps = ps.y * scale;
-                v[q].base = (i0 - g.ey0) * g.EW + (j0 - g.ex0);
+                v[q].base = (i0 - g.ey0) * g.P + (j0 - g.ax0);
                 v[q].shape = ((uint32_t)(j0 - pi.x) & 0xFFu) | (((uint32_t)(i0 - pi.y) & 0xFFu) << 8) |
                              ((uint32_t)nx << 16) | ((uint32_t)ny << 24);
                 const int m = max(nx, ny);
                 const int cls = m > kNarrowMax ? kWideClass : (m - 1) >> 1;
                 key[q] = cls * 32 + (v[q].base & 31);
                 slot[q] = atomicAdd(ss.cnt + key[q], 1u);
+                const int bx0 = (j0 - g.ax0) >> kBlkShift, bx1 = (j1 - g.ax0) >> kBlkShift;
+                const int by0 = (i0 - g.ey0) >> kBlkShift, by1 = (i1 - g.ey0) >> kBlkShift;
+                for (int by = by0; by <= by1; ++by)
+                    for (int bx = bx0; bx <= bx1; ++bx) atomicAdd(ss.blk + by * kBlkSide + bx, 1u);
             }
         }
     }
@@ -367,6 +398,12 @@ __device__ __forceinline__ void splat_chunk(const unsigned char *recs, unsigned 
         }
         if (lane == 31) ss.off[kBuckets] = incl;
         if (lane == 0) *ss.next = 0;
+        uint32_t mx = 0;
+#pragma unroll
+        for (int j = 0; j < kBlkSide * kBlkSide / 32; ++j) mx = max(mx, ss.blk[lane + 32 * j]);
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) mx = max(mx, __shfl_xor_sync(FULL, mx, d));
+        if (lane == 0) *ss.checked = mx > kSafeVisits ? 1 : 0;
     }
     __syncthreads();
     float2 *o8 = reinterpret_cast<float2 *>(out);  // 16-byte aligned; a Visit is three 8-byte words
@@ -380,6 +417,32 @@ __device__ __forceinline__ void splat_chunk(const unsigned char *recs, unsigned 
         }
     }
     __syncthreads();
+    if (*ss.checked) {  // dense item: a warp per visit, adds checked for wrapping
+        const uint32_t total = ss.off[kBuckets];
+        for (;;) {
+            uint32_t sl = 0;
+            if (lane == 0) sl = atomicAdd(ss.next, 1u);
+            sl = __shfl_sync(FULL, sl, 0);
+            if (sl * 32 >= total) break;
+            const uint32_t idx = sl * 32 + lane;
+            const bool valid = idx < total;
+            Visit e;
+            e.px = e.py = e.inv = e.amps = 0.0f;
+            e.base = 0;
+            e.shape = 0;
+            if (valid) {
+                const float2 a = o8[3 * idx], b = o8[3 * idx + 1], d = o8[3 * idx + 2];
+                e.px = a.x;
+                e.py = a.y;
+                e.inv = b.x;
+                e.amps = b.y;
+                e.base = __float_as_int(d.x);
+                e.shape = __float_as_uint(d.y);
+            }
+            splat_coop<true>(e, valid, acc, scr, wq, tab);
+        }
+        return;
+    }
     for (;;) {
         uint32_t sl = 0;
         if (lane == 0) sl = atomicAdd(ss.next, 1u);
@@ -413,15 +476,15 @@ __device__ __forceinline__ void splat_chunk(const unsigned char *recs, unsigned 
             e.shape = 0;
         }
         switch (c) {
-        case 0: splat_group<2, class_lanes(0), class_rows(0)>(e, g.EW, hi, lo, tab); break;
-        case 1: splat_group<4, class_lanes(1), class_rows(1)>(e, g.EW, hi, lo, tab); break;
-        case 2: splat_group<6, class_lanes(2), class_rows(2)>(e, g.EW, hi, lo, tab); break;
-        case 3: splat_group<8, class_lanes(3), class_rows(3)>(e, g.EW, hi, lo, tab); break;
-        case 4: splat_group<10, class_lanes(4), class_rows(4)>(e, g.EW, hi, lo, tab); break;
-        case 5: splat_group<12, class_lanes(5), class_rows(5)>(e, g.EW, hi, lo, tab); break;
-        case 6: splat_group<14, class_lanes(6), class_rows(6)>(e, g.EW, hi, lo, tab); break;
-        case 7: splat_group<16, class_lanes(7), class_rows(7)>(e, g.EW, hi, lo, tab); break;
-        default: splat_coop(e, valid, g.EW, hi, lo, scr, wq, tab); break;
+        case 0: splat_group<2, class_lanes(0), class_rows(0)>(e, acc, tab); break;
+        case 1: splat_group<4, class_lanes(1), class_rows(1)>(e, acc, tab); break;
+        case 2: splat_group<6, class_lanes(2), class_rows(2)>(e, acc, tab); break;
+        case 3: splat_group<8, class_lanes(3), class_rows(3)>(e, acc, tab); break;
+        case 4: splat_group<10, class_lanes(4), class_rows(4)>(e, acc, tab); break;
+        case 5: splat_group<12, class_lanes(5), class_rows(5)>(e, acc, tab); break;
+        case 6: splat_group<14, class_lanes(6), class_rows(6)>(e, acc, tab); break;
+        case 7: splat_group<16, class_lanes(7), class_rows(7)>(e, acc, tab); break;
+        default: splat_coop<false>(e, valid, acc, scr, wq, tab); break;
         }
     }
 }
@@ -499,26 +562,31 @@ __device__ __forceinline__ void store_group(T *o, float *v, int nvalid, float M)
     if (nvalid == 4 && (reinterpret_cast<uintptr_t>(o) % (4 * sizeof(T))) == 0) {
         Out<T>::store4(o, v);
     } else {
-        for (int j = 0; j < nvalid; ++j) o[j] = Out<T>::cvt(v[j]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (j < nvalid) o[j] = Out<T>::cvt(v[j]);
     }
 }
 
 // Horizontal pass (rows of the full halo rectangle, tile columns) and
 // vertical pass with store; taps w[|k|], k = -R..R, replicate border already
-// materialised in A.  R is a compile-time radius (0 < R <= 6).
+// materialised in A.  R is a compile-time radius (0 < R <= 6).  Tiles start
+// on multiples of 4, so the tile's first input column x0 - R sits
+// OFF = (-R) mod 4 columns into A's 16-byte aligned rows.
 template <typename T, int R>
 __device__ __forceinline__ void blur_store(const Geo &g, const float *A, float *Bh, int BP, const float *w, T *out,
                                            float M) {
+    constexpr int OFF = (4 - R % 4) % 4;
     const int TW = g.x1 - g.x0, TH = g.y1 - g.y0;
     const int G = (TW + 3) >> 2;
     const float iG = 1.0f / (float)G;
     float wr[R + 1];
 #pragma unroll
     for (int k = 0; k <= R; ++k) wr[k] = w[k];
-    constexpr int NV = (4 + 2 * R + 3) / 4;  // float4 loads covering the 4 + 2R inputs
+    constexpr int NV = (OFF + 4 + 2 * R + 3) / 4;  // float4 loads covering the 4 + 2R inputs
     for (int it = threadIdx.x; it < g.FH * G; it += blockDim.x) {
         const int r = small_div(it, iG), c0 = (it - r * G) * 4;
-        // 16-byte aligned (AP and c0 multiples of 4); inputs past FW feed only outputs past the tile
+        // 16-byte aligned (AP and c0 multiples of 4); inputs past the halo feed only outputs past the tile
         const float4 *row = reinterpret_cast<const float4 *>(A + r * g.AP + c0);
         float v[4 * NV];
 #pragma unroll
@@ -533,9 +601,9 @@ __device__ __forceinline__ void blur_store(const Geo &g, const float *A, float *
         float *op = &o.x;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            float acc = wr[0] * v[j + R];
+            float acc = wr[0] * v[OFF + j + R];
 #pragma unroll
-            for (int k = 1; k <= R; ++k) acc = fmaf(wr[k], v[j + R - k] + v[j + R + k], acc);
+            for (int k = 1; k <= R; ++k) acc = fmaf(wr[k], v[OFF + j + R - k] + v[OFF + j + R + k], acc);
             op[j] = acc;
         }
         *reinterpret_cast<float4 *>(Bh + r * BP + c0) = o;
@@ -564,9 +632,10 @@ template <typename T>
 __device__ __noinline__ void blur_store_any(const Geo &g, const float *A, float *Bh, int BP, const float *w, T *out,
                                             float M) {
     const int R = g.R, TW = g.x1 - g.x0, TH = g.y1 - g.y0;
+    const int cx = g.fx0 - g.afx0 + R;  // A column of the tile's first column
     for (int it = threadIdx.x; it < g.FH * TW; it += blockDim.x) {
         const int r = it / TW, c = it - r * TW;
-        const float *row = A + r * g.AP + c + R;
+        const float *row = A + r * g.AP + cx + c;
         float acc = w[0] * row[0];
         for (int k = 1; k <= R; ++k) acc = fmaf(w[k], row[-k] + row[k], acc);
         Bh[r * BP + c] = acc;
@@ -582,15 +651,16 @@ __device__ __noinline__ void blur_store_any(const Geo &g, const float *A, float 
     }
 }
 
+// R = 0: A's first column is the tile's first column (x0 is a multiple of 4).
 template <typename T>
 __device__ __forceinline__ void store_unblurred(const Geo &g, const float *A, T *out, float M) {
     const int TW = g.x1 - g.x0, TH = g.y1 - g.y0;
     const int G = (TW + 3) >> 2;
+    const float iG = 1.0f / (float)G;
     for (int it = threadIdx.x; it < TH * G; it += blockDim.x) {
-        const int r = it / G, c0 = (it - r * G) * 4;
-        float v[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) v[j] = A[r * g.AP + min(c0 + j, g.FW - 1)];
+        const int r = small_div(it, iG), c0 = (it - r * G) * 4;
+        const float4 t = *reinterpret_cast<const float4 *>(A + r * g.AP + c0);
+        float v[4] = {t.x, t.y, t.z, t.w};
         store_group<T>(out + r * g.W + c0, v, min(4, TW - c0), M);
     }
 }
@@ -599,12 +669,18 @@ __device__ __forceinline__ void store_unblurred(const Geo &g, const float *A, T 
 // one work item
 // ---------------------------------------------------------------------------
 struct Smem {
-    int32_t *hi, *lo;
+    uint32_t *acc;  // accumulator words; carry words at acc + co
+    int co;
+    int *wrap;      // set by any add that wrapped a word (read after the splat)
     float *A, *Bh, *sx2, *sy2, *scr;
     const float4 *phi;
     SortSmem sort;
     int BP;
 };
+
+// Row pitch capacity of the accumulator and finishing buffer for a capacity
+// edge E (tile + 2 max radius): the aligned widths stay within E + 6.
+__host__ __device__ inline int pitch_cap(int E) { return ((E + 3) & ~3) + 4; }
 
 __device__ __forceinline__ Geo make_geo(const synthpix_pair_desc &D, const PairPlan &pl, int tile_edge, int tile,
                                         int halo) {
@@ -623,46 +699,151 @@ __device__ __forceinline__ Geo make_geo(const synthpix_pair_desc &D, const PairP
     g.ey1 = min(g.y1 + halo, g.H);
     g.EW = g.ex1 - g.ex0;
     g.EH = g.ey1 - g.ey0;
+    g.ax0 = g.ex0 & ~3;
+    g.P = (g.ex1 - g.ax0 + 3) & ~3;
+    g.fx0 = g.x0 - g.R;
+    g.fy0 = g.y0 - g.R;
     g.FW = (g.x1 - g.x0) + 2 * g.R;
-    g.AP = (g.FW + 3) & ~3;
     g.FH = (g.y1 - g.y0) + 2 * g.R;
+    g.afx0 = g.fx0 & ~3;  // rounds down for negative columns too (two's complement)
+    g.AP = (g.x1 + g.R - g.afx0 + 3) & ~3;
     return g;
 }
 
-// separable illumination factors sin^2 of the clipped halo rectangle
+// separable illumination factors sin^2: columns [ax0, ax0 + P) and rows
+// [ey0, ey1) of the accumulator rectangle
 __device__ __forceinline__ bool illum_factors(const Geo &g, const synthpix_pair_desc &D, const Smem &s) {
     const bool illum = D.illum_min != 1.0f || D.illum_max != 1.0f;
     if (illum) {
-        for (int k = threadIdx.x; k < g.EW + g.EH; k += blockDim.x) {
-            if (k < g.EW) {
-                const float sv = sinpif(((float)(g.ex0 + k) + 0.5f) / (float)g.W);
+        for (int k = threadIdx.x; k < g.P + g.EH; k += blockDim.x) {
+            if (k < g.P) {
+                const float sv = sinpif(((float)(g.ax0 + k) + 0.5f) / (float)g.W);
                 s.sx2[k] = sv * sv;
             } else {
-                const float sv = sinpif(((float)(g.ey0 + k - g.EW) + 0.5f) / (float)g.H);
-                s.sy2[k - g.EW] = sv * sv;
+                const float sv = sinpif(((float)(g.ey0 + k - g.P) + 0.5f) / (float)g.H);
+                s.sy2[k - g.P] = sv * sv;
             }
         }
     }
     return illum;
 }
 
-// The finishing steps of one tile of one frame: A = L * S + sigma_n * n over
-// the clipped halo rectangle, border replication, separable blur, store.
-// src(idx, r, c) gives S at row r, column c of the clipped halo rectangle
-// (idx = r * EW + c).  The illumination factors must be in s.sx2 / s.sy2 and
-// visible (a barrier after illum_factors).
-template <typename T, typename Src>
-__device__ __forceinline__ void finish_tile(const KernelArgs &a, const Geo &g, const synthpix_pair_desc &D,
-                                            const float *wtab, int frame, bool illum, const Smem &s, Src src) {
-    const float dl = D.illum_max - D.illum_min;
-    const int fx0 = g.x0 - g.R, fy0 = g.y0 - g.R;
-    if (D.noise_sigma != 0.0f) {
-        // 32-bit pixel indices: frames hold at most 32768^2 = 2^30 pixels
+// S of the fused path: the accumulator words (and carry words when an add
+// wrapped), each cleared for the next item as it is read.  r: accumulator
+// row, c: column from ax0 (a multiple of 4 for quad()).
+struct AccSource {
+    uint32_t *acc;
+    int co, P;
+    float unit;  // i_max 2^-28
+    bool wrapped;
+    __device__ __forceinline__ float value(uint32_t v, uint32_t h) const {
+        return fmaf((float)h, kWrapValue, (float)v) * unit;
+    }
+    __device__ __forceinline__ float4 quad(int r, int c) const {
+        uint4 *p = reinterpret_cast<uint4 *>(acc + r * P + c);
+        const uint4 v = *p;
+        *p = make_uint4(0u, 0u, 0u, 0u);
+        uint4 h = make_uint4(0u, 0u, 0u, 0u);
+        if (wrapped) {
+            uint4 *q = reinterpret_cast<uint4 *>(acc + co + r * P + c);
+            h = *q;
+            *q = make_uint4(0u, 0u, 0u, 0u);
+        }
+        return make_float4(value(v.x, h.x), value(v.y, h.y), value(v.z, h.z), value(v.w, h.w));
+    }
+    __device__ __forceinline__ float pixel(int r, int c) const {
+        uint32_t *p = acc + r * P + c;
+        const uint32_t v = *p;
+        *p = 0u;
+        uint32_t h = 0u;
+        if (wrapped) {
+            h = p[co];
+            p[co] = 0u;
+        }
+        return value(v, h);
+    }
+};
+
+template <typename I>
+__device__ __forceinline__ float4 load4_inter(const I *p);
+template <>
+__device__ __forceinline__ float4 load4_inter<__half>(const __half *p) {
+    const uint2 u = *reinterpret_cast<const uint2 *>(p);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+template <>
+__device__ __forceinline__ float4 load4_inter<__nv_bfloat16>(const __nv_bfloat16 *p) {
+    const uint2 u = *reinterpret_cast<const uint2 *>(p);
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// S of the 16-bit path: the intermediate frame (frame row ey0 + r, column ax0 + c).
+template <typename I>
+struct InterSource {
+    const I *S;  // the frame
+    int W, ey0, ax0;
+    bool vec;    // 8-byte aligned quads
+    __device__ __forceinline__ float4 quad(int r, int c) const {
+        const I *p = S + (ey0 + r) * W + ax0 + c;
+        if (vec) return load4_inter<I>(p);
+        // W not a multiple of 4: the quad may run past the row (and the frame)
+        const int n = W - (ax0 + c);
+        return make_float4(n > 0 ? (float)p[0] : 0.0f, n > 1 ? (float)p[1] : 0.0f, n > 2 ? (float)p[2] : 0.0f,
+                           n > 3 ? (float)p[3] : 0.0f);
+    }
+    __device__ __forceinline__ float pixel(int r, int c) const { return (float)S[(ey0 + r) * W + ax0 + c]; }
+};
+
+// First pass of the finishing steps of one tile of one frame, over the
+// accumulator rectangle: A = L * S + sigma_n * n.  The illumination factors
+// must be in s.sx2 / s.sy2 and visible (a barrier after illum_factors).
+// With W a multiple of 4 (or without noise) a thread takes a 16-byte
+// aligned quad of a row, which is then also one Philox call of the noise
+// stream (pixels 4q..4q+3 of the frame's row-major order); otherwise noise
+// quads straddle rows and pixels are taken one by one.
+template <typename Src>
+__device__ __forceinline__ void finish_pass1(const KernelArgs &a, const Geo &g, const synthpix_pair_desc &D,
+                                             int frame, bool illum, const Smem &s, const Src &src) {
+    const float dl = D.illum_max - D.illum_min, lmin = D.illum_min, sn = D.noise_sigma;
+    const bool noise = sn != 0.0f;
+    const uint32_t tag = kTagNoise + (uint32_t)frame;
+    float *A0 = s.A + (g.ey0 - g.fy0) * g.AP + (g.ax0 - g.afx0);  // A at accumulator (row 0, column 0)
+    if (!noise || (g.W & 3) == 0) {
+        const int nq = g.P >> 2;
+        const float inq = 1.0f / (float)nq;
+        for (int item = threadIdx.x; item < g.EH * nq; item += blockDim.x) {
+            const int r = small_div(item, inq), c = 4 * (item - r * nq);
+            const float4 S = src.quad(r, c);
+            float4 L = make_float4(1.0f, 1.0f, 1.0f, 1.0f);
+            if (illum) {
+                const float4 sx = *reinterpret_cast<const float4 *>(s.sx2 + c);
+                const float ly = s.sy2[r];
+                L = make_float4(fmaf(dl, sx.x * ly, lmin), fmaf(dl, sx.y * ly, lmin), fmaf(dl, sx.z * ly, lmin),
+                                fmaf(dl, sx.w * ly, lmin));
+            }
+            float4 o;
+            if (noise) {
+                // 32-bit pixel indices: frames hold at most 32768^2 = 2^30 pixels
+                const uint32_t q = (uint32_t)(((g.ey0 + r) * g.W + g.ax0 + c) >> 2);
+                const uint4 w = stream_words(a.keys, D.pair_id, q, tag);
+                float n0, n1, n2, n3;
+                box_muller(w.x, w.y, n0, n1);
+                box_muller(w.z, w.w, n2, n3);
+                o = make_float4(fmaf(L.x, S.x, sn * n0), fmaf(L.y, S.y, sn * n1), fmaf(L.z, S.z, sn * n2),
+                                fmaf(L.w, S.w, sn * n3));
+            } else {
+                o = make_float4(L.x * S.x, L.y * S.y, L.z * S.z, L.w * S.w);
+            }
+            *reinterpret_cast<float4 *>(A0 + r * g.AP + c) = o;
+        }
+    } else {
         const int nq = (g.EW + 6) / 4 + 1;
         const float inq = 1.0f / (float)nq;
-        const uint32_t tag = kTagNoise + (uint32_t)frame;
-        const int fpitch = g.AP;
-        float *Abase = s.A + (g.ey0 - fy0) * fpitch + (g.ex0 - fx0);
+        const int cx = g.ex0 - g.ax0;  // accumulator column of ex0
         for (int item = threadIdx.x; item < g.EH * nq; item += blockDim.x) {
             const int r = small_div(item, inq), qi = item - r * nq;
             const int rowlin = (g.ey0 + r) * g.W;
@@ -672,37 +853,36 @@ __device__ __forceinline__ void finish_tile(const KernelArgs &a, const Geo &g, c
             float nv[4];
             box_muller(w.x, w.y, nv[0], nv[1]);
             box_muller(w.z, w.w, nv[2], nv[3]);
-            const int c0 = p0 - rowlin - g.ex0;  // column of the quad's first pixel in the halo rectangle
+            const int c0 = p0 - rowlin - g.ex0;  // column of the quad's first pixel from ex0
             const float ly = illum ? s.sy2[r] : 0.0f;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const int c = c0 + k;
                 if (c >= 0 && c < g.EW) {
-                    const float S = src(r * g.EW + c, r, c);
-                    const float L = illum ? fmaf(dl, s.sx2[c] * ly, D.illum_min) : 1.0f;
-                    Abase[r * fpitch + c] = fmaf(L, S, D.noise_sigma * nv[k]);
+                    const float S = src.pixel(r, cx + c);
+                    const float L = illum ? fmaf(dl, s.sx2[cx + c] * ly, lmin) : 1.0f;
+                    A0[r * g.AP + cx + c] = fmaf(L, S, sn * nv[k]);
                 }
             }
         }
-    } else {
-        const float iew = 1.0f / (float)g.EW;
-        for (int idx = threadIdx.x; idx < g.EH * g.EW; idx += blockDim.x) {
-            const int r = small_div(idx, iew), c = idx - r * g.EW;
-            const float S = src(idx, r, c);
-            const float L = illum ? fmaf(dl, s.sx2[c] * s.sy2[r], D.illum_min) : 1.0f;
-            s.A[(g.ey0 + r - fy0) * g.AP + (g.ex0 + c - fx0)] = L * S;
-        }
     }
-    __syncthreads();
-    // replicate the border into the halo outside the frame
-    if (g.R > 0 && (fx0 < 0 || fy0 < 0 || g.x1 + g.R > g.W || g.y1 + g.R > g.H)) {
+}
+
+// The rest of the finishing steps once A is complete over the accumulator
+// rectangle (a barrier after finish_pass1): border replication into the halo
+// outside the frame, separable blur, quantisation, one store per pixel.
+template <typename T>
+__device__ __forceinline__ void finish_rest(const KernelArgs &a, const Geo &g, const synthpix_pair_desc &D,
+                                            const float *wtab, int frame, const Smem &s) {
+    if (g.R > 0 && (g.fx0 < 0 || g.fy0 < 0 || g.x1 + g.R > g.W || g.y1 + g.R > g.H)) {
         const float ifw = 1.0f / (float)g.FW;
+        const int cx = g.fx0 - g.afx0;  // A column of frame column fx0
         for (int k = threadIdx.x; k < g.FH * g.FW; k += blockDim.x) {
             const int r = small_div(k, ifw), c = k - r * g.FW;
-            const int gi = fy0 + r, gj = fx0 + c;
+            const int gi = g.fy0 + r, gj = g.fx0 + c;
             if (gi < 0 || gi >= g.H || gj < 0 || gj >= g.W) {
-                const int ci = min(max(gi, 0), g.H - 1) - fy0, cj = min(max(gj, 0), g.W - 1) - fx0;
-                s.A[r * g.AP + c] = s.A[ci * g.AP + cj];
+                const int ci = min(max(gi, 0), g.H - 1) - g.fy0, cj = min(max(gj, 0), g.W - 1) - g.fx0;
+                s.A[r * g.AP + cx + c] = s.A[ci * g.AP + cx + cj];
             }
         }
     }
@@ -733,9 +913,12 @@ __device__ __forceinline__ __nv_bfloat16 to_inter<__nv_bfloat16>(float v) { retu
 // One work item of k_splat.  Fused (inter_dtype F32): splat the tile plus
 // its blur halo and finish it on chip.  Otherwise splat the tile alone and
 // store S in 16 bits to the intermediate frames; k_finish does the rest.
+// Thread 0 reads the work item of ticket t2 into `after` once the splat is
+// done (the ticket's atomic has long returned by then), so the read's
+// latency hides behind the finishing steps.
 template <typename T, int NT>
 __device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo &it, unsigned char *buf,
-                                             uint32_t cap, const Smem &s) {
+                                             uint32_t cap, const Smem &s, uint32_t t2, ItemInfo &after) {
     const synthpix_pair_desc &D = *reinterpret_cast<const synthpix_pair_desc *>(buf);
     const PairPlan &pl = *reinterpret_cast<const PairPlan *>(buf + 128);
     const float *wtab = reinterpret_cast<const float *>(buf + 192);
@@ -745,16 +928,16 @@ __device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo
 
     // splat, chunk by chunk of staged records
     const float imax = D.i_max > 0.0f ? D.i_max : 1.0f;
-    const float scale = 1024.0f / imax;
+    const float scale = kFixedScale / imax;
+    const Acc acc{s.acc, s.co, g.P, s.wrap};
     uint32_t done = 0;
     while (done < it.count) {
         const uint32_t n = min(it.count - done, cap);
-        splat_chunk<NT>(buf + kStageHeader + record_lead(it.rec0 + done), buf + kStageHeader, n, g, scale, s.hi,
-                        s.lo, s.sort, s.scr + (threadIdx.x >> 5) * a.warp_scratch, a.warp_scratch >> 2, s.phi);
+        splat_chunk<NT>(buf + kStageHeader + record_lead(it.rec0 + done), buf + kStageHeader, n, g, scale, acc,
+                        s.sort, s.scr + (threadIdx.x >> 5) * a.warp_scratch, a.warp_scratch >> 2, s.phi);
         done += n;
         __syncthreads();
-        if (done < it.count) {  // more records: carry lo before the next chunk (the last carry is in pass 1)
-            carry_fixed(s.hi, s.lo, g.EH * g.EW);
+        if (done < it.count) {  // more records: stage the next chunk
             stage_records(a, it.rec0 + done, min(it.count - done, cap), buf + kStageHeader);
             cp_async_commit();
             cp_async_wait_all();
@@ -762,56 +945,54 @@ __device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo
         }
     }
     if (it.count == 0) __syncthreads();  // illumination factors
+    // block counts of the next item start from zero (its first count comes after a barrier)
+    for (int k = threadIdx.x; k < kBlkSide * kBlkSide; k += blockDim.x) s.sort.blk[k] = 0u;
+    if (threadIdx.x == 0) {
+        if ((int64_t)t2 < a.n_tiles) after = a.items[t2];
+        else after.pair = -1;
+    }
 
-    const float unit = imax * (1.0f / 1024.0f);
-    int32_t *hi = s.hi, *lo = s.lo;
-    // S from the fixed-point sums, carrying lo into hi on the fly; each pixel
-    // is read once, and its accumulator cleared for the next item
-    auto fixed_src = [hi, lo, unit](int idx, int, int) {
-        const int32_t l = lo[idx], c = l >> 22;
-        const float v = fmaf((float)(l - (c << 22)), 1.0f / 4194304.0f, (float)(hi[idx] + c)) * unit;
-        hi[idx] = 0;
-        lo[idx] = 0;
-        return v;
-    };
+    const AccSource src{s.acc, s.co, g.P, imax * kFixedUnit, *s.wrap != 0};
     if (!fused) {
-        // halo 0: the clipped rectangle is the tile
+        // halo 0: the accumulator rectangle is the tile (ax0 = ex0 = x0)
         const int64_t HW = (int64_t)g.H * g.W;
         const int64_t base = pl.inter_base + (int64_t)it.frame * HW;
         const float iew = 1.0f / (float)g.EW;
         for (int idx = threadIdx.x; idx < g.EH * g.EW; idx += blockDim.x) {
             const int r = small_div(idx, iew), c = idx - r * g.EW;
-            const float S = fixed_src(idx, r, c);
+            const float S = src.pixel(r, c);
             const int64_t o = base + (int64_t)(g.ey0 + r) * g.W + (g.ex0 + c);
             if (a.inter_dtype == SYNTHPIX_F16) reinterpret_cast<__half *>(a.inter)[o] = to_inter<__half>(S);
             else reinterpret_cast<__nv_bfloat16 *>(a.inter)[o] = to_inter<__nv_bfloat16>(S);
         }
         return;  // the caller's loop ends with a barrier
     }
-    finish_tile<T>(a, g, D, wtab, it.frame, illum, s, fixed_src);
+    finish_pass1(a, g, D, it.frame, illum, s, src);
+    __syncthreads();
+    finish_rest<T>(a, g, D, wtab, it.frame, s);
 }
 
 // ---------------------------------------------------------------------------
 // the persistent kernel
 // ---------------------------------------------------------------------------
 struct SmemLayout {
-    size_t hi, lo, A, Bh, sx2, sy2, scr, phi, bufs, total;
+    size_t acc, A, Bh, sx2, sy2, scr, phi, bufs, total;
 };
 
 __host__ __device__ inline SmemLayout smem_layout(int E, int tile, int warp_scratch, int rec_buf_bytes) {
     SmemLayout L;
     const int BP = (tile + 3) & ~3;
+    const size_t PC = (size_t)pitch_cap(E);
     size_t o = 0;
     auto take = [&](size_t bytes) {
         const size_t at = o;
         o = (o + bytes + 15) & ~(size_t)15;
         return at;
     };
-    L.hi = take((size_t)E * E * 4);
-    L.lo = take((size_t)E * E * 4);
-    L.A = take(((size_t)E * (size_t)((E + 3) & ~3) + 16) * 4);
+    L.acc = take(2 * (size_t)E * PC * 4);  // words, then carry words
+    L.A = take(((size_t)E * PC + 32) * 4);  // + padding read by the last row's blur loads
     L.Bh = take((size_t)E * BP * 4);
-    L.sx2 = take((size_t)E * 4);
+    L.sx2 = take(PC * 4);
     L.sy2 = take((size_t)E * 4);
     L.scr = take((size_t)(kSplatMaxThreads / 32) * warp_scratch * 4);
     L.phi = take((size_t)(kPhiDegree + 1) * kPhiPieces * 4);
@@ -825,11 +1006,14 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_splat(KernelArgs a) {
     if (*a.check != 1) return;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ ItemInfo s_item[2];
-    __shared__ uint32_t s_cnt[kBuckets], s_off[kBuckets + 1], s_next;
+    __shared__ uint32_t s_cnt[kBuckets], s_off[kBuckets + 1], s_next, s_blk[kBlkSide * kBlkSide];
+    __shared__ int s_wrap, s_checked;
     const SmemLayout L = smem_layout(a.smem_edge, a.tile, a.warp_scratch, a.rec_buf_bytes);
+    const int co = a.smem_edge * pitch_cap(a.smem_edge);
     Smem s;
-    s.hi = reinterpret_cast<int32_t *>(smem + L.hi);
-    s.lo = reinterpret_cast<int32_t *>(smem + L.lo);
+    s.acc = reinterpret_cast<uint32_t *>(smem + L.acc);
+    s.co = co;
+    s.wrap = &s_wrap;
     s.A = reinterpret_cast<float *>(smem + L.A);
     s.Bh = reinterpret_cast<float *>(smem + L.Bh);
     s.sx2 = reinterpret_cast<float *>(smem + L.sx2);
@@ -841,16 +1025,16 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_splat(KernelArgs a) {
     s.sort.cnt = s_cnt;
     s.sort.off = s_off;
     s.sort.next = &s_next;
+    s.sort.blk = s_blk;
+    s.sort.checked = &s_checked;
     for (int k = threadIdx.x; k < kBuckets; k += blockDim.x) s_cnt[k] = 0;
+    for (int k = threadIdx.x; k < kBlkSide * kBlkSide; k += blockDim.x) s_blk[k] = 0;
     s.BP = (a.tile + 3) & ~3;
     unsigned char *bufs = smem + L.bufs;
     const uint32_t cap = (uint32_t)kRecCap;
-    const int E2 = a.smem_edge * a.smem_edge;
-    for (int k = threadIdx.x; k < E2; k += blockDim.x) {
-        s.hi[k] = 0;
-        s.lo[k] = 0;
-    }
+    for (int k = threadIdx.x; k < 2 * co; k += blockDim.x) s.acc[k] = 0u;
     if (threadIdx.x == 0) {
+        s_wrap = 0;
         for (int q = 0; q < 2; ++q) {
             const uint32_t t = atomicAdd(a.ticket, 1u);
             ItemInfo it;
@@ -869,8 +1053,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_splat(KernelArgs a) {
         const ItemInfo it = s_item[cur];
         const ItemInfo nx = s_item[cur ^ 1];
         cp_async_wait_all();
-        __syncthreads();  // staged data of `it` visible; the other buffer is free
+        __syncthreads();  // staged data of `it` visible; the other buffer is free; the wrap flag is read
         if (it.pair < 0) break;
+        // the splat's first add comes after a barrier inside splat_chunk
+        if (threadIdx.x == 0) s_wrap = 0;
         unsigned char *bnext = bufs + (cur ^ 1) * a.rec_buf_bytes;
         if (nx.pair >= 0) {
             stage_header(a, nx.pair, bnext);
@@ -879,13 +1065,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_splat(KernelArgs a) {
         cp_async_commit();
         uint32_t t2 = 0;
         if (threadIdx.x == 0) t2 = atomicAdd(a.ticket, 1u);
-        process_item<T, NT>(a, it, bufs + cur * a.rec_buf_bytes, cap, s);
-        if (threadIdx.x == 0) {
-            ItemInfo after;
-            if ((int64_t)t2 < a.n_tiles) after = a.items[t2];
-            else after.pair = -1;
-            s_item[cur] = after;
-        }
+        ItemInfo after;
+        process_item<T, NT>(a, it, bufs + cur * a.rec_buf_bytes, cap, s, t2, after);
+        if (threadIdx.x == 0) s_item[cur] = after;
         cur ^= 1;
         __syncthreads();
     }
@@ -904,15 +1086,16 @@ struct FinishLayout {
 __host__ __device__ inline FinishLayout finish_layout(int E, int tile) {
     FinishLayout L;
     const int BP = (tile + 3) & ~3;
+    const size_t PC = (size_t)pitch_cap(E);
     size_t o = 0;
     auto take = [&](size_t bytes) {
         const size_t at = o;
         o = (o + bytes + 15) & ~(size_t)15;
         return at;
     };
-    L.A = take(((size_t)E * (size_t)((E + 3) & ~3) + 16) * 4);
+    L.A = take(((size_t)E * PC + 32) * 4);
     L.Bh = take((size_t)E * BP * 4);
-    L.sx2 = take((size_t)E * 4);
+    L.sx2 = take(PC * 4);
     L.sy2 = take((size_t)E * 4);
     L.total = o;
     return L;
@@ -925,14 +1108,16 @@ __global__ void __launch_bounds__(kSplatThreads) k_finish(KernelArgs a) {
     __shared__ float wtab[kBlurStride];
     const FinishLayout FL = finish_layout(a.smem_edge, a.tile);
     Smem s;
-    s.hi = s.lo = nullptr;
+    s.acc = nullptr;
+    s.co = 0;
+    s.wrap = nullptr;
     s.A = reinterpret_cast<float *>(smem + FL.A);
     s.Bh = reinterpret_cast<float *>(smem + FL.Bh);
     s.sx2 = reinterpret_cast<float *>(smem + FL.sx2);
     s.sy2 = reinterpret_cast<float *>(smem + FL.sy2);
     s.scr = nullptr;
     s.phi = nullptr;
-    s.sort = SortSmem{nullptr, nullptr, nullptr};
+    s.sort = SortSmem{nullptr, nullptr, nullptr, nullptr, nullptr};
     s.BP = (a.tile + 3) & ~3;
     const ItemInfo it = a.items[blockIdx.x];
     const synthpix_pair_desc &D = a.descs[it.pair];
@@ -942,11 +1127,11 @@ __global__ void __launch_bounds__(kSplatThreads) k_finish(KernelArgs a) {
     const bool illum = illum_factors(g, D, s);
     __syncthreads();
     const I *S16 = reinterpret_cast<const I *>(a.inter) + pl.inter_base + (int64_t)it.frame * g.H * g.W;
-    const int W = g.W, ex0 = g.ex0, ey0 = g.ey0;
-    auto src = [S16, W, ex0, ey0](int, int r, int c) {
-        return (float)S16[(int64_t)(ey0 + r) * W + (ex0 + c)];
-    };
-    finish_tile<T>(a, g, D, wtab, it.frame, illum, s, src);
+    const bool vec = (g.W & 3) == 0 && (reinterpret_cast<uintptr_t>(S16) & 7) == 0;
+    const InterSource<I> src{S16, g.W, g.ey0, g.ax0, vec};
+    finish_pass1(a, g, D, it.frame, illum, s, src);
+    __syncthreads();
+    finish_rest<T>(a, g, D, wtab, it.frame, s);
 }
 
 size_t splat_smem_bytes(int edge, int tile, int warp_scratch, int rec_buf_bytes) {

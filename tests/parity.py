@@ -18,11 +18,11 @@ FLOAT_TOL = 1e-4
 BAND = 1e-6
 
 
-def gpu_render(wl, tile: int = 0, out_dtype=None, renderer=None):
+def gpu_render(wl, tile: int = 0, out_dtype=None, renderer=None, inter_dtype=None):
     import torch
 
     from paper_2512_09664_b300.binding import Renderer
-    r = renderer or Renderer(wl, tile=tile, out_dtype=out_dtype)
+    r = renderer or Renderer(wl, tile=tile, out_dtype=out_dtype, inter_dtype=inter_dtype)
     r.render()
     torch.cuda.synchronize()
     outs = []

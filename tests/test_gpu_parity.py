@@ -169,3 +169,34 @@ def test_integer_translation_exact_shift_on_gpu():
     s2 = g[1][m[1]:H - m[1], m[0]:Wd - m[0]]
     s1 = g[0][m[1] - b:H - m[1] - b, m[0] - a:Wd - m[0] - a]
     assert np.array_equal(s1, s2)
+
+
+def test_dense_overlap_checked_adds():
+    # every 8x8 block of the accumulator is met by far more than 63 windows:
+    # the splat takes its checked path (pixel sums stay below 64 i_max)
+    flows = [W.fourier_flow(40, 40, 40, 40, rms=1.0, seed=21)]
+    p = _small(40, 40, 1600, d_min=4.0, d_max=8.0, noise_sigma=0.01, blur_sigma=0.7)
+    wl = _wl([p], flows)
+    ref = oracle_render(wl)
+    outs = [gpu_render(wl, tile=t) for t in (16, 32, 64)]
+    st = compare(wl, outs[0], ref)
+    print("dense checked", st, "max S", float(ref[0]["S"].max()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[1][0], outs[2][0])
+
+
+def test_pixel_sums_beyond_64_imax_carry_exactly():
+    # pixel sums well above 64 i_max wrap the 32-bit words; the carries keep
+    # them exact (compared in float output, gain 1, no epilogue)
+    flows = [W.zero_flow(32, 32)]
+    p = _small(32, 32, 4096, d_min=8.0, d_max=10.0, sheet_sigma=0.0)
+    wl = _wl([p], flows)
+    ref = oracle_render(wl)
+    assert ref[0]["S"].max() > 64.0
+    outs = [gpu_render(wl, tile=t) for t in (16, 32)]
+    st = compare(wl, outs[0], ref)
+    print("carries", st, "max S", float(ref[0]["S"].max()))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    for inter in ("f16", "bf16"):  # the 16-bit path reads the same words
+        g = gpu_render(wl, tile=16, inter_dtype=inter)
+        rel = np.abs(g[0] - ref[0]["B"]) / np.maximum(np.abs(ref[0]["B"]), 1.0)
+        assert rel.max() < {"f16": 2.0 ** -10, "bf16": 2.0 ** -7}[inter] + 1e-4
