@@ -20,6 +20,22 @@ __device__ __forceinline__ int upper_find(int n, int64_t key, F base) {
     return lo;
 }
 
+// The same search by a whole block, for a key common to the block: thread
+// t tests the bases m = t, t + blockDim, ... with independent loads (one
+// memory round trip instead of log2(n) dependent ones); the one m with
+// base(m) <= key < base(m + 1) is the answer.  Ends with a barrier.
+template <typename F>
+__device__ __forceinline__ int block_upper_find(int n, int64_t key, F base) {
+    __shared__ int s_found;
+    for (int m = threadIdx.x; m < n; m += blockDim.x) {
+        const int64_t b0 = base(m);
+        const int64_t b1 = m + 1 < n ? base(m + 1) : INT64_MAX;
+        if (b0 <= key && key < b1) s_found = m;
+    }
+    __syncthreads();
+    return s_found;
+}
+
 struct Flow {
     const float2 *f;
     int32_t gh, gw, H, W;

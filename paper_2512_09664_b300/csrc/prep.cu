@@ -124,11 +124,7 @@ struct ChunkCtx {
 // The chunk of this CTA: pair (largest b with chunk_base(b) <= blockIdx.x),
 // descriptor and plan in shared memory.  Ends with a barrier.
 __device__ __forceinline__ void load_chunk(const KernelArgs &a, ChunkCtx &c) {
-    __shared__ int32_t s_pair;
-    if (threadIdx.x == 0)
-        s_pair = upper_find(a.n_pairs, (int64_t)blockIdx.x, [&](int m) { return (int64_t)a.plan[m].chunk_base; });
-    __syncthreads();
-    const int b = s_pair;
+    const int b = block_upper_find(a.n_pairs, (int64_t)blockIdx.x, [&](int m) { return (int64_t)a.plan[m].chunk_base; });
     if (threadIdx.x < 8)
         reinterpret_cast<int4 *>(&c.d)[threadIdx.x] = reinterpret_cast<const int4 *>(a.descs + b)[threadIdx.x];
     else if (threadIdx.x < 12)
@@ -354,11 +350,7 @@ __device__ __forceinline__ TileCtx frame1_tile(const KernelArgs &a, const PairPl
 }
 
 __device__ __forceinline__ int frame1_pair(const KernelArgs &a) {
-    __shared__ int32_t s_b;
-    if (threadIdx.x == 0)
-        s_b = upper_find(a.n_pairs, (int64_t)blockIdx.x, [&](int m) { return (int64_t)(a.plan[m].tile_base >> 1); });
-    __syncthreads();
-    return s_b;
+    return block_upper_find(a.n_pairs, (int64_t)blockIdx.x, [&](int m) { return (int64_t)(a.plan[m].tile_base >> 1); });
 }
 
 // Calls put(k, tile) for each frame-2 tile of advected record r; k = index of
@@ -405,11 +397,16 @@ __global__ void __launch_bounds__(kAdvThreads) k_advect(KernelArgs a) {
     Wn.nh = min(max(k1 + 1, 0), F.gh - 1) - Wn.gy0 + 1;
     if (Wn.nw * Wn.nh > adv_window_nodes(a.tile)) Wn.nw = Wn.nh = 0;  // finer grid than fits: all lookups global
     for (int i = threadIdx.x; i < kNbrSide * kNbrSide; i += kAdvThreads) s_nb[i] = 0u;
-    // a warp per row: consecutive lanes read consecutive nodes (coalesced 8-byte loads)
+    // a warp per row: consecutive lanes copy consecutive nodes (coalesced 8-byte
+    // asynchronous copies, all in flight at once; waited for before the barrier below)
     for (int r = threadIdx.x >> 5; r < Wn.nh; r += kAdvThreads / 32) {
         const float2 *src = F.f + (size_t)(Wn.gy0 + r) * F.gw + Wn.gx0;
-        for (int q = threadIdx.x & 31; q < Wn.nw; q += 32) s_flow[r * Wn.nw + q] = __ldg(src + q);
+        for (int q = threadIdx.x & 31; q < Wn.nw; q += 32) {
+            const unsigned d = (unsigned)__cvta_generic_to_shared(s_flow + r * Wn.nw + q);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src + q) : "memory");
+        }
     }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
     uint32_t *cnt2 = a.count + pl.tile_base + pl.ntiles;
     for (uint32_t base = 0; base < c.it.count; base += kAdvBatch) {
         // compact this batch's home particles (integer position inside the tile); the others are
@@ -423,6 +420,7 @@ __global__ void __launch_bounds__(kAdvThreads) k_advect(KernelArgs a) {
             else
                 s_home[atomicAdd(&s_nhome, 1u)] = (uint16_t)(k - base);
         }
+        asm volatile("cp.async.wait_all;\n" ::: "memory");  // the flow window (overlapped with the compaction)
         __syncthreads();
         for (uint32_t h = threadIdx.x; h < s_nhome; h += kAdvThreads) {
             const uint32_t k = base + s_home[h];
@@ -449,6 +447,7 @@ __global__ void __launch_bounds__(kAdvThreads) k_advect(KernelArgs a) {
         }
         __syncthreads();
     }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");  // an empty bin never waited for the window
     for (int i = threadIdx.x; i < kNbrSide * kNbrSide; i += kAdvThreads) {
         if (!s_nb[i]) continue;
         const int ty = c.ty + i / kNbrSide - kNbr, tx = c.tx + i % kNbrSide - kNbr;

@@ -874,7 +874,7 @@ __device__ __forceinline__ void finish_pass1(const KernelArgs &a, const Geo &g, 
 template <typename T>
 __device__ __forceinline__ void finish_rest(const KernelArgs &a, const Geo &g, const synthpix_pair_desc &D,
                                             const float *wtab, int frame, const Smem &s) {
-    if (g.R > 0 && (g.fx0 < 0 || g.fy0 < 0 || g.x1 + g.R > g.W || g.y1 + g.R > g.H)) {
+    if (g.R > 0 && (g.fx0 < 0 || g.fy0 < 0 || g.x1 + g.R > g.W || g.y1 + g.R > g.H)) {  // uniform
         const float ifw = 1.0f / (float)g.FW;
         const int cx = g.fx0 - g.afx0;  // A column of frame column fx0
         for (int k = threadIdx.x; k < g.FH * g.FW; k += blockDim.x) {
@@ -885,8 +885,8 @@ __device__ __forceinline__ void finish_rest(const KernelArgs &a, const Geo &g, c
                 s.A[r * g.AP + cx + c] = s.A[ci * g.AP + cx + cj];
             }
         }
+        __syncthreads();
     }
-    __syncthreads();
     const int64_t HW = (int64_t)g.H * g.W;
     // the tile's first output pixel; stores add 32-bit row / column offsets
     T *out = reinterpret_cast<T *>(a.images) + D.image_offset + (int64_t)frame * HW + (int64_t)g.y0 * g.W + g.x0;
@@ -914,8 +914,8 @@ __device__ __forceinline__ __nv_bfloat16 to_inter<__nv_bfloat16>(float v) { retu
 // its blur halo and finish it on chip.  Otherwise splat the tile alone and
 // store S in 16 bits to the intermediate frames; k_finish does the rest.
 // Thread 0 reads the work item of ticket t2 into `after` once the splat is
-// done (the ticket's atomic has long returned by then), so the read's
-// latency hides behind the finishing steps.
+// done (the ticket was taken an item earlier), so the read's latency hides
+// behind the finishing steps.
 template <typename T, int NT>
 __device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo &it, unsigned char *buf,
                                              uint32_t cap, const Smem &s, uint32_t t2, ItemInfo &after) {
@@ -1033,6 +1033,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_splat(KernelArgs a) {
     unsigned char *bufs = smem + L.bufs;
     const uint32_t cap = (uint32_t)kRecCap;
     for (int k = threadIdx.x; k < 2 * co; k += blockDim.x) s.acc[k] = 0u;
+    // work queue: the current item, the next one (staged while the current
+    // one renders) and the ticket of the one after (its item read during
+    // the current item); tickets only grow, so a CTA never drops a valid one
+    uint32_t t_pending = 0;
     if (threadIdx.x == 0) {
         s_wrap = 0;
         for (int q = 0; q < 2; ++q) {
@@ -1042,6 +1046,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_splat(KernelArgs a) {
             else it.pair = -1;
             s_item[q] = it;
         }
+        t_pending = atomicAdd(a.ticket, 1u);
     }
     __syncthreads();
     if (s_item[0].pair < 0) return;
@@ -1063,8 +1068,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_splat(KernelArgs a) {
             stage_records(a, nx.rec0, min(nx.count, cap), bnext + kStageHeader);
         }
         cp_async_commit();
-        uint32_t t2 = 0;
-        if (threadIdx.x == 0) t2 = atomicAdd(a.ticket, 1u);
+        const uint32_t t2 = t_pending;
+        if (threadIdx.x == 0) t_pending = atomicAdd(a.ticket, 1u);  // returns while this item renders
         ItemInfo after;
         process_item<T, NT>(a, it, bufs + cur * a.rec_buf_bytes, cap, s, t2, after);
         if (threadIdx.x == 0) s_item[cur] = after;
