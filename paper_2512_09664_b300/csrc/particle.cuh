@@ -241,4 +241,30 @@ __device__ __forceinline__ float2 velocity_windowed(const Flow &F, const FlowWin
     return make_float2(fmaf(ty, bu - tu, tu), fmaf(ty, bv - tv, tv));
 }
 
+// velocity() for a grid with the image's resolution (gw = W, gh = H), the
+// common case: the node below the position is (ix + floor(fx - 1/2),
+// iy + floor(fy - 1/2)).  When it and its three neighbours lie in the staged
+// window, they are read from shared memory with one row offset; otherwise
+// (window edge, grid border clamping) velocity() reads the grid.  The
+// nodes and the arithmetic are those of velocity(), so the result is
+// identical.
+__device__ __forceinline__ float2 velocity_tile(const Flow &F, const FlowWindow &Wn, int32_t ix, float fx,
+                                                int32_t iy, float fy) {
+    const float gx = fx - 0.5f, gy = fy - 0.5f;
+    const float flx = floorf(gx), fly = floorf(gy);
+    const float tx = gx - flx, ty = gy - fly;
+    // small integral floats to int without the conversion unit (|fl| < 2^22)
+    const int32_t u = ix - Wn.gx0 + (__float_as_int(flx + 12582912.0f) - 0x4B400000);
+    const int32_t v = iy - Wn.gy0 + (__float_as_int(fly + 12582912.0f) - 0x4B400000);
+    const unsigned lx = Wn.nw > 1 ? (unsigned)(Wn.nw - 1) : 0u, ly = Wn.nh > 1 ? (unsigned)(Wn.nh - 1) : 0u;
+    if ((unsigned)u < lx && (unsigned)v < ly) {
+        const float2 *p = Wn.s + v * Wn.nw + u;
+        const float2 a = p[0], b = p[1], c = p[Wn.nw], d = p[Wn.nw + 1];
+        const float tu = fmaf(tx, b.x - a.x, a.x), tv = fmaf(tx, b.y - a.y, a.y);
+        const float bu = fmaf(tx, d.x - c.x, c.x), bv = fmaf(tx, d.y - c.y, c.y);
+        return make_float2(fmaf(ty, bu - tu, tu), fmaf(ty, bv - tv, tv));
+    }
+    return velocity(F, ix, fx, iy, fy);
+}
+
 }  // namespace spx

@@ -408,6 +408,7 @@ __global__ void __launch_bounds__(kAdvThreads) k_advect(KernelArgs a) {
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     uint32_t *cnt2 = a.count + pl.tile_base + pl.ntiles;
+    const bool same_res = F.gw == F.W && F.gh == F.H;
     for (uint32_t base = 0; base < c.it.count; base += kAdvBatch) {
         // compact this batch's home particles (integer position inside the tile); the others are
         // advected by their own home tile and marked here
@@ -434,9 +435,14 @@ __global__ void __launch_bounds__(kAdvThreads) k_advect(KernelArgs a) {
             r.iy = __float_as_int(p1.y);
             r.sigma = p2.x;
             r.amp = p2.y;
-            advect_split_with(
-                [&](int32_t ix, float fx, int32_t iy, float fy) { return velocity_windowed(F, Wn, ix, fx, iy, fy); },
-                a.dt, a.n_substeps, a.integrator, r.ix, r.fx, r.iy, r.fy);
+            if (same_res)
+                advect_split_with(
+                    [&](int32_t ix, float fx, int32_t iy, float fy) { return velocity_tile(F, Wn, ix, fx, iy, fy); },
+                    a.dt, a.n_substeps, a.integrator, r.ix, r.fx, r.iy, r.fy);
+            else
+                advect_split_with(
+                    [&](int32_t ix, float fx, int32_t iy, float fy) { return velocity_windowed(F, Wn, ix, fx, iy, fy); },
+                    a.dt, a.n_substeps, a.integrator, r.ix, r.fx, r.iy, r.fy);
             o[0] = make_float2(r.fx, r.fy);
             o[1] = make_float2(__int_as_float(r.ix), __int_as_float(r.iy));
             o[2] = make_float2(r.sigma, r.amp);

@@ -243,7 +243,7 @@ __device__ __forceinline__ void splat_group(const Visit &v, const Acc &A, const 
 
 // Windows with more than 30 edges: per-warp scratch in shared memory.
 template <bool CHECKED>
-__device__ __noinline__ void splat_particle_wide(const Acc &A, float px, float py, float inv,
+__device__ __noinline__ void splat_particle_wide(const Acc A, float px, float py, float inv,
                                                  float amps, int32_t base, int bx, int by, int nx, int ny,
                                                  float *scr, int wq, const float4 *tab) {
     const int lane = threadIdx.x & 31;
