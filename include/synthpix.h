@@ -110,9 +110,12 @@ typedef struct synthpix_batch_desc {
     int32_t  integrator;         /* SYNTHPIX_RK4 or SYNTHPIX_EULER                      */
     int32_t  n_substeps;         /* substeps over dt, 1..1024                          */
     float    dt;                 /* time between the frames, in frames (|dt| <= 64)    */
-    int32_t  tile;               /* square screen tile edge: 16, 32 or 64, or 0 for a
-                                    default from the frame sizes (64 when the mean
-                                    frame area is >= 256x256, else 32)                 */
+    int32_t  tile;               /* square screen tile edge: 16, 32, 64 or 128, or 0
+                                    for a default from the frame sizes (128 when the
+                                    mean frame area is >= 512x512, 64 when >= 256x256,
+                                    else 32).  Tile 128 fails with
+                                    SYNTHPIX_EUNSUPPORTED when the largest blur radius
+                                    needs more shared memory than a CTA has.           */
     int32_t  flags;              /* 0 or SYNTHPIX_FLAG_GATHER_ADVECT.  By default a
                                     seeded render advects the particles tile by tile:
                                     the flow nodes under each frame-1 tile are staged
@@ -253,7 +256,8 @@ int synthpix_render_pairs_noalloc(const synthpix_batch_desc *batch, const synthp
 
 /*
  * Autotuner of the screen tile edge (a scheduling parameter; the paper has no
- * counterpart).  Renders the batch with each candidate edge (16, 32, 64):
+ * counterpart).  Renders the batch with each candidate edge (16, 32, 64,
+ * 128; edges whose shared memory does not fit the blur radius are skipped):
  * once to warm up, then `reps` (1..1000) timed times on `stream`, timed with
  * CUDA events, and returns the fastest edge in *best_tile and its mean time
  * per render in *best_ms (nullable).  The images are overwritten.  The

@@ -49,8 +49,8 @@ int check_batch(const synthpix_batch_desc *b) {
     if (b->n_substeps < 1 || b->n_substeps > 1024)
         return fail(SYNTHPIX_EINVAL, "n_substeps %d outside 1..1024", b->n_substeps);
     if (!finite(b->dt) || std::fabs(b->dt) > 64.0f) return fail(SYNTHPIX_EINVAL, "dt must be finite with |dt| <= 64");
-    if (b->tile != 0 && b->tile != 16 && b->tile != 32 && b->tile != 64)
-        return fail(SYNTHPIX_EINVAL, "tile %d is not 0, 16, 32 or 64", b->tile);
+    if (b->tile != 0 && b->tile != 16 && b->tile != 32 && b->tile != 64 && b->tile != 128)
+        return fail(SYNTHPIX_EINVAL, "tile %d is not 0, 16, 32, 64 or 128", b->tile);
     if (b->flags & ~SYNTHPIX_FLAG_GATHER_ADVECT)
         return fail(SYNTHPIX_EUNSUPPORTED, "unknown flags 0x%x", b->flags);
     for (int k = 0; k < 6; ++k)
@@ -87,13 +87,15 @@ int check_pair(const synthpix_pair_desc &d, int b) {
     return SYNTHPIX_OK;
 }
 
-// Tile edge used when batch->tile is 0: 64 when the batch's mean frame area
-// is at least 256 x 256 (fewer particles rendered twice at tile borders),
-// else 32 (more work items for small frames).
+// Tile edge used when batch->tile is 0, by the batch's mean frame area:
+// 128 from 512 x 512 up, 64 from 256 x 256 up (fewer particles rendered
+// twice at tile borders, fewer work items), else 32 (enough work items for
+// small frames).
 int default_tile(const synthpix_pair_desc *pairs, int32_t n_pairs) {
     double area = 0.0;
     for (int32_t b = 0; b < n_pairs; ++b) area += (double)pairs[b].height * pairs[b].width;
-    return (n_pairs > 0 && area / n_pairs >= 65536.0) ? 64 : 32;
+    const double mean = n_pairs > 0 ? area / n_pairs : 0.0;
+    return mean >= 262144.0 ? 128 : (mean >= 65536.0 ? 64 : 32);
 }
 
 int make_plan_tile(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs, int32_t n_pairs, int tile,
@@ -165,7 +167,7 @@ size_t elem_size(int32_t dt) {
     }
 }
 
-constexpr int kTileCandidates[3] = {16, 32, 64};
+constexpr int kTileCandidates[4] = {16, 32, 64, 128};
 
 }  // namespace
 
@@ -296,7 +298,7 @@ static int run(Mode mode, const synthpix_batch_desc *batch, const synthpix_pair_
     a.adv = reinterpret_cast<spx::Record *>(ws + L.adv);
     a.tiled = (mode == Mode::Render && !x.particles_in && !(batch->flags & SYNTHPIX_FLAG_GATHER_ADVECT)) ? 1 : 0;
     a.ticket = ticket;
-    a.rec_buf_bytes = spx::kRecBufBytes;
+    a.rec_buf_bytes = spx::rec_buf_bytes_for(P.tile);
     a.blur_w = blur_w;
     a.inter_dtype = batch->inter_dtype;
     a.inter = ws + L.inter;
@@ -318,7 +320,7 @@ static int run(Mode mode, const synthpix_batch_desc *batch, const synthpix_pair_
         if (e == cudaSuccess) e = spx::launch_adjoint(a, st);
         if (e != cudaSuccess) return fail(SYNTHPIX_ECUDA, "adjoint launch: %s", cudaGetErrorString(e));
     } else {
-        if (spx::splat_smem_bytes(a.smem_edge, a.tile, a.warp_scratch, a.rec_buf_bytes) > 227 * 1024)
+        if (spx::splat_smem_bytes(a.smem_edge, a.tile, a.warp_scratch, a.rec_buf_bytes) > spx::kMaxSmemBytes)
             return fail(SYNTHPIX_EUNSUPPORTED, "tile %d with blur radius %d needs too much shared memory", P.tile,
                         P.max_r);
         e = spx::launch_prep(a, st, ev);
@@ -366,6 +368,10 @@ int synthpix_autotune_tile(const synthpix_batch_desc *batch, const synthpix_pair
     for (int t : kTileCandidates) {
         b.tile = t;
         rc = render_impl(&b, pairs, pairs_dev, n_pairs, flows, images, workspace, workspace_bytes, stream, nullptr);
+        if (rc == SYNTHPIX_EUNSUPPORTED) {  // this edge does not fit the blur radius on chip: try the others
+            rc = SYNTHPIX_OK;
+            continue;
+        }
         if (rc) break;  // warm-up; also validates the workspace for this tile
         cudaEventRecord(e0, st);
         for (int k = 0; k < reps && !rc; ++k)
@@ -387,6 +393,7 @@ int synthpix_autotune_tile(const synthpix_batch_desc *batch, const synthpix_pair
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
+    if (best < 0.0f) return fail(SYNTHPIX_EUNSUPPORTED, "autotune: no tile edge fits the batch's blur radius on chip");
     *best_tile = best_t;
     if (best_ms) *best_ms = best;
     g_err[0] = 0;

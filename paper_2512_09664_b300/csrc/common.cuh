@@ -147,8 +147,8 @@ __device__ __forceinline__ void split_add(int32_t &i, float &f, float d) {
     int32_t ni = (int32_t)fminf(fmaxf(n, -1.0e9f), 1.0e9f);
     if (r >= 1.0f) { r = __fsub_rn(r, 1.0f); ni += 1; }
     else if (r < 0.0f) { r = __fadd_rn(r, 1.0f); ni -= 1; }
-    long long t = (long long)i + ni;
-    i = (int32_t)(t > 1000000000LL ? 1000000000LL : (t < -1000000000LL ? -1000000000LL : t));
+    // |i|, |ni| <= 1e9: the sum fits in int32
+    i = min(max(i + ni, -1000000000), 1000000000);
     f = r;
 }
 

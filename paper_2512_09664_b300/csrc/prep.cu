@@ -370,7 +370,9 @@ __device__ __forceinline__ void frame2_tiles(const KernelArgs &a, const PairPlan
         }
 }
 
-__global__ void __launch_bounds__(kAdvThreads) k_advect(KernelArgs a) {
+// NT threads: 256, or 1024 at tile 128 (one CTA per SM with its larger window).
+template <int NT>
+__global__ void __launch_bounds__(NT) k_advect(KernelArgs a) {
     if (*a.check != 1) return;
     extern __shared__ __align__(16) float2 s_flow[];
     __shared__ uint32_t s_nb[kNbrSide * kNbrSide];
@@ -396,10 +398,10 @@ __global__ void __launch_bounds__(kAdvThreads) k_advect(KernelArgs a) {
     Wn.nw = min(max(l1 + 1, 0), F.gw - 1) - Wn.gx0 + 1;
     Wn.nh = min(max(k1 + 1, 0), F.gh - 1) - Wn.gy0 + 1;
     if (Wn.nw * Wn.nh > adv_window_nodes(a.tile)) Wn.nw = Wn.nh = 0;  // finer grid than fits: all lookups global
-    for (int i = threadIdx.x; i < kNbrSide * kNbrSide; i += kAdvThreads) s_nb[i] = 0u;
+    for (int i = threadIdx.x; i < kNbrSide * kNbrSide; i += NT) s_nb[i] = 0u;
     // a warp per row: consecutive lanes copy consecutive nodes (coalesced 8-byte
     // asynchronous copies, all in flight at once; waited for before the barrier below)
-    for (int r = threadIdx.x >> 5; r < Wn.nh; r += kAdvThreads / 32) {
+    for (int r = threadIdx.x >> 5; r < Wn.nh; r += NT / 32) {
         const float2 *src = F.f + (size_t)(Wn.gy0 + r) * F.gw + Wn.gx0;
         for (int q = threadIdx.x & 31; q < Wn.nw; q += 32) {
             const unsigned d = (unsigned)__cvta_generic_to_shared(s_flow + r * Wn.nw + q);
@@ -414,7 +416,7 @@ __global__ void __launch_bounds__(kAdvThreads) k_advect(KernelArgs a) {
         // advected by their own home tile and marked here
         if (threadIdx.x == 0) s_nhome = 0u;
         __syncthreads();
-        for (uint32_t k = base + threadIdx.x; k < min(c.it.count, base + kAdvBatch); k += kAdvThreads) {
+        for (uint32_t k = base + threadIdx.x; k < min(c.it.count, base + kAdvBatch); k += NT) {
             const int2 ip = reinterpret_cast<const int2 *>(a.rec + c.it.rec0 + k)[1];
             if (ip.x < c.x0 || ip.x >= c.x1 || ip.y < c.y0 || ip.y >= c.y1)
                 reinterpret_cast<float2 *>(a.adv + c.adv0 + k)[2] = make_float2(-1.0f, 0.0f);
@@ -423,7 +425,7 @@ __global__ void __launch_bounds__(kAdvThreads) k_advect(KernelArgs a) {
         }
         asm volatile("cp.async.wait_all;\n" ::: "memory");  // the flow window (overlapped with the compaction)
         __syncthreads();
-        for (uint32_t h = threadIdx.x; h < s_nhome; h += kAdvThreads) {
+        for (uint32_t h = threadIdx.x; h < s_nhome; h += NT) {
             const uint32_t k = base + s_home[h];
             const float2 *rp = reinterpret_cast<const float2 *>(a.rec + c.it.rec0 + k);
             const float2 p0 = rp[0], p1 = rp[1], p2 = rp[2];
@@ -454,7 +456,7 @@ __global__ void __launch_bounds__(kAdvThreads) k_advect(KernelArgs a) {
         __syncthreads();
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");  // an empty bin never waited for the window
-    for (int i = threadIdx.x; i < kNbrSide * kNbrSide; i += kAdvThreads) {
+    for (int i = threadIdx.x; i < kNbrSide * kNbrSide; i += NT) {
         if (!s_nb[i]) continue;
         const int ty = c.ty + i / kNbrSide - kNbr, tx = c.tx + i % kNbrSide - kNbr;
         atomicAdd(cnt2 + ty * pl.tiles_x + tx, s_nb[i]);
@@ -548,12 +550,17 @@ cudaError_t launch_prep(const KernelArgs &a, cudaStream_t st, cudaEvent_t const 
     // seeded render: seed + frame-1 bins, tiled advection, frame-2 bins
     const unsigned nt1 = (unsigned)(a.n_tiles / 2);
     const size_t adv_smem = (size_t)adv_window_nodes(a.tile) * sizeof(float2);
-    cudaError_t e = cudaFuncSetAttribute(k_advect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adv_smem);
+    const bool big = a.tile >= 128;
+    cudaError_t e = big ? cudaFuncSetAttribute(k_advect<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adv_smem)
+                        : cudaFuncSetAttribute(k_advect<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adv_smem);
     if (e != cudaSuccess) return e;
     if (nb > 0) k_seed_advect<<<nb, kPrepThreads, 0, st>>>(a);
     k_scan<<<a.n_pairs, 1024, 0, st>>>(a, 0);
     if (nb > 0) k_scatter<<<nb, kPrepThreads, 0, st>>>(a);
-    if (nt1 > 0) k_advect<<<nt1, kAdvThreads, adv_smem, st>>>(a);
+    if (nt1 > 0) {
+        if (big) k_advect<1024><<<nt1, 1024, adv_smem, st>>>(a);
+        else k_advect<256><<<nt1, 256, adv_smem, st>>>(a);
+    }
     mark(2);
     k_scan<<<a.n_pairs, 1024, 0, st>>>(a, 1);
     mark(3);

@@ -79,7 +79,7 @@ constexpr float kFixedUnit = 1.0f / 67108864.0f;
 constexpr float kWrapValue = 4294967296.0f;     // 2^32: the weight of a carry
 constexpr uint32_t kSafeVisits = 63;            // visits per block that cannot wrap a word
 constexpr int kBlkShift = 3;                    // 8 x 8 pixel blocks
-constexpr int kBlkSide = 16;                    // blocks per side of the counter grid (edge <= 128)
+constexpr int kBlkSide = 24;                    // blocks per side of the counter grid (row pitch <= 192)
 
 // Tile geometry of one work item.  The accumulator covers the halo-widened
 // rectangle clipped to the frame, from column ax0 (ex0 rounded down to a
@@ -99,12 +99,27 @@ struct Geo {
     int32_t afx0, AP;            // finishing buffer: first column, row pitch
 };
 
+// Visit classes of the splat's sort (see splat_chunk): windows of at most
+// 2 (c + 1) pixels a side for c < kWideClass, wider ones in kWideClass;
+// 32 accumulator-bank buckets per class.
+constexpr int kNarrowMax = 16;
+constexpr int kWideClass = kNarrowMax / 2;
+constexpr int kBuckets = (kWideClass + 1) * 32;
+
+// Sort and work-queue state of a k_splat CTA (static shared memory).
+__shared__ uint32_t sh_cnt[kBuckets];              // visits of the chunk per (class, bank) key
+__shared__ uint32_t sh_off[kBuckets + 1];          // their exclusive offsets
+__shared__ uint32_t sh_next;                       // warp-slot ticket of the chunk's render
+__shared__ uint32_t sh_blk[kBlkSide * kBlkSide];  // visits of the item so far per 8 x 8 block
+__shared__ int sh_checked;                         // the chunk takes the checked path
+__shared__ int sh_carry_clean;                     // the item's carry words are zero
+__shared__ int sh_wrap;                            // a checked add wrapped a word in this item
+
 // The tile's accumulator as the splat sees it.
 struct Acc {
     uint32_t *acc;  // [rows][P] words; carry words at acc + co
     int co;
     int P;
-    int *wrap;      // set when a checked add wrapped a word
 };
 
 // Add one contribution to the word at w (a pixel of A).
@@ -118,7 +133,7 @@ __device__ __forceinline__ void add_contrib(uint32_t *w, const Acc &A, float mx,
     const uint32_t old = atomicAdd(w, l);
     if (old + l < old) {
         atomicAdd(w + A.co, 1u);
-        *A.wrap = 1;
+        sh_wrap = 1;
     }
 }
 
@@ -179,9 +194,6 @@ __device__ __forceinline__ int visit_ny(uint32_t s) { return (int)(s >> 24); }
 // Class 8 holds the wider windows, rendered by a whole warp per visit.  The
 // visits of one warp are spread over the bank order, so their accumulator
 // addresses fall in different banks.
-constexpr int kNarrowMax = 16;
-constexpr int kWideClass = kNarrowMax / 2;
-constexpr int kBuckets = (kWideClass + 1) * 32;
 __host__ __device__ constexpr int class_lanes(int c) { return c < 2 ? 1 : (c < 4 ? 2 : 4); }
 __host__ __device__ constexpr int class_rows(int c) { return c == 0 ? 2 : (c == 2 || c == 4 || c == 5 ? 3 : 4); }
 
@@ -311,14 +323,6 @@ __device__ __forceinline__ void splat_coop(const Visit &v, bool valid, const Acc
     }
 }
 
-// Counters of the per-chunk visit sort (static shared memory of k_splat).
-struct SortSmem {
-    uint32_t *cnt;   // [kBuckets] visits per (class, bank) key
-    uint32_t *off;   // [kBuckets + 1] exclusive offsets
-    uint32_t *blk;   // [kBlkSide^2] visits of the item so far per 8 x 8 block
-    int *checked;    // the chunk takes the checked path
-    uint32_t *next;  // warp-slot ticket
-};
 
 // Splat n staged records (at recs) into the tile's accumulator:
 //   A. each thread sets up its records' visits (window clipped to the halo
@@ -331,9 +335,9 @@ struct SortSmem {
 //      (checked: every visit by a whole warp, with checked adds).
 template <int NT>
 __device__ __forceinline__ void splat_chunk(const unsigned char *recs, unsigned char *out, uint32_t n, const Geo &g,
-                                            float scale, const Acc &acc, const SortSmem &ss, float *scr,
+                                            float scale, const Acc &acc, float *scr,
                                             int wq, const float4 *tab) {
-    constexpr int RPT = (kRecCap + NT - 1) / NT;
+    constexpr int RPT = (rec_cap(NT >= 1024 ? kRecBufBytesLarge : kRecBufBytes) + NT - 1) / NT;
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
     Visit v[RPT];
@@ -366,11 +370,11 @@ __device__ __forceinline__ void splat_chunk(const unsigned char *recs, unsigned 
                 const int m = max(nx, ny);
                 const int cls = m > kNarrowMax ? kWideClass : (m - 1) >> 1;
                 key[q] = cls * 32 + (v[q].base & 31);
-                slot[q] = atomicAdd(ss.cnt + key[q], 1u);
+                slot[q] = atomicAdd(sh_cnt + key[q], 1u);
                 const int bx0 = (j0 - g.ax0) >> kBlkShift, bx1 = (j1 - g.ax0) >> kBlkShift;
                 const int by0 = (i0 - g.ey0) >> kBlkShift, by1 = (i1 - g.ey0) >> kBlkShift;
                 for (int by = by0; by <= by1; ++by)
-                    for (int bx = bx0; bx <= bx1; ++bx) atomicAdd(ss.blk + by * kBlkSide + bx, 1u);
+                    for (int bx = bx0; bx <= bx1; ++bx) atomicAdd(sh_blk + by * kBlkSide + bx, 1u);
             }
         }
     }
@@ -380,8 +384,8 @@ __device__ __forceinline__ void splat_chunk(const unsigned char *recs, unsigned 
         uint32_t c[PER], sum = 0;
 #pragma unroll
         for (int j = 0; j < PER; ++j) {
-            c[j] = ss.cnt[lane * PER + j];
-            ss.cnt[lane * PER + j] = 0;
+            c[j] = sh_cnt[lane * PER + j];
+            sh_cnt[lane * PER + j] = 0;
             sum += c[j];
         }
         uint32_t incl = sum;
@@ -393,35 +397,41 @@ __device__ __forceinline__ void splat_chunk(const unsigned char *recs, unsigned 
         uint32_t run = incl - sum;
 #pragma unroll
         for (int j = 0; j < PER; ++j) {
-            ss.off[lane * PER + j] = run;
+            sh_off[lane * PER + j] = run;
             run += c[j];
         }
-        if (lane == 31) ss.off[kBuckets] = incl;
-        if (lane == 0) *ss.next = 0;
+        if (lane == 31) sh_off[kBuckets] = incl;
+        if (lane == 0) sh_next = 0;
         uint32_t mx = 0;
 #pragma unroll
-        for (int j = 0; j < kBlkSide * kBlkSide / 32; ++j) mx = max(mx, ss.blk[lane + 32 * j]);
+        for (int j = 0; j < kBlkSide * kBlkSide / 32; ++j) mx = max(mx, sh_blk[lane + 32 * j]);
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) mx = max(mx, __shfl_xor_sync(FULL, mx, d));
-        if (lane == 0) *ss.checked = mx > kSafeVisits ? 1 : 0;
+        if (lane == 0) sh_checked = mx > kSafeVisits ? 1 : 0;
     }
     __syncthreads();
     float2 *o8 = reinterpret_cast<float2 *>(out);  // 16-byte aligned; a Visit is three 8-byte words
+    const bool chk = sh_checked != 0;
+    if (chk && !sh_carry_clean) {  // the carry words share memory with the finishing buffer: clear them
+        uint4 *cw = reinterpret_cast<uint4 *>(acc.acc + acc.co);
+        for (int k = threadIdx.x; k < (g.EH * g.P) >> 2; k += blockDim.x) cw[k] = make_uint4(0u, 0u, 0u, 0u);
+    }
 #pragma unroll
     for (int q = 0; q < RPT; ++q) {
         if (key[q] >= 0) {
-            const uint32_t p = ss.off[key[q]] + slot[q];
+            const uint32_t p = sh_off[key[q]] + slot[q];
             o8[3 * p] = make_float2(v[q].px, v[q].py);
             o8[3 * p + 1] = make_float2(v[q].inv, v[q].amps);
             o8[3 * p + 2] = make_float2(__int_as_float(v[q].base), __uint_as_float(v[q].shape));
         }
     }
     __syncthreads();
-    if (*ss.checked) {  // dense item: a warp per visit, adds checked for wrapping
-        const uint32_t total = ss.off[kBuckets];
+    if (chk) {  // dense item: a warp per visit, adds checked for wrapping
+        if (threadIdx.x == 0) sh_carry_clean = 1;  // read again after this chunk's last barrier
+        const uint32_t total = sh_off[kBuckets];
         for (;;) {
             uint32_t sl = 0;
-            if (lane == 0) sl = atomicAdd(ss.next, 1u);
+            if (lane == 0) sl = atomicAdd(&sh_next, 1u);
             sl = __shfl_sync(FULL, sl, 0);
             if (sl * 32 >= total) break;
             const uint32_t idx = sl * 32 + lane;
@@ -445,13 +455,13 @@ __device__ __forceinline__ void splat_chunk(const unsigned char *recs, unsigned 
     }
     for (;;) {
         uint32_t sl = 0;
-        if (lane == 0) sl = atomicAdd(ss.next, 1u);
+        if (lane == 0) sl = atomicAdd(&sh_next, 1u);
         sl = __shfl_sync(FULL, sl, 0);
         int c = kWideClass;
         uint32_t g0 = 0, G = 0, nw = 0;
         for (; c >= 0; --c) {
-            g0 = ss.off[32 * c];
-            G = ss.off[32 * c + 32] - g0;
+            g0 = sh_off[32 * c];
+            G = sh_off[32 * c + 32] - g0;
             const uint32_t per = c == kWideClass ? 32u : 32u / (uint32_t)class_lanes(c);  // visits per slot
             nw = (G + per - 1) / per;
             if (sl < nw) break;
@@ -669,13 +679,12 @@ __device__ __forceinline__ void store_unblurred(const Geo &g, const float *A, T 
 // one work item
 // ---------------------------------------------------------------------------
 struct Smem {
-    uint32_t *acc;  // accumulator words; carry words at acc + co
+    uint32_t *acc;  // accumulator words; carry words at acc + co (the finishing buffer's memory)
     int co;
-    int *wrap;      // set by any add that wrapped a word (read after the splat)
     float *A, *Bh, *sx2, *sy2, *scr;
     const float4 *phi;
-    SortSmem sort;
     int BP;
+    bool bh_alias;  // Bh shares memory with the accumulator words (cleared again after the blur)
 };
 
 // Row pitch capacity of the accumulator and finishing buffer for a capacity
@@ -728,41 +737,39 @@ __device__ __forceinline__ bool illum_factors(const Geo &g, const synthpix_pair_
     return illum;
 }
 
-// S of the fused path: the accumulator words (and carry words when an add
-// wrapped), each cleared for the next item as it is read.  r: accumulator
-// row, c: column from ax0 (a multiple of 4 for quad()).
+// S of the fused path: the accumulator words, each cleared for the next
+// item as it is read.  r: accumulator row, c: column from ax0 (a multiple
+// of 4 for quad()).  When an add wrapped a word, the words were first
+// converted to S in place (float bits), carries included (wrapped_to_float).
 struct AccSource {
     uint32_t *acc;
-    int co, P;
-    float unit;  // i_max 2^-28
-    bool wrapped;
-    __device__ __forceinline__ float value(uint32_t v, uint32_t h) const {
-        return fmaf((float)h, kWrapValue, (float)v) * unit;
-    }
+    int P;
+    float unit;   // i_max 2^-26
+    bool floats;  // the words hold S as float bits
+    __device__ __forceinline__ float value(uint32_t v) const { return floats ? __uint_as_float(v) : (float)v * unit; }
     __device__ __forceinline__ float4 quad(int r, int c) const {
         uint4 *p = reinterpret_cast<uint4 *>(acc + r * P + c);
         const uint4 v = *p;
         *p = make_uint4(0u, 0u, 0u, 0u);
-        uint4 h = make_uint4(0u, 0u, 0u, 0u);
-        if (wrapped) {
-            uint4 *q = reinterpret_cast<uint4 *>(acc + co + r * P + c);
-            h = *q;
-            *q = make_uint4(0u, 0u, 0u, 0u);
-        }
-        return make_float4(value(v.x, h.x), value(v.y, h.y), value(v.z, h.z), value(v.w, h.w));
+        return make_float4(value(v.x), value(v.y), value(v.z), value(v.w));
     }
     __device__ __forceinline__ float pixel(int r, int c) const {
         uint32_t *p = acc + r * P + c;
         const uint32_t v = *p;
         *p = 0u;
-        uint32_t h = 0u;
-        if (wrapped) {
-            h = p[co];
-            p[co] = 0u;
-        }
-        return value(v, h);
+        return value(v);
     }
 };
+
+// A wrapped item: S = (word + carry 2^32) q written over the words, before
+// the finishing buffer (which holds the carry words) is written.  Ends with
+// a barrier.
+__device__ __forceinline__ void wrapped_to_float(const Smem &s, const Geo &g, float unit) {
+    const uint32_t *cw = s.acc + s.co;
+    for (int k = threadIdx.x; k < g.EH * g.P; k += blockDim.x)
+        s.acc[k] = __float_as_uint(fmaf((float)cw[k], kWrapValue, (float)s.acc[k]) * unit);
+    __syncthreads();
+}
 
 template <typename I>
 __device__ __forceinline__ float4 load4_inter(const I *p);
@@ -901,6 +908,11 @@ __device__ __forceinline__ void finish_rest(const KernelArgs &a, const Geo &g, c
     case 6: blur_store<T, 6>(g, s.A, s.Bh, s.BP, wtab, out, M); break;
     default: blur_store_any<T>(g, s.A, s.Bh, s.BP, wtab, out, M); break;
     }
+    if (g.R > 0 && s.bh_alias) {  // Bh lives in the accumulator words: clear them for the next item
+        __syncthreads();
+        float4 *b4 = reinterpret_cast<float4 *>(s.Bh);
+        for (int k = threadIdx.x; k < (g.FH * s.BP) >> 2; k += blockDim.x) b4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
 }
 
 template <typename I>
@@ -929,12 +941,12 @@ __device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo
     // splat, chunk by chunk of staged records
     const float imax = D.i_max > 0.0f ? D.i_max : 1.0f;
     const float scale = kFixedScale / imax;
-    const Acc acc{s.acc, s.co, g.P, s.wrap};
+    const Acc acc{s.acc, s.co, g.P};
     uint32_t done = 0;
     while (done < it.count) {
         const uint32_t n = min(it.count - done, cap);
         splat_chunk<NT>(buf + kStageHeader + record_lead(it.rec0 + done), buf + kStageHeader, n, g, scale, acc,
-                        s.sort, s.scr + (threadIdx.x >> 5) * a.warp_scratch, a.warp_scratch >> 2, s.phi);
+                        s.scr + (threadIdx.x >> 5) * a.warp_scratch, a.warp_scratch >> 2, s.phi);
         done += n;
         __syncthreads();
         if (done < it.count) {  // more records: stage the next chunk
@@ -946,13 +958,16 @@ __device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo
     }
     if (it.count == 0) __syncthreads();  // illumination factors
     // block counts of the next item start from zero (its first count comes after a barrier)
-    for (int k = threadIdx.x; k < kBlkSide * kBlkSide; k += blockDim.x) s.sort.blk[k] = 0u;
+    for (int k = threadIdx.x; k < kBlkSide * kBlkSide; k += blockDim.x) sh_blk[k] = 0u;
     if (threadIdx.x == 0) {
         if ((int64_t)t2 < a.n_tiles) after = a.items[t2];
         else after.pair = -1;
     }
 
-    const AccSource src{s.acc, s.co, g.P, imax * kFixedUnit, *s.wrap != 0};
+    const float unit = imax * kFixedUnit;
+    const bool wrapped = sh_wrap != 0;
+    if (wrapped) wrapped_to_float(s, g, unit);
+    const AccSource src{s.acc, g.P, unit, wrapped};
     if (!fused) {
         // halo 0: the accumulator rectangle is the tile (ax0 = ex0 = x0)
         const int64_t HW = (int64_t)g.H * g.W;
@@ -977,8 +992,14 @@ __device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo
 // ---------------------------------------------------------------------------
 struct SmemLayout {
     size_t acc, A, Bh, sx2, sy2, scr, phi, bufs, total;
+    bool bh_alias;
 };
 
+// The accumulator words; the finishing buffer A (which holds the carry words
+// during the splat); the horizontal-blur buffer Bh, in memory of its own when
+// that fits, else in the accumulator words (free between the first
+// finishing pass and the next item); illumination factors; per-warp window
+// scratch; the normal-tail table; two staged-record buffers.
 __host__ __device__ inline SmemLayout smem_layout(int E, int tile, int warp_scratch, int rec_buf_bytes) {
     SmemLayout L;
     const int BP = (tile + 3) & ~3;
@@ -989,14 +1010,16 @@ __host__ __device__ inline SmemLayout smem_layout(int E, int tile, int warp_scra
         o = (o + bytes + 15) & ~(size_t)15;
         return at;
     };
-    L.acc = take(2 * (size_t)E * PC * 4);  // words, then carry words
+    L.acc = take((size_t)E * PC * 4);
     L.A = take(((size_t)E * PC + 32) * 4);  // + padding read by the last row's blur loads
-    L.Bh = take((size_t)E * BP * 4);
     L.sx2 = take(PC * 4);
     L.sy2 = take((size_t)E * 4);
-    L.scr = take((size_t)(kSplatMaxThreads / 32) * warp_scratch * 4);
+    L.scr = take((size_t)(splat_threads(tile) / 32) * warp_scratch * 4);
     L.phi = take((size_t)(kPhiDegree + 1) * kPhiPieces * 4);
     L.bufs = take(2 * (size_t)rec_buf_bytes);
+    const size_t bh = (size_t)E * BP * 4;
+    L.bh_alias = o + bh > kMaxSmemBytes;
+    L.Bh = L.bh_alias ? L.acc : take(bh);
     L.total = o;
     return L;
 }
@@ -1006,14 +1029,12 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_splat(KernelArgs a) {
     if (*a.check != 1) return;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ ItemInfo s_item[2];
-    __shared__ uint32_t s_cnt[kBuckets], s_off[kBuckets + 1], s_next, s_blk[kBlkSide * kBlkSide];
-    __shared__ int s_wrap, s_checked;
     const SmemLayout L = smem_layout(a.smem_edge, a.tile, a.warp_scratch, a.rec_buf_bytes);
-    const int co = a.smem_edge * pitch_cap(a.smem_edge);
+    const int words = a.smem_edge * pitch_cap(a.smem_edge);
     Smem s;
     s.acc = reinterpret_cast<uint32_t *>(smem + L.acc);
-    s.co = co;
-    s.wrap = &s_wrap;
+    s.co = (int)((L.A - L.acc) / 4);
+    s.bh_alias = L.bh_alias;
     s.A = reinterpret_cast<float *>(smem + L.A);
     s.Bh = reinterpret_cast<float *>(smem + L.Bh);
     s.sx2 = reinterpret_cast<float *>(smem + L.sx2);
@@ -1022,23 +1043,18 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_splat(KernelArgs a) {
     float *phi = reinterpret_cast<float *>(smem + L.phi);
     for (int k = threadIdx.x; k < (kPhiDegree + 1) * kPhiPieces; k += blockDim.x) phi[k] = kPhiTable[k];
     s.phi = reinterpret_cast<const float4 *>(phi);
-    s.sort.cnt = s_cnt;
-    s.sort.off = s_off;
-    s.sort.next = &s_next;
-    s.sort.blk = s_blk;
-    s.sort.checked = &s_checked;
-    for (int k = threadIdx.x; k < kBuckets; k += blockDim.x) s_cnt[k] = 0;
-    for (int k = threadIdx.x; k < kBlkSide * kBlkSide; k += blockDim.x) s_blk[k] = 0;
+    for (int k = threadIdx.x; k < kBuckets; k += blockDim.x) sh_cnt[k] = 0;
+    for (int k = threadIdx.x; k < kBlkSide * kBlkSide; k += blockDim.x) sh_blk[k] = 0;
     s.BP = (a.tile + 3) & ~3;
     unsigned char *bufs = smem + L.bufs;
-    const uint32_t cap = (uint32_t)kRecCap;
-    for (int k = threadIdx.x; k < 2 * co; k += blockDim.x) s.acc[k] = 0u;
+    const uint32_t cap = (uint32_t)rec_cap(a.rec_buf_bytes);
+    for (int k = threadIdx.x; k < words; k += blockDim.x) s.acc[k] = 0u;
     // work queue: the current item, the next one (staged while the current
     // one renders) and the ticket of the one after (its item read during
     // the current item); tickets only grow, so a CTA never drops a valid one
     uint32_t t_pending = 0;
     if (threadIdx.x == 0) {
-        s_wrap = 0;
+        sh_wrap = 0;
         for (int q = 0; q < 2; ++q) {
             const uint32_t t = atomicAdd(a.ticket, 1u);
             ItemInfo it;
@@ -1061,7 +1077,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_splat(KernelArgs a) {
         __syncthreads();  // staged data of `it` visible; the other buffer is free; the wrap flag is read
         if (it.pair < 0) break;
         // the splat's first add comes after a barrier inside splat_chunk
-        if (threadIdx.x == 0) s_wrap = 0;
+        if (threadIdx.x == 0) {
+            sh_wrap = 0;
+            sh_carry_clean = 0;
+        }
         unsigned char *bnext = bufs + (cur ^ 1) * a.rec_buf_bytes;
         if (nx.pair >= 0) {
             stage_header(a, nx.pair, bnext);
@@ -1115,14 +1134,13 @@ __global__ void __launch_bounds__(kSplatThreads) k_finish(KernelArgs a) {
     Smem s;
     s.acc = nullptr;
     s.co = 0;
-    s.wrap = nullptr;
     s.A = reinterpret_cast<float *>(smem + FL.A);
     s.Bh = reinterpret_cast<float *>(smem + FL.Bh);
     s.sx2 = reinterpret_cast<float *>(smem + FL.sx2);
     s.sy2 = reinterpret_cast<float *>(smem + FL.sy2);
     s.scr = nullptr;
     s.phi = nullptr;
-    s.sort = SortSmem{nullptr, nullptr, nullptr, nullptr, nullptr};
+    s.bh_alias = false;
     s.BP = (a.tile + 3) & ~3;
     const ItemInfo it = a.items[blockIdx.x];
     const synthpix_pair_desc &D = a.descs[it.pair];
@@ -1150,24 +1168,22 @@ cudaError_t launch_splat(const KernelArgs &a, int32_t out_dtype, cudaStream_t st
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
+#define SPX_LAUNCH_NT(T, NT)                                                                                 \
+    do {                                                                                                     \
+        e = cudaFuncSetAttribute(k_splat<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
+        if (e != cudaSuccess) return e;                                                                      \
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_splat<T, NT>, NT, smem);                   \
+        if (e != cudaSuccess) return e;                                                                      \
+        const int64_t want = (int64_t)nsm * (occ > 0 ? occ : 1);                                             \
+        k_splat<T, NT><<<(unsigned)(a.n_tiles < want ? a.n_tiles : want), NT, smem, st>>>(a);                \
+    } while (0)
 #define SPX_LAUNCH(T)                                                                                        \
     do {                                                                                                     \
-        if (a.tile >= 64) {                                                                                  \
-            e = cudaFuncSetAttribute(k_splat<T, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);\
-            if (e != cudaSuccess) return e;                                                                  \
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_splat<T, 512>, 512, smem);             \
-            if (e != cudaSuccess) return e;                                                                  \
-            const int64_t want = (int64_t)nsm * (occ > 0 ? occ : 1);                                         \
-            k_splat<T, 512><<<(unsigned)(a.n_tiles < want ? a.n_tiles : want), 512, smem, st>>>(a);          \
-        } else {                                                                                             \
-            e = cudaFuncSetAttribute(k_splat<T, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);\
-            if (e != cudaSuccess) return e;                                                                  \
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_splat<T, 256>, 256, smem);             \
-            if (e != cudaSuccess) return e;                                                                  \
-            const int64_t want = (int64_t)nsm * (occ > 0 ? occ : 1);                                         \
-            k_splat<T, 256><<<(unsigned)(a.n_tiles < want ? a.n_tiles : want), 256, smem, st>>>(a);          \
-        }                                                                                                    \
+        if (nt == 1024) SPX_LAUNCH_NT(T, 1024);                                                              \
+        else if (nt == 512) SPX_LAUNCH_NT(T, 512);                                                           \
+        else SPX_LAUNCH_NT(T, 256);                                                                          \
     } while (0)
+    const int nt = splat_threads(a.tile);
     switch (out_dtype) {
     case SYNTHPIX_F32: SPX_LAUNCH(float); break;
     case SYNTHPIX_F16: SPX_LAUNCH(__half); break;
@@ -1176,6 +1192,7 @@ cudaError_t launch_splat(const KernelArgs &a, int32_t out_dtype, cudaStream_t st
     default: SPX_LAUNCH(uint16_t); break;
     }
 #undef SPX_LAUNCH
+#undef SPX_LAUNCH_NT
     if (a.inter_dtype != SYNTHPIX_F32) {
         const size_t fsm = finish_layout(a.smem_edge, a.tile).total;
         const unsigned grid = (unsigned)a.n_tiles;

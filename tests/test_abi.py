@@ -106,7 +106,7 @@ def test_zero_pairs_is_a_no_op():
 def test_auto_tile_workspace_covers_every_candidate():
     pk = _packed()
     auto = B.workspace_bytes(pk)
-    for t in (16, 32, 64):
+    for t in (16, 32, 64, 128):
         pk.batch.tile = t
         assert B.workspace_bytes(pk) <= auto
 

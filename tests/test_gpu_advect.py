@@ -40,7 +40,7 @@ def _workload(size, grid, rms, integ="rk4", n_sub=4, n_pairs=3, ppp=0.05, seed=2
                       integrator=integ, n_substeps=n_sub, dt=1.0)
 
 
-@pytest.mark.parametrize("tile", [16, 32, 64])
+@pytest.mark.parametrize("tile", [16, 32, 64, 128])
 def test_tiled_and_gather_advection_render_identically(tile):
     import torch
     cases = [
