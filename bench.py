@@ -265,21 +265,31 @@ def run_ours(args, rank, world, dist):
         flush.fill_(1)
         r.render()
     torch.cuda.synchronize()
-    events = [new_events() for _ in range(args.steps)]
-    torch.cuda.synchronize()
+    # timed steps: one event pair around each render (nothing between its launches)
+    events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     with ClockSampler(dev.index) as clk:
         barrier()
         torch.cuda.synchronize()
         for k in range(args.steps):
             flush.fill_(k & 0xFF)
-            r.render_staged(events[k])
+            events[k][0].record(stream)
+            r.render()
+            events[k][1].record(stream)
         torch.cuda.synchronize()
         barrier()
     clocks = clk.summary()
-    step_ms = [ev[0].elapsed_time(ev[5]) for ev in events]
-    stage_ms = {name: sum(ev[i].elapsed_time(ev[i + 1]) for ev in events) / args.steps
-                for i, name in enumerate(STAGES)}
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in events]
     total_ms = sum(step_ms)
+    # per-stage breakdown: a separate pass with events recorded by the library between its launches
+    n_staged = min(args.steps, 50)
+    staged = [new_events() for _ in range(n_staged)]
+    torch.cuda.synchronize()
+    for k in range(n_staged):
+        flush.fill_(k & 0xFF)
+        r.render_staged(staged[k])
+    torch.cuda.synchronize()
+    stage_ms = {name: sum(ev[i].elapsed_time(ev[i + 1]) for ev in staged) / n_staged
+                for i, name in enumerate(STAGES)}
     if dist is not None:
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -310,7 +320,9 @@ def run_ours(args, rank, world, dist):
 
     # the batched path with FP16 intermediate frames (splat, then a separate
     # finishing kernel reading the 16-bit frames)
-    r16 = Renderer(wl, device=dev, tile=r.pk.batch.tile, inter_dtype="f16")
+    r16 = Renderer(wl, device=dev, tile=args.tile, inter_dtype="f16")
+    if args.tile == 0:
+        r16.autotune(reps=2)
     for _ in range(3):
         r16.render()
     torch.cuda.synchronize()
@@ -325,6 +337,7 @@ def run_ours(args, rank, world, dist):
         h1.synchronize()
         f_ms += h0.elapsed_time(h1)
     f16_ms = f_ms / nf
+    f16_tile = r16.pk.batch.tile
     del r16
 
     # end to end through the same C ABI: pinned host flows in, images out
@@ -352,6 +365,10 @@ def run_ours(args, rank, world, dist):
     # plain FP32 per-pair path: one launch sequence per pair, FP32 output
     from paper_2512_09664_b300 import workloads as W
     plain = [Renderer(wl.subset([b]), device=dev, tile=args.tile, out_dtype="f32") for b in range(wl.n_pairs)]
+    if args.tile == 0:  # the single-pair path at its own best tile edge
+        t_one, _ = plain[0].autotune(reps=3)
+        for p in plain:
+            p.pk.batch.tile = t_one
     for p in plain:
         p.render()
     torch.cuda.synchronize()
@@ -364,7 +381,6 @@ def run_ours(args, rank, world, dist):
     p1.record(stream)
     torch.cuda.synchronize()
     plain_pairs_s = reps * wl.n_pairs / (p0.elapsed_time(p1) / 1e3)
-    del plain
 
     peaks, peak_kind = measured_peaks()
     alg_bytes, alg_ops = algorithmic(wl)
@@ -395,8 +411,10 @@ def run_ours(args, rank, world, dist):
                      "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_mhz:.0f} MHz"},
         "step_roofline_hbm": {"achieved_gbs": step_gbs, "peak_gbs": hbm_peak, "frac": step_gbs / hbm_peak,
                               "peak_source": peak_kind, "algorithmic_bytes_per_step": alg_bytes},
-        "plain_fp32_per_pair": {"value": plain_pairs_s, "unit": UNIT, "speedup": value / world / plain_pairs_s},
-        "batched_f16_intermediate": {"value": wl.n_pairs / (f16_ms / 1e3), "unit": UNIT, "ms_per_step": f16_ms},
+        "plain_fp32_per_pair": {"value": plain_pairs_s, "unit": UNIT, "speedup": value / world / plain_pairs_s,
+                                "tile": plain[0].pk.batch.tile if plain else None},
+        "batched_f16_intermediate": {"value": wl.n_pairs / (f16_ms / 1e3), "unit": UNIT, "ms_per_step": f16_ms,
+                                     "tile": f16_tile},
         "graph_replay": {"ms_per_step": graph_ms, "value": world * wl.n_pairs / (graph_ms / 1e3), "unit": UNIT},
         "e2e": {"value": world * wl.n_pairs / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},

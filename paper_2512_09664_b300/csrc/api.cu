@@ -262,12 +262,9 @@ static int run(Mode mode, const synthpix_batch_desc *batch, const synthpix_pair_
     uint32_t *ticket = reinterpret_cast<uint32_t *>(ws + L.check + 16);
     float *blur_w = reinterpret_cast<float *>(ws + L.blur);
     if (ev && ev[0]) cudaEventRecord(ev[0], st);
-    e = spx::launch_plan(descs, n_pairs, P.tile, P.fused, plan, L, check, blur_w, ticket, st);
+    e = spx::launch_plan(descs, n_pairs, P.tile, P.fused, plan, L, check, blur_w, ticket,
+                         mode == Mode::Render ? reinterpret_cast<uint32_t *>(ws + L.count) : nullptr, st);
     if (e != cudaSuccess) return fail(SYNTHPIX_ECUDA, "plan launch: %s", cudaGetErrorString(e));
-    if (mode == Mode::Render) {
-        e = cudaMemsetAsync(ws + L.count, 0, (size_t)L.n_tiles * 4, st);
-        if (e != cudaSuccess) return fail(SYNTHPIX_ECUDA, "count reset: %s", cudaGetErrorString(e));
-    }
     if (ev && ev[1]) cudaEventRecord(ev[1], st);
 
     spx::KernelArgs a;

@@ -48,6 +48,16 @@ struct KernelArgs {
 };
 
 constexpr int kStageEvents = 6;
+
+// Launch a kernel of the render sequence; returns the launch's error.
+// (Programmatic dependent launch was measured: a replayed render took 12 us
+// longer with it, so the kernels are launched plainly.)
+template <typename... P, typename... A>
+inline cudaError_t launch_kernel(void (*kernel)(P...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                                  A &&...args) {
+    kernel<<<grid, block, smem, st>>>(static_cast<A &&>(args)...);
+    return cudaGetLastError();
+}
 constexpr int kSplatThreads = 256;      // k_splat below tile 64, k_finish
 constexpr int kSplatMaxThreads = 1024;  // k_splat at tile 128 (one CTA per SM)
 constexpr int kStageHeader = 320;       // descriptor (128) + plan (64) + blur taps (128)
@@ -60,9 +70,10 @@ __host__ __device__ constexpr int splat_threads(int tile) { return tile >= 128 ?
 __host__ __device__ constexpr int rec_buf_bytes_for(int tile) { return tile >= 128 ? kRecBufBytesLarge : kRecBufBytes; }
 constexpr size_t kMaxSmemBytes = 227 * 1024;  // dynamic shared memory of one CTA
 
+// count: NULL, or the per-(pair, frame, tile) bin counts, zeroed by the plan launch
 cudaError_t launch_plan(const synthpix_pair_desc *descs, int32_t n_pairs, int32_t tile, int32_t fused,
                         PairPlan *plan, const Layout &L, int32_t *check, float *blur_w, uint32_t *ticket,
-                        cudaStream_t st);
+                        uint32_t *count, cudaStream_t st);
 // ev: NULL or kStageEvents events recorded at the stage boundaries.
 cudaError_t launch_prep(const KernelArgs &a, cudaStream_t st, cudaEvent_t const *ev);
 cudaError_t launch_splat(const KernelArgs &a, int32_t out_dtype, cudaStream_t st, cudaEvent_t const *ev);

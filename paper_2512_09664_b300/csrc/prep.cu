@@ -28,13 +28,23 @@ namespace spx {
 // ---------------------------------------------------------------------------
 
 // ---------------------------------------------------------------------------
-// k_plan: per-pair prefix sums (one CTA of 1024 threads)
+// k_plan: per-pair prefix sums (CTA 0, 1024 threads); CTAs 1.. clear the
+// bin counts of a render
 // ---------------------------------------------------------------------------
+constexpr int kPlanZeroWords = 16384;
+
 __global__ void __launch_bounds__(1024) k_plan(const synthpix_pair_desc *__restrict__ descs, int32_t n_pairs,
                                                int32_t tile, int32_t fused, PairPlan *__restrict__ plan,
                                                int64_t want_part, int64_t want_tiles, int64_t want_list,
                                                int64_t want_inter, int64_t want_chunks, int32_t *__restrict__ check,
-                                               float *__restrict__ blur_w, uint32_t *__restrict__ ticket) {
+                                               float *__restrict__ blur_w, uint32_t *__restrict__ ticket,
+                                               uint32_t *__restrict__ count, int64_t n_count) {
+    if (blockIdx.x > 0) {  // the other CTAs clear the bin counts, 16 Ki words each
+        const int64_t k0 = ((int64_t)blockIdx.x - 1) * kPlanZeroWords;
+        const int64_t n = min((int64_t)kPlanZeroWords, n_count - k0);
+        for (int64_t k = threadIdx.x; k < n; k += blockDim.x) count[k0 + k] = 0u;
+        return;
+    }
     __shared__ long long s_part[1024], s_tile[1024], s_list[1024], s_inter[1024], s_chunk[1024];
     const int t = threadIdx.x;
     const int per = (n_pairs + 1023) / 1024;
@@ -527,10 +537,11 @@ __global__ void __launch_bounds__(kAdvThreads) k_scatter2(KernelArgs a) {
 // ---------------------------------------------------------------------------
 cudaError_t launch_plan(const synthpix_pair_desc *descs, int32_t n_pairs, int32_t tile, int32_t fused,
                         PairPlan *plan, const Layout &L, int32_t *check, float *blur_w, uint32_t *ticket,
-                        cudaStream_t st) {
-    k_plan<<<1, 1024, 0, st>>>(descs, n_pairs, tile, fused, plan, L.n_part, L.n_tiles, L.n_list, L.n_inter,
-                               L.n_chunks, check, blur_w, ticket);
-    return cudaGetLastError();
+                        uint32_t *count, cudaStream_t st) {
+    const int64_t n_count = count ? L.n_tiles : 0;
+    const unsigned grid = 1u + (unsigned)((n_count + kPlanZeroWords - 1) / kPlanZeroWords);
+    return launch_kernel(k_plan, grid, 1024, 0, st, descs, n_pairs, tile, fused, plan, L.n_part, L.n_tiles, L.n_list,
+                          L.n_inter, L.n_chunks, check, blur_w, ticket, count, n_count);
 }
 
 cudaError_t launch_prep(const KernelArgs &a, cudaStream_t st, cudaEvent_t const *ev) {
@@ -538,35 +549,39 @@ cudaError_t launch_prep(const KernelArgs &a, cudaStream_t st, cudaEvent_t const 
         if (ev && ev[k]) cudaEventRecord(ev[k], st);
     };
     const unsigned nb = (unsigned)a.n_chunks;
+    cudaError_t e = cudaSuccess;
+    auto ok = [&](cudaError_t r) {
+        if (e == cudaSuccess) e = r;
+    };
     if (!a.tiled) {
-        if (nb > 0) k_seed_advect<<<nb, kPrepThreads, 0, st>>>(a);
+        if (nb > 0) ok(launch_kernel(k_seed_advect, nb, kPrepThreads, 0, st, a));
         mark(2);
-        k_scan<<<2 * a.n_pairs, 1024, 0, st>>>(a, -1);
+        ok(launch_kernel(k_scan, 2u * (unsigned)a.n_pairs, 1024, 0, st, a, -1));
         mark(3);
-        if (nb > 0) k_scatter<<<nb, kPrepThreads, 0, st>>>(a);
+        if (nb > 0) ok(launch_kernel(k_scatter, nb, kPrepThreads, 0, st, a));
         mark(4);
-        return cudaGetLastError();
+        return e;
     }
     // seeded render: seed + frame-1 bins, tiled advection, frame-2 bins
     const unsigned nt1 = (unsigned)(a.n_tiles / 2);
     const size_t adv_smem = (size_t)adv_window_nodes(a.tile) * sizeof(float2);
     const bool big = a.tile >= 128;
-    cudaError_t e = big ? cudaFuncSetAttribute(k_advect<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adv_smem)
-                        : cudaFuncSetAttribute(k_advect<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adv_smem);
+    ok(big ? cudaFuncSetAttribute(k_advect<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adv_smem)
+           : cudaFuncSetAttribute(k_advect<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adv_smem));
     if (e != cudaSuccess) return e;
-    if (nb > 0) k_seed_advect<<<nb, kPrepThreads, 0, st>>>(a);
-    k_scan<<<a.n_pairs, 1024, 0, st>>>(a, 0);
-    if (nb > 0) k_scatter<<<nb, kPrepThreads, 0, st>>>(a);
+    if (nb > 0) ok(launch_kernel(k_seed_advect, nb, kPrepThreads, 0, st, a));
+    ok(launch_kernel(k_scan, (unsigned)a.n_pairs, 1024, 0, st, a, 0));
+    if (nb > 0) ok(launch_kernel(k_scatter, nb, kPrepThreads, 0, st, a));
     if (nt1 > 0) {
-        if (big) k_advect<1024><<<nt1, 1024, adv_smem, st>>>(a);
-        else k_advect<256><<<nt1, 256, adv_smem, st>>>(a);
+        if (big) ok(launch_kernel(k_advect<1024>, nt1, 1024, adv_smem, st, a));
+        else ok(launch_kernel(k_advect<256>, nt1, 256, adv_smem, st, a));
     }
     mark(2);
-    k_scan<<<a.n_pairs, 1024, 0, st>>>(a, 1);
+    ok(launch_kernel(k_scan, (unsigned)a.n_pairs, 1024, 0, st, a, 1));
     mark(3);
-    if (nt1 > 0) k_scatter2<<<nt1, kAdvThreads, 0, st>>>(a);
+    if (nt1 > 0) ok(launch_kernel(k_scatter2, nt1, kAdvThreads, 0, st, a));
     mark(4);
-    return cudaGetLastError();
+    return e;
 }
 
 }  // namespace spx

@@ -1175,7 +1175,8 @@ cudaError_t launch_splat(const KernelArgs &a, int32_t out_dtype, cudaStream_t st
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_splat<T, NT>, NT, smem);                   \
         if (e != cudaSuccess) return e;                                                                      \
         const int64_t want = (int64_t)nsm * (occ > 0 ? occ : 1);                                             \
-        k_splat<T, NT><<<(unsigned)(a.n_tiles < want ? a.n_tiles : want), NT, smem, st>>>(a);                \
+        e = launch_kernel(k_splat<T, NT>, (unsigned)(a.n_tiles < want ? a.n_tiles : want), NT, smem, st, a);  \
+        if (e != cudaSuccess) return e;                                                                      \
     } while (0)
 #define SPX_LAUNCH(T)                                                                                        \
     do {                                                                                                     \
@@ -1200,7 +1201,8 @@ cudaError_t launch_splat(const KernelArgs &a, int32_t out_dtype, cudaStream_t st
     do {                                                                                                     \
         e = cudaFuncSetAttribute(k_finish<T, I>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);     \
         if (e != cudaSuccess) return e;                                                                      \
-        k_finish<T, I><<<grid, kSplatThreads, fsm, st>>>(a);                                                 \
+        e = launch_kernel(k_finish<T, I>, grid, kSplatThreads, fsm, st, a);                                 \
+        if (e != cudaSuccess) return e;                                                                      \
     } while (0)
 #define SPX_FINISH_I(I)                                                                                      \
     switch (out_dtype) {                                                                                     \
