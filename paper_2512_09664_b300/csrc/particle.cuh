@@ -98,10 +98,11 @@ __device__ __forceinline__ Window particle_window(int32_t ix, float fx, int32_t 
 // Tiles whose halo-widened rectangle meets the window.
 __device__ __forceinline__ void window_tiles(const Window &w, int32_t halo, int32_t tile, int32_t W, int32_t H,
                                              int32_t &tx0, int32_t &tx1, int32_t &ty0, int32_t &ty1) {
-    tx0 = max(w.j0 - halo, 0) / tile;
-    tx1 = min(w.j1 + halo, W - 1) / tile;
-    ty0 = max(w.i0 - halo, 0) / tile;
-    ty1 = min(w.i1 + halo, H - 1) / tile;
+    const int sh = __ffs(tile) - 1;  // tile edges are powers of two; the coordinates are non-negative
+    tx0 = max(w.j0 - halo, 0) >> sh;
+    tx1 = min(w.j1 + halo, W - 1) >> sh;
+    ty0 = max(w.i0 - halo, 0) >> sh;
+    ty1 = min(w.i1 + halo, H - 1) >> sh;
 }
 
 

@@ -503,11 +503,25 @@ __device__ __forceinline__ void splat_chunk(const unsigned char *recs, unsigned 
 // epilogue helpers
 // ---------------------------------------------------------------------------
 
+// -2 ln u for u = uo24(w) = ((w >> 8) + 1) 2^-24 in (0, 1].  With x = 1 - u
+// (exact in FP32): for x < 2^-8 the series -ln(1 - x) = x + x^2/2 + x^3/3 +
+// x^4/4 (truncation below 1e-10 relative); otherwise -2 ln 2 log2(u) from
+// the hardware base-2 logarithm, whose absolute error (about 2^-22 on
+// log2) is then at most 3e-5 of the result, i.e. below 2e-6 on the normal
+// deviate (and below 5e-8 of full scale at a noise sigma of 0.02).
+__device__ __forceinline__ float neg2_log_uo24(uint32_t w) {
+    const float u = uo24f(w);
+    const float x = 1.0f - u;
+    const float series = 2.0f * x * fmaf(x, fmaf(x, fmaf(x, 0.25f, 1.0f / 3.0f), 0.5f), 1.0f);
+    const float viaLog2 = -1.38629436111989061883f * __log2f(u);  // -2 ln 2 log2(u)
+    return x < 0.00390625f ? series : viaLog2;
+}
+
 // Box-Muller pair from two Philox words: r = sqrt(-2 ln u), theta = 2 pi v,
 // evaluated as -r (cos, sin)(theta - pi) so the fast sine and cosine work on
 // [-pi, pi).
 __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float &n0, float &n1) {
-    const float x = -2.0f * logf(uo24f(wa));
+    const float x = neg2_log_uo24(wa);
     const float r = x > 0.0f ? x * rsqrtf(x) : 0.0f;
     float s, c;
     __sincosf(6.28318530717958647692f * (u24f(wb) - 0.5f), &s, &c);
@@ -564,7 +578,41 @@ struct Out<uint16_t> {
 
 // Store up to 4 consecutive outputs of a row (quantised when M > 0).
 template <typename T>
+struct IsCode {
+    static constexpr bool value = false;
+};
+template <>
+struct IsCode<uint8_t> {
+    static constexpr bool value = true;
+};
+template <>
+struct IsCode<uint16_t> {
+    static constexpr bool value = true;
+};
+
+template <typename T>
 __device__ __forceinline__ void store_group(T *o, float *v, int nvalid, float M) {
+    if constexpr (IsCode<T>::value) {
+        if (M > 0.0f) {
+            // Q = clamp(rint(B M), 0, M): the conversion rounds half to even and
+            // takes negative values (and NaN) to 0
+            const uint32_t Mi = (uint32_t)M;
+            uint32_t q[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) q[j] = min(__float2uint_rn(v[j] * M), Mi);
+            if (nvalid == 4 && (reinterpret_cast<uintptr_t>(o) % (4 * sizeof(T))) == 0) {
+                if (sizeof(T) == 1)
+                    *reinterpret_cast<uint32_t *>(o) = q[0] | (q[1] << 8) | (q[2] << 16) | (q[3] << 24);
+                else
+                    *reinterpret_cast<uint2 *>(o) = make_uint2(q[0] | (q[1] << 16), q[2] | (q[3] << 16));
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (j < nvalid) o[j] = (T)q[j];
+            }
+            return;
+        }
+    }
     if (M > 0.0f) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) v[j] = fminf(fmaxf(rintf(v[j] * M), 0.0f), M);
