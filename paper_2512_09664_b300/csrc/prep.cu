@@ -335,7 +335,13 @@ constexpr int kNbr = 3;        // on-chip counters for frame-2 tiles within +-kN
 constexpr int kNbrSide = 2 * kNbr + 1;
 constexpr int kAdvBatch = 2048;  // records of a bin examined per pass (home list in shared memory)
 
-__host__ __device__ inline int adv_window_nodes(int tile) { return (tile + 2 * kAdvMargin + 2) * (tile + 2 * kAdvMargin + 2); }
+// A tile's advection is split into adv_bands(tile) row bands, one CTA each
+// (two at tile 128, so that two CTAs with their flow windows fit on an SM).
+__host__ __device__ inline int adv_bands(int tile) { return tile >= 128 ? 2 : 1; }
+__host__ __device__ inline int adv_window_nodes(int tile) {
+    const int band = (tile + adv_bands(tile) - 1) / adv_bands(tile);
+    return (tile + 2 * kAdvMargin + 2) * (band + 2 * kAdvMargin + 2);
+}
 
 struct TileCtx {
     int32_t b, t, tx, ty, x0, x1, y0, y1;
@@ -343,11 +349,12 @@ struct TileCtx {
     int64_t adv0;  // first adv slot of the tile's frame-1 bin
 };
 
-// The frame-1 tile of this CTA (blockIdx.x over all pairs' frame-1 tiles).
-__device__ __forceinline__ TileCtx frame1_tile(const KernelArgs &a, const PairPlan &pl, int b, int W, int H) {
+// Frame-1 tile gt (over all pairs' frame-1 tiles) of pair b.
+__device__ __forceinline__ TileCtx frame1_tile(const KernelArgs &a, const PairPlan &pl, int b, int W, int H,
+                                               int64_t gt) {
     TileCtx c;
     c.b = b;
-    c.t = (int32_t)blockIdx.x - (pl.tile_base >> 1);
+    c.t = (int32_t)(gt - (pl.tile_base >> 1));
     c.ty = c.t / pl.tiles_x;
     c.tx = c.t - c.ty * pl.tiles_x;
     c.x0 = c.tx * a.tile;
@@ -359,8 +366,8 @@ __device__ __forceinline__ TileCtx frame1_tile(const KernelArgs &a, const PairPl
     return c;
 }
 
-__device__ __forceinline__ int frame1_pair(const KernelArgs &a) {
-    return block_upper_find(a.n_pairs, (int64_t)blockIdx.x, [&](int m) { return (int64_t)(a.plan[m].tile_base >> 1); });
+__device__ __forceinline__ int frame1_pair(const KernelArgs &a, int64_t gt) {
+    return block_upper_find(a.n_pairs, gt, [&](int m) { return (int64_t)(a.plan[m].tile_base >> 1); });
 }
 
 // Calls put(k, tile) for each frame-2 tile of advected record r; k = index of
@@ -381,26 +388,32 @@ __device__ __forceinline__ void frame2_tiles(const KernelArgs &a, const PairPlan
 }
 
 // NT threads: 256, or 1024 at tile 128 (one CTA per SM with its larger window).
-template <int NT>
+// NT threads per CTA, NB row bands per tile (blockIdx.x = NB tile + band).
+template <int NT, int NB>
 __global__ void __launch_bounds__(NT) k_advect(KernelArgs a) {
     if (*a.check != 1) return;
     extern __shared__ __align__(16) float2 s_flow[];
     __shared__ uint32_t s_nb[kNbrSide * kNbrSide];
     __shared__ uint16_t s_home[kAdvBatch];
     __shared__ uint32_t s_nhome;
-    const int b = frame1_pair(a);
+    const int64_t gt = (int64_t)(blockIdx.x / NB);
+    const int band = (int)(blockIdx.x - gt * NB);
+    const int b = frame1_pair(a, gt);
     const PairPlan pl = a.plan[b];
     const synthpix_pair_desc &D = a.descs[b];
     const int W = D.width, H = D.height;
-    const TileCtx c = frame1_tile(a, pl, b, W, H);
+    const TileCtx c = frame1_tile(a, pl, b, W, H, gt);
+    // this CTA's home rows [hy0, hy1): its band of the tile
+    const int bh = (a.tile + NB - 1) / NB;
+    const int hy0 = min(c.y0 + band * bh, c.y1), hy1 = min(hy0 + bh, c.y1);
     const Flow F = pair_flow(a, D);
-    // grid nodes under [x0 - M, x1 + M) x [y0 - M, y1 + M), bilinear neighbours included
+    // grid nodes under [x0 - M, x1 + M) x [hy0 - M, hy1 + M), bilinear neighbours included
     int32_t l0, l1, k0, k1;
     float t_;
     grid_coord(c.x0 - kAdvMargin, 0.0f, F.gw, F.W, l0, t_);
     grid_coord(c.x1 + kAdvMargin, 0.0f, F.gw, F.W, l1, t_);
-    grid_coord(c.y0 - kAdvMargin, 0.0f, F.gh, F.H, k0, t_);
-    grid_coord(c.y1 + kAdvMargin, 0.0f, F.gh, F.H, k1, t_);
+    grid_coord(hy0 - kAdvMargin, 0.0f, F.gh, F.H, k0, t_);
+    grid_coord(hy1 + kAdvMargin, 0.0f, F.gh, F.H, k1, t_);
     FlowWindow Wn;
     Wn.s = s_flow;
     Wn.gx0 = min(max(l0, 0), F.gw - 1);
@@ -422,15 +435,16 @@ __global__ void __launch_bounds__(NT) k_advect(KernelArgs a) {
     uint32_t *cnt2 = a.count + pl.tile_base + pl.ntiles;
     const bool same_res = F.gw == F.W && F.gh == F.H;
     for (uint32_t base = 0; base < c.it.count; base += kAdvBatch) {
-        // compact this batch's home particles (integer position inside the tile); the others are
-        // advected by their own home tile and marked here
+        // compact this batch's home particles (integer position inside the band); particles
+        // outside the tile are advected by their own home tile and marked here (by every
+        // band, with the same value); those of the tile's other bands are left to them
         if (threadIdx.x == 0) s_nhome = 0u;
         __syncthreads();
         for (uint32_t k = base + threadIdx.x; k < min(c.it.count, base + kAdvBatch); k += NT) {
             const int2 ip = reinterpret_cast<const int2 *>(a.rec + c.it.rec0 + k)[1];
             if (ip.x < c.x0 || ip.x >= c.x1 || ip.y < c.y0 || ip.y >= c.y1)
                 reinterpret_cast<float2 *>(a.adv + c.adv0 + k)[2] = make_float2(-1.0f, 0.0f);
-            else
+            else if (ip.y >= hy0 && ip.y < hy1)
                 s_home[atomicAdd(&s_nhome, 1u)] = (uint16_t)(k - base);
         }
         asm volatile("cp.async.wait_all;\n" ::: "memory");  // the flow window (overlapped with the compaction)
@@ -478,10 +492,10 @@ __global__ void __launch_bounds__(NT) k_advect(KernelArgs a) {
 __global__ void __launch_bounds__(kAdvThreads) k_scatter2(KernelArgs a) {
     if (*a.check != 1) return;
     __shared__ uint32_t s_cnt[kNbrSide * kNbrSide], s_base[kNbrSide * kNbrSide];
-    const int b = frame1_pair(a);
+    const int b = frame1_pair(a, (int64_t)blockIdx.x);
     const PairPlan pl = a.plan[b];
     const int W = a.descs[b].width, H = a.descs[b].height;
-    const TileCtx c = frame1_tile(a, pl, b, W, H);
+    const TileCtx c = frame1_tile(a, pl, b, W, H, (int64_t)blockIdx.x);
     uint32_t *cur2 = a.cursor + pl.tile_base + pl.ntiles;
     Record *seg = a.rec + pl.list_base + pl.list_cap;
     for (int i = threadIdx.x; i < kNbrSide * kNbrSide; i += kAdvThreads) s_cnt[i] = 0u;
@@ -565,16 +579,16 @@ cudaError_t launch_prep(const KernelArgs &a, cudaStream_t st, cudaEvent_t const 
     // seeded render: seed + frame-1 bins, tiled advection, frame-2 bins
     const unsigned nt1 = (unsigned)(a.n_tiles / 2);
     const size_t adv_smem = (size_t)adv_window_nodes(a.tile) * sizeof(float2);
-    const bool big = a.tile >= 128;
-    ok(big ? cudaFuncSetAttribute(k_advect<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adv_smem)
-           : cudaFuncSetAttribute(k_advect<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adv_smem));
+    const bool big = a.tile >= 128;  // two row bands per tile, 512 threads each
+    ok(big ? cudaFuncSetAttribute(k_advect<512, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adv_smem)
+           : cudaFuncSetAttribute(k_advect<256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adv_smem));
     if (e != cudaSuccess) return e;
     if (nb > 0) ok(launch_kernel(k_seed_advect, nb, kPrepThreads, 0, st, a));
     ok(launch_kernel(k_scan, (unsigned)a.n_pairs, 1024, 0, st, a, 0));
     if (nb > 0) ok(launch_kernel(k_scatter, nb, kPrepThreads, 0, st, a));
     if (nt1 > 0) {
-        if (big) ok(launch_kernel(k_advect<1024>, nt1, 1024, adv_smem, st, a));
-        else ok(launch_kernel(k_advect<256>, nt1, 256, adv_smem, st, a));
+        if (big) ok(launch_kernel(k_advect<512, 2>, 2 * nt1, 512, adv_smem, st, a));
+        else ok(launch_kernel(k_advect<256, 1>, nt1, 256, adv_smem, st, a));
     }
     mark(2);
     ok(launch_kernel(k_scan, (unsigned)a.n_pairs, 1024, 0, st, a, 1));
