@@ -110,6 +110,7 @@ constexpr int kBuckets = (kWideClass + 1) * 32;
 __shared__ uint32_t sh_cnt[kBuckets];              // visits of the chunk per (class, bank) key
 __shared__ uint32_t sh_off[kBuckets + 1];          // their exclusive offsets
 __shared__ uint32_t sh_next;                       // warp-slot ticket of the chunk's render
+__shared__ uint32_t sh_slot_end[kWideClass + 1];   // slots of the classes, widest first: cumulative ends
 __shared__ uint32_t sh_blk[kBlkSide * kBlkSide];  // visits of the item so far per 8 x 8 block
 __shared__ int sh_checked;                         // the chunk takes the checked path
 __shared__ int sh_carry_clean;                     // the item's carry words are zero
@@ -195,6 +196,8 @@ __device__ __forceinline__ int visit_ny(uint32_t s) { return (int)(s >> 24); }
 // visits of one warp are spread over the bank order, so their accumulator
 // addresses fall in different banks.
 __host__ __device__ constexpr int class_lanes(int c) { return c < 2 ? 1 : (c < 4 ? 2 : 4); }
+// log2 of the visits one warp slot of class c renders (32 / lanes per visit; 32 for the wide class)
+__host__ __device__ constexpr int class_slot_shift(int c) { return c >= 8 ? 5 : (c < 2 ? 5 : (c < 4 ? 4 : 3)); }
 __host__ __device__ constexpr int class_rows(int c) { return c == 0 ? 2 : (c == 2 || c == 4 || c == 5 ? 3 : 4); }
 
 // Quotient of small non-negative integers a / b (a < 2^20, 1 <= b <= 2^10)
@@ -402,6 +405,21 @@ __device__ __forceinline__ void splat_chunk(const unsigned char *recs, unsigned 
         }
         if (lane == 31) sh_off[kBuckets] = incl;
         if (lane == 0) sh_next = 0;
+        __syncwarp();
+        // warp slots per class (widest first) and their cumulative ends
+        uint32_t nsl = 0;
+        if (lane <= kWideClass) {
+            const int cc = kWideClass - lane;
+            const uint32_t G = sh_off[32 * cc + 32] - sh_off[32 * cc];
+            const int sh = class_slot_shift(cc);
+            nsl = (G + (1u << sh) - 1u) >> sh;
+        }
+#pragma unroll
+        for (int d = 1; d < 16; d <<= 1) {
+            const uint32_t t = __shfl_up_sync(FULL, nsl, d);
+            if (lane >= d) nsl += t;
+        }
+        if (lane <= kWideClass) sh_slot_end[lane] = nsl;
         uint32_t mx = 0;
 #pragma unroll
         for (int j = 0; j < kBlkSide * kBlkSide / 32; ++j) mx = max(mx, sh_blk[lane + 32 * j]);
@@ -453,23 +471,22 @@ __device__ __forceinline__ void splat_chunk(const unsigned char *recs, unsigned 
         }
         return;
     }
+    const uint32_t total_slots = sh_slot_end[kWideClass];
+    const uint32_t my_end = lane <= kWideClass ? sh_slot_end[lane] : 0xffffffffu;
     for (;;) {
         uint32_t sl = 0;
         if (lane == 0) sl = atomicAdd(&sh_next, 1u);
         sl = __shfl_sync(FULL, sl, 0);
-        int c = kWideClass;
-        uint32_t g0 = 0, G = 0, nw = 0;
-        for (; c >= 0; --c) {
-            g0 = sh_off[32 * c];
-            G = sh_off[32 * c + 32] - g0;
-            const uint32_t per = c == kWideClass ? 32u : 32u / (uint32_t)class_lanes(c);  // visits per slot
-            nw = (G + per - 1) / per;
-            if (sl < nw) break;
-            sl -= nw;
-        }
-        if (c < 0) break;
+        if (sl >= total_slots) break;
+        // the slot's class: the first (widest-first) class whose slots end beyond sl
+        const int o = __ffs(__ballot_sync(FULL, sl < my_end)) - 1;
+        const int c = kWideClass - o;
+        sl -= o ? __shfl_sync(FULL, my_end, o - 1) : 0u;  // slot within the class
+        const uint32_t g0 = sh_off[32 * c], G = sh_off[32 * c + 32] - g0;
+        const int csh = class_slot_shift(c);
+        const uint32_t nw = (G + (1u << csh) - 1u) >> csh;  // slots of the class
         // wide: visits 32 sl + lane; narrow: group q of U lanes takes visit sl + q nw (spread over the bank order)
-        const uint32_t idx = c == kWideClass ? sl * 32 + lane : sl + (uint32_t)(lane / class_lanes(c)) * nw;
+        const uint32_t idx = c == kWideClass ? sl * 32 + lane : sl + (uint32_t)(lane >> (5 - csh)) * nw;
         const bool valid = idx < G;
         Visit e;
         if (valid) {
