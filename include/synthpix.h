@@ -188,6 +188,27 @@ int synthpix_seed_particles(const synthpix_batch_desc *batch, const synthpix_pai
                             void *workspace, size_t workspace_bytes, void *stream);
 
 /*
+ * Particle reuse across consecutive frames (the paper's Conclusions list it
+ * as planned work: the flow applied for a second, possibly different, dt' to
+ * the frame-2 positions gives the frame-1 positions of the next batch).
+ * Writes [sum of n_particles][3] (x, y, d) to particles_out (device, 4-byte
+ * aligned, caller-owned): each particle advected from its frame-1 position
+ * over batch->dt exactly as synthpix_render_pairs advects it, rounded once to
+ * FP32, and its diameter.  particles_in (nullable) as in
+ * synthpix_render_pairs_from: the frame-1 (x0, y0, d); NULL takes the seeded
+ * ones.  A sequence: advect a batch's particles over dt' (this call, with
+ * particles_in = its frame-2 positions, themselves from this call over dt),
+ * then render the next batch with synthpix_render_pairs_from and the same
+ * pair_id, which keeps each particle's intensity and depth (drawn from the
+ * same Philox counters).  Same workspace as synthpix_render_pairs; images
+ * are not needed.
+ */
+int synthpix_advect_particles(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
+                              const synthpix_pair_desc *pairs_dev, int32_t n_pairs, const float *particles_in,
+                              const float *flows, float *particles_out, void *workspace, size_t workspace_bytes,
+                              void *stream);
+
+/*
  * Adjoint of the render (not in the paper; its differentiable use): given
  * grad_images = dL/d(images) (FP32, same packing as the images), computes
  *   grad_flows      dL/d(flows), ADDED to the caller's array (same layout as

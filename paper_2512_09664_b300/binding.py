@@ -84,6 +84,9 @@ def lib():
         L.synthpix_seed_particles.argtypes = [C.POINTER(BatchDesc), C.POINTER(PairDesc), vp, C.c_int32, vp, vp,
                                               sz, vp]
         L.synthpix_seed_particles.restype = C.c_int
+        L.synthpix_advect_particles.argtypes = [C.POINTER(BatchDesc), C.POINTER(PairDesc), vp, C.c_int32, vp, vp,
+                                                vp, vp, sz, vp]
+        L.synthpix_advect_particles.restype = C.c_int
         L.synthpix_render_backward.argtypes = [C.POINTER(BatchDesc), C.POINTER(PairDesc), vp, C.c_int32,
                                                vp, vp, vp, vp, vp, vp, sz, vp]
         L.synthpix_render_backward.restype = C.c_int
@@ -302,6 +305,25 @@ class Renderer:
         pd, ws, wsn, st = self._ptrs(stream)
         _check(lib().synthpix_seed_particles(C.byref(self.pk.batch), self.pk.pairs, pd, self.pk.n_pairs,
                                              self._vp(out), ws, wsn, st))
+        return out[:n]
+
+    def advect_particles(self, particles=None, dt=None, flows=None, stream=None):
+        """[sum N, 3] float32 device tensor: (x, y, d) advected over dt (default: the batch's dt)
+        from the given frame-1 particles (default: the seeded ones)."""
+        import torch
+        flows = self.flows if flows is None else flows
+        n = sum(p.n_particles for p in self.pk.pairs[:self.pk.n_pairs])
+        out = torch.empty((max(n, 1), 3), dtype=torch.float32, device=self.device)
+        saved = self.pk.batch.dt
+        if dt is not None:
+            self.pk.batch.dt = float(dt)
+        try:
+            pd, ws, wsn, st = self._ptrs(stream)
+            _check(lib().synthpix_advect_particles(C.byref(self.pk.batch), self.pk.pairs, pd, self.pk.n_pairs,
+                                                   self._vp(particles), self._vp(flows), self._vp(out), ws, wsn,
+                                                   st))
+        finally:
+            self.pk.batch.dt = saved
         return out[:n]
 
     def render_from(self, flows=None, particles=None, stream=None):

@@ -198,7 +198,7 @@ size_t synthpix_workspace_bytes(const synthpix_batch_desc *batch, const synthpix
 
 }  // extern "C"
 
-enum class Mode { Render, Seed, Backward };
+enum class Mode { Render, Seed, Advect, Backward };
 
 // Optional arguments of the seeding and adjoint entry points.
 struct Extra {
@@ -219,11 +219,12 @@ static int run(Mode mode, const synthpix_batch_desc *batch, const synthpix_pair_
         g_err[0] = 0;
         return SYNTHPIX_OK;
     }
+    const bool exporting = mode == Mode::Seed || mode == Mode::Advect;
     if (mode != Mode::Seed && (!flows || ((uintptr_t)flows & 7)))
         return fail(SYNTHPIX_EINVAL, "flows is NULL or not 8-byte aligned");
     if (mode == Mode::Render && (!images || ((uintptr_t)images % elem_size(batch->out_dtype))))
         return fail(SYNTHPIX_EINVAL, "images is NULL or misaligned for its element type");
-    if (mode == Mode::Seed && (!x.particles_out || ((uintptr_t)x.particles_out & 3)))
+    if (exporting && (!x.particles_out || ((uintptr_t)x.particles_out & 3)))
         return fail(SYNTHPIX_EINVAL, "particles_out is NULL or not 4-byte aligned");
     if (x.particles_in && ((uintptr_t)x.particles_in & 3))
         return fail(SYNTHPIX_EINVAL, "particles_in is not 4-byte aligned");
@@ -300,7 +301,8 @@ static int run(Mode mode, const synthpix_batch_desc *batch, const synthpix_pair_
     a.inter_dtype = batch->inter_dtype;
     a.inter = ws + L.inter;
     a.particles_in = x.particles_in;
-    a.particles_out = mode == Mode::Seed ? x.particles_out : nullptr;
+    a.particles_out = exporting ? x.particles_out : nullptr;
+    a.export_frame = mode == Mode::Advect ? 1 : 0;
     a.grad_images = x.grad_images;
     a.grad_flows = x.grad_flows;
     a.grad_particles = x.grad_particles;
@@ -308,7 +310,7 @@ static int run(Mode mode, const synthpix_batch_desc *batch, const synthpix_pair_
     a.smem_edge = P.tile + 2 * P.max_r;
     const int wmax = std::min(spx::window_max(P.max_d), a.smem_edge);
     a.warp_scratch = 4 * (wmax + 2);
-    if (mode == Mode::Seed) {
+    if (exporting) {
         e = spx::launch_seed_only(a, st);
         if (e != cudaSuccess) return fail(SYNTHPIX_ECUDA, "seeding launch: %s", cudaGetErrorString(e));
     } else if (mode == Mode::Backward) {
@@ -413,6 +415,17 @@ int synthpix_seed_particles(const synthpix_batch_desc *batch, const synthpix_pai
     Extra x;
     x.particles_out = particles_out;
     return run(Mode::Seed, batch, pairs, pairs_dev, n_pairs, nullptr, nullptr, workspace, workspace_bytes, stream,
+               nullptr, x);
+}
+
+int synthpix_advect_particles(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
+                              const synthpix_pair_desc *pairs_dev, int32_t n_pairs, const float *particles_in,
+                              const float *flows, float *particles_out, void *workspace, size_t workspace_bytes,
+                              void *stream) {
+    Extra x;
+    x.particles_in = particles_in;
+    x.particles_out = particles_out;
+    return run(Mode::Advect, batch, pairs, pairs_dev, n_pairs, flows, nullptr, workspace, workspace_bytes, stream,
                nullptr, x);
 }
 

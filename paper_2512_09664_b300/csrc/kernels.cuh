@@ -39,7 +39,8 @@ struct KernelArgs {
     int32_t inter_dtype;              // SYNTHPIX_F32: fused; F16 / BF16: intermediate frames
     void *inter;                      // 16-bit intermediate frames (non-fused path)
     const float *particles_in;        // NULL or [n_part][3] (x0, y0, d) replacing the seeded values
-    float *particles_out;             // NULL, or seeding only: [n_part][3] seeded (x0, y0, d)
+    float *particles_out;             // NULL, or export only: [n_part][3] (x, y, d) of frame export_frame
+    int32_t export_frame;             // 0: the seeded (frame-1) positions; 1: the advected (frame-2) ones
     // adjoint
     const float *grad_images;         // dL/d(images), FP32, same packing as the images
     float *grad_flows;                // NULL or dL/d(flows), accumulated
@@ -78,7 +79,7 @@ cudaError_t launch_plan(const synthpix_pair_desc *descs, int32_t n_pairs, int32_
 cudaError_t launch_prep(const KernelArgs &a, cudaStream_t st, cudaEvent_t const *ev);
 cudaError_t launch_splat(const KernelArgs &a, int32_t out_dtype, cudaStream_t st, cudaEvent_t const *ev);
 size_t splat_smem_bytes(int edge, int tile, int warp_scratch, int rec_buf_bytes);
-// seeding only (a.particles_out set): k_seed_advect exports the seeded particles
+// export only (a.particles_out set): k_seed_advect exports the particles of frame a.export_frame
 cudaError_t launch_seed_only(const KernelArgs &a, cudaStream_t st);
 // adjoint: splat gradients per (particle, frame), then the reverse advection
 cudaError_t launch_adjoint(const KernelArgs &a, cudaStream_t st);

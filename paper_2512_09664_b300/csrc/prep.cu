@@ -165,7 +165,8 @@ __device__ __forceinline__ void count_window(const KernelArgs &a, const ChunkCtx
 
 // ---------------------------------------------------------------------------
 // k_seed_advect: Philox attributes, frame-1 position, advection to frame 2,
-// split positions and bin counts (seeding only: exports (x0, y0, d))
+// split positions and bin counts (export only: writes (x, y, d) of frame 1
+// or, advected, of frame 2)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kPrepThreads, 5) k_seed_advect(KernelArgs a) {
     if (*a.check != 1) return;
@@ -187,8 +188,12 @@ __global__ void __launch_bounds__(kPrepThreads, 5) k_seed_advect(KernelArgs a) {
         a.sa[g] = make_float2(P.sigma, P.amp);
         a.pos0[g] = make_float4(P.fx, P.fy, __int_as_float(P.ix), __int_as_float(P.iy));
         if (a.particles_out) {
-            a.particles_out[3 * g] = (float)P.ix + P.fx;
-            a.particles_out[3 * g + 1] = (float)P.iy + P.fy;
+            int32_t jx = P.ix, jy = P.iy;
+            float gx = P.fx, gy = P.fy;
+            if (a.export_frame) advect_split(F, a.dt, a.n_substeps, a.integrator, jx, gx, jy, gy);
+            // the split position rounded once to FP32; d = 4 sigma exactly
+            a.particles_out[3 * g] = (float)jx + gx;
+            a.particles_out[3 * g + 1] = (float)jy + gy;
             a.particles_out[3 * g + 2] = 4.0f * P.sigma;
             continue;
         }

@@ -121,3 +121,12 @@ def test_gather_advection_flag_accepted():
     pk = _packed()
     pk.batch.flags = B.FLAG_GATHER_ADVECT
     assert B.workspace_bytes(pk) > 0
+
+
+def test_advect_particles_rejects_missing_buffers():
+    pk = _packed()
+    L = B.lib()
+    assert L.synthpix_advect_particles(C.byref(pk.batch), pk.pairs, None, pk.n_pairs, None, FAKE, None, FAKE,
+                                       1 << 30, None) == B.EINVAL
+    assert L.synthpix_advect_particles(C.byref(pk.batch), pk.pairs, None, pk.n_pairs, None, None, FAKE, FAKE,
+                                       1 << 30, None) == B.EINVAL
