@@ -647,47 +647,60 @@ __device__ __forceinline__ void store_group(T *o, float *v, int nvalid, float M)
 // vertical pass with store; taps w[|k|], k = -R..R, replicate border already
 // materialised in A.  R is a compile-time radius (0 < R <= 6).  Tiles start
 // on multiples of 4, so the tile's first input column x0 - R sits
-// OFF = (-R) mod 4 columns into A's 16-byte aligned rows.
+// OFF = (-R) mod 4 columns into A's 16-byte aligned rows, and its first
+// output column at CB = OFF + R, a multiple of 4.
+//
+// The horizontal pass works in place: a warp takes whole rows (32 / G rows
+// of G output quads per pass), its lanes read their inputs, the warp
+// synchronises, and the lanes write their outputs over the row at CB.  No
+// other warp reads those rows in that pass except past the row's end, which
+// feeds only outputs beyond the tile.
 template <typename T, int R>
-__device__ __forceinline__ void blur_store(const Geo &g, const float *A, float *Bh, int BP, const float *w, T *out,
-                                           float M) {
+__device__ __forceinline__ void blur_store(const Geo &g, float *A, const float *w, T *out, float M) {
     constexpr int OFF = (4 - R % 4) % 4;
+    constexpr int CB = OFF + R;
     const int TW = g.x1 - g.x0, TH = g.y1 - g.y0;
-    const int G = (TW + 3) >> 2;
-    const float iG = 1.0f / (float)G;
+    const int G = (TW + 3) >> 2;  // output quads per row (<= 32: tiles are at most 128 wide)
     float wr[R + 1];
 #pragma unroll
     for (int k = 0; k <= R; ++k) wr[k] = w[k];
     constexpr int NV = (OFF + 4 + 2 * R + 3) / 4;  // float4 loads covering the 4 + 2R inputs
-    for (int it = threadIdx.x; it < g.FH * G; it += blockDim.x) {
-        const int r = small_div(it, iG), c0 = (it - r * G) * 4;
-        // 16-byte aligned (AP and c0 multiples of 4); inputs past the halo feed only outputs past the tile
-        const float4 *row = reinterpret_cast<const float4 *>(A + r * g.AP + c0);
-        float v[4 * NV];
+    const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const int rpp = 32 / G;                       // rows per warp pass
+    const int lr = small_div(lane, 1.0f / (float)G), lg = lane - lr * G;
+    for (int rb = (threadIdx.x >> 5) * rpp; rb < g.FH; rb += nwarps * rpp) {
+        const int r = rb + lr;
+        const bool on = lr < rpp && r < g.FH;
+        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (on) {
+            const float4 *row = reinterpret_cast<const float4 *>(A + r * g.AP + 4 * lg);
+            float v[4 * NV];
 #pragma unroll
-        for (int q = 0; q < NV; ++q) {
-            const float4 t = row[q];
-            v[4 * q] = t.x;
-            v[4 * q + 1] = t.y;
-            v[4 * q + 2] = t.z;
-            v[4 * q + 3] = t.w;
+            for (int q = 0; q < NV; ++q) {
+                const float4 t = row[q];
+                v[4 * q] = t.x;
+                v[4 * q + 1] = t.y;
+                v[4 * q + 2] = t.z;
+                v[4 * q + 3] = t.w;
+            }
+            float *op = &o.x;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float acc = wr[0] * v[OFF + j + R];
+#pragma unroll
+                for (int k = 1; k <= R; ++k) acc = fmaf(wr[k], v[OFF + j + R - k] + v[OFF + j + R + k], acc);
+                op[j] = acc;
+            }
         }
-        float4 o;
-        float *op = &o.x;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            float acc = wr[0] * v[OFF + j + R];
-#pragma unroll
-            for (int k = 1; k <= R; ++k) acc = fmaf(wr[k], v[OFF + j + R - k] + v[OFF + j + R + k], acc);
-            op[j] = acc;
-        }
-        *reinterpret_cast<float4 *>(Bh + r * BP + c0) = o;
+        __syncwarp();  // the warp's rows are read before they are overwritten
+        if (on) *reinterpret_cast<float4 *>(A + r * g.AP + CB + 4 * lg) = o;
     }
     __syncthreads();
+    const float iG = 1.0f / (float)G;
+    const int p4 = g.AP >> 2;
     for (int it = threadIdx.x; it < TH * G; it += blockDim.x) {
         const int r = small_div(it, iG), c0 = (it - r * G) * 4;
-        const float4 *col = reinterpret_cast<const float4 *>(Bh + c0);
-        const int p4 = BP >> 2;
+        const float4 *col = reinterpret_cast<const float4 *>(A + CB + c0);
         const float4 m0 = col[(r + R) * p4];
         float v[4] = {wr[0] * m0.x, wr[0] * m0.y, wr[0] * m0.z, wr[0] * m0.w};
 #pragma unroll
@@ -965,15 +978,15 @@ __device__ __forceinline__ void finish_rest(const KernelArgs &a, const Geo &g, c
     const float M = a.quant_bits > 0 ? (float)((1u << a.quant_bits) - 1u) : 0.0f;
     switch (g.R) {
     case 0: store_unblurred<T>(g, s.A, out, M); break;
-    case 1: blur_store<T, 1>(g, s.A, s.Bh, s.BP, wtab, out, M); break;
-    case 2: blur_store<T, 2>(g, s.A, s.Bh, s.BP, wtab, out, M); break;
-    case 3: blur_store<T, 3>(g, s.A, s.Bh, s.BP, wtab, out, M); break;
-    case 4: blur_store<T, 4>(g, s.A, s.Bh, s.BP, wtab, out, M); break;
-    case 5: blur_store<T, 5>(g, s.A, s.Bh, s.BP, wtab, out, M); break;
-    case 6: blur_store<T, 6>(g, s.A, s.Bh, s.BP, wtab, out, M); break;
+    case 1: blur_store<T, 1>(g, s.A, wtab, out, M); break;
+    case 2: blur_store<T, 2>(g, s.A, wtab, out, M); break;
+    case 3: blur_store<T, 3>(g, s.A, wtab, out, M); break;
+    case 4: blur_store<T, 4>(g, s.A, wtab, out, M); break;
+    case 5: blur_store<T, 5>(g, s.A, wtab, out, M); break;
+    case 6: blur_store<T, 6>(g, s.A, wtab, out, M); break;
     default: blur_store_any<T>(g, s.A, s.Bh, s.BP, wtab, out, M); break;
     }
-    if (g.R > 0 && s.bh_alias) {  // Bh lives in the accumulator words: clear them for the next item
+    if (g.R > 6 && s.bh_alias) {  // Bh lives in the accumulator words: clear them for the next item
         __syncthreads();
         float4 *b4 = reinterpret_cast<float4 *>(s.Bh);
         for (int k = threadIdx.x; k < (g.FH * s.BP) >> 2; k += blockDim.x) b4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1061,10 +1074,11 @@ struct SmemLayout {
 };
 
 // The accumulator words; the finishing buffer A (which holds the carry words
-// during the splat); the horizontal-blur buffer Bh, in memory of its own when
-// that fits, else in the accumulator words (free between the first
-// finishing pass and the next item); illumination factors; per-warp window
-// scratch; the normal-tail table; two staged-record buffers.
+// during the splat); the horizontal-blur buffer Bh of the blur for radii
+// above 6 (the others blur rows in place), in memory of its own when that
+// fits, else in the accumulator words (free between the first finishing pass
+// and the next item); illumination factors; per-warp window scratch; the
+// normal-tail table; two staged-record buffers.
 __host__ __device__ inline SmemLayout smem_layout(int E, int tile, int warp_scratch, int rec_buf_bytes) {
     SmemLayout L;
     const int BP = (tile + 3) & ~3;
@@ -1082,9 +1096,10 @@ __host__ __device__ inline SmemLayout smem_layout(int E, int tile, int warp_scra
     L.scr = take((size_t)(splat_threads(tile) / 32) * warp_scratch * 4);
     L.phi = take((size_t)(kPhiDegree + 1) * kPhiPieces * 4);
     L.bufs = take(2 * (size_t)rec_buf_bytes);
-    const size_t bh = (size_t)E * BP * 4;
-    L.bh_alias = o + bh > kMaxSmemBytes;
-    L.Bh = L.bh_alias ? L.acc : take(bh);
+    const bool need_bh = (E - tile) / 2 > 6;  // only the blur of radii above 6 uses Bh
+    const size_t bh = need_bh ? (size_t)E * BP * 4 : 0;
+    L.bh_alias = need_bh && o + bh > kMaxSmemBytes;
+    L.Bh = (!need_bh || L.bh_alias) ? L.acc : take(bh);
     L.total = o;
     return L;
 }
@@ -1183,7 +1198,7 @@ __host__ __device__ inline FinishLayout finish_layout(int E, int tile) {
         return at;
     };
     L.A = take(((size_t)E * PC + 32) * 4);
-    L.Bh = take((size_t)E * BP * 4);
+    L.Bh = take((E - tile) / 2 > 6 ? (size_t)E * BP * 4 : 0);  // only radii above 6 use Bh
     L.sx2 = take(PC * 4);
     L.sy2 = take((size_t)E * 4);
     L.total = o;
