@@ -59,7 +59,7 @@ inline cudaError_t launch_kernel(void (*kernel)(P...), unsigned grid, unsigned b
     kernel<<<grid, block, smem, st>>>(static_cast<A &&>(args)...);
     return cudaGetLastError();
 }
-constexpr int kSplatThreads = 256;      // k_splat below tile 64, k_finish
+constexpr int kSplatThreads = 256;      // k_splat below tile 128, k_finish
 constexpr int kSplatMaxThreads = 1024;  // k_splat at tile 128 (one CTA per SM)
 constexpr int kStageHeader = 320;       // descriptor (128) + plan (64) + blur taps (128)
 constexpr int kRecBufBytes = 8192;      // each staged-records buffer of k_splat (tiles up to 64)
@@ -67,7 +67,9 @@ constexpr int kRecBufBytesLarge = 24576;  // the same at tile 128
 // records per staged chunk of a buffer
 __host__ __device__ constexpr int rec_cap(int buf_bytes) { return (buf_bytes - kStageHeader - 32) / 24; }
 // threads of a k_splat CTA at a tile edge
-__host__ __device__ constexpr int splat_threads(int tile) { return tile >= 128 ? 1024 : (tile >= 64 ? 512 : 256); }
+// (256 below tile 128: three CTAs per SM hide each other's barriers better
+// than two of 512)
+__host__ __device__ constexpr int splat_threads(int tile) { return tile >= 128 ? 1024 : 256; }
 __host__ __device__ constexpr int rec_buf_bytes_for(int tile) { return tile >= 128 ? kRecBufBytesLarge : kRecBufBytes; }
 constexpr size_t kMaxSmemBytes = 227 * 1024;  // dynamic shared memory of one CTA
 

@@ -1261,7 +1261,6 @@ cudaError_t launch_splat(const KernelArgs &a, int32_t out_dtype, cudaStream_t st
 #define SPX_LAUNCH(T)                                                                                        \
     do {                                                                                                     \
         if (nt == 1024) SPX_LAUNCH_NT(T, 1024);                                                              \
-        else if (nt == 512) SPX_LAUNCH_NT(T, 512);                                                           \
         else SPX_LAUNCH_NT(T, 256);                                                                          \
     } while (0)
     const int nt = splat_threads(a.tile);
