@@ -960,15 +960,29 @@ template <typename T>
 __device__ __forceinline__ void finish_rest(const KernelArgs &a, const Geo &g, const synthpix_pair_desc &D,
                                             const float *wtab, int frame, const Smem &s) {
     if (g.R > 0 && (g.fx0 < 0 || g.fy0 < 0 || g.x1 + g.R > g.W || g.y1 + g.R > g.H)) {  // uniform
-        const float ifw = 1.0f / (float)g.FW;
+        // only the pixels of the full halo rectangle outside the frame: whole rows
+        // above and below it, then the columns left and right of it in the rows
+        // between; each copies an in-frame pixel, so the order does not matter
         const int cx = g.fx0 - g.afx0;  // A column of frame column fx0
-        for (int k = threadIdx.x; k < g.FH * g.FW; k += blockDim.x) {
-            const int r = small_div(k, ifw), c = k - r * g.FW;
-            const int gi = g.fy0 + r, gj = g.fx0 + c;
-            if (gi < 0 || gi >= g.H || gj < 0 || gj >= g.W) {
-                const int ci = min(max(gi, 0), g.H - 1) - g.fy0, cj = min(max(gj, 0), g.W - 1) - g.fx0;
-                s.A[r * g.AP + cx + c] = s.A[ci * g.AP + cx + cj];
+        const int top = max(-g.fy0, 0), bot = max(g.fy0 + g.FH - g.H, 0);
+        const int left = max(-g.fx0, 0), right = max(g.fx0 + g.FW - g.W, 0);
+        const int nband = (top + bot) * g.FW, nside = left + right;
+        const int n = nband + (g.FH - top - bot) * nside;
+        const float ifw = 1.0f / (float)g.FW, ins = 1.0f / (float)max(nside, 1);
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            int r, c;
+            if (k < nband) {
+                const int q = small_div(k, ifw);
+                r = q < top ? q : g.FH - bot + (q - top);
+                c = k - q * g.FW;
+            } else {
+                const int q = small_div(k - nband, ins), e = k - nband - q * nside;
+                r = top + q;
+                c = e < left ? e : g.FW - right + (e - left);
             }
+            const int gi = g.fy0 + r, gj = g.fx0 + c;
+            const int ci = min(max(gi, 0), g.H - 1) - g.fy0, cj = min(max(gj, 0), g.W - 1) - g.fx0;
+            s.A[r * g.AP + cx + c] = s.A[ci * g.AP + cx + cj];
         }
         __syncthreads();
     }
