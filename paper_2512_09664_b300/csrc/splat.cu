@@ -195,10 +195,10 @@ __device__ __forceinline__ int visit_ny(uint32_t s) { return (int)(s >> 24); }
 // Class 8 holds the wider windows, rendered by a whole warp per visit.  The
 // visits of one warp are spread over the bank order, so their accumulator
 // addresses fall in different banks.
-__host__ __device__ constexpr int class_lanes(int c) { return c < 2 ? 1 : (c < 4 ? 2 : 4); }
+__host__ __device__ constexpr int class_lanes(int c) { return c < 2 ? 1 : 2; }
 // log2 of the visits one warp slot of class c renders (32 / lanes per visit; 32 for the wide class)
-__host__ __device__ constexpr int class_slot_shift(int c) { return c >= 8 ? 5 : (c < 2 ? 5 : (c < 4 ? 4 : 3)); }
-__host__ __device__ constexpr int class_rows(int c) { return c == 0 ? 2 : (c == 2 || c == 4 || c == 5 ? 3 : 4); }
+__host__ __device__ constexpr int class_slot_shift(int c) { return c >= 8 ? 5 : (c < 2 ? 5 : 4); }
+__host__ __device__ constexpr int class_rows(int c) { return c == 0 ? 2 : (c == 1 ? 4 : c + 1); }
 
 // Quotient of small non-negative integers a / b (a < 2^20, 1 <= b <= 2^10)
 // from b's reciprocal: (a + 1/2) / b is at least 1/(2b) away from an integer,
