@@ -42,6 +42,9 @@ class OraclePair(C.Structure):
         ("illum_min", C.c_double), ("illum_max", C.c_double),
         ("noise_sigma", C.c_double), ("blur_sigma", C.c_double),
         ("dt", C.c_double),
+        ("dy_min", C.c_double), ("dy_max", C.c_double), ("rho_min", C.c_double), ("rho_max", C.c_double),
+        ("jitter_d", C.c_double), ("jitter_i", C.c_double), ("jitter_rho", C.c_double),
+        ("hide_prob", C.c_double),
     ]
 
 
@@ -71,6 +74,15 @@ def lib():
         L.oracle_particles.restype = C.c_int
         L.oracle_pixel_mass.argtypes = [C.c_double, C.c_double, C.c_int64]
         L.oracle_pixel_mass.restype = C.c_double
+        L.oracle_pixel_mass2.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                         C.c_int64, C.c_int64]
+        L.oracle_pixel_mass2.restype = C.c_double
+        L.oracle_splat_shapes.argtypes = [C.c_int32, C.c_int32, dp, C.c_int64, C.c_int32, dp]
+        L.oracle_splat_shapes.restype = C.c_int
+        L.oracle_particle_shapes.argtypes = [C.POINTER(OraclePair), dp]
+        L.oracle_particle_shapes.restype = C.c_int
+        L.oracle_round_particles.argtypes = [C.POINTER(OraclePair)]
+        L.oracle_round_particles.restype = C.c_int
         L.oracle_splat.argtypes = [C.c_int32, C.c_int32, dp, C.c_int64, C.c_int32, dp]
         L.oracle_splat.restype = C.c_int
         L.oracle_noise.argtypes = [C.c_uint64, C.c_uint64, C.c_int32, C.c_int64]
@@ -100,11 +112,14 @@ def _ptr(a, ctype):
 # ----------------------------------------------------------------------------
 
 def make_pair(spec, seed: int, integrator: str = "rk4", n_substeps: int = 4, dt=1.0,
-              quant_bits: int = 0, flow_shape=None) -> OraclePair:
+              quant_bits: int = 0, flow_shape=None, hide_prob=0.0) -> OraclePair:
     """Oracle parameters from a workload PairSpec (FP32 values widened to FP64)."""
     gh, gw = flow_shape if flow_shape is not None else (spec.height, spec.width)
     f = lambda v: float(np.float32(v))  # noqa: E731
+    g = lambda k: f(getattr(spec, k, 0.0))  # noqa: E731
     return OraclePair(
+        dy_min=g("dy_min"), dy_max=g("dy_max"), rho_min=g("rho_min"), rho_max=g("rho_max"),
+        jitter_d=g("jitter_d"), jitter_i=g("jitter_i"), jitter_rho=g("jitter_rho"), hide_prob=f(hide_prob),
         height=spec.height, width=spec.width, flow_h=gh, flow_w=gw,
         n_particles=spec.n_particles, seed=seed, pair_id=spec.pair_id,
         d_dist=spec.d_dist, integrator=0 if integrator == "rk4" else 1,
@@ -119,7 +134,7 @@ def pair_from_workload(wl, b: int) -> OraclePair:
     spec = wl.pairs[b]
     flow = wl.flows[spec.flow_index]
     return make_pair(spec, wl.seed, wl.integrator, wl.n_substeps, wl.dt, wl.quant_bits,
-                     flow_shape=flow.shape[:2])
+                     flow_shape=flow.shape[:2], hide_prob=getattr(wl, "hide_prob", 0.0))
 
 
 # ----------------------------------------------------------------------------
@@ -168,6 +183,29 @@ def particles(pair: OraclePair, flow: np.ndarray) -> np.ndarray:
 
 def pixel_mass(c: float, sigma: float, j: int) -> float:
     return lib().oracle_pixel_mass(c, sigma, j)
+
+
+def pixel_mass2(x0: float, y0: float, sx: float, sy: float, rho: float, j: int, i: int) -> float:
+    """Probability of pixel (i, j) under the normal density of Eq. 1 (general shape)."""
+    return lib().oracle_pixel_mass2(x0, y0, sx, sy, rho, j, i)
+
+
+SHAPE_COLUMNS = ("dx", "dy", "rho", "Ieff", "visible")
+
+
+def particle_shapes(pair: OraclePair) -> np.ndarray:
+    """[N, 2, 5] per particle and frame: d_x, d_y, rho, Ieff, visible (1.0 / 0.0)."""
+    out = np.zeros((max(pair.n_particles, 0), 2, 5), dtype=np.float64)
+    lib().oracle_particle_shapes(C.byref(pair), _ptr(out, C.c_double))
+    return out
+
+
+def splat_shapes(height: int, width: int, parts: np.ndarray, mode: int = 0) -> np.ndarray:
+    """Splat rows (x, y, d_x, d_y, rho, Ieff) into a fresh [H, W] frame (modes as splat())."""
+    p = np.ascontiguousarray(parts, dtype=np.float64).reshape(-1, 6)
+    S = np.zeros((height, width), dtype=np.float64)
+    lib().oracle_splat_shapes(height, width, _ptr(p, C.c_double), p.shape[0], mode, _ptr(S, C.c_double))
+    return S
 
 
 def splat(height: int, width: int, parts: np.ndarray, mode: int = 0) -> np.ndarray:

@@ -13,7 +13,8 @@
  *                                                       text after Eq. 1)
  *   - image-2 positions from the displacement map (x, y) -> (x+u, y+v)
  *                                                     ("Sampling the particles")
- *   - single-particle image: the Gaussian of Eq. 1 (rho = 0, sigma_x = sigma_y)
+ *   - single-particle image: the Gaussian of Eq. 1 (round by default; general
+ *     sigma_x, sigma_y, rho under R8)
  *   - contributions summed (superposition)          ("aggregation of the
  *                                                       particle contributions")
  *   - each particle rendered on a patch of 3 max(d)+1 px ("Efficient rasterization")
@@ -42,7 +43,20 @@
  *       FP32 like the GPU's FP32 epilogue.
  *   R7  random numbers: Philox4x32-10 (Salmon et al., SC'11) keyed by the seed,
  *       counter (index, stream tag, pair id): tag 0 -> (x, y, d, I) words,
- *       tag 1 -> (z, d2) words, tag 0x100 + f -> noise words of frame f.
+ *       tag 1 -> (z, d2) words, tag 2 -> (hide 1, hide 2, two normals for
+ *       the frame-2 change of d and I0), tag 3 -> (d_y, rho, two normals for
+ *       the frame-2 change of d_y and rho), tag 0x100 + f -> noise words of
+ *       frame f.
+ *   R8  general particle shapes (Eq. 1 with sigma_x != sigma_y and rho != 0;
+ *       text after Eq. 1): sigma_x = d / 4, sigma_y = d_y / 4 with d_y drawn
+ *       from its own interval (d_y = d when that interval is [0, 0]), rho from
+ *       its interval.  Frame-2 parameters are the frame-1 ones plus a zero-mean
+ *       Gaussian change of the configured std, clamped to the parameter's
+ *       interval (I0 to [i_min, i_max]).  A particle is hidden from each frame
+ *       independently with probability hide_prob (aggregation paragraph).
+ *       The pixel value is the integral of Eq. 1 over the pixel: the
+ *       integrated image of a particle is I0 2 pi sigma_x sigma_y sqrt(1-rho^2)
+ *       and its window is floor(x +- 1.5 d) by floor(y +- 1.5 d_y).
  *
  * Precision: FP64 everywhere except the quantisation decision (R6).
  */
@@ -66,6 +80,9 @@ typedef struct {
     double i_min, i_max, z_min, z_max, sheet_sigma;
     double illum_min, illum_max, noise_sigma, blur_sigma;
     double dt;
+    /* general shapes, frame-2 variation, hiding (R8); all 0: round particles */
+    double dy_min, dy_max, rho_min, rho_max;
+    double jitter_d, jitter_i, jitter_rho, hide_prob;
 } oracle_pair;
 
 /* ------------------------------------------------------------------------ */
@@ -118,7 +135,7 @@ static double box_muller(uint32_t wa, uint32_t wb, int second)
 /* ------------------------------------------------------------------------ */
 /* particle attributes (paper Section 2, text after Eq. 1; R1, R3, R7)      */
 /* ------------------------------------------------------------------------ */
-typedef struct { double x0, y0, d, intensity, z, ieff; } oracle_attr;
+typedef struct { double x0, y0, d, intensity, z, gain, ieff; } oracle_attr;
 
 static void particle_attr(const oracle_pair *p, uint32_t i, oracle_attr *a)
 {
@@ -139,7 +156,60 @@ static void particle_attr(const oracle_pair *p, uint32_t i, oracle_attr *a)
     double gain = 1.0;
     if (p->sheet_sigma > 0.0)
         gain = exp(-(a->z * a->z) / (2.0 * p->sheet_sigma * p->sheet_sigma));
+    a->gain = gain;
     a->ieff = a->intensity * gain;
+}
+
+static double clampd(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* A particle as rendered in one frame (R8). */
+typedef struct { double dx, dy, rho, ieff; int visible; } oracle_shape;
+
+int oracle_round_particles(const oracle_pair *p)
+{
+    return p->dy_min == 0.0 && p->dy_max == 0.0 && p->rho_min == 0.0 && p->rho_max == 0.0;
+}
+
+/* Frame 1 and frame 2 shapes of particle i with attributes a (R8). */
+static void particle_shapes(const oracle_pair *p, uint32_t i, const oracle_attr *a, oracle_shape s[2])
+{
+    uint32_t w2[4], w3[4];
+    oracle_stream_words(p->seed, p->pair_id, i, 2u, w2);
+    oracle_stream_words(p->seed, p->pair_id, i, 3u, w3);
+    const int same_d = p->dy_min == 0.0 && p->dy_max == 0.0;
+    double dy = same_d ? a->d : p->dy_min + u24(w3[0]) * (p->dy_max - p->dy_min);
+    double rho = p->rho_min + u24(w3[1]) * (p->rho_max - p->rho_min);
+    s[0].dx = a->d;
+    s[0].dy = dy;
+    s[0].rho = rho;
+    s[0].ieff = a->ieff;
+    s[0].visible = !(u24(w2[0]) < p->hide_prob);
+    double dx2 = clampd(a->d + p->jitter_d * box_muller(w2[2], w2[3], 0), p->d_min, p->d_max);
+    double i2 = clampd(a->intensity + p->jitter_i * box_muller(w2[2], w2[3], 1), p->i_min, p->i_max);
+    s[1].dx = dx2;
+    s[1].dy = same_d ? dx2 : clampd(dy + p->jitter_d * box_muller(w3[2], w3[3], 0), p->dy_min, p->dy_max);
+    s[1].rho = clampd(rho + p->jitter_rho * box_muller(w3[2], w3[3], 1), p->rho_min, p->rho_max);
+    s[1].ieff = i2 * a->gain;
+    s[1].visible = !(u24(w2[1]) < p->hide_prob);
+}
+
+/*
+ * Per-particle shape table, 10 doubles per particle: for frame 1 then
+ * frame 2, (d_x, d_y, rho, Ieff, visible).
+ */
+int oracle_particle_shapes(const oracle_pair *p, double *out)
+{
+    for (int64_t i = 0; i < p->n_particles; ++i) {
+        oracle_attr a;
+        oracle_shape s[2];
+        particle_attr(p, (uint32_t)i, &a);
+        particle_shapes(p, (uint32_t)i, &a, s);
+        for (int f = 0; f < 2; ++f) {
+            double *o = out + 10 * i + 5 * f;
+            o[0] = s[f].dx; o[1] = s[f].dy; o[2] = s[f].rho; o[3] = s[f].ieff; o[4] = (double)s[f].visible;
+        }
+    }
+    return 0;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -276,6 +346,114 @@ int oracle_splat(int32_t height, int32_t width, const double *parts, int64_t n, 
 }
 
 /* ------------------------------------------------------------------------ */
+/* pixel integration of Eq. 1 with sigma_x != sigma_y and rho != 0 (R8)     */
+/* ------------------------------------------------------------------------ */
+
+/* Gauss-Legendre rule on [-1, 1] with 16 nodes: the roots of the Legendre
+ * polynomial P_16 by Newton's method (P_n from its three-term recurrence,
+ * starting points cos(pi (k - 1/4) / (n + 1/2))); weight 2 / ((1 - t^2) P_n'(t)^2). */
+#define ORACLE_GL 16
+static double gl_x[ORACLE_GL], gl_w[ORACLE_GL];
+
+static void legendre(int n, double t, double *pn, double *dpn)
+{
+    double p0 = 1.0, p1 = t;
+    for (int m = 2; m <= n; ++m) {
+        double p2 = ((2.0 * m - 1.0) * t * p1 - (m - 1.0) * p0) / (double)m;
+        p0 = p1;
+        p1 = p2;
+    }
+    *pn = p1;
+    *dpn = (double)n * (t * p1 - p0) / (t * t - 1.0);
+}
+
+static void __attribute__((constructor)) gauss_legendre_init(void)
+{
+    const int n = ORACLE_GL;
+    for (int k = 1; k <= n; ++k) {
+        double t = cos(ORACLE_PI * ((double)k - 0.25) / ((double)n + 0.5)), pn, dpn;
+        for (int it = 0; it < 100; ++it) {
+            legendre(n, t, &pn, &dpn);
+            double step = pn / dpn;
+            t -= step;
+            if (fabs(step) < 1e-16) break;
+        }
+        legendre(n, t, &pn, &dpn);
+        gl_x[k - 1] = t;
+        gl_w[k - 1] = 2.0 / ((1.0 - t * t) * dpn * dpn);
+    }
+}
+
+/*
+ * Probability of the pixel [j, j+1) x [i, i+1) under the normal density of
+ * Eq. 1 centred at (x0, y0) with (sigma_x, sigma_y, rho).  rho = 0: the
+ * product of the 1-D masses.  Otherwise the x-marginal N(x0, sigma_x^2)
+ * times the conditional mass of y, which is normal with mean
+ * y0 + rho sigma_y (x - x0) / sigma_x and std sigma_y sqrt(1 - rho^2): exact
+ * in y (erfc), composite 16-node Gauss-Legendre in x over sub-intervals no
+ * wider than half the shortest x-scale of the integrand,
+ * min(sigma_x, sigma_x sqrt(1 - rho^2) / |rho|).
+ */
+double oracle_pixel_mass2(double x0, double y0, double sx, double sy, double rho, int64_t j, int64_t i)
+{
+    if (rho == 0.0) return oracle_pixel_mass(x0, sx, j) * oracle_pixel_mass(y0, sy, i);
+    const double c = sqrt(1.0 - rho * rho);
+    const double ell = fabs(rho) > c ? sx * c / fabs(rho) : sx;
+    long nsub = (long)ceil(2.0 / ell);
+    if (nsub < 1) nsub = 1;
+    if (nsub > 4096) nsub = 4096;
+    const double h = 1.0 / (double)nsub;
+    double sum = 0.0;
+    for (long q = 0; q < nsub; ++q) {
+        const double a = (double)j + (double)q * h;
+        for (int k = 0; k < ORACLE_GL; ++k) {
+            const double x = a + 0.5 * h * (gl_x[k] + 1.0);
+            const double t = (x - x0) / sx;
+            const double px = exp(-0.5 * t * t) / (2.50662827463100050242 * sx);
+            sum += 0.5 * h * gl_w[k] * px * oracle_pixel_mass(y0 + rho * sy * t, sy * c, i);
+        }
+    }
+    return sum;
+}
+
+/*
+ * Accumulate particles of general shape into one frame S[H][W] (R8; not
+ * cleared here).  parts: n rows of (x, y, d_x, d_y, rho, Ieff).  mode 0:
+ * windowed, pixel-integrated (the method); mode 1: pixel-integrated over
+ * every pixel (brute force); mode 2: Eq. 1 point-sampled at pixel centres
+ * inside the window.
+ */
+int oracle_splat_shapes(int32_t height, int32_t width, const double *parts, int64_t n, int32_t mode, double *S)
+{
+    for (int64_t k = 0; k < n; ++k) {
+        const double *r = parts + 6 * k;
+        double x = r[0], y = r[1], dx = r[2], dy = r[3], rho = r[4], ieff = r[5];
+        double sx = dx / 4.0, sy = dy / 4.0, c = sqrt(1.0 - rho * rho);
+        double amp = ieff * 2.0 * ORACLE_PI * sx * sy * c;
+        long j0 = (long)floor(x - 1.5 * dx), j1 = (long)floor(x + 1.5 * dx);
+        long i0 = (long)floor(y - 1.5 * dy), i1 = (long)floor(y + 1.5 * dy);
+        if (mode == 1) {
+            j0 = 0; j1 = width - 1; i0 = 0; i1 = height - 1;
+        }
+        if (j0 < 0) j0 = 0;
+        if (i0 < 0) i0 = 0;
+        if (j1 > width - 1) j1 = width - 1;
+        if (i1 > height - 1) i1 = height - 1;
+        for (long i = i0; i <= i1; ++i)
+            for (long j = j0; j <= j1; ++j) {
+                if (mode == 2) {
+                    double tx = ((double)j + 0.5 - x) / sx, ty = ((double)i + 0.5 - y) / sy;
+                    double e = (tx * tx - 2.0 * rho * tx * ty + ty * ty) / (2.0 * (1.0 - rho * rho));
+                    S[i * width + j] += ieff * exp(-e);
+                } else {
+                    S[i * width + j] += amp * oracle_pixel_mass2(x, y, sx, sy, rho, j, i);
+                }
+            }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* epilogue (R6)                                                            */
 /* ------------------------------------------------------------------------ */
 
@@ -376,6 +554,34 @@ int oracle_render_pair(const oracle_pair *p, const float *flow, double *S, doubl
     if (!tab || !xy || !s) { free(tab); free(xy); if (!S) free(s); return -1; }
     oracle_particles(p, flow, tab);
     memset(s, 0, sizeof(double) * (size_t)(2 * HW));
+    const int general = !oracle_round_particles(p) || p->jitter_d != 0.0 || p->jitter_i != 0.0 ||
+                        p->jitter_rho != 0.0 || p->hide_prob > 0.0;
+    if (general) {
+        double *sh = (double *)malloc(sizeof(double) * (size_t)(10 * (n > 0 ? n : 1)));
+        double *rows = (double *)malloc(sizeof(double) * (size_t)(6 * (n > 0 ? n : 1)));
+        if (!sh || !rows) { free(sh); free(rows); free(tab); free(xy); if (!S) free(s); return -1; }
+        oracle_particle_shapes(p, sh);
+        for (int f = 0; f < 2; ++f) {
+            int64_t m = 0;
+            for (int64_t i = 0; i < n; ++i) {
+                const double *q = sh + 10 * i + 5 * f;
+                if (q[4] == 0.0) continue; /* hidden from this frame */
+                double *r = rows + 6 * m++;
+                r[0] = tab[8 * i + (f ? 6 : 0)];
+                r[1] = tab[8 * i + (f ? 7 : 1)];
+                r[2] = q[0]; r[3] = q[1]; r[4] = q[2]; r[5] = q[3];
+            }
+            oracle_splat_shapes(p->height, p->width, rows, m, splat_mode, s + f * HW);
+            oracle_epilogue(p, f, s + f * HW, B + f * HW, Q ? Q + f * HW : NULL);
+        }
+        free(sh);
+        free(rows);
+        if (parts) memcpy(parts, tab, sizeof(double) * (size_t)(8 * n));
+        free(tab);
+        free(xy);
+        if (!S) free(s);
+        return 0;
+    }
     for (int f = 0; f < 2; ++f) {
         for (int64_t i = 0; i < n; ++i) {
             xy[4 * i] = tab[8 * i + (f ? 6 : 0)];

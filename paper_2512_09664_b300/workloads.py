@@ -57,11 +57,21 @@ class PairSpec:
     illum_max: np.float32 = F32(1.0)
     noise_sigma: np.float32 = F32(0.0)
     blur_sigma: np.float32 = F32(0.0)
+    # general particle shapes and frame-2 variation (all 0: round particles,
+    # identical parameters in both frames)
+    dy_min: np.float32 = F32(0.0)   # diameter along y ~ U[dy_min, dy_max]; 0, 0: d_y = d
+    dy_max: np.float32 = F32(0.0)
+    rho_min: np.float32 = F32(0.0)  # correlation of Eq. 1 ~ U[rho_min, rho_max]
+    rho_max: np.float32 = F32(0.0)
+    jitter_d: np.float32 = F32(0.0)    # std of the frame-2 change of each diameter (px)
+    jitter_i: np.float32 = F32(0.0)    # std of the frame-2 change of I0
+    jitter_rho: np.float32 = F32(0.0)  # std of the frame-2 change of rho
 
     def __post_init__(self):
         for k in ("d_min", "d_max", "d_mu", "d_sigma", "i_min", "i_max", "z_min",
                   "z_max", "sheet_sigma", "illum_min", "illum_max", "noise_sigma",
-                  "blur_sigma"):
+                  "blur_sigma", "dy_min", "dy_max", "rho_min", "rho_max", "jitter_d",
+                  "jitter_i", "jitter_rho"):
             setattr(self, k, F32(getattr(self, k)))
 
 
@@ -81,9 +91,11 @@ class Workload:
     dt: np.float32 = F32(1.0)
     description: str = ""
     meta: dict = field(default_factory=dict)
+    hide_prob: np.float32 = F32(0.0)  # probability of hiding a particle from each frame
 
     def __post_init__(self):
         self.dt = F32(self.dt)
+        self.hide_prob = F32(self.hide_prob)
 
     @property
     def n_pairs(self) -> int:
