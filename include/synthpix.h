@@ -18,7 +18,11 @@
  *  - sigma = d / 4 for a particle of diameter d; the particle image is
  *    integrated over each pixel (separable erf differences) on the window
  *    [floor(x - 1.5 d), floor(x + 1.5 d)]^2, the 3 d + 1 patch of Section 2
- *    "Efficient rasterization".
+ *    "Efficient rasterization".  General particles (Eq. 1 with
+ *    sigma_x = d / 4, sigma_y = d_y / 4 and correlation rho) are integrated
+ *    over each pixel too, on the window floor(x +- 1.5 d) by
+ *    floor(y +- 1.5 d_y); their integrated image is
+ *    Ieff 2 pi sigma_x sigma_y sqrt(1 - rho^2).
  *  - Random numbers: Philox4x32-10 keyed by the batch seed; the output of a
  *    pair depends only on (seed, pair_id, its descriptor, its flow grid).
  *  - All device pointers are owned by the caller.  The library allocates no
@@ -39,7 +43,7 @@
 extern "C" {
 #endif
 
-#define SYNTHPIX_ABI_VERSION 1
+#define SYNTHPIX_ABI_VERSION 2
 
 /* ---- status codes ------------------------------------------------------ */
 #define SYNTHPIX_OK            0
@@ -90,7 +94,24 @@ typedef struct synthpix_pair_desc {
                                     L = min + (max-min) sin^2(pi (j+.5)/W) sin^2(pi (i+.5)/H) */
     float noise_sigma;           /* additive Gaussian noise std (full scale 1.0)      */
     float blur_sigma;            /* Gaussian blur std in px (radius ceil(3 sigma)), 0..8 */
-    float reserved[7];           /* must be zero                                       */
+    /* General particle shapes and second-image variation (text after Eq. 1:
+       sigma_x, sigma_y, rho drawn per particle from intervals; each parameter
+       of the second image varies by a zero-mean Gaussian).  All zero: round
+       particles, the same parameters in both frames.  Drawn from Philox
+       stream 2 (hiding words, normals of the d and I0 changes) and stream 3
+       (d_y, rho, normals of the d_y and rho changes).  Any non-zero field
+       (or batch->hide_prob > 0) makes the render advect per particle; d_y or
+       rho non-zero in any pair selects the general-shape splat (32-byte
+       bin records, per-pixel quadrature when rho != 0).                       */
+    float dy_min, dy_max;        /* diameter along y, sigma_y = d_y / 4, d_y ~ U[dy_min,
+                                    dy_max]; 0, 0: d_y = d.  Else 0 < dy_min <= dy_max <= 32 */
+    float rho_min, rho_max;      /* correlation of Eq. 1 ~ U[rho_min, rho_max],
+                                    -0.95 <= rho_min <= rho_max <= 0.95              */
+    float jitter_d;              /* std (px) of the frame-2 change of d and of d_y (drawn
+                                    independently; with d_y = d one change for both),
+                                    the results clamped to [d_min, d_max] / [dy_min, dy_max] */
+    float jitter_i;              /* std of the frame-2 change of I0, clamped to [i_min, i_max] */
+    float jitter_rho;            /* std of the frame-2 change of rho, clamped to its interval */
 } synthpix_pair_desc;
 
 /*
@@ -122,7 +143,10 @@ typedef struct synthpix_batch_desc {
                                     on chip with coalesced loads.  Renders from given
                                     particles and the adjoint always gather per
                                     particle.  Both give the same positions.          */
-    int32_t  reserved[6];        /* must be zero                                       */
+    float    hide_prob;          /* probability, 0..1, that a particle is left out of a
+                                    frame, independently per frame (Section 2,
+                                    aggregation of the particle contributions)         */
+    int32_t  reserved[5];        /* must be zero                                       */
 } synthpix_batch_desc;
 
 /*
@@ -171,6 +195,8 @@ int synthpix_render_pairs(const synthpix_batch_desc *batch, const synthpix_pair_
  * seeded values (then identical to synthpix_render_pairs).  Intensities and
  * out-of-plane positions still come from the seeded streams.  Used for
  * differentiation (finite differences, optimisation over positions).
+ * Round particles only: a batch with hide_prob or any general-shape or
+ * variation field set fails with SYNTHPIX_EUNSUPPORTED.
  */
 int synthpix_render_pairs_from(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
                                const synthpix_pair_desc *pairs_dev, int32_t n_pairs,
@@ -216,8 +242,8 @@ int synthpix_advect_particles(const synthpix_batch_desc *batch, const synthpix_p
  *   grad_particles  [sum of n_particles][3] dL/d(x0, y0, d), overwritten, or NULL;
  * for the frames B = L * S + noise (the splat of Eq. 1 integrated per pixel,
  * times the illumination field).  Requires out_dtype F32 (quantisation has no
- * gradient), blur_sigma = 0 for every pair, and at most 64 substeps
- * (SYNTHPIX_EUNSUPPORTED otherwise).  particles_in as in
+ * gradient), blur_sigma = 0 for every pair, at most 64 substeps and round
+ * particles without hiding or variation (SYNTHPIX_EUNSUPPORTED otherwise).  particles_in as in
  * synthpix_render_pairs_from.  Positions and bins are recomputed, not taken
  * from a forward call.  The splat gradient is a per-particle reduction over
  * its window; flow gradients are accumulated with atomics, so their last bits

@@ -39,7 +39,8 @@ class PairDesc(C.Structure):
         ("i_min", C.c_float), ("i_max", C.c_float), ("z_min", C.c_float), ("z_max", C.c_float),
         ("sheet_sigma", C.c_float), ("illum_min", C.c_float), ("illum_max", C.c_float),
         ("noise_sigma", C.c_float), ("blur_sigma", C.c_float),
-        ("reserved", C.c_float * 7),
+        ("dy_min", C.c_float), ("dy_max", C.c_float), ("rho_min", C.c_float), ("rho_max", C.c_float),
+        ("jitter_d", C.c_float), ("jitter_i", C.c_float), ("jitter_rho", C.c_float),
     ]
 
 
@@ -47,7 +48,8 @@ class BatchDesc(C.Structure):
     _fields_ = [
         ("seed", C.c_uint64), ("out_dtype", C.c_int32), ("quant_bits", C.c_int32),
         ("inter_dtype", C.c_int32), ("integrator", C.c_int32), ("n_substeps", C.c_int32),
-        ("dt", C.c_float), ("tile", C.c_int32), ("flags", C.c_int32), ("reserved", C.c_int32 * 6),
+        ("dt", C.c_float), ("tile", C.c_int32), ("flags", C.c_int32), ("hide_prob", C.c_float),
+        ("reserved", C.c_int32 * 5),
     ]
 
 
@@ -121,7 +123,7 @@ def _check(rc: int):
 # ----------------------------------------------------------------------------
 
 def batch_desc(seed: int, out_dtype="f32", quant_bits=0, inter_dtype="f32", integrator="rk4",
-               n_substeps=4, dt=1.0, tile=0) -> BatchDesc:
+               n_substeps=4, dt=1.0, tile=0, hide_prob=0.0) -> BatchDesc:
     b = BatchDesc()
     b.seed = seed
     b.out_dtype = DTYPE_CODE[out_dtype]
@@ -131,6 +133,7 @@ def batch_desc(seed: int, out_dtype="f32", quant_bits=0, inter_dtype="f32", inte
     b.n_substeps = n_substeps
     b.dt = float(np.float32(dt))
     b.tile = tile
+    b.hide_prob = float(np.float32(hide_prob))
     return b
 
 
@@ -145,6 +148,8 @@ def pair_desc(spec, image_offset: int, flow_offset: int, flow_shape) -> PairDesc
     for k in ("d_min", "d_max", "d_mu", "d_sigma", "i_min", "i_max", "z_min", "z_max", "sheet_sigma",
               "illum_min", "illum_max", "noise_sigma", "blur_sigma"):
         setattr(p, k, float(getattr(spec, k)))
+    for k in ("dy_min", "dy_max", "rho_min", "rho_max", "jitter_d", "jitter_i", "jitter_rho"):
+        setattr(p, k, float(getattr(spec, k, 0.0)))
     return p
 
 
@@ -183,7 +188,8 @@ def pack(wl, tile: int = 0, out_dtype: Optional[str] = None, inter_dtype: Option
         arr[b] = pair_desc(spec, io, flow_off[spec.flow_index], wl.flows[spec.flow_index].shape[:2])
         io += 2 * spec.height * spec.width
     bd = batch_desc(wl.seed, out_dtype, wl.quant_bits if out_dtype in ("u8", "u16") else 0,
-                    inter_dtype or wl.inter_dtype, wl.integrator, wl.n_substeps, wl.dt, tile)
+                    inter_dtype or wl.inter_dtype, wl.integrator, wl.n_substeps, wl.dt, tile,
+                    getattr(wl, "hide_prob", 0.0))
     flows = np.concatenate(flat) if flat else np.zeros(2, np.float32)
     return Packed(bd, arr, wl.n_pairs, flows, img_off, io, out_dtype,
                   [(p.height, p.width) for p in wl.pairs])

@@ -30,6 +30,8 @@ struct Plan {
     int32_t max_halo;
     int32_t max_r;
     float max_d;
+    int32_t ext;      // per-frame shapes: general shapes, frame-2 variation or hiding
+    int32_t general;  // general-shape splat (32-byte records)
 };
 
 int check_batch(const synthpix_batch_desc *b) {
@@ -53,7 +55,9 @@ int check_batch(const synthpix_batch_desc *b) {
         return fail(SYNTHPIX_EINVAL, "tile %d is not 0, 16, 32, 64 or 128", b->tile);
     if (b->flags & ~SYNTHPIX_FLAG_GATHER_ADVECT)
         return fail(SYNTHPIX_EUNSUPPORTED, "unknown flags 0x%x", b->flags);
-    for (int k = 0; k < 6; ++k)
+    if (!finite(b->hide_prob) || b->hide_prob < 0.0f || b->hide_prob > 1.0f)
+        return fail(SYNTHPIX_EINVAL, "hide_prob must lie in [0, 1]");
+    for (int k = 0; k < 5; ++k)
         if (b->reserved[k] != 0) return fail(SYNTHPIX_EUNSUPPORTED, "batch reserved[%d] is not zero", k);
     return SYNTHPIX_OK;
 }
@@ -69,7 +73,8 @@ int check_pair(const synthpix_pair_desc &d, int b) {
         return fail(SYNTHPIX_EINVAL, "pair %d: image_offset out of range", b);
     if (d.d_dist != 0 && d.d_dist != 1) return fail(SYNTHPIX_EINVAL, "pair %d: d_dist must be 0 or 1", b);
     const float fs[] = {d.d_min, d.d_max, d.d_mu, d.d_sigma, d.i_min, d.i_max, d.z_min, d.z_max,
-                        d.sheet_sigma, d.illum_min, d.illum_max, d.noise_sigma, d.blur_sigma};
+                        d.sheet_sigma, d.illum_min, d.illum_max, d.noise_sigma, d.blur_sigma,
+                        d.dy_min, d.dy_max, d.rho_min, d.rho_max, d.jitter_d, d.jitter_i, d.jitter_rho};
     for (float v : fs)
         if (!finite(v)) return fail(SYNTHPIX_EINVAL, "pair %d: non-finite parameter", b);
     if (!(d.d_min > 0.0f) || d.d_max < d.d_min || d.d_max > 32.0f)
@@ -82,8 +87,13 @@ int check_pair(const synthpix_pair_desc &d, int b) {
         return fail(SYNTHPIX_EINVAL, "pair %d: need illum_min <= illum_max within +-1e6", b);
     if (d.noise_sigma < 0.0f || d.noise_sigma > 1e6f) return fail(SYNTHPIX_EINVAL, "pair %d: noise_sigma < 0", b);
     if (d.blur_sigma < 0.0f || d.blur_sigma > 8.0f) return fail(SYNTHPIX_EINVAL, "pair %d: blur_sigma outside 0..8", b);
-    for (int k = 0; k < 7; ++k)
-        if (d.reserved[k] != 0.0f) return fail(SYNTHPIX_EUNSUPPORTED, "pair %d: reserved[%d] is not zero", b, k);
+    if (!(d.dy_min == 0.0f && d.dy_max == 0.0f) && !(d.dy_min > 0.0f && d.dy_max >= d.dy_min && d.dy_max <= 32.0f))
+        return fail(SYNTHPIX_EINVAL, "pair %d: need dy_min = dy_max = 0 or 0 < dy_min <= dy_max <= 32", b);
+    if (d.rho_min < -0.95f || d.rho_max < d.rho_min || d.rho_max > 0.95f)
+        return fail(SYNTHPIX_EINVAL, "pair %d: need -0.95 <= rho_min <= rho_max <= 0.95", b);
+    if (d.jitter_d < 0.0f || d.jitter_i < 0.0f || d.jitter_rho < 0.0f || d.jitter_d > 1e6f || d.jitter_i > 1e6f ||
+        d.jitter_rho > 1e6f)
+        return fail(SYNTHPIX_EINVAL, "pair %d: jitter stds must lie in [0, 1e6]", b);
     return SYNTHPIX_OK;
 }
 
@@ -117,6 +127,8 @@ int make_plan_tile(const synthpix_batch_desc *batch, const synthpix_pair_desc *p
     P.max_halo = 0;
     P.max_r = 0;
     P.max_d = 0.0f;
+    P.ext = batch->hide_prob > 0.0f ? 1 : 0;
+    P.general = 0;
     spx::Layout &L = P.L;
     L.n_part = L.n_tiles = L.n_list = L.n_inter = L.n_chunks = 0;
     for (int32_t b = 0; b < n_pairs; ++b) {
@@ -130,7 +142,10 @@ int make_plan_tile(const synthpix_batch_desc *batch, const synthpix_pair_desc *p
         if (!P.fused) L.n_inter += 2LL * pairs[b].height * pairs[b].width;
         if (g.halo > P.max_halo) P.max_halo = g.halo;
         if (g.blur_r > P.max_r) P.max_r = g.blur_r;
-        if (pairs[b].d_max > P.max_d) P.max_d = pairs[b].d_max;
+        const float dmax = spx::pair_max_diameter(pairs[b]);
+        if (dmax > P.max_d) P.max_d = dmax;
+        if (spx::pair_general_shape(pairs[b])) P.general = P.ext = 1;
+        if (pairs[b].jitter_d != 0.0f || pairs[b].jitter_i != 0.0f || pairs[b].jitter_rho != 0.0f) P.ext = 1;
     }
     if (L.n_tiles > 0x7FFFFFFFLL) return fail(SYNTHPIX_EINVAL, "batch has more than 2^31-1 tiles");
     if (L.n_chunks > 0x7FFFFFFFLL) return fail(SYNTHPIX_EINVAL, "batch has more than 2^40 particles");
@@ -151,7 +166,9 @@ int make_plan_tile(const synthpix_batch_desc *batch, const synthpix_pair_desc *p
     L.items = take((size_t)L.n_tiles * sizeof(spx::ItemInfo));
     L.pos = take((size_t)L.n_part * 32);
     L.sa = take((size_t)L.n_part * 8);
-    L.rec = take((size_t)L.n_list * sizeof(spx::Record) + 64);  // + read-over of 16-byte staging
+    L.shape = take(P.ext ? (size_t)L.n_part * 2 * sizeof(float4) : 0);
+    const size_t rec_bytes = P.general ? sizeof(spx::RecordG) : sizeof(spx::Record);
+    L.rec = take((size_t)L.n_list * rec_bytes + 64);  // + read-over of 16-byte staging
     L.adv = take((size_t)(L.n_list / 2) * sizeof(spx::Record));  // frame-1 segments only
     L.inter = take((size_t)L.n_inter * 2);
     L.gfr = take((size_t)L.n_part * 2 * sizeof(float4));
@@ -228,6 +245,9 @@ static int run(Mode mode, const synthpix_batch_desc *batch, const synthpix_pair_
         return fail(SYNTHPIX_EINVAL, "particles_out is NULL or not 4-byte aligned");
     if (x.particles_in && ((uintptr_t)x.particles_in & 3))
         return fail(SYNTHPIX_EINVAL, "particles_in is not 4-byte aligned");
+    if ((x.particles_in || mode == Mode::Backward) && P.ext)
+        return fail(SYNTHPIX_EUNSUPPORTED,
+                    "given particles and the adjoint need round particles without hiding or frame-2 variation");
     if (mode == Mode::Backward) {
         if (!x.grad_images || ((uintptr_t)x.grad_images & 3))
             return fail(SYNTHPIX_EINVAL, "grad_images is NULL or not 4-byte aligned");
@@ -288,13 +308,19 @@ static int run(Mode mode, const synthpix_batch_desc *batch, const synthpix_pair_
     a.pos0 = reinterpret_cast<float4 *>(ws + L.pos);
     a.pos1 = a.pos0 + L.n_part;
     a.sa = reinterpret_cast<float2 *>(ws + L.sa);
+    a.shape = reinterpret_cast<float4 *>(ws + L.shape);
+    a.ext = P.ext;
+    a.general = P.general;
+    a.hide_prob = batch->hide_prob;
     a.count = mode == Mode::Render ? reinterpret_cast<uint32_t *>(ws + L.count) : nullptr;
     a.off = reinterpret_cast<uint32_t *>(ws + L.off);
     a.cursor = reinterpret_cast<uint32_t *>(ws + L.cursor);
     a.items = reinterpret_cast<spx::ItemInfo *>(ws + L.items);
     a.rec = reinterpret_cast<spx::Record *>(ws + L.rec);
     a.adv = reinterpret_cast<spx::Record *>(ws + L.adv);
-    a.tiled = (mode == Mode::Render && !x.particles_in && !(batch->flags & SYNTHPIX_FLAG_GATHER_ADVECT)) ? 1 : 0;
+    // per-frame shapes need each particle's index: those renders advect per particle
+    a.tiled = (mode == Mode::Render && !x.particles_in && !P.ext && !(batch->flags & SYNTHPIX_FLAG_GATHER_ADVECT))
+                  ? 1 : 0;
     a.ticket = ticket;
     a.rec_buf_bytes = spx::rec_buf_bytes_for(P.tile);
     a.blur_w = blur_w;

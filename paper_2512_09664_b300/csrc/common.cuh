@@ -45,6 +45,16 @@ __host__ __device__ inline int32_t blur_radius_of(float blur_sigma) {
 // Upper bound of the pixels along one axis of a particle window [floor(x-1.5d), floor(x+1.5d)].
 __host__ __device__ inline int32_t window_max(float d_max) { return (int32_t)floor(3.0 * (double)d_max) + 5; }
 
+// Largest particle diameter of a pair along either axis.
+__host__ __device__ inline float pair_max_diameter(const synthpix_pair_desc &d) {
+    return d.dy_max > d.d_max ? d.dy_max : d.d_max;
+}
+
+// The pair draws general shapes (d_y or rho intervals set).
+__host__ __device__ inline bool pair_general_shape(const synthpix_pair_desc &d) {
+    return d.dy_min != 0.0f || d.dy_max != 0.0f || d.rho_min != 0.0f || d.rho_max != 0.0f;
+}
+
 __host__ __device__ inline PairGeom pair_geom(const synthpix_pair_desc &d, int tile, bool fused) {
     PairGeom g;
     g.tiles_x = (d.width + tile - 1) / tile;
@@ -54,7 +64,7 @@ __host__ __device__ inline PairGeom pair_geom(const synthpix_pair_desc &d, int t
     g.halo = fused ? g.blur_r : 0;
     // pixels of a clipped particle window: <= floor(3 d_max) + 2, plus margin
     // for FP32 rounding of d and x +- 1.5 d; widened by the halo on both sides
-    int32_t ext = window_max(d.d_max) + 2 * g.halo;
+    int32_t ext = window_max(pair_max_diameter(d)) + 2 * g.halo;
     g.span = (ext - 1) / tile + 2;
     int32_t sx = g.span < g.tiles_x ? g.span : g.tiles_x;
     int32_t sy = g.span < g.tiles_y ? g.span : g.tiles_y;
@@ -71,6 +81,17 @@ struct Record {
 };
 static_assert(sizeof(Record) == 24, "Record layout");
 
+// A particle of general shape as binned for one frame (Eq. 1 with
+// sigma_x != sigma_y or rho != 0).
+struct RecordG {
+    float fx, fy;      // fractions of the split position
+    int32_t ix, iy;    // integer parts
+    float sx, sy;      // d / 4 and d_y / 4
+    float rho;         // correlation
+    float amp;         // Ieff * 2 pi sigma_x sigma_y sqrt(1 - rho^2)
+};
+static_assert(sizeof(RecordG) == 32, "RecordG layout");
+
 // One work item of the splat: the bin of one (pair, frame, tile).
 struct ItemInfo {
     int32_t pair, frame, tile;
@@ -81,7 +102,7 @@ static_assert(sizeof(ItemInfo) == 24, "ItemInfo layout");
 
 // Workspace layout (byte offsets, 256-aligned), computed on the host.
 struct Layout {
-    size_t plan, desc, check, blur, count, off, cursor, items, pos, sa, rec, adv, inter, gfr, total;
+    size_t plan, desc, check, blur, count, off, cursor, items, pos, sa, shape, rec, adv, inter, gfr, total;
     int64_t n_part, n_tiles, n_list, n_inter, n_chunks;
 };
 
@@ -97,6 +118,8 @@ __host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~(size
 // Stream layout: counter = (index, tag, pair_id lo, pair_id hi), key = seed.
 constexpr uint32_t kTagAttrA = 0u;      // (x, y, d, I)
 constexpr uint32_t kTagAttrB = 1u;      // (z, d2, -, -)
+constexpr uint32_t kTagShapeA = 2u;     // (hide 1, hide 2, normals of the frame-2 d and I0 changes)
+constexpr uint32_t kTagShapeB = 3u;     // (d_y, rho, normals of the frame-2 d_y and rho changes)
 constexpr uint32_t kTagNoise = 0x100u;  // + frame; index = pixel / 4
 
 // The ten round keys (key + r * Weyl increments) are computed once per

@@ -26,6 +26,11 @@ struct KernelArgs {
     void *images;
     float4 *pos0, *pos1;              // split positions of frames 1 and 2
     float2 *sa;                       // (sigma, Ieff * 2 pi sigma^2)
+    float4 *shape;                    // ext: [2][n_part] (sigma_x, sigma_y, rho, amplitude) per frame;
+                                      // sigma_x < 0: hidden from that frame
+    int32_t ext;                      // 1: per-frame shapes (general shapes, variation or hiding)
+    int32_t general;                  // 1: bins hold RecordG (general-shape splat)
+    float hide_prob;                  // probability of hiding a particle from a frame
     uint32_t *count, *off, *cursor;   // per (pair, frame, tile)
     ItemInfo *items;                  // per (pair, frame, tile): the splat's work items
     Record *rec;                      // bins
@@ -64,8 +69,10 @@ constexpr int kSplatMaxThreads = 1024;  // k_splat at tile 128 (one CTA per SM)
 constexpr int kStageHeader = 320;       // descriptor (128) + plan (64) + blur taps (128)
 constexpr int kRecBufBytes = 8192;      // each staged-records buffer of k_splat (tiles up to 64)
 constexpr int kRecBufBytesLarge = 24576;  // the same at tile 128
-// records per staged chunk of a buffer
-__host__ __device__ constexpr int rec_cap(int buf_bytes) { return (buf_bytes - kStageHeader - 32) / 24; }
+// records of rec_bytes bytes per staged chunk of a buffer
+__host__ __device__ constexpr int rec_cap(int buf_bytes, int rec_bytes = 24) {
+    return (buf_bytes - kStageHeader - 32) / rec_bytes;
+}
 // threads of a k_splat CTA at a tile edge
 // (256 below tile 128: three CTAs per SM hide each other's barriers better
 // than two of 512)

@@ -95,6 +95,17 @@ __device__ __forceinline__ Window particle_window(int32_t ix, float fx, int32_t 
     return w;
 }
 
+// The same with half-extents r15x = 1.5 d along x and r15y = 1.5 d_y along y.
+__device__ __forceinline__ Window particle_window2(int32_t ix, float fx, int32_t iy, float fy, float r15x,
+                                                   float r15y, int32_t W, int32_t H) {
+    Window w;
+    w.j0 = max(ix + (int32_t)floorf(fx - r15x), 0);
+    w.j1 = min(ix + (int32_t)floorf(fx + r15x), W - 1);
+    w.i0 = max(iy + (int32_t)floorf(fy - r15y), 0);
+    w.i1 = min(iy + (int32_t)floorf(fy + r15y), H - 1);
+    return w;
+}
+
 // Tiles whose halo-widened rectangle meets the window.
 __device__ __forceinline__ void window_tiles(const Window &w, int32_t halo, int32_t tile, int32_t W, int32_t H,
                                              int32_t &tx0, int32_t &tx1, int32_t &ty0, int32_t &ty1) {
@@ -123,11 +134,13 @@ __device__ __forceinline__ float pixel_mass(float sa, float sb, bool a_pos, bool
     return fmaxf(sb - sa, 0.0f);
 }
 
-// A particle of frame 1: split position, sigma = d / 4, amplitude Ieff 2 pi sigma^2.
+// A particle of frame 1: split position, sigma = d / 4, amplitude Ieff 2 pi sigma^2;
+// d, I0 and the sheet gain for the per-frame shapes.
 struct Seeded {
     int32_t ix, iy;
     float fx, fy;
     float sigma, amp;
+    float d, i0, gain;
 };
 
 // Attributes of particle i of a pair (Section 2, "Sampling the particles":
@@ -171,7 +184,53 @@ __device__ __forceinline__ Seeded seed_particle(const KernelArgs &a, const synth
     if (D.sheet_sigma > 0.0f) gain = expf(-(z * z) / (2.0f * D.sheet_sigma * D.sheet_sigma));
     P.sigma = 0.25f * d;
     P.amp = (I0 * gain) * (6.28318530717958647692f * P.sigma * P.sigma);  // Ieff * 2 pi sigma^2
+    P.d = d;
+    P.i0 = I0;
+    P.gain = gain;
     return P;
+}
+
+// Standard normals (cos and sin branches of Box-Muller) from two words.
+__device__ __forceinline__ void normal_pair(uint32_t wa, uint32_t wb, float &n0, float &n1) {
+    float s, c;
+    sincospif(2.0f * u24f(wb), &s, &c);
+    const float r = sqrtf(-2.0f * logf(uo24f(wa)));
+    n0 = r * c;
+    n1 = r * s;
+}
+
+__device__ __forceinline__ float clampf(float v, float lo, float hi) { return fminf(fmaxf(v, lo), hi); }
+
+// (sigma_x, sigma_y, rho, Ieff 2 pi sigma_x sigma_y sqrt(1 - rho^2)) of a
+// particle in one frame; sigma_x = -1 when it is hidden from the frame.
+__device__ __forceinline__ float4 frame_shape(float dx, float dy, float rho, float ieff, bool hidden) {
+    const float sx = 0.25f * dx, sy = 0.25f * dy;
+    const float amp = ieff * (6.28318530717958647692f * sx * sy * sqrtf(1.0f - rho * rho));
+    return make_float4(hidden ? -1.0f : sx, sy, rho, amp);
+}
+
+// Frame-1 and frame-2 shapes of particle i (Section 2, text after Eq. 1:
+// sigma_x, sigma_y and rho drawn per particle from their intervals; every
+// parameter of the second image is the first image's plus a zero-mean
+// Gaussian change, clamped to the parameter's interval; aggregation
+// paragraph: a particle hidden from each image with probability hide_prob).
+// d_y = d when the d_y interval is [0, 0] (then one change for both axes).
+__device__ __forceinline__ void frame_shapes(const KernelArgs &a, const synthpix_pair_desc &D, uint32_t i,
+                                             const Seeded &P, float4 &s1, float4 &s2) {
+    const uint4 w2 = stream_words(a.keys, D.pair_id, i, kTagShapeA);
+    const uint4 w3 = stream_words(a.keys, D.pair_id, i, kTagShapeB);
+    const bool same_d = D.dy_min == 0.0f && D.dy_max == 0.0f;
+    const float dy = same_d ? P.d : fminf(fmaf(u24f(w3.x), D.dy_max - D.dy_min, D.dy_min), D.dy_max);
+    const float rho = fminf(fmaf(u24f(w3.y), D.rho_max - D.rho_min, D.rho_min), D.rho_max);
+    float nd, ni, ndy, nr;
+    normal_pair(w2.z, w2.w, nd, ni);
+    normal_pair(w3.z, w3.w, ndy, nr);
+    const float dx2 = clampf(fmaf(D.jitter_d, nd, P.d), D.d_min, D.d_max);
+    const float dy2 = same_d ? dx2 : clampf(fmaf(D.jitter_d, ndy, dy), D.dy_min, D.dy_max);
+    const float rho2 = clampf(fmaf(D.jitter_rho, nr, rho), D.rho_min, D.rho_max);
+    const float i2 = clampf(fmaf(D.jitter_i, ni, P.i0), D.i_min, D.i_max);
+    s1 = frame_shape(P.d, dy, rho, P.i0 * P.gain, u24f(w2.x) < a.hide_prob);
+    s2 = frame_shape(dx2, dy2, rho2, i2 * P.gain, u24f(w2.y) < a.hide_prob);
 }
 
 __device__ __forceinline__ Flow pair_flow(const KernelArgs &a, const synthpix_pair_desc &D) {

@@ -197,17 +197,28 @@ __global__ void __launch_bounds__(kPrepThreads, 5) k_seed_advect(KernelArgs a) {
             a.particles_out[3 * g + 2] = 4.0f * P.sigma;
             continue;
         }
-        const float r15 = 6.0f * P.sigma;  // 1.5 d
-        if (counting)
-            count_window(a, c, particle_window(P.ix, P.fx, P.iy, P.fy, r15, c.d.width, c.d.height), 0,
+        // window half-extents 1.5 d (x) and 1.5 d_y (y) of each frame; < 0: hidden
+        float r1x = 6.0f * P.sigma, r1y = r1x, r2x = r1x, r2y = r1x;
+        if (a.ext) {
+            float4 s1, s2;
+            frame_shapes(a, c.d, i, P, s1, s2);
+            a.shape[g] = s1;
+            a.shape[a.n_part + g] = s2;
+            r1x = 6.0f * s1.x;
+            r1y = 6.0f * s1.y;
+            r2x = 6.0f * s2.x;
+            r2y = 6.0f * s2.y;
+        }
+        if (counting && r1x >= 0.0f)
+            count_window(a, c, particle_window2(P.ix, P.fx, P.iy, P.fy, r1x, r1y, c.d.width, c.d.height), 0,
                          local ? hist : nullptr);
         if (a.tiled) continue;  // frame 2 from k_advect
         int32_t jx = P.ix, jy = P.iy;
         float gx = P.fx, gy = P.fy;
         advect_split(F, a.dt, a.n_substeps, a.integrator, jx, gx, jy, gy);
         a.pos1[g] = make_float4(gx, gy, __int_as_float(jx), __int_as_float(jy));
-        if (counting)
-            count_window(a, c, particle_window(jx, gx, jy, gy, r15, c.d.width, c.d.height), 1,
+        if (counting && r2x >= 0.0f)
+            count_window(a, c, particle_window2(jx, gx, jy, gy, r2x, r2y, c.d.width, c.d.height), 1,
                          local ? hist : nullptr);
     }
     if (local) {
@@ -267,32 +278,48 @@ __global__ void __launch_bounds__(1024) k_scan(KernelArgs a, int frame) {
 // order-independent).  On chip: count the chunk's records per tile, reserve
 // each tile's range with one global atomic, then place the records.
 // ---------------------------------------------------------------------------
+// put(f, k, p, sh) for each bin k of frame f a particle's window meets; sh =
+// (sigma_x, sigma_y, rho, amplitude) of the frame (hidden particles skipped).
 template <typename Put>
 __device__ __forceinline__ void chunk_windows(const KernelArgs &a, const ChunkCtx &c, int nf, Put put) {
     for (int q = threadIdx.x; q < c.n; q += kPrepThreads) {
         const int64_t g = c.pl.part_base + c.first + q;
-        const float2 sa = a.sa[g];
-        const float r15 = 6.0f * sa.x;
+        float4 sh = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (!a.ext) {
+            const float2 sa = a.sa[g];
+            sh = make_float4(sa.x, sa.x, 0.0f, sa.y);
+        }
         for (int f = 0; f < nf; ++f) {
+            if (a.ext) sh = a.shape[f * a.n_part + g];
+            if (sh.x < 0.0f) continue;  // hidden from this frame
             const float4 p = f ? a.pos1[g] : a.pos0[g];
-            const Window w = particle_window(__float_as_int(p.z), p.x, __float_as_int(p.w), p.y, r15, c.d.width,
-                                             c.d.height);
+            const Window w = particle_window2(__float_as_int(p.z), p.x, __float_as_int(p.w), p.y, 6.0f * sh.x,
+                                              6.0f * sh.y, c.d.width, c.d.height);
             if (w.j0 > w.j1 || w.i0 > w.i1) continue;
             int32_t tx0, tx1, ty0, ty1;
             window_tiles(w, c.pl.halo, a.tile, c.d.width, c.d.height, tx0, tx1, ty0, ty1);
             for (int32_t ty = ty0; ty <= ty1; ++ty)
-                for (int32_t tx = tx0; tx <= tx1; ++tx) put(f, f * c.pl.ntiles + ty * c.pl.tiles_x + tx, p, sa);
+                for (int32_t tx = tx0; tx <= tx1; ++tx) put(f, f * c.pl.ntiles + ty * c.pl.tiles_x + tx, p, sh);
         }
     }
 }
 
+// One bin record: 24 bytes (Record) for round particles, 32 (RecordG) for
+// the general-shape splat.
 __device__ __forceinline__ void put_record(const KernelArgs &a, const ChunkCtx &c, int f, uint32_t slot,
-                                           const float4 &p, const float2 &sa) {
+                                           const float4 &p, const float4 &sh) {
     if ((int64_t)slot < c.pl.list_cap) {
-        float2 *r = reinterpret_cast<float2 *>(a.rec + c.pl.list_base + (int64_t)f * c.pl.list_cap + slot);
-        r[0] = make_float2(p.x, p.y);
-        r[1] = make_float2(p.z, p.w);
-        r[2] = sa;
+        const int64_t k = c.pl.list_base + (int64_t)f * c.pl.list_cap + slot;
+        if (a.general) {
+            float4 *r = reinterpret_cast<float4 *>(reinterpret_cast<RecordG *>(a.rec) + k);
+            r[0] = p;
+            r[1] = sh;
+        } else {
+            float2 *r = reinterpret_cast<float2 *>(a.rec + k);
+            r[0] = make_float2(p.x, p.y);
+            r[1] = make_float2(p.z, p.w);
+            r[2] = make_float2(sh.x, sh.w);
+        }
     }
 }
 
@@ -305,14 +332,14 @@ __global__ void __launch_bounds__(kPrepThreads) k_scatter(KernelArgs a) {
     const int nk = nf * c.pl.ntiles;
     uint32_t *cursor = a.cursor + c.pl.tile_base;
     if (nk > kHistMax) {
-        chunk_windows(a, c, nf, [&](int f, int k, const float4 &p, const float2 &sa) {
-            put_record(a, c, f, atomicAdd(cursor + k, 1u), p, sa);
+        chunk_windows(a, c, nf, [&](int f, int k, const float4 &p, const float4 &sh) {
+            put_record(a, c, f, atomicAdd(cursor + k, 1u), p, sh);
         });
         return;
     }
     for (int k = threadIdx.x; k < nk; k += kPrepThreads) cnt[k] = 0u;
     __syncthreads();
-    chunk_windows(a, c, nf, [&](int, int k, const float4 &, const float2 &) { atomicAdd(cnt + k, 1u); });
+    chunk_windows(a, c, nf, [&](int, int k, const float4 &, const float4 &) { atomicAdd(cnt + k, 1u); });
     __syncthreads();
     for (int k = threadIdx.x; k < nk; k += kPrepThreads) {
         const uint32_t n = cnt[k];
@@ -320,8 +347,8 @@ __global__ void __launch_bounds__(kPrepThreads) k_scatter(KernelArgs a) {
         cnt[k] = 0u;
     }
     __syncthreads();
-    chunk_windows(a, c, nf, [&](int f, int k, const float4 &p, const float2 &sa) {
-        put_record(a, c, f, base[k] + atomicAdd(cnt + k, 1u), p, sa);
+    chunk_windows(a, c, nf, [&](int f, int k, const float4 &p, const float4 &sh) {
+        put_record(a, c, f, base[k] + atomicAdd(cnt + k, 1u), p, sh);
     });
 }
 

@@ -42,19 +42,21 @@ __device__ __forceinline__ void stage_header(const KernelArgs &a, int pair, unsi
     }
 }
 
-// records [first, first + n) of the bins, copied in 16-byte chunks from the
-// 16-byte boundary at or below the first record: record k of the span lands
-// at dst + lead + 24 k with lead = (24 first) mod 16.
+// records [first, first + n) of the bins (RS bytes each), copied in 16-byte
+// chunks from the 16-byte boundary at or below the first record: record k of
+// the span lands at dst + lead + RS k with lead = (RS first) mod 16.
+template <int RS>
 __device__ __forceinline__ void stage_records(const KernelArgs &a, int64_t first, uint32_t n, unsigned char *dst) {
-    const int64_t start = first * (int64_t)sizeof(Record);
+    const int64_t start = first * (int64_t)RS;
     const int64_t astart = start & ~(int64_t)15;
-    const int64_t nbytes = (start - astart) + (int64_t)n * (int64_t)sizeof(Record);
+    const int64_t nbytes = (start - astart) + (int64_t)n * (int64_t)RS;
     const int nchunks = (int)((nbytes + 15) >> 4);
     const unsigned char *base = reinterpret_cast<const unsigned char *>(a.rec) + astart;
     for (int c = threadIdx.x; c < nchunks; c += blockDim.x) cp_async16(dst + 16 * c, base + 16 * c);
 }
 
-__device__ __forceinline__ int record_lead(int64_t first) { return (int)((first * (int64_t)sizeof(Record)) & 15); }
+template <int RS>
+__device__ __forceinline__ int record_lead(int64_t first) { return (int)((first * (int64_t)RS) & 15); }
 
 // ---------------------------------------------------------------------------
 // exact fixed-point accumulation
@@ -512,6 +514,86 @@ __device__ __forceinline__ void splat_chunk(const unsigned char *recs, unsigned 
         case 6: splat_group<14, class_lanes(6), class_rows(6)>(e, acc, tab); break;
         case 7: splat_group<16, class_lanes(7), class_rows(7)>(e, acc, tab); break;
         default: splat_coop<false>(e, valid, acc, scr, wq, tab); break;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// general particle shapes (Eq. 1 with sigma_x != sigma_y or rho != 0)
+// ---------------------------------------------------------------------------
+// Gauss-Legendre rule with 4 nodes on [-1, 1] (the roots of P_4 and their weights).
+__constant__ float kGl4X[4] = {-0.8611363115940526f, -0.3399810435848563f, 0.3399810435848563f,
+                               0.8611363115940526f};
+__constant__ float kGl4W[4] = {0.3478548451374538f, 0.6521451548625461f, 0.6521451548625461f,
+                               0.3478548451374538f};
+
+// Mass of the standard normal over [lo, hi] from erfc tails.
+__device__ __forceinline__ float normal_mass(float lo, float hi) {
+    return pixel_mass(edge_value(lo), edge_value(hi), lo > 0.0f, hi > 0.0f);
+}
+
+// Probability of the pixel whose left and top edges lie u0, v0 pixels from
+// the particle centre, under the normal density of Eq. 1.  rho = 0: the
+// product of the 1-D masses.  Otherwise the x-marginal times the conditional
+// mass of y (normal, mean rho sigma_y u / sigma_x, std sigma_y
+// sqrt(1 - rho^2)): exact in y, 4-node Gauss-Legendre in x on m equal
+// sub-intervals of the pixel no wider than the integrand's shortest x-scale
+// min(sigma_x, sigma_x sqrt(1 - rho^2) / |rho|) (quadrature error below
+// 1e-7 of I0).
+__device__ __forceinline__ float shape_pixel_mass(float u0, float v0, float sx, float sy, float rho, float isx,
+                                                  float isy) {
+    if (rho == 0.0f) return normal_mass(u0 * isx, (u0 + 1.0f) * isx) * normal_mass(v0 * isy, (v0 + 1.0f) * isy);
+    const float c = sqrtf(1.0f - rho * rho);
+    const float is = isy / c;                       // 1 / conditional std
+    const float k = rho * sy * isx;                 // conditional mean per pixel of u
+    const float ell = fabsf(rho) > c ? sx * c / fabsf(rho) : sx;
+    const int m = min(max((int)ceilf(1.0f / ell), 1), 256);
+    const float h = 1.0f / (float)m;
+    const float scale = 0.5f * h * isx * 0.39894228040143267794f;  // h/2 * pdf normalisation 1/(sqrt(2 pi) sigma_x)
+    float sum = 0.0f;
+    for (int q = 0; q < m; ++q) {
+        const float a = fmaf((float)q, h, u0);
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+            const float u = fmaf(0.5f * h, kGl4X[n] + 1.0f, a);
+            const float t = u * isx;
+            const float lo = (v0 - k * u) * is;
+            sum = fmaf(kGl4W[n] * __expf(-0.5f * t * t), normal_mass(lo, lo + is), sum);
+        }
+    }
+    return sum * scale;
+}
+
+// Splat n staged general records: a warp per record, its lanes over the
+// window's pixels, every add checked for wrapping (the carry words are
+// cleared at the item's first chunk).
+__device__ __forceinline__ void splat_chunk_general(const unsigned char *recs, uint32_t n, const Geo &g, float scale,
+                                                    const Acc &acc) {
+    __syncthreads();  // the item's carry flag is read after the loop top's reset
+    if (!sh_carry_clean) {
+        uint4 *cw = reinterpret_cast<uint4 *>(acc.acc + acc.co);
+        for (int k = threadIdx.x; k < (g.EH * g.P) >> 2; k += blockDim.x) cw[k] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) sh_carry_clean = 1;  // read again only after the chunk's last barrier
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (uint32_t k = warp; k < n; k += nwarps) {
+        const RecordG r = reinterpret_cast<const RecordG *>(recs)[k];
+        const float r15x = 6.0f * r.sx, r15y = 6.0f * r.sy;
+        const int32_t j0 = max(r.ix + (int32_t)floorf(r.fx - r15x), g.ex0);
+        const int32_t j1 = min(r.ix + (int32_t)floorf(r.fx + r15x), g.ex1 - 1);
+        const int32_t i0 = max(r.iy + (int32_t)floorf(r.fy - r15y), g.ey0);
+        const int32_t i1 = min(r.iy + (int32_t)floorf(r.fy + r15y), g.ey1 - 1);
+        if (j0 > j1 || i0 > i1) continue;
+        const int nx = j1 - j0 + 1, npx = nx * (i1 - i0 + 1);
+        const float amps = r.amp * scale, isx = 1.0f / r.sx, isy = 1.0f / r.sy;
+        uint32_t *w0 = acc.acc + (i0 - g.ey0) * acc.P + (j0 - g.ax0);
+        for (int p = lane; p < npx; p += 32) {
+            const int rr = p / nx, cc = p - rr * nx;
+            const float u0 = __fsub_rn((float)(j0 + cc - r.ix), r.fx);
+            const float v0 = __fsub_rn((float)(i0 + rr - r.iy), r.fy);
+            const float P = shape_pixel_mass(u0, v0, r.sx, r.sy, r.rho, isx, isy);
+            add_contrib<true>(w0 + rr * acc.P + cc, acc, amps, fmaxf(P, 0.0f));
         }
     }
 }
@@ -1020,7 +1102,7 @@ __device__ __forceinline__ __nv_bfloat16 to_inter<__nv_bfloat16>(float v) { retu
 // Thread 0 reads the work item of ticket t2 into `after` once the splat is
 // done (the ticket was taken an item earlier), so the read's latency hides
 // behind the finishing steps.
-template <typename T, int NT>
+template <typename T, int NT, int RS>
 __device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo &it, unsigned char *buf,
                                              uint32_t cap, const Smem &s, uint32_t t2, ItemInfo &after) {
     const synthpix_pair_desc &D = *reinterpret_cast<const synthpix_pair_desc *>(buf);
@@ -1037,12 +1119,15 @@ __device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo
     uint32_t done = 0;
     while (done < it.count) {
         const uint32_t n = min(it.count - done, cap);
-        splat_chunk<NT>(buf + kStageHeader + record_lead(it.rec0 + done), buf + kStageHeader, n, g, scale, acc,
-                        s.scr + (threadIdx.x >> 5) * a.warp_scratch, a.warp_scratch >> 2, s.phi);
+        if constexpr (RS == (int)sizeof(RecordG))
+            splat_chunk_general(buf + kStageHeader + record_lead<RS>(it.rec0 + done), n, g, scale, acc);
+        else
+            splat_chunk<NT>(buf + kStageHeader + record_lead<RS>(it.rec0 + done), buf + kStageHeader, n, g, scale,
+                            acc, s.scr + (threadIdx.x >> 5) * a.warp_scratch, a.warp_scratch >> 2, s.phi);
         done += n;
         __syncthreads();
         if (done < it.count) {  // more records: stage the next chunk
-            stage_records(a, it.rec0 + done, min(it.count - done, cap), buf + kStageHeader);
+            stage_records<RS>(a, it.rec0 + done, min(it.count - done, cap), buf + kStageHeader);
             cp_async_commit();
             cp_async_wait_all();
             __syncthreads();
@@ -1118,7 +1203,8 @@ __host__ __device__ inline SmemLayout smem_layout(int E, int tile, int warp_scra
     return L;
 }
 
-template <typename T, int NT>
+// RS: bytes of a bin record (24: Record, round particles; 32: RecordG, general shapes).
+template <typename T, int NT, int RS>
 __global__ void __launch_bounds__(NT, 1024 / NT) k_splat(KernelArgs a) {
     if (*a.check != 1) return;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1141,7 +1227,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_splat(KernelArgs a) {
     for (int k = threadIdx.x; k < kBlkSide * kBlkSide; k += blockDim.x) sh_blk[k] = 0;
     s.BP = (a.tile + 3) & ~3;
     unsigned char *bufs = smem + L.bufs;
-    const uint32_t cap = (uint32_t)rec_cap(a.rec_buf_bytes);
+    const uint32_t cap = (uint32_t)rec_cap(a.rec_buf_bytes, RS);
     for (int k = threadIdx.x; k < words; k += blockDim.x) s.acc[k] = 0u;
     // work queue: the current item, the next one (staged while the current
     // one renders) and the ticket of the one after (its item read during
@@ -1161,7 +1247,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_splat(KernelArgs a) {
     __syncthreads();
     if (s_item[0].pair < 0) return;
     stage_header(a, s_item[0].pair, bufs);
-    stage_records(a, s_item[0].rec0, min(s_item[0].count, cap), bufs + kStageHeader);
+    stage_records<RS>(a, s_item[0].rec0, min(s_item[0].count, cap), bufs + kStageHeader);
     cp_async_commit();
     int cur = 0;
     for (;;) {
@@ -1178,13 +1264,13 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_splat(KernelArgs a) {
         unsigned char *bnext = bufs + (cur ^ 1) * a.rec_buf_bytes;
         if (nx.pair >= 0) {
             stage_header(a, nx.pair, bnext);
-            stage_records(a, nx.rec0, min(nx.count, cap), bnext + kStageHeader);
+            stage_records<RS>(a, nx.rec0, min(nx.count, cap), bnext + kStageHeader);
         }
         cp_async_commit();
         const uint32_t t2 = t_pending;
         if (threadIdx.x == 0) t_pending = atomicAdd(a.ticket, 1u);  // returns while this item renders
         ItemInfo after;
-        process_item<T, NT>(a, it, bufs + cur * a.rec_buf_bytes, cap, s, t2, after);
+        process_item<T, NT, RS>(a, it, bufs + cur * a.rec_buf_bytes, cap, s, t2, after);
         if (threadIdx.x == 0) s_item[cur] = after;
         cur ^= 1;
         __syncthreads();
@@ -1262,20 +1348,26 @@ cudaError_t launch_splat(const KernelArgs &a, int32_t out_dtype, cudaStream_t st
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-#define SPX_LAUNCH_NT(T, NT)                                                                                 \
+#define SPX_LAUNCH_NT(T, NT, RS)                                                                             \
     do {                                                                                                     \
-        e = cudaFuncSetAttribute(k_splat<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
+        auto kern = k_splat<T, NT, RS>;                                                                      \
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);              \
         if (e != cudaSuccess) return e;                                                                      \
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_splat<T, NT>, NT, smem);                   \
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem);                             \
         if (e != cudaSuccess) return e;                                                                      \
         const int64_t want = (int64_t)nsm * (occ > 0 ? occ : 1);                                             \
-        e = launch_kernel(k_splat<T, NT>, (unsigned)(a.n_tiles < want ? a.n_tiles : want), NT, smem, st, a);  \
+        e = launch_kernel(kern, (unsigned)(a.n_tiles < want ? a.n_tiles : want), NT, smem, st, a);           \
         if (e != cudaSuccess) return e;                                                                      \
     } while (0)
 #define SPX_LAUNCH(T)                                                                                        \
     do {                                                                                                     \
-        if (nt == 1024) SPX_LAUNCH_NT(T, 1024);                                                              \
-        else SPX_LAUNCH_NT(T, 256);                                                                          \
+        if (a.general) {                                                                                     \
+            if (nt == 1024) SPX_LAUNCH_NT(T, 1024, 32);                                                      \
+            else SPX_LAUNCH_NT(T, 256, 32);                                                                  \
+        } else {                                                                                             \
+            if (nt == 1024) SPX_LAUNCH_NT(T, 1024, 24);                                                      \
+            else SPX_LAUNCH_NT(T, 256, 24);                                                                  \
+        }                                                                                                    \
     } while (0)
     const int nt = splat_threads(a.tile);
     switch (out_dtype) {

@@ -293,3 +293,29 @@ def large_mixed_batch(n_big: int = 16, n_hd: int = 16, seed: int = 4,
                     quant_bits=16, inter_dtype=inter_dtype, n_substeps=4, dt=1.0,
                     description="16x 2048^2 ppp 0.1 d~U[1,4] + 16x 1920x1080 ppp 0.002 d~U[4,10], "
                                 f"Fourier rms 8, {inter_dtype} intermediates, 16-bit")
+
+
+def shapes_batch(n_pairs: int = 64, seed: int = 5, size: int = 512, general: bool = True,
+                 hide_prob: float = 0.05) -> Workload:
+    """The 512x512 u8 workload with the Eq. 1 shape options of Section 2.
+
+    d~U[1,4] (sigma_x = d/4); with `general`, d_y~U[1,4] and rho~U[-0.6,0.6]
+    (axis-misaligned elliptical particles), else round particles; frame-2
+    changes of std 0.1 px (each diameter), 0.05 (I0) and 0.05 (rho); each
+    particle hidden from each frame with probability hide_prob.
+    """
+    h = w = size
+    flows = [fourier_flow(h, w, h, w, rms=3.0, seed=5000 + b) for b in range(n_pairs)]
+    extra = dict(dy_min=1.0, dy_max=4.0, rho_min=-0.6, rho_max=0.6) if general else {}
+    pairs = [PairSpec(height=h, width=w, n_particles=n_particles_for(0.05, h, w), pair_id=b,
+                      flow_index=b, d_dist=0, d_min=1.0, d_max=4.0, illum_min=0.7, illum_max=1.0,
+                      noise_sigma=0.02, blur_sigma=0.7, jitter_d=0.1, jitter_i=0.05,
+                      jitter_rho=0.05 if general else 0.0, **extra)
+             for b in range(n_pairs)]
+    kind = "elliptical d_y~U[1,4] rho~U[-0.6,0.6]" if general else "round"
+    return Workload(name=f"shapes{n_pairs}_{size}_{'general' if general else 'round'}", seed=seed,
+                    pairs=pairs, flows=flows, out_dtype="u8", quant_bits=8, n_substeps=4, dt=1.0,
+                    hide_prob=hide_prob,
+                    description=f"{n_pairs} pairs {size}x{size} ppp 0.05, d~U[1,4], {kind}, frame-2 "
+                                f"jitter (d 0.1, I0 0.05, rho 0.05), hide {hide_prob}, Fourier rms 3, "
+                                f"illum 0.7-1, noise 0.02, blur 0.7, 8-bit")

@@ -22,7 +22,7 @@ def test_library_exports_every_declared_symbol():
     L = B.lib()
     for name in _declared():
         assert hasattr(L, name), name
-    assert L.synthpix_version() == 1
+    assert L.synthpix_version() == 2
 
 
 def test_descriptor_sizes_match_header():
@@ -43,7 +43,7 @@ def _render(pk, ws_bytes=1 << 30, ws=FAKE, flows=FAKE, images=FAKE):
 
 @pytest.mark.parametrize("field,value", [
     ("out_dtype", 9), ("quant_bits", 0), ("integrator", 3), ("n_substeps", 0), ("n_substeps", 5000),
-    ("dt", float("nan")), ("tile", 48)])
+    ("dt", float("nan")), ("tile", 48), ("hide_prob", -0.1), ("hide_prob", 1.5), ("hide_prob", float("nan"))])
 def test_bad_batch_fields_are_rejected(field, value):
     pk = _packed()
     setattr(pk.batch, field, value)
@@ -55,7 +55,9 @@ def test_bad_batch_fields_are_rejected(field, value):
 @pytest.mark.parametrize("field,value", [
     ("height", 0), ("width", 40000), ("flow_h", 0), ("flow_offset", -2), ("flow_offset", 3),
     ("d_min", 0.0), ("d_max", 40.0), ("d_dist", 2), ("i_min", 2.0), ("blur_sigma", 9.0),
-    ("noise_sigma", -1.0), ("z_min", 5.0), ("sheet_sigma", float("inf"))])
+    ("noise_sigma", -1.0), ("z_min", 5.0), ("sheet_sigma", float("inf")), ("dy_min", 2.0), ("dy_max", 40.0),
+    ("dy_min", -1.0), ("rho_max", 0.99), ("rho_min", 0.5), ("jitter_d", -0.1), ("jitter_i", float("nan")),
+    ("jitter_rho", -1.0)])
 def test_bad_pair_fields_are_rejected(field, value):
     pk = _packed()
     setattr(pk.pairs[1], field, value)
@@ -64,9 +66,6 @@ def test_bad_pair_fields_are_rejected(field, value):
 
 
 def test_reserved_fields_and_flags_unsupported():
-    pk = _packed()
-    pk.pairs[0].reserved[3] = 1.0
-    assert _render(pk) == B.EUNSUPPORTED
     pk = _packed()
     pk.batch.flags = 4
     assert _render(pk) == B.EUNSUPPORTED
@@ -130,3 +129,29 @@ def test_advect_particles_rejects_missing_buffers():
                                        1 << 30, None) == B.EINVAL
     assert L.synthpix_advect_particles(C.byref(pk.batch), pk.pairs, None, pk.n_pairs, None, None, FAKE, FAKE,
                                        1 << 30, None) == B.EINVAL
+
+
+def test_general_shape_fields_accepted_and_size_the_workspace():
+    pk = _packed()
+    base = B.workspace_bytes(pk)
+    pk.batch.hide_prob = 0.25  # per-frame shapes: one float4 per particle and frame more
+    hidden = B.workspace_bytes(pk)
+    assert hidden > base
+    pk.pairs[0].dy_min, pk.pairs[0].dy_max = 1.0, 3.0  # general shapes: 32-byte bin records
+    pk.pairs[1].rho_min, pk.pairs[1].rho_max = -0.5, 0.5
+    assert B.workspace_bytes(pk) > hidden
+    assert _render(pk, ws_bytes=16) == B.EWORKSPACE  # validation passed up to the workspace check
+
+
+def test_given_particles_and_adjoint_reject_shape_variation():
+    pk = _packed()
+    pk.pairs[0].jitter_i = 0.1
+    L = B.lib()
+    assert L.synthpix_render_pairs_from(C.byref(pk.batch), pk.pairs, None, pk.n_pairs, FAKE, FAKE, FAKE, FAKE,
+                                        1 << 30, None) == B.EUNSUPPORTED
+    assert "round particles" in B.last_error()
+    pk.batch.out_dtype = B.DTYPE_CODE["f32"]
+    pk.batch.quant_bits = 0
+    assert L.synthpix_render_backward(C.byref(pk.batch), pk.pairs, None, pk.n_pairs, None, FAKE, FAKE, FAKE,
+                                      None, FAKE, 1 << 30, None) == B.EUNSUPPORTED
+    assert "round particles" in B.last_error()
