@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--pairs", type=int, default=N_PAIRS, help="pairs per step (profiling a smaller case)")
     ap.add_argument("--workload", default="batch64_512_u8",
-                    choices=("batch64_512_u8", "uneven256", "diff32_256", "large_mixed"),
+                    choices=("batch64_512_u8", "uneven256", "diff32_256", "large_mixed", "shapes64_512"),
                     help="the headline workload (default) or one of the other workloads, measured on their own")
     ap.add_argument("--quick", action="store_true",
                     help="timed steps only (no autotune, graph, FP16, e2e, per-pair or CPU legs): for profilers")
@@ -127,6 +127,41 @@ def algorithmic(wl):
         ops += 2 * p.height * p.width * per_px
     flow_bytes = sum(f.size * 4 for f in wl.flows)
     return nbytes + flow_bytes, ops
+
+
+def shapes_algorithmic(wl, samples: int = 200000, seed: int = 0):
+    """Lane-operations of the general-shape splat plus the epilogue (batch sum).
+
+    Per visible particle and frame (expectations over the drawn d, d_y, rho):
+      rho = 0: (n_x + 1 + n_y + 1) edge values x 12 + n_x n_y pixels x 2;
+      rho != 0: per window column 4 m Gauss-Legendre nodes (m sub-intervals
+      of the pixel no wider than min(sigma_x, sigma_x sqrt(1-rho^2)/|rho|)),
+      each with its density weight (6) and n_y + 1 conditional edge values
+      (x 12) and n_y weighted differences (x 2); + n_x n_y accumulations.
+    with n_x = 3 d + 1, n_y = 3 d_y + 1.  Epilogue per output pixel as in
+    algorithmic().  Frame-2 variation is small and not modelled.
+    """
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    ops = 0.0
+    for p in wl.pairs:
+        d = rng.uniform(float(p.d_min), float(p.d_max), samples)
+        same = float(p.dy_min) == 0.0 and float(p.dy_max) == 0.0
+        dy = d if same else rng.uniform(float(p.dy_min), float(p.dy_max), samples)
+        rho = rng.uniform(float(p.rho_min), float(p.rho_max), samples)
+        nx, ny = 3 * d + 1, 3 * dy + 1
+        c = np.sqrt(1 - rho * rho)
+        sx = d / 4
+        ell = np.where(np.abs(rho) > c, sx * c / np.maximum(np.abs(rho), 1e-30), sx)
+        m = np.clip(np.ceil(1.0 / ell), 1, 256)
+        sep = (nx + 1 + ny + 1) * 12 + nx * ny * 2
+        quad = nx * 4 * m * (6 + (ny + 1) * 12 + ny * 2) + nx * ny
+        per = np.where(rho == 0.0, sep, quad).mean()
+        ops += 2 * p.n_particles * (1.0 - float(wl.hide_prob)) * per
+        R = math.ceil(3 * float(p.blur_sigma)) if p.blur_sigma > 0 else 0
+        per_px = 1 + (13 if p.noise_sigma > 0 else 0) + (2 * (2 * R + 1) if R else 0) + 2
+        ops += 2 * p.height * p.width * per_px
+    return ops
 
 
 # ----------------------------------------------------------------------------
@@ -445,6 +480,25 @@ def _time_device(fn, steps, flush, stream):
     return tot / steps
 
 
+def _stage_ms(r, n, flush, stream):
+    """Mean per-stage times over n renders with the library's stage events."""
+    import torch
+
+    from paper_2512_09664_b300.binding import STAGES
+    staged = []
+    for k in range(n):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        for e in evs:
+            e.record(stream)
+        staged.append(evs)
+    torch.cuda.synchronize()
+    for k in range(n):
+        flush.fill_(k & 0xFF)
+        r.render_staged(staged[k])
+    torch.cuda.synchronize()
+    return {name: sum(ev[i].elapsed_time(ev[i + 1]) for ev in staged) / n for i, name in enumerate(STAGES)}
+
+
 def run_other(args):
     import numpy as np
     import torch
@@ -493,6 +547,43 @@ def run_other(args):
         b_ms = _time_device(lambda: r.backward(G, grad_flows=gf, grad_particles=gp), args.steps, flush, stream)
         line.update({"config": wl.description, "forward_ms": f_ms, "backward_ms": b_ms,
                      "value": wl.n_pairs / ((f_ms + b_ms) / 1e3), "forward_value": wl.n_pairs / (f_ms / 1e3)})
+    elif args.workload == "shapes64_512":
+        # Eq. 1 shape options: elliptical axis-misaligned particles with frame-2
+        # variation and hiding (general-shape splat), and round particles with
+        # variation and hiding (round splat, per-particle advection)
+        res = {}
+        for kind in ("general", "round"):
+            wl = W.shapes_batch(n_pairs=64, general=kind == "general")
+            r = Renderer(wl)
+            tile, _ = r.autotune(reps=1)
+            for _ in range(args.warmup):
+                flush.fill_(1)
+                r.render()
+            with ClockSampler(0) as clk:
+                ms = _time_device(r.render, args.steps, flush, stream)
+            st = _stage_ms(r, min(args.steps, 20), flush, stream)
+            res[kind] = {"ms_per_step": ms, "value": wl.n_pairs / (ms / 1e3), "tile": tile, "stage_ms": st,
+                         "config": wl.description, "clocks": clk.summary()}
+            if kind == "general":
+                peaks, peak_kind = measured_peaks()
+                sm_mhz = float(peaks.get("sm_max_mhz", 2032.0))
+                alu_peak = SM_COUNT * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+                achieved = shapes_algorithmic(wl) / (st["splat_epilogue"] / 1e3) / 1e12
+                alg_bytes, _ = algorithmic(wl)
+                step_gbs = alg_bytes / (ms / 1e3) / 1e9
+                res[kind]["roofline"] = {
+                    "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tlane-op/s",
+                    "frac": achieved / alu_peak, "traffic": None, "kernel": "k_splat (general shapes)",
+                    "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_mhz:.0f} MHz"}
+                res[kind]["step_roofline_hbm"] = {"achieved_gbs": step_gbs, "peak_gbs": float(peaks["hbm_gbs"]),
+                                                  "frac": step_gbs / float(peaks["hbm_gbs"]),
+                                                  "peak_source": peak_kind}
+                if not args.no_cpu_baseline:
+                    res[kind]["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
+            del r
+            torch.cuda.empty_cache()
+        line.update({"paths": res, "value": res["general"]["value"],
+                     "general_over_round_ms": res["general"]["ms_per_step"] / res["round"]["ms_per_step"]})
     else:  # large_mixed
         wl = W.large_mixed_batch()
         res = {}

@@ -521,80 +521,200 @@ __device__ __forceinline__ void splat_chunk(const unsigned char *recs, unsigned 
 // ---------------------------------------------------------------------------
 // general particle shapes (Eq. 1 with sigma_x != sigma_y or rho != 0)
 // ---------------------------------------------------------------------------
-// Gauss-Legendre rule with 4 nodes on [-1, 1] (the roots of P_4 and their weights).
-__constant__ float kGl4X[4] = {-0.8611363115940526f, -0.3399810435848563f, 0.3399810435848563f,
-                               0.8611363115940526f};
-__constant__ float kGl4W[4] = {0.3478548451374538f, 0.6521451548625461f, 0.6521451548625461f,
-                               0.3478548451374538f};
+// The 4-node Gauss-Legendre rule on [-1, 1]: nodes +-0.8611363115940526 and
+// +-0.3399810435848563 (the roots of P_4), weights 0.3478548451374538 and
+// 0.6521451548625461.
 
-// Mass of the standard normal over [lo, hi] from erfc tails.
-__device__ __forceinline__ float normal_mass(float lo, float hi) {
-    return pixel_mass(edge_value(lo), edge_value(hi), lo > 0.0f, hi > 0.0f);
+// rho = 0 (axis-aligned ellipse), a warp per visit: lanes [0, nx] evaluate
+// the x edges (1 / sigma_x), lanes [nx + 1, nx + ny + 1] the y edges
+// (1 / sigma_y), then the lanes take the window's pixels 32 at a time and
+// fetch their column and row masses by shuffles.  Windows with more edges
+// than lanes evaluate both masses per pixel.
+template <bool CHECKED>
+__device__ __forceinline__ void splat_general_sep(const RecordG &r, int32_t j0, int32_t i0, int nx, int ny,
+                                                  float amps, uint32_t *w0, const Acc &acc, const float4 *tab) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const float isx = 1.0f / r.sx, isy = 1.0f / r.sy;
+    const float ux = __fsub_rn((float)(j0 - r.ix), r.fx), vy = __fsub_rn((float)(i0 - r.iy), r.fy);
+    const int npx = nx * ny;
+    const float invn = __frcp_rn((float)nx);
+    if (nx + ny + 2 <= 32) {
+        const bool isx_lane = lane <= nx;
+        const int e = isx_lane ? lane : lane - (nx + 1);
+        const float ev = lane <= nx + ny + 1
+                             ? edge_value_tab(__fadd_rn(isx_lane ? ux : vy, (float)e), isx_lane ? isx : isy, tab)
+                             : 0.0f;
+        float m = edge_mass(ev, __shfl_down_sync(FULL, ev, 1));
+        if (!isx_lane) m = __fmul_rn(m, amps);
+        for (int b = 0; b < npx; b += 32) {
+            const int p = min(b + lane, npx - 1);
+            const int rr = small_div(p, invn), cc = p - rr * nx;
+            const float mx = __shfl_sync(FULL, m, cc), my = __shfl_sync(FULL, m, nx + 1 + rr);
+            if (b + lane < npx) add_contrib<CHECKED>(w0 + rr * acc.P + cc, acc, mx, my);
+        }
+        return;
+    }
+    for (int p = lane; p < npx; p += 32) {
+        const int rr = small_div(p, invn), cc = p - rr * nx;
+        const float u = __fadd_rn(ux, (float)cc), v = __fadd_rn(vy, (float)rr);
+        const float mx = edge_mass(edge_value_tab(u, isx, tab), edge_value_tab(__fadd_rn(u, 1.0f), isx, tab));
+        const float my = edge_mass(edge_value_tab(v, isy, tab), edge_value_tab(__fadd_rn(v, 1.0f), isy, tab));
+        add_contrib<CHECKED>(w0 + rr * acc.P + cc, acc, mx, __fmul_rn(my, amps));
+    }
 }
 
-// Probability of the pixel whose left and top edges lie u0, v0 pixels from
-// the particle centre, under the normal density of Eq. 1.  rho = 0: the
-// product of the 1-D masses.  Otherwise the x-marginal times the conditional
-// mass of y (normal, mean rho sigma_y u / sigma_x, std sigma_y
-// sqrt(1 - rho^2)): exact in y, 4-node Gauss-Legendre in x on m equal
-// sub-intervals of the pixel no wider than the integrand's shortest x-scale
-// min(sigma_x, sigma_x sqrt(1 - rho^2) / |rho|) (quadrature error below
-// 1e-7 of I0).
-__device__ __forceinline__ float shape_pixel_mass(float u0, float v0, float sx, float sy, float rho, float isx,
-                                                  float isy) {
-    if (rho == 0.0f) return normal_mass(u0 * isx, (u0 + 1.0f) * isx) * normal_mass(v0 * isy, (v0 + 1.0f) * isy);
-    const float c = sqrtf(1.0f - rho * rho);
-    const float is = isy / c;                       // 1 / conditional std
-    const float k = rho * sy * isx;                 // conditional mean per pixel of u
-    const float ell = fabsf(rho) > c ? sx * c / fabsf(rho) : sx;
-    const int m = min(max((int)ceilf(1.0f / ell), 1), 256);
-    const float h = 1.0f / (float)m;
-    const float scale = 0.5f * h * isx * 0.39894228040143267794f;  // h/2 * pdf normalisation 1/(sqrt(2 pi) sigma_x)
-    float sum = 0.0f;
-    for (int q = 0; q < m; ++q) {
-        const float a = fmaf((float)q, h, u0);
+// rho != 0, a warp per visit.  The pixel's probability is the x-marginal
+// times the conditional mass of y (normal, mean rho sigma_y u / sigma_x at
+// offset u, std sigma_y sqrt(1 - rho^2)), exact in y and integrated in x by
+// the 4-node Gauss-Legendre rule on M equal sub-intervals of the pixel.  The
+// Q = 4 M nodes of a window column go to a group of G = min(Q, 32) lanes
+// (Q / G nodes each); walking down the column, each lane carries its nodes'
+// last edge value to the next row, and the group sums the row's node masses
+// by shuffles.
+template <int M, bool CHECKED>
+__device__ __forceinline__ void splat_general_corr(const RecordG &r, int32_t j0, int32_t i0, int nx, int ny,
+                                                   float amps, uint32_t *w0, const Acc &acc, const float4 *tab) {
+    constexpr int Q = 4 * M, G = Q < 32 ? Q : 32, L = Q / G, CPP = 32 / G;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, gl = lane & (G - 1), gc = lane / G;
+    const float c = sqrtf(1.0f - r.rho * r.rho);
+    const float isx = 1.0f / r.sx, is = 1.0f / (r.sy * c), k = r.rho * r.sy * isx;
+    constexpr float h = 1.0f / (float)M;
+    const float ux = __fsub_rn((float)(j0 - r.ix), r.fx), vy = __fsub_rn((float)(i0 - r.iy), r.fy);
+    const float wscale = 0.5f * h * isx * 0.39894228040143267794f * amps;  // h/2, 1/(sqrt(2 pi) sigma_x), units
+    // this lane's nodes: offsets within the pixel and weights (same for every column)
+    float du[L], wq[L];
 #pragma unroll
-        for (int n = 0; n < 4; ++n) {
-            const float u = fmaf(0.5f * h, kGl4X[n] + 1.0f, a);
-            const float t = u * isx;
-            const float lo = (v0 - k * u) * is;
-            sum = fmaf(kGl4W[n] * __expf(-0.5f * t * t), normal_mass(lo, lo + is), sum);
+    for (int t = 0; t < L; ++t) {
+        const int n = gl + G * t, g4 = n & 3;
+        const float xg = g4 == 0 ? -0.8611363115940526f : g4 == 1 ? -0.3399810435848563f
+                       : g4 == 2 ? 0.3399810435848563f : 0.8611363115940526f;
+        du[t] = h * ((float)(n >> 2) + 0.5f * (xg + 1.0f));
+        wq[t] = (g4 == 0 || g4 == 3) ? 0.3478548451374538f : 0.6521451548625461f;
+    }
+    for (int c0 = 0; c0 < nx; c0 += CPP) {
+        const int col = c0 + gc;
+        const bool live = col < nx;
+        const float ul = __fadd_rn(ux, (float)col);
+        float wn[L], dv[L], ev[L];
+#pragma unroll
+        for (int t = 0; t < L; ++t) {
+            const float u = __fadd_rn(ul, du[t]);
+            const float tt = u * isx;
+            wn[t] = live ? wq[t] * __expf(-0.5f * tt * tt) * wscale : 0.0f;
+            dv[t] = __fsub_rn(vy, k * u);  // top edge of the window minus the conditional mean
+            ev[t] = edge_value_tab(dv[t], is, tab);
+        }
+        uint32_t *wc = w0 + col;
+#pragma unroll 1
+        for (int rr = 0; rr < ny; ++rr) {
+            float v = 0.0f;
+#pragma unroll
+            for (int t = 0; t < L; ++t) {
+                const float en = edge_value_tab(__fadd_rn(dv[t], (float)(rr + 1)), is, tab);
+                v = fmaf(wn[t], edge_mass(ev[t], en), v);
+                ev[t] = en;
+            }
+#pragma unroll
+            for (int o = G >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+            if (gl == 0 && live) add_contrib<CHECKED>(wc + rr * acc.P, acc, v, 1.0f);
         }
     }
-    return sum * scale;
 }
 
-// Splat n staged general records: a warp per record, its lanes over the
-// window's pixels, every add checked for wrapping (the carry words are
-// cleared at the item's first chunk).
+// Sub-intervals of the x quadrature of a correlated particle: a power of two
+// no smaller than 1 / min(sigma_x, sigma_x sqrt(1 - rho^2) / |rho|) (the
+// integrand's shortest x-scale; quadrature error below 1e-7 of I0), at most 64.
+__device__ __forceinline__ int corr_subintervals(float sx, float rho) {
+    const float c = sqrtf(1.0f - rho * rho);
+    const float ell = fabsf(rho) > c ? sx * c / fabsf(rho) : sx;
+    const int m = min(max((int)ceilf(1.0f / ell), 1), 64);
+    return 1 << (32 - __clz(m - 1));  // next power of two (1 stays 1)
+}
+
+template <bool CHECKED>
+__device__ __forceinline__ void splat_general_visit(const RecordG &r, int32_t j0, int32_t i0, int nx, int ny,
+                                                    float amps, uint32_t *w0, const Acc &acc, const float4 *tab) {
+    if (r.rho == 0.0f) {
+        splat_general_sep<CHECKED>(r, j0, i0, nx, ny, amps, w0, acc, tab);
+        return;
+    }
+    switch (corr_subintervals(r.sx, r.rho)) {
+    case 1: splat_general_corr<1, CHECKED>(r, j0, i0, nx, ny, amps, w0, acc, tab); break;
+    case 2: splat_general_corr<2, CHECKED>(r, j0, i0, nx, ny, amps, w0, acc, tab); break;
+    case 4: splat_general_corr<4, CHECKED>(r, j0, i0, nx, ny, amps, w0, acc, tab); break;
+    case 8: splat_general_corr<8, CHECKED>(r, j0, i0, nx, ny, amps, w0, acc, tab); break;
+    case 16: splat_general_corr<16, CHECKED>(r, j0, i0, nx, ny, amps, w0, acc, tab); break;
+    case 32: splat_general_corr<32, CHECKED>(r, j0, i0, nx, ny, amps, w0, acc, tab); break;
+    default: splat_general_corr<64, CHECKED>(r, j0, i0, nx, ny, amps, w0, acc, tab); break;
+    }
+}
+
+// A general record's window clipped to the tile's halo rectangle (empty: j0 > j1).
+__device__ __forceinline__ void general_window(const RecordG &r, const Geo &g, int32_t &j0, int32_t &j1, int32_t &i0,
+                                               int32_t &i1) {
+    const float r15x = 6.0f * r.sx, r15y = 6.0f * r.sy;  // 1.5 d, 1.5 d_y
+    j0 = max(r.ix + (int32_t)floorf(r.fx - r15x), g.ex0);
+    j1 = min(r.ix + (int32_t)floorf(r.fx + r15x), g.ex1 - 1);
+    i0 = max(r.iy + (int32_t)floorf(r.fy - r15y), g.ey0);
+    i1 = min(r.iy + (int32_t)floorf(r.fy + r15y), g.ey1 - 1);
+}
+
+// Splat n staged general records:
+//   A. each thread counts its records' windows in the 8 x 8 blocks they meet
+//      (the item's counts so far, as in splat_chunk);
+//   B. warp 0 decides whether the chunk's adds must be checked for wrapping;
+//   C. warps take records from a shared counter, a warp per record.
 __device__ __forceinline__ void splat_chunk_general(const unsigned char *recs, uint32_t n, const Geo &g, float scale,
-                                                    const Acc &acc) {
-    __syncthreads();  // the item's carry flag is read after the loop top's reset
-    if (!sh_carry_clean) {
-        uint4 *cw = reinterpret_cast<uint4 *>(acc.acc + acc.co);
-        for (int k = threadIdx.x; k < (g.EH * g.P) >> 2; k += blockDim.x) cw[k] = make_uint4(0u, 0u, 0u, 0u);
+                                                    const Acc &acc, const float4 *tab) {
+    const RecordG *R = reinterpret_cast<const RecordG *>(recs);
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    for (uint32_t k = threadIdx.x; k < n; k += blockDim.x) {
+        int32_t j0, j1, i0, i1;
+        general_window(R[k], g, j0, j1, i0, i1);
+        if (j0 > j1 || i0 > i1) continue;
+        const int bx0 = (j0 - g.ax0) >> kBlkShift, bx1 = (j1 - g.ax0) >> kBlkShift;
+        const int by0 = (i0 - g.ey0) >> kBlkShift, by1 = (i1 - g.ey0) >> kBlkShift;
+        for (int by = by0; by <= by1; ++by)
+            for (int bx = bx0; bx <= bx1; ++bx) atomicAdd(sh_blk + by * kBlkSide + bx, 1u);
     }
     __syncthreads();
-    if (threadIdx.x == 0) sh_carry_clean = 1;  // read again only after the chunk's last barrier
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (uint32_t k = warp; k < n; k += nwarps) {
-        const RecordG r = reinterpret_cast<const RecordG *>(recs)[k];
-        const float r15x = 6.0f * r.sx, r15y = 6.0f * r.sy;
-        const int32_t j0 = max(r.ix + (int32_t)floorf(r.fx - r15x), g.ex0);
-        const int32_t j1 = min(r.ix + (int32_t)floorf(r.fx + r15x), g.ex1 - 1);
-        const int32_t i0 = max(r.iy + (int32_t)floorf(r.fy - r15y), g.ey0);
-        const int32_t i1 = min(r.iy + (int32_t)floorf(r.fy + r15y), g.ey1 - 1);
-        if (j0 > j1 || i0 > i1) continue;
-        const int nx = j1 - j0 + 1, npx = nx * (i1 - i0 + 1);
-        const float amps = r.amp * scale, isx = 1.0f / r.sx, isy = 1.0f / r.sy;
-        uint32_t *w0 = acc.acc + (i0 - g.ey0) * acc.P + (j0 - g.ax0);
-        for (int p = lane; p < npx; p += 32) {
-            const int rr = p / nx, cc = p - rr * nx;
-            const float u0 = __fsub_rn((float)(j0 + cc - r.ix), r.fx);
-            const float v0 = __fsub_rn((float)(i0 + rr - r.iy), r.fy);
-            const float P = shape_pixel_mass(u0, v0, r.sx, r.sy, r.rho, isx, isy);
-            add_contrib<true>(w0 + rr * acc.P + cc, acc, amps, fmaxf(P, 0.0f));
+    if (threadIdx.x < 32) {
+        uint32_t mx = 0;
+#pragma unroll
+        for (int j = 0; j < kBlkSide * kBlkSide / 32; ++j) mx = max(mx, sh_blk[lane + 32 * j]);
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) mx = max(mx, __shfl_xor_sync(FULL, mx, d));
+        if (lane == 0) {
+            sh_checked = mx > kSafeVisits ? 1 : 0;
+            sh_next = 0;
         }
+    }
+    __syncthreads();
+    const bool chk = sh_checked != 0;
+    if (chk) {
+        if (!sh_carry_clean) {  // the carry words share memory with the finishing buffer: clear them
+            uint4 *cw = reinterpret_cast<uint4 *>(acc.acc + acc.co);
+            for (int k = threadIdx.x; k < (g.EH * g.P) >> 2; k += blockDim.x) cw[k] = make_uint4(0u, 0u, 0u, 0u);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) sh_carry_clean = 1;  // read again only after the chunk's last barrier
+    }
+    for (;;) {
+        uint32_t k = 0;
+        if (lane == 0) k = atomicAdd(&sh_next, 1u);
+        k = __shfl_sync(FULL, k, 0);
+        if (k >= n) break;
+        const RecordG r = R[k];
+        int32_t j0, j1, i0, i1;
+        general_window(r, g, j0, j1, i0, i1);
+        if (j0 > j1 || i0 > i1) continue;
+        uint32_t *w0 = acc.acc + (i0 - g.ey0) * acc.P + (j0 - g.ax0);
+        const float amps = r.amp * scale;
+        if (chk) splat_general_visit<true>(r, j0, i0, j1 - j0 + 1, i1 - i0 + 1, amps, w0, acc, tab);
+        else splat_general_visit<false>(r, j0, i0, j1 - j0 + 1, i1 - i0 + 1, amps, w0, acc, tab);
     }
 }
 
@@ -1120,7 +1240,7 @@ __device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo
     while (done < it.count) {
         const uint32_t n = min(it.count - done, cap);
         if constexpr (RS == (int)sizeof(RecordG))
-            splat_chunk_general(buf + kStageHeader + record_lead<RS>(it.rec0 + done), n, g, scale, acc);
+            splat_chunk_general(buf + kStageHeader + record_lead<RS>(it.rec0 + done), n, g, scale, acc, s.phi);
         else
             splat_chunk<NT>(buf + kStageHeader + record_lead<RS>(it.rec0 + done), buf + kStageHeader, n, g, scale,
                             acc, s.scr + (threadIdx.x >> 5) * a.warp_scratch, a.warp_scratch >> 2, s.phi);
