@@ -61,7 +61,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--pairs", type=int, default=N_PAIRS, help="pairs per step (profiling a smaller case)")
     ap.add_argument("--workload", default="batch64_512_u8",
-                    choices=("batch64_512_u8", "uneven256", "diff32_256", "large_mixed", "shapes64_512"),
+                    choices=("batch64_512_u8", "uneven256", "diff32_256", "large_mixed", "shapes64_512",
+                             "ablations"),
                     help="the headline workload (default) or one of the other workloads, measured on their own")
     ap.add_argument("--quick", action="store_true",
                     help="timed steps only (no autotune, graph, FP16, e2e, per-pair or CPU legs): for profilers")
@@ -499,6 +500,84 @@ def _stage_ms(r, n, flush, stream):
     return {name: sum(ev[i].elapsed_time(ev[i + 1]) for ev in staged) / n for i, name in enumerate(STAGES)}
 
 
+def _step_stats(ms):
+    """pairs/s statistics over per-step times (ms) of n_pairs-pair steps: filled in by the caller."""
+    import numpy as np
+    a = np.asarray(ms)
+    return {"ms_mean": float(a.mean()), "ms_min": float(a.min()), "ms_max": float(a.max()),
+            "ms_q1": float(np.percentile(a, 25)), "ms_q3": float(np.percentile(a, 75)), "ms_std": float(a.std())}
+
+
+def run_ablations(args, flush, stream):
+    """The throughput ablations of Section 3.3 on synthetic inputs: one axis at
+    a time around the paper's fixed point (512^2, ppp 0.06, d~U[0.8,1.2], B 64,
+    F 1).  Each point: per-step device times over args.steps renders (L2
+    flushed before each), as pairs/s mean and spread.  The flow-reuse axis
+    times the end-to-end loop: flows copied from pinned host memory once
+    every R batches, images copied back every batch."""
+    import torch
+
+    from paper_2512_09664_b300 import workloads as W
+    from paper_2512_09664_b300.binding import Renderer
+
+    def point(axis, value, wl, reuse=None):
+        r = Renderer(wl)
+        for _ in range(2):
+            r.render()
+        torch.cuda.synchronize()
+        ms = []
+        if reuse is None:
+            for k in range(args.steps):
+                flush.fill_(k & 0xFF)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                r.render()
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+        else:
+            fh = torch.from_numpy(r.pk.flows_host).pin_memory()
+            ih = torch.empty(r.images.shape, dtype=r.images.dtype).pin_memory()
+            for k in range(args.steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                if reuse == 0 or k % reuse == 0:
+                    r.flows.copy_(fh, non_blocking=True)
+                r.render()
+                ih.copy_(r.images, non_blocking=True)
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+        st = _step_stats(ms)
+        n = wl.n_pairs
+        out = {"axis": axis, "value": value, "pairs_s": n / (st["ms_mean"] / 1e3),
+               "pairs_s_min": n / (st["ms_max"] / 1e3), "pairs_s_max": n / (st["ms_min"] / 1e3),
+               "pairs_s_q1": n / (st["ms_q3"] / 1e3), "pairs_s_q3": n / (st["ms_q1"] / 1e3),
+               "tile": r.pk.batch.tile, **st}
+        del r
+        torch.cuda.empty_cache()
+        return out
+
+    pts = []
+    for size in (128, 256, 512, 1024, 2048):
+        pts.append(point("image_size", size, W.ablation_batch(size=size)))
+    for ppp in (0.01, 0.02, 0.04, 0.06, 0.08, 0.1):
+        pts.append(point("ppp", ppp, W.ablation_batch(ppp=ppp)))
+    for dmax in (1.2, 2.0, 3.0, 4.0, 6.0, 8.0):
+        pts.append(point("d_max", dmax, W.ablation_batch(d_max=dmax)))
+    for pmin in (0.01, 0.02, 0.04, 0.06):
+        pts.append(point("ppp_min", pmin, W.ablation_batch(ppp=0.06, ppp_min=pmin)))
+    for B in (1, 4, 16, 64, 256, 1024):
+        pts.append(point("batch", B, W.ablation_batch(n_pairs=B)))
+    for F in (1, 4, 16, 64):
+        pts.append(point("flows_per_batch", F, W.ablation_batch(n_flows=F)))
+    for R in (1, 2, 4, 16):
+        pts.append(point("batches_per_flow", R, W.ablation_batch(), reuse=R))
+    return {"config": "Section 3.3 ablations around 512^2, ppp 0.06, d~U[0.8,1.2], B 64, F 1 (synthetic "
+                      "Fourier flows, RK4 x4, f32 output, no epilogue)", "points": pts,
+            "value": next(p["pairs_s"] for p in pts if p["axis"] == "batch" and p["value"] == 64)}
+
+
 def run_other(args):
     import numpy as np
     import torch
@@ -584,6 +663,8 @@ def run_other(args):
             torch.cuda.empty_cache()
         line.update({"paths": res, "value": res["general"]["value"],
                      "general_over_round_ms": res["general"]["ms_per_step"] / res["round"]["ms_per_step"]})
+    elif args.workload == "ablations":
+        line.update(run_ablations(args, flush, stream))
     else:  # large_mixed
         wl = W.large_mixed_batch()
         res = {}

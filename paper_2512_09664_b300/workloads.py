@@ -319,3 +319,24 @@ def shapes_batch(n_pairs: int = 64, seed: int = 5, size: int = 512, general: boo
                     description=f"{n_pairs} pairs {size}x{size} ppp 0.05, d~U[1,4], {kind}, frame-2 "
                                 f"jitter (d 0.1, I0 0.05, rho 0.05), hide {hide_prob}, Fourier rms 3, "
                                 f"illum 0.7-1, noise 0.02, blur 0.7, 8-bit")
+
+
+def ablation_batch(size: int = 512, ppp: float = 0.06, d_min: float = 0.8, d_max: float = 1.2,
+                   n_pairs: int = 64, n_flows: int = 1, ppp_min=None, seed: int = 6) -> Workload:
+    """One point of the throughput ablations of Section 3.3.
+
+    Defaults are the paper's fixed parameters: 512x512, seeding density 0.06,
+    d~U[0.8, 1.2], B = 64 pairs, F = 1 flow field per batch.  With ppp_min,
+    each pair's density is drawn from U[ppp_min, ppp] (the spread study).
+    Fourier flows (rms 3), RK4 x4, no epilogue, FP32 output.
+    """
+    rng = np.random.default_rng(seed)
+    flows = [fourier_flow(size, size, size, size, rms=3.0, seed=6000 + f) for f in range(n_flows)]
+    dens = rng.uniform(ppp_min, ppp, size=n_pairs) if ppp_min is not None else np.full(n_pairs, ppp)
+    pairs = [PairSpec(height=size, width=size, n_particles=n_particles_for(float(dens[b]), size, size),
+                      pair_id=b, flow_index=b % n_flows, d_dist=0, d_min=d_min, d_max=d_max)
+             for b in range(n_pairs)]
+    return Workload(name=f"ablation_{size}_{ppp}_{d_max}_{n_pairs}_{n_flows}", seed=seed, pairs=pairs,
+                    flows=flows, out_dtype="f32", quant_bits=0, n_substeps=4, dt=1.0,
+                    description=f"{n_pairs} pairs {size}x{size}, ppp {ppp if ppp_min is None else (ppp_min, ppp)}, "
+                                f"d~U[{d_min},{d_max}], F={n_flows}, f32")
