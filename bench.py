@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--pairs", type=int, default=N_PAIRS, help="pairs per step (profiling a smaller case)")
     ap.add_argument("--workload", default="batch64_512_u8",
                     choices=("batch64_512_u8", "uneven256", "diff32_256", "large_mixed", "shapes64_512",
-                             "ablations"),
+                             "ablations", "stream512"),
                     help="the headline workload (default) or one of the other workloads, measured on their own")
     ap.add_argument("--quick", action="store_true",
                     help="timed steps only (no autotune, graph, FP16, e2e, per-pair or CPU legs): for profilers")
@@ -665,6 +665,35 @@ def run_other(args):
                      "general_over_round_ms": res["general"]["ms_per_step"] / res["round"]["ms_per_step"]})
     elif args.workload == "ablations":
         line.update(run_ablations(args, flush, stream))
+    elif args.workload == "stream512":
+        # the streaming sampler on the headline configuration: a new set of
+        # procedural flows every batch (generated on a side stream, one set
+        # ahead) or one set reused; device time per batch on the render stream
+        from paper_2512_09664_b300 import sampler as S
+        res = {}
+        for name, F, R in (("F64_R1", 64, 1), ("F1_R1", 1, 1), ("F64_reused", 64, 10 ** 9)):
+            cfg = {"image_shape": [512, 512], "batch_size": 64, "flows_per_batch": F, "batches_per_flow": R,
+                   "seed": 1, "seeding_density": 0.05, "diameter": [1.0, 4.0], "illumination": [0.7, 1.0],
+                   "noise_sigma": 0.02, "blur_sigma": 0.7, "output": "u8", "bits": 8,
+                   "flow": {"kind": "fourier", "rms": 3.0}}
+            smp = S.make(cfg)
+            for _ in range(args.warmup):
+                next(smp)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                next(smp)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            res[name] = {"ms_per_batch": ms, "value": 64 / (ms / 1e3), "flows_per_batch": F,
+                         "batches_per_flow": R if R < 10 ** 9 else "all"}
+            del smp
+            torch.cuda.empty_cache()
+        line.update({"config": "streaming sampler, 64 pairs 512x512 u8 per batch (the headline recipe), "
+                               "Fourier flows rms 3 generated on the device", "paths": res,
+                     "value": res["F64_R1"]["value"]})
     else:  # large_mixed
         wl = W.large_mixed_batch()
         res = {}

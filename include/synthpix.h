@@ -322,6 +322,30 @@ int synthpix_autotune_tile(const synthpix_batch_desc *batch, const synthpix_pair
 /* Message of the last failing call on this host thread ("" if none). */
 const char *synthpix_last_error(void);
 
+/*
+ * Procedural flow fields on the device, for streaming renders (Section 2,
+ * "Data loaders": flows may be supplied procedurally).  Writes n_flows
+ * divergence-free fields to flows (device, float32 [n_flows][flow_h][flow_w]
+ * [2], 8-byte aligned, caller-owned): field f is the curl of the stream
+ * function psi = sum_m a_m sin(kx_m x + ky_m y + phi_m), u = d psi / dy,
+ * v = -d psi / dx, at the cell-centred nodes ((l + 1/2) width / flow_w,
+ * (k + 1/2) height / flow_h) of a height x width image, scaled so that
+ * sqrt(mean(u^2 + v^2)) = rms (rms = 0 leaves the field unscaled).
+ *   modes      device, 8-byte aligned, float64 [n_flows][n_modes][4]:
+ *              (kx, ky, phi, a) per mode, k in radians per pixel;
+ *   n_flows    1..65535; n_modes 1..256; sizes 1..32768;
+ *   workspace  device, 256-byte aligned, at least
+ *              synthpix_fourier_flows_workspace_bytes(...) bytes (per-mode
+ *              cos / sin tables of the grid's columns and rows).
+ * Angles are formed and reduced in FP64, their cos / sin tabulated in FP32;
+ * the sums over the modes are FP32, the normalisation FP64.  Asynchronous on stream;
+ * SYNTHPIX_EINVAL / SYNTHPIX_EWORKSPACE before any launch on bad arguments.
+ */
+size_t synthpix_fourier_flows_workspace_bytes(int32_t n_flows, int32_t n_modes, int32_t flow_h, int32_t flow_w);
+int synthpix_fourier_flows(int32_t n_flows, int32_t n_modes, int32_t flow_h, int32_t flow_w, int32_t height,
+                           int32_t width, const double *modes, float rms, float *flows, void *workspace,
+                           size_t workspace_bytes, void *stream);
+
 /* SYNTHPIX_ABI_VERSION of the loaded library. */
 int synthpix_version(void);
 

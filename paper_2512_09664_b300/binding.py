@@ -96,6 +96,11 @@ def lib():
                                              vp, vp, vp, sz, vp, C.c_int32, C.POINTER(C.c_int32),
                                              C.POINTER(C.c_float)]
         L.synthpix_autotune_tile.restype = C.c_int
+        L.synthpix_fourier_flows_workspace_bytes.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32]
+        L.synthpix_fourier_flows_workspace_bytes.restype = sz
+        L.synthpix_fourier_flows.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                             vp, C.c_float, vp, vp, sz, vp]
+        L.synthpix_fourier_flows.restype = C.c_int
         L.synthpix_last_error.argtypes = []
         L.synthpix_last_error.restype = C.c_char_p
         L.synthpix_version.argtypes = []
@@ -226,6 +231,26 @@ def render_pairs_staged(pk: Packed, flows_dev, images_dev, workspace_dev, events
         C.c_void_p(workspace_dev.data_ptr()), workspace_dev.numel() * workspace_dev.element_size(),
         C.c_void_p(st.cuda_stream), arr)
     _check(rc)
+
+
+def fourier_flows(modes_dev, flow_h: int, flow_w: int, height: int, width: int, rms: float, flows_dev,
+                  workspace_dev, stream=None) -> None:
+    """synthpix_fourier_flows: modes_dev float64 [F, M, 4] -> flows_dev float32 [F, flow_h, flow_w, 2]."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    F, M = int(modes_dev.shape[0]), int(modes_dev.shape[1])
+    rc = lib().synthpix_fourier_flows(F, M, flow_h, flow_w, height, width, C.c_void_p(modes_dev.data_ptr()),
+                                      float(rms), C.c_void_p(flows_dev.data_ptr()),
+                                      C.c_void_p(workspace_dev.data_ptr()),
+                                      workspace_dev.numel() * workspace_dev.element_size(), C.c_void_p(st.cuda_stream))
+    _check(rc)
+
+
+def fourier_flows_workspace_bytes(n_flows: int, n_modes: int, flow_h: int, flow_w: int) -> int:
+    n = lib().synthpix_fourier_flows_workspace_bytes(n_flows, n_modes, flow_h, flow_w)
+    if n == 0:
+        raise SynthpixError(EINVAL, last_error())
+    return n
 
 
 class Renderer:

@@ -166,6 +166,40 @@ def lamb_oseen_flow(gh: int, gw: int, height: int, width: int,
     return f.astype(np.float32)
 
 
+def fourier_modes(seed: int, height: int, width: int, n_modes: int = 64,
+                  k_max_wavelength: float = 16.0) -> np.ndarray:
+    """[n_modes, 4] float64 (kx, ky, phi, a) of the stream function of fourier_flow.
+
+    |k_m| log-spaced between 2 pi / max(H, W) and 2 pi / k_max_wavelength,
+    directions and phases uniform from the seeded generator, a_m ~ |k_m|^(-4/3).
+    """
+    rng = np.random.default_rng(seed)
+    kmin = 2.0 * math.pi / max(height, width)
+    kmax = 2.0 * math.pi / k_max_wavelength
+    kmag = np.exp(np.linspace(math.log(kmin), math.log(kmax), n_modes))
+    theta = rng.uniform(0.0, 2.0 * math.pi, n_modes)
+    phi = rng.uniform(0.0, 2.0 * math.pi, n_modes)
+    amp = kmag ** (-4.0 / 3.0)
+    return np.stack([kmag * np.cos(theta), kmag * np.sin(theta), phi, amp], axis=1)
+
+
+def fourier_modes_set(key, n_flows: int, height: int, width: int, n_modes: int = 64,
+                      k_max_wavelength: float = 16.0) -> np.ndarray:
+    """[n_flows, n_modes, 4] modes (kx, ky, phi, a) of n_flows fields from one generator keyed by key.
+
+    The same spectrum as fourier_modes; directions and phases of all the
+    fields are drawn at once (a [n_flows, n_modes] array each).
+    """
+    rng = np.random.default_rng(key)
+    kmin = 2.0 * math.pi / max(height, width)
+    kmax = 2.0 * math.pi / k_max_wavelength
+    kmag = np.exp(np.linspace(math.log(kmin), math.log(kmax), n_modes))[None, :]
+    theta = rng.uniform(0.0, 2.0 * math.pi, (n_flows, n_modes))
+    phi = rng.uniform(0.0, 2.0 * math.pi, (n_flows, n_modes))
+    amp = np.broadcast_to(kmag ** (-4.0 / 3.0), (n_flows, n_modes))
+    return np.stack([kmag * np.cos(theta), kmag * np.sin(theta), phi, amp], axis=2)
+
+
 def fourier_flow(gh: int, gw: int, height: int, width: int, rms: float,
                  seed: int, n_modes: int = 64, k_max_wavelength: float = 16.0) -> np.ndarray:
     """Divergence-free random flow from a streamfunction of n_modes plane waves.
@@ -176,14 +210,14 @@ def fourier_flow(gh: int, gw: int, height: int, width: int, rms: float,
     E(k) ~ k^(-5/3).  u = d psi / dy, v = -d psi / dx; rescaled to the
     requested RMS speed (px/frame).
     """
-    rng = np.random.default_rng(seed)
-    kmin = 2.0 * math.pi / max(height, width)
-    kmax = 2.0 * math.pi / k_max_wavelength
-    kmag = np.exp(np.linspace(math.log(kmin), math.log(kmax), n_modes))
-    theta = rng.uniform(0.0, 2.0 * math.pi, n_modes)
-    phi = rng.uniform(0.0, 2.0 * math.pi, n_modes)
-    amp = kmag ** (-4.0 / 3.0)
-    kx, ky = kmag * np.cos(theta), kmag * np.sin(theta)
+    return fourier_flow_from_modes(fourier_modes(seed, height, width, n_modes, k_max_wavelength),
+                                   gh, gw, height, width, rms)
+
+
+def fourier_flow_from_modes(modes: np.ndarray, gh: int, gw: int, height: int, width: int,
+                            rms: float) -> np.ndarray:
+    """The field of fourier_modes' stream function on a gh x gw cell-centred grid (FP64, stored FP32)."""
+    kx, ky, phi, amp = modes[:, 0], modes[:, 1], modes[:, 2], modes[:, 3]
     xs, ys = node_centres(gh, gw, height, width)
     # cos(kx x + phi + ky y) = cos(ky y) cos(kx x + phi) - sin(ky y) sin(kx x + phi),
     # summed over the modes as two matrix products
