@@ -45,6 +45,7 @@ class OraclePair(C.Structure):
         ("dy_min", C.c_double), ("dy_max", C.c_double), ("rho_min", C.c_double), ("rho_max", C.c_double),
         ("jitter_d", C.c_double), ("jitter_i", C.c_double), ("jitter_rho", C.c_double),
         ("hide_prob", C.c_double),
+        ("sheet_model", C.c_int32), ("sheet_shape", C.c_double),
     ]
 
 
@@ -95,6 +96,13 @@ def lib():
         L.oracle_epilogue.restype = C.c_int
         L.oracle_render_pair.argtypes = [C.POINTER(OraclePair), fp, dp, dp, up, dp, C.c_int32]
         L.oracle_render_pair.restype = C.c_int
+        L.oracle_render_pair3.argtypes = [C.POINTER(OraclePair), fp, fp, dp, dp, up, dp, C.c_int32]
+        L.oracle_render_pair3.restype = C.c_int
+        L.oracle_sheet_gain.argtypes = [C.POINTER(OraclePair), C.c_double]
+        L.oracle_sheet_gain.restype = C.c_double
+        L.oracle_scalar_at.argtypes = [fp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double]
+        L.oracle_scalar_at.restype = C.c_double
+        L.oracle_advect3.argtypes = [C.POINTER(OraclePair), fp, fp, C.c_double, C.c_double, C.c_double, dp, dp, dp]
         L.oracle_render_from.argtypes = [C.POINTER(OraclePair), fp, dp, dp]
         L.oracle_render_from.restype = C.c_int
         L.oracle_backward.argtypes = [C.POINTER(OraclePair), fp, dp, dp, dp, dp]
@@ -120,6 +128,7 @@ def make_pair(spec, seed: int, integrator: str = "rk4", n_substeps: int = 4, dt=
     return OraclePair(
         dy_min=g("dy_min"), dy_max=g("dy_max"), rho_min=g("rho_min"), rho_max=g("rho_max"),
         jitter_d=g("jitter_d"), jitter_i=g("jitter_i"), jitter_rho=g("jitter_rho"), hide_prob=f(hide_prob),
+        sheet_model=int(getattr(spec, "sheet_model", 0)), sheet_shape=g("sheet_shape"),
         height=spec.height, width=spec.width, flow_h=gh, flow_w=gw,
         n_particles=spec.n_particles, seed=seed, pair_id=spec.pair_id,
         d_dist=spec.d_dist, integrator=0 if integrator == "rk4" else 1,
@@ -237,17 +246,37 @@ def epilogue(pair: OraclePair, frame: int, S: np.ndarray):
     return B, Q
 
 
-def render_pair(pair: OraclePair, flow: np.ndarray, splat_mode: int = 0, want_particles=False):
-    """Returns dict with S [2,H,W], B [2,H,W], Q [2,H,W] (uint32 codes) and parts."""
+def sheet_gain(pair: OraclePair, z: float) -> float:
+    return lib().oracle_sheet_gain(C.byref(pair), z)
+
+
+def scalar_at(w: np.ndarray, height: int, width: int, x: float, y: float) -> float:
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    return lib().oracle_scalar_at(_ptr(w, C.c_float), w.shape[0], w.shape[1], height, width, x, y)
+
+
+def advect3(pair: OraclePair, flow: np.ndarray, w: np.ndarray, x: float, y: float, z: float):
     flow = np.ascontiguousarray(flow, dtype=np.float32)
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    xo, yo, zo = C.c_double(), C.c_double(), C.c_double()
+    lib().oracle_advect3(C.byref(pair), _ptr(flow, C.c_float), _ptr(w, C.c_float), x, y, z, C.byref(xo),
+                         C.byref(yo), C.byref(zo))
+    return xo.value, yo.value, zo.value
+
+
+def render_pair(pair: OraclePair, flow: np.ndarray, splat_mode: int = 0, want_particles=False, wgrid=None):
+    """Returns dict with S [2,H,W], B [2,H,W], Q [2,H,W] (uint32 codes) and parts.
+    wgrid: optional [flow_h, flow_w] out-of-plane velocity (moves z along the path)."""
+    flow = np.ascontiguousarray(flow, dtype=np.float32)
+    wg = None if wgrid is None else np.ascontiguousarray(wgrid, dtype=np.float32)
     H, W = pair.height, pair.width
     S = np.zeros((2, H, W), dtype=np.float64)
     B = np.zeros((2, H, W), dtype=np.float64)
     Q = np.zeros((2, H, W), dtype=np.uint32)
     parts = np.zeros((max(pair.n_particles, 0), 8), dtype=np.float64) if want_particles else None
-    rc = lib().oracle_render_pair(C.byref(pair), _ptr(flow, C.c_float), _ptr(S, C.c_double),
-                                  _ptr(B, C.c_double), _ptr(Q, C.c_uint32),
-                                  _ptr(parts, C.c_double), splat_mode)
+    rc = lib().oracle_render_pair3(C.byref(pair), _ptr(flow, C.c_float), _ptr(wg, C.c_float), _ptr(S, C.c_double),
+                                   _ptr(B, C.c_double), _ptr(Q, C.c_uint32),
+                                   _ptr(parts, C.c_double), splat_mode)
     if rc != 0:
         raise MemoryError("oracle_render_pair failed")
     return {"S": S, "B": B, "Q": Q, "parts": parts}
@@ -281,9 +310,12 @@ def render_workload(wl, pairs=None, threads: int | None = None, want_particles=F
     """Render the selected pairs of a workload on host threads (ctypes releases the GIL)."""
     idx = list(range(wl.n_pairs)) if pairs is None else list(pairs)
     lib()
+    fw = getattr(wl, "flows_w", None)
+
     def one(b):
-        return render_pair(pair_from_workload(wl, b), wl.flows[wl.pairs[b].flow_index],
-                           want_particles=want_particles)
+        fi = wl.pairs[b].flow_index
+        return render_pair(pair_from_workload(wl, b), wl.flows[fi], want_particles=want_particles,
+                           wgrid=None if fw is None else fw[fi])
     n = threads or min(len(idx), os.cpu_count() or 1)
     if n <= 1:
         return [one(b) for b in idx]

@@ -47,6 +47,13 @@
  *       the frame-2 change of d and I0), tag 3 -> (d_y, rho, two normals for
  *       the frame-2 change of d_y and rho), tag 0x100 + f -> noise words of
  *       frame f.
+ *   R9  out-of-focus intensity: the Gaussian sheet of R3, or the Remark
+ *       "out-of-focus" form exp(-|2 z^2 / dz0^2|^s / sqrt(2 pi)) with the
+ *       sheet thickness dz0 and shape factor s, the drawn I0 playing the
+ *       scattering efficiency q.  Out-of-plane motion (the Remark's 3-D flow):
+ *       an optional scalar grid w (same nodes as the flow) moves z along the
+ *       particle's path, integrated with the same substeps and stages as x,
+ *       y; frame 2's intensity then uses the moved z.
  *   R8  general particle shapes (Eq. 1 with sigma_x != sigma_y and rho != 0;
  *       text after Eq. 1): sigma_x = d / 4, sigma_y = d_y / 4 with d_y drawn
  *       from its own interval (d_y = d when that interval is [0, 0]), rho from
@@ -83,6 +90,9 @@ typedef struct {
     /* general shapes, frame-2 variation, hiding (R8); all 0: round particles */
     double dy_min, dy_max, rho_min, rho_max;
     double jitter_d, jitter_i, jitter_rho, hide_prob;
+    /* out-of-focus model (R9): 0 Gaussian sheet, 1 Remark form with shape factor */
+    int32_t sheet_model;
+    double sheet_shape;
 } oracle_pair;
 
 /* ------------------------------------------------------------------------ */
@@ -137,6 +147,17 @@ static double box_muller(uint32_t wa, uint32_t wb, int second)
 /* ------------------------------------------------------------------------ */
 typedef struct { double x0, y0, d, intensity, z, gain, ieff; } oracle_attr;
 
+/* Intensity factor of a particle at out-of-plane position z (R3, R9). */
+double oracle_sheet_gain(const oracle_pair *p, double z)
+{
+    if (!(p->sheet_sigma > 0.0)) return 1.0;
+    if (p->sheet_model == 1) {
+        double q = fabs(2.0 * z * z / (p->sheet_sigma * p->sheet_sigma));
+        return exp(-pow(q, p->sheet_shape) / sqrt(2.0 * ORACLE_PI));
+    }
+    return exp(-(z * z) / (2.0 * p->sheet_sigma * p->sheet_sigma));
+}
+
 static void particle_attr(const oracle_pair *p, uint32_t i, oracle_attr *a)
 {
     uint32_t w0[4], w1[4];
@@ -153,11 +174,8 @@ static void particle_attr(const oracle_pair *p, uint32_t i, oracle_attr *a)
     }
     a->intensity = p->i_min + u24(w0[3]) * (p->i_max - p->i_min);
     a->z = p->z_min + u24(w1[0]) * (p->z_max - p->z_min);
-    double gain = 1.0;
-    if (p->sheet_sigma > 0.0)
-        gain = exp(-(a->z * a->z) / (2.0 * p->sheet_sigma * p->sheet_sigma));
-    a->gain = gain;
-    a->ieff = a->intensity * gain;
+    a->gain = oracle_sheet_gain(p, a->z);
+    a->ieff = a->intensity * a->gain;
 }
 
 static double clampd(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
@@ -170,8 +188,9 @@ int oracle_round_particles(const oracle_pair *p)
     return p->dy_min == 0.0 && p->dy_max == 0.0 && p->rho_min == 0.0 && p->rho_max == 0.0;
 }
 
-/* Frame 1 and frame 2 shapes of particle i with attributes a (R8). */
-static void particle_shapes(const oracle_pair *p, uint32_t i, const oracle_attr *a, oracle_shape s[2])
+/* Frame 1 and frame 2 shapes of particle i with attributes a (R8); gain2 is
+ * the sheet factor in frame 2 (a->gain unless the particle moved in z, R9). */
+static void particle_shapes(const oracle_pair *p, uint32_t i, const oracle_attr *a, double gain2, oracle_shape s[2])
 {
     uint32_t w2[4], w3[4];
     oracle_stream_words(p->seed, p->pair_id, i, 2u, w2);
@@ -189,7 +208,7 @@ static void particle_shapes(const oracle_pair *p, uint32_t i, const oracle_attr 
     s[1].dx = dx2;
     s[1].dy = same_d ? dx2 : clampd(dy + p->jitter_d * box_muller(w3[2], w3[3], 0), p->dy_min, p->dy_max);
     s[1].rho = clampd(rho + p->jitter_rho * box_muller(w3[2], w3[3], 1), p->rho_min, p->rho_max);
-    s[1].ieff = i2 * a->gain;
+    s[1].ieff = i2 * gain2;
     s[1].visible = !(u24(w2[1]) < p->hide_prob);
 }
 
@@ -203,7 +222,7 @@ int oracle_particle_shapes(const oracle_pair *p, double *out)
         oracle_attr a;
         oracle_shape s[2];
         particle_attr(p, (uint32_t)i, &a);
-        particle_shapes(p, (uint32_t)i, &a, s);
+        particle_shapes(p, (uint32_t)i, &a, a.gain, s);
         for (int f = 0; f < 2; ++f) {
             double *o = out + 10 * i + 5 * f;
             o[0] = s[f].dx; o[1] = s[f].dy; o[2] = s[f].rho; o[3] = s[f].ieff; o[4] = (double)s[f].visible;
@@ -264,6 +283,57 @@ void oracle_advect(const oracle_pair *p, const float *flow, double x, double y,
     }
     *xo = x;
     *yo = y;
+}
+
+/* Scalar w (out-of-plane velocity) at (x, y): bilinear on the same nodes as the flow (R9). */
+double oracle_scalar_at(const float *w, int32_t gh, int32_t gw, int32_t height, int32_t width, double x, double y)
+{
+    double gx = x * (double)gw / (double)width - 0.5;
+    double gy = y * (double)gh / (double)height - 0.5;
+    double fl = floor(gx), fk = floor(gy);
+    double tx = gx - fl, ty = gy - fk;
+    long l0 = clampl((long)fl, 0, gw - 1), l1 = clampl((long)fl + 1, 0, gw - 1);
+    long k0 = clampl((long)fk, 0, gh - 1), k1 = clampl((long)fk + 1, 0, gh - 1);
+    double a = w[k0 * gw + l0], b = w[k0 * gw + l1], e = w[k1 * gw + l0], f = w[k1 * gw + l1];
+    double top = a + tx * (b - a), bot = e + tx * (f - e);
+    return top + ty * (bot - top);
+}
+
+/* Position after dt and the out-of-plane position moved by w along the path
+ * (R9): the stages of oracle_advect, each also evaluating w. */
+void oracle_advect3(const oracle_pair *p, const float *flow, const float *w, double x, double y, double z,
+                    double *xo, double *yo, double *zo)
+{
+    int n = p->n_substeps;
+    double h = p->dt / (double)n;
+    const int32_t gh = p->flow_h, gw = p->flow_w, H = p->height, W = p->width;
+    for (int s = 0; s < n; ++s) {
+        double u1, v1;
+        oracle_velocity(flow, gh, gw, H, W, x, y, &u1, &v1);
+        double w1 = oracle_scalar_at(w, gh, gw, H, W, x, y);
+        if (p->integrator == 1) {
+            x += h * u1;
+            y += h * v1;
+            z += h * w1;
+            continue;
+        }
+        double u2, v2, u3, v3, u4, v4;
+        double x2 = x + 0.5 * h * u1, y2 = y + 0.5 * h * v1;
+        oracle_velocity(flow, gh, gw, H, W, x2, y2, &u2, &v2);
+        double w2 = oracle_scalar_at(w, gh, gw, H, W, x2, y2);
+        double x3 = x + 0.5 * h * u2, y3 = y + 0.5 * h * v2;
+        oracle_velocity(flow, gh, gw, H, W, x3, y3, &u3, &v3);
+        double w3 = oracle_scalar_at(w, gh, gw, H, W, x3, y3);
+        double x4 = x + h * u3, y4 = y + h * v3;
+        oracle_velocity(flow, gh, gw, H, W, x4, y4, &u4, &v4);
+        double w4 = oracle_scalar_at(w, gh, gw, H, W, x4, y4);
+        x += h / 6.0 * (u1 + 2.0 * u2 + 2.0 * u3 + u4);
+        y += h / 6.0 * (v1 + 2.0 * v2 + 2.0 * v3 + v4);
+        z += h / 6.0 * (w1 + 2.0 * w2 + 2.0 * w3 + w4);
+    }
+    *xo = x;
+    *yo = y;
+    *zo = z;
 }
 
 /*
@@ -543,8 +613,18 @@ int oracle_epilogue(const oracle_pair *p, int32_t frame, const double *S, double
  * (nullable) the particle table of oracle_particles.  Frame f occupies
  * [f*H*W, (f+1)*H*W) of each output.
  */
+int oracle_render_pair3(const oracle_pair *p, const float *flow, const float *wgrid, double *S, double *B,
+                        uint32_t *Q, double *parts, int32_t splat_mode);
+
 int oracle_render_pair(const oracle_pair *p, const float *flow, double *S, double *B, uint32_t *Q,
                        double *parts, int32_t splat_mode)
+{
+    return oracle_render_pair3(p, flow, NULL, S, B, Q, parts, splat_mode);
+}
+
+/* oracle_render_pair with out-of-plane motion: wgrid (nullable) [flow_h][flow_w] (R9). */
+int oracle_render_pair3(const oracle_pair *p, const float *flow, const float *wgrid, double *S, double *B,
+                        uint32_t *Q, double *parts, int32_t splat_mode)
 {
     const int64_t HW = (int64_t)p->height * p->width;
     const int64_t n = p->n_particles;
@@ -555,12 +635,29 @@ int oracle_render_pair(const oracle_pair *p, const float *flow, double *S, doubl
     oracle_particles(p, flow, tab);
     memset(s, 0, sizeof(double) * (size_t)(2 * HW));
     const int general = !oracle_round_particles(p) || p->jitter_d != 0.0 || p->jitter_i != 0.0 ||
-                        p->jitter_rho != 0.0 || p->hide_prob > 0.0;
+                        p->jitter_rho != 0.0 || p->hide_prob > 0.0 || wgrid != NULL;
     if (general) {
         double *sh = (double *)malloc(sizeof(double) * (size_t)(10 * (n > 0 ? n : 1)));
         double *rows = (double *)malloc(sizeof(double) * (size_t)(6 * (n > 0 ? n : 1)));
         if (!sh || !rows) { free(sh); free(rows); free(tab); free(xy); if (!S) free(s); return -1; }
-        oracle_particle_shapes(p, sh);
+        for (int64_t i = 0; i < n; ++i) {
+            oracle_attr a;
+            oracle_shape sp[2];
+            particle_attr(p, (uint32_t)i, &a);
+            double gain2 = a.gain;
+            if (wgrid) {  /* frame-2 position and depth moved together (R9) */
+                double x1, y1, z1;
+                oracle_advect3(p, flow, wgrid, a.x0, a.y0, a.z, &x1, &y1, &z1);
+                tab[8 * i + 6] = x1;
+                tab[8 * i + 7] = y1;
+                gain2 = oracle_sheet_gain(p, z1);
+            }
+            particle_shapes(p, (uint32_t)i, &a, gain2, sp);
+            for (int f = 0; f < 2; ++f) {
+                double *o = sh + 10 * i + 5 * f;
+                o[0] = sp[f].dx; o[1] = sp[f].dy; o[2] = sp[f].rho; o[3] = sp[f].ieff; o[4] = (double)sp[f].visible;
+            }
+        }
         for (int f = 0; f < 2; ++f) {
             int64_t m = 0;
             for (int64_t i = 0; i < n; ++i) {

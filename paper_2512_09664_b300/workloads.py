@@ -23,7 +23,7 @@ from __future__ import annotations
 
 import math
 from dataclasses import dataclass, field, replace
-from typing import List
+from typing import List, Optional
 
 import numpy as np
 
@@ -66,12 +66,14 @@ class PairSpec:
     jitter_d: np.float32 = F32(0.0)    # std of the frame-2 change of each diameter (px)
     jitter_i: np.float32 = F32(0.0)    # std of the frame-2 change of I0
     jitter_rho: np.float32 = F32(0.0)  # std of the frame-2 change of rho
+    sheet_model: int = 0               # 0: Gaussian sheet; 1: the out-of-focus Remark form
+    sheet_shape: np.float32 = F32(0.0)  # shape factor s of the Remark form
 
     def __post_init__(self):
         for k in ("d_min", "d_max", "d_mu", "d_sigma", "i_min", "i_max", "z_min",
                   "z_max", "sheet_sigma", "illum_min", "illum_max", "noise_sigma",
                   "blur_sigma", "dy_min", "dy_max", "rho_min", "rho_max", "jitter_d",
-                  "jitter_i", "jitter_rho"):
+                  "jitter_i", "jitter_rho", "sheet_shape"):
             setattr(self, k, F32(getattr(self, k)))
 
 
@@ -92,6 +94,7 @@ class Workload:
     description: str = ""
     meta: dict = field(default_factory=dict)
     hide_prob: np.float32 = F32(0.0)  # probability of hiding a particle from each frame
+    flows_w: Optional[List[np.ndarray]] = None  # per flow grid: out-of-plane velocity [gh, gw] (moves z)
 
     def __post_init__(self):
         self.dt = F32(self.dt)
@@ -107,7 +110,8 @@ class Workload:
         used = sorted({self.pairs[i].flow_index for i in idx})
         remap = {f: n for n, f in enumerate(used)}
         pairs = [replace(self.pairs[i], flow_index=remap[self.pairs[i].flow_index]) for i in idx]
-        return replace(self, pairs=pairs, flows=[self.flows[f] for f in used],
+        fw = None if self.flows_w is None else [self.flows_w[f] for f in used]
+        return replace(self, pairs=pairs, flows=[self.flows[f] for f in used], flows_w=fw,
                        name=f"{self.name}[{len(idx)}]")
 
     def image_elems(self) -> int:
