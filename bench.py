@@ -631,8 +631,10 @@ def run_other(args):
         # variation and hiding (general-shape splat), and round particles with
         # variation and hiding (round splat, per-particle advection)
         res = {}
-        for kind in ("general", "round"):
-            wl = W.shapes_batch(n_pairs=64, general=kind == "general")
+        for kind in ("general", "round", "focus"):
+            # focus: round particles, the Remark's out-of-focus intensity and a w grid per pair
+            wl = W.focus_batch(n_pairs=64) if kind == "focus" else W.shapes_batch(n_pairs=64,
+                                                                                 general=kind == "general")
             r = Renderer(wl)
             tile, _ = r.autotune(reps=1)
             for _ in range(args.warmup):

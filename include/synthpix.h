@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define SYNTHPIX_ABI_VERSION 2
+#define SYNTHPIX_ABI_VERSION 3
 
 /* ---- status codes ------------------------------------------------------ */
 #define SYNTHPIX_OK            0
@@ -63,15 +63,28 @@ extern "C" {
 #define SYNTHPIX_RK4   0
 #define SYNTHPIX_EULER 1
 
+/* sheet models (pair->sheet_model) */
+#define SYNTHPIX_SHEET_GAUSSIAN 0
+#define SYNTHPIX_SHEET_REMARK   1
+
 /* batch flags */
 #define SYNTHPIX_FLAG_GATHER_ADVECT 1  /* advect every particle by direct flow-grid gathers
                                           instead of the tiled advection (same result)  */
+#define SYNTHPIX_FLAG_OUT_OF_PLANE  2  /* out-of-plane motion (Remark "out-of-focus": a
+                                          three-dimensional flow): each pair's flow grid
+                                          is followed in `flows`, at flow_offset +
+                                          2 flow_h flow_w, by flow_h x flow_w floats w,
+                                          the out-of-plane velocity in units of z per
+                                          frame on the same nodes.  z moves along the
+                                          particle's path (the same RK4 / Euler stages
+                                          as x, y) and frame 2's intensity uses the
+                                          moved z.  Such renders advect per particle. */
 
 /*
  * Per-pair acquisition parameters (Abstract: seeding density, particle image
  * size, illumination non-uniformity, noise, blur, timing; Section 2 "Sampling
  * the particles": parameters drawn uniformly from configured intervals).
- * 128 bytes, naturally aligned; reserved fields must be zero.
+ * 160 bytes, naturally aligned; reserved fields must be zero.
  */
 typedef struct synthpix_pair_desc {
     int32_t  height, width;      /* frame size in pixels, 1..32768                   */
@@ -88,7 +101,8 @@ typedef struct synthpix_pair_desc {
     float d_mu, d_sigma;         /* normal diameter parameters (d_dist = 1)           */
     float i_min, i_max;          /* peak intensity I0 of Eq. 1 ~ U[i_min, i_max]       */
     float z_min, z_max;          /* out-of-plane position ~ U[z_min, z_max]            */
-    float sheet_sigma;           /* Gaussian laser sheet: I = I0 exp(-z^2/(2 s^2));
+    float sheet_sigma;           /* laser sheet: Gaussian I = I0 exp(-z^2/(2 s^2)), or the
+                                    thickness dz0 of the Remark form (sheet_model);
                                     <= 0 disables the attenuation                     */
     float illum_min, illum_max;  /* illumination field L in [illum_min, illum_max]:
                                     L = min + (max-min) sin^2(pi (j+.5)/W) sin^2(pi (i+.5)/H) */
@@ -112,6 +126,15 @@ typedef struct synthpix_pair_desc {
                                     the results clamped to [d_min, d_max] / [dy_min, dy_max] */
     float jitter_i;              /* std of the frame-2 change of I0, clamped to [i_min, i_max] */
     float jitter_rho;            /* std of the frame-2 change of rho, clamped to its interval */
+    /* Out-of-focus intensity (Remark "out-of-focus").                          */
+    int32_t sheet_model;         /* SYNTHPIX_SHEET_GAUSSIAN (0): exp(-z^2 / (2 sheet_sigma^2));
+                                    SYNTHPIX_SHEET_REMARK (1): the Remark's
+                                    exp(-|2 z^2 / sheet_sigma^2|^sheet_shape / sqrt(2 pi)),
+                                    I0 drawn in [i_min, i_max] playing the scattering
+                                    efficiency q                                       */
+    float sheet_shape;           /* shape factor s of the Remark form, 0 < s <= 16
+                                    (ignored, may be 0, for the Gaussian sheet)        */
+    int32_t reserved[6];         /* must be zero                                       */
 } synthpix_pair_desc;
 
 /*

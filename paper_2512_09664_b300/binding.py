@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_PKG, "libsynthpix.so")
 
 OK, EINVAL, EWORKSPACE, ECUDA, EUNSUPPORTED = 0, -1, -2, -3, -4
 FLAG_GATHER_ADVECT = 1  # advect per particle by direct flow gathers (default: tiled advection)
+FLAG_OUT_OF_PLANE = 2   # a w grid follows each flow grid; particles move in z (set by pack for flows_w)
 DTYPE_CODE = {"f32": 0, "f16": 1, "bf16": 2, "u8": 3, "u16": 4}
 INTEGRATOR_CODE = {"rk4": 0, "euler": 1}
 _EXPORTS = ("synthpix_workspace_bytes", "synthpix_render_pairs", "synthpix_render_pairs_staged",
@@ -41,6 +42,7 @@ class PairDesc(C.Structure):
         ("noise_sigma", C.c_float), ("blur_sigma", C.c_float),
         ("dy_min", C.c_float), ("dy_max", C.c_float), ("rho_min", C.c_float), ("rho_max", C.c_float),
         ("jitter_d", C.c_float), ("jitter_i", C.c_float), ("jitter_rho", C.c_float),
+        ("sheet_model", C.c_int32), ("sheet_shape", C.c_float), ("reserved", C.c_int32 * 6),
     ]
 
 
@@ -53,7 +55,7 @@ class BatchDesc(C.Structure):
     ]
 
 
-assert C.sizeof(PairDesc) == 128 and C.sizeof(BatchDesc) == 64
+assert C.sizeof(PairDesc) == 160 and C.sizeof(BatchDesc) == 64
 
 _lib = None
 
@@ -153,8 +155,9 @@ def pair_desc(spec, image_offset: int, flow_offset: int, flow_shape) -> PairDesc
     for k in ("d_min", "d_max", "d_mu", "d_sigma", "i_min", "i_max", "z_min", "z_max", "sheet_sigma",
               "illum_min", "illum_max", "noise_sigma", "blur_sigma"):
         setattr(p, k, float(getattr(spec, k)))
-    for k in ("dy_min", "dy_max", "rho_min", "rho_max", "jitter_d", "jitter_i", "jitter_rho"):
+    for k in ("dy_min", "dy_max", "rho_min", "rho_max", "jitter_d", "jitter_i", "jitter_rho", "sheet_shape"):
         setattr(p, k, float(getattr(spec, k, 0.0)))
+    p.sheet_model = int(getattr(spec, "sheet_model", 0))
     return p
 
 
@@ -182,10 +185,16 @@ def pack(wl, tile: int = 0, out_dtype: Optional[str] = None, inter_dtype: Option
     out_dtype = out_dtype or wl.out_dtype
     flat, flow_off = [], []
     off = 0
-    for f in wl.flows:
+    fw = getattr(wl, "flows_w", None)
+    for i, f in enumerate(wl.flows):  # each grid's (u, v), then its w when the batch moves particles in z
         flow_off.append(off)
         flat.append(np.ascontiguousarray(f, dtype=np.float32).reshape(-1))
         off += f.size
+        if fw is not None:
+            w = np.ascontiguousarray(fw[i], dtype=np.float32).reshape(-1)
+            assert w.size * 2 == f.size, "w grid must have the flow grid's nodes"
+            flat.append(w)
+            off += w.size
     arr = (PairDesc * max(wl.n_pairs, 1))()
     img_off, io = [], 0
     for b, spec in enumerate(wl.pairs):
@@ -195,6 +204,8 @@ def pack(wl, tile: int = 0, out_dtype: Optional[str] = None, inter_dtype: Option
     bd = batch_desc(wl.seed, out_dtype, wl.quant_bits if out_dtype in ("u8", "u16") else 0,
                     inter_dtype or wl.inter_dtype, wl.integrator, wl.n_substeps, wl.dt, tile,
                     getattr(wl, "hide_prob", 0.0))
+    if fw is not None:
+        bd.flags |= FLAG_OUT_OF_PLANE
     flows = np.concatenate(flat) if flat else np.zeros(2, np.float32)
     return Packed(bd, arr, wl.n_pairs, flows, img_off, io, out_dtype,
                   [(p.height, p.width) for p in wl.pairs])
@@ -260,7 +271,7 @@ class Renderer:
                  device_descriptors: bool = True, flags: int = 0):
         import torch
         self.pk = pack(wl, tile=tile, out_dtype=out_dtype, inter_dtype=inter_dtype)
-        self.pk.batch.flags = flags
+        self.pk.batch.flags |= flags
         self.device = torch.device(device)
         self.flows = torch.from_numpy(self.pk.flows_host).to(self.device)
         ws = workspace_bytes(self.pk)
@@ -269,7 +280,8 @@ class Renderer:
                                   device=self.device)
         self.pairs_dev = None
         if device_descriptors and self.pk.n_pairs > 0:
-            raw = np.frombuffer(C.string_at(C.addressof(self.pk.pairs), 128 * self.pk.n_pairs), dtype=np.uint8)
+            raw = np.frombuffer(C.string_at(C.addressof(self.pk.pairs), C.sizeof(PairDesc) * self.pk.n_pairs),
+                                dtype=np.uint8)
             self.pairs_dev = torch.from_numpy(raw.copy()).to(self.device)
 
     def render(self, stream=None):

@@ -53,7 +53,7 @@ int check_batch(const synthpix_batch_desc *b) {
     if (!finite(b->dt) || std::fabs(b->dt) > 64.0f) return fail(SYNTHPIX_EINVAL, "dt must be finite with |dt| <= 64");
     if (b->tile != 0 && b->tile != 16 && b->tile != 32 && b->tile != 64 && b->tile != 128)
         return fail(SYNTHPIX_EINVAL, "tile %d is not 0, 16, 32, 64 or 128", b->tile);
-    if (b->flags & ~SYNTHPIX_FLAG_GATHER_ADVECT)
+    if (b->flags & ~(SYNTHPIX_FLAG_GATHER_ADVECT | SYNTHPIX_FLAG_OUT_OF_PLANE))
         return fail(SYNTHPIX_EUNSUPPORTED, "unknown flags 0x%x", b->flags);
     if (!finite(b->hide_prob) || b->hide_prob < 0.0f || b->hide_prob > 1.0f)
         return fail(SYNTHPIX_EINVAL, "hide_prob must lie in [0, 1]");
@@ -94,6 +94,13 @@ int check_pair(const synthpix_pair_desc &d, int b) {
     if (d.jitter_d < 0.0f || d.jitter_i < 0.0f || d.jitter_rho < 0.0f || d.jitter_d > 1e6f || d.jitter_i > 1e6f ||
         d.jitter_rho > 1e6f)
         return fail(SYNTHPIX_EINVAL, "pair %d: jitter stds must lie in [0, 1e6]", b);
+    if (d.sheet_model != SYNTHPIX_SHEET_GAUSSIAN && d.sheet_model != SYNTHPIX_SHEET_REMARK)
+        return fail(SYNTHPIX_EINVAL, "pair %d: sheet_model must be 0 (Gaussian) or 1 (Remark form)", b);
+    if (d.sheet_model == SYNTHPIX_SHEET_REMARK && !(d.sheet_shape > 0.0f && d.sheet_shape <= 16.0f))
+        return fail(SYNTHPIX_EINVAL, "pair %d: the Remark form needs 0 < sheet_shape <= 16", b);
+    if (!finite(d.sheet_shape)) return fail(SYNTHPIX_EINVAL, "pair %d: non-finite sheet_shape", b);
+    for (int k = 0; k < 6; ++k)
+        if (d.reserved[k] != 0) return fail(SYNTHPIX_EUNSUPPORTED, "pair %d: reserved[%d] is not zero", b, k);
     return SYNTHPIX_OK;
 }
 
@@ -127,7 +134,7 @@ int make_plan_tile(const synthpix_batch_desc *batch, const synthpix_pair_desc *p
     P.max_halo = 0;
     P.max_r = 0;
     P.max_d = 0.0f;
-    P.ext = batch->hide_prob > 0.0f ? 1 : 0;
+    P.ext = (batch->hide_prob > 0.0f || (batch->flags & SYNTHPIX_FLAG_OUT_OF_PLANE)) ? 1 : 0;
     P.general = 0;
     spx::Layout &L = P.L;
     L.n_part = L.n_tiles = L.n_list = L.n_inter = L.n_chunks = 0;
@@ -188,7 +195,7 @@ constexpr int kTileCandidates[4] = {16, 32, 64, 128};
 
 }  // namespace
 
-static_assert(sizeof(synthpix_pair_desc) == 128, "pair descriptor ABI");
+static_assert(sizeof(synthpix_pair_desc) == 160, "pair descriptor ABI");
 static_assert(sizeof(synthpix_batch_desc) == 64, "batch descriptor ABI");
 
 extern "C" {
@@ -312,6 +319,7 @@ static int run(Mode mode, const synthpix_batch_desc *batch, const synthpix_pair_
     a.ext = P.ext;
     a.general = P.general;
     a.hide_prob = batch->hide_prob;
+    a.out_of_plane = (batch->flags & SYNTHPIX_FLAG_OUT_OF_PLANE) ? 1 : 0;
     a.count = mode == Mode::Render ? reinterpret_cast<uint32_t *>(ws + L.count) : nullptr;
     a.off = reinterpret_cast<uint32_t *>(ws + L.off);
     a.cursor = reinterpret_cast<uint32_t *>(ws + L.cursor);

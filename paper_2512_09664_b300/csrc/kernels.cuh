@@ -31,6 +31,7 @@ struct KernelArgs {
     int32_t ext;                      // 1: per-frame shapes (general shapes, variation or hiding)
     int32_t general;                  // 1: bins hold RecordG (general-shape splat)
     float hide_prob;                  // probability of hiding a particle from a frame
+    int32_t out_of_plane;             // 1: a w grid follows each flow grid; z moves along the path
     uint32_t *count, *off, *cursor;   // per (pair, frame, tile)
     ItemInfo *items;                  // per (pair, frame, tile): the splat's work items
     Record *rec;                      // bins
@@ -66,7 +67,9 @@ inline cudaError_t launch_kernel(void (*kernel)(P...), unsigned grid, unsigned b
 }
 constexpr int kSplatThreads = 256;      // k_splat below tile 128, k_finish
 constexpr int kSplatMaxThreads = 1024;  // k_splat at tile 128 (one CTA per SM)
-constexpr int kStageHeader = 320;       // descriptor (128) + plan (64) + blur taps (128)
+constexpr int kStageDesc = (int)sizeof(synthpix_pair_desc);  // staged header: descriptor (160),
+constexpr int kStagePlan = kStageDesc + (int)sizeof(PairPlan);  // plan (64),
+constexpr int kStageHeader = kStagePlan + 128;                  // blur taps (128)
 constexpr int kRecBufBytes = 8192;      // each staged-records buffer of k_splat (tiles up to 64)
 constexpr int kRecBufBytesLarge = 24576;  // the same at tile 128
 // records of rec_bytes bytes per staged chunk of a buffer

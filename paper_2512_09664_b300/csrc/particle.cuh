@@ -135,13 +135,25 @@ __device__ __forceinline__ float pixel_mass(float sa, float sb, bool a_pos, bool
 }
 
 // A particle of frame 1: split position, sigma = d / 4, amplitude Ieff 2 pi sigma^2;
-// d, I0 and the sheet gain for the per-frame shapes.
+// d, I0, the out-of-plane position z and its sheet gain for the per-frame shapes.
 struct Seeded {
     int32_t ix, iy;
     float fx, fy;
     float sigma, amp;
-    float d, i0, gain;
+    float d, i0, z, gain;
 };
+
+// Intensity factor at out-of-plane position z: the Gaussian sheet
+// exp(-z^2 / (2 s^2)), or the out-of-focus form of the Remark
+// exp(-|2 z^2 / dz0^2|^shape / sqrt(2 pi)) with dz0 = sheet_sigma.
+__device__ __forceinline__ float sheet_gain(const synthpix_pair_desc &D, float z) {
+    if (!(D.sheet_sigma > 0.0f)) return 1.0f;
+    if (D.sheet_model == SYNTHPIX_SHEET_REMARK) {
+        const float q = fabsf(2.0f * z * z / (D.sheet_sigma * D.sheet_sigma));
+        return expf(-powf(q, D.sheet_shape) * 0.39894228040143267794f);
+    }
+    return expf(-(z * z) / (2.0f * D.sheet_sigma * D.sheet_sigma));
+}
 
 // Attributes of particle i of a pair (Section 2, "Sampling the particles":
 // uniform position over the image, parameters from their intervals; the
@@ -180,12 +192,12 @@ __device__ __forceinline__ Seeded seed_particle(const KernelArgs &a, const synth
     }
     const float I0 = fmaf(u24f(wa.w), D.i_max - D.i_min, D.i_min);
     const float z = fmaf(u24f(wb.x), D.z_max - D.z_min, D.z_min);
-    float gain = 1.0f;
-    if (D.sheet_sigma > 0.0f) gain = expf(-(z * z) / (2.0f * D.sheet_sigma * D.sheet_sigma));
+    const float gain = sheet_gain(D, z);
     P.sigma = 0.25f * d;
     P.amp = (I0 * gain) * (6.28318530717958647692f * P.sigma * P.sigma);  // Ieff * 2 pi sigma^2
     P.d = d;
     P.i0 = I0;
+    P.z = z;
     P.gain = gain;
     return P;
 }
@@ -215,8 +227,9 @@ __device__ __forceinline__ float4 frame_shape(float dx, float dy, float rho, flo
 // Gaussian change, clamped to the parameter's interval; aggregation
 // paragraph: a particle hidden from each image with probability hide_prob).
 // d_y = d when the d_y interval is [0, 0] (then one change for both axes).
+// gain2: the sheet factor in frame 2 (P.gain unless the particle moved in z).
 __device__ __forceinline__ void frame_shapes(const KernelArgs &a, const synthpix_pair_desc &D, uint32_t i,
-                                             const Seeded &P, float4 &s1, float4 &s2) {
+                                             const Seeded &P, float gain2, float4 &s1, float4 &s2) {
     const uint4 w2 = stream_words(a.keys, D.pair_id, i, kTagShapeA);
     const uint4 w3 = stream_words(a.keys, D.pair_id, i, kTagShapeB);
     const bool same_d = D.dy_min == 0.0f && D.dy_max == 0.0f;
@@ -230,7 +243,7 @@ __device__ __forceinline__ void frame_shapes(const KernelArgs &a, const synthpix
     const float rho2 = clampf(fmaf(D.jitter_rho, nr, rho), D.rho_min, D.rho_max);
     const float i2 = clampf(fmaf(D.jitter_i, ni, P.i0), D.i_min, D.i_max);
     s1 = frame_shape(P.d, dy, rho, P.i0 * P.gain, u24f(w2.x) < a.hide_prob);
-    s2 = frame_shape(dx2, dy2, rho2, i2 * P.gain, u24f(w2.y) < a.hide_prob);
+    s2 = frame_shape(dx2, dy2, rho2, i2 * gain2, u24f(w2.y) < a.hide_prob);
 }
 
 __device__ __forceinline__ Flow pair_flow(const KernelArgs &a, const synthpix_pair_desc &D) {
@@ -269,6 +282,52 @@ __device__ __forceinline__ void advect_split(const Flow &F, float dt, int n_subs
                                              float &gx, int32_t &jy, float &gy) {
     advect_split_with([&](int32_t ix, float fx, int32_t iy, float fy) { return velocity(F, ix, fx, iy, fy); }, dt,
                       n_substeps, integrator, jx, gx, jy, gy);
+}
+
+// The scalar grid w (same nodes as the flow) at a split position: the
+// bilinear weights of velocity().
+__device__ __forceinline__ float scalar_at(const Flow &F, const float *w, int32_t ix, float fx, int32_t iy, float fy) {
+    int32_t l, k;
+    float tx, ty;
+    grid_coord(ix, fx, F.gw, F.W, l, tx);
+    grid_coord(iy, fy, F.gh, F.H, k, ty);
+    const int32_t l0 = min(max(l, 0), F.gw - 1), l1 = min(max(l + 1, 0), F.gw - 1);
+    const int32_t k0 = min(max(k, 0), F.gh - 1), k1 = min(max(k + 1, 0), F.gh - 1);
+    const float a = __ldg(w + (size_t)k0 * F.gw + l0), b = __ldg(w + (size_t)k0 * F.gw + l1);
+    const float c = __ldg(w + (size_t)k1 * F.gw + l0), d = __ldg(w + (size_t)k1 * F.gw + l1);
+    const float t = fmaf(tx, b - a, a), u = fmaf(tx, d - c, c);
+    return fmaf(ty, u - t, t);
+}
+
+// advect_split with the out-of-plane position z moved by the scalar grid w
+// along the path: the same stages (and the same position arithmetic) as
+// advect_split_with, each also evaluating w.
+__device__ __forceinline__ void advect_split_z(const Flow &F, const float *w, float dt, int n_substeps, int integrator,
+                                               int32_t &jx, float &gx, int32_t &jy, float &gy, float &z) {
+    const float h = dt / (float)n_substeps;
+    const float hh = 0.5f * h, h6 = h / 6.0f;
+    for (int s = 0; s < n_substeps; ++s) {
+        const float2 k1 = velocity(F, jx, gx, jy, gy);
+        const float w1 = scalar_at(F, w, jx, gx, jy, gy);
+        if (integrator == SYNTHPIX_EULER) {
+            split_add(jx, gx, __fmul_rn(h, k1.x));
+            split_add(jy, gy, __fmul_rn(h, k1.y));
+            z = fmaf(h, w1, z);
+            continue;
+        }
+        const float x2 = fmaf(hh, k1.x, gx), y2 = fmaf(hh, k1.y, gy);
+        const float2 k2 = velocity(F, jx, x2, jy, y2);
+        const float w2 = scalar_at(F, w, jx, x2, jy, y2);
+        const float x3 = fmaf(hh, k2.x, gx), y3 = fmaf(hh, k2.y, gy);
+        const float2 k3 = velocity(F, jx, x3, jy, y3);
+        const float w3 = scalar_at(F, w, jx, x3, jy, y3);
+        const float x4 = fmaf(h, k3.x, gx), y4 = fmaf(h, k3.y, gy);
+        const float2 k4 = velocity(F, jx, x4, jy, y4);
+        const float w4 = scalar_at(F, w, jx, x4, jy, y4);
+        split_add(jx, gx, __fmul_rn(h6, (k1.x + k4.x) + 2.0f * (k2.x + k3.x)));
+        split_add(jy, gy, __fmul_rn(h6, (k1.y + k4.y) + 2.0f * (k2.y + k3.y)));
+        z = fmaf(h6, (w1 + w4) + 2.0f * (w2 + w3), z);
+    }
 }
 
 // A block of flow-grid nodes [gx0, gx0 + nw) x [gy0, gy0 + nh) staged in

@@ -135,10 +135,11 @@ struct ChunkCtx {
 // descriptor and plan in shared memory.  Ends with a barrier.
 __device__ __forceinline__ void load_chunk(const KernelArgs &a, ChunkCtx &c) {
     const int b = block_upper_find(a.n_pairs, (int64_t)blockIdx.x, [&](int m) { return (int64_t)a.plan[m].chunk_base; });
-    if (threadIdx.x < 8)
+    constexpr int kD = sizeof(synthpix_pair_desc) / 16, kP = sizeof(PairPlan) / 16;
+    if (threadIdx.x < kD)
         reinterpret_cast<int4 *>(&c.d)[threadIdx.x] = reinterpret_cast<const int4 *>(a.descs + b)[threadIdx.x];
-    else if (threadIdx.x < 12)
-        reinterpret_cast<int4 *>(&c.pl)[threadIdx.x - 8] = reinterpret_cast<const int4 *>(a.plan + b)[threadIdx.x - 8];
+    else if (threadIdx.x < kD + kP)
+        reinterpret_cast<int4 *>(&c.pl)[threadIdx.x - kD] = reinterpret_cast<const int4 *>(a.plan + b)[threadIdx.x - kD];
     __syncthreads();
     if (threadIdx.x == 0) {
         c.pair = b;
@@ -197,11 +198,22 @@ __global__ void __launch_bounds__(kPrepThreads, 5) k_seed_advect(KernelArgs a) {
             a.particles_out[3 * g + 2] = 4.0f * P.sigma;
             continue;
         }
+        // frame 2 here unless the tiled advection (k_advect) makes it
+        int32_t jx = P.ix, jy = P.iy;
+        float gx = P.fx, gy = P.fy, z2 = P.z;
+        if (!a.tiled) {
+            if (a.out_of_plane)
+                advect_split_z(F, a.flows + c.d.flow_offset + 2LL * c.d.flow_h * c.d.flow_w, a.dt, a.n_substeps,
+                               a.integrator, jx, gx, jy, gy, z2);
+            else
+                advect_split(F, a.dt, a.n_substeps, a.integrator, jx, gx, jy, gy);
+            a.pos1[g] = make_float4(gx, gy, __int_as_float(jx), __int_as_float(jy));
+        }
         // window half-extents 1.5 d (x) and 1.5 d_y (y) of each frame; < 0: hidden
         float r1x = 6.0f * P.sigma, r1y = r1x, r2x = r1x, r2y = r1x;
         if (a.ext) {
             float4 s1, s2;
-            frame_shapes(a, c.d, i, P, s1, s2);
+            frame_shapes(a, c.d, i, P, a.out_of_plane ? sheet_gain(c.d, z2) : P.gain, s1, s2);
             a.shape[g] = s1;
             a.shape[a.n_part + g] = s2;
             r1x = 6.0f * s1.x;
@@ -212,12 +224,7 @@ __global__ void __launch_bounds__(kPrepThreads, 5) k_seed_advect(KernelArgs a) {
         if (counting && r1x >= 0.0f)
             count_window(a, c, particle_window2(P.ix, P.fx, P.iy, P.fy, r1x, r1y, c.d.width, c.d.height), 0,
                          local ? hist : nullptr);
-        if (a.tiled) continue;  // frame 2 from k_advect
-        int32_t jx = P.ix, jy = P.iy;
-        float gx = P.fx, gy = P.fy;
-        advect_split(F, a.dt, a.n_substeps, a.integrator, jx, gx, jy, gy);
-        a.pos1[g] = make_float4(gx, gy, __int_as_float(jx), __int_as_float(jy));
-        if (counting && r2x >= 0.0f)
+        if (!a.tiled && counting && r2x >= 0.0f)
             count_window(a, c, particle_window2(jx, gx, jy, gy, r2x, r2y, c.d.width, c.d.height), 1,
                          local ? hist : nullptr);
     }

@@ -30,14 +30,15 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// descriptor (128 B), plan (64 B), blur taps (128 B) of a pair
+// descriptor, plan and blur taps (128 B) of a pair, in 16-byte copies
 __device__ __forceinline__ void stage_header(const KernelArgs &a, int pair, unsigned char *buf) {
+    constexpr int kD = kStageDesc / 16, kP = kStagePlan / 16, kH = kStageHeader / 16;
     const int t = threadIdx.x;
-    if (t < 20) {
+    if (t < kH) {
         const unsigned char *src;
-        if (t < 8) src = reinterpret_cast<const unsigned char *>(a.descs + pair) + 16 * t;
-        else if (t < 12) src = reinterpret_cast<const unsigned char *>(a.plan + pair) + 16 * (t - 8);
-        else src = reinterpret_cast<const unsigned char *>(a.blur_w + (int64_t)pair * kBlurStride) + 16 * (t - 12);
+        if (t < kD) src = reinterpret_cast<const unsigned char *>(a.descs + pair) + 16 * t;
+        else if (t < kP) src = reinterpret_cast<const unsigned char *>(a.plan + pair) + 16 * (t - kD);
+        else src = reinterpret_cast<const unsigned char *>(a.blur_w + (int64_t)pair * kBlurStride) + 16 * (t - kP);
         cp_async16(buf + 16 * t, src);
     }
 }
@@ -1226,8 +1227,8 @@ template <typename T, int NT, int RS>
 __device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo &it, unsigned char *buf,
                                              uint32_t cap, const Smem &s, uint32_t t2, ItemInfo &after) {
     const synthpix_pair_desc &D = *reinterpret_cast<const synthpix_pair_desc *>(buf);
-    const PairPlan &pl = *reinterpret_cast<const PairPlan *>(buf + 128);
-    const float *wtab = reinterpret_cast<const float *>(buf + 192);
+    const PairPlan &pl = *reinterpret_cast<const PairPlan *>(buf + kStageDesc);
+    const float *wtab = reinterpret_cast<const float *>(buf + kStagePlan);
     const Geo g = make_geo(D, pl, a.tile, it.tile, pl.halo);
     const bool fused = a.inter_dtype == SYNTHPIX_F32;
     const bool illum = fused ? illum_factors(g, D, s) : false;

@@ -378,3 +378,28 @@ def ablation_batch(size: int = 512, ppp: float = 0.06, d_min: float = 0.8, d_max
                     flows=flows, out_dtype="f32", quant_bits=0, n_substeps=4, dt=1.0,
                     description=f"{n_pairs} pairs {size}x{size}, ppp {ppp if ppp_min is None else (ppp_min, ppp)}, "
                                 f"d~U[{d_min},{d_max}], F={n_flows}, f32")
+
+
+def focus_batch(n_pairs: int = 64, seed: int = 7, size: int = 512, w_rms: float = 0.15,
+                sheet_shape: float = 2.0) -> Workload:
+    """The 512x512 u8 workload with the Remark's out-of-focus intensity and out-of-plane motion.
+
+    Sheet thickness dz0 = 0.5 (z~U[-1,1]) with shape factor sheet_shape; an
+    out-of-plane velocity grid w per pair: the u component of an independent
+    Fourier field, rescaled to RMS w_rms (z units per frame).
+    """
+    h = w = size
+    flows = [fourier_flow(h, w, h, w, rms=3.0, seed=7000 + b) for b in range(n_pairs)]
+    ws = []
+    for b in range(n_pairs):
+        g = fourier_flow(h, w, h, w, rms=1.0, seed=7500 + b)[..., 0].astype(np.float64)
+        ws.append((g * (w_rms / math.sqrt(np.mean(g * g)))).astype(np.float32))
+    pairs = [PairSpec(height=h, width=w, n_particles=n_particles_for(0.05, h, w), pair_id=b, flow_index=b,
+                      d_dist=0, d_min=1.0, d_max=4.0, illum_min=0.7, illum_max=1.0, noise_sigma=0.02,
+                      blur_sigma=0.7, sheet_sigma=0.5, sheet_model=1, sheet_shape=sheet_shape)
+             for b in range(n_pairs)]
+    return Workload(name=f"focus{n_pairs}_{size}", seed=seed, pairs=pairs, flows=flows, flows_w=ws,
+                    out_dtype="u8", quant_bits=8, n_substeps=4, dt=1.0,
+                    description=f"{n_pairs} pairs {size}x{size} ppp 0.05, d~U[1,4], Remark out-of-focus "
+                                f"(dz0 0.5, s {sheet_shape}), out-of-plane w rms {w_rms}, Fourier rms 3, "
+                                f"illum 0.7-1, noise 0.02, blur 0.7, 8-bit")

@@ -22,11 +22,11 @@ def test_library_exports_every_declared_symbol():
     L = B.lib()
     for name in _declared():
         assert hasattr(L, name), name
-    assert L.synthpix_version() == 2
+    assert L.synthpix_version() == 3
 
 
 def test_descriptor_sizes_match_header():
-    assert C.sizeof(B.PairDesc) == 128 and C.sizeof(B.BatchDesc) == 64
+    assert C.sizeof(B.PairDesc) == 160 and C.sizeof(B.BatchDesc) == 64
 
 
 def _packed():
