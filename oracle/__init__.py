@@ -98,6 +98,8 @@ def lib():
         L.oracle_render_pair.restype = C.c_int
         L.oracle_render_pair3.argtypes = [C.POINTER(OraclePair), fp, fp, dp, dp, up, dp, C.c_int32]
         L.oracle_render_pair3.restype = C.c_int
+        L.oracle_match_histogram.argtypes = [up, C.c_int64, C.c_int32, C.POINTER(C.c_uint64)]
+        L.oracle_match_histogram.restype = C.c_int
         L.oracle_sheet_gain.argtypes = [C.POINTER(OraclePair), C.c_double]
         L.oracle_sheet_gain.restype = C.c_double
         L.oracle_scalar_at.argtypes = [fp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double]
@@ -244,6 +246,16 @@ def epilogue(pair: OraclePair, frame: int, S: np.ndarray):
     lib().oracle_epilogue(C.byref(pair), frame, _ptr(S, C.c_double), _ptr(B, C.c_double),
                           _ptr(Q, C.c_uint32))
     return B, Q
+
+
+def match_histogram(codes: np.ndarray, n_codes: int, target) -> np.ndarray:
+    """Histogram specification of one quantised frame to target counts (a new array)."""
+    c = np.ascontiguousarray(codes, dtype=np.uint32).copy()
+    t = np.ascontiguousarray(target, dtype=np.uint64)
+    assert t.size == n_codes and int(c.max(initial=0)) < n_codes
+    if lib().oracle_match_histogram(_ptr(c, C.c_uint32), c.size, n_codes, t.ctypes.data_as(C.POINTER(C.c_uint64))):
+        raise MemoryError("oracle_match_histogram failed")
+    return c
 
 
 def sheet_gain(pair: OraclePair, z: float) -> float:

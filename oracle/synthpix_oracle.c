@@ -697,6 +697,42 @@ int oracle_render_pair3(const oracle_pair *p, const float *flow, const float *wg
 }
 
 /* ------------------------------------------------------------------------ */
+/* intensity-histogram matching of a quantised frame (R10)                  */
+/* ------------------------------------------------------------------------ */
+/*
+ * R10: the paper adjusts generated images to a user-specified intensity
+ * histogram (Section 2, end of "Mathematical model").  Reading: histogram
+ * specification on the quantised codes.  With the frame's code counts h_s
+ * (N pixels) and the target counts h_t (T in all), cumulative C_s, C_t, code
+ * c becomes the smallest t with C_t(t) / T >= C_s(c) / N, compared exactly as
+ * C_t(t) N >= C_s(c) T.  n_codes = M + 1.  codes: n pixels, rewritten in place.
+ */
+int oracle_match_histogram(uint32_t *codes, int64_t n, int32_t n_codes, const uint64_t *target)
+{
+    uint64_t *hs = (uint64_t *)calloc((size_t)n_codes, sizeof(uint64_t));
+    uint32_t *map = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n_codes);
+    if (!hs || !map) { free(hs); free(map); return -1; }
+    for (int64_t k = 0; k < n; ++k) hs[codes[k]] += 1;
+    uint64_t T = 0;
+    for (int32_t t = 0; t < n_codes; ++t) T += target[t];
+    uint64_t cs = 0;
+    for (int32_t c = 0; c < n_codes; ++c) {
+        cs += hs[c];
+        uint64_t ct = 0;
+        int32_t t = 0;
+        for (; t < n_codes; ++t) {
+            ct += target[t];
+            if ((unsigned __int128)ct * (uint64_t)n >= (unsigned __int128)cs * T) break;
+        }
+        map[c] = (uint32_t)(t < n_codes ? t : n_codes - 1);
+    }
+    for (int64_t k = 0; k < n; ++k) codes[k] = map[codes[k]];
+    free(hs);
+    free(map);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* forward with given particles, and its adjoint (gradients)                */
 /* ------------------------------------------------------------------------ */
 /*

@@ -89,3 +89,54 @@ def test_render_zero_w_equals_render_without_and_large_w_empties_frame2():
     far = oracle.render_pair(pr, flow, wgrid=np.full((48, 64), 5.0, np.float32))  # 5 sheet widths per frame
     assert np.allclose(far["S"][0], base["S"][0], rtol=0, atol=1e-13)  # general vs separable splat rounding
     assert far["S"][1].max() < 1e-20 * base["S"][1].max()
+
+
+# ----------------------------------------------------------------------------
+# intensity-histogram matching of quantised frames
+# ----------------------------------------------------------------------------
+
+def _match_fractions(codes, n_codes, target):
+    """Brute force with exact rationals: code c -> min t with C_t(t)/T >= C_s(c)/N."""
+    from fractions import Fraction
+    N, T = codes.size, int(sum(int(x) for x in target))
+    hs = np.bincount(codes, minlength=n_codes)
+    cs, out = 0, {}
+    for c in range(n_codes):
+        cs += int(hs[c])
+        p = Fraction(cs, N)
+        ct = 0
+        for t in range(n_codes):
+            ct += int(target[t])
+            if Fraction(ct, T) >= p:
+                break
+        out[c] = t
+    return np.array([out[c] for c in codes], dtype=np.uint32)
+
+
+@pytest.mark.parametrize("n_codes,seed", [(16, 0), (256, 1), (64, 2)])
+def test_histogram_matching_equals_exact_quantile_mapping(n_codes, seed):
+    rng = np.random.default_rng(seed)
+    codes = np.minimum(rng.gamma(2.0, n_codes / 8, size=3000).astype(np.int64), n_codes - 1).astype(np.uint32)
+    target = rng.integers(0, 50, size=n_codes).astype(np.uint64)
+    target[rng.integers(0, n_codes)] += 1  # non-empty
+    got = oracle.match_histogram(codes, n_codes, target)
+    assert np.array_equal(got, _match_fractions(codes, n_codes, target))
+
+
+def test_histogram_matching_properties():
+    rng = np.random.default_rng(5)
+    n_codes = 256
+    codes = rng.integers(0, 200, size=5000).astype(np.uint32)
+    # identity when the target is the frame's own histogram
+    own = np.bincount(codes, minlength=n_codes).astype(np.uint64)
+    assert np.array_equal(oracle.match_histogram(codes, n_codes, own), codes)
+    # monotone mapping, and the output follows the target's CDF within one source bin
+    target = np.exp(-np.arange(n_codes) / 30.0) * 1000
+    target = target.astype(np.uint64) + 1
+    out = oracle.match_histogram(codes, n_codes, target)
+    order = np.argsort(codes, kind="stable")
+    assert np.all(np.diff(out[order].astype(np.int64)) >= 0)
+    cdf_out = np.cumsum(np.bincount(out, minlength=n_codes)) / codes.size
+    cdf_t = np.cumsum(target) / target.sum()
+    max_bin = np.bincount(codes).max() / codes.size
+    assert np.all(cdf_out >= cdf_t - max_bin - 1e-12)
