@@ -673,11 +673,14 @@ def run_other(args):
         # ahead) or one set reused; device time per batch on the render stream
         from paper_2512_09664_b300 import sampler as S
         res = {}
-        for name, F, R in (("F64_R1", 64, 1), ("F1_R1", 1, 1), ("F64_reused", 64, 10 ** 9)):
+        import numpy as np
+        hist = ((np.exp(-np.arange(256) / 40.0) * 1e5).astype(np.int64) + 1).tolist()
+        for name, F, R, th in (("F64_R1", 64, 1, None), ("F1_R1", 1, 1, None), ("F64_reused", 64, 10 ** 9, None),
+                               ("F1_R1_histogram_matched", 1, 1, hist)):
             cfg = {"image_shape": [512, 512], "batch_size": 64, "flows_per_batch": F, "batches_per_flow": R,
                    "seed": 1, "seeding_density": 0.05, "diameter": [1.0, 4.0], "illumination": [0.7, 1.0],
                    "noise_sigma": 0.02, "blur_sigma": 0.7, "output": "u8", "bits": 8,
-                   "flow": {"kind": "fourier", "rms": 3.0}}
+                   "flow": {"kind": "fourier", "rms": 3.0}, "target_histogram": th}
             smp = S.make(cfg)
             for _ in range(args.warmup):
                 next(smp)

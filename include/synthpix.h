@@ -369,6 +369,30 @@ int synthpix_fourier_flows(int32_t n_flows, int32_t n_modes, int32_t flow_h, int
                            int32_t width, const double *modes, float rms, float *flows, void *workspace,
                            size_t workspace_bytes, void *stream);
 
+/*
+ * Intensity-histogram matching of rendered frames (Section 2: generated
+ * images are optionally adjusted to a user-specified intensity histogram).
+ * Acts in place on quantised outputs (batch->out_dtype U8 or U16 with
+ * quant_bits b, n_codes = 2^b codes); every frame of the n_pairs pairs (two
+ * per pair, at image_offset and image_offset + H W, as rendered) is matched
+ * to the same target by histogram specification: with the frame's code
+ * counts (N pixels) and the target counts (T in all, 0 < T < 2^64), code c
+ * becomes the smallest t with C_t(t) N >= C_s(c) T (cumulative counts,
+ * compared exactly); the mapping is monotone.
+ *   images     device, the render's output buffer (element type out_dtype);
+ *   target     device, 8-byte aligned, uint64 [n_codes] counts per code;
+ *   workspace  device, 256-byte aligned, at least
+ *              synthpix_match_histogram_workspace_bytes(...) bytes.
+ * SYNTHPIX_EUNSUPPORTED for float outputs; asynchronous on stream (five
+ * launches; the frame table is copied from host memory with
+ * cudaMemcpyAsync).
+ */
+size_t synthpix_match_histogram_workspace_bytes(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
+                                                int32_t n_pairs);
+int synthpix_match_histogram(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs, int32_t n_pairs,
+                             void *images, const uint64_t *target, void *workspace, size_t workspace_bytes,
+                             void *stream);
+
 /* SYNTHPIX_ABI_VERSION of the loaded library. */
 int synthpix_version(void);
 

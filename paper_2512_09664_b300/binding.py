@@ -103,6 +103,11 @@ def lib():
         L.synthpix_fourier_flows.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                              vp, C.c_float, vp, vp, sz, vp]
         L.synthpix_fourier_flows.restype = C.c_int
+        L.synthpix_match_histogram_workspace_bytes.argtypes = [C.POINTER(BatchDesc), C.POINTER(PairDesc), C.c_int32]
+        L.synthpix_match_histogram_workspace_bytes.restype = sz
+        L.synthpix_match_histogram.argtypes = [C.POINTER(BatchDesc), C.POINTER(PairDesc), C.c_int32, vp, vp, vp, sz,
+                                               vp]
+        L.synthpix_match_histogram.restype = C.c_int
         L.synthpix_last_error.argtypes = []
         L.synthpix_last_error.restype = C.c_char_p
         L.synthpix_version.argtypes = []
@@ -262,6 +267,22 @@ def fourier_flows_workspace_bytes(n_flows: int, n_modes: int, flow_h: int, flow_
     if n == 0:
         raise SynthpixError(EINVAL, last_error())
     return n
+
+
+def match_histogram(pk: Packed, images_dev, target_dev, workspace_dev=None, stream=None):
+    """synthpix_match_histogram on a packed batch's rendered images (in place); returns the workspace."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    if workspace_dev is None:
+        n = lib().synthpix_match_histogram_workspace_bytes(C.byref(pk.batch), pk.pairs, pk.n_pairs)
+        if n == 0 and pk.n_pairs > 0:
+            raise SynthpixError(EINVAL, last_error())
+        workspace_dev = torch.empty(max(n, 256), dtype=torch.uint8, device=images_dev.device)
+    rc = lib().synthpix_match_histogram(C.byref(pk.batch), pk.pairs, pk.n_pairs, C.c_void_p(images_dev.data_ptr()),
+                                        C.c_void_p(target_dev.data_ptr()), C.c_void_p(workspace_dev.data_ptr()),
+                                        workspace_dev.numel(), C.c_void_p(st.cuda_stream))
+    _check(rc)
+    return workspace_dev
 
 
 class Renderer:

@@ -35,6 +35,8 @@ Configuration keys (all optional except image_shape):
     jitter: {diameter: 0, intensity: 0, rho: 0}
     output: f32 | f16 | bf16 | u8 | u16     bits: 8           intermediate: f32 | f16 | bf16
     integrator: rk4 | euler        substeps: 4                dt: 1.0
+    sheet_model: gaussian | remark  sheet_shape: 2.0 (the Remark's out-of-focus form)
+    target_histogram: [counts per code]  (quantised outputs: frames matched to it after each render)
     flow: {kind: fourier, rms: 3.0, modes: 64, min_wavelength: 16.0, grid: [gh, gw]}
           {kind: uniform, u: 1.0, v: 0.0} | {kind: lamb_oseen, gamma: 200.0, core: 20.0}
           or a callable passed to make(): provider(set_index, n_flows, (gh, gw)) -> [F, gh, gw, 2]
@@ -68,6 +70,7 @@ DEFAULTS = {
     "diameter_y": [0.0, 0.0], "rho": [0.0, 0.0], "hide_prob": 0.0,
     "jitter": {"diameter": 0.0, "intensity": 0.0, "rho": 0.0},
     "output": "f32", "bits": 8, "intermediate": "f32", "integrator": "rk4", "substeps": 4, "dt": 1.0,
+    "sheet_model": "gaussian", "sheet_shape": 0.0, "target_histogram": None,
     "flow": {"kind": "fourier", "rms": 3.0, "modes": 64, "min_wavelength": 16.0},
 }
 
@@ -172,7 +175,8 @@ def pair_spec(cfg: dict, density: float, pair_id: int, flow_index: int) -> W.Pai
         z_max=cfg["out_of_plane"][1], sheet_sigma=cfg["sheet_sigma"], illum_min=cfg["illumination"][0],
         illum_max=cfg["illumination"][1], noise_sigma=cfg["noise_sigma"], blur_sigma=cfg["blur_sigma"],
         dy_min=cfg["diameter_y"][0], dy_max=cfg["diameter_y"][1], rho_min=cfg["rho"][0], rho_max=cfg["rho"][1],
-        jitter_d=jit.get("diameter", 0.0), jitter_i=jit.get("intensity", 0.0), jitter_rho=jit.get("rho", 0.0))
+        jitter_d=jit.get("diameter", 0.0), jitter_i=jit.get("intensity", 0.0), jitter_rho=jit.get("rho", 0.0),
+        sheet_model=1 if cfg["sheet_model"] == "remark" else 0, sheet_shape=cfg["sheet_shape"])
 
 
 def batch_specs(cfg: dict, densities, batch_index: int) -> list:
@@ -270,6 +274,15 @@ class Sampler:
             self.flow_ws = torch.empty(fws, dtype=torch.uint8, device=self.device)
         self._flow_index_host = np.array([b * self.F // self.B for b in range(self.B)])
         self.flow_index = torch.from_numpy(self._flow_index_host).to(self.device)
+        self.target = None
+        if cfg["target_histogram"] is not None:
+            if self.out_dtype not in ("u8", "u16"):
+                raise ValueError("target_histogram needs a quantised output (u8 / u16)")
+            t = np.asarray(cfg["target_histogram"], dtype=np.uint64)
+            if t.size != 1 << bits or t.sum() == 0:
+                raise ValueError(f"target_histogram needs {1 << bits} counts with a positive total")
+            self.target = torch.from_numpy(t).to(self.device)
+            self.match_ws = None
         self.k = 0
         self._generate(0)
 
@@ -350,6 +363,9 @@ class Sampler:
             C.c_void_p(out.data_ptr()), C.c_void_p(self.workspace.data_ptr()), self.workspace.numel(),
             C.c_void_p(main.cuda_stream))
         B._check(rc)
+        if self.target is not None:  # frames matched to the target histogram, in place
+            pk = B.Packed(self.batch, self.pairs, self.B, None, [], 0, self.out_dtype, [])
+            self.match_ws = B.match_histogram(pk, out, self.target, self.match_ws, stream=main)
         self.flow_free[j].record(main)
         self.k += 1
         if (k + 1) // self.R != s:  # the next batch starts a new set: generate it while this one renders

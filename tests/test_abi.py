@@ -155,3 +155,17 @@ def test_given_particles_and_adjoint_reject_shape_variation():
     assert L.synthpix_render_backward(C.byref(pk.batch), pk.pairs, None, pk.n_pairs, None, FAKE, FAKE, FAKE,
                                       None, FAKE, 1 << 30, None) == B.EUNSUPPORTED
     assert "round particles" in B.last_error()
+
+
+def test_histogram_matching_validation():
+    pk = _packed()
+    L = B.lib()
+    assert L.synthpix_match_histogram_workspace_bytes(C.byref(pk.batch), pk.pairs, pk.n_pairs) > 0
+    assert L.synthpix_match_histogram(C.byref(pk.batch), pk.pairs, pk.n_pairs, FAKE, FAKE, FAKE, 16, None) == \
+        B.EWORKSPACE
+    assert L.synthpix_match_histogram(C.byref(pk.batch), pk.pairs, pk.n_pairs, None, FAKE, FAKE, 1 << 30, None) == \
+        B.EINVAL
+    pk.batch.out_dtype, pk.batch.quant_bits = B.DTYPE_CODE["f32"], 0
+    assert L.synthpix_match_histogram(C.byref(pk.batch), pk.pairs, pk.n_pairs, FAKE, FAKE, FAKE, 1 << 30, None) == \
+        B.EUNSUPPORTED
+    assert L.synthpix_match_histogram_workspace_bytes(C.byref(pk.batch), pk.pairs, pk.n_pairs) == 0

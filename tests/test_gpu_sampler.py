@@ -101,3 +101,20 @@ def test_sampler_flow_providers():
     b1 = next(smp)
     b2 = next(smp)
     assert float(b2.flows[0, 0, 0, 0]) == 0.5 and calls[:2] == [0, 1]
+
+
+def test_sampler_target_histogram_and_remark_sheet():
+    import oracle
+    from paper_2512_09664_b300 import sampler as S
+    target = (np.exp(-np.arange(256) / 40.0) * 1e5).astype(np.uint64) + 1
+    cfg = _cfg(sheet_model="remark", sheet_shape=2.0, sheet_sigma=0.5, target_histogram=target.tolist())
+    smp = S.make(cfg)
+    batch = next(smp)
+    got = batch.images.cpu().numpy()
+    wl = smp.workload(0)
+    assert wl.pairs[0].sheet_model == 1
+    direct = gpu_render(wl)
+    for b in range(4):
+        for f in range(2):
+            want = oracle.match_histogram(direct[b][f].astype(np.uint32).ravel(), 256, target)
+            assert np.array_equal(got[b, f].astype(np.uint32).ravel(), want)
