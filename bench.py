@@ -69,12 +69,38 @@ def parse():
     return ap.parse_args()
 
 
+# ----------------------------------------------------------------------------
+# replicas over ranks: each rank renders its own pairs (disjoint pair ids, so
+# the outputs are those of one large batch); the step time is the maximum
+# over ranks and the value counts the pairs of every rank
+# ----------------------------------------------------------------------------
+
+def rank_pair_ids(rank: int, n_pairs: int):
+    """Pair ids rank `rank` renders: [rank * n_pairs, (rank + 1) * n_pairs)."""
+    return [rank * n_pairs + b for b in range(n_pairs)]
+
+
+def max_over_ranks(x: float, dist, device="cpu") -> float:
+    """The maximum of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_pairs_per_s(world: int, pairs_per_rank: int, steps: int, total_ms: float) -> float:
+    """Whole-job throughput: the pairs of all ranks over the slowest rank's time."""
+    return world * pairs_per_rank * steps / (total_ms / 1e3)
+
+
 def workload(rank: int = 0, n_pairs: int = N_PAIRS):
     from paper_2512_09664_b300 import workloads as W
     wl = W.batch_512_u8(n_pairs=n_pairs, seed=1)
     if rank:  # weak scaling: every rank renders its own pairs
-        for p in wl.pairs:
-            p.pair_id += rank * n_pairs
+        for p, pid in zip(wl.pairs, rank_pair_ids(rank, n_pairs)):
+            p.pair_id = pid
     return wl
 
 
@@ -326,11 +352,8 @@ def run_ours(args, rank, world, dist):
     torch.cuda.synchronize()
     stage_ms = {name: sum(ev[i].elapsed_time(ev[i + 1]) for ev in staged) / n_staged
                 for i, name in enumerate(STAGES)}
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * wl.n_pairs * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(total_ms, dist, dev)
+    value = aggregate_pairs_per_s(world, wl.n_pairs, args.steps, total_ms)
     ms_per_step = total_ms / args.steps
     if args.quick:
         if rank == 0:
