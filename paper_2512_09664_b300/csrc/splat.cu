@@ -537,15 +537,15 @@ __device__ __forceinline__ void splat_general_sep(const RecordG &r, int32_t j0, 
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const float isx = 1.0f / r.sx, isy = 1.0f / r.sy;
-    const float ux = __fsub_rn((float)(j0 - r.ix), r.fx), vy = __fsub_rn((float)(i0 - r.iy), r.fy);
     const int npx = nx * ny;
     const float invn = __frcp_rn((float)nx);
+    // an edge's offset from the centre: (edge - integer part) - fraction, one rounding, so the
+    // values do not depend on where the tile clips the window
     if (nx + ny + 2 <= 32) {
         const bool isx_lane = lane <= nx;
         const int e = isx_lane ? lane : lane - (nx + 1);
-        const float ev = lane <= nx + ny + 1
-                             ? edge_value_tab(__fadd_rn(isx_lane ? ux : vy, (float)e), isx_lane ? isx : isy, tab)
-                             : 0.0f;
+        const float dd = isx_lane ? __fsub_rn((float)(j0 + e - r.ix), r.fx) : __fsub_rn((float)(i0 + e - r.iy), r.fy);
+        const float ev = lane <= nx + ny + 1 ? edge_value_tab(dd, isx_lane ? isx : isy, tab) : 0.0f;
         float m = edge_mass(ev, __shfl_down_sync(FULL, ev, 1));
         if (!isx_lane) m = __fmul_rn(m, amps);
         for (int b = 0; b < npx; b += 32) {
@@ -558,9 +558,11 @@ __device__ __forceinline__ void splat_general_sep(const RecordG &r, int32_t j0, 
     }
     for (int p = lane; p < npx; p += 32) {
         const int rr = small_div(p, invn), cc = p - rr * nx;
-        const float u = __fadd_rn(ux, (float)cc), v = __fadd_rn(vy, (float)rr);
-        const float mx = edge_mass(edge_value_tab(u, isx, tab), edge_value_tab(__fadd_rn(u, 1.0f), isx, tab));
-        const float my = edge_mass(edge_value_tab(v, isy, tab), edge_value_tab(__fadd_rn(v, 1.0f), isy, tab));
+        const int jc = j0 + cc - r.ix, ir = i0 + rr - r.iy;
+        const float mx = edge_mass(edge_value_tab(__fsub_rn((float)jc, r.fx), isx, tab),
+                                   edge_value_tab(__fsub_rn((float)(jc + 1), r.fx), isx, tab));
+        const float my = edge_mass(edge_value_tab(__fsub_rn((float)ir, r.fy), isy, tab),
+                                   edge_value_tab(__fsub_rn((float)(ir + 1), r.fy), isy, tab));
         add_contrib<CHECKED>(w0 + rr * acc.P + cc, acc, mx, __fmul_rn(my, amps));
     }
 }
@@ -582,7 +584,6 @@ __device__ __forceinline__ void splat_general_corr(const RecordG &r, int32_t j0,
     const float c = sqrtf(1.0f - r.rho * r.rho);
     const float isx = 1.0f / r.sx, is = 1.0f / (r.sy * c), k = r.rho * r.sy * isx;
     constexpr float h = 1.0f / (float)M;
-    const float ux = __fsub_rn((float)(j0 - r.ix), r.fx), vy = __fsub_rn((float)(i0 - r.iy), r.fy);
     const float wscale = 0.5f * h * isx * 0.39894228040143267794f * amps;  // h/2, 1/(sqrt(2 pi) sigma_x), units
     // this lane's nodes: offsets within the pixel and weights (same for every column)
     float du[L], wq[L];
@@ -597,23 +598,27 @@ __device__ __forceinline__ void splat_general_corr(const RecordG &r, int32_t j0,
     for (int c0 = 0; c0 < nx; c0 += CPP) {
         const int col = c0 + gc;
         const bool live = col < nx;
-        const float ul = __fadd_rn(ux, (float)col);
-        float wn[L], dv[L], ev[L];
+        // offsets from the centre formed from exact integers (one rounding each), so the
+        // values do not depend on where the tile clips the window
+        const float ul = __fsub_rn((float)(j0 + col - r.ix), r.fx);  // the column's left edge
+        const float fy = r.fy;
+        float wn[L], mu[L], ev[L];
 #pragma unroll
         for (int t = 0; t < L; ++t) {
             const float u = __fadd_rn(ul, du[t]);
             const float tt = u * isx;
             wn[t] = live ? wq[t] * __expf(-0.5f * tt * tt) * wscale : 0.0f;
-            dv[t] = __fsub_rn(vy, k * u);  // top edge of the window minus the conditional mean
-            ev[t] = edge_value_tab(dv[t], is, tab);
+            mu[t] = k * u;  // conditional mean of y at this node
+            ev[t] = edge_value_tab(__fsub_rn(__fsub_rn((float)(i0 - r.iy), fy), mu[t]), is, tab);
         }
         uint32_t *wc = w0 + col;
 #pragma unroll 1
         for (int rr = 0; rr < ny; ++rr) {
             float v = 0.0f;
+            const float ye = __fsub_rn((float)(i0 + rr + 1 - r.iy), fy);  // the row's lower edge
 #pragma unroll
             for (int t = 0; t < L; ++t) {
-                const float en = edge_value_tab(__fadd_rn(dv[t], (float)(rr + 1)), is, tab);
+                const float en = edge_value_tab(__fsub_rn(ye, mu[t]), is, tab);
                 v = fmaf(wn[t], edge_mass(ev[t], en), v);
                 ev[t] = en;
             }

@@ -124,3 +124,37 @@ def test_render_is_independent_of_tile_and_batch():
         assert all(np.array_equal(a, b) for a, b in zip(g, ref))
     one = gpu_render(wl.subset([1]), tile=64)[0]
     assert np.array_equal(one, ref[1])
+
+
+def test_general_dense_overlap_and_carries():
+    # general shapes with sums above 64 i_max: the checked adds and carries of the general splat
+    p = _spec(32, 32, 3000, d_min=8.0, d_max=10.0, dy_min=6.0, dy_max=12.0, rho_min=-0.5, rho_max=0.5,
+              sheet_sigma=0.0)
+    wl = _wl([p], [W.zero_flow(32, 32)])
+    ref = oracle_render(wl)
+    assert ref[0]["S"].max() > 64.0
+    outs = [gpu_render(wl, tile=t) for t in (16, 32, 128)]
+    st = compare(wl, outs[0], ref)
+    print("general carries", st, "max S", float(ref[0]["S"].max()))
+    assert all(np.array_equal(outs[0][0], o[0]) for o in outs[1:])
+
+
+def test_general_wide_windows_both_paths():
+    # windows wider than the lanes' edge budget (separable fallback) and many
+    # quadrature columns (correlated), large and thin particles mixed
+    for rho in ((0.0, 0.0), (-0.9, 0.9)):
+        p = _spec(96, 120, 120, d_min=2.0, d_max=14.0, dy_min=0.6, dy_max=20.0, rho_min=rho[0], rho_max=rho[1])
+        wl = _wl([p], [W.fourier_flow(96, 120, 96, 120, rms=2.0, seed=5)])
+        st = compare(wl, gpu_render(wl, tile=32), oracle_render(wl))
+        print("wide", rho, st)
+        assert st["max_abs"] < 4e-6
+
+
+def test_general_batch_with_empty_and_tiny_pairs():
+    flows = [W.fourier_flow(40, 56, 40, 56, rms=1.5, seed=6), W.fourier_flow(9, 7, 9, 7, rms=1.0, seed=7)]
+    pairs = [_spec(40, 56, 0, dy_min=1.0, dy_max=3.0, rho_min=0.2, rho_max=0.2),
+             _spec(9, 7, 5, pair_id=1, flow_index=1, dy_min=1.0, dy_max=3.0, rho_min=-0.3, rho_max=0.3),
+             _spec(40, 56, 90, pair_id=2, dy_min=1.0, dy_max=3.0, rho_min=-0.3, rho_max=0.3)]
+    wl = _wl(pairs, flows, hide_prob=0.2)
+    for tile in (16, 64):
+        compare(wl, gpu_render(wl, tile=tile), oracle_render(wl))
