@@ -719,9 +719,51 @@ def run_other(args):
                          "batches_per_flow": R if R < 10 ** 9 else "all"}
             del smp
             torch.cuda.empty_cache()
+        # the two kernels the sampler adds, timed alone: histogram matching of a
+        # rendered 64 x 512^2 u8 batch (HBM: codes read twice, written once) and
+        # 64 Fourier fields of 512^2 with 64 modes (FP32: a product and three FMAs,
+        # 7 flops, per node and mode)
+        from paper_2512_09664_b300 import binding as Bn
+        peaks, peak_kind = measured_peaks()
+        wlh = W.batch_512_u8(n_pairs=64, seed=1)
+        r = Renderer(wlh)
+        r.render()
+        tgt = torch.tensor(hist, dtype=torch.int64, device="cuda")
+        ws = Bn.match_histogram(r.pk, r.images, tgt)
+        n = max(args.steps, 10)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n):
+            Bn.match_histogram(r.pk, r.images, tgt, ws)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        h_ms = e0.elapsed_time(e1) / n
+        h_bytes = 3 * r.images.numel()
+        modes = torch.from_numpy(np.stack([W.fourier_modes(9000 + f, 512, 512) for f in range(64)])).cuda()
+        fl = torch.empty((64, 512, 512, 2), dtype=torch.float32, device="cuda")
+        fws = torch.empty(Bn.fourier_flows_workspace_bytes(64, 64, 512, 512), dtype=torch.uint8, device="cuda")
+        Bn.fourier_flows(modes, 512, 512, 512, 512, 3.0, fl, fws)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(n):
+            Bn.fourier_flows(modes, 512, 512, 512, 512, 3.0, fl, fws)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        f_ms = e0.elapsed_time(e1) / n
+        f_flop = 64 * 512 * 512 * 64 * 7.0
+        fp32_peak = SM_COUNT * FP32_LANES_PER_SM * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 * 2 / 1e12
         line.update({"config": "streaming sampler, 64 pairs 512x512 u8 per batch (the headline recipe), "
                                "Fourier flows rms 3 generated on the device", "paths": res,
-                     "value": res["F64_R1"]["value"]})
+                     "value": res["F64_R1"]["value"],
+                     "histogram_matching": {"ms_per_batch": h_ms, "roofline": {
+                         "bound": "hbm", "achieved": h_bytes / (h_ms / 1e3) / 1e9, "peak": float(peaks["hbm_gbs"]),
+                         "unit": "GB/s", "frac": h_bytes / (h_ms / 1e3) / 1e9 / float(peaks["hbm_gbs"]),
+                         "algorithmic_bytes": h_bytes, "peak_source": peak_kind}},
+                     "flow_generation_64x512": {"ms": f_ms, "roofline": {
+                         "bound": "alu", "achieved": f_flop / (f_ms / 1e3) / 1e12, "peak": fp32_peak,
+                         "unit": "TFLOP/s (FP32)", "frac": f_flop / (f_ms / 1e3) / 1e12 / fp32_peak,
+                         "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 flops x max clock"}}})
     else:  # large_mixed
         wl = W.large_mixed_batch()
         res = {}

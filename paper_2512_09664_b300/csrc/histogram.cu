@@ -106,29 +106,82 @@ __global__ void k_hist_prep(HistArgs h) {
         h.hist[k] = 0u;
 }
 
+// A chunk's element range [e0, e1) of the images split into a scalar head
+// [e0, a0), 16-byte vectors [a0, a1) and a scalar tail [a1, e1) (all scalar
+// when the images are not 16-byte aligned).
+template <typename T>
+__device__ __forceinline__ void vector_span(const void *img, int64_t e0, int64_t e1, int64_t &a0, int64_t &a1) {
+    constexpr int64_t V = 16 / sizeof(T);
+    if ((reinterpret_cast<uintptr_t>(img) & 15) != 0) {
+        a0 = a1 = e1;
+        return;
+    }
+    a0 = min(e1, (e0 + V - 1) / V * V);
+    a1 = max(a0, e1 / V * V);
+}
+
+template <typename T>
+__device__ __forceinline__ uint32_t lane_code(const uint4 &x, int j) {
+    const uint32_t w = j < 16 / (int)sizeof(T) / 4 ? x.x : j < 2 * (16 / (int)sizeof(T) / 4) ? x.y
+                     : j < 3 * (16 / (int)sizeof(T) / 4) ? x.z : x.w;
+    constexpr int per = 4 / (int)sizeof(T);
+    return (w >> (8 * sizeof(T) * (j % per))) & (sizeof(T) == 1 ? 0xFFu : 0xFFFFu);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kHistThreads) k_hist_count(HistArgs h, const T *__restrict__ img) {
     __shared__ uint32_t s_h[kSharedCodesMax];
+    constexpr int V = 16 / sizeof(T);
     const int64_t q = blockIdx.x;
     const int f = frame_of_chunk(h, q);
     const Frame fr = h.frames[f];
     const int64_t p0 = (q - fr.chunk0) * kChunkPx, p1 = min(p0 + kChunkPx, fr.npx);
-    const T *src = img + fr.offset;
+    const int64_t e0 = fr.offset + p0, e1 = fr.offset + p1;
     uint32_t *gh = h.hist + (size_t)f * h.n_codes;
     const bool local = h.n_codes <= kSharedCodesMax;
+    // one copy of the counts per warp when they fit (frames are mostly background, so a
+    // few codes take most pixels: private copies spread those atomics)
+    constexpr int kWarps = kHistThreads / 32;
+    const int copies = h.n_codes * kWarps <= kSharedCodesMax ? kWarps : 1;
+    uint32_t *mine = s_h + (copies > 1 ? (threadIdx.x >> 5) * h.n_codes : 0);
+    const uint32_t cmax = (uint32_t)(h.n_codes - 1);
     if (local) {
-        for (int c = threadIdx.x; c < h.n_codes; c += kHistThreads) s_h[c] = 0u;
+        for (int c = threadIdx.x; c < h.n_codes * copies; c += kHistThreads) s_h[c] = 0u;
         __syncthreads();
     }
-    for (int64_t p = p0 + threadIdx.x; p < p1; p += kHistThreads) {
-        const uint32_t c = min((uint32_t)src[p], (uint32_t)(h.n_codes - 1));
-        if (local) atomicAdd(s_h + c, 1u);
+    auto count = [&](uint32_t c) {
+        c = min(c, cmax);
+        if (local) atomicAdd(mine + c, 1u);
         else atomicAdd(gh + c, 1u);
+    };
+    int64_t a0, a1;
+    vector_span<T>(img, e0, e1, a0, a1);
+    for (int64_t e = e0 + threadIdx.x; e < a0; e += kHistThreads) count((uint32_t)img[e]);
+    for (int64_t e = a1 + threadIdx.x; e < e1; e += kHistThreads) count((uint32_t)img[e]);
+    const uint4 *vec = reinterpret_cast<const uint4 *>(img + a0);
+    const int64_t nv = (a1 - a0) / V;
+    constexpr int kU = 4;  // vectors loaded before they are counted (loads in flight)
+    for (int64_t k0 = threadIdx.x; k0 < nv; k0 += kU * kHistThreads) {
+        uint4 x[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int64_t k = k0 + (int64_t)u * kHistThreads;
+            x[u] = k < nv ? vec[k] : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            if (k0 + (int64_t)u * kHistThreads >= nv) break;
+#pragma unroll
+            for (int j = 0; j < V; ++j) count(lane_code<T>(x[u], j));
+        }
     }
     if (local) {
         __syncthreads();
-        for (int c = threadIdx.x; c < h.n_codes; c += kHistThreads)
-            if (s_h[c]) atomicAdd(gh + c, s_h[c]);
+        for (int c = threadIdx.x; c < h.n_codes; c += kHistThreads) {
+            uint32_t n = 0;
+            for (int w = 0; w < copies; ++w) n += s_h[w * h.n_codes + c];
+            if (n) atomicAdd(gh + c, n);
+        }
     }
 }
 
@@ -185,15 +238,36 @@ __global__ void __launch_bounds__(1024) k_hist_map(HistArgs h) {
 
 template <typename T>
 __global__ void __launch_bounds__(kHistThreads) k_hist_apply(HistArgs h, T *__restrict__ img) {
+    __shared__ uint16_t s_lut[kSharedCodesMax];
+    constexpr int V = 16 / sizeof(T);
     const int64_t q = blockIdx.x;
     const int f = frame_of_chunk(h, q);
     const Frame fr = h.frames[f];
     const int64_t p0 = (q - fr.chunk0) * kChunkPx, p1 = min(p0 + kChunkPx, fr.npx);
-    T *dst = img + fr.offset;
-    const uint16_t *lut = h.lut + (size_t)f * h.n_codes;
-    for (int64_t p = p0 + threadIdx.x; p < p1; p += kHistThreads) {
-        const uint32_t c = min((uint32_t)dst[p], (uint32_t)(h.n_codes - 1));
-        dst[p] = (T)lut[c];
+    const int64_t e0 = fr.offset + p0, e1 = fr.offset + p1;
+    const uint16_t *glut = h.lut + (size_t)f * h.n_codes;
+    const bool local = h.n_codes <= kSharedCodesMax;  // the frame's map staged in shared memory
+    if (local) {
+        for (int c = threadIdx.x; c < h.n_codes; c += kHistThreads) s_lut[c] = glut[c];
+        __syncthreads();
+    }
+    const uint32_t cmax = (uint32_t)(h.n_codes - 1);
+    auto map = [&](uint32_t c) -> uint32_t {
+        c = min(c, cmax);
+        return local ? s_lut[c] : glut[c];
+    };
+    int64_t a0, a1;
+    vector_span<T>(img, e0, e1, a0, a1);
+    for (int64_t e = e0 + threadIdx.x; e < a0; e += kHistThreads) img[e] = (T)map((uint32_t)img[e]);
+    for (int64_t e = a1 + threadIdx.x; e < e1; e += kHistThreads) img[e] = (T)map((uint32_t)img[e]);
+    uint4 *vec = reinterpret_cast<uint4 *>(img + a0);
+    for (int64_t k = threadIdx.x; k < (a1 - a0) / V; k += kHistThreads) {
+        const uint4 x = vec[k];
+        uint32_t o[4] = {0u, 0u, 0u, 0u};
+        constexpr int per = 4 / (int)sizeof(T);
+#pragma unroll
+        for (int j = 0; j < V; ++j) o[j / per] |= map(lane_code<T>(x, j)) << (8 * sizeof(T) * (j % per));
+        vec[k] = make_uint4(o[0], o[1], o[2], o[3]);
     }
 }
 
