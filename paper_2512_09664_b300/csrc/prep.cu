@@ -28,21 +28,39 @@ namespace spx {
 // ---------------------------------------------------------------------------
 
 // ---------------------------------------------------------------------------
-// k_plan: per-pair prefix sums (CTA 0, 1024 threads); CTAs 1.. clear the
-// bin counts of a render
+// k_plan: per-pair prefix sums (CTA 0, 1024 threads); the next CTAs clear
+// the bin counts of a render; the last ones form the FP64 blur taps, 32
+// pairs each (FP64 is slow on this part: spread over SMs, off CTA 0's path)
 // ---------------------------------------------------------------------------
 constexpr int kPlanZeroWords = 16384;
+constexpr int kPlanTapPairs = 32;
 
 __global__ void __launch_bounds__(1024) k_plan(const synthpix_pair_desc *__restrict__ descs, int32_t n_pairs,
                                                int32_t tile, int32_t fused, PairPlan *__restrict__ plan,
                                                int64_t want_part, int64_t want_tiles, int64_t want_list,
                                                int64_t want_inter, int64_t want_chunks, int32_t *__restrict__ check,
                                                float *__restrict__ blur_w, uint32_t *__restrict__ ticket,
-                                               uint32_t *__restrict__ count, int64_t n_count) {
-    if (blockIdx.x > 0) {  // the other CTAs clear the bin counts, 16 Ki words each
+                                               uint32_t *__restrict__ count, int64_t n_count, int32_t zero_ctas) {
+    if (blockIdx.x > 0 && (int)blockIdx.x <= zero_ctas) {  // clear the bin counts, 16 Ki words per CTA
         const int64_t k0 = ((int64_t)blockIdx.x - 1) * kPlanZeroWords;
         const int64_t n = min((int64_t)kPlanZeroWords, n_count - k0);
         for (int64_t k = threadIdx.x; k < n; k += blockDim.x) count[k0 + k] = 0u;
+        return;
+    }
+    if (blockIdx.x > 0) {  // normalised blur taps w[|k|], k = -R..R (FP64, stored FP32), a pair per thread
+        const int b = ((int)blockIdx.x - 1 - zero_ctas) * kPlanTapPairs + (int)threadIdx.x;
+        if (threadIdx.x >= kPlanTapPairs || b >= n_pairs) return;
+        const float bs = descs[b].blur_sigma;
+        const int32_t R = blur_radius_of(bs);
+        if (R > 0) {
+            double w[kMaxBlurRadius + 1], sum = 0.0;
+            const double sb = (double)bs;
+            for (int k = 0; k <= R; ++k) {
+                w[k] = exp(-(double)(k * k) / (2.0 * sb * sb));
+                sum += k ? 2.0 * w[k] : w[k];
+            }
+            for (int k = 0; k <= R; ++k) blur_w[b * kBlurStride + k] = (float)(w[k] / sum);
+        }
         return;
     }
     __shared__ long long s_part[1024], s_tile[1024], s_list[1024], s_inter[1024], s_chunk[1024];
@@ -90,16 +108,6 @@ __global__ void __launch_bounds__(1024) k_plan(const synthpix_pair_desc *__restr
         p.chunk_base = (int32_t)bc;
         p.pad = 0;
         plan[b] = p;
-        // normalised blur taps w[|k|], k = -R..R (FP64, stored FP32)
-        if (g.blur_r > 0) {
-            double w[kMaxBlurRadius + 1], sum = 0.0;
-            const double sb = (double)d.blur_sigma;
-            for (int k = 0; k <= g.blur_r; ++k) {
-                w[k] = exp(-(double)(k * k) / (2.0 * sb * sb));
-                sum += k ? 2.0 * w[k] : w[k];
-            }
-            for (int k = 0; k <= g.blur_r; ++k) blur_w[b * kBlurStride + k] = (float)(w[k] / sum);
-        }
         bp += d.n_particles;
         bt += 2LL * g.ntiles;
         bl += 2LL * g.list_cap;
@@ -592,9 +600,11 @@ cudaError_t launch_plan(const synthpix_pair_desc *descs, int32_t n_pairs, int32_
                         PairPlan *plan, const Layout &L, int32_t *check, float *blur_w, uint32_t *ticket,
                         uint32_t *count, cudaStream_t st) {
     const int64_t n_count = count ? L.n_tiles : 0;
-    const unsigned grid = 1u + (unsigned)((n_count + kPlanZeroWords - 1) / kPlanZeroWords);
+    const int32_t zero_ctas = (int32_t)((n_count + kPlanZeroWords - 1) / kPlanZeroWords);
+    const int32_t tap_ctas = (n_pairs + kPlanTapPairs - 1) / kPlanTapPairs;
+    const unsigned grid = 1u + (unsigned)zero_ctas + (unsigned)tap_ctas;
     return launch_kernel(k_plan, grid, 1024, 0, st, descs, n_pairs, tile, fused, plan, L.n_part, L.n_tiles, L.n_list,
-                          L.n_inter, L.n_chunks, check, blur_w, ticket, count, n_count);
+                          L.n_inter, L.n_chunks, check, blur_w, ticket, count, n_count, zero_ctas);
 }
 
 cudaError_t launch_prep(const KernelArgs &a, cudaStream_t st, cudaEvent_t const *ev) {
