@@ -63,34 +63,52 @@ __global__ void __launch_bounds__(1024) k_plan(const synthpix_pair_desc *__restr
         }
         return;
     }
-    __shared__ long long s_part[1024], s_tile[1024], s_list[1024], s_inter[1024], s_chunk[1024];
-    const int t = threadIdx.x;
+    // block scan of five per-thread sums: inclusive scans within each warp by
+    // shuffles, the warps' totals scanned by warp 0, two barriers in all
+    __shared__ long long s_w[5][32];
+    __shared__ long long s_tot[5];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int per = (n_pairs + 1023) / 1024;
     const int b0 = min(t * per, n_pairs), b1 = min(b0 + per, n_pairs);
-    long long np = 0, nt = 0, nl = 0, ni = 0, nc = 0;
+    long long v[5] = {0, 0, 0, 0, 0};  // particles, tiles, bin slots, intermediate elements, chunks
     for (int b = b0; b < b1; ++b) {
         const synthpix_pair_desc d = descs[b];
         const PairGeom g = pair_geom(d, tile, fused != 0);
-        np += d.n_particles;
-        nt += 2LL * g.ntiles;
-        nl += 2LL * g.list_cap;
-        ni += fused ? 0LL : 2LL * d.height * d.width;
-        nc += g.chunks;
+        v[0] += d.n_particles;
+        v[1] += 2LL * g.ntiles;
+        v[2] += 2LL * g.list_cap;
+        v[3] += fused ? 0LL : 2LL * d.height * d.width;
+        v[4] += g.chunks;
     }
-    s_part[t] = np; s_tile[t] = nt; s_list[t] = nl; s_inter[t] = ni; s_chunk[t] = nc;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {  // inclusive Hillis-Steele scan
-        long long a = 0, bq = 0, c = 0, e = 0, h = 0;
-        if (t >= off) {
-            a = s_part[t - off]; bq = s_tile[t - off]; c = s_list[t - off]; e = s_inter[t - off];
-            h = s_chunk[t - off];
+    long long inc[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        inc[j] = v[j];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const long long o = __shfl_up_sync(0xffffffffu, inc[j], d);
+            if (lane >= d) inc[j] += o;
         }
-        __syncthreads();
-        s_part[t] += a; s_tile[t] += bq; s_list[t] += c; s_inter[t] += e; s_chunk[t] += h;
-        __syncthreads();
+        if (lane == 31) s_w[j][warp] = inc[j];
     }
-    long long bp = s_part[t] - np, bt = s_tile[t] - nt, bl = s_list[t] - nl, bi = s_inter[t] - ni;
-    long long bc = s_chunk[t] - nc;
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            long long x = s_w[j][lane];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const long long o = __shfl_up_sync(0xffffffffu, x, d);
+                if (lane >= d) x += o;
+            }
+            s_w[j][lane] = x - s_w[j][lane];  // exclusive offset of each warp
+            if (lane == 31) s_tot[j] = x;
+        }
+    }
+    __syncthreads();
+    long long bp = s_w[0][warp] + inc[0] - v[0], bt = s_w[1][warp] + inc[1] - v[1];
+    long long bl = s_w[2][warp] + inc[2] - v[2], bi = s_w[3][warp] + inc[3] - v[3];
+    long long bc = s_w[4][warp] + inc[4] - v[4];
     for (int b = b0; b < b1; ++b) {
         const synthpix_pair_desc d = descs[b];
         const PairGeom g = pair_geom(d, tile, fused != 0);
@@ -116,8 +134,8 @@ __global__ void __launch_bounds__(1024) k_plan(const synthpix_pair_desc *__restr
     }
     if (t == 1023) {
         *ticket = 0u;
-        const bool ok = s_part[1023] == want_part && s_tile[1023] == want_tiles && s_list[1023] == want_list &&
-                        s_inter[1023] == want_inter && s_chunk[1023] == want_chunks;
+        const bool ok = s_tot[0] == want_part && s_tot[1] == want_tiles && s_tot[2] == want_list &&
+                        s_tot[3] == want_inter && s_tot[4] == want_chunks;
         *check = ok ? 1 : 0;
     }
 }
