@@ -178,6 +178,11 @@ int make_plan_tile(const synthpix_batch_desc *batch, const synthpix_pair_desc *p
     L.rec = take((size_t)L.n_list * rec_bytes + 64);  // + read-over of 16-byte staging
     L.adv = take((size_t)(L.n_list / 2) * sizeof(spx::Record));  // frame-1 segments only
     L.inter = take((size_t)L.n_inter * 2);
+    {  // carry words of the splat's CTAs: one accumulator's worth each
+        const int E = tile + 2 * P.max_r;
+        L.carry_stride = (int64_t)E * spx::pitch_cap(E);
+        L.carry = take((size_t)spx::splat_max_ctas(tile, L.n_tiles) * (size_t)L.carry_stride * 4);
+    }
     L.gfr = take((size_t)L.n_part * 2 * sizeof(float4));
     L.total = o;
     return SYNTHPIX_OK;
@@ -341,6 +346,8 @@ static int run(Mode mode, const synthpix_batch_desc *batch, const synthpix_pair_
     a.grad_flows = x.grad_flows;
     a.grad_particles = x.grad_particles;
     a.grad_frames = reinterpret_cast<float4 *>(ws + L.gfr);
+    a.carry = reinterpret_cast<uint32_t *>(ws + L.carry);
+    a.carry_stride = L.carry_stride;
     a.smem_edge = P.tile + 2 * P.max_r;
     const int wmax = std::min(spx::window_max(P.max_d), a.smem_edge);
     a.warp_scratch = 4 * (wmax + 2);

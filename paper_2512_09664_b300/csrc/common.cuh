@@ -102,8 +102,9 @@ static_assert(sizeof(ItemInfo) == 24, "ItemInfo layout");
 
 // Workspace layout (byte offsets, 256-aligned), computed on the host.
 struct Layout {
-    size_t plan, desc, check, blur, count, off, cursor, items, pos, sa, shape, rec, adv, inter, gfr, total;
+    size_t plan, desc, check, blur, count, off, cursor, items, pos, sa, shape, rec, adv, inter, gfr, carry, total;
     int64_t n_part, n_tiles, n_list, n_inter, n_chunks;
+    int64_t carry_stride;  // carry words per k_splat CTA
 };
 
 __host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }

@@ -31,6 +31,8 @@ struct KernelArgs {
     int32_t ext;                      // 1: per-frame shapes (general shapes, variation or hiding)
     int32_t general;                  // 1: bins hold RecordG (general-shape splat)
     float hide_prob;                  // probability of hiding a particle from a frame
+    uint32_t *carry;                  // k_splat: carry words, carry_stride per CTA (wrapped fixed-point sums)
+    int64_t carry_stride;
     int32_t out_of_plane;             // 1: a w grid follows each flow grid; z moves along the path
     uint32_t *count, *off, *cursor;   // per (pair, frame, tile)
     ItemInfo *items;                  // per (pair, frame, tile): the splat's work items
@@ -71,15 +73,25 @@ constexpr int kStageDesc = (int)sizeof(synthpix_pair_desc);  // staged header: d
 constexpr int kStagePlan = kStageDesc + (int)sizeof(PairPlan);  // plan (64),
 constexpr int kStageHeader = kStagePlan + 128;                  // blur taps (128)
 constexpr int kRecBufBytes = 8192;      // each staged-records buffer of k_splat (tiles up to 64)
-constexpr int kRecBufBytesLarge = 24576;  // the same at tile 128
+constexpr int kRecBufBytesLarge = 12288;  // the same at tile 128
 // records of rec_bytes bytes per staged chunk of a buffer
 __host__ __device__ constexpr int rec_cap(int buf_bytes, int rec_bytes = 24) {
     return (buf_bytes - kStageHeader - 32) / rec_bytes;
 }
-// threads of a k_splat CTA at a tile edge
-// (256 below tile 128: three CTAs per SM hide each other's barriers better
-// than two of 512)
-__host__ __device__ constexpr int splat_threads(int tile) { return tile >= 128 ? 1024 : 256; }
+// threads of a k_splat CTA at a tile edge: 512 at tile 128 (two CTAs per
+// SM), else 256 (several CTAs per SM hide each other's barriers)
+__host__ __device__ constexpr int splat_threads(int tile) { return tile >= 128 ? 512 : 256; }
+// k_splat CTAs the carry words are laid out for: a bound on SMs times the
+// CTAs an SM holds at 64 registers a thread (65536 / (64 NT)), and never
+// more than the batch's work items; the launch is clamped to it
+constexpr int kCarrySms = 160;
+__host__ __device__ constexpr int64_t splat_max_ctas(int tile, int64_t n_items) {
+    const int64_t m = (int64_t)kCarrySms * (1024 / splat_threads(tile));
+    return n_items < m ? n_items : m;
+}
+// Row pitch capacity of the accumulator for a capacity edge E (tile + 2 max
+// radius): the aligned widths stay within E + 6.
+__host__ __device__ inline int pitch_cap(int E) { return ((E + 3) & ~3) + 4; }
 __host__ __device__ constexpr int rec_buf_bytes_for(int tile) { return tile >= 128 ? kRecBufBytesLarge : kRecBufBytes; }
 constexpr size_t kMaxSmemBytes = 227 * 1024;  // dynamic shared memory of one CTA
 

@@ -84,13 +84,14 @@ constexpr uint32_t kSafeVisits = 63;            // visits per block that cannot 
 constexpr int kBlkShift = 3;                    // 8 x 8 pixel blocks
 constexpr int kBlkSide = 24;                    // blocks per side of the counter grid (row pitch <= 192)
 
-// Tile geometry of one work item.  The accumulator covers the halo-widened
-// rectangle clipped to the frame, from column ax0 (ex0 rounded down to a
-// multiple of 4) with a row pitch P (a multiple of 4), so quads of 4 pixels
-// are 16-byte aligned.  The finishing buffer A covers the full halo
-// rectangle [x0 - R, x1 + R) x [y0 - R, y1 + R) from column afx0 (x0 - R
-// rounded down to a multiple of 4) with pitch AP; outside the frame it holds
-// replicated border values.
+// Tile geometry of one work item.  The accumulator and the finishing buffer A
+// share memory: the full halo rectangle [x0 - R, x1 + R) x [y0 - R, y1 + R)
+// from column afx0 (x0 - R rounded down to a multiple of 4) with row pitch AP,
+// so quads of 4 pixels are 16-byte aligned.  Particles are splatted into its
+// part inside the frame, the halo-widened rectangle clipped to the frame
+// (from column ax0, ex0 rounded down to a multiple of 4, P columns); the first
+// finishing pass turns those words into A in place, and the pixels outside
+// the frame take replicated border values.
 struct Geo {
     int32_t W, H;
     int32_t x0, x1, y0, y1;      // tile pixels [x0, x1) x [y0, y1)
@@ -99,7 +100,8 @@ struct Geo {
     int32_t R;                   // blur radius
     int32_t ax0, P;              // accumulator: first column, row pitch
     int32_t fx0, fy0, FW, FH;    // full halo rectangle (may leave the frame)
-    int32_t afx0, AP;            // finishing buffer: first column, row pitch
+    int32_t afx0, AP;            // accumulator = finishing buffer: first column, row pitch
+    int32_t aoff;                // index of (ey0, ax0) in it (rows from fy0, columns from afx0)
 };
 
 // Visit classes of the splat's sort (see splat_chunk): windows of at most
@@ -121,8 +123,8 @@ __shared__ int sh_wrap;                            // a checked add wrapped a wo
 
 // The tile's accumulator as the splat sees it.
 struct Acc {
-    uint32_t *acc;  // [rows][P] words; carry words at acc + co
-    int co;
+    uint32_t *acc;    // [rows][P] words in shared memory
+    uint32_t *carry;  // the CTA's carry words in global memory, same indices
     int P;
 };
 
@@ -136,7 +138,7 @@ __device__ __forceinline__ void add_contrib(uint32_t *w, const Acc &A, float mx,
     }
     const uint32_t old = atomicAdd(w, l);
     if (old + l < old) {
-        atomicAdd(w + A.co, 1u);
+        atomicAdd(A.carry + (w - A.acc), 1u);
         sh_wrap = 1;
     }
 }
@@ -343,7 +345,7 @@ template <int NT>
 __device__ __forceinline__ void splat_chunk(const unsigned char *recs, unsigned char *out, uint32_t n, const Geo &g,
                                             float scale, const Acc &acc, float *scr,
                                             int wq, const float4 *tab) {
-    constexpr int RPT = (rec_cap(NT >= 1024 ? kRecBufBytesLarge : kRecBufBytes) + NT - 1) / NT;
+    constexpr int RPT = (rec_cap(NT >= 512 ? kRecBufBytesLarge : kRecBufBytes) + NT - 1) / NT;
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
     Visit v[RPT];
@@ -370,15 +372,15 @@ __device__ __forceinline__ void splat_chunk(const unsigned char *recs, unsigned 
                 v[q].py = pf.y;
                 v[q].inv = __frcp_rn(ps.x);
                 v[q].amps = ps.y * scale;
-                v[q].base = (i0 - g.ey0) * g.P + (j0 - g.ax0);
+                v[q].base = (i0 - g.fy0) * g.AP + (j0 - g.afx0);
                 v[q].shape = ((uint32_t)(j0 - pi.x) & 0xFFu) | (((uint32_t)(i0 - pi.y) & 0xFFu) << 8) |
                              ((uint32_t)nx << 16) | ((uint32_t)ny << 24);
                 const int m = max(nx, ny);
                 const int cls = m > kNarrowMax ? kWideClass : (m - 1) >> 1;
                 key[q] = cls * 32 + (v[q].base & 31);
                 slot[q] = atomicAdd(sh_cnt + key[q], 1u);
-                const int bx0 = (j0 - g.ax0) >> kBlkShift, bx1 = (j1 - g.ax0) >> kBlkShift;
-                const int by0 = (i0 - g.ey0) >> kBlkShift, by1 = (i1 - g.ey0) >> kBlkShift;
+                const int bx0 = (j0 - g.afx0) >> kBlkShift, bx1 = (j1 - g.afx0) >> kBlkShift;
+                const int by0 = (i0 - g.fy0) >> kBlkShift, by1 = (i1 - g.fy0) >> kBlkShift;
                 for (int by = by0; by <= by1; ++by)
                     for (int bx = bx0; bx <= bx1; ++bx) atomicAdd(sh_blk + by * kBlkSide + bx, 1u);
             }
@@ -433,9 +435,9 @@ __device__ __forceinline__ void splat_chunk(const unsigned char *recs, unsigned 
     __syncthreads();
     float2 *o8 = reinterpret_cast<float2 *>(out);  // 16-byte aligned; a Visit is three 8-byte words
     const bool chk = sh_checked != 0;
-    if (chk && !sh_carry_clean) {  // the carry words share memory with the finishing buffer: clear them
-        uint4 *cw = reinterpret_cast<uint4 *>(acc.acc + acc.co);
-        for (int k = threadIdx.x; k < (g.EH * g.P) >> 2; k += blockDim.x) cw[k] = make_uint4(0u, 0u, 0u, 0u);
+    if (chk && !sh_carry_clean) {  // the item's first checked chunk: clear the CTA's carry words
+        uint4 *cw = reinterpret_cast<uint4 *>(acc.carry);
+        for (int k = threadIdx.x; k < (g.FH * g.AP) >> 2; k += blockDim.x) cw[k] = make_uint4(0u, 0u, 0u, 0u);
     }
 #pragma unroll
     for (int q = 0; q < RPT; ++q) {
@@ -681,8 +683,8 @@ __device__ __forceinline__ void splat_chunk_general(const unsigned char *recs, u
         int32_t j0, j1, i0, i1;
         general_window(R[k], g, j0, j1, i0, i1);
         if (j0 > j1 || i0 > i1) continue;
-        const int bx0 = (j0 - g.ax0) >> kBlkShift, bx1 = (j1 - g.ax0) >> kBlkShift;
-        const int by0 = (i0 - g.ey0) >> kBlkShift, by1 = (i1 - g.ey0) >> kBlkShift;
+        const int bx0 = (j0 - g.afx0) >> kBlkShift, bx1 = (j1 - g.afx0) >> kBlkShift;
+        const int by0 = (i0 - g.fy0) >> kBlkShift, by1 = (i1 - g.fy0) >> kBlkShift;
         for (int by = by0; by <= by1; ++by)
             for (int bx = bx0; bx <= bx1; ++bx) atomicAdd(sh_blk + by * kBlkSide + bx, 1u);
     }
@@ -701,9 +703,9 @@ __device__ __forceinline__ void splat_chunk_general(const unsigned char *recs, u
     __syncthreads();
     const bool chk = sh_checked != 0;
     if (chk) {
-        if (!sh_carry_clean) {  // the carry words share memory with the finishing buffer: clear them
-            uint4 *cw = reinterpret_cast<uint4 *>(acc.acc + acc.co);
-            for (int k = threadIdx.x; k < (g.EH * g.P) >> 2; k += blockDim.x) cw[k] = make_uint4(0u, 0u, 0u, 0u);
+        if (!sh_carry_clean) {  // the item's first checked chunk: clear the CTA's carry words
+            uint4 *cw = reinterpret_cast<uint4 *>(acc.carry);
+            for (int k = threadIdx.x; k < (g.FH * g.AP) >> 2; k += blockDim.x) cw[k] = make_uint4(0u, 0u, 0u, 0u);
         }
         __syncthreads();
         if (threadIdx.x == 0) sh_carry_clean = 1;  // read again only after the chunk's last barrier
@@ -717,7 +719,7 @@ __device__ __forceinline__ void splat_chunk_general(const unsigned char *recs, u
         int32_t j0, j1, i0, i1;
         general_window(r, g, j0, j1, i0, i1);
         if (j0 > j1 || i0 > i1) continue;
-        uint32_t *w0 = acc.acc + (i0 - g.ey0) * acc.P + (j0 - g.ax0);
+        uint32_t *w0 = acc.acc + (i0 - g.fy0) * acc.P + (j0 - g.afx0);
         const float amps = r.amp * scale;
         if (chk) splat_general_visit<true>(r, j0, i0, j1 - j0 + 1, i1 - i0 + 1, amps, w0, acc, tab);
         else splat_general_visit<false>(r, j0, i0, j1 - j0 + 1, i1 - i0 + 1, amps, w0, acc, tab);
@@ -965,17 +967,12 @@ __device__ __forceinline__ void store_unblurred(const Geo &g, const float *A, T 
 // one work item
 // ---------------------------------------------------------------------------
 struct Smem {
-    uint32_t *acc;  // accumulator words; carry words at acc + co (the finishing buffer's memory)
-    int co;
+    uint32_t *acc;    // accumulator words; A (floats) in the same memory after the first finishing pass
+    uint32_t *carry;  // the CTA's carry words (global memory)
     float *A, *Bh, *sx2, *sy2, *scr;
     const float4 *phi;
     int BP;
-    bool bh_alias;  // Bh shares memory with the accumulator words (cleared again after the blur)
 };
-
-// Row pitch capacity of the accumulator and finishing buffer for a capacity
-// edge E (tile + 2 max radius): the aligned widths stay within E + 6.
-__host__ __device__ inline int pitch_cap(int E) { return ((E + 3) & ~3) + 4; }
 
 __device__ __forceinline__ Geo make_geo(const synthpix_pair_desc &D, const PairPlan &pl, int tile_edge, int tile,
                                         int halo) {
@@ -1002,6 +999,7 @@ __device__ __forceinline__ Geo make_geo(const synthpix_pair_desc &D, const PairP
     g.FH = (g.y1 - g.y0) + 2 * g.R;
     g.afx0 = g.fx0 & ~3;  // rounds down for negative columns too (two's complement)
     g.AP = (g.x1 + g.R - g.afx0 + 3) & ~3;
+    g.aoff = (g.ey0 - g.fy0) * g.AP + (g.ax0 - g.afx0);
     return g;
 }
 
@@ -1051,9 +1049,11 @@ struct AccSource {
 // the finishing buffer (which holds the carry words) is written.  Ends with
 // a barrier.
 __device__ __forceinline__ void wrapped_to_float(const Smem &s, const Geo &g, float unit) {
-    const uint32_t *cw = s.acc + s.co;
-    for (int k = threadIdx.x; k < g.EH * g.P; k += blockDim.x)
-        s.acc[k] = __float_as_uint(fmaf((float)cw[k], kWrapValue, (float)s.acc[k]) * unit);
+    const float ip = 1.0f / (float)g.P;
+    for (int k = threadIdx.x; k < g.EH * g.P; k += blockDim.x) {
+        const int r = small_div(k, ip), i = g.aoff + r * g.AP + (k - r * g.P);
+        s.acc[i] = __float_as_uint(fmaf((float)s.carry[i], kWrapValue, (float)s.acc[i]) * unit);
+    }
     __syncthreads();
 }
 
@@ -1104,7 +1104,7 @@ __device__ __forceinline__ void finish_pass1(const KernelArgs &a, const Geo &g, 
     const float dl = D.illum_max - D.illum_min, lmin = D.illum_min, sn = D.noise_sigma;
     const bool noise = sn != 0.0f;
     const uint32_t tag = kTagNoise + (uint32_t)frame;
-    float *A0 = s.A + (g.ey0 - g.fy0) * g.AP + (g.ax0 - g.afx0);  // A at accumulator (row 0, column 0)
+    float *A0 = s.A + g.aoff;  // A at (ey0, ax0): in place over the accumulator words it is made from
     if (!noise || (g.W & 3) == 0) {
         const int nq = g.P >> 2;
         const float inq = 1.0f / (float)nq;
@@ -1164,9 +1164,10 @@ __device__ __forceinline__ void finish_pass1(const KernelArgs &a, const Geo &g, 
 // The rest of the finishing steps once A is complete over the accumulator
 // rectangle (a barrier after finish_pass1): border replication into the halo
 // outside the frame, separable blur, quantisation, one store per pixel.
+// clear_after: clear A (the accumulator's memory) for the next item.
 template <typename T>
 __device__ __forceinline__ void finish_rest(const KernelArgs &a, const Geo &g, const synthpix_pair_desc &D,
-                                            const float *wtab, int frame, const Smem &s) {
+                                            const float *wtab, int frame, const Smem &s, bool clear_after) {
     if (g.R > 0 && (g.fx0 < 0 || g.fy0 < 0 || g.x1 + g.R > g.W || g.y1 + g.R > g.H)) {  // uniform
         // only the pixels of the full halo rectangle outside the frame: whole rows
         // above and below it, then the columns left and right of it in the rows
@@ -1208,10 +1209,10 @@ __device__ __forceinline__ void finish_rest(const KernelArgs &a, const Geo &g, c
     case 6: blur_store<T, 6>(g, s.A, wtab, out, M); break;
     default: blur_store_any<T>(g, s.A, s.Bh, s.BP, wtab, out, M); break;
     }
-    if (g.R > 6 && s.bh_alias) {  // Bh lives in the accumulator words: clear them for the next item
+    if (clear_after) {  // A is the next item's accumulator: zero once every pass has read it
         __syncthreads();
-        float4 *b4 = reinterpret_cast<float4 *>(s.Bh);
-        for (int k = threadIdx.x; k < (g.FH * s.BP) >> 2; k += blockDim.x) b4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 *a4 = reinterpret_cast<float4 *>(s.A);
+        for (int k = threadIdx.x; k < (g.FH * g.AP) >> 2; k += blockDim.x) a4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 
@@ -1241,7 +1242,7 @@ __device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo
     // splat, chunk by chunk of staged records
     const float imax = D.i_max > 0.0f ? D.i_max : 1.0f;
     const float scale = kFixedScale / imax;
-    const Acc acc{s.acc, s.co, g.P};
+    const Acc acc{s.acc, s.carry, g.AP};
     uint32_t done = 0;
     while (done < it.count) {
         const uint32_t n = min(it.count - done, cap);
@@ -1270,7 +1271,7 @@ __device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo
     const float unit = imax * kFixedUnit;
     const bool wrapped = sh_wrap != 0;
     if (wrapped) wrapped_to_float(s, g, unit);
-    const AccSource src{s.acc, g.P, unit, wrapped};
+    const AccSource src{s.acc + g.aoff, g.AP, unit, wrapped};
     if (!fused) {
         // halo 0: the accumulator rectangle is the tile (ax0 = ex0 = x0)
         const int64_t HW = (int64_t)g.H * g.W;
@@ -1287,23 +1288,21 @@ __device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo
     }
     finish_pass1(a, g, D, it.frame, illum, s, src);
     __syncthreads();
-    finish_rest<T>(a, g, D, wtab, it.frame, s);
+    finish_rest<T>(a, g, D, wtab, it.frame, s, true);
 }
 
 // ---------------------------------------------------------------------------
 // the persistent kernel
 // ---------------------------------------------------------------------------
 struct SmemLayout {
-    size_t acc, A, Bh, sx2, sy2, scr, phi, bufs, total;
-    bool bh_alias;
+    size_t acc, Bh, sx2, sy2, scr, phi, bufs, total;
 };
 
-// The accumulator words; the finishing buffer A (which holds the carry words
-// during the splat); the horizontal-blur buffer Bh of the blur for radii
-// above 6 (the others blur rows in place), in memory of its own when that
-// fits, else in the accumulator words (free between the first finishing pass
-// and the next item); illumination factors; per-warp window scratch; the
-// normal-tail table; two staged-record buffers.
+// The accumulator words, which hold the finishing buffer A after the first
+// finishing pass (+ padding read by the last row's blur loads); illumination
+// factors; per-warp window scratch; the normal-tail table; two
+// staged-record buffers; the horizontal-blur buffer Bh of the blur for radii
+// above 6 (the others blur rows in place).
 __host__ __device__ inline SmemLayout smem_layout(int E, int tile, int warp_scratch, int rec_buf_bytes) {
     SmemLayout L;
     const int BP = (tile + 3) & ~3;
@@ -1314,17 +1313,14 @@ __host__ __device__ inline SmemLayout smem_layout(int E, int tile, int warp_scra
         o = (o + bytes + 15) & ~(size_t)15;
         return at;
     };
-    L.acc = take((size_t)E * PC * 4);
-    L.A = take(((size_t)E * PC + 32) * 4);  // + padding read by the last row's blur loads
+    L.acc = take(((size_t)E * PC + 32) * 4);
     L.sx2 = take(PC * 4);
     L.sy2 = take((size_t)E * 4);
     L.scr = take((size_t)(splat_threads(tile) / 32) * warp_scratch * 4);
     L.phi = take((size_t)(kPhiDegree + 1) * kPhiPieces * 4);
     L.bufs = take(2 * (size_t)rec_buf_bytes);
     const bool need_bh = (E - tile) / 2 > 6;  // only the blur of radii above 6 uses Bh
-    const size_t bh = need_bh ? (size_t)E * BP * 4 : 0;
-    L.bh_alias = need_bh && o + bh > kMaxSmemBytes;
-    L.Bh = (!need_bh || L.bh_alias) ? L.acc : take(bh);
+    L.Bh = need_bh ? take((size_t)E * BP * 4) : L.acc;
     L.total = o;
     return L;
 }
@@ -1339,9 +1335,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_splat(KernelArgs a) {
     const int words = a.smem_edge * pitch_cap(a.smem_edge);
     Smem s;
     s.acc = reinterpret_cast<uint32_t *>(smem + L.acc);
-    s.co = (int)((L.A - L.acc) / 4);
-    s.bh_alias = L.bh_alias;
-    s.A = reinterpret_cast<float *>(smem + L.A);
+    s.carry = a.carry + (int64_t)blockIdx.x * a.carry_stride;
+    s.A = reinterpret_cast<float *>(smem + L.acc);
     s.Bh = reinterpret_cast<float *>(smem + L.Bh);
     s.sx2 = reinterpret_cast<float *>(smem + L.sx2);
     s.sy2 = reinterpret_cast<float *>(smem + L.sy2);
@@ -1439,14 +1434,13 @@ __global__ void __launch_bounds__(kSplatThreads) k_finish(KernelArgs a) {
     const FinishLayout FL = finish_layout(a.smem_edge, a.tile);
     Smem s;
     s.acc = nullptr;
-    s.co = 0;
+    s.carry = nullptr;
     s.A = reinterpret_cast<float *>(smem + FL.A);
     s.Bh = reinterpret_cast<float *>(smem + FL.Bh);
     s.sx2 = reinterpret_cast<float *>(smem + FL.sx2);
     s.sy2 = reinterpret_cast<float *>(smem + FL.sy2);
     s.scr = nullptr;
     s.phi = nullptr;
-    s.bh_alias = false;
     s.BP = (a.tile + 3) & ~3;
     const ItemInfo it = a.items[blockIdx.x];
     const synthpix_pair_desc &D = a.descs[it.pair];
@@ -1460,7 +1454,7 @@ __global__ void __launch_bounds__(kSplatThreads) k_finish(KernelArgs a) {
     const InterSource<I> src{S16, g.W, g.ey0, g.ax0, vec};
     finish_pass1(a, g, D, it.frame, illum, s, src);
     __syncthreads();
-    finish_rest<T>(a, g, D, wtab, it.frame, s);
+    finish_rest<T>(a, g, D, wtab, it.frame, s, false);
 }
 
 size_t splat_smem_bytes(int edge, int tile, int warp_scratch, int rec_buf_bytes) {
@@ -1481,17 +1475,18 @@ cudaError_t launch_splat(const KernelArgs &a, int32_t out_dtype, cudaStream_t st
         if (e != cudaSuccess) return e;                                                                      \
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem);                             \
         if (e != cudaSuccess) return e;                                                                      \
-        const int64_t want = (int64_t)nsm * (occ > 0 ? occ : 1);                                             \
+        int64_t want = (int64_t)nsm * (occ > 0 ? occ : 1);                                                   \
+        if (want > splat_max_ctas(a.tile, a.n_tiles)) want = splat_max_ctas(a.tile, a.n_tiles); /* carries */\
         e = launch_kernel(kern, (unsigned)(a.n_tiles < want ? a.n_tiles : want), NT, smem, st, a);           \
         if (e != cudaSuccess) return e;                                                                      \
     } while (0)
 #define SPX_LAUNCH(T)                                                                                        \
     do {                                                                                                     \
         if (a.general) {                                                                                     \
-            if (nt == 1024) SPX_LAUNCH_NT(T, 1024, 32);                                                      \
+            if (nt == 512) SPX_LAUNCH_NT(T, 512, 32);                                                        \
             else SPX_LAUNCH_NT(T, 256, 32);                                                                  \
         } else {                                                                                             \
-            if (nt == 1024) SPX_LAUNCH_NT(T, 1024, 24);                                                      \
+            if (nt == 512) SPX_LAUNCH_NT(T, 512, 24);                                                        \
             else SPX_LAUNCH_NT(T, 256, 24);                                                                  \
         }                                                                                                    \
     } while (0)
