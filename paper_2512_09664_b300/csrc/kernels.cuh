@@ -72,7 +72,7 @@ constexpr int kSplatMaxThreads = 1024;  // k_splat at tile 128 (one CTA per SM)
 constexpr int kStageDesc = (int)sizeof(synthpix_pair_desc);  // staged header: descriptor (160),
 constexpr int kStagePlan = kStageDesc + (int)sizeof(PairPlan);  // plan (64),
 constexpr int kStageHeader = kStagePlan + 128;                  // blur taps (128)
-constexpr int kRecBufBytes = 8192;      // each staged-records buffer of k_splat (tiles up to 64)
+constexpr int kRecBufBytes = 10240;     // each staged-records buffer of k_splat (tiles up to 64)
 constexpr int kRecBufBytesLarge = 13312;  // the same at tile 128 (two CTAs per SM: 2 chunks for most items)
 // records of rec_bytes bytes per staged chunk of a buffer
 __host__ __device__ constexpr int rec_cap(int buf_bytes, int rec_bytes = 24) {
