@@ -197,12 +197,14 @@ __device__ __forceinline__ int visit_ny(uint32_t s) { return (int)(s >> 24); }
 // c < 8 holds windows of at most N = 2 (c + 1) pixels a side; each is
 // rendered by a group of U = class_lanes(c) adjacent lanes (splat_group):
 // the lanes share the N + 1 x edges and take RG = class_rows(c) rows each.
-// Class 8 holds the wider windows, rendered by a whole warp per visit.  The
-// visits of one warp are spread over the bank order, so their accumulator
-// addresses fall in different banks.
+// Class 8 holds the wider windows, rendered by a whole warp per visit, four
+// visits per warp slot (more slots spread the long wide visits over the
+// warps: with 32 per slot a few warps held them all while the rest waited
+// at the chunk's barrier).  The visits of one warp are spread over the bank
+// order, so their accumulator addresses fall in different banks.
 __host__ __device__ constexpr int class_lanes(int c) { return c < 2 ? 1 : 2; }
-// log2 of the visits one warp slot of class c renders (32 / lanes per visit; 32 for the wide class)
-__host__ __device__ constexpr int class_slot_shift(int c) { return c >= 8 ? 5 : (c < 2 ? 5 : 4); }
+// log2 of the visits one warp slot of class c renders (32 / lanes per visit; 4 for the wide class)
+__host__ __device__ constexpr int class_slot_shift(int c) { return c >= 8 ? 2 : (c < 2 ? 5 : 4); }
 __host__ __device__ constexpr int class_rows(int c) { return c == 0 ? 2 : (c == 1 ? 4 : c + 1); }
 
 // Quotient of small non-negative integers a / b (a < 2^20, 1 <= b <= 2^10)
@@ -356,6 +358,13 @@ __device__ __forceinline__ void splat_coop(const Visit &v, bool valid, const Acc
     }
 }
 
+
+// The wide class out of line (the render loop's registers serve the narrow classes).
+template <bool CHECKED>
+__device__ __noinline__ void splat_coop_out(const Visit v, bool valid, const Acc A, float *scr, int wq,
+                                            const float4 *tab) {
+    splat_coop<CHECKED>(v, valid, A, scr, wq, tab);
+}
 
 // Splat n staged records (at recs) into the tile's accumulator:
 //   A. each thread sets up its records' visits (window clipped to the halo
@@ -515,9 +524,10 @@ __device__ __forceinline__ void splat_chunk(const unsigned char *recs, unsigned 
         const uint32_t g0 = sh_off[32 * c], G = sh_off[32 * c + 32] - g0;
         const int csh = class_slot_shift(c);
         const uint32_t nw = (G + (1u << csh) - 1u) >> csh;  // slots of the class
-        // wide: visits 32 sl + lane; narrow: group q of U lanes takes visit sl + q nw (spread over the bank order)
-        const uint32_t idx = c == kWideClass ? sl * 32 + lane : sl + (uint32_t)(lane >> (5 - csh)) * nw;
-        const bool valid = idx < G;
+        // wide: visits 4 sl + lane (lanes 0..3); narrow: group q of U lanes takes visit sl + q nw (spread
+        // over the bank order)
+        const uint32_t idx = c == kWideClass ? (sl << csh) + lane : sl + (uint32_t)(lane >> (5 - csh)) * nw;
+        const bool valid = idx < G && (c != kWideClass || lane < (1 << csh));
         Visit e;
         if (valid) {
             const float2 a = o8[3 * (g0 + idx)], b = o8[3 * (g0 + idx) + 1], d = o8[3 * (g0 + idx) + 2];
@@ -541,7 +551,7 @@ __device__ __forceinline__ void splat_chunk(const unsigned char *recs, unsigned 
         case 5: splat_group<12, class_lanes(5), class_rows(5)>(e, acc, tab); break;
         case 6: splat_group<14, class_lanes(6), class_rows(6)>(e, acc, tab); break;
         case 7: splat_group<16, class_lanes(7), class_rows(7)>(e, acc, tab); break;
-        default: splat_coop<false>(e, valid, acc, scr, wq, tab); break;
+        default: splat_coop_out<false>(e, valid, acc, scr, wq, tab); break;
         }
     }
 }
