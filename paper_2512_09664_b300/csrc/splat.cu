@@ -200,7 +200,8 @@ __device__ __forceinline__ int visit_ny(uint32_t s) { return (int)(s >> 24); }
 // Class 8 holds the wider windows, rendered by a whole warp per visit, four
 // visits per warp slot (more slots spread the long wide visits over the
 // warps: with 32 per slot a few warps held them all while the rest waited
-// at the chunk's barrier).  The visits of one warp are spread over the bank
+// at the chunk's barrier); its slots come first and are rendered by a loop of
+// their own, so the narrow classes' loop keeps its registers.  The visits of one warp are spread over the bank
 // order, so their accumulator addresses fall in different banks.
 __host__ __device__ constexpr int class_lanes(int c) { return c < 2 ? 1 : 2; }
 // log2 of the visits one warp slot of class c renders (32 / lanes per visit; 4 for the wide class)
@@ -359,13 +360,6 @@ __device__ __forceinline__ void splat_coop(const Visit &v, bool valid, const Acc
 }
 
 
-// The wide class out of line (the render loop's registers serve the narrow classes).
-template <bool CHECKED>
-__device__ __noinline__ void splat_coop_out(const Visit v, bool valid, const Acc A, float *scr, int wq,
-                                            const float4 *tab) {
-    splat_coop<CHECKED>(v, valid, A, scr, wq, tab);
-}
-
 // Splat n staged records (at recs) into the tile's accumulator:
 //   A. each thread sets up its records' visits (window clipped to the halo
 //      rectangle), takes a slot in its (class, bank) bucket and counts the
@@ -512,22 +506,45 @@ __device__ __forceinline__ void splat_chunk(const unsigned char *recs, unsigned 
     }
     const uint32_t total_slots = sh_slot_end[kWideClass];
     const uint32_t my_end = lane <= kWideClass ? sh_slot_end[lane] : 0xffffffffu;
-    for (;;) {
-        uint32_t sl = 0;
-        if (lane == 0) sl = atomicAdd(&sh_next, 1u);
-        sl = __shfl_sync(FULL, sl, 0);
-        if (sl >= total_slots) break;
+    const uint32_t wide_end = sh_slot_end[0];  // the wide class's slots come first
+    auto claim = [&]() {
+        uint32_t t = 0;
+        if (lane == 0) t = atomicAdd(&sh_next, 1u);
+        return __shfl_sync(FULL, t, 0);
+    };
+    uint32_t sl = claim();
+    {  // the wide class: a warp per visit, four visits per slot
+        const uint32_t g0 = sh_off[32 * kWideClass], G = sh_off[32 * kWideClass + 32] - g0;
+        for (; sl < wide_end; sl = claim()) {
+            const uint32_t idx = (sl << class_slot_shift(kWideClass)) + lane;
+            const bool valid = lane < (1 << class_slot_shift(kWideClass)) && idx < G;
+            Visit e;
+            e.px = e.py = e.inv = e.amps = 0.0f;
+            e.base = 0;
+            e.shape = 0;
+            if (valid) {
+                const float2 a = o8[3 * (g0 + idx)], b = o8[3 * (g0 + idx) + 1], d = o8[3 * (g0 + idx) + 2];
+                e.px = a.x;
+                e.py = a.y;
+                e.inv = b.x;
+                e.amps = b.y;
+                e.base = __float_as_int(d.x);
+                e.shape = __float_as_uint(d.y);
+            }
+            splat_coop<false>(e, valid, acc, scr, wq, tab);
+        }
+    }
+    for (; sl < total_slots; sl = claim()) {
         // the slot's class: the first (widest-first) class whose slots end beyond sl
         const int o = __ffs(__ballot_sync(FULL, sl < my_end)) - 1;
         const int c = kWideClass - o;
-        sl -= o ? __shfl_sync(FULL, my_end, o - 1) : 0u;  // slot within the class
+        const uint32_t sc = sl - (o ? __shfl_sync(FULL, my_end, o - 1) : 0u);  // slot within the class
         const uint32_t g0 = sh_off[32 * c], G = sh_off[32 * c + 32] - g0;
         const int csh = class_slot_shift(c);
         const uint32_t nw = (G + (1u << csh) - 1u) >> csh;  // slots of the class
-        // wide: visits 4 sl + lane (lanes 0..3); narrow: group q of U lanes takes visit sl + q nw (spread
-        // over the bank order)
-        const uint32_t idx = c == kWideClass ? (sl << csh) + lane : sl + (uint32_t)(lane >> (5 - csh)) * nw;
-        const bool valid = idx < G && (c != kWideClass || lane < (1 << csh));
+        // group q of U lanes takes visit sc + q nw (spread over the bank order)
+        const uint32_t idx = sc + (uint32_t)(lane >> (5 - csh)) * nw;
+        const bool valid = idx < G;
         Visit e;
         if (valid) {
             const float2 a = o8[3 * (g0 + idx)], b = o8[3 * (g0 + idx) + 1], d = o8[3 * (g0 + idx) + 2];
@@ -550,8 +567,7 @@ __device__ __forceinline__ void splat_chunk(const unsigned char *recs, unsigned 
         case 4: splat_group<10, class_lanes(4), class_rows(4)>(e, acc, tab); break;
         case 5: splat_group<12, class_lanes(5), class_rows(5)>(e, acc, tab); break;
         case 6: splat_group<14, class_lanes(6), class_rows(6)>(e, acc, tab); break;
-        case 7: splat_group<16, class_lanes(7), class_rows(7)>(e, acc, tab); break;
-        default: splat_coop_out<false>(e, valid, acc, scr, wq, tab); break;
+        default: splat_group<16, class_lanes(7), class_rows(7)>(e, acc, tab); break;
         }
     }
 }
