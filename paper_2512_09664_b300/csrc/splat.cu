@@ -264,12 +264,39 @@ __device__ __forceinline__ void splat_group(const Visit &v, const Acc &A, const 
     }
 }
 
-// Windows with more than 30 edges: per-warp scratch in shared memory.
+// Windows with more edges than lanes (out of line: the inlined renders keep
+// their registers).  Up to 64 edges: two per lane, entries k = lane and
+// k = lane + 32 of the x edges 0..nx followed by the y edges 0..ny; lane c
+// owns columns c and c + 32 and walks the rows, each row's mass broadcast by
+// one shuffle.  Wider windows: per-warp scratch in shared memory.
 template <bool CHECKED>
 __device__ __noinline__ void splat_particle_wide(const Acc A, float px, float py, float inv,
                                                  float amps, int32_t base, int bx, int by, int nx, int ny,
                                                  float *scr, int wq, const float4 *tab) {
     const int lane = threadIdx.x & 31;
+    if (nx + ny + 2 <= 64) {
+        const unsigned FULL = 0xffffffffu;
+        auto edge = [&](int k) {
+            const float dd = k <= nx ? __fsub_rn((float)(bx + k), px) : __fsub_rn((float)(by + k - nx - 1), py);
+            return k < nx + ny + 2 ? edge_value_tab(dd, inv, tab) : 0.0f;
+        };
+        const float e0 = edge(lane), e1 = edge(lane + 32);
+        const float e1l0 = __shfl_sync(FULL, e1, 0);
+        float n0 = __shfl_down_sync(FULL, e0, 1);
+        if (lane == 31) n0 = e1l0;
+        const float n1 = __shfl_down_sync(FULL, e1, 1);
+        float m0 = edge_mass(e0, n0), m1 = edge_mass(e1, n1);
+        if (lane > nx) m0 = __fmul_rn(m0, amps);  // row masses carry the amplitude
+        if (lane + 32 > nx) m1 = __fmul_rn(m1, amps);
+        uint32_t *col = A.acc + base + lane;
+        for (int r = 0; r < ny; ++r) {
+            const int k = nx + 1 + r;  // uniform across the warp
+            const float my = k < 32 ? __shfl_sync(FULL, m0, k) : __shfl_sync(FULL, m1, k - 32);
+            if (lane < nx) add_contrib<CHECKED>(col + r * A.P, A, m0, my);
+            if (lane + 32 < nx) add_contrib<CHECKED>(col + r * A.P + 32, A, m1, my);
+        }
+        return;
+    }
     float *exe = scr, *eye = scr + wq, *ex = scr + 2 * wq, *ey = scr + 3 * wq;
     for (int e = lane; e <= nx; e += 32) exe[e] = edge_value_tab(__fsub_rn((float)(bx + e), px), inv, tab);
     for (int e = lane; e <= ny; e += 32) eye[e] = edge_value_tab(__fsub_rn((float)(by + e), py), inv, tab);
@@ -290,8 +317,8 @@ __device__ __noinline__ void splat_particle_wide(const Acc A, float px, float py
 
 // Wide visits, a warp per visit: lanes [0, nx] evaluate the x edges, lanes
 // [nx+1, nx+ny+1] the y edges; each lane then takes one column and every
-// rpr-th row of the window.  Windows with up to 64 edges hold two per lane;
-// wider ones go through the scratch path.
+// rpr-th row of the window.  Windows with more edges than lanes go through
+// splat_particle_wide.
 template <bool CHECKED>
 __device__ __forceinline__ void splat_coop(const Visit &v, bool valid, const Acc &A, float *scr,
                                            int wq, const float4 *tab) {
@@ -306,33 +333,8 @@ __device__ __forceinline__ void splat_coop(const Visit &v, bool valid, const Acc
         const int32_t base = __shfl_sync(FULL, v.base, src);
         const uint32_t shape = __shfl_sync(FULL, v.shape, src);
         const int nx = visit_nx(shape), ny = visit_ny(shape), bx = visit_bx(shape), by = visit_by(shape);
-        if (nx + ny + 2 > 64) {
-            splat_particle_wide<CHECKED>(A, px, py, inv, amps, base, bx, by, nx, ny, scr, wq, tab);
-            continue;
-        }
         if (nx + ny + 2 > 32) {
-            // two edges per lane: entries k = lane and k = lane + 32 of the x edges
-            // 0..nx followed by the y edges 0..ny; lane c owns columns c and c + 32
-            // and walks the rows, each row's mass broadcast by one shuffle
-            auto edge = [&](int k) {
-                const float dd = k <= nx ? __fsub_rn((float)(bx + k), px) : __fsub_rn((float)(by + k - nx - 1), py);
-                return k < nx + ny + 2 ? edge_value_tab(dd, inv, tab) : 0.0f;
-            };
-            const float e0 = edge(lane), e1 = edge(lane + 32);
-            const float e1l0 = __shfl_sync(FULL, e1, 0);
-            float n0 = __shfl_down_sync(FULL, e0, 1);
-            if (lane == 31) n0 = e1l0;
-            const float n1 = __shfl_down_sync(FULL, e1, 1);
-            float m0 = edge_mass(e0, n0), m1 = edge_mass(e1, n1);
-            if (lane > nx) m0 = __fmul_rn(m0, amps);  // row masses carry the amplitude
-            if (lane + 32 > nx) m1 = __fmul_rn(m1, amps);
-            uint32_t *col = A.acc + base + lane;
-            for (int r = 0; r < ny; ++r) {
-                const int k = nx + 1 + r;  // uniform across the warp
-                const float my = k < 32 ? __shfl_sync(FULL, m0, k) : __shfl_sync(FULL, m1, k - 32);
-                if (lane < nx) add_contrib<CHECKED>(col + r * A.P, A, m0, my);
-                if (lane + 32 < nx) add_contrib<CHECKED>(col + r * A.P + 32, A, m1, my);
-            }
+            splat_particle_wide<CHECKED>(A, px, py, inv, amps, base, bx, by, nx, ny, scr, wq, tab);
             continue;
         }
         const int nxe = nx + 1;
