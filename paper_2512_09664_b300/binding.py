@@ -24,8 +24,10 @@ FLAG_OUT_OF_PLANE = 2   # a w grid follows each flow grid; particles move in z (
 DTYPE_CODE = {"f32": 0, "f16": 1, "bf16": 2, "u8": 3, "u16": 4}
 INTEGRATOR_CODE = {"rk4": 0, "euler": 1}
 _EXPORTS = ("synthpix_workspace_bytes", "synthpix_render_pairs", "synthpix_render_pairs_staged",
-            "synthpix_render_pairs_from", "synthpix_seed_particles", "synthpix_render_backward",
-            "synthpix_autotune_tile", "synthpix_last_error", "synthpix_version")
+            "synthpix_render_pairs_from", "synthpix_seed_particles", "synthpix_advect_particles",
+            "synthpix_render_backward", "synthpix_autotune_tile", "synthpix_render_pairs_noalloc",
+            "synthpix_fourier_flows", "synthpix_fourier_flows_workspace_bytes", "synthpix_match_histogram",
+            "synthpix_match_histogram_workspace_bytes", "synthpix_last_error", "synthpix_version")
 STAGES = ("plan", "seed_advect", "bin_scan", "bin_scatter", "splat_epilogue")
 
 

@@ -169,3 +169,7 @@ def test_histogram_matching_validation():
     assert L.synthpix_match_histogram(C.byref(pk.batch), pk.pairs, pk.n_pairs, FAKE, FAKE, FAKE, 1 << 30, None) == \
         B.EUNSUPPORTED
     assert L.synthpix_match_histogram_workspace_bytes(C.byref(pk.batch), pk.pairs, pk.n_pairs) == 0
+
+
+def test_binding_export_list_is_the_header():
+    assert sorted(B.exported_symbols()) == _declared()
