@@ -271,20 +271,26 @@ def fourier_flows_workspace_bytes(n_flows: int, n_modes: int, flow_h: int, flow_
     return n
 
 
-def match_histogram(pk: Packed, images_dev, target_dev, workspace_dev=None, stream=None):
-    """synthpix_match_histogram on a packed batch's rendered images (in place); returns the workspace."""
+def match_histogram_desc(batch: BatchDesc, pairs, n_pairs: int, images_dev, target_dev, workspace_dev=None,
+                         stream=None):
+    """synthpix_match_histogram on rendered images (in place) from raw descriptors; returns the workspace."""
     import torch
     st = stream if stream is not None else torch.cuda.current_stream()
     if workspace_dev is None:
-        n = lib().synthpix_match_histogram_workspace_bytes(C.byref(pk.batch), pk.pairs, pk.n_pairs)
-        if n == 0 and pk.n_pairs > 0:
+        n = lib().synthpix_match_histogram_workspace_bytes(C.byref(batch), pairs, n_pairs)
+        if n == 0 and n_pairs > 0:
             raise SynthpixError(EINVAL, last_error())
         workspace_dev = torch.empty(max(n, 256), dtype=torch.uint8, device=images_dev.device)
-    rc = lib().synthpix_match_histogram(C.byref(pk.batch), pk.pairs, pk.n_pairs, C.c_void_p(images_dev.data_ptr()),
+    rc = lib().synthpix_match_histogram(C.byref(batch), pairs, n_pairs, C.c_void_p(images_dev.data_ptr()),
                                         C.c_void_p(target_dev.data_ptr()), C.c_void_p(workspace_dev.data_ptr()),
                                         workspace_dev.numel(), C.c_void_p(st.cuda_stream))
     _check(rc)
     return workspace_dev
+
+
+def match_histogram(pk: Packed, images_dev, target_dev, workspace_dev=None, stream=None):
+    """synthpix_match_histogram on a packed batch's rendered images (in place); returns the workspace."""
+    return match_histogram_desc(pk.batch, pk.pairs, pk.n_pairs, images_dev, target_dev, workspace_dev, stream)
 
 
 class Renderer:

@@ -364,8 +364,8 @@ class Sampler:
             C.c_void_p(main.cuda_stream))
         B._check(rc)
         if self.target is not None:  # frames matched to the target histogram, in place
-            pk = B.Packed(self.batch, self.pairs, self.B, None, [], 0, self.out_dtype, [])
-            self.match_ws = B.match_histogram(pk, out, self.target, self.match_ws, stream=main)
+            self.match_ws = B.match_histogram_desc(self.batch, self.pairs, self.B, out, self.target, self.match_ws,
+                                                   stream=main)
         self.flow_free[j].record(main)
         self.k += 1
         if (k + 1) // self.R != s:  # the next batch starts a new set: generate it while this one renders
