@@ -1,9 +1,10 @@
 """The workloads at their full sizes, in the launch configuration bench.py
 uses (autotuned tile, persistent splat), against the FP64 oracle: every pair
 of the 64-pair 512^2 batch, every pair of the 256-pair uneven batch, the
-32-pair differentiable batch (forward and gradients), and a reduced large
+32-pair differentiable batch (forward and gradients), a reduced large
 mixed-precision batch (2048^2 and 1920x1080 frames) with its 16-bit error
-reported."""
+reported, and the 64-pair shape, variation, hiding and out-of-focus
+batches (sampled pairs for the elliptical one)."""
 import numpy as np
 import pytest
 
@@ -93,3 +94,31 @@ def test_large_mixed_reduced_16bit_error(inter):
     if inter == "f32":  # the fused FP32 path: exact codes away from rounding boundaries
         st = compare(wl, g, ref)
         print("large_mixed f32", st)
+
+
+def test_shapes64_512_general_sampled_pairs():
+    # the elliptical workload rendered whole in the bench's configuration;
+    # sampled pairs against the oracle (its quadrature is slow on the host)
+    wl = W.shapes_batch(n_pairs=64)
+    r = _autotuned(wl)
+    g = gpu_render(wl, renderer=r)
+    idx = [0, 9, 31, 63]
+    st = compare(wl, [g[b] for b in idx], oracle_render(wl, pairs=idx))
+    print("shapes64_512 general", st, "tile", r.pk.batch.tile)
+    assert st["mismatch"] <= st["band"]
+
+
+def test_shapes64_512_round_every_pair():
+    wl = W.shapes_batch(n_pairs=64, general=False)
+    r = _autotuned(wl)
+    st = compare(wl, gpu_render(wl, renderer=r), oracle_render(wl))
+    print("shapes64_512 round", st, "tile", r.pk.batch.tile)
+    assert st["mismatch"] <= st["band"]
+
+
+def test_focus64_512_every_pair():
+    wl = W.focus_batch(n_pairs=64)
+    r = _autotuned(wl)
+    st = compare(wl, gpu_render(wl, renderer=r), oracle_render(wl))
+    print("focus64_512", st, "tile", r.pk.batch.tile)
+    assert st["mismatch"] <= st["band"]
