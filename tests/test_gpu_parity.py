@@ -200,3 +200,32 @@ def test_pixel_sums_beyond_64_imax_carry_exactly():
         g = gpu_render(wl, tile=16, inter_dtype=inter)
         rel = np.abs(g[0] - ref[0]["B"]) / np.maximum(np.abs(ref[0]["B"]), 1.0)
         assert rel.max() < {"f16": 2.0 ** -10, "bf16": 2.0 ** -7}[inter] + 1e-4
+
+
+@pytest.mark.parametrize("sb,tiles", [(3.0, (16, 32, 64, 128)), (8.0, (16, 32, 64))])
+def test_blur_radius_above_six_uses_its_own_buffer(sb, tiles):
+    # radii above 6 blur rows through a buffer of their own (the in-place row
+    # pass covers radii up to 6); sigma 8 is the largest blur (radius 24)
+    flows = [W.fourier_flow(150, 170, 150, 170, rms=2.0, seed=12)]
+    p = _small(150, 170, 800, d_min=1.0, d_max=4.0, illum_min=0.7, illum_max=1.0, noise_sigma=0.02,
+               blur_sigma=sb)
+    wl = _wl([p], flows, out_dtype="u16", quant_bits=12)
+    ref = oracle_render(wl)
+    outs = [gpu_render(wl, tile=t) for t in tiles]
+    for o in outs:
+        compare(wl, o, ref)
+
+
+def test_largest_blur_at_tile_128_is_unsupported_and_autotune_skips_it():
+    from paper_2512_09664_b300 import binding as B
+    flows = [W.fourier_flow(150, 170, 150, 170, rms=2.0, seed=12)]
+    p = _small(150, 170, 800, blur_sigma=8.0)
+    wl = _wl([p], flows, out_dtype="u16", quant_bits=12)
+    r = B.Renderer(wl, tile=128)
+    with pytest.raises(B.SynthpixError) as e:
+        r.render()
+    assert e.value.code == B.EUNSUPPORTED
+    r = B.Renderer(wl)
+    tile, _ = r.autotune(reps=1)
+    assert tile in (16, 32, 64)
+    compare(wl, gpu_render(wl, renderer=r), oracle_render(wl))
