@@ -303,7 +303,7 @@ def splat_source_hash():
 def run_ours(args, rank, world, dist):
     import torch
 
-    from paper_2512_09664_b300.binding import STAGES, Renderer
+    from paper_2512_09664_b300.binding import Renderer
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     wl = workload(rank, args.pairs)
@@ -350,8 +350,7 @@ def run_ours(args, rank, world, dist):
         flush.fill_(k & 0xFF)
         r.render_staged(staged[k])
     torch.cuda.synchronize()
-    stage_ms = {name: sum(ev[i].elapsed_time(ev[i + 1]) for ev in staged) / n_staged
-                for i, name in enumerate(STAGES)}
+    stage_ms = _stage_medians(staged)
     total_ms = max_over_ranks(total_ms, dist, dev)
     value = aggregate_pairs_per_s(world, wl.n_pairs, args.steps, total_ms)
     ms_per_step = total_ms / args.steps
@@ -505,10 +504,9 @@ def _time_device(fn, steps, flush, stream):
 
 
 def _stage_ms(r, n, flush, stream):
-    """Mean per-stage times over n renders with the library's stage events."""
+    """Median per-stage times over n renders with the library's stage events."""
     import torch
 
-    from paper_2512_09664_b300.binding import STAGES
     staged = []
     for k in range(n):
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
@@ -520,7 +518,20 @@ def _stage_ms(r, n, flush, stream):
         flush.fill_(k & 0xFF)
         r.render_staged(staged[k])
     torch.cuda.synchronize()
-    return {name: sum(ev[i].elapsed_time(ev[i + 1]) for ev in staged) / n for i, name in enumerate(STAGES)}
+    return _stage_medians(staged)
+
+
+def _stage_medians(staged):
+    """Per-stage median over renders of the times between the library's stage events.
+
+    The median, not the mean: a render whose launches the host enqueued late
+    (the GPU idle between two stage events) would otherwise inflate a stage.
+    """
+    import numpy as np
+
+    from paper_2512_09664_b300.binding import STAGES
+    return {name: float(np.median([ev[i].elapsed_time(ev[i + 1]) for ev in staged]))
+            for i, name in enumerate(STAGES)}
 
 
 def _step_stats(ms):

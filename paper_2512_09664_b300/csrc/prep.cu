@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(1024) k_plan(const synthpix_pair_desc *__restr
 // makes one global atomic per tile it touches instead of one per particle.
 // ---------------------------------------------------------------------------
 constexpr int kPrepThreads = 256;
-constexpr int kHistMax = 4096;  // (frame, tile) counters of a pair held on chip; larger pairs count in global
+constexpr int kHistMax = 2048;  // (frame, tile) counters of a pair held on chip; larger pairs count in global
 
 struct ChunkCtx {
     synthpix_pair_desc d;
@@ -315,17 +315,35 @@ __global__ void __launch_bounds__(1024) k_scan(KernelArgs a, int frame) {
 // (sigma_x, sigma_y, rho, amplitude) of the frame (hidden particles skipped).
 template <typename Put>
 __device__ __forceinline__ void chunk_windows(const KernelArgs &a, const ChunkCtx &c, int nf, Put put) {
-    for (int q = threadIdx.x; q < c.n; q += kPrepThreads) {
-        const int64_t g = c.pl.part_base + c.first + q;
-        float4 sh = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        if (!a.ext) {
-            const float2 sa = a.sa[g];
-            sh = make_float4(sa.x, sa.x, 0.0f, sa.y);
+    static_assert(kChunk == 2 * kPrepThreads, "two particles of the chunk per thread");
+    // both particles' loads are issued before either is binned (two requests in flight)
+    const int64_t g0 = c.pl.part_base + c.first + threadIdx.x, g1 = g0 + kPrepThreads;
+    const bool v0 = (int)threadIdx.x < c.n, v1 = (int)threadIdx.x + kPrepThreads < c.n;
+    float4 s0 = make_float4(-1.0f, 0.0f, 0.0f, 0.0f), s1 = s0;
+    if (!a.ext) {
+        if (v0) {
+            const float2 sa = a.sa[g0];
+            s0 = make_float4(sa.x, sa.x, 0.0f, sa.y);
         }
-        for (int f = 0; f < nf; ++f) {
-            if (a.ext) sh = a.shape[f * a.n_part + g];
-            if (sh.x < 0.0f) continue;  // hidden from this frame
-            const float4 p = f ? a.pos1[g] : a.pos0[g];
+        if (v1) {
+            const float2 sa = a.sa[g1];
+            s1 = make_float4(sa.x, sa.x, 0.0f, sa.y);
+        }
+    }
+    for (int f = 0; f < nf; ++f) {
+        const float4 *pos = f ? a.pos1 : a.pos0;
+        float4 p0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), p1 = p0;
+        if (a.ext) {
+            s0.x = s1.x = -1.0f;
+            if (v0) s0 = a.shape[f * a.n_part + g0];
+            if (v1) s1 = a.shape[f * a.n_part + g1];
+        }
+        if (v0) p0 = pos[g0];
+        if (v1) p1 = pos[g1];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const float4 &p = u ? p1 : p0, &sh = u ? s1 : s0;
+            if (sh.x < 0.0f) continue;  // outside the chunk, or hidden from this frame
             const Window w = particle_window2(__float_as_int(p.z), p.x, __float_as_int(p.w), p.y, 6.0f * sh.x,
                                               6.0f * sh.y, c.d.width, c.d.height);
             if (w.j0 > w.j1 || w.i0 > w.i1) continue;
@@ -565,18 +583,20 @@ __global__ void __launch_bounds__(kAdvThreads) k_scatter2(KernelArgs a) {
     Record *seg = a.rec + pl.list_base + pl.list_cap;
     for (int i = threadIdx.x; i < kNbrSide * kNbrSide; i += kAdvThreads) s_cnt[i] = 0u;
     __syncthreads();
+    constexpr int U = 4;  // records per thread and pass, loaded together
     auto load = [&](uint32_t k, Record &r) {
+        if (k >= c.it.count) {
+            r.sigma = -1.0f;
+            return;
+        }
         const float2 *rp = reinterpret_cast<const float2 *>(a.adv + c.adv0 + k);
-        const float2 p2 = rp[2];
-        if (p2.x < 0.0f) return false;
-        const float2 p0 = rp[0], p1 = rp[1];
+        const float2 p0 = rp[0], p1 = rp[1], p2 = rp[2];
         r.fx = p0.x;
         r.fy = p0.y;
         r.ix = __float_as_int(p1.x);
         r.iy = __float_as_int(p1.y);
-        r.sigma = p2.x;
+        r.sigma = p2.x;  // negative: advected by another tile
         r.amp = p2.y;
-        return true;
     };
     auto place = [&](uint32_t slot, const Record &r) {
         if ((int64_t)slot < pl.list_cap) {
@@ -586,13 +606,18 @@ __global__ void __launch_bounds__(kAdvThreads) k_scatter2(KernelArgs a) {
             o[2] = make_float2(r.sigma, r.amp);
         }
     };
-    for (uint32_t k = threadIdx.x; k < c.it.count; k += kAdvThreads) {
-        Record r;
-        if (!load(k, r)) continue;
-        frame2_tiles(a, pl, c, r, W, H, [&](int kk, int32_t tile) {
-            if (kk >= 0) atomicAdd(s_cnt + kk, 1u);
-            else place(atomicAdd(cur2 + tile, 1u), r);
-        });
+    for (uint32_t k0 = threadIdx.x; k0 < c.it.count; k0 += U * kAdvThreads) {
+        Record r[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) load(k0 + u * kAdvThreads, r[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (r[u].sigma < 0.0f) continue;
+            frame2_tiles(a, pl, c, r[u], W, H, [&](int kk, int32_t tile) {
+                if (kk >= 0) atomicAdd(s_cnt + kk, 1u);
+                else place(atomicAdd(cur2 + tile, 1u), r[u]);
+            });
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kNbrSide * kNbrSide; i += kAdvThreads) {
@@ -602,12 +627,17 @@ __global__ void __launch_bounds__(kAdvThreads) k_scatter2(KernelArgs a) {
         s_cnt[i] = 0u;
     }
     __syncthreads();
-    for (uint32_t k = threadIdx.x; k < c.it.count; k += kAdvThreads) {
-        Record r;
-        if (!load(k, r)) continue;
-        frame2_tiles(a, pl, c, r, W, H, [&](int kk, int32_t) {
-            if (kk >= 0) place(s_base[kk] + atomicAdd(s_cnt + kk, 1u), r);
-        });
+    for (uint32_t k0 = threadIdx.x; k0 < c.it.count; k0 += U * kAdvThreads) {
+        Record r[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) load(k0 + u * kAdvThreads, r[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (r[u].sigma < 0.0f) continue;
+            frame2_tiles(a, pl, c, r[u], W, H, [&](int kk, int32_t) {
+                if (kk >= 0) place(s_base[kk] + atomicAdd(s_cnt + kk, 1u), r[u]);
+            });
+        }
     }
 }
 
