@@ -422,6 +422,69 @@ class Renderer:
         return self.images[o:o + 2 * h * w].view(2, h, w)
 
 
+class HostPipeline:
+    """Batches rendered from pinned host flow grids into pinned host images.
+
+    A step copies its flow grids in on an upload stream, renders them with
+    synthpix_render_pairs on the caller's stream and copies the images out on
+    a download stream.  `depth` device sets of (flows, images) let the upload
+    of step k+1 and the download of step k-1 run on the copy engines while
+    step k renders, so in steady state a step costs its longest part, not the
+    sum of the three.  Every step uses the renderer's packed batch (pair
+    descriptors and sizes); only the flows differ.  The caller must not
+    overwrite a step's host flows before its `uploaded` event nor read its
+    host images before the event submit() returns.
+    """
+
+    def __init__(self, renderer: "Renderer", depth: int = 2):
+        import torch
+        if depth < 1:
+            raise ValueError("depth must be at least 1")
+        self.r = renderer
+        self.depth = depth
+        self.flows = [renderer.flows] + [torch.empty_like(renderer.flows) for _ in range(depth - 1)]
+        self.images = [renderer.images] + [torch.empty_like(renderer.images) for _ in range(depth - 1)]
+        self.up = torch.cuda.Stream(renderer.device)
+        self.down = torch.cuda.Stream(renderer.device)
+        self.uploaded = [torch.cuda.Event() for _ in range(depth)]
+        self.rendered = [torch.cuda.Event() for _ in range(depth)]
+        self.downloaded = [torch.cuda.Event() for _ in range(depth)]
+        self.used = [False] * depth
+        self.k = 0
+
+    def submit(self, flows_host, images_host, stream=None):
+        """Queue one step; returns the event after which images_host holds its images."""
+        import torch
+        st = stream if stream is not None else torch.cuda.current_stream(self.r.device)
+        if flows_host.numel() != self.flows[0].numel() or images_host.numel() != self.images[0].numel():
+            raise ValueError("host buffers do not match the packed batch")
+        s = self.k % self.depth
+        if self.used[s]:
+            self.up.wait_event(self.rendered[s])  # the render that last read this flow set
+        with torch.cuda.stream(self.up):
+            self.flows[s].copy_(flows_host, non_blocking=True)
+        self.uploaded[s].record(self.up)
+        st.wait_event(self.uploaded[s])
+        if self.used[s]:
+            st.wait_event(self.downloaded[s])  # the download that last read this image set
+        render_pairs(self.r.pk, self.flows[s], self.images[s], self.r.workspace, self.r.pairs_dev, st)
+        self.rendered[s].record(st)
+        self.down.wait_event(self.rendered[s])
+        with torch.cuda.stream(self.down):
+            images_host.copy_(self.images[s], non_blocking=True)
+        self.downloaded[s].record(self.down)
+        self.used[s] = True
+        self.k += 1
+        return self.downloaded[s]
+
+    def synchronize(self, stream=None):
+        """Make `stream` (default: the current one) wait for every queued copy."""
+        import torch
+        st = stream if stream is not None else torch.cuda.current_stream(self.r.device)
+        st.wait_stream(self.up)
+        st.wait_stream(self.down)
+
+
 def _render_fn():
     import torch
 

@@ -55,3 +55,38 @@ def test_uneven_batch_full_size_mix_sampled_against_oracle():
     wl = W.uneven_batch(n_pairs=6, sizes=(128, 256, 512, 1024))
     st = compare(wl, gpu_render(wl), oracle_render(wl))
     print("uneven full-size mix", st)
+
+
+def test_host_pipeline_steps_match_plain_renders():
+    # a stream of steps from pinned host flows to pinned host images, copies
+    # overlapped with rendering: each step's images equal a plain render of
+    # its flows, whatever the steps before it left in the other buffer set
+    import torch
+
+    from paper_2512_09664_b300.binding import HostPipeline, Renderer
+    wl = W.uneven_batch(n_pairs=3, sizes=(64, 128))
+    r = Renderer(wl, tile=32)
+    base = torch.from_numpy(r.pk.flows_host)
+    scales = (1.0, -0.6, 0.35)
+    flows_host = [(base * s).pin_memory() for s in scales]
+    pipe = HostPipeline(r, depth=2)
+    outs, events = [], []
+    for k in range(5):
+        out = torch.empty(r.images.shape, dtype=r.images.dtype).pin_memory()
+        events.append(pipe.submit(flows_host[k % 3], out))
+        outs.append(out)
+    pipe.synchronize()
+    torch.cuda.synchronize()
+    ref = Renderer(wl, tile=32)
+    for k, out in enumerate(outs):
+        img = ref.render_from(flows=flows_host[k % 3].to(ref.device)).cpu()
+        torch.cuda.synchronize()
+        assert torch.equal(out.view(torch.uint8), img.view(torch.uint8)), k
+    # the unscaled step against the oracle
+    pipe_frames = []
+    for b in range(wl.n_pairs):
+        h, w = r.pk.shapes[b]
+        o = r.pk.image_offsets[b]
+        t = outs[3][o:o + 2 * h * w].view(2, h, w)
+        pipe_frames.append(t.view(torch.int16).numpy().view(np.uint16) if t.dtype == torch.uint16 else t.numpy())
+    compare(wl, pipe_frames, oracle_render(wl))
