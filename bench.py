@@ -456,6 +456,7 @@ def run_ours(args, rank, world, dist):
         traffic = SPLAT_TRAFFIC["bytes_per_launch"]
     hbm_peak = float(peaks["hbm_gbs"])
     step_gbs = alg_bytes / (ms_per_step / 1e3) / 1e9
+    probes = alu_probes(stream)
     # k_plan, k_seed_advect, k_scan (frame 1), k_scatter, k_advect, k_scan (frame 2), k_scatter2, k_splat
     launches_per_step = 8
     line = {
@@ -469,7 +470,10 @@ def run_ours(args, rank, world, dist):
         "stage_ms": stage_ms,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tlane-op/s",
                      "frac": achieved / alu_peak, "traffic": traffic, "kernel": "k_splat",
-                     "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_mhz:.0f} MHz"},
+                     "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_mhz:.0f} MHz",
+                     "measured_fma_peak": probes["fma"], "frac_of_measured_fma": achieved / probes["fma"]},
+        "alu_probes": {"unit": "T op/s", **probes,
+                       "source": "synthpix_alu_probe, best of 3 launches of one full wave after the timed steps"},
         "step_roofline_hbm": {"achieved_gbs": step_gbs, "peak_gbs": hbm_peak, "frac": step_gbs / hbm_peak,
                               "peak_source": peak_kind, "algorithmic_bytes_per_step": alg_bytes},
         "plain_fp32_per_pair": {"value": plain_pairs_s, "unit": UNIT, "speedup": value / world / plain_pairs_s,
@@ -507,6 +511,13 @@ def _time_device(fn, steps, flush, stream):
         e1.synchronize()
         tot += e0.elapsed_time(e1)
     return tot / steps
+
+
+def alu_probes(stream):
+    """Measured throughput (T op/s) of FP32 FMA, erfcf, ex2 and the Philox high multiply."""
+    from paper_2512_09664_b300 import binding as B
+    iters = {"fma": 4096, "erfc": 256, "ex2": 2048, "umulhi": 2048}
+    return {k: B.alu_probe(k, iters=n, reps=3, stream=stream) / 1e12 for k, n in iters.items()}
 
 
 def _e2e_serial_ms(r, flows_host, img_host, stream, steps):

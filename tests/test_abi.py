@@ -173,3 +173,18 @@ def test_histogram_matching_validation():
 
 def test_binding_export_list_is_the_header():
     assert sorted(B.exported_symbols()) == _declared()
+
+
+def test_alu_probe_validation_before_any_launch():
+    L = B.lib()
+    ops = C.c_int64(-1)
+    sink = C.c_void_p(256)  # never dereferenced: every call below fails its argument checks first
+    assert L.synthpix_alu_probe(4, 16, sink, 1 << 20, C.byref(ops), None) == B.EINVAL
+    assert L.synthpix_alu_probe(-1, 16, sink, 1 << 20, C.byref(ops), None) == B.EINVAL
+    assert L.synthpix_alu_probe(0, 0, sink, 1 << 20, C.byref(ops), None) == B.EINVAL
+    assert L.synthpix_alu_probe(0, (1 << 16) + 1, sink, 1 << 20, C.byref(ops), None) == B.EINVAL
+    assert L.synthpix_alu_probe(0, 16, sink, 1 << 20, None, None) == B.EINVAL
+    assert L.synthpix_alu_probe(0, 16, None, 1 << 20, C.byref(ops), None) == B.EINVAL
+    assert L.synthpix_alu_probe(0, 16, C.c_void_p(258), 1 << 20, C.byref(ops), None) == B.EINVAL
+    assert ops.value == -1
+    assert "alu probe" in B.last_error()
