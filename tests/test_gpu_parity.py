@@ -229,3 +229,17 @@ def test_largest_blur_at_tile_128_is_unsupported_and_autotune_skips_it():
     tile, _ = r.autotune(reps=1)
     assert tile in (16, 32, 64)
     compare(wl, gpu_render(wl, renderer=r), oracle_render(wl))
+
+
+@pytest.mark.parametrize("out", [("u16", 16), ("f32", 0)])
+def test_largest_round_particles_take_the_scratch_path(out):
+    # windows of more than 64 edges (d > 10) render through the per-warp
+    # scratch buffers of the wide path; d reaches 32, the largest diameter
+    flows = [W.fourier_flow(96, 120, 96, 120, rms=3.0, seed=21)]
+    p = _small(96, 120, 40, d_min=11.0, d_max=32.0, illum_min=0.7, illum_max=1.0, noise_sigma=0.02,
+               blur_sigma=1.0)
+    wl = _wl([p], flows, out_dtype=out[0], quant_bits=out[1])
+    ref = oracle_render(wl)
+    for tile in (16, 32, 64, 128):
+        st = compare(wl, gpu_render(wl, tile=tile), ref)
+        print("largest round", out, tile, st)
