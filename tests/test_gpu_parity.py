@@ -243,3 +243,17 @@ def test_largest_round_particles_take_the_scratch_path(out):
     for tile in (16, 32, 64, 128):
         st = compare(wl, gpu_render(wl, tile=tile), ref)
         print("largest round", out, tile, st)
+
+
+@pytest.mark.parametrize("grid", [(1, 1), (2, 3), (150, 190)])
+def test_degenerate_and_finer_flow_grids(grid):
+    # one node (uniform flow), a 2 x 3 grid (clamping at every border) and a
+    # grid finer than the frame (more nodes than the staged window holds:
+    # every lookup reads the grid), each at several tile edges
+    gh, gw = grid
+    flows = [W.fourier_flow(gh, gw, 75, 95, rms=2.5, seed=31)]
+    p = _small(75, 95, 260, d_min=1.0, d_max=4.0, noise_sigma=0.02, blur_sigma=0.7)
+    wl = _wl([p], flows, out_dtype="u16", quant_bits=12)
+    ref = oracle_render(wl)
+    for tile in (16, 64, 128):
+        compare(wl, gpu_render(wl, tile=tile), ref)
