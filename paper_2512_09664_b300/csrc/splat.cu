@@ -684,6 +684,68 @@ __device__ __forceinline__ void splat_general_corr(const RecordG &r, int32_t j0,
     }
 }
 
+// rho != 0 with windows at most 32 / S columns wide: the same quadrature,
+// S lanes per (column, chunk of rows), each lane summing Q / S <= 8 of the
+// Q = 4 M nodes (consecutive ones, in node order).  The window's columns
+// repeat floor(32 / (S nx)) times across the warp, each copy taking its own
+// chunk of rows; walking down its rows a lane carries its nodes' last edge
+// values, the S partial sums meet by butterfly shuffles, and the column's
+// first lane adds the pixel.  A pixel's value depends only on its offset
+// from the particle, not on the tile's clipping of the window nor on the
+// lanes that compute it.
+template <int M, int S, bool CHECKED>
+__device__ __forceinline__ void splat_general_corr_cols(const RecordG &r, int32_t j0, int32_t i0, int nx, int ny,
+                                                        float amps, uint32_t *w0, const Acc &acc,
+                                                        const float4 *tab) {
+    constexpr int Q = 4 * M, QL = Q / S;
+    static_assert(QL >= 1 && QL <= 8 && (S & (S - 1)) == 0, "at most 8 nodes per lane");
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int span = S * nx;       // lanes of one copy of the window's columns (<= 32)
+    const int nch = 32 / span;     // copies across the warp, each with its chunk of rows
+    const int chunk = lane / span, within = lane - chunk * span;
+    const int col = within / S, sub = within & (S - 1);
+    const int rpc = (ny + nch - 1) / nch;  // rows per chunk (the loop below is warp-uniform)
+    const bool live = chunk < nch;
+    const int r0 = chunk * rpc;
+    const float c = sqrtf(1.0f - r.rho * r.rho);
+    const float isx = 1.0f / r.sx, is = 1.0f / (r.sy * c), k = r.rho * r.sy * isx;
+    constexpr float h = 1.0f / (float)M;
+    const float wscale = 0.5f * h * isx * 0.39894228040143267794f * amps;  // h/2, 1/(sqrt(2 pi) sigma_x), units
+    // offsets from the centre formed from exact integers (one rounding each)
+    const float ul = __fsub_rn((float)(j0 + col - r.ix), r.fx);  // the column's left edge
+    const float yt = __fsub_rn((float)(i0 + r0 - r.iy), r.fy);   // the top edge of the chunk's first row
+    float wn[QL], mu[QL], ev[QL];
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+        const int t = sub * QL + q, g4 = t & 3;
+        const float xg = g4 == 0 ? -0.8611363115940526f : g4 == 1 ? -0.3399810435848563f
+                       : g4 == 2 ? 0.3399810435848563f : 0.8611363115940526f;
+        const float wgt = (g4 == 0 || g4 == 3) ? 0.3478548451374538f : 0.6521451548625461f;
+        const float u = __fadd_rn(ul, h * ((float)(t >> 2) + 0.5f * (xg + 1.0f)));
+        const float tt = u * isx;
+        wn[q] = wgt * __expf(-0.5f * tt * tt) * wscale;
+        mu[q] = k * u;  // conditional mean of y at this node
+        ev[q] = edge_value_tab(__fsub_rn(yt, mu[q]), is, tab);
+    }
+    uint32_t *wc = w0 + col;
+#pragma unroll 1
+    for (int i = 0; i < rpc; ++i) {
+        const int rr = r0 + i;
+        const float ye = __fsub_rn((float)(i0 + rr + 1 - r.iy), r.fy);  // the row's lower edge
+        float v = 0.0f;
+#pragma unroll
+        for (int q = 0; q < QL; ++q) {
+            const float en = edge_value_tab(__fsub_rn(ye, mu[q]), is, tab);
+            v = fmaf(wn[q], edge_mass(ev[q], en), v);
+            ev[q] = en;
+        }
+#pragma unroll
+        for (int o = S >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+        if (live && sub == 0 && rr < ny) add_contrib<CHECKED>(wc + rr * acc.P, acc, v, 1.0f);
+    }
+}
+
 // Sub-intervals of the x quadrature of a correlated particle: a power of two
 // no smaller than 1 / min(sigma_x, sigma_x sqrt(1 - rho^2) / |rho|) (the
 // integrand's shortest x-scale; quadrature error below 1e-7 of I0), at most 64.
@@ -701,7 +763,24 @@ __device__ __forceinline__ void splat_general_visit(const RecordG &r, int32_t j0
         splat_general_sep<CHECKED>(r, j0, i0, nx, ny, amps, w0, acc, tab);
         return;
     }
-    switch (corr_subintervals(r.sx, r.rho)) {
+    const int m = corr_subintervals(r.sx, r.rho);
+    if (m <= 8) {
+        // lanes per column: at most 8 nodes per lane; the particle's unclipped window
+        // width (not the tile's clipping of it) decides, so every tile renders it the same way
+        const int lpc = m <= 2 ? 1 : m / 2;
+        const float r15x = 6.0f * r.sx;
+        const int width = (int)floorf(r.fx + r15x) - (int)floorf(r.fx - r15x) + 1;
+        if (width * lpc <= 32) {
+            switch (m) {
+            case 1: splat_general_corr_cols<1, 1, CHECKED>(r, j0, i0, nx, ny, amps, w0, acc, tab); break;
+            case 2: splat_general_corr_cols<2, 1, CHECKED>(r, j0, i0, nx, ny, amps, w0, acc, tab); break;
+            case 4: splat_general_corr_cols<4, 2, CHECKED>(r, j0, i0, nx, ny, amps, w0, acc, tab); break;
+            default: splat_general_corr_cols<8, 4, CHECKED>(r, j0, i0, nx, ny, amps, w0, acc, tab); break;
+            }
+            return;
+        }
+    }
+    switch (m) {
     case 1: splat_general_corr<1, CHECKED>(r, j0, i0, nx, ny, amps, w0, acc, tab); break;
     case 2: splat_general_corr<2, CHECKED>(r, j0, i0, nx, ny, amps, w0, acc, tab); break;
     case 4: splat_general_corr<4, CHECKED>(r, j0, i0, nx, ny, amps, w0, acc, tab); break;
