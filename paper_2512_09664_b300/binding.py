@@ -464,7 +464,9 @@ class HostPipeline:
     sum of the three.  Every step uses the renderer's packed batch (pair
     descriptors and sizes); only the flows differ.  The caller must not
     overwrite a step's host flows before its `uploaded` event nor read its
-    host images before the event submit() returns.
+    host images before the event submit() returns.  Every step must render
+    on the same stream: the renders share the renderer's workspace, so two
+    of them must never overlap.
     """
 
     def __init__(self, renderer: "Renderer", depth: int = 2):
