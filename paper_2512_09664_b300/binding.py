@@ -484,11 +484,16 @@ class HostPipeline:
         self.downloaded = [torch.cuda.Event() for _ in range(depth)]
         self.used = [False] * depth
         self.k = 0
+        self.stream = None  # the render stream, fixed by the first step
 
     def submit(self, flows_host, images_host, stream=None):
         """Queue one step; returns the event after which images_host holds its images."""
         import torch
         st = stream if stream is not None else torch.cuda.current_stream(self.r.device)
+        if self.stream is None:
+            self.stream = st
+        elif st.cuda_stream != self.stream.cuda_stream:
+            raise ValueError("every step must render on the stream of the first one (shared workspace)")
         if flows_host.numel() != self.flows[0].numel() or images_host.numel() != self.images[0].numel():
             raise ValueError("host buffers do not match the packed batch")
         s = self.k % self.depth
