@@ -77,6 +77,8 @@ def test_host_pipeline_steps_match_plain_renders():
         outs.append(out)
     pipe.synchronize()
     torch.cuda.synchronize()
+    with pytest.raises(ValueError):  # the steps share the renderer's workspace: one stream only
+        pipe.submit(flows_host[0], outs[0], torch.cuda.Stream())
     ref = Renderer(wl, tile=32)
     for k, out in enumerate(outs):
         img = ref.render_from(flows=flows_host[k % 3].to(ref.device)).cpu()
