@@ -208,6 +208,9 @@ def pack(wl, tile: int = 0, out_dtype: Optional[str] = None, inter_dtype: Option
             assert w.size * 2 == f.size, "w grid must have the flow grid's nodes"
             flat.append(w)
             off += w.size
+            if w.size & 1:  # the next grid must start on an even float (8-byte float2 nodes)
+                flat.append(np.zeros(1, np.float32))
+                off += 1
     arr = (PairDesc * max(wl.n_pairs, 1))()
     img_off, io = [], 0
     for b, spec in enumerate(wl.pairs):

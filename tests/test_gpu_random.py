@@ -3,7 +3,8 @@
 Each case draws frame sizes (ragged, down to one pixel), particle counts
 (zero included), diameter ranges, blur, noise, illumination, output type,
 integrator, substeps, dt, flow-grid resolution (one node up to finer than
-the frame), general shapes, frame-2 variation, hiding and the tile edge,
+the frame), general shapes, frame-2 variation, hiding, the sheet model,
+out-of-plane motion and the tile edge,
 and compares the CUDA path with the oracle element by element.
 """
 import numpy as np
@@ -48,17 +49,25 @@ def _case(seed: int):
         if variation:
             kw.update(jitter_d=F32(rng.uniform(0.0, 0.3)), jitter_i=F32(rng.uniform(0.0, 0.1)))
         pairs.append(W.PairSpec(**kw))
+    # the out-of-focus sheet and out-of-plane motion, from a stream of their own
+    xr = np.random.default_rng(10_000 + seed)
+    if xr.random() < 0.3:
+        for p in pairs:
+            p.sheet_model, p.sheet_shape = 1, F32(xr.uniform(1.0, 3.0))
+    flows_w = None
+    if xr.random() < 0.3:
+        flows_w = [xr.normal(0.0, 0.2, size=f.shape[:2]).astype(np.float32) for f in flows]
     out = str(rng.choice(["f32", "u8", "u16", "f16", "bf16"]))
     bits = {"u8": 8, "u16": int(rng.choice([10, 12, 16]))}.get(out, 0)
     wl = W.Workload(name=f"random{seed}", seed=1000 + seed, pairs=pairs, flows=flows, out_dtype=out,
                     quant_bits=bits, integrator=str(rng.choice(["rk4", "euler"])),
                     n_substeps=int(rng.integers(1, 5)), dt=F32(rng.uniform(0.5, 1.5)),
-                    hide_prob=F32(rng.uniform(0.0, 0.3)) if variation else F32(0.0))
+                    hide_prob=F32(rng.uniform(0.0, 0.3)) if variation else F32(0.0), flows_w=flows_w)
     tile = int(rng.choice([16, 32, 64, 128]))
     return wl, tile
 
 
-@pytest.mark.parametrize("seed", range(24))
+@pytest.mark.parametrize("seed", range(32))
 def test_random_configuration_matches_oracle(seed):
     wl, tile = _case(seed)
     compare(wl, gpu_render(wl, tile=tile), oracle_render(wl))
