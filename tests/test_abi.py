@@ -188,3 +188,17 @@ def test_alu_probe_validation_before_any_launch():
     assert L.synthpix_alu_probe(0, 16, C.c_void_p(258), 1 << 20, C.byref(ops), None) == B.EINVAL
     assert ops.value == -1
     assert "alu probe" in B.last_error()
+
+
+def test_pack_keeps_flow_grids_on_even_floats_with_odd_w_grids():
+    # 3 x 5 nodes: an odd w grid after the first flow grid must not shift the
+    # second grid onto an odd float (its float2 nodes need 8-byte alignment)
+    import numpy as np
+    flows = [W.fourier_flow(3, 5, 20, 24, rms=1.0, seed=1), W.fourier_flow(3, 5, 20, 24, rms=1.0, seed=2)]
+    pairs = [W.PairSpec(height=20, width=24, n_particles=10, pair_id=b, flow_index=b) for b in range(2)]
+    wl = W.Workload(name="w", seed=3, pairs=pairs, flows=flows,
+                    flows_w=[np.full((3, 5), 0.1, np.float32), np.full((3, 5), -0.1, np.float32)])
+    pk = B.pack(wl)
+    assert [pk.pairs[b].flow_offset % 2 for b in range(2)] == [0, 0]
+    assert pk.pairs[1].flow_offset >= 2 * 15 + 15
+    assert B.workspace_bytes(pk) > 0
