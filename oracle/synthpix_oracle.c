@@ -39,8 +39,9 @@
  *       bump between illum_min and illum_max, n standard normal (Box-Muller on
  *       Philox words); separable normalised Gaussian blur, radius ceil(3 sigma_b),
  *       replicate border, horizontal pass first; quantisation
- *       clamp(rint(B * M), 0, M), M = 2^bits - 1, round-half-even, decided in
- *       FP32 like the GPU's FP32 epilogue.
+ *       clamp(rint(B * M), 0, M), M = 2^bits - 1, round-half-even, decided on
+ *       the FP64 value B (codes are defined on the exact value; a renderer in
+ *       lower precision can differ only within its error of a boundary).
  *   R7  random numbers: Philox4x32-10 (Salmon et al., SC'11) keyed by the seed,
  *       counter (index, stream tag, pair id): tag 0 -> (x, y, d, I) words,
  *       tag 1 -> (z, d2) words, tag 2 -> (hide 1, hide 2, two normals for
@@ -65,7 +66,7 @@
  *       integrated image of a particle is I0 2 pi sigma_x sigma_y sqrt(1-rho^2)
  *       and its window is floor(x +- 1.5 d) by floor(y +- 1.5 d_y).
  *
- * Precision: FP64 everywhere except the quantisation decision (R6).
+ * Precision: FP64 everywhere, the quantisation decision included (R6).
  */
 #include <math.h>
 #include <stdint.h>
@@ -598,10 +599,12 @@ int oracle_epilogue(const oracle_pair *p, int32_t frame, const double *S, double
     }
     free(A);
     if (Q && p->quant_bits > 0) {
-        float M = (float)((1u << p->quant_bits) - 1u);
+        /* Q = clamp(rint(B M), 0, M) on the FP64 value B: rint rounds half to
+           even in the default rounding mode (reading C10) */
+        double M = (double)((1u << p->quant_bits) - 1u);
         for (long k = 0; k < H * W; ++k) {
-            float q = rintf((float)B[k] * M);
-            Q[k] = q < 0.0f ? 0u : (q > M ? (uint32_t)M : (uint32_t)q);
+            double q = rint(B[k] * M);
+            Q[k] = q < 0.0 ? 0u : (q > M ? (uint32_t)M : (uint32_t)q);
         }
     }
     return 0;

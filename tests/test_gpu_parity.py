@@ -44,13 +44,14 @@ def test_batch_512_u8_epilogue(tile):
 
 def test_batch_512_float_error_budget():
     # the same pairs with float output: the error of B itself, which decides
-    # the quantised codes; it must sit far below the 1e-6 boundary band
+    # the quantised codes.  Codes are exact outside the 1e-6 boundary band only
+    # if B is within 1e-6 of the FP64 value, so that is the bound asserted
     wl = W.batch_512_u8(n_pairs=2)
     wl.out_dtype, wl.quant_bits = "f32", 0
     ref = oracle_render(wl)
     st = compare(wl, gpu_render(wl), ref)
     print("float error of the u8 workload", st)
-    assert st["max_abs"] < 2e-6
+    assert st["max_abs"] < 1e-6
 
 
 def test_ragged_non_square_12bit():

@@ -424,18 +424,33 @@ def test_oracle_noise_enters_additively_with_sigma():
 
 @pytest.mark.parametrize("bits", [8, 12, 16])
 def test_oracle_quantisation_round_half_even_and_clamp(bits):
+    # Q = clamp(round-half-even(B M), 0, M) on the FP64 value B.  The expected
+    # codes are written from that definition with integers: a value a fixed
+    # 1e-9 (in units of B M) above or below the boundary k + 1/2 must give
+    # k + 1 or k.  The FP64 product is exact to ~1e-12 there, so the decision
+    # is unambiguous in FP64; an FP32 decision (relative error 6e-8 of B M)
+    # misrounds some of these and fails the test.
     M = 2 ** bits - 1
-    H, Wd = 4, 8
-    k = np.array([0, 1, 2, 3, 100, M - 1, M - 2, 7], dtype=np.float64)
-    S = np.stack([(k + 0.5) / M,           # exact half steps (representable in FP32 * M)
-                  k / M + 0.2 / M,         # rounds down
-                  k / M - 0.2 / M,         # rounds up to k
-                  np.array([-0.3, -1e-9, 1.0, 1.2, 2.0, 1.0 - 0.4 / M, 1.0 + 0.4 / M, 0.5])])
-    pr = oracle.make_pair(_spec(3, Wd, 0), seed=0, quant_bits=bits)
-    pr.height = 3
-    B, Q = oracle.epilogue(pr, 0, S[:3])
-    want = np.clip(np.rint(S[:3].astype(np.float32) * np.float32(M)), 0, M)
-    assert np.array_equal(Q, want.astype(np.uint32))
-    pr4 = oracle.make_pair(_spec(1, Wd, 0), seed=0, quant_bits=bits)
-    _, Q4 = oracle.epilogue(pr4, 0, S[3:4])
-    assert Q4[0, 0] == 0 and Q4[0, 1] == 0 and Q4[0, 2] == M and Q4[0, 3] == M
+    ks = [0, 1, 2, 3, 100, M // 3, M // 2, M - 2, M - 1]
+    delta = 1e-9
+    above = np.array([(k + 0.5 + delta) / M for k in ks])
+    below = np.array([(k + 0.5 - delta) / M for k in ks])
+    want_above = [k + 1 for k in ks]
+    want_below = [k for k in ks]
+    # B = 1/2 is the one exact half step in [0, 1]: B M = (M - 1) / 2 + 1/2
+    # exactly; (M - 1) / 2 = 2^(bits-1) - 1 is odd, so round-half-even picks
+    # the upper neighbour 2^(bits-1).  Then zero, full scale and the clamps.
+    special = np.array([0.5, 0.0, 1.0, -0.3, -1e-9, 1.2, 2.0, 1.0 + 0.4 / M, 1.0 - 0.4 / M])
+    want_special = [2 ** (bits - 1), 0, M, 0, 0, M, M, M, M]
+    n = len(ks)
+    S = np.zeros((3, n))
+    S[0], S[1], S[2] = above, below, special
+    pr = oracle.make_pair(_spec(3, n, 0), seed=0, quant_bits=bits)
+    B, Q = oracle.epilogue(pr, 0, S)
+    assert np.array_equal(B, S)  # no illumination, noise or blur: B is S
+    assert Q[0].tolist() == want_above
+    assert Q[1].tolist() == want_below
+    assert Q[2].tolist() == want_special
+    # the same values decided in FP32 disagree somewhere: the test tells the two apart
+    f32 = np.clip(np.rint(S[:2].astype(np.float32) * np.float32(M)), 0, M).astype(np.int64)
+    assert (f32 != np.array([want_above, want_below])).any()
