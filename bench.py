@@ -517,7 +517,8 @@ def alu_probes(stream):
     """Measured throughput (T op/s) of FP32 FMA, erfcf, ex2 and the Philox high multiply."""
     from paper_2512_09664_b300 import binding as B
     iters = {"fma": 4096, "erfc": 256, "ex2": 2048, "umulhi": 2048}
-    return {k: B.alu_probe(k, iters=n, reps=3, stream=stream) / 1e12 for k, n in iters.items()}
+    from paper_2512_09664_b300 import measure
+    return {k: measure.alu_probe(k, iters=n, reps=3, stream=stream) / 1e12 for k, n in iters.items()}
 
 
 def _e2e_serial_ms(r, flows_host, img_host, stream, steps):

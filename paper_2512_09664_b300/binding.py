@@ -27,9 +27,7 @@ _EXPORTS = ("synthpix_workspace_bytes", "synthpix_render_pairs", "synthpix_rende
             "synthpix_render_pairs_from", "synthpix_seed_particles", "synthpix_advect_particles",
             "synthpix_render_backward", "synthpix_autotune_tile", "synthpix_render_pairs_noalloc",
             "synthpix_fourier_flows", "synthpix_fourier_flows_workspace_bytes", "synthpix_match_histogram",
-            "synthpix_match_histogram_workspace_bytes", "synthpix_alu_probe_threads", "synthpix_alu_probe",
-            "synthpix_last_error", "synthpix_version")
-PROBE_KINDS = {"fma": 0, "erfc": 1, "ex2": 2, "umulhi": 3}
+            "synthpix_match_histogram_workspace_bytes", "synthpix_last_error", "synthpix_version")
 STAGES = ("plan", "seed_advect", "bin_scan", "bin_scatter", "splat_epilogue")
 
 
@@ -112,10 +110,6 @@ def lib():
         L.synthpix_match_histogram.argtypes = [C.POINTER(BatchDesc), C.POINTER(PairDesc), C.c_int32, vp, vp, vp, sz,
                                                vp]
         L.synthpix_match_histogram.restype = C.c_int
-        L.synthpix_alu_probe_threads.argtypes = []
-        L.synthpix_alu_probe_threads.restype = C.c_int64
-        L.synthpix_alu_probe.argtypes = [C.c_int32, C.c_int32, vp, C.c_int64, C.POINTER(C.c_int64), vp]
-        L.synthpix_alu_probe.restype = C.c_int
         L.synthpix_last_error.argtypes = []
         L.synthpix_last_error.restype = C.c_char_p
         L.synthpix_version.argtypes = []
@@ -271,31 +265,6 @@ def fourier_flows(modes_dev, flow_h: int, flow_w: int, height: int, width: int, 
                                       C.c_void_p(workspace_dev.data_ptr()),
                                       workspace_dev.numel() * workspace_dev.element_size(), C.c_void_p(st.cuda_stream))
     _check(rc)
-
-
-def alu_probe(kind: str, iters: int = 4096, reps: int = 3, stream=None) -> float:
-    """Best of `reps` timed synthpix_alu_probe launches: operations per second.
-
-    kind is one of PROBE_KINDS; the launches run on `stream` (default: the
-    current one) and are timed with CUDA events there (this synchronises).
-    """
-    import torch
-    st = stream if stream is not None else torch.cuda.current_stream()
-    n = lib().synthpix_alu_probe_threads()
-    if n <= 0:
-        _check(ECUDA)
-    sink = torch.empty(n, dtype=torch.float32, device=st.device)
-    ops = C.c_int64(0)
-    best = 0.0
-    for _ in range(reps + 1):  # the first launch is a warm-up
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        _check(lib().synthpix_alu_probe(PROBE_KINDS[kind], iters, C.c_void_p(sink.data_ptr()), n, C.byref(ops),
-                                        C.c_void_p(st.cuda_stream)))
-        e1.record(st)
-        e1.synchronize()
-        best = max(best, ops.value / (e0.elapsed_time(e1) * 1e-3))
-    return best
 
 
 def fourier_flows_workspace_bytes(n_flows: int, n_modes: int, flow_h: int, flow_w: int) -> int:

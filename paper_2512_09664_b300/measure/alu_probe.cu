@@ -6,19 +6,26 @@
 // latency; the grid is one full wave (up to 2048 threads per SM, as the
 // kernel's registers allow).  The caller times a
 // launch with CUDA events and divides the operation count it is given.
+//
+// This is measurement support for the benchmark, built into a library of its
+// own (libsynthpix_probe.so); it is no part of the rendering method nor of
+// the renderer's C ABI.
 #include <algorithm>
 #include <cstdint>
 #include <cstdio>
 
 #include <cuda_runtime.h>
 
-#include "synthpix.h"
-
-namespace spx {
-int set_error(int code, const char *msg);
-}
+#include "alu_probe.h"
 
 namespace {
+
+thread_local char g_probe_error[256] = "";
+
+int fail(int code, const char *what) {
+    snprintf(g_probe_error, sizeof(g_probe_error), "%s", what);
+    return code;
+}
 
 constexpr int kProbeThreads = 256;
 constexpr int kProbeCtasPerSm = 8;  // 2048 resident threads per SM
@@ -56,8 +63,6 @@ __global__ void __launch_bounds__(kProbeThreads) k_alu_probe(int32_t iters, floa
     sink[t] = s;
 }
 
-int fail(int code, const char *what) { return spx::set_error(code, what); }
-
 int sm_count() {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return -1;
@@ -94,20 +99,20 @@ extern "C" {
 int64_t synthpix_alu_probe_threads(void) {
     const int64_t n = probe_threads();
     if (n < 0) {
-        fail(SYNTHPIX_ECUDA, "alu probe: no current CUDA device");
+        fail(SYNTHPIX_PROBE_ECUDA, "alu probe: no current CUDA device");
         return 0;
     }
     return n;
 }
 
 int synthpix_alu_probe(int32_t kind, int32_t iters, float *sink, int64_t sink_elems, int64_t *ops, void *stream) {
-    if (kind < SYNTHPIX_PROBE_FMA || kind > SYNTHPIX_PROBE_UMULHI) return fail(SYNTHPIX_EINVAL, "alu probe: unknown kind");
-    if (iters < 1 || iters > kMaxIters) return fail(SYNTHPIX_EINVAL, "alu probe: iters outside 1..65536");
-    if (!ops) return fail(SYNTHPIX_EINVAL, "alu probe: ops is NULL");
-    if (!sink || ((uintptr_t)sink & 3)) return fail(SYNTHPIX_EINVAL, "alu probe: sink NULL or misaligned");
+    if (kind < SYNTHPIX_PROBE_FMA || kind > SYNTHPIX_PROBE_UMULHI) return fail(SYNTHPIX_PROBE_EINVAL, "alu probe: unknown kind");
+    if (iters < 1 || iters > kMaxIters) return fail(SYNTHPIX_PROBE_EINVAL, "alu probe: iters outside 1..65536");
+    if (!ops) return fail(SYNTHPIX_PROBE_EINVAL, "alu probe: ops is NULL");
+    if (!sink || ((uintptr_t)sink & 3)) return fail(SYNTHPIX_PROBE_EINVAL, "alu probe: sink NULL or misaligned");
     const int64_t n = probe_threads();
-    if (n <= 0) return fail(SYNTHPIX_ECUDA, "alu probe: no current CUDA device");
-    if (sink_elems < n) return fail(SYNTHPIX_EINVAL, "alu probe: sink smaller than synthpix_alu_probe_threads()");
+    if (n <= 0) return fail(SYNTHPIX_PROBE_ECUDA, "alu probe: no current CUDA device");
+    if (sink_elems < n) return fail(SYNTHPIX_PROBE_EINVAL, "alu probe: sink smaller than synthpix_alu_probe_threads()");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     int64_t launched = -1;
     switch (kind) {
@@ -116,15 +121,18 @@ int synthpix_alu_probe(int32_t kind, int32_t iters, float *sink, int64_t sink_el
     case SYNTHPIX_PROBE_EX2: launched = launch_probe<SYNTHPIX_PROBE_EX2>(iters, sink, st); break;
     default: launched = launch_probe<SYNTHPIX_PROBE_UMULHI>(iters, sink, st); break;
     }
-    if (launched <= 0) return fail(SYNTHPIX_ECUDA, "alu probe: occupancy query failed");
+    if (launched <= 0) return fail(SYNTHPIX_PROBE_ECUDA, "alu probe: occupancy query failed");
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         char msg[256];
         snprintf(msg, sizeof(msg), "alu probe launch: %s", cudaGetErrorString(e));
-        return fail(SYNTHPIX_ECUDA, msg);
+        return fail(SYNTHPIX_PROBE_ECUDA, msg);
     }
     *ops = launched * (int64_t)iters * kChains;
-    return spx::set_error(SYNTHPIX_OK, "");
+    g_probe_error[0] = 0;
+    return 0;
 }
+
+const char *synthpix_probe_last_error(void) { return g_probe_error; }
 
 }  // extern "C"

@@ -176,18 +176,21 @@ def test_binding_export_list_is_the_header():
 
 
 def test_alu_probe_validation_before_any_launch():
-    L = B.lib()
+    # the probes live in a measurement library of their own, not in the renderer's ABI
+    from paper_2512_09664_b300 import measure
+    assert not hasattr(B.lib(), "synthpix_alu_probe")
+    L = measure.lib()
     ops = C.c_int64(-1)
     sink = C.c_void_p(256)  # never dereferenced: every call below fails its argument checks first
-    assert L.synthpix_alu_probe(4, 16, sink, 1 << 20, C.byref(ops), None) == B.EINVAL
-    assert L.synthpix_alu_probe(-1, 16, sink, 1 << 20, C.byref(ops), None) == B.EINVAL
-    assert L.synthpix_alu_probe(0, 0, sink, 1 << 20, C.byref(ops), None) == B.EINVAL
-    assert L.synthpix_alu_probe(0, (1 << 16) + 1, sink, 1 << 20, C.byref(ops), None) == B.EINVAL
-    assert L.synthpix_alu_probe(0, 16, sink, 1 << 20, None, None) == B.EINVAL
-    assert L.synthpix_alu_probe(0, 16, None, 1 << 20, C.byref(ops), None) == B.EINVAL
-    assert L.synthpix_alu_probe(0, 16, C.c_void_p(258), 1 << 20, C.byref(ops), None) == B.EINVAL
+    assert L.synthpix_alu_probe(4, 16, sink, 1 << 20, C.byref(ops), None) == measure.EINVAL
+    assert L.synthpix_alu_probe(-1, 16, sink, 1 << 20, C.byref(ops), None) == measure.EINVAL
+    assert L.synthpix_alu_probe(0, 0, sink, 1 << 20, C.byref(ops), None) == measure.EINVAL
+    assert L.synthpix_alu_probe(0, (1 << 16) + 1, sink, 1 << 20, C.byref(ops), None) == measure.EINVAL
+    assert L.synthpix_alu_probe(0, 16, sink, 1 << 20, None, None) == measure.EINVAL
+    assert L.synthpix_alu_probe(0, 16, None, 1 << 20, C.byref(ops), None) == measure.EINVAL
+    assert L.synthpix_alu_probe(0, 16, C.c_void_p(258), 1 << 20, C.byref(ops), None) == measure.EINVAL
     assert ops.value == -1
-    assert "alu probe" in B.last_error()
+    assert "alu probe" in measure.last_error()
 
 
 def test_pack_keeps_flow_grids_on_even_floats_with_odd_w_grids():

@@ -14,7 +14,7 @@ def _need_cuda():
 def test_probe_rates_are_physical():
     import torch
 
-    from paper_2512_09664_b300 import binding as B
+    from paper_2512_09664_b300 import measure as B
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     # an upper bound no probe can pass: every FP32 lane busy every cycle at 2.2 GHz
     ceiling = sms * 128 * 2.2e9
