@@ -133,8 +133,8 @@ def algorithmic(wl):
     bytes: both output frames written once + the FP32 flow grid read once.
     lane-ops (minimum arithmetic of the method, an FMA counted once):
       per particle and frame: (6 E[d] + 4) window edges x 12 (one Phi value:
-      a degree-8 polynomial, the exp, scaling) + E[(3d + 1)^2] pixels x 2
-      (product and accumulation);
+      a cubic piece of the tabulated normal tail, its index and scaling) +
+      E[(3d + 1)^2] pixels x 2 (product and accumulation);
       per output pixel: illumination 1, noise 13 (a quarter of a 10-round
       Philox call at 4 ops per round plus half a Box-Muller pair),
       blur 2 (2R + 1), quantisation 2.

@@ -310,9 +310,18 @@ int synthpix_render_pairs_staged(const synthpix_batch_desc *batch, const synthpi
  *  - A batch that needs more scratch than the array holds (compare
  *    synthpix_workspace_bytes) is rejected with SYNTHPIX_EWORKSPACE and a
  *    message, before anything is launched.
+ *  - The scratch needed is that of the plan the render runs: the tile edge
+ *    batch->tile, or for 0 the default edge the render picks (so a batch can
+ *    fit here although synthpix_workspace_bytes, which for tile 0 covers
+ *    every edge the autotuner tries, reports more).
  *  - The first call on a device looks up the array's device address on that
  *    device (cudaGetSymbolAddress with the device current) and caches it;
  *    make that first call on each device before any stream capture.
+ *  - The cached address belongs to the device's context at the time of the
+ *    first call.  A device reset (cudaDeviceReset) after that call is not
+ *    supported: the next call would use a stale address.  Reset devices only
+ *    before the first call, or not at all in a process that uses this entry
+ *    point.
  *  - All calls share the one array, which keeps the last call's contents;
  *    the call clears what must start at zero itself.  Calls whose work
  *    overlaps on the GPU (other streams, other host threads) race on the

@@ -501,4 +501,16 @@ int set_error(int code, const char *msg) {
     return code;
 }
 
+// Workspace bytes of the plan synthpix_render_pairs runs for this batch, with
+// the tile edge it resolves (batch->tile, or the default edge for 0), in
+// *need; SYNTHPIX_OK, or the plan's error status with its message set.
+int render_workspace_need(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs, int32_t n_pairs,
+                          size_t *need) {
+    Plan P;
+    const int rc = make_plan(batch, pairs, n_pairs, P);
+    if (rc) return rc;
+    *need = n_pairs > 0 ? P.L.total : 0;
+    return SYNTHPIX_OK;
+}
+
 }  // namespace spx

@@ -16,6 +16,8 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[SYNTHPIX_NOALLO
 
 namespace spx {
 int set_error(int code, const char *msg);
+int render_workspace_need(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs, int32_t n_pairs,
+                          size_t *need);
 }
 
 namespace {
@@ -57,11 +59,13 @@ int scratch_address(void **out) {
 extern "C" int synthpix_render_pairs_noalloc(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
                                              const synthpix_pair_desc *pairs_dev, int32_t n_pairs,
                                              const float *flows, void *images, void *stream) {
-    // validation and the scratch size come from the host descriptors alone
-    const size_t need = synthpix_workspace_bytes(batch, pairs, n_pairs);
-    if (need == 0 && n_pairs != 0)  // invalid descriptors: report them with their own status code
-        return synthpix_render_pairs(batch, pairs, pairs_dev, n_pairs, flows, images, nullptr, 0, stream);
-    if (n_pairs == 0) return SYNTHPIX_OK;
+    // validation and the scratch size come from the host descriptors alone: the
+    // plan of the tile edge the render itself resolves (batch->tile, or the
+    // default edge for 0), checked the way the render checks it
+    size_t need = 0;
+    const int prc = spx::render_workspace_need(batch, pairs, n_pairs, &need);
+    if (prc != SYNTHPIX_OK) return prc;  // invalid descriptors: the plan's own status and message
+    if (n_pairs == 0) return spx::set_error(SYNTHPIX_OK, "");
     if (need > (size_t)SYNTHPIX_NOALLOC_SCRATCH_BYTES) {
         char msg[256];
         snprintf(msg, sizeof(msg),

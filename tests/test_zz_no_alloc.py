@@ -39,6 +39,32 @@ def test_noalloc_rejects_batches_larger_than_its_scratch():
     assert _fn()(C.byref(pk.batch), pk.pairs, None, pk.n_pairs, FAKE, FAKE, None) == B.EINVAL
 
 
+def test_noalloc_sizes_its_check_from_the_tile_the_render_runs():
+    # tile 0: synthpix_workspace_bytes covers every edge the autotuner tries
+    # (tile 16 has the most bin counters), more than the 32 MiB array; the
+    # render itself runs the default edge (128 at 512 x 512), which fits.  The
+    # size check must pass; without a GPU the call then stops at the device
+    # query, never at the size check.
+    import torch
+    pk = B.pack(W.batch_512_u8(n_pairs=4))
+    assert pk.batch.tile == 0
+    assert B.workspace_bytes(pk) > SCRATCH_BYTES
+    assert B.workspace_bytes(B.pack(W.batch_512_u8(n_pairs=4), tile=128)) <= SCRATCH_BYTES
+    if torch.cuda.is_available():
+        pytest.skip("checks the size decision without launching; a GPU would render here")
+    rc = _fn()(C.byref(pk.batch), pk.pairs, None, pk.n_pairs, FAKE, FAKE, None)
+    assert rc == B.ECUDA and "scratch" not in B.last_error()
+
+
+def test_noalloc_reports_invalid_descriptors_with_the_plans_message():
+    pk = B.pack(W.batch_512_u8(n_pairs=2))
+    pk.pairs[1].d_min = -1.0
+    rc = _fn()(C.byref(pk.batch), pk.pairs, None, pk.n_pairs, FAKE, FAKE, None)
+    assert rc == B.EINVAL
+    msg = B.last_error()
+    assert "pair 1" in msg and "workspace" not in msg
+
+
 @pytest.mark.gpu
 def test_noalloc_matches_workspace_entry_point_on_two_calls_in_a_row():
     import torch
