@@ -43,7 +43,7 @@ SM_COUNT = 148
 FP32_LANES_PER_SM = 128
 
 # ncu DRAM traffic of k_splat per launch (bytes), with the sha256 of the
-# kernel source (splat.cu) it was taken on; reported only while the source is
+# kernel source (splat.cuh) it was taken on; reported only while the source is
 # unchanged.
 SPLAT_TRAFFIC = {"sha256": "e92f3479fde2cebde48a920373d5551e09ca782b859075574e646ca456048203",
                  "bytes_per_launch": 49466368 + 7684608,
@@ -296,7 +296,7 @@ def run_reference(args, rank, world):
 # ----------------------------------------------------------------------------
 
 def splat_source_hash():
-    with open(os.path.join(ROOT, "paper_2512_09664_b300", "csrc", "splat.cu"), "rb") as f:
+    with open(os.path.join(ROOT, "paper_2512_09664_b300", "csrc", "splat.cuh"), "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()
 
 

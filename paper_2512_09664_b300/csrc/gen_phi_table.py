@@ -83,7 +83,7 @@ def write(path=os.path.join(HERE, "phi_table.cuh")):
              f"constexpr int kPhiPieces = {N_PIECES};", f"constexpr int kPhiDegree = {DEGREE};",
              f"constexpr float kPhiPerUnit = {float(PIECES_PER_UNIT):.1f}f;",
              f"constexpr float kPhiTMax = {T_MAX:.1f}f;",
-             f"__device__ __constant__ float kPhiTable[{(DEGREE + 1) * N_PIECES}] = {{"]
+             f"static __device__ __constant__ float kPhiTable[{(DEGREE + 1) * N_PIECES}] = {{"]
     for k in range(N_PIECES):
         vals = ", ".join(f"{float(v):.9e}f" for v in table[k])
         lines.append(f"    {vals},")

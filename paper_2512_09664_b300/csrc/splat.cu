@@ -1,1663 +1,30 @@
-// The splat + epilogue of the PIV image-pair renderer (SynthPix, arXiv
-// 2512.09664, Section 2): Eq. 1 integrated over each pixel and summed over
-// the particles ("aggregation of the particle contributions"), then the
-// imaging steps named in the Abstract (illumination non-uniformity, noise,
-// blur) and quantisation.
-//
-// k_splat is persistent: each CTA takes (pair, frame, tile) work items from a
-// ticket counter (atomicAdd, no waiting on other CTAs) and, while it renders
-// one item, stages the next item's descriptor, plan, blur taps and binned
-// particle records into shared memory with cp.async.  An item renders the
-// tile plus the blur halo into an on-chip fixed-point accumulator, finishes
-// it, and writes every output pixel of the tile once.
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
-
-#include "common.cuh"
-#include "kernels.cuh"
-#include "particle.cuh"
-#include "phi_table.cuh"
+// Dispatch of the splat launch by output type (the kernels of each type are
+// instantiated in splat_<type>.cu from splat.cuh) and the splat's shared
+// memory size.
+#include "splat.cuh"
 
 namespace spx {
-
-// ---------------------------------------------------------------------------
-// asynchronous copies into shared memory
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-
-// descriptor, plan and blur taps (128 B) of a pair, in 16-byte copies
-__device__ __forceinline__ void stage_header(const KernelArgs &a, int pair, unsigned char *buf) {
-    constexpr int kD = kStageDesc / 16, kP = kStagePlan / 16, kH = kStageHeader / 16;
-    const int t = threadIdx.x;
-    if (t < kH) {
-        const unsigned char *src;
-        if (t < kD) src = reinterpret_cast<const unsigned char *>(a.descs + pair) + 16 * t;
-        else if (t < kP) src = reinterpret_cast<const unsigned char *>(a.plan + pair) + 16 * (t - kD);
-        else src = reinterpret_cast<const unsigned char *>(a.blur_w + (int64_t)pair * kBlurStride) + 16 * (t - kP);
-        cp_async16(buf + 16 * t, src);
-    }
-}
-
-// records [first, first + n) of the bins (RS bytes each), copied in 16-byte
-// chunks from the 16-byte boundary at or below the first record: record k of
-// the span lands at dst + lead + RS k with lead = (RS first) mod 16.
-template <int RS>
-__device__ __forceinline__ void stage_records(const KernelArgs &a, int64_t first, uint32_t n, unsigned char *dst) {
-    const int64_t start = first * (int64_t)RS;
-    const int64_t astart = start & ~(int64_t)15;
-    const int64_t nbytes = (start - astart) + (int64_t)n * (int64_t)RS;
-    const int nchunks = (int)((nbytes + 15) >> 4);
-    const unsigned char *base = reinterpret_cast<const unsigned char *>(a.rec) + astart;
-    for (int c = threadIdx.x; c < nchunks; c += blockDim.x) cp_async16(dst + 16 * c, base + 16 * c);
-}
-
-template <int RS>
-__device__ __forceinline__ int record_lead(int64_t first) { return (int)((first * (int64_t)RS) & 15); }
-
-// ---------------------------------------------------------------------------
-// exact fixed-point accumulation
-// ---------------------------------------------------------------------------
-// A contribution v = mx * my * amp (at most i_max: the pixel mass of a unit
-// Gaussian is at most 1 / (sqrt(2 pi) sigma)) is rounded once to an integer
-// number of units q = i_max 2^-26 and added to the pixel's 32-bit word with
-// one shared-memory atomic.  Integer addition is associative: a pixel's
-// value does not depend on the order of its contributions, the tile size or
-// the batch it is rendered in.
-//
-// A word holds 64 i_max.  Before a chunk of visits is splatted, the visits
-// of the item so far are counted per 8 x 8 block of the accumulator; while
-// no block is met by more than 63 visits, no pixel sum can reach 2^32 units
-// and the adds go unchecked.  Otherwise the chunk takes the checked path:
-// the thread whose add wraps a word adds 1 to the pixel's carry word (worth
-// 2^32 units), so no sum is ever lost.
-constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
-constexpr int32_t kMagicBits = 0x4B400000;
-constexpr float kFixedScale = 67108864.0f;      // 2^26 units per i_max
-constexpr float kFixedUnit = 1.0f / 67108864.0f;
-constexpr float kWrapValue = 4294967296.0f;     // 2^32: the weight of a carry
-constexpr uint32_t kSafeVisits = 63;            // visits per block that cannot wrap a word
-constexpr int kBlkShift = 3;                    // 8 x 8 pixel blocks
-constexpr int kBlkSide = 24;                    // blocks per side of the counter grid (row pitch <= 192)
-
-// Tile geometry of one work item.  The accumulator and the finishing buffer A
-// share memory: the full halo rectangle [x0 - R, x1 + R) x [y0 - R, y1 + R)
-// from column afx0 (x0 - R rounded down to a multiple of 4) with row pitch AP,
-// so quads of 4 pixels are 16-byte aligned.  Particles are splatted into its
-// part inside the frame, the halo-widened rectangle clipped to the frame
-// (from column ax0, ex0 rounded down to a multiple of 4, P columns); the first
-// finishing pass turns those words into A in place, and the pixels outside
-// the frame take replicated border values.
-struct Geo {
-    int32_t W, H;
-    int32_t x0, x1, y0, y1;      // tile pixels [x0, x1) x [y0, y1)
-    int32_t ex0, ex1, ey0, ey1;  // halo-widened rectangle clipped to the frame
-    int32_t EW, EH;              // its width and height
-    int32_t R;                   // blur radius
-    int32_t ax0, P;              // accumulator: first column, row pitch
-    int32_t fx0, fy0, FW, FH;    // full halo rectangle (may leave the frame)
-    int32_t afx0, AP;            // accumulator = finishing buffer: first column, row pitch
-    int32_t aoff;                // index of (ey0, ax0) in it (rows from fy0, columns from afx0)
-};
-
-// Visit classes of the splat's sort (see splat_chunk): windows of at most
-// 2 (c + 1) pixels a side for c < kWideClass, wider ones in kWideClass;
-// 32 accumulator-bank buckets per class.
-constexpr int kNarrowMax = 16;
-constexpr int kWideClass = kNarrowMax / 2;
-constexpr int kBuckets = (kWideClass + 1) * 32;
-
-// Sort and work-queue state of a k_splat CTA (static shared memory).
-__shared__ uint32_t sh_cnt[kBuckets];              // visits of the chunk per (class, bank) key
-__shared__ uint32_t sh_off[kBuckets + 1];          // their exclusive offsets
-__shared__ uint32_t sh_next;                       // warp-slot ticket of the chunk's render
-__shared__ uint32_t sh_slot_end[kWideClass + 1];   // slots of the classes, widest first: cumulative ends
-__shared__ uint32_t sh_blk[kBlkSide * kBlkSide];  // visits of the item so far per 8 x 8 block
-__shared__ int sh_checked;                         // the chunk takes the checked path
-__shared__ int sh_carry_clean;                     // the item's carry words are zero
-__shared__ int sh_wrap;                            // a checked add wrapped a word in this item
-
-// The tile's accumulator as the splat sees it.
-struct Acc {
-    uint32_t *acc;    // [rows][P] words in shared memory
-    uint32_t *carry;  // the CTA's carry words in global memory, same indices
-    int P;
-};
-
-// Add one contribution to the word at w (a pixel of A).
-template <bool CHECKED>
-__device__ __forceinline__ void add_contrib(uint32_t *w, const Acc &A, float mx, float my) {
-    const uint32_t l = __float2uint_rn(__fmul_rn(mx, my));
-    if (!CHECKED) {
-        atomicAdd(w, l);
-        return;
-    }
-    const uint32_t old = atomicAdd(w, l);
-    if (old + l < old) {
-        atomicAdd(A.carry + (w - A.acc), 1u);
-        sh_wrap = 1;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// pixel integration of Eq. 1
-// ---------------------------------------------------------------------------
-// Upper normal tail Q(a) = erfc(a / sqrt 2) / 2 for a >= 0 from the cubic
-// table (one float4 per piece, staged in shared memory).  a is clamped to
-// the table's end (Q(8) = 6e-16); the piece is k = rint(16 a), so
-// s = a - k / 16 is exact and |s| <= 1/32.
-__device__ __forceinline__ float phi_tail(float a, const float4 *tab) {
-    a = fminf(a, kPhiTMax);
-    const float kf = fmaf(a, kPhiPerUnit, kMagic);
-    const int k = __float_as_int(kf) - kMagicBits;
-    const float s = fmaf(__fsub_rn(kf, kMagic), -1.0f / kPhiPerUnit, a);
-    const float4 c = tab[k];
-    return fmaf(fmaf(fmaf(c.w, s, c.z), s, c.y), s, c.x);
-}
-
-// Edge value of a pixel edge at offset dd = edge - particle centre (pixels):
-// the lower tail Phi(t), t = dd / sigma, for dd < 0, and minus the upper tail
-// -(1 - Phi(t)) for dd >= +0, so both tails keep their absolute accuracy.
-// Q never reaches 0 on the table (Q(8) > 0), so the sign bit of the value
-// tells the side of the centre.
-__device__ __forceinline__ float edge_value_tab(float dd, float inv, const float4 *tab) {
-    const float q = phi_tail(fabsf(__fmul_rn(dd, inv)), tab);
-    return __int_as_float(__float_as_int(q) ^ (~__float_as_int(dd) & (int)0x80000000));
-}
-
-// Mass of the unit Gaussian between two pixel edges from their edge values:
-// Phi(b) - Phi(a) = sb - sa, plus 1 when the centre lies between them (sa on
-// the lower side, sb on the upper side).
-__device__ __forceinline__ float edge_mass(float sa, float sb) {
-    const int across = (__float_as_int(sb) & ~__float_as_int(sa)) >> 31;  // -1 or 0
-    return fmaxf(__fadd_rn(__fsub_rn(sb, sa), __int_as_float(across & 0x3F800000)), 0.0f);
-}
-
-// One particle's visit of a tile, set up for the splat (same size as a
-// Record, written over the staged records it comes from).
-struct Visit {
-    float px, py;    // fractions of the split position
-    float inv;       // 1 / sigma
-    float amps;      // amplitude * 2^26 / i_max (fixed-point units)
-    int32_t base;    // accumulator index of the clipped window's first pixel
-    uint32_t shape;  // bx | by << 8 (int8: window start - integer position) | nx << 16 | ny << 24
-};
-static_assert(sizeof(Visit) == sizeof(Record), "Visit layout");
-
-__device__ __forceinline__ int visit_bx(uint32_t s) { return (int)(int8_t)(s & 0xFFu); }
-__device__ __forceinline__ int visit_by(uint32_t s) { return (int)(int8_t)((s >> 8) & 0xFFu); }
-__device__ __forceinline__ int visit_nx(uint32_t s) { return (int)((s >> 16) & 0xFFu); }
-__device__ __forceinline__ int visit_ny(uint32_t s) { return (int)(s >> 24); }
-
-// Visits are sorted by (class, accumulator bank) before the splat.  Class
-// c < 8 holds windows of at most N = 2 (c + 1) pixels a side; each is
-// rendered by a group of U = class_lanes(c) adjacent lanes (splat_group):
-// the lanes share the N + 1 x edges and take RG = class_rows(c) rows each.
-// Class 8 holds the wider windows, rendered by a whole warp per visit, four
-// visits per warp slot (more slots spread the long wide visits over the
-// warps: with 32 per slot a few warps held them all while the rest waited
-// at the chunk's barrier); its slots come first and are rendered by a loop of
-// their own, so the narrow classes' loop keeps its registers.  The visits of one warp are spread over the bank
-// order, so their accumulator addresses fall in different banks.
-__host__ __device__ constexpr int class_lanes(int c) { return c < 2 ? 1 : 2; }
-// log2 of the visits one warp slot of class c renders (32 / lanes per visit; 4 for the wide class)
-__host__ __device__ constexpr int class_slot_shift(int c) { return c >= 8 ? 2 : (c < 2 ? 5 : 4); }
-__host__ __device__ constexpr int class_rows(int c) { return c == 0 ? 2 : (c == 1 ? 4 : c + 1); }
-
-// Quotient of small non-negative integers a / b (a < 2^20, 1 <= b <= 2^10)
-// from b's reciprocal: (a + 1/2) / b is at least 1/(2b) away from an integer,
-// far more than the rounding error of the product.
-__device__ __forceinline__ int small_div(int a, float inv_b) { return (int)(((float)a + 0.5f) * inv_b); }
-
-// One visit per group of U lanes, window at most N x N.  Lane j of the group
-// evaluates the x edges e = j + U k and the masses that start there; the
-// group exchanges them by shuffles, then lane j renders rows
-// [j RG, j RG + RG) of the window.  All lanes of the warp take part (the
-// shuffles); lanes of an empty visit add nothing.
-template <int N, int U, int RG>
-__device__ __forceinline__ void splat_group(const Visit &v, const Acc &A, const float4 *tab) {
-    static_assert(U * RG >= N, "rows of a window");
-    constexpr int EPL = (N + U) / U;  // ceil((N + 1) / U) x edges per lane
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31, j = lane & (U - 1), gbase = lane & ~(U - 1);
-    const int nx = visit_nx(v.shape), ny = visit_ny(v.shape);
-    const float fbx = (float)(visit_bx(v.shape) + j);
-    float ev[EPL];
-#pragma unroll
-    for (int k = 0; k < EPL; ++k) ev[k] = edge_value_tab(__fsub_rn(__fadd_rn(fbx, (float)(U * k)), v.px), v.inv, tab);
-    float m[EPL];
-#pragma unroll
-    for (int k = 0; k < EPL; ++k) {
-        float nb;
-        if (U == 1) {
-            nb = ev[k + 1 < EPL ? k + 1 : k];
-        } else {
-            const float a = __shfl_sync(FULL, ev[k], lane + 1);                  // edge e + 1 of lanes j < U - 1
-            const float b = __shfl_sync(FULL, ev[k + 1 < EPL ? k + 1 : k], gbase);  // of lane U - 1
-            nb = j == U - 1 ? b : a;
-        }
-        m[k] = edge_mass(ev[k], nb);
-    }
-    float mx[N];
-#pragma unroll
-    for (int e = 0; e < N; ++e) mx[e] = U == 1 ? m[e] : __shfl_sync(FULL, m[e / U], gbase + e % U);
-    const int r0 = j * RG;
-    const int rows = min(max(ny - r0, 0), RG);
-    const float fby = (float)(visit_by(v.shape) + r0);
-    float ey = edge_value_tab(__fsub_rn(fby, v.py), v.inv, tab);
-    uint32_t *hr = A.acc + v.base + r0 * A.P;
-#pragma unroll 1  // a rolled row loop keeps the class templates small enough for the instruction cache
-    for (int q = 0; q < RG; ++q) {
-        const float en = edge_value_tab(__fsub_rn(__fadd_rn(fby, (float)(q + 1)), v.py), v.inv, tab);
-        const float my = __fmul_rn(edge_mass(ey, en), v.amps);
-        ey = en;
-        if (q < rows) {
-#pragma unroll
-            for (int c = 0; c < N; ++c)
-                if (c < nx) add_contrib<false>(hr + c, A, mx[c], my);
-        }
-        hr += A.P;
-    }
-}
-
-// Windows with more edges than lanes (out of line: the inlined renders keep
-// their registers).  Up to 64 edges: two per lane, entries k = lane and
-// k = lane + 32 of the x edges 0..nx followed by the y edges 0..ny; lane c
-// owns columns c and c + 32 and walks the rows, each row's mass broadcast by
-// one shuffle.  Wider windows: per-warp scratch in shared memory.
-template <bool CHECKED>
-__device__ __noinline__ void splat_particle_wide(const Acc A, float px, float py, float inv,
-                                                 float amps, int32_t base, int bx, int by, int nx, int ny,
-                                                 float *scr, int wq, const float4 *tab) {
-    const int lane = threadIdx.x & 31;
-    if (nx + ny + 2 <= 64) {
-        const unsigned FULL = 0xffffffffu;
-        auto edge = [&](int k) {
-            const float dd = k <= nx ? __fsub_rn((float)(bx + k), px) : __fsub_rn((float)(by + k - nx - 1), py);
-            return k < nx + ny + 2 ? edge_value_tab(dd, inv, tab) : 0.0f;
-        };
-        const float e0 = edge(lane), e1 = edge(lane + 32);
-        const float e1l0 = __shfl_sync(FULL, e1, 0);
-        float n0 = __shfl_down_sync(FULL, e0, 1);
-        if (lane == 31) n0 = e1l0;
-        const float n1 = __shfl_down_sync(FULL, e1, 1);
-        float m0 = edge_mass(e0, n0), m1 = edge_mass(e1, n1);
-        if (lane > nx) m0 = __fmul_rn(m0, amps);  // row masses carry the amplitude
-        if (lane + 32 > nx) m1 = __fmul_rn(m1, amps);
-        uint32_t *col = A.acc + base + lane;
-        for (int r = 0; r < ny; ++r) {
-            const int k = nx + 1 + r;  // uniform across the warp
-            const float my = k < 32 ? __shfl_sync(FULL, m0, k) : __shfl_sync(FULL, m1, k - 32);
-            if (lane < nx) add_contrib<CHECKED>(col + r * A.P, A, m0, my);
-            if (lane + 32 < nx) add_contrib<CHECKED>(col + r * A.P + 32, A, m1, my);
-        }
-        return;
-    }
-    float *exe = scr, *eye = scr + wq, *ex = scr + 2 * wq, *ey = scr + 3 * wq;
-    for (int e = lane; e <= nx; e += 32) exe[e] = edge_value_tab(__fsub_rn((float)(bx + e), px), inv, tab);
-    for (int e = lane; e <= ny; e += 32) eye[e] = edge_value_tab(__fsub_rn((float)(by + e), py), inv, tab);
-    __syncwarp();
-    for (int e = lane; e < nx; e += 32) ex[e] = edge_mass(exe[e], exe[e + 1]);
-    for (int e = lane; e < ny; e += 32) ey[e] = __fmul_rn(edge_mass(eye[e], eye[e + 1]), amps);
-    __syncwarp();
-    const int n = nx * ny;
-    const float invx = 1.0f / (float)nx;
-    for (int m = lane; m < n; m += 32) {
-        const int r = min((int)(((float)m + 0.5f) * invx), ny - 1);
-        const int cc = m - r * nx;
-        if ((unsigned)cc >= (unsigned)nx) continue;
-        add_contrib<CHECKED>(A.acc + base + r * A.P + cc, A, ex[cc], ey[r]);
-    }
-    __syncwarp();
-}
-
-// Wide visits, a warp per visit: lanes [0, nx] evaluate the x edges, lanes
-// [nx+1, nx+ny+1] the y edges; each lane then takes one column and every
-// rpr-th row of the window.  Windows with more edges than lanes go through
-// splat_particle_wide.
-template <bool CHECKED>
-__device__ __forceinline__ void splat_coop(const Visit &v, bool valid, const Acc &A, float *scr,
-                                           int wq, const float4 *tab) {
-    const int lane = threadIdx.x & 31;
-    const unsigned FULL = 0xffffffffu;
-    uint32_t todo = __ballot_sync(FULL, valid);
-    while (todo) {
-        const int src = __ffs(todo) - 1;
-        todo &= todo - 1;
-        const float px = __shfl_sync(FULL, v.px, src), py = __shfl_sync(FULL, v.py, src);
-        const float inv = __shfl_sync(FULL, v.inv, src), amps = __shfl_sync(FULL, v.amps, src);
-        const int32_t base = __shfl_sync(FULL, v.base, src);
-        const uint32_t shape = __shfl_sync(FULL, v.shape, src);
-        const int nx = visit_nx(shape), ny = visit_ny(shape), bx = visit_bx(shape), by = visit_by(shape);
-        if (nx + ny + 2 > 32) {
-            splat_particle_wide<CHECKED>(A, px, py, inv, amps, base, bx, by, nx, ny, scr, wq, tab);
-            continue;
-        }
-        const int nxe = nx + 1;
-        const bool isx = lane < nxe;
-        const int e = isx ? lane : lane - nxe;
-        const float dd = __fsub_rn((float)((isx ? bx : by) + e), isx ? px : py);
-        const float ev = lane < nxe + ny + 1 ? edge_value_tab(dd, inv, tab) : 0.0f;
-        const float evn = __shfl_down_sync(FULL, ev, 1);
-        float m = edge_mass(ev, evn);
-        if (!isx) m = __fmul_rn(m, amps);
-        // lane -> (row offset lr, column lc); rpr rows per round
-        const float invn = __frcp_rn((float)nx);
-        const int rpr = small_div(32, invn);
-        const int lr = small_div(lane, invn);
-        const int lc = lane - lr * nx;
-        const float exv = __shfl_sync(FULL, m, lc);
-        const bool act = lr < rpr;
-        uint32_t *dst = A.acc + base + lr * A.P + lc;
-        for (int r0 = 0; r0 < ny; r0 += rpr) {
-            const int r = r0 + lr;
-            const float eyv = __shfl_sync(FULL, m, nxe + min(r, ny - 1));
-            if (act && r < ny) add_contrib<CHECKED>(dst + r0 * A.P, A, exv, eyv);
-        }
-    }
-}
-
-
-// Splat n staged records (at recs) into the tile's accumulator:
-//   A. each thread sets up its records' visits (window clipped to the halo
-//      rectangle), takes a slot in its (class, bank) bucket and counts the
-//      visit in the 8 x 8 blocks its window meets;
-//   B. warp 0 scans the bucket counts and decides from the block counts
-//      whether the chunk's adds must be checked for wrapping;
-//   C. the visits are written in key order over the staged records (out);
-//   D. warps claim slots of 32 visits, widest class first, and render them
-//      (checked: every visit by a whole warp, with checked adds).
-template <int NT>
-__device__ __forceinline__ void splat_chunk(const unsigned char *recs, unsigned char *out, uint32_t n, const Geo &g,
-                                            float scale, const Acc &acc, float *scr,
-                                            int wq, const float4 *tab) {
-    constexpr int RPT = (rec_cap(NT >= 512 ? kRecBufBytesLarge : kRecBufBytes) + NT - 1) / NT;
-    const int lane = threadIdx.x & 31;
-    const unsigned FULL = 0xffffffffu;
-    Visit v[RPT];
-    int key[RPT];
-    uint32_t slot[RPT];
-#pragma unroll
-    for (int q = 0; q < RPT; ++q) {
-        const uint32_t k = threadIdx.x + (uint32_t)q * NT;
-        key[q] = -1;
-        slot[q] = 0;
-        if (k < n) {
-            const unsigned char *rp = recs + (size_t)k * sizeof(Record);
-            const float2 pf = *reinterpret_cast<const float2 *>(rp);
-            const int2 pi = *reinterpret_cast<const int2 *>(rp + 8);
-            const float2 ps = *reinterpret_cast<const float2 *>(rp + 16);
-            const float r15 = 6.0f * ps.x;  // 1.5 d
-            const int32_t j0 = max(pi.x + (int32_t)floorf(pf.x - r15), g.ex0);
-            const int32_t j1 = min(pi.x + (int32_t)floorf(pf.x + r15), g.ex1 - 1);
-            const int32_t i0 = max(pi.y + (int32_t)floorf(pf.y - r15), g.ey0);
-            const int32_t i1 = min(pi.y + (int32_t)floorf(pf.y + r15), g.ey1 - 1);
-            if (j0 <= j1 && i0 <= i1) {
-                const int nx = j1 - j0 + 1, ny = i1 - i0 + 1;
-                v[q].px = pf.x;
-                v[q].py = pf.y;
-                v[q].inv = __frcp_rn(ps.x);
-                v[q].amps = ps.y * scale;
-                v[q].base = (i0 - g.fy0) * g.AP + (j0 - g.afx0);
-                v[q].shape = ((uint32_t)(j0 - pi.x) & 0xFFu) | (((uint32_t)(i0 - pi.y) & 0xFFu) << 8) |
-                             ((uint32_t)nx << 16) | ((uint32_t)ny << 24);
-                const int m = max(nx, ny);
-                const int cls = m > kNarrowMax ? kWideClass : (m - 1) >> 1;
-                key[q] = cls * 32 + (v[q].base & 31);
-                slot[q] = atomicAdd(sh_cnt + key[q], 1u);
-                const int bx0 = (j0 - g.afx0) >> kBlkShift, bx1 = (j1 - g.afx0) >> kBlkShift;
-                const int by0 = (i0 - g.fy0) >> kBlkShift, by1 = (i1 - g.fy0) >> kBlkShift;
-                for (int by = by0; by <= by1; ++by)
-                    for (int bx = bx0; bx <= bx1; ++bx) atomicAdd(sh_blk + by * kBlkSide + bx, 1u);
-            }
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        constexpr int PER = kBuckets / 32;
-        uint32_t c[PER], sum = 0;
-#pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            c[j] = sh_cnt[lane * PER + j];
-            sh_cnt[lane * PER + j] = 0;
-            sum += c[j];
-        }
-        uint32_t incl = sum;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t t = __shfl_up_sync(FULL, incl, d);
-            if (lane >= d) incl += t;
-        }
-        uint32_t run = incl - sum;
-#pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            sh_off[lane * PER + j] = run;
-            run += c[j];
-        }
-        if (lane == 31) sh_off[kBuckets] = incl;
-        if (lane == 0) sh_next = 0;
-        __syncwarp();
-        // warp slots per class (widest first) and their cumulative ends
-        uint32_t nsl = 0;
-        if (lane <= kWideClass) {
-            const int cc = kWideClass - lane;
-            const uint32_t G = sh_off[32 * cc + 32] - sh_off[32 * cc];
-            const int sh = class_slot_shift(cc);
-            nsl = (G + (1u << sh) - 1u) >> sh;
-        }
-#pragma unroll
-        for (int d = 1; d < 16; d <<= 1) {
-            const uint32_t t = __shfl_up_sync(FULL, nsl, d);
-            if (lane >= d) nsl += t;
-        }
-        if (lane <= kWideClass) sh_slot_end[lane] = nsl;
-        uint32_t mx = 0;
-#pragma unroll
-        for (int j = 0; j < kBlkSide * kBlkSide / 32; ++j) mx = max(mx, sh_blk[lane + 32 * j]);
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) mx = max(mx, __shfl_xor_sync(FULL, mx, d));
-        if (lane == 0) sh_checked = mx > kSafeVisits ? 1 : 0;
-    }
-    __syncthreads();
-    float2 *o8 = reinterpret_cast<float2 *>(out);  // 16-byte aligned; a Visit is three 8-byte words
-    const bool chk = sh_checked != 0;
-    if (chk && !sh_carry_clean) {  // the item's first checked chunk: clear the CTA's carry words
-        uint4 *cw = reinterpret_cast<uint4 *>(acc.carry);
-        for (int k = threadIdx.x; k < (g.FH * g.AP) >> 2; k += blockDim.x) cw[k] = make_uint4(0u, 0u, 0u, 0u);
-    }
-#pragma unroll
-    for (int q = 0; q < RPT; ++q) {
-        if (key[q] >= 0) {
-            const uint32_t p = sh_off[key[q]] + slot[q];
-            o8[3 * p] = make_float2(v[q].px, v[q].py);
-            o8[3 * p + 1] = make_float2(v[q].inv, v[q].amps);
-            o8[3 * p + 2] = make_float2(__int_as_float(v[q].base), __uint_as_float(v[q].shape));
-        }
-    }
-    __syncthreads();
-    if (chk) {  // dense item: a warp per visit, adds checked for wrapping
-        if (threadIdx.x == 0) sh_carry_clean = 1;  // read again after this chunk's last barrier
-        const uint32_t total = sh_off[kBuckets];
-        for (;;) {
-            uint32_t sl = 0;
-            if (lane == 0) sl = atomicAdd(&sh_next, 1u);
-            sl = __shfl_sync(FULL, sl, 0);
-            if (sl * 32 >= total) break;
-            const uint32_t idx = sl * 32 + lane;
-            const bool valid = idx < total;
-            Visit e;
-            e.px = e.py = e.inv = e.amps = 0.0f;
-            e.base = 0;
-            e.shape = 0;
-            if (valid) {
-                const float2 a = o8[3 * idx], b = o8[3 * idx + 1], d = o8[3 * idx + 2];
-                e.px = a.x;
-                e.py = a.y;
-                e.inv = b.x;
-                e.amps = b.y;
-                e.base = __float_as_int(d.x);
-                e.shape = __float_as_uint(d.y);
-            }
-            splat_coop<true>(e, valid, acc, scr, wq, tab);
-        }
-        return;
-    }
-    const uint32_t total_slots = sh_slot_end[kWideClass];
-    const uint32_t my_end = lane <= kWideClass ? sh_slot_end[lane] : 0xffffffffu;
-    const uint32_t wide_end = sh_slot_end[0];  // the wide class's slots come first
-    auto claim = [&]() {
-        uint32_t t = 0;
-        if (lane == 0) t = atomicAdd(&sh_next, 1u);
-        return __shfl_sync(FULL, t, 0);
-    };
-    uint32_t sl = claim();
-    {  // the wide class: a warp per visit, four visits per slot
-        const uint32_t g0 = sh_off[32 * kWideClass], G = sh_off[32 * kWideClass + 32] - g0;
-        for (; sl < wide_end; sl = claim()) {
-            const uint32_t idx = (sl << class_slot_shift(kWideClass)) + lane;
-            const bool valid = lane < (1 << class_slot_shift(kWideClass)) && idx < G;
-            Visit e;
-            e.px = e.py = e.inv = e.amps = 0.0f;
-            e.base = 0;
-            e.shape = 0;
-            if (valid) {
-                const float2 a = o8[3 * (g0 + idx)], b = o8[3 * (g0 + idx) + 1], d = o8[3 * (g0 + idx) + 2];
-                e.px = a.x;
-                e.py = a.y;
-                e.inv = b.x;
-                e.amps = b.y;
-                e.base = __float_as_int(d.x);
-                e.shape = __float_as_uint(d.y);
-            }
-            splat_coop<false>(e, valid, acc, scr, wq, tab);
-        }
-    }
-    for (; sl < total_slots; sl = claim()) {
-        // the slot's class: the first (widest-first) class whose slots end beyond sl
-        const int o = __ffs(__ballot_sync(FULL, sl < my_end)) - 1;
-        const int c = kWideClass - o;
-        const uint32_t sc = sl - (o ? __shfl_sync(FULL, my_end, o - 1) : 0u);  // slot within the class
-        const uint32_t g0 = sh_off[32 * c], G = sh_off[32 * c + 32] - g0;
-        const int csh = class_slot_shift(c);
-        const uint32_t nw = (G + (1u << csh) - 1u) >> csh;  // slots of the class
-        // group q of U lanes takes visit sc + q nw (spread over the bank order)
-        const uint32_t idx = sc + (uint32_t)(lane >> (5 - csh)) * nw;
-        const bool valid = idx < G;
-        Visit e;
-        if (valid) {
-            const float2 a = o8[3 * (g0 + idx)], b = o8[3 * (g0 + idx) + 1], d = o8[3 * (g0 + idx) + 2];
-            e.px = a.x;
-            e.py = a.y;
-            e.inv = b.x;
-            e.amps = b.y;
-            e.base = __float_as_int(d.x);
-            e.shape = __float_as_uint(d.y);
-        } else {
-            e.px = e.py = e.inv = e.amps = 0.0f;
-            e.base = 0;
-            e.shape = 0;
-        }
-        switch (c) {
-        case 0: splat_group<2, class_lanes(0), class_rows(0)>(e, acc, tab); break;
-        case 1: splat_group<4, class_lanes(1), class_rows(1)>(e, acc, tab); break;
-        case 2: splat_group<6, class_lanes(2), class_rows(2)>(e, acc, tab); break;
-        case 3: splat_group<8, class_lanes(3), class_rows(3)>(e, acc, tab); break;
-        case 4: splat_group<10, class_lanes(4), class_rows(4)>(e, acc, tab); break;
-        case 5: splat_group<12, class_lanes(5), class_rows(5)>(e, acc, tab); break;
-        case 6: splat_group<14, class_lanes(6), class_rows(6)>(e, acc, tab); break;
-        default: splat_group<16, class_lanes(7), class_rows(7)>(e, acc, tab); break;
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// general particle shapes (Eq. 1 with sigma_x != sigma_y or rho != 0)
-// ---------------------------------------------------------------------------
-// The 4-node Gauss-Legendre rule on [-1, 1]: nodes +-0.8611363115940526 and
-// +-0.3399810435848563 (the roots of P_4), weights 0.3478548451374538 and
-// 0.6521451548625461.
-
-// rho = 0 (axis-aligned ellipse), a warp per visit: lanes [0, nx] evaluate
-// the x edges (1 / sigma_x), lanes [nx + 1, nx + ny + 1] the y edges
-// (1 / sigma_y), then the lanes take the window's pixels 32 at a time and
-// fetch their column and row masses by shuffles.  Windows with more edges
-// than lanes evaluate both masses per pixel.
-template <bool CHECKED>
-__device__ __forceinline__ void splat_general_sep(const RecordG &r, int32_t j0, int32_t i0, int nx, int ny,
-                                                  float amps, uint32_t *w0, const Acc &acc, const float4 *tab) {
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const float isx = 1.0f / r.sx, isy = 1.0f / r.sy;
-    const int npx = nx * ny;
-    const float invn = __frcp_rn((float)nx);
-    // an edge's offset from the centre: (edge - integer part) - fraction, one rounding, so the
-    // values do not depend on where the tile clips the window
-    if (nx + ny + 2 <= 32) {
-        const bool isx_lane = lane <= nx;
-        const int e = isx_lane ? lane : lane - (nx + 1);
-        const float dd = isx_lane ? __fsub_rn((float)(j0 + e - r.ix), r.fx) : __fsub_rn((float)(i0 + e - r.iy), r.fy);
-        const float ev = lane <= nx + ny + 1 ? edge_value_tab(dd, isx_lane ? isx : isy, tab) : 0.0f;
-        float m = edge_mass(ev, __shfl_down_sync(FULL, ev, 1));
-        if (!isx_lane) m = __fmul_rn(m, amps);
-        for (int b = 0; b < npx; b += 32) {
-            const int p = min(b + lane, npx - 1);
-            const int rr = small_div(p, invn), cc = p - rr * nx;
-            const float mx = __shfl_sync(FULL, m, cc), my = __shfl_sync(FULL, m, nx + 1 + rr);
-            if (b + lane < npx) add_contrib<CHECKED>(w0 + rr * acc.P + cc, acc, mx, my);
-        }
-        return;
-    }
-    for (int p = lane; p < npx; p += 32) {
-        const int rr = small_div(p, invn), cc = p - rr * nx;
-        const int jc = j0 + cc - r.ix, ir = i0 + rr - r.iy;
-        const float mx = edge_mass(edge_value_tab(__fsub_rn((float)jc, r.fx), isx, tab),
-                                   edge_value_tab(__fsub_rn((float)(jc + 1), r.fx), isx, tab));
-        const float my = edge_mass(edge_value_tab(__fsub_rn((float)ir, r.fy), isy, tab),
-                                   edge_value_tab(__fsub_rn((float)(ir + 1), r.fy), isy, tab));
-        add_contrib<CHECKED>(w0 + rr * acc.P + cc, acc, mx, __fmul_rn(my, amps));
-    }
-}
-
-// rho != 0, a warp per visit.  The pixel's probability is the x-marginal
-// times the conditional mass of y (normal, mean rho sigma_y u / sigma_x at
-// offset u, std sigma_y sqrt(1 - rho^2)), exact in y and integrated in x by
-// the 4-node Gauss-Legendre rule on M equal sub-intervals of the pixel.  The
-// Q = 4 M nodes of a window column go to a group of G = min(Q, 32) lanes
-// (Q / G nodes each); walking down the column, each lane carries its nodes'
-// last edge value to the next row, and the group sums the row's node masses
-// by shuffles.
-template <int M, bool CHECKED>
-__device__ __forceinline__ void splat_general_corr(const RecordG &r, int32_t j0, int32_t i0, int nx, int ny,
-                                                   float amps, uint32_t *w0, const Acc &acc, const float4 *tab) {
-    constexpr int Q = 4 * M, G = Q < 32 ? Q : 32, L = Q / G, CPP = 32 / G;
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31, gl = lane & (G - 1), gc = lane / G;
-    const float c = sqrtf(1.0f - r.rho * r.rho);
-    const float isx = 1.0f / r.sx, is = 1.0f / (r.sy * c), k = r.rho * r.sy * isx;
-    constexpr float h = 1.0f / (float)M;
-    const float wscale = 0.5f * h * isx * 0.39894228040143267794f * amps;  // h/2, 1/(sqrt(2 pi) sigma_x), units
-    // this lane's nodes: offsets within the pixel and weights (same for every column)
-    float du[L], wq[L];
-#pragma unroll
-    for (int t = 0; t < L; ++t) {
-        const int n = gl + G * t, g4 = n & 3;
-        const float xg = g4 == 0 ? -0.8611363115940526f : g4 == 1 ? -0.3399810435848563f
-                       : g4 == 2 ? 0.3399810435848563f : 0.8611363115940526f;
-        du[t] = h * ((float)(n >> 2) + 0.5f * (xg + 1.0f));
-        wq[t] = (g4 == 0 || g4 == 3) ? 0.3478548451374538f : 0.6521451548625461f;
-    }
-    for (int c0 = 0; c0 < nx; c0 += CPP) {
-        const int col = c0 + gc;
-        const bool live = col < nx;
-        // offsets from the centre formed from exact integers (one rounding each), so the
-        // values do not depend on where the tile clips the window
-        const float ul = __fsub_rn((float)(j0 + col - r.ix), r.fx);  // the column's left edge
-        const float fy = r.fy;
-        float wn[L], mu[L], ev[L];
-#pragma unroll
-        for (int t = 0; t < L; ++t) {
-            const float u = __fadd_rn(ul, du[t]);
-            const float tt = u * isx;
-            wn[t] = live ? wq[t] * __expf(-0.5f * tt * tt) * wscale : 0.0f;
-            mu[t] = k * u;  // conditional mean of y at this node
-            ev[t] = edge_value_tab(__fsub_rn(__fsub_rn((float)(i0 - r.iy), fy), mu[t]), is, tab);
-        }
-        uint32_t *wc = w0 + col;
-#pragma unroll 1
-        for (int rr = 0; rr < ny; ++rr) {
-            float v = 0.0f;
-            const float ye = __fsub_rn((float)(i0 + rr + 1 - r.iy), fy);  // the row's lower edge
-#pragma unroll
-            for (int t = 0; t < L; ++t) {
-                const float en = edge_value_tab(__fsub_rn(ye, mu[t]), is, tab);
-                v = fmaf(wn[t], edge_mass(ev[t], en), v);
-                ev[t] = en;
-            }
-#pragma unroll
-            for (int o = G >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-            if (gl == 0 && live) add_contrib<CHECKED>(wc + rr * acc.P, acc, v, 1.0f);
-        }
-    }
-}
-
-// rho != 0 with windows at most 32 / S columns wide: the same quadrature,
-// S lanes per (column, chunk of rows), each lane summing Q / S <= 8 of the
-// Q = 4 M nodes (consecutive ones, in node order).  The window's columns
-// repeat floor(32 / (S nx)) times across the warp, each copy taking its own
-// chunk of rows; walking down its rows a lane carries its nodes' last edge
-// values, the S partial sums meet by butterfly shuffles, and the column's
-// first lane adds the pixel.  A pixel's value depends only on its offset
-// from the particle, not on the tile's clipping of the window nor on the
-// lanes that compute it.
-template <int M, int S, bool CHECKED>
-__device__ __forceinline__ void splat_general_corr_cols(const RecordG &r, int32_t j0, int32_t i0, int nx, int ny,
-                                                        float amps, uint32_t *w0, const Acc &acc,
-                                                        const float4 *tab) {
-    constexpr int Q = 4 * M, QL = Q / S;
-    static_assert(QL >= 1 && QL <= 8 && (S & (S - 1)) == 0, "at most 8 nodes per lane");
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const int span = S * nx;       // lanes of one copy of the window's columns (<= 32)
-    const int nch = 32 / span;     // copies across the warp, each with its chunk of rows
-    const int chunk = lane / span, within = lane - chunk * span;
-    const int col = within / S, sub = within & (S - 1);
-    const int rpc = (ny + nch - 1) / nch;  // rows per chunk (the loop below is warp-uniform)
-    const bool live = chunk < nch;
-    const int r0 = chunk * rpc;
-    const float c = sqrtf(1.0f - r.rho * r.rho);
-    const float isx = 1.0f / r.sx, is = 1.0f / (r.sy * c), k = r.rho * r.sy * isx;
-    constexpr float h = 1.0f / (float)M;
-    const float wscale = 0.5f * h * isx * 0.39894228040143267794f * amps;  // h/2, 1/(sqrt(2 pi) sigma_x), units
-    // offsets from the centre formed from exact integers (one rounding each)
-    const float ul = __fsub_rn((float)(j0 + col - r.ix), r.fx);  // the column's left edge
-    const float yt = __fsub_rn((float)(i0 + r0 - r.iy), r.fy);   // the top edge of the chunk's first row
-    float wn[QL], mu[QL], ev[QL];
-#pragma unroll
-    for (int q = 0; q < QL; ++q) {
-        const int t = sub * QL + q, g4 = t & 3;
-        const float xg = g4 == 0 ? -0.8611363115940526f : g4 == 1 ? -0.3399810435848563f
-                       : g4 == 2 ? 0.3399810435848563f : 0.8611363115940526f;
-        const float wgt = (g4 == 0 || g4 == 3) ? 0.3478548451374538f : 0.6521451548625461f;
-        const float u = __fadd_rn(ul, h * ((float)(t >> 2) + 0.5f * (xg + 1.0f)));
-        const float tt = u * isx;
-        wn[q] = wgt * __expf(-0.5f * tt * tt) * wscale;
-        mu[q] = k * u;  // conditional mean of y at this node
-        ev[q] = edge_value_tab(__fsub_rn(yt, mu[q]), is, tab);
-    }
-    uint32_t *wc = w0 + col;
-#pragma unroll 1
-    for (int i = 0; i < rpc; ++i) {
-        const int rr = r0 + i;
-        const float ye = __fsub_rn((float)(i0 + rr + 1 - r.iy), r.fy);  // the row's lower edge
-        float v = 0.0f;
-#pragma unroll
-        for (int q = 0; q < QL; ++q) {
-            const float en = edge_value_tab(__fsub_rn(ye, mu[q]), is, tab);
-            v = fmaf(wn[q], edge_mass(ev[q], en), v);
-            ev[q] = en;
-        }
-#pragma unroll
-        for (int o = S >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-        if (live && sub == 0 && rr < ny) add_contrib<CHECKED>(wc + rr * acc.P, acc, v, 1.0f);
-    }
-}
-
-// Sub-intervals of the x quadrature of a correlated particle: a power of two
-// no smaller than 1 / min(sigma_x, sigma_x sqrt(1 - rho^2) / |rho|) (the
-// integrand's shortest x-scale; quadrature error below 1e-7 of I0), at most 64.
-__device__ __forceinline__ int corr_subintervals(float sx, float rho) {
-    const float c = sqrtf(1.0f - rho * rho);
-    const float ell = fabsf(rho) > c ? sx * c / fabsf(rho) : sx;
-    const int m = min(max((int)ceilf(1.0f / ell), 1), 64);
-    return 1 << (32 - __clz(m - 1));  // next power of two (1 stays 1)
-}
-
-template <bool CHECKED>
-__device__ __forceinline__ void splat_general_visit(const RecordG &r, int32_t j0, int32_t i0, int nx, int ny,
-                                                    float amps, uint32_t *w0, const Acc &acc, const float4 *tab) {
-    if (r.rho == 0.0f) {
-        splat_general_sep<CHECKED>(r, j0, i0, nx, ny, amps, w0, acc, tab);
-        return;
-    }
-    const int m = corr_subintervals(r.sx, r.rho);
-    if (m <= 8) {
-        // lanes per column: at most 8 nodes per lane; the particle's unclipped window
-        // width (not the tile's clipping of it) decides, so every tile renders it the same way
-        const int lpc = m <= 2 ? 1 : m / 2;
-        const float r15x = 6.0f * r.sx;
-        const int width = (int)floorf(r.fx + r15x) - (int)floorf(r.fx - r15x) + 1;
-        if (width * lpc <= 32) {
-            switch (m) {
-            case 1: splat_general_corr_cols<1, 1, CHECKED>(r, j0, i0, nx, ny, amps, w0, acc, tab); break;
-            case 2: splat_general_corr_cols<2, 1, CHECKED>(r, j0, i0, nx, ny, amps, w0, acc, tab); break;
-            case 4: splat_general_corr_cols<4, 2, CHECKED>(r, j0, i0, nx, ny, amps, w0, acc, tab); break;
-            default: splat_general_corr_cols<8, 4, CHECKED>(r, j0, i0, nx, ny, amps, w0, acc, tab); break;
-            }
-            return;
-        }
-    }
-    switch (m) {
-    case 1: splat_general_corr<1, CHECKED>(r, j0, i0, nx, ny, amps, w0, acc, tab); break;
-    case 2: splat_general_corr<2, CHECKED>(r, j0, i0, nx, ny, amps, w0, acc, tab); break;
-    case 4: splat_general_corr<4, CHECKED>(r, j0, i0, nx, ny, amps, w0, acc, tab); break;
-    case 8: splat_general_corr<8, CHECKED>(r, j0, i0, nx, ny, amps, w0, acc, tab); break;
-    case 16: splat_general_corr<16, CHECKED>(r, j0, i0, nx, ny, amps, w0, acc, tab); break;
-    case 32: splat_general_corr<32, CHECKED>(r, j0, i0, nx, ny, amps, w0, acc, tab); break;
-    default: splat_general_corr<64, CHECKED>(r, j0, i0, nx, ny, amps, w0, acc, tab); break;
-    }
-}
-
-// A general record's window clipped to the tile's halo rectangle (empty: j0 > j1).
-__device__ __forceinline__ void general_window(const RecordG &r, const Geo &g, int32_t &j0, int32_t &j1, int32_t &i0,
-                                               int32_t &i1) {
-    const float r15x = 6.0f * r.sx, r15y = 6.0f * r.sy;  // 1.5 d, 1.5 d_y
-    j0 = max(r.ix + (int32_t)floorf(r.fx - r15x), g.ex0);
-    j1 = min(r.ix + (int32_t)floorf(r.fx + r15x), g.ex1 - 1);
-    i0 = max(r.iy + (int32_t)floorf(r.fy - r15y), g.ey0);
-    i1 = min(r.iy + (int32_t)floorf(r.fy + r15y), g.ey1 - 1);
-}
-
-// Splat n staged general records:
-//   A. each thread counts its records' windows in the 8 x 8 blocks they meet
-//      (the item's counts so far, as in splat_chunk);
-//   B. warp 0 decides whether the chunk's adds must be checked for wrapping;
-//   C. warps take records from a shared counter, a warp per record.
-__device__ __forceinline__ void splat_chunk_general(const unsigned char *recs, uint32_t n, const Geo &g, float scale,
-                                                    const Acc &acc, const float4 *tab) {
-    const RecordG *R = reinterpret_cast<const RecordG *>(recs);
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    for (uint32_t k = threadIdx.x; k < n; k += blockDim.x) {
-        int32_t j0, j1, i0, i1;
-        general_window(R[k], g, j0, j1, i0, i1);
-        if (j0 > j1 || i0 > i1) continue;
-        const int bx0 = (j0 - g.afx0) >> kBlkShift, bx1 = (j1 - g.afx0) >> kBlkShift;
-        const int by0 = (i0 - g.fy0) >> kBlkShift, by1 = (i1 - g.fy0) >> kBlkShift;
-        for (int by = by0; by <= by1; ++by)
-            for (int bx = bx0; bx <= bx1; ++bx) atomicAdd(sh_blk + by * kBlkSide + bx, 1u);
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        uint32_t mx = 0;
-#pragma unroll
-        for (int j = 0; j < kBlkSide * kBlkSide / 32; ++j) mx = max(mx, sh_blk[lane + 32 * j]);
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) mx = max(mx, __shfl_xor_sync(FULL, mx, d));
-        if (lane == 0) {
-            sh_checked = mx > kSafeVisits ? 1 : 0;
-            sh_next = 0;
-        }
-    }
-    __syncthreads();
-    const bool chk = sh_checked != 0;
-    if (chk) {
-        if (!sh_carry_clean) {  // the item's first checked chunk: clear the CTA's carry words
-            uint4 *cw = reinterpret_cast<uint4 *>(acc.carry);
-            for (int k = threadIdx.x; k < (g.FH * g.AP) >> 2; k += blockDim.x) cw[k] = make_uint4(0u, 0u, 0u, 0u);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) sh_carry_clean = 1;  // read again only after the chunk's last barrier
-    }
-    for (;;) {
-        uint32_t k = 0;
-        if (lane == 0) k = atomicAdd(&sh_next, 1u);
-        k = __shfl_sync(FULL, k, 0);
-        if (k >= n) break;
-        const RecordG r = R[k];
-        int32_t j0, j1, i0, i1;
-        general_window(r, g, j0, j1, i0, i1);
-        if (j0 > j1 || i0 > i1) continue;
-        uint32_t *w0 = acc.acc + (i0 - g.fy0) * acc.P + (j0 - g.afx0);
-        const float amps = r.amp * scale;
-        if (chk) splat_general_visit<true>(r, j0, i0, j1 - j0 + 1, i1 - i0 + 1, amps, w0, acc, tab);
-        else splat_general_visit<false>(r, j0, i0, j1 - j0 + 1, i1 - i0 + 1, amps, w0, acc, tab);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// epilogue helpers
-// ---------------------------------------------------------------------------
-
-// -2 ln u for u = uo24(w) = ((w >> 8) + 1) 2^-24 in (0, 1].  With x = 1 - u
-// (exact in FP32): for x < 2^-8 the series -ln(1 - x) = x + x^2/2 + x^3/3 +
-// x^4/4 (truncation below 1e-10 relative); otherwise -2 ln 2 log2(u) from
-// the hardware base-2 logarithm, whose absolute error (about 2^-22 on
-// log2) is then at most 3e-5 of the result, i.e. below 2e-6 on the normal
-// deviate (and below 5e-8 of full scale at a noise sigma of 0.02).
-__device__ __forceinline__ float neg2_log_uo24(uint32_t w) {
-    const float u = uo24f(w);
-    const float x = 1.0f - u;
-    const float series = 2.0f * x * fmaf(x, fmaf(x, fmaf(x, 0.25f, 1.0f / 3.0f), 0.5f), 1.0f);
-    const float viaLog2 = -1.38629436111989061883f * __log2f(u);  // -2 ln 2 log2(u)
-    return x < 0.00390625f ? series : viaLog2;
-}
-
-// Box-Muller pair from two Philox words: r = sqrt(-2 ln u), theta = 2 pi v,
-// evaluated as -r (cos, sin)(theta - pi) so the fast sine and cosine work on
-// [-pi, pi).
-__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float &n0, float &n1) {
-    const float x = neg2_log_uo24(wa);
-    const float r = x > 0.0f ? x * rsqrtf(x) : 0.0f;
-    float s, c;
-    __sincosf(6.28318530717958647692f * (u24f(wb) - 0.5f), &s, &c);
-    n0 = -r * c;
-    n1 = -r * s;
-}
-
-template <typename T>
-struct Out;
-template <>
-struct Out<float> {
-    static __device__ __forceinline__ float cvt(float v) { return v; }
-    static __device__ __forceinline__ void store4(float *p, const float *v) {
-        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
-    }
-};
-template <>
-struct Out<__half> {
-    static __device__ __forceinline__ __half cvt(float v) { return __float2half_rn(v); }
-    static __device__ __forceinline__ void store4(__half *p, const float *v) {
-        __half2 a = __floats2half2_rn(v[0], v[1]), b = __floats2half2_rn(v[2], v[3]);
-        uint2 u;
-        u.x = *reinterpret_cast<unsigned *>(&a);
-        u.y = *reinterpret_cast<unsigned *>(&b);
-        *reinterpret_cast<uint2 *>(p) = u;
-    }
-};
-template <>
-struct Out<__nv_bfloat16> {
-    static __device__ __forceinline__ __nv_bfloat16 cvt(float v) { return __float2bfloat16_rn(v); }
-    static __device__ __forceinline__ void store4(__nv_bfloat16 *p, const float *v) {
-        __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]), b = __floats2bfloat162_rn(v[2], v[3]);
-        uint2 u;
-        u.x = *reinterpret_cast<unsigned *>(&a);
-        u.y = *reinterpret_cast<unsigned *>(&b);
-        *reinterpret_cast<uint2 *>(p) = u;
-    }
-};
-template <>
-struct Out<uint8_t> {
-    static __device__ __forceinline__ uint8_t cvt(float v) { return (uint8_t)v; }
-    static __device__ __forceinline__ void store4(uint8_t *p, const float *v) {
-        *reinterpret_cast<uchar4 *>(p) = make_uchar4((uint8_t)v[0], (uint8_t)v[1], (uint8_t)v[2], (uint8_t)v[3]);
-    }
-};
-template <>
-struct Out<uint16_t> {
-    static __device__ __forceinline__ uint16_t cvt(float v) { return (uint16_t)v; }
-    static __device__ __forceinline__ void store4(uint16_t *p, const float *v) {
-        *reinterpret_cast<ushort4 *>(p) =
-            make_ushort4((uint16_t)v[0], (uint16_t)v[1], (uint16_t)v[2], (uint16_t)v[3]);
-    }
-};
-
-// Store up to 4 consecutive outputs of a row (quantised when M > 0).
-template <typename T>
-struct IsCode {
-    static constexpr bool value = false;
-};
-template <>
-struct IsCode<uint8_t> {
-    static constexpr bool value = true;
-};
-template <>
-struct IsCode<uint16_t> {
-    static constexpr bool value = true;
-};
-
-template <typename T>
-__device__ __forceinline__ void store_group(T *o, float *v, int nvalid, float M) {
-    if constexpr (IsCode<T>::value) {
-        if (M > 0.0f) {
-            // Q = clamp(rint(B M), 0, M): the conversion rounds half to even and
-            // takes negative values (and NaN) to 0
-            const uint32_t Mi = (uint32_t)M;
-            uint32_t q[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) q[j] = min(__float2uint_rn(v[j] * M), Mi);
-            if (nvalid == 4 && (reinterpret_cast<uintptr_t>(o) % (4 * sizeof(T))) == 0) {
-                if (sizeof(T) == 1)
-                    *reinterpret_cast<uint32_t *>(o) = q[0] | (q[1] << 8) | (q[2] << 16) | (q[3] << 24);
-                else
-                    *reinterpret_cast<uint2 *>(o) = make_uint2(q[0] | (q[1] << 16), q[2] | (q[3] << 16));
-            } else {
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (j < nvalid) o[j] = (T)q[j];
-            }
-            return;
-        }
-    }
-    if (M > 0.0f) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) v[j] = fminf(fmaxf(rintf(v[j] * M), 0.0f), M);
-    }
-    if (nvalid == 4 && (reinterpret_cast<uintptr_t>(o) % (4 * sizeof(T))) == 0) {
-        Out<T>::store4(o, v);
-    } else {
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (j < nvalid) o[j] = Out<T>::cvt(v[j]);
-    }
-}
-
-// Horizontal pass (rows of the full halo rectangle, tile columns) and
-// vertical pass with store; taps w[|k|], k = -R..R, replicate border already
-// materialised in A.  R is a compile-time radius (0 < R <= 6).  Tiles start
-// on multiples of 4, so the tile's first input column x0 - R sits
-// OFF = (-R) mod 4 columns into A's 16-byte aligned rows, and its first
-// output column at CB = OFF + R, a multiple of 4.
-//
-// The horizontal pass works in place: a warp takes whole rows (32 / G rows
-// of G output quads per pass), its lanes read their inputs, the warp
-// synchronises, and the lanes write their outputs over the row at CB.  No
-// other warp reads those rows in that pass except past the row's end, which
-// feeds only outputs beyond the tile.
-template <typename T, int R>
-__device__ __forceinline__ void blur_store(const Geo &g, float *A, const float *w, T *out, float M) {
-    constexpr int OFF = (4 - R % 4) % 4;
-    constexpr int CB = OFF + R;
-    const int TW = g.x1 - g.x0, TH = g.y1 - g.y0;
-    const int G = (TW + 3) >> 2;  // output quads per row (<= 32: tiles are at most 128 wide)
-    float wr[R + 1];
-#pragma unroll
-    for (int k = 0; k <= R; ++k) wr[k] = w[k];
-    constexpr int NV = (OFF + 4 + 2 * R + 3) / 4;  // float4 loads covering the 4 + 2R inputs
-    const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    const int rpp = 32 / G;                       // rows per warp pass
-    const int lr = small_div(lane, 1.0f / (float)G), lg = lane - lr * G;
-    for (int rb = (threadIdx.x >> 5) * rpp; rb < g.FH; rb += nwarps * rpp) {
-        const int r = rb + lr;
-        const bool on = lr < rpp && r < g.FH;
-        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (on) {
-            const float4 *row = reinterpret_cast<const float4 *>(A + r * g.AP + 4 * lg);
-            float v[4 * NV];
-#pragma unroll
-            for (int q = 0; q < NV; ++q) {
-                const float4 t = row[q];
-                v[4 * q] = t.x;
-                v[4 * q + 1] = t.y;
-                v[4 * q + 2] = t.z;
-                v[4 * q + 3] = t.w;
-            }
-            float *op = &o.x;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                float acc = wr[0] * v[OFF + j + R];
-#pragma unroll
-                for (int k = 1; k <= R; ++k) acc = fmaf(wr[k], v[OFF + j + R - k] + v[OFF + j + R + k], acc);
-                op[j] = acc;
-            }
-        }
-        __syncwarp();  // the warp's rows are read before they are overwritten
-        if (on) *reinterpret_cast<float4 *>(A + r * g.AP + CB + 4 * lg) = o;
-    }
-    __syncthreads();
-    const float iG = 1.0f / (float)G;
-    const int p4 = g.AP >> 2;
-    for (int it = threadIdx.x; it < TH * G; it += blockDim.x) {
-        const int r = small_div(it, iG), c0 = (it - r * G) * 4;
-        const float4 *col = reinterpret_cast<const float4 *>(A + CB + c0);
-        const float4 m0 = col[(r + R) * p4];
-        float v[4] = {wr[0] * m0.x, wr[0] * m0.y, wr[0] * m0.z, wr[0] * m0.w};
-#pragma unroll
-        for (int k = 1; k <= R; ++k) {
-            const float4 a = col[(r + R - k) * p4], b = col[(r + R + k) * p4];
-            v[0] = fmaf(wr[k], a.x + b.x, v[0]);
-            v[1] = fmaf(wr[k], a.y + b.y, v[1]);
-            v[2] = fmaf(wr[k], a.z + b.z, v[2]);
-            v[3] = fmaf(wr[k], a.w + b.w, v[3]);
-        }
-        store_group<T>(out + r * g.W + c0, v, min(4, TW - c0), M);
-    }
-}
-
-// Any radius (slow path for R > 6), same arithmetic.
-template <typename T>
-__device__ __noinline__ void blur_store_any(const Geo &g, const float *A, float *Bh, int BP, const float *w, T *out,
-                                            float M) {
-    const int R = g.R, TW = g.x1 - g.x0, TH = g.y1 - g.y0;
-    const int cx = g.fx0 - g.afx0 + R;  // A column of the tile's first column
-    for (int it = threadIdx.x; it < g.FH * TW; it += blockDim.x) {
-        const int r = it / TW, c = it - r * TW;
-        const float *row = A + r * g.AP + cx + c;
-        float acc = w[0] * row[0];
-        for (int k = 1; k <= R; ++k) acc = fmaf(w[k], row[-k] + row[k], acc);
-        Bh[r * BP + c] = acc;
-    }
-    __syncthreads();
-    for (int it = threadIdx.x; it < TH * TW; it += blockDim.x) {
-        const int r = it / TW, c = it - r * TW;
-        const float *col = Bh + (r + R) * BP + c;
-        float acc = w[0] * col[0];
-        for (int k = 1; k <= R; ++k) acc = fmaf(w[k], col[-k * BP] + col[k * BP], acc);
-        float v[4] = {acc, 0.f, 0.f, 0.f};
-        store_group<T>(out + r * g.W + c, v, 1, M);
-    }
-}
-
-// R = 0: A's first column is the tile's first column (x0 is a multiple of 4).
-template <typename T>
-__device__ __forceinline__ void store_unblurred(const Geo &g, const float *A, T *out, float M) {
-    const int TW = g.x1 - g.x0, TH = g.y1 - g.y0;
-    const int G = (TW + 3) >> 2;
-    const float iG = 1.0f / (float)G;
-    for (int it = threadIdx.x; it < TH * G; it += blockDim.x) {
-        const int r = small_div(it, iG), c0 = (it - r * G) * 4;
-        const float4 t = *reinterpret_cast<const float4 *>(A + r * g.AP + c0);
-        float v[4] = {t.x, t.y, t.z, t.w};
-        store_group<T>(out + r * g.W + c0, v, min(4, TW - c0), M);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// one work item
-// ---------------------------------------------------------------------------
-struct Smem {
-    uint32_t *acc;    // accumulator words; A (floats) in the same memory after the first finishing pass
-    uint32_t *carry;  // the CTA's carry words (global memory)
-    float *A, *Bh, *sx2, *sy2, *scr;
-    const float4 *phi;
-    int BP;
-};
-
-__device__ __forceinline__ Geo make_geo(const synthpix_pair_desc &D, const PairPlan &pl, int tile_edge, int tile,
-                                        int halo) {
-    Geo g;
-    g.W = D.width;
-    g.H = D.height;
-    const int ty = tile / pl.tiles_x, tx = tile - ty * pl.tiles_x;
-    g.R = pl.blur_r;
-    g.x0 = tx * tile_edge;
-    g.x1 = min(g.x0 + tile_edge, g.W);
-    g.y0 = ty * tile_edge;
-    g.y1 = min(g.y0 + tile_edge, g.H);
-    g.ex0 = max(g.x0 - halo, 0);
-    g.ex1 = min(g.x1 + halo, g.W);
-    g.ey0 = max(g.y0 - halo, 0);
-    g.ey1 = min(g.y1 + halo, g.H);
-    g.EW = g.ex1 - g.ex0;
-    g.EH = g.ey1 - g.ey0;
-    g.ax0 = g.ex0 & ~3;
-    g.P = (g.ex1 - g.ax0 + 3) & ~3;
-    g.fx0 = g.x0 - g.R;
-    g.fy0 = g.y0 - g.R;
-    g.FW = (g.x1 - g.x0) + 2 * g.R;
-    g.FH = (g.y1 - g.y0) + 2 * g.R;
-    g.afx0 = g.fx0 & ~3;  // rounds down for negative columns too (two's complement)
-    g.AP = (g.x1 + g.R - g.afx0 + 3) & ~3;
-    g.aoff = (g.ey0 - g.fy0) * g.AP + (g.ax0 - g.afx0);
-    return g;
-}
-
-// separable illumination factors sin^2: columns [ax0, ax0 + P) and rows
-// [ey0, ey1) of the accumulator rectangle
-__device__ __forceinline__ bool illum_factors(const Geo &g, const synthpix_pair_desc &D, const Smem &s) {
-    const bool illum = D.illum_min != 1.0f || D.illum_max != 1.0f;
-    if (illum) {
-        for (int k = threadIdx.x; k < g.P + g.EH; k += blockDim.x) {
-            if (k < g.P) {
-                const float sv = sinpif(((float)(g.ax0 + k) + 0.5f) / (float)g.W);
-                s.sx2[k] = sv * sv;
-            } else {
-                const float sv = sinpif(((float)(g.ey0 + k - g.P) + 0.5f) / (float)g.H);
-                s.sy2[k - g.P] = sv * sv;
-            }
-        }
-    }
-    return illum;
-}
-
-// S of the fused path: the accumulator words, each cleared for the next
-// item as it is read.  r: accumulator row, c: column from ax0 (a multiple
-// of 4 for quad()).  When an add wrapped a word, the words were first
-// converted to S in place (float bits), carries included (wrapped_to_float).
-struct AccSource {
-    uint32_t *acc;
-    int P;
-    float unit;   // i_max 2^-26
-    bool floats;  // the words hold S as float bits
-    __device__ __forceinline__ float value(uint32_t v) const { return floats ? __uint_as_float(v) : (float)v * unit; }
-    __device__ __forceinline__ float4 quad(int r, int c) const {
-        uint4 *p = reinterpret_cast<uint4 *>(acc + r * P + c);
-        const uint4 v = *p;
-        *p = make_uint4(0u, 0u, 0u, 0u);
-        return make_float4(value(v.x), value(v.y), value(v.z), value(v.w));
-    }
-    __device__ __forceinline__ float pixel(int r, int c) const {
-        uint32_t *p = acc + r * P + c;
-        const uint32_t v = *p;
-        *p = 0u;
-        return value(v);
-    }
-};
-
-// A wrapped item: S = (word + carry 2^32) q written over the words, before
-// the finishing buffer (which holds the carry words) is written.  Ends with
-// a barrier.
-__device__ __forceinline__ void wrapped_to_float(const Smem &s, const Geo &g, float unit) {
-    const float ip = 1.0f / (float)g.P;
-    for (int k = threadIdx.x; k < g.EH * g.P; k += blockDim.x) {
-        const int r = small_div(k, ip), i = g.aoff + r * g.AP + (k - r * g.P);
-        s.acc[i] = __float_as_uint(fmaf((float)s.carry[i], kWrapValue, (float)s.acc[i]) * unit);
-    }
-    __syncthreads();
-}
-
-template <typename I>
-__device__ __forceinline__ float4 load4_inter(const I *p);
-template <>
-__device__ __forceinline__ float4 load4_inter<__half>(const __half *p) {
-    const uint2 u = *reinterpret_cast<const uint2 *>(p);
-    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
-    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
-    return make_float4(a.x, a.y, b.x, b.y);
-}
-template <>
-__device__ __forceinline__ float4 load4_inter<__nv_bfloat16>(const __nv_bfloat16 *p) {
-    const uint2 u = *reinterpret_cast<const uint2 *>(p);
-    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.x));
-    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.y));
-    return make_float4(a.x, a.y, b.x, b.y);
-}
-
-// S of the 16-bit path: the intermediate frame (frame row ey0 + r, column ax0 + c).
-template <typename I>
-struct InterSource {
-    const I *S;  // the frame
-    int W, ey0, ax0;
-    bool vec;    // 8-byte aligned quads
-    __device__ __forceinline__ float4 quad(int r, int c) const {
-        const I *p = S + (ey0 + r) * W + ax0 + c;
-        if (vec) return load4_inter<I>(p);
-        // W not a multiple of 4: the quad may run past the row (and the frame)
-        const int n = W - (ax0 + c);
-        return make_float4(n > 0 ? (float)p[0] : 0.0f, n > 1 ? (float)p[1] : 0.0f, n > 2 ? (float)p[2] : 0.0f,
-                           n > 3 ? (float)p[3] : 0.0f);
-    }
-    __device__ __forceinline__ float pixel(int r, int c) const { return (float)S[(ey0 + r) * W + ax0 + c]; }
-};
-
-// First pass of the finishing steps of one tile of one frame, over the
-// accumulator rectangle: A = L * S + sigma_n * n.  The illumination factors
-// must be in s.sx2 / s.sy2 and visible (a barrier after illum_factors).
-// With W a multiple of 4 (or without noise) a thread takes a 16-byte
-// aligned quad of a row, which is then also one Philox call of the noise
-// stream (pixels 4q..4q+3 of the frame's row-major order); otherwise noise
-// quads straddle rows and pixels are taken one by one.
-template <typename Src>
-__device__ __forceinline__ void finish_pass1(const KernelArgs &a, const Geo &g, const synthpix_pair_desc &D,
-                                             int frame, bool illum, const Smem &s, const Src &src) {
-    const float dl = D.illum_max - D.illum_min, lmin = D.illum_min, sn = D.noise_sigma;
-    const bool noise = sn != 0.0f;
-    const uint32_t tag = kTagNoise + (uint32_t)frame;
-    float *A0 = s.A + g.aoff;  // A at (ey0, ax0): in place over the accumulator words it is made from
-    if (!noise || (g.W & 3) == 0) {
-        const int nq = g.P >> 2;
-        const float inq = 1.0f / (float)nq;
-        for (int item = threadIdx.x; item < g.EH * nq; item += blockDim.x) {
-            const int r = small_div(item, inq), c = 4 * (item - r * nq);
-            const float4 S = src.quad(r, c);
-            float4 L = make_float4(1.0f, 1.0f, 1.0f, 1.0f);
-            if (illum) {
-                const float4 sx = *reinterpret_cast<const float4 *>(s.sx2 + c);
-                const float ly = s.sy2[r];
-                L = make_float4(fmaf(dl, sx.x * ly, lmin), fmaf(dl, sx.y * ly, lmin), fmaf(dl, sx.z * ly, lmin),
-                                fmaf(dl, sx.w * ly, lmin));
-            }
-            float4 o;
-            if (noise) {
-                // 32-bit pixel indices: frames hold at most 32768^2 = 2^30 pixels
-                const uint32_t q = (uint32_t)(((g.ey0 + r) * g.W + g.ax0 + c) >> 2);
-                const uint4 w = stream_words(a.keys, D.pair_id, q, tag);
-                float n0, n1, n2, n3;
-                box_muller(w.x, w.y, n0, n1);
-                box_muller(w.z, w.w, n2, n3);
-                o = make_float4(fmaf(L.x, S.x, sn * n0), fmaf(L.y, S.y, sn * n1), fmaf(L.z, S.z, sn * n2),
-                                fmaf(L.w, S.w, sn * n3));
-            } else {
-                o = make_float4(L.x * S.x, L.y * S.y, L.z * S.z, L.w * S.w);
-            }
-            *reinterpret_cast<float4 *>(A0 + r * g.AP + c) = o;
-        }
-    } else {
-        const int nq = (g.EW + 6) / 4 + 1;
-        const float inq = 1.0f / (float)nq;
-        const int cx = g.ex0 - g.ax0;  // accumulator column of ex0
-        for (int item = threadIdx.x; item < g.EH * nq; item += blockDim.x) {
-            const int r = small_div(item, inq), qi = item - r * nq;
-            const int rowlin = (g.ey0 + r) * g.W;
-            const int p0 = (((rowlin + g.ex0) >> 2) + qi) << 2;
-            if (p0 > rowlin + g.ex1 - 1) continue;
-            const uint4 w = stream_words(a.keys, D.pair_id, (uint32_t)(p0 >> 2), tag);
-            float nv[4];
-            box_muller(w.x, w.y, nv[0], nv[1]);
-            box_muller(w.z, w.w, nv[2], nv[3]);
-            const int c0 = p0 - rowlin - g.ex0;  // column of the quad's first pixel from ex0
-            const float ly = illum ? s.sy2[r] : 0.0f;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int c = c0 + k;
-                if (c >= 0 && c < g.EW) {
-                    const float S = src.pixel(r, cx + c);
-                    const float L = illum ? fmaf(dl, s.sx2[cx + c] * ly, lmin) : 1.0f;
-                    A0[r * g.AP + cx + c] = fmaf(L, S, sn * nv[k]);
-                }
-            }
-        }
-    }
-}
-
-// The rest of the finishing steps once A is complete over the accumulator
-// rectangle (a barrier after finish_pass1): border replication into the halo
-// outside the frame, separable blur, quantisation, one store per pixel.
-// clear_after: clear A (the accumulator's memory) for the next item.
-template <typename T>
-__device__ __forceinline__ void finish_rest(const KernelArgs &a, const Geo &g, const synthpix_pair_desc &D,
-                                            const float *wtab, int frame, const Smem &s, bool clear_after) {
-    if (g.R > 0 && (g.fx0 < 0 || g.fy0 < 0 || g.x1 + g.R > g.W || g.y1 + g.R > g.H)) {  // uniform
-        // only the pixels of the full halo rectangle outside the frame: whole rows
-        // above and below it, then the columns left and right of it in the rows
-        // between; each copies an in-frame pixel, so the order does not matter
-        const int cx = g.fx0 - g.afx0;  // A column of frame column fx0
-        const int top = max(-g.fy0, 0), bot = max(g.fy0 + g.FH - g.H, 0);
-        const int left = max(-g.fx0, 0), right = max(g.fx0 + g.FW - g.W, 0);
-        const int nband = (top + bot) * g.FW, nside = left + right;
-        const int n = nband + (g.FH - top - bot) * nside;
-        const float ifw = 1.0f / (float)g.FW, ins = 1.0f / (float)max(nside, 1);
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {
-            int r, c;
-            if (k < nband) {
-                const int q = small_div(k, ifw);
-                r = q < top ? q : g.FH - bot + (q - top);
-                c = k - q * g.FW;
-            } else {
-                const int q = small_div(k - nband, ins), e = k - nband - q * nside;
-                r = top + q;
-                c = e < left ? e : g.FW - right + (e - left);
-            }
-            const int gi = g.fy0 + r, gj = g.fx0 + c;
-            const int ci = min(max(gi, 0), g.H - 1) - g.fy0, cj = min(max(gj, 0), g.W - 1) - g.fx0;
-            s.A[r * g.AP + cx + c] = s.A[ci * g.AP + cx + cj];
-        }
-        __syncthreads();
-    }
-    const int64_t HW = (int64_t)g.H * g.W;
-    // the tile's first output pixel; stores add 32-bit row / column offsets
-    T *out = reinterpret_cast<T *>(a.images) + D.image_offset + (int64_t)frame * HW + (int64_t)g.y0 * g.W + g.x0;
-    const float M = a.quant_bits > 0 ? (float)((1u << a.quant_bits) - 1u) : 0.0f;
-    switch (g.R) {
-    case 0: store_unblurred<T>(g, s.A, out, M); break;
-    case 1: blur_store<T, 1>(g, s.A, wtab, out, M); break;
-    case 2: blur_store<T, 2>(g, s.A, wtab, out, M); break;
-    case 3: blur_store<T, 3>(g, s.A, wtab, out, M); break;
-    case 4: blur_store<T, 4>(g, s.A, wtab, out, M); break;
-    case 5: blur_store<T, 5>(g, s.A, wtab, out, M); break;
-    case 6: blur_store<T, 6>(g, s.A, wtab, out, M); break;
-    default: blur_store_any<T>(g, s.A, s.Bh, s.BP, wtab, out, M); break;
-    }
-    if (clear_after) {  // A is the next item's accumulator: zero once every pass has read it
-        __syncthreads();
-        float4 *a4 = reinterpret_cast<float4 *>(s.A);
-        for (int k = threadIdx.x; k < (g.FH * g.AP) >> 2; k += blockDim.x) a4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-}
-
-template <typename I>
-__device__ __forceinline__ I to_inter(float v);
-template <>
-__device__ __forceinline__ __half to_inter<__half>(float v) { return __float2half_rn(v); }
-template <>
-__device__ __forceinline__ __nv_bfloat16 to_inter<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
-
-// One work item of k_splat.  Fused (inter_dtype F32): splat the tile plus
-// its blur halo and finish it on chip.  Otherwise splat the tile alone and
-// store S in 16 bits to the intermediate frames; k_finish does the rest.
-// Thread 0 reads the work item of ticket t2 into `after` once the splat is
-// done (the ticket was taken an item earlier), so the read's latency hides
-// behind the finishing steps.
-template <typename T, int NT, int RS>
-__device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo &it, unsigned char *buf,
-                                             uint32_t cap, const Smem &s, uint32_t t2, ItemInfo &after) {
-    const synthpix_pair_desc &D = *reinterpret_cast<const synthpix_pair_desc *>(buf);
-    const PairPlan &pl = *reinterpret_cast<const PairPlan *>(buf + kStageDesc);
-    const float *wtab = reinterpret_cast<const float *>(buf + kStagePlan);
-    const Geo g = make_geo(D, pl, a.tile, it.tile, pl.halo);
-    const bool fused = a.inter_dtype == SYNTHPIX_F32;
-    const bool illum = fused ? illum_factors(g, D, s) : false;
-
-    // splat, chunk by chunk of staged records
-    const float imax = D.i_max > 0.0f ? D.i_max : 1.0f;
-    const float scale = kFixedScale / imax;
-    const Acc acc{s.acc, s.carry, g.AP};
-    uint32_t done = 0;
-    while (done < it.count) {
-        const uint32_t n = min(it.count - done, cap);
-        if constexpr (RS == (int)sizeof(RecordG))
-            splat_chunk_general(buf + kStageHeader + record_lead<RS>(it.rec0 + done), n, g, scale, acc, s.phi);
-        else
-            splat_chunk<NT>(buf + kStageHeader + record_lead<RS>(it.rec0 + done), buf + kStageHeader, n, g, scale,
-                            acc, s.scr + (threadIdx.x >> 5) * a.warp_scratch, a.warp_scratch >> 2, s.phi);
-        done += n;
-        __syncthreads();
-        if (done < it.count) {  // more records: stage the next chunk
-            stage_records<RS>(a, it.rec0 + done, min(it.count - done, cap), buf + kStageHeader);
-            cp_async_commit();
-            cp_async_wait_all();
-            __syncthreads();
-        }
-    }
-    if (it.count == 0) __syncthreads();  // illumination factors
-    // block counts of the next item start from zero (its first count comes after a barrier)
-    for (int k = threadIdx.x; k < kBlkSide * kBlkSide; k += blockDim.x) sh_blk[k] = 0u;
-    if (threadIdx.x == 0) {
-        if ((int64_t)t2 < a.n_tiles) after = a.items[t2];
-        else after.pair = -1;
-    }
-
-    const float unit = imax * kFixedUnit;
-    const bool wrapped = sh_wrap != 0;
-    if (wrapped) wrapped_to_float(s, g, unit);
-    const AccSource src{s.acc + g.aoff, g.AP, unit, wrapped};
-    if (!fused) {
-        // halo 0: the accumulator rectangle is the tile (ax0 = ex0 = x0)
-        const int64_t HW = (int64_t)g.H * g.W;
-        const int64_t base = pl.inter_base + (int64_t)it.frame * HW;
-        const float iew = 1.0f / (float)g.EW;
-        for (int idx = threadIdx.x; idx < g.EH * g.EW; idx += blockDim.x) {
-            const int r = small_div(idx, iew), c = idx - r * g.EW;
-            const float S = src.pixel(r, c);
-            const int64_t o = base + (int64_t)(g.ey0 + r) * g.W + (g.ex0 + c);
-            if (a.inter_dtype == SYNTHPIX_F16) reinterpret_cast<__half *>(a.inter)[o] = to_inter<__half>(S);
-            else reinterpret_cast<__nv_bfloat16 *>(a.inter)[o] = to_inter<__nv_bfloat16>(S);
-        }
-        return;  // the caller's loop ends with a barrier
-    }
-    finish_pass1(a, g, D, it.frame, illum, s, src);
-    __syncthreads();
-    finish_rest<T>(a, g, D, wtab, it.frame, s, true);
-}
-
-// ---------------------------------------------------------------------------
-// the persistent kernel
-// ---------------------------------------------------------------------------
-struct SmemLayout {
-    size_t acc, Bh, sx2, sy2, scr, phi, bufs, total;
-};
-
-// The accumulator words, which hold the finishing buffer A after the first
-// finishing pass (+ padding read by the last row's blur loads); illumination
-// factors; per-warp window scratch; the normal-tail table; two
-// staged-record buffers; the horizontal-blur buffer Bh of the blur for radii
-// above 6 (the others blur rows in place).
-__host__ __device__ inline SmemLayout smem_layout(int E, int tile, int warp_scratch, int rec_buf_bytes) {
-    SmemLayout L;
-    const int BP = (tile + 3) & ~3;
-    const size_t PC = (size_t)pitch_cap(E);
-    size_t o = 0;
-    auto take = [&](size_t bytes) {
-        const size_t at = o;
-        o = (o + bytes + 15) & ~(size_t)15;
-        return at;
-    };
-    L.acc = take(((size_t)E * PC + 32) * 4);
-    L.sx2 = take(PC * 4);
-    L.sy2 = take((size_t)E * 4);
-    L.scr = take((size_t)(splat_threads(tile) / 32) * warp_scratch * 4);
-    L.phi = take((size_t)(kPhiDegree + 1) * kPhiPieces * 4);
-    L.bufs = take(2 * (size_t)rec_buf_bytes);
-    const bool need_bh = (E - tile) / 2 > 6;  // only the blur of radii above 6 uses Bh
-    L.Bh = need_bh ? take((size_t)E * BP * 4) : L.acc;
-    L.total = o;
-    return L;
-}
-
-// RS: bytes of a bin record (24: Record, round particles; 32: RecordG, general shapes).
-template <typename T, int NT, int RS>
-__global__ void __launch_bounds__(NT, 1024 / NT) k_splat(KernelArgs a) {
-    if (*a.check != 1) return;
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ ItemInfo s_item[2];
-    const SmemLayout L = smem_layout(a.smem_edge, a.tile, a.warp_scratch, a.rec_buf_bytes);
-    const int words = a.smem_edge * pitch_cap(a.smem_edge);
-    Smem s;
-    s.acc = reinterpret_cast<uint32_t *>(smem + L.acc);
-    s.carry = a.carry + (int64_t)blockIdx.x * a.carry_stride;
-    s.A = reinterpret_cast<float *>(smem + L.acc);
-    s.Bh = reinterpret_cast<float *>(smem + L.Bh);
-    s.sx2 = reinterpret_cast<float *>(smem + L.sx2);
-    s.sy2 = reinterpret_cast<float *>(smem + L.sy2);
-    s.scr = reinterpret_cast<float *>(smem + L.scr);
-    float *phi = reinterpret_cast<float *>(smem + L.phi);
-    for (int k = threadIdx.x; k < (kPhiDegree + 1) * kPhiPieces; k += blockDim.x) phi[k] = kPhiTable[k];
-    s.phi = reinterpret_cast<const float4 *>(phi);
-    for (int k = threadIdx.x; k < kBuckets; k += blockDim.x) sh_cnt[k] = 0;
-    for (int k = threadIdx.x; k < kBlkSide * kBlkSide; k += blockDim.x) sh_blk[k] = 0;
-    s.BP = (a.tile + 3) & ~3;
-    unsigned char *bufs = smem + L.bufs;
-    const uint32_t cap = (uint32_t)rec_cap(a.rec_buf_bytes, RS);
-    for (int k = threadIdx.x; k < words; k += blockDim.x) s.acc[k] = 0u;
-    // work queue: the current item, the next one (staged while the current
-    // one renders) and the ticket of the one after (its item read during
-    // the current item); tickets only grow, so a CTA never drops a valid one
-    uint32_t t_pending = 0;
-    if (threadIdx.x == 0) {
-        sh_wrap = 0;
-        for (int q = 0; q < 2; ++q) {
-            const uint32_t t = atomicAdd(a.ticket, 1u);
-            ItemInfo it;
-            if ((int64_t)t < a.n_tiles) it = a.items[t];
-            else it.pair = -1;
-            s_item[q] = it;
-        }
-        t_pending = atomicAdd(a.ticket, 1u);
-    }
-    __syncthreads();
-    if (s_item[0].pair < 0) return;
-    stage_header(a, s_item[0].pair, bufs);
-    stage_records<RS>(a, s_item[0].rec0, min(s_item[0].count, cap), bufs + kStageHeader);
-    cp_async_commit();
-    int cur = 0;
-    for (;;) {
-        const ItemInfo it = s_item[cur];
-        const ItemInfo nx = s_item[cur ^ 1];
-        cp_async_wait_all();
-        __syncthreads();  // staged data of `it` visible; the other buffer is free; the wrap flag is read
-        if (it.pair < 0) break;
-        // the splat's first add comes after a barrier inside splat_chunk
-        if (threadIdx.x == 0) {
-            sh_wrap = 0;
-            sh_carry_clean = 0;
-        }
-        unsigned char *bnext = bufs + (cur ^ 1) * a.rec_buf_bytes;
-        if (nx.pair >= 0) {
-            stage_header(a, nx.pair, bnext);
-            stage_records<RS>(a, nx.rec0, min(nx.count, cap), bnext + kStageHeader);
-        }
-        cp_async_commit();
-        const uint32_t t2 = t_pending;
-        if (threadIdx.x == 0) t_pending = atomicAdd(a.ticket, 1u);  // returns while this item renders
-        ItemInfo after;
-        process_item<T, NT, RS>(a, it, bufs + cur * a.rec_buf_bytes, cap, s, t2, after);
-        if (threadIdx.x == 0) s_item[cur] = after;
-        cur ^= 1;
-        __syncthreads();
-    }
-    cp_async_wait_all();
-}
-
-// ---------------------------------------------------------------------------
-// k_finish: the epilogue of the 16-bit intermediate path, one CTA per item
-// (pair, frame, tile).  S of the tile and its blur halo is read from the
-// intermediate frames written by k_splat; every output pixel written once.
-// ---------------------------------------------------------------------------
-struct FinishLayout {
-    size_t A, Bh, sx2, sy2, total;
-};
-
-__host__ __device__ inline FinishLayout finish_layout(int E, int tile) {
-    FinishLayout L;
-    const int BP = (tile + 3) & ~3;
-    const size_t PC = (size_t)pitch_cap(E);
-    size_t o = 0;
-    auto take = [&](size_t bytes) {
-        const size_t at = o;
-        o = (o + bytes + 15) & ~(size_t)15;
-        return at;
-    };
-    L.A = take(((size_t)E * PC + 32) * 4);
-    L.Bh = take((E - tile) / 2 > 6 ? (size_t)E * BP * 4 : 0);  // only radii above 6 use Bh
-    L.sx2 = take(PC * 4);
-    L.sy2 = take((size_t)E * 4);
-    L.total = o;
-    return L;
-}
-
-template <typename T, typename I>
-__global__ void __launch_bounds__(kSplatThreads) k_finish(KernelArgs a) {
-    if (*a.check != 1) return;
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ float wtab[kBlurStride];
-    const FinishLayout FL = finish_layout(a.smem_edge, a.tile);
-    Smem s;
-    s.acc = nullptr;
-    s.carry = nullptr;
-    s.A = reinterpret_cast<float *>(smem + FL.A);
-    s.Bh = reinterpret_cast<float *>(smem + FL.Bh);
-    s.sx2 = reinterpret_cast<float *>(smem + FL.sx2);
-    s.sy2 = reinterpret_cast<float *>(smem + FL.sy2);
-    s.scr = nullptr;
-    s.phi = nullptr;
-    s.BP = (a.tile + 3) & ~3;
-    const ItemInfo it = a.items[blockIdx.x];
-    const synthpix_pair_desc &D = a.descs[it.pair];
-    const PairPlan pl = a.plan[it.pair];
-    if (threadIdx.x < kBlurStride) wtab[threadIdx.x] = a.blur_w[(int64_t)it.pair * kBlurStride + threadIdx.x];
-    const Geo g = make_geo(D, pl, a.tile, it.tile, pl.blur_r);
-    const bool illum = illum_factors(g, D, s);
-    __syncthreads();
-    const I *S16 = reinterpret_cast<const I *>(a.inter) + pl.inter_base + (int64_t)it.frame * g.H * g.W;
-    const bool vec = (g.W & 3) == 0 && (reinterpret_cast<uintptr_t>(S16) & 7) == 0;
-    const InterSource<I> src{S16, g.W, g.ey0, g.ax0, vec};
-    finish_pass1(a, g, D, it.frame, illum, s, src);
-    __syncthreads();
-    finish_rest<T>(a, g, D, wtab, it.frame, s, false);
-}
 
 size_t splat_smem_bytes(int edge, int tile, int warp_scratch, int rec_buf_bytes) {
     return smem_layout(edge, tile, warp_scratch, rec_buf_bytes).total;
 }
 
+cudaError_t launch_splat_f32(const KernelArgs &a, cudaStream_t st);
+cudaError_t launch_splat_f16(const KernelArgs &a, cudaStream_t st);
+cudaError_t launch_splat_bf16(const KernelArgs &a, cudaStream_t st);
+cudaError_t launch_splat_u8(const KernelArgs &a, cudaStream_t st);
+cudaError_t launch_splat_u16(const KernelArgs &a, cudaStream_t st);
+
 cudaError_t launch_splat(const KernelArgs &a, int32_t out_dtype, cudaStream_t st, cudaEvent_t const *ev) {
-    const size_t smem = splat_smem_bytes(a.smem_edge, a.tile, a.warp_scratch, a.rec_buf_bytes);
-    int dev = 0, nsm = 0, occ = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-#define SPX_LAUNCH_NT(T, NT, RS)                                                                             \
-    do {                                                                                                     \
-        auto kern = k_splat<T, NT, RS>;                                                                      \
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);              \
-        if (e != cudaSuccess) return e;                                                                      \
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem);                             \
-        if (e != cudaSuccess) return e;                                                                      \
-        int64_t want = (int64_t)nsm * (occ > 0 ? occ : 1);                                                   \
-        if (want > splat_max_ctas(a.tile, a.n_tiles)) want = splat_max_ctas(a.tile, a.n_tiles); /* carries */\
-        e = launch_kernel(kern, (unsigned)(a.n_tiles < want ? a.n_tiles : want), NT, smem, st, a);           \
-        if (e != cudaSuccess) return e;                                                                      \
-    } while (0)
-#define SPX_LAUNCH(T)                                                                                        \
-    do {                                                                                                     \
-        if (a.general) {                                                                                     \
-            if (nt == 512) SPX_LAUNCH_NT(T, 512, 32);                                                        \
-            else SPX_LAUNCH_NT(T, 256, 32);                                                                  \
-        } else {                                                                                             \
-            if (nt == 512) SPX_LAUNCH_NT(T, 512, 24);                                                        \
-            else SPX_LAUNCH_NT(T, 256, 24);                                                                  \
-        }                                                                                                    \
-    } while (0)
-    const int nt = splat_threads(a.tile);
+    cudaError_t e;
     switch (out_dtype) {
-    case SYNTHPIX_F32: SPX_LAUNCH(float); break;
-    case SYNTHPIX_F16: SPX_LAUNCH(__half); break;
-    case SYNTHPIX_BF16: SPX_LAUNCH(__nv_bfloat16); break;
-    case SYNTHPIX_U8: SPX_LAUNCH(uint8_t); break;
-    default: SPX_LAUNCH(uint16_t); break;
+    case SYNTHPIX_F32: e = launch_splat_f32(a, st); break;
+    case SYNTHPIX_F16: e = launch_splat_f16(a, st); break;
+    case SYNTHPIX_BF16: e = launch_splat_bf16(a, st); break;
+    case SYNTHPIX_U8: e = launch_splat_u8(a, st); break;
+    default: e = launch_splat_u16(a, st); break;
     }
-#undef SPX_LAUNCH
-#undef SPX_LAUNCH_NT
-    if (a.inter_dtype != SYNTHPIX_F32) {
-        const size_t fsm = finish_layout(a.smem_edge, a.tile).total;
-        const unsigned grid = (unsigned)a.n_tiles;
-#define SPX_FINISH(T, I)                                                                                     \
-    do {                                                                                                     \
-        e = cudaFuncSetAttribute(k_finish<T, I>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);     \
-        if (e != cudaSuccess) return e;                                                                      \
-        e = launch_kernel(k_finish<T, I>, grid, kSplatThreads, fsm, st, a);                                 \
-        if (e != cudaSuccess) return e;                                                                      \
-    } while (0)
-#define SPX_FINISH_I(I)                                                                                      \
-    switch (out_dtype) {                                                                                     \
-    case SYNTHPIX_F32: SPX_FINISH(float, I); break;                                                          \
-    case SYNTHPIX_F16: SPX_FINISH(__half, I); break;                                                         \
-    case SYNTHPIX_BF16: SPX_FINISH(__nv_bfloat16, I); break;                                                 \
-    case SYNTHPIX_U8: SPX_FINISH(uint8_t, I); break;                                                         \
-    default: SPX_FINISH(uint16_t, I); break;                                                                 \
-    }
-        if (a.inter_dtype == SYNTHPIX_F16) {
-            SPX_FINISH_I(__half)
-        } else {
-            SPX_FINISH_I(__nv_bfloat16)
-        }
-#undef SPX_FINISH_I
-#undef SPX_FINISH
-    }
+    if (e != cudaSuccess) return e;
     if (ev && ev[5]) cudaEventRecord(ev[5], st);
     return cudaGetLastError();
 }
