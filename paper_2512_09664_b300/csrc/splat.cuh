@@ -938,16 +938,53 @@ __device__ __forceinline__ float neg2_log_uo24(uint32_t w) {
     return x < 0.00390625f ? series : viaLog2;
 }
 
-// Box-Muller pair from two Philox words: r = sqrt(-2 ln u), theta = 2 pi v,
-// evaluated as -r (cos, sin)(theta - pi) so the fast sine and cosine work on
-// [-pi, pi).
-__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float &n0, float &n1) {
+// Box-Muller pair from two Philox words, times the noise sigma sn:
+// r = sqrt(-2 ln u), theta = 2 pi v, evaluated as -(sn r) (cos, sin)(theta - pi)
+// so the fast sine and cosine work on [-pi, pi).
+__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float sn, float &n0, float &n1) {
     const float x = neg2_log_uo24(wa);
-    const float r = x > 0.0f ? x * rsqrtf(x) : 0.0f;
+    const float r = sn * (x > 0.0f ? x * rsqrtf(x) : 0.0f);
     float s, c;
     __sincosf(6.28318530717958647692f * (u24f(wb) - 0.5f), &s, &c);
     n0 = -r * c;
     n1 = -r * s;
+}
+
+// Quantised code clamp(rint(v M), 0, M): v clamped to [0, 1] first, then the
+// product rounded half to even by one FMA with 1.5 2^23 (exact for products
+// below 2^22; M <= 65535).  NaN gives 0.
+__device__ __forceinline__ uint32_t quant_code(float v, float M) {
+    const float t = fmaf(fminf(fmaxf(v, 0.0f), 1.0f), M, kMagic);
+    return (uint32_t)(__float_as_int(t) - kMagicBits);
+}
+
+// Packed FP32 pairs (two lanes of one 64-bit register; each lane rounds as
+// the scalar instruction would, so results equal the scalar arithmetic).
+__device__ __forceinline__ unsigned long long f2_pack(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 f2_unpack(unsigned long long r) {
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
 }
 
 template <typename T>
@@ -1015,12 +1052,10 @@ template <typename T>
 __device__ __forceinline__ void store_group(T *o, float *v, int nvalid, float M) {
     if constexpr (IsCode<T>::value) {
         if (M > 0.0f) {
-            // Q = clamp(rint(B M), 0, M): the conversion rounds half to even and
-            // takes negative values (and NaN) to 0
-            const uint32_t Mi = (uint32_t)M;
+            // Q = clamp(rint(B M), 0, M)
             uint32_t q[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) q[j] = min(__float2uint_rn(v[j] * M), Mi);
+            for (int j = 0; j < 4; ++j) q[j] = quant_code(v[j], M);
             if (nvalid == 4 && (reinterpret_cast<uintptr_t>(o) % (4 * sizeof(T))) == 0) {
                 if (sizeof(T) == 1)
                     *reinterpret_cast<uint32_t *>(o) = q[0] | (q[1] << 8) | (q[2] << 16) | (q[3] << 24);
@@ -1036,7 +1071,7 @@ __device__ __forceinline__ void store_group(T *o, float *v, int nvalid, float M)
     }
     if (M > 0.0f) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) v[j] = fminf(fmaxf(rintf(v[j] * M), 0.0f), M);
+        for (int j = 0; j < 4; ++j) v[j] = (float)quant_code(v[j], M);
     }
     if (nvalid == 4 && (reinterpret_cast<uintptr_t>(o) % (4 * sizeof(T))) == 0) {
         Out<T>::store4(o, v);
@@ -1197,38 +1232,80 @@ __device__ __forceinline__ Geo make_geo(const synthpix_pair_desc &D, const PairP
     return g;
 }
 
-// separable illumination factors sin^2: columns [ax0, ax0 + P) and rows
-// [ey0, ey1) of the accumulator rectangle
-__device__ __forceinline__ bool illum_factors(const Geo &g, const synthpix_pair_desc &D, const Smem &s) {
-    const bool illum = D.illum_min != 1.0f || D.illum_max != 1.0f;
-    if (illum) {
-        for (int k = threadIdx.x; k < g.P + g.EH; k += blockDim.x) {
-            if (k < g.P) {
-                const float sv = sinpif(((float)(g.ax0 + k) + 0.5f) / (float)g.W);
-                s.sx2[k] = sv * sv;
-            } else {
-                const float sv = sinpif(((float)(g.ey0 + k - g.P) + 0.5f) / (float)g.H);
-                s.sy2[k - g.P] = sv * sv;
-            }
-        }
-    }
-    return illum;
+// Constants of an item's finishing steps, A = Lu S + sigma_n n: S is in units
+// of `unit` (accumulator units on the fused path, full scale on the 16-bit
+// path), Lu = (lmin + dl sx^2 sy^2) unit, with s.sx2[k] = dl sx^2 unit per
+// column and s.sy2[r] = sy^2 per row (illum_factors).
+struct EpiK {
+    float lminu;       // lmin unit
+    float unit;        // value of one unit of S
+    float sn;          // noise sigma
+    bool illum, noise;
+    uint32_t tag;      // noise stream of the frame
+    uint64_t pair_id;
+};
+
+__device__ __forceinline__ EpiK epi_consts(const synthpix_pair_desc &D, int frame, float unit) {
+    EpiK K;
+    K.illum = D.illum_min != 1.0f || D.illum_max != 1.0f;
+    K.lminu = D.illum_min * unit;
+    K.unit = unit;
+    K.sn = D.noise_sigma;
+    K.noise = D.noise_sigma != 0.0f;
+    K.tag = kTagNoise + (uint32_t)frame;
+    K.pair_id = D.pair_id;
+    return K;
 }
 
-// S of the fused path: the accumulator words, each cleared for the next
-// item as it is read.  r: accumulator row, c: column from ax0 (a multiple
-// of 4 for quad()).  When an add wrapped a word, the words were first
-// converted to S in place (float bits), carries included (wrapped_to_float).
+// separable illumination factors: dl sin^2 unit for columns [ax0, ax0 + P)
+// and sin^2 for rows [ey0, ey1) of the accumulator rectangle
+__device__ __forceinline__ void illum_factors(const Geo &g, const synthpix_pair_desc &D, const EpiK &K, const Smem &s) {
+    if (!K.illum) return;
+    const float dl = D.illum_max - D.illum_min;
+    for (int k = threadIdx.x; k < g.P + g.EH; k += blockDim.x) {
+        if (k < g.P) {
+            const float sv = sinpif(((float)(g.ax0 + k) + 0.5f) / (float)g.W);
+            s.sx2[k] = (dl * (sv * sv)) * K.unit;
+        } else {
+            const float sv = sinpif(((float)(g.ey0 + k - g.P) + 0.5f) / (float)g.H);
+            s.sy2[k - g.P] = sv * sv;
+        }
+    }
+}
+
+// Lu of 4 pixels of a row from their column factors (16-byte aligned) and the row factor
+__device__ __forceinline__ float4 lu_quad(const EpiK &K, const float *sx, float ly) {
+    if (!K.illum) return make_float4(K.unit, K.unit, K.unit, K.unit);
+    const float4 c = *reinterpret_cast<const float4 *>(sx);
+    return make_float4(fmaf(c.x, ly, K.lminu), fmaf(c.y, ly, K.lminu), fmaf(c.z, ly, K.lminu),
+                       fmaf(c.w, ly, K.lminu));
+}
+
+// A = Lu S + sigma_n n of one aligned quad (q: its call of the noise stream)
+__device__ __forceinline__ float4 a_quad(const KernelArgs &a, const EpiK &K, const float4 &S, const float4 &Lu,
+                                         uint32_t q) {
+    if (!K.noise) return make_float4(Lu.x * S.x, Lu.y * S.y, Lu.z * S.z, Lu.w * S.w);
+    const uint4 w = stream_words(a.keys, K.pair_id, q, K.tag);
+    float n0, n1, n2, n3;
+    box_muller(w.x, w.y, K.sn, n0, n1);
+    box_muller(w.z, w.w, K.sn, n2, n3);
+    return make_float4(fmaf(Lu.x, S.x, n0), fmaf(Lu.y, S.y, n1), fmaf(Lu.z, S.z, n2), fmaf(Lu.w, S.w, n3));
+}
+
+// S of the fused path in accumulator units: the accumulator words.  r:
+// accumulator row, c: column from ax0 (a multiple of 4 for quad()).  quad()
+// leaves the words (the finishing buffer is written over them and cleared
+// after the blur); pixel() clears each word as it is read (the 16-bit path,
+// which leaves the accumulator to the next item).  When an add wrapped a word,
+// the words were first converted to S in place (float bits), carries
+// included (wrapped_to_float).
 struct AccSource {
     uint32_t *acc;
     int P;
-    float unit;   // i_max 2^-26
     bool floats;  // the words hold S as float bits
-    __device__ __forceinline__ float value(uint32_t v) const { return floats ? __uint_as_float(v) : (float)v * unit; }
+    __device__ __forceinline__ float value(uint32_t v) const { return floats ? __uint_as_float(v) : (float)v; }
     __device__ __forceinline__ float4 quad(int r, int c) const {
-        uint4 *p = reinterpret_cast<uint4 *>(acc + r * P + c);
-        const uint4 v = *p;
-        *p = make_uint4(0u, 0u, 0u, 0u);
+        const uint4 v = *reinterpret_cast<const uint4 *>(acc + r * P + c);
         return make_float4(value(v.x), value(v.y), value(v.z), value(v.w));
     }
     __device__ __forceinline__ float pixel(int r, int c) const {
@@ -1239,14 +1316,14 @@ struct AccSource {
     }
 };
 
-// A wrapped item: S = (word + carry 2^32) q written over the words, before
-// the finishing buffer (which holds the carry words) is written.  Ends with
-// a barrier.
-__device__ __forceinline__ void wrapped_to_float(const Smem &s, const Geo &g, float unit) {
+// A wrapped item: S = word + carry 2^32 (units) written over the words as
+// floats, before the finishing buffer (which holds the carry words) is
+// written.  Ends with a barrier.
+__device__ __forceinline__ void wrapped_to_float(const Smem &s, const Geo &g) {
     const float ip = 1.0f / (float)g.P;
     for (int k = threadIdx.x; k < g.EH * g.P; k += blockDim.x) {
         const int r = small_div(k, ip), i = g.aoff + r * g.AP + (k - r * g.P);
-        s.acc[i] = __float_as_uint(fmaf((float)s.carry[i], kWrapValue, (float)s.acc[i]) * unit);
+        s.acc[i] = __float_as_uint(fmaf((float)s.carry[i], kWrapValue, (float)s.acc[i]));
     }
     __syncthreads();
 }
@@ -1286,46 +1363,26 @@ struct InterSource {
 };
 
 // First pass of the finishing steps of one tile of one frame, over the
-// accumulator rectangle: A = L * S + sigma_n * n.  The illumination factors
+// accumulator rectangle: A = Lu S + sigma_n n.  The illumination factors
 // must be in s.sx2 / s.sy2 and visible (a barrier after illum_factors).
 // With W a multiple of 4 (or without noise) a thread takes a 16-byte
 // aligned quad of a row, which is then also one Philox call of the noise
 // stream (pixels 4q..4q+3 of the frame's row-major order); otherwise noise
 // quads straddle rows and pixels are taken one by one.
 template <typename Src>
-__device__ __forceinline__ void finish_pass1(const KernelArgs &a, const Geo &g, const synthpix_pair_desc &D,
-                                             int frame, bool illum, const Smem &s, const Src &src) {
-    const float dl = D.illum_max - D.illum_min, lmin = D.illum_min, sn = D.noise_sigma;
-    const bool noise = sn != 0.0f;
-    const uint32_t tag = kTagNoise + (uint32_t)frame;
+__device__ __forceinline__ void finish_pass1(const KernelArgs &a, const Geo &g, const EpiK &K, const Smem &s,
+                                             const Src &src) {
     float *A0 = s.A + g.aoff;  // A at (ey0, ax0): in place over the accumulator words it is made from
-    if (!noise || (g.W & 3) == 0) {
+    if (!K.noise || (g.W & 3) == 0) {
         const int nq = g.P >> 2;
         const float inq = 1.0f / (float)nq;
         for (int item = threadIdx.x; item < g.EH * nq; item += blockDim.x) {
             const int r = small_div(item, inq), c = 4 * (item - r * nq);
             const float4 S = src.quad(r, c);
-            float4 L = make_float4(1.0f, 1.0f, 1.0f, 1.0f);
-            if (illum) {
-                const float4 sx = *reinterpret_cast<const float4 *>(s.sx2 + c);
-                const float ly = s.sy2[r];
-                L = make_float4(fmaf(dl, sx.x * ly, lmin), fmaf(dl, sx.y * ly, lmin), fmaf(dl, sx.z * ly, lmin),
-                                fmaf(dl, sx.w * ly, lmin));
-            }
-            float4 o;
-            if (noise) {
-                // 32-bit pixel indices: frames hold at most 32768^2 = 2^30 pixels
-                const uint32_t q = (uint32_t)(((g.ey0 + r) * g.W + g.ax0 + c) >> 2);
-                const uint4 w = stream_words(a.keys, D.pair_id, q, tag);
-                float n0, n1, n2, n3;
-                box_muller(w.x, w.y, n0, n1);
-                box_muller(w.z, w.w, n2, n3);
-                o = make_float4(fmaf(L.x, S.x, sn * n0), fmaf(L.y, S.y, sn * n1), fmaf(L.z, S.z, sn * n2),
-                                fmaf(L.w, S.w, sn * n3));
-            } else {
-                o = make_float4(L.x * S.x, L.y * S.y, L.z * S.z, L.w * S.w);
-            }
-            *reinterpret_cast<float4 *>(A0 + r * g.AP + c) = o;
+            const float4 Lu = lu_quad(K, s.sx2 + c, K.illum ? s.sy2[r] : 0.0f);
+            // 32-bit pixel indices: frames hold at most 32768^2 = 2^30 pixels
+            const uint32_t q = (uint32_t)(((g.ey0 + r) * g.W + g.ax0 + c) >> 2);
+            *reinterpret_cast<float4 *>(A0 + r * g.AP + c) = a_quad(a, K, S, Lu, q);
         }
     } else {
         const int nq = (g.EW + 6) / 4 + 1;
@@ -1336,19 +1393,19 @@ __device__ __forceinline__ void finish_pass1(const KernelArgs &a, const Geo &g, 
             const int rowlin = (g.ey0 + r) * g.W;
             const int p0 = (((rowlin + g.ex0) >> 2) + qi) << 2;
             if (p0 > rowlin + g.ex1 - 1) continue;
-            const uint4 w = stream_words(a.keys, D.pair_id, (uint32_t)(p0 >> 2), tag);
+            const uint4 w = stream_words(a.keys, K.pair_id, (uint32_t)(p0 >> 2), K.tag);
             float nv[4];
-            box_muller(w.x, w.y, nv[0], nv[1]);
-            box_muller(w.z, w.w, nv[2], nv[3]);
+            box_muller(w.x, w.y, K.sn, nv[0], nv[1]);
+            box_muller(w.z, w.w, K.sn, nv[2], nv[3]);
             const int c0 = p0 - rowlin - g.ex0;  // column of the quad's first pixel from ex0
-            const float ly = illum ? s.sy2[r] : 0.0f;
+            const float ly = K.illum ? s.sy2[r] : 0.0f;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const int c = c0 + k;
                 if (c >= 0 && c < g.EW) {
                     const float S = src.pixel(r, cx + c);
-                    const float L = illum ? fmaf(dl, s.sx2[cx + c] * ly, lmin) : 1.0f;
-                    A0[r * g.AP + cx + c] = fmaf(L, S, sn * nv[k]);
+                    const float Lu = K.illum ? fmaf(s.sx2[cx + c], ly, K.lminu) : K.unit;
+                    A0[r * g.AP + cx + c] = fmaf(Lu, S, nv[k]);
                 }
             }
         }
@@ -1410,6 +1467,145 @@ __device__ __forceinline__ void finish_rest(const KernelArgs &a, const Geo &g, c
     }
 }
 
+// The finishing steps of a full 128 x 128 tile (fused path, 16 warps, W a
+// multiple of 4, blur radius R <= 4), with the blur in registers:
+//   1. the quads just left and right of the tile (columns x0 - 4 .. x0 - 1
+//      and x1 .. x1 + 3, where inside the frame) of every row of the
+//      accumulator rectangle: A written in place;
+//   2. a warp per row, lane l on the tile's quad l: A of the quad, then the
+//      horizontal blur of its 4 pixels from its own values and those of its
+//      neighbours (shuffles; the quads of step 1 from shared memory; the
+//      pixel at the frame's edge repeated past it), written in place;
+//   3. a warp per 8 output rows, lane l on quad l: the vertical blur over the
+//      8 + 2R rows it needs (row indices clamped into the frame: replicated
+//      border), in packed FP32 pairs, then quantisation and the stores.
+// The arithmetic (a_quad, the tap order of both passes, quant_code) is that
+// of finish_pass1 / blur_store, so a pixel's value does not depend on the
+// tile edge that renders it.  R = 0: step 2 stores the quantised A directly.
+template <typename T, int R>
+__device__ __forceinline__ void finish_fast(const KernelArgs &a, const Geo &g, const synthpix_pair_desc &D,
+                                            const float *wtab, int frame, const EpiK &K, const Smem &s,
+                                            const AccSource &src) {
+    static_assert(R >= 0 && R <= 4, "halo of at most one quad");
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int AP = g.AP;
+    const int cx = g.x0 - g.afx0;       // accumulator column of the tile's first column
+    const int sc = g.ax0 - g.afx0;      // src columns count from ax0
+    float *A = s.A;                     // accumulator rows from fy0, columns from afx0
+    const int rlo = g.ey0 - g.fy0, rhi = g.ey1 - g.fy0;  // accumulator rows inside the frame
+    const float M = a.quant_bits > 0 ? (float)((1u << a.quant_bits) - 1u) : 0.0f;
+    T *out = reinterpret_cast<T *>(a.images) + D.image_offset + (int64_t)frame * ((int64_t)g.H * g.W) +
+             (int64_t)g.y0 * g.W + g.x0;
+    float w[R + 1];
+#pragma unroll
+    for (int k = 0; k <= R; ++k) w[k] = wtab[k];
+    const bool left = g.x0 > 0, right = g.x1 < g.W;  // the side quads lie inside the frame
+    if constexpr (R > 0) {  // 1. side quads
+        for (int k = threadIdx.x; k < 2 * (rhi - rlo); k += blockDim.x) {
+            const int r = rlo + (k >> 1);
+            const bool rt = (k & 1) != 0;
+            if (rt ? !right : !left) continue;
+            const int c = rt ? cx + 128 : cx - 4;
+            const float4 S = src.quad(r - rlo, c - sc);
+            const float4 Lu = lu_quad(K, s.sx2 + (c - sc), K.illum ? s.sy2[r - rlo] : 0.0f);
+            const uint32_t q = (uint32_t)(((g.fy0 + r) * g.W + g.afx0 + c) >> 2);
+            *reinterpret_cast<float4 *>(A + r * AP + c) = a_quad(a, K, S, Lu, q);
+        }
+        __syncthreads();
+    }
+    // 2. A and the horizontal blur, a warp per row
+    const int cl = cx + 4 * lane;  // this lane's accumulator column
+    for (int r = rlo + warp; r < rhi; r += 16) {
+        const float4 S = src.quad(r - rlo, cl - sc);
+        const float4 Lu = lu_quad(K, s.sx2 + (cl - sc), K.illum ? s.sy2[r - rlo] : 0.0f);
+        const float4 v4 = a_quad(a, K, S, Lu, (uint32_t)(((g.fy0 + r) * g.W + g.afx0 + cl) >> 2));
+        const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+        if constexpr (R == 0) {
+            float o[4] = {v[0], v[1], v[2], v[3]};
+            store_group<T>(out + (r - rlo) * g.W + 4 * lane, o, 4, M);
+        } else {
+            // x[m], m = -R .. 3 + R: the row's A around this lane's 4 pixels
+            float x[4 + 2 * R];
+    #pragma unroll
+            for (int j = 0; j < 4; ++j) x[R + j] = v[j];
+    #pragma unroll
+            for (int k = 1; k <= R; ++k) {
+                x[R - k] = __shfl_up_sync(FULL, v[4 - k], 1);       // column 4l - k, lane l - 1
+                x[R + 3 + k] = __shfl_down_sync(FULL, v[k - 1], 1);  // column 4l + 3 + k, lane l + 1
+            }
+            if (lane == 0) {
+    #pragma unroll
+                for (int k = 1; k <= R; ++k) x[R - k] = left ? A[r * AP + cx - k] : v[0];
+            }
+            if (lane == 31) {
+    #pragma unroll
+                for (int k = 1; k <= R; ++k) x[R + 3 + k] = right ? A[r * AP + cx + 127 + k] : v[3];
+            }
+            float h[4];
+    #pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float acc = w[0] * x[R + j];
+    #pragma unroll
+                for (int k = 1; k <= R; ++k) acc = fmaf(w[k], x[R + j - k] + x[R + j + k], acc);
+                h[j] = acc;
+            }
+            *reinterpret_cast<float4 *>(A + r * AP + cl) = make_float4(h[0], h[1], h[2], h[3]);
+        }
+    }
+    if constexpr (R > 0) {
+        __syncthreads();
+        // 3. the vertical blur of output rows [8 warp, 8 warp + 8), quantisation, stores
+        unsigned long long wp[R + 1];
+#pragma unroll
+        for (int k = 0; k <= R; ++k) wp[k] = f2_pack(w[k], w[k]);
+        const int t0 = 8 * warp;  // first output row (tile row); its accumulator row is t0 + R
+        unsigned long long hv[8 + 2 * R][2];
+#pragma unroll
+        for (int i = 0; i < 8 + 2 * R; ++i) {
+            const int ra = min(max(t0 + i, rlo), rhi - 1);  // tile row t0 + i - R
+            const float4 t = *reinterpret_cast<const float4 *>(A + ra * AP + cl);
+            hv[i][0] = f2_pack(t.x, t.y);
+            hv[i][1] = f2_pack(t.z, t.w);
+        }
+#pragma unroll
+        for (int o = 0; o < 8; ++o) {
+            unsigned long long p0 = f2_mul(wp[0], hv[o + R][0]), p1 = f2_mul(wp[0], hv[o + R][1]);
+#pragma unroll
+            for (int k = 1; k <= R; ++k) {
+                p0 = f2_fma(wp[k], f2_add(hv[o + R - k][0], hv[o + R + k][0]), p0);
+                p1 = f2_fma(wp[k], f2_add(hv[o + R - k][1], hv[o + R + k][1]), p1);
+            }
+            const float2 a0 = f2_unpack(p0), a1 = f2_unpack(p1);
+            float ov[4] = {a0.x, a0.y, a1.x, a1.y};
+            store_group<T>(out + (t0 + o) * g.W + 4 * lane, ov, 4, M);
+        }
+    }
+    __syncthreads();
+    // the accumulator's rows inside the frame start the next item at zero
+    float4 *a4 = reinterpret_cast<float4 *>(A + rlo * AP);
+    for (int k = threadIdx.x; k < ((rhi - rlo) * AP) >> 2; k += blockDim.x) a4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// The fast finishing path applies: a full 128 x 128 tile, W a multiple of 4
+// (aligned noise quads), blur radius at most 4.
+__device__ __forceinline__ bool fast_finish_ok(const Geo &g) {
+    return g.x1 - g.x0 == 128 && g.y1 - g.y0 == 128 && (g.W & 3) == 0 && g.R <= 4;
+}
+
+template <typename T>
+__device__ __forceinline__ void finish_fast_r(const KernelArgs &a, const Geo &g, const synthpix_pair_desc &D,
+                                              const float *wtab, int frame, const EpiK &K, const Smem &s,
+                                              const AccSource &src) {
+    switch (g.R) {
+    case 0: finish_fast<T, 0>(a, g, D, wtab, frame, K, s, src); break;
+    case 1: finish_fast<T, 1>(a, g, D, wtab, frame, K, s, src); break;
+    case 2: finish_fast<T, 2>(a, g, D, wtab, frame, K, s, src); break;
+    case 3: finish_fast<T, 3>(a, g, D, wtab, frame, K, s, src); break;
+    default: finish_fast<T, 4>(a, g, D, wtab, frame, K, s, src); break;
+    }
+}
+
 template <typename I>
 __device__ __forceinline__ I to_inter(float v);
 template <>
@@ -1431,10 +1627,12 @@ __device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo
     const float *wtab = reinterpret_cast<const float *>(buf + kStagePlan);
     const Geo g = make_geo(D, pl, a.tile, it.tile, pl.halo);
     const bool fused = a.inter_dtype == SYNTHPIX_F32;
-    const bool illum = fused ? illum_factors(g, D, s) : false;
+    const float imax = D.i_max > 0.0f ? D.i_max : 1.0f;
+    const float unit = imax * kFixedUnit;
+    const EpiK K = epi_consts(D, it.frame, unit);
+    if (fused) illum_factors(g, D, K, s);
 
     // splat, chunk by chunk of staged records
-    const float imax = D.i_max > 0.0f ? D.i_max : 1.0f;
     const float scale = kFixedScale / imax;
     const Acc acc{sh_addr(s.acc), s.carry, g.AP};
     uint32_t done = 0;
@@ -1462,10 +1660,9 @@ __device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo
         else after.pair = -1;
     }
 
-    const float unit = imax * kFixedUnit;
     const bool wrapped = sh_wrap != 0;
-    if (wrapped) wrapped_to_float(s, g, unit);
-    const AccSource src{s.acc + g.aoff, g.AP, unit, wrapped};
+    if (wrapped) wrapped_to_float(s, g);
+    const AccSource src{s.acc + g.aoff, g.AP, wrapped};
     if (!fused) {
         // halo 0: the accumulator rectangle is the tile (ax0 = ex0 = x0)
         const int64_t HW = (int64_t)g.H * g.W;
@@ -1473,14 +1670,18 @@ __device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo
         const float iew = 1.0f / (float)g.EW;
         for (int idx = threadIdx.x; idx < g.EH * g.EW; idx += blockDim.x) {
             const int r = small_div(idx, iew), c = idx - r * g.EW;
-            const float S = src.pixel(r, c);
+            const float S = src.pixel(r, c) * unit;  // full scale
             const int64_t o = base + (int64_t)(g.ey0 + r) * g.W + (g.ex0 + c);
             if (a.inter_dtype == SYNTHPIX_F16) reinterpret_cast<__half *>(a.inter)[o] = to_inter<__half>(S);
             else reinterpret_cast<__nv_bfloat16 *>(a.inter)[o] = to_inter<__nv_bfloat16>(S);
         }
         return;  // the caller's loop ends with a barrier
     }
-    finish_pass1(a, g, D, it.frame, illum, s, src);
+    if (NT == 512 && fast_finish_ok(g)) {
+        finish_fast_r<T>(a, g, D, wtab, it.frame, K, s, src);
+        return;
+    }
+    finish_pass1(a, g, K, s, src);
     __syncthreads();
     finish_rest<T>(a, g, D, wtab, it.frame, s, true);
 }
@@ -1641,12 +1842,13 @@ __global__ void __launch_bounds__(kSplatThreads) k_finish(KernelArgs a) {
     const PairPlan pl = a.plan[it.pair];
     if (threadIdx.x < kBlurStride) wtab[threadIdx.x] = a.blur_w[(int64_t)it.pair * kBlurStride + threadIdx.x];
     const Geo g = make_geo(D, pl, a.tile, it.tile, pl.blur_r);
-    const bool illum = illum_factors(g, D, s);
+    const EpiK K = epi_consts(D, it.frame, 1.0f);  // the intermediate frames hold S at full scale
+    illum_factors(g, D, K, s);
     __syncthreads();
     const I *S16 = reinterpret_cast<const I *>(a.inter) + pl.inter_base + (int64_t)it.frame * g.H * g.W;
     const bool vec = (g.W & 3) == 0 && (reinterpret_cast<uintptr_t>(S16) & 7) == 0;
     const InterSource<I> src{S16, g.W, g.ey0, g.ax0, vec};
-    finish_pass1(a, g, D, it.frame, illum, s, src);
+    finish_pass1(a, g, K, s, src);
     __syncthreads();
     finish_rest<T>(a, g, D, wtab, it.frame, s, false);
 }
