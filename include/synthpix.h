@@ -154,12 +154,14 @@ typedef struct synthpix_batch_desc {
     int32_t  integrator;         /* SYNTHPIX_RK4 or SYNTHPIX_EULER                      */
     int32_t  n_substeps;         /* substeps over dt, 1..1024                          */
     float    dt;                 /* time between the frames, in frames (|dt| <= 64)    */
-    int32_t  tile;               /* square screen tile edge: 16, 32, 64 or 128, or 0
-                                    for a default from the frame sizes (128 when the
-                                    mean frame area is >= 512x512, 64 when >= 256x256,
-                                    else 32).  Tile 128 fails with
-                                    SYNTHPIX_EUNSUPPORTED when the largest blur radius
-                                    needs more shared memory than a CTA has.           */
+    int32_t  tile;               /* square screen tile edge of every pair: 16, 32, 64 or
+                                    128; or 0: an edge per frame size class (frame area
+                                    < 2^15, < 2^17, < 2^19 pixels, larger), from the
+                                    autotuner's table where synthpix_autotune has an
+                                    entry for the class, else 32, 64, 128, 128.  Tile
+                                    128 fails with SYNTHPIX_EUNSUPPORTED when the
+                                    largest blur radius needs more shared memory than a
+                                    CTA has.                                           */
     int32_t  flags;              /* 0 or SYNTHPIX_FLAG_GATHER_ADVECT.  By default a
                                     seeded render advects the particles tile by tile:
                                     the flow nodes under each frame-1 tile are staged
@@ -175,7 +177,7 @@ typedef struct synthpix_batch_desc {
 /*
  * Bytes of device workspace synthpix_render_pairs needs for this batch
  * (a 256-byte aligned region the caller allocates).  With batch->tile = 0 it
- * is the largest over the tile edges synthpix_autotune_tile tries, so one
+ * is an upper bound over every tuning the autotuners try or cache, so one
  * workspace serves every choice.  Returns 0 and sets the last error if the
  * descriptors are invalid.  Only the host arrays are read.
  */
@@ -311,9 +313,10 @@ int synthpix_render_pairs_staged(const synthpix_batch_desc *batch, const synthpi
  *    synthpix_workspace_bytes) is rejected with SYNTHPIX_EWORKSPACE and a
  *    message, before anything is launched.
  *  - The scratch needed is that of the plan the render runs: the tile edge
- *    batch->tile, or for 0 the default edge the render picks (so a batch can
- *    fit here although synthpix_workspace_bytes, which for tile 0 covers
- *    every edge the autotuner tries, reports more).
+ *    batch->tile, or for 0 the edges the render picks (the autotuner's table
+ *    or the defaults), so a batch can fit here although
+ *    synthpix_workspace_bytes, which for tile 0 covers every tuning, reports
+ *    more.
  *  - The first call on a device looks up the array's device address on that
  *    device (cudaGetSymbolAddress with the device current) and caches it;
  *    make that first call on each device before any stream capture.
@@ -334,9 +337,11 @@ int synthpix_render_pairs_noalloc(const synthpix_batch_desc *batch, const synthp
                                   const float *flows, void *images, void *stream);
 
 /*
- * Autotuner of the screen tile edge (a scheduling parameter; the paper has no
- * counterpart).  Renders the batch with each candidate edge (16, 32, 64,
- * 128; edges whose shared memory does not fit the blur radius are skipped):
+ * Autotuner of one screen tile edge for the whole batch (a scheduling
+ * parameter; the paper has no counterpart; synthpix_autotune below tunes an
+ * edge per frame size class and more, and caches the result).  Renders the
+ * batch with each candidate edge (16, 32, 64, 128; edges whose shared memory
+ * does not fit the blur radius are skipped):
  * once to warm up, then `reps` (1..1000) timed times on `stream`, timed with
  * CUDA events, and returns the fastest edge in *best_tile and its mean time
  * per render in *best_ms (nullable).  The images are overwritten.  The
@@ -350,6 +355,65 @@ int synthpix_autotune_tile(const synthpix_batch_desc *batch, const synthpix_pair
                            const float *flows, void *images,
                            void *workspace, size_t workspace_bytes, void *stream,
                            int32_t reps, int32_t *best_tile, float *best_ms);
+
+/*
+ * Launch parameters of a render (a scheduling choice; the paper has no
+ * counterpart beyond batching, Section 2 "Configuration file").  Results
+ * never depend on them (exact fixed-point sums; every finishing path has the
+ * same arithmetic), only the speed does.
+ */
+typedef struct synthpix_tuning {
+    int32_t tile[4];            /* screen tile edge per frame size class, by frame area:
+                                   < 2^15 pixels, < 2^17, < 2^19, larger; 16, 32, 64 or
+                                   128, or 0 for a class the batch does not have          */
+    int32_t records_per_stage;  /* round-particle records staged on chip per chunk of a tile */
+    int32_t register_epilogue;  /* 1: full 128 x 128 tiles finish with the blur in
+                                   registers; 0: with the shared-memory passes            */
+    float   ms;                 /* mean time of one render (synthpix_autotune), else 0    */
+    int32_t reserved[2];
+} synthpix_tuning;
+
+/*
+ * Autotuner of the launch parameters (Section 2 / 3.3: batching amortises
+ * overhead; the tile edges, records per stage and blur path are this
+ * library's).  The batch must have tile = 0.  Starting from the default edges
+ * (32, 64, 128, 128 by size class), it renders the batch with each candidate
+ * edge of each size class present (the class with the most pixels first,
+ * the others' best edges kept), then with each records-per-stage candidate,
+ * then with the other epilogue path: once to warm up, then `reps` (1..1000)
+ * timed times each on `stream` with CUDA events.  Candidates that do not fit
+ * on chip (shared memory for the blur radius) are skipped.  The best
+ * parameters are written to *out (nullable) and kept in a process-wide table
+ * keyed by (frame size class, largest particle diameter in quarter pixels,
+ * blur radius, general-shape splat, fused epilogue); every later render of a
+ * batch with tile = 0 whose classes have entries uses them, with no timing.
+ * The table is guarded by a mutex: renders, lookups and autotune calls may
+ * come from any host thread.  The images are overwritten.  The workspace must
+ * hold synthpix_workspace_bytes for the batch (tile = 0).  Unlike the render
+ * entry points this call BLOCKS the host until its timings are done.
+ */
+int synthpix_autotune(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
+                      const synthpix_pair_desc *pairs_dev, int32_t n_pairs, const float *flows, void *images,
+                      void *workspace, size_t workspace_bytes, void *stream, int32_t reps, synthpix_tuning *out);
+
+/* The parameters a render of this batch runs with now (batch->tile, or the
+   table's entries and the defaults for tile = 0); ms = 0.  No device call. */
+int synthpix_tuning_lookup(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs, int32_t n_pairs,
+                           synthpix_tuning *out);
+
+/*
+ * Writes parameters into the autotuner's table for this batch's classes
+ * (tile = 0 batches), e.g. ones saved from an earlier process: the tile
+ * edges of the classes present (others ignored), records_per_stage
+ * (1..4096; larger than the splat's staging buffers hold for the largest
+ * edge gives SYNTHPIX_EUNSUPPORTED) and register_epilogue (0 or 1); ms is
+ * ignored.  No device call.
+ */
+int synthpix_tuning_set(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs, int32_t n_pairs,
+                        const synthpix_tuning *tuning);
+
+/* Empties the autotuner's table (renders fall back to the defaults). */
+void synthpix_tuning_clear(void);
 
 /* Message of the last failing call on this host thread ("" if none). */
 const char *synthpix_last_error(void);

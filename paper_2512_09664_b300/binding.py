@@ -25,7 +25,8 @@ DTYPE_CODE = {"f32": 0, "f16": 1, "bf16": 2, "u8": 3, "u16": 4}
 INTEGRATOR_CODE = {"rk4": 0, "euler": 1}
 _EXPORTS = ("synthpix_workspace_bytes", "synthpix_render_pairs", "synthpix_render_pairs_staged",
             "synthpix_render_pairs_from", "synthpix_seed_particles", "synthpix_advect_particles",
-            "synthpix_render_backward", "synthpix_autotune_tile", "synthpix_render_pairs_noalloc",
+            "synthpix_render_backward", "synthpix_autotune_tile", "synthpix_autotune", "synthpix_tuning_lookup",
+            "synthpix_tuning_set", "synthpix_tuning_clear", "synthpix_render_pairs_noalloc",
             "synthpix_fourier_flows", "synthpix_fourier_flows_workspace_bytes", "synthpix_match_histogram",
             "synthpix_match_histogram_workspace_bytes", "synthpix_last_error", "synthpix_version")
 STAGES = ("plan", "seed_advect", "bin_scan", "bin_scatter", "splat_epilogue")
@@ -57,7 +58,16 @@ class BatchDesc(C.Structure):
     ]
 
 
-assert C.sizeof(PairDesc) == 160 and C.sizeof(BatchDesc) == 64
+class Tuning(C.Structure):
+    _fields_ = [("tile", C.c_int32 * 4), ("records_per_stage", C.c_int32), ("register_epilogue", C.c_int32),
+                ("ms", C.c_float), ("reserved", C.c_int32 * 2)]
+
+    def as_dict(self):
+        return {"tile": list(self.tile), "records_per_stage": self.records_per_stage,
+                "register_epilogue": self.register_epilogue, "ms": self.ms}
+
+
+assert C.sizeof(PairDesc) == 160 and C.sizeof(BatchDesc) == 64 and C.sizeof(Tuning) == 36
 
 _lib = None
 
@@ -100,6 +110,15 @@ def lib():
                                              vp, vp, vp, sz, vp, C.c_int32, C.POINTER(C.c_int32),
                                              C.POINTER(C.c_float)]
         L.synthpix_autotune_tile.restype = C.c_int
+        L.synthpix_autotune.argtypes = [C.POINTER(BatchDesc), C.POINTER(PairDesc), vp, C.c_int32,
+                                        vp, vp, vp, sz, vp, C.c_int32, C.POINTER(Tuning)]
+        L.synthpix_autotune.restype = C.c_int
+        L.synthpix_tuning_lookup.argtypes = [C.POINTER(BatchDesc), C.POINTER(PairDesc), C.c_int32, C.POINTER(Tuning)]
+        L.synthpix_tuning_lookup.restype = C.c_int
+        L.synthpix_tuning_set.argtypes = [C.POINTER(BatchDesc), C.POINTER(PairDesc), C.c_int32, C.POINTER(Tuning)]
+        L.synthpix_tuning_set.restype = C.c_int
+        L.synthpix_tuning_clear.argtypes = []
+        L.synthpix_tuning_clear.restype = None
         L.synthpix_fourier_flows_workspace_bytes.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32]
         L.synthpix_fourier_flows_workspace_bytes.restype = sz
         L.synthpix_fourier_flows.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
@@ -296,6 +315,17 @@ def match_histogram(pk: Packed, images_dev, target_dev, workspace_dev=None, stre
     return match_histogram_desc(pk.batch, pk.pairs, pk.n_pairs, images_dev, target_dev, workspace_dev, stream)
 
 
+def size_class(height: int, width: int) -> int:
+    """Frame size class of the tuning table (the library's rule): area < 2^15, < 2^17, < 2^19, larger."""
+    a = height * width
+    return 0 if a < (1 << 15) else (1 if a < (1 << 17) else (2 if a < (1 << 19) else 3))
+
+
+def tuning_clear():
+    """Empty the library's tuning table (synthpix_tuning_clear)."""
+    lib().synthpix_tuning_clear()
+
+
 class Renderer:
     """Device buffers for repeated rendering of one packed workload."""
 
@@ -325,7 +355,7 @@ class Renderer:
         return self.images
 
     def autotune(self, reps: int = 3, stream=None):
-        """Pick the tile edge with synthpix_autotune_tile; later renders use it."""
+        """Pick one tile edge for the whole batch with synthpix_autotune_tile; later renders use it."""
         import torch
         st = stream if stream is not None else torch.cuda.current_stream()
         best, ms = C.c_int32(0), C.c_float(0.0)
@@ -342,6 +372,48 @@ class Renderer:
             _check(rc)
         self.pk.batch.tile = best.value
         return best.value, ms.value
+
+    def _tile0(self):
+        """Switch to tile 0 (per-class edges from the tuning table), growing the workspace if needed."""
+        import torch
+        self.pk.batch.tile = 0
+        ws = workspace_bytes(self.pk)
+        if ws > self.workspace.numel():
+            self.workspace = torch.empty(ws, dtype=torch.uint8, device=self.device)
+
+    def tune(self, reps: int = 3, stream=None) -> dict:
+        """synthpix_autotune: tile edge per size class, records per stage and epilogue path.
+
+        The result goes into the library's table; this renderer switches to
+        tile 0, so its later renders use it (as does any batch of the same
+        classes).  Returns the chosen parameters and their time per render.
+        """
+        import torch
+        st = stream if stream is not None else torch.cuda.current_stream()
+        self._tile0()
+        t = Tuning()
+        _check(lib().synthpix_autotune(
+            C.byref(self.pk.batch), self.pk.pairs,
+            C.c_void_p(self.pairs_dev.data_ptr()) if self.pairs_dev is not None else None, self.pk.n_pairs,
+            C.c_void_p(self.flows.data_ptr()), C.c_void_p(self.images.data_ptr()),
+            C.c_void_p(self.workspace.data_ptr()), self.workspace.numel(), C.c_void_p(st.cuda_stream), reps,
+            C.byref(t)))
+        return t.as_dict()
+
+    def tuning(self) -> dict:
+        """The parameters this renderer's next render runs with (synthpix_tuning_lookup)."""
+        t = Tuning()
+        _check(lib().synthpix_tuning_lookup(C.byref(self.pk.batch), self.pk.pairs, self.pk.n_pairs, C.byref(t)))
+        return t.as_dict()
+
+    def set_tuning(self, tile, records_per_stage: int, register_epilogue: int):
+        """Write parameters into the tuning table for this batch's classes and switch to tile 0."""
+        self._tile0()
+        t = Tuning()
+        for k in range(4):
+            t.tile[k] = int(tile[k])
+        t.records_per_stage, t.register_epilogue = int(records_per_stage), int(register_epilogue)
+        _check(lib().synthpix_tuning_set(C.byref(self.pk.batch), self.pk.pairs, self.pk.n_pairs, C.byref(t)))
 
     def capture(self):
         """Capture one render into a CUDA graph (descriptors must be on the device)."""

@@ -1,10 +1,13 @@
 // Host entry points of the C ABI declared in include/synthpix.h: argument
 // validation, workspace layout and the launch sequence.  Nothing here touches
 // the device before every argument has been checked.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -23,9 +26,18 @@ int fail(int code, const char *fmt, ...) {
 
 bool finite(float v) { return std::isfinite(v); }
 
+// Launch parameters a render runs with (a scheduling choice: results do not
+// depend on them).
+struct Tuning {
+    spx::TileRule rule;  // tile edge per frame size class
+    int32_t rec_buf;     // bytes of each staged-records buffer of the splat
+    int32_t reg_epi;     // 1: full 128 x 128 tiles finish with the register blur
+};
+
 struct Plan {
     spx::Layout L;
-    int32_t tile;
+    Tuning T;
+    int32_t tile;     // largest tile edge of the batch's pairs
     int32_t fused;
     int32_t max_halo;
     int32_t max_r;
@@ -104,32 +116,127 @@ int check_pair(const synthpix_pair_desc &d, int b) {
     return SYNTHPIX_OK;
 }
 
-// Tile edge used when batch->tile is 0, by the batch's mean frame area:
-// 128 from 512 x 512 up, 64 from 256 x 256 up (fewer particles rendered
-// twice at tile borders, fewer work items), else 32 (enough work items for
-// small frames).
-int default_tile(const synthpix_pair_desc *pairs, int32_t n_pairs) {
-    double area = 0.0;
-    for (int32_t b = 0; b < n_pairs; ++b) area += (double)pairs[b].height * pairs[b].width;
-    const double mean = n_pairs > 0 ? area / n_pairs : 0.0;
-    return mean >= 262144.0 ? 128 : (mean >= 65536.0 ? 64 : 32);
+// Tile edges used when batch->tile is 0 and no tuned entry exists, by frame
+// size class: 32 below 2^15 pixels (enough work items for small frames), 64
+// below 2^17, 128 from there (fewer particles rendered twice at tile
+// borders, fewer work items).
+constexpr spx::TileRule kDefaultRule = {{32, 64, 128, 128}};
+constexpr int kTileCandidates[4] = {16, 32, 64, 128};
+constexpr int kRecBufCandidates[3] = {8192, 10240, spx::kRecBufBytesLarge};
+
+spx::TileRule uniform_rule(int t) { return spx::TileRule{{t, t, t, t}}; }
+
+Tuning default_tuning(const spx::TileRule &rule) {
+    Tuning T;
+    T.rule = rule;
+    T.rec_buf = 0;  // resolved from the largest edge by make_plan_tuned
+    T.reg_epi = 1;
+    return T;
 }
 
-int make_plan_tile(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs, int32_t n_pairs, int tile,
-                   Plan &P);
+// The autotuner's cache: per (frame size class, largest diameter in quarter
+// pixels, blur radius, general-shape splat, fused epilogue) the tuned tile
+// edge, and the batch-level choices (records per stage, register epilogue)
+// of the batch that was tuned.  Guarded by a mutex; renders with tile 0 read
+// it, synthpix_autotune writes it (after its timed renders, never while
+// holding the lock).
+struct TuneKey {
+    int32_t cls, dq, r, general, fused;
+    bool operator<(const TuneKey &o) const {
+        if (cls != o.cls) return cls < o.cls;
+        if (dq != o.dq) return dq < o.dq;
+        if (r != o.r) return r < o.r;
+        if (general != o.general) return general < o.general;
+        return fused < o.fused;
+    }
+};
+struct TuneEntry {
+    int32_t tile, rec_buf, reg_epi;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneEntry> g_tune;
 
-int make_plan(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs, int32_t n_pairs, Plan &P) {
+// Per size class of the batch: present, its key, and its pixels (work).
+struct ClassInfo {
+    bool present[spx::kSizeClasses];
+    TuneKey key[spx::kSizeClasses];
+    double pixels[spx::kSizeClasses];
+    int largest;  // the class with the most pixels
+};
+
+ClassInfo batch_classes(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs, int32_t n_pairs) {
+    ClassInfo c;
+    float dmax[spx::kSizeClasses] = {0.f, 0.f, 0.f, 0.f};
+    int32_t rmax[spx::kSizeClasses] = {0, 0, 0, 0};
+    bool general = false;
+    for (int k = 0; k < spx::kSizeClasses; ++k) {
+        c.present[k] = false;
+        c.pixels[k] = 0.0;
+    }
+    for (int32_t b = 0; b < n_pairs; ++b) {
+        const int k = spx::size_class(pairs[b].height, pairs[b].width);
+        c.present[k] = true;
+        c.pixels[k] += (double)pairs[b].height * pairs[b].width;
+        dmax[k] = std::max(dmax[k], spx::pair_max_diameter(pairs[b]));
+        rmax[k] = std::max(rmax[k], spx::blur_radius_of(pairs[b].blur_sigma));
+        general = general || spx::pair_general_shape(pairs[b]);
+    }
+    c.largest = 0;
+    for (int k = 0; k < spx::kSizeClasses; ++k) {
+        c.key[k] = TuneKey{k, (int32_t)std::ceil(4.0f * dmax[k]), rmax[k], general ? 1 : 0,
+                           batch->inter_dtype == SYNTHPIX_F32 ? 1 : 0};
+        if (c.pixels[k] > c.pixels[c.largest]) c.largest = k;
+    }
+    return c;
+}
+
+// The tuning a render runs with: batch->tile for every class when it is
+// set; otherwise the cached entries of the batch's classes, default edges
+// where none is cached.
+Tuning resolve_tuning(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs, int32_t n_pairs) {
+    if (batch->tile != 0) return default_tuning(uniform_rule(batch->tile));
+    Tuning T = default_tuning(kDefaultRule);
+    if (n_pairs <= 0 || !pairs) return T;
+    const ClassInfo c = batch_classes(batch, pairs, n_pairs);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (int k = 0; k < spx::kSizeClasses; ++k) {
+        if (!c.present[k]) continue;
+        const auto it = g_tune.find(c.key[k]);
+        if (it == g_tune.end()) continue;
+        T.rule.edge[k] = it->second.tile;
+        if (k == c.largest) {
+            T.rec_buf = it->second.rec_buf;
+            T.reg_epi = it->second.reg_epi;
+        }
+    }
+    return T;
+}
+
+int make_plan_tuned(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs, int32_t n_pairs,
+                    const Tuning &T, Plan &P);
+
+int check_counts(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs, int32_t n_pairs) {
     int rc = check_batch(batch);
     if (rc) return rc;
     if (n_pairs < 0 || n_pairs > (1 << 20)) return fail(SYNTHPIX_EINVAL, "n_pairs %d outside 0..2^20", n_pairs);
     if (n_pairs > 0 && !pairs) return fail(SYNTHPIX_EINVAL, "pairs is NULL");
-    return make_plan_tile(batch, pairs, n_pairs, batch->tile ? batch->tile : default_tile(pairs, n_pairs), P);
+    return SYNTHPIX_OK;
 }
 
-int make_plan_tile(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs, int32_t n_pairs, int tile,
-                   Plan &P) {
+int make_plan(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs, int32_t n_pairs, Plan &P) {
+    const int rc = check_counts(batch, pairs, n_pairs);
+    if (rc) return rc;
+    return make_plan_tuned(batch, pairs, n_pairs, resolve_tuning(batch, pairs, n_pairs), P);
+}
+
+// The workspace plan of a batch under tuning T.  With worst = true, every
+// pair takes the largest of its per-tile sizes over all candidate edges and
+// the carry words those of the largest edge: an upper bound for any tuning.
+int make_plan_any(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs, int32_t n_pairs,
+                  const Tuning &T, bool worst, Plan &P) {
     int rc;
-    P.tile = tile;
+    P.T = T;
+    P.tile = 0;
     P.fused = batch->inter_dtype == SYNTHPIX_F32 ? 1 : 0;
     P.max_halo = 0;
     P.max_r = 0;
@@ -141,7 +248,17 @@ int make_plan_tile(const synthpix_batch_desc *batch, const synthpix_pair_desc *p
     for (int32_t b = 0; b < n_pairs; ++b) {
         rc = check_pair(pairs[b], b);
         if (rc) return rc;
-        const spx::PairGeom g = spx::pair_geom(pairs[b], P.tile, P.fused != 0);
+        const int32_t t = worst ? 128 : spx::rule_tile(T.rule, pairs[b]);
+        if (t != 16 && t != 32 && t != 64 && t != 128)
+            return fail(SYNTHPIX_EINVAL, "pair %d: tile edge %d is not 16, 32, 64 or 128", b, t);
+        P.tile = std::max(P.tile, t);
+        spx::PairGeom g = spx::pair_geom(pairs[b], t, P.fused != 0);
+        if (worst)
+            for (int c : kTileCandidates) {
+                const spx::PairGeom h = spx::pair_geom(pairs[b], c, P.fused != 0);
+                g.ntiles = std::max(g.ntiles, h.ntiles);
+                g.list_cap = std::max(g.list_cap, h.list_cap);
+            }
         L.n_part += pairs[b].n_particles;
         L.n_tiles += 2LL * g.ntiles;
         L.n_list += 2LL * g.list_cap;
@@ -178,14 +295,31 @@ int make_plan_tile(const synthpix_batch_desc *batch, const synthpix_pair_desc *p
     L.rec = take((size_t)L.n_list * rec_bytes + 64);  // + read-over of 16-byte staging
     L.adv = take((size_t)(L.n_list / 2) * sizeof(spx::Record));  // frame-1 segments only
     L.inter = take((size_t)L.n_inter * 2);
+    if (P.tile == 0) P.tile = 16;  // no pairs: nothing is launched
     {  // carry words of the splat's CTAs: one accumulator's worth each
-        const int E = tile + 2 * P.max_r;
+        const int E = P.tile + 2 * P.max_r;
         L.carry_stride = (int64_t)E * spx::pitch_cap(E);
-        L.carry = take((size_t)spx::splat_max_ctas(tile, L.n_tiles) * (size_t)L.carry_stride * 4);
+        size_t cw = (size_t)spx::splat_max_ctas(P.tile, L.n_tiles) * (size_t)L.carry_stride;
+        if (worst)  // the largest over every edge the pairs could take
+            for (int c : kTileCandidates) {
+                const int Ec = c + 2 * P.max_r;
+                cw = std::max(cw, (size_t)spx::splat_max_ctas(c, L.n_tiles) * (size_t)Ec * spx::pitch_cap(Ec));
+            }
+        L.carry = take(cw * 4);
     }
+    if (P.T.rec_buf == 0) P.T.rec_buf = spx::rec_buf_bytes_for(P.tile);
+    // at least one record of either size; at most what the splat's per-thread slots cover
+    if (P.T.rec_buf < spx::kStageHeader + 32 + (int)sizeof(spx::RecordG) ||
+        P.T.rec_buf > spx::rec_buf_bytes_for(P.tile) || (P.T.rec_buf & 15))
+        return fail(SYNTHPIX_EUNSUPPORTED, "%d-byte record buffers do not fit tile edge %d", P.T.rec_buf, P.tile);
     L.gfr = take((size_t)L.n_part * 2 * sizeof(float4));
     L.total = o;
     return SYNTHPIX_OK;
+}
+
+int make_plan_tuned(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs, int32_t n_pairs,
+                    const Tuning &T, Plan &P) {
+    return make_plan_any(batch, pairs, n_pairs, T, false, P);
 }
 
 size_t elem_size(int32_t dt) {
@@ -195,8 +329,6 @@ size_t elem_size(int32_t dt) {
     default: return 2;
     }
 }
-
-constexpr int kTileCandidates[4] = {16, 32, 64, 128};
 
 }  // namespace
 
@@ -214,12 +346,10 @@ size_t synthpix_workspace_bytes(const synthpix_batch_desc *batch, const synthpix
     Plan P;
     if (make_plan(batch, pairs, n_pairs, P) != SYNTHPIX_OK) return 0;
     size_t need = P.L.total;
-    if (batch->tile == 0) {  // large enough for every tile the autotuner tries
-        for (int t : kTileCandidates) {
-            Plan Q;
-            if (make_plan_tile(batch, pairs, n_pairs, t, Q) != SYNTHPIX_OK) return 0;
-            if (Q.L.total > need) need = Q.L.total;
-        }
+    if (batch->tile == 0) {  // large enough for every tuning the autotuner may try or cache
+        Plan Q;
+        if (make_plan_any(batch, pairs, n_pairs, default_tuning(kDefaultRule), true, Q) != SYNTHPIX_OK) return 0;
+        need = std::max(need, Q.L.total);
     }
     g_err[0] = 0;
     return need;
@@ -240,9 +370,12 @@ struct Extra {
 
 static int run(Mode mode, const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
                const synthpix_pair_desc *pairs_dev, int32_t n_pairs, const float *flows, void *images,
-               void *workspace, size_t workspace_bytes, void *stream, cudaEvent_t const *ev, const Extra &x) {
+               void *workspace, size_t workspace_bytes, void *stream, cudaEvent_t const *ev, const Extra &x,
+               const Tuning *tuning = nullptr) {
     Plan P;
-    int rc = make_plan(batch, pairs, n_pairs, P);
+    int rc = check_counts(batch, pairs, n_pairs);
+    if (rc) return rc;
+    rc = make_plan_tuned(batch, pairs, n_pairs, tuning ? *tuning : resolve_tuning(batch, pairs, n_pairs), P);
     if (rc) return rc;
     if (n_pairs == 0) {
         g_err[0] = 0;
@@ -295,7 +428,7 @@ static int run(Mode mode, const synthpix_batch_desc *batch, const synthpix_pair_
     uint32_t *ticket = reinterpret_cast<uint32_t *>(ws + L.check + 16);
     float *blur_w = reinterpret_cast<float *>(ws + L.blur);
     if (ev && ev[0]) cudaEventRecord(ev[0], st);
-    e = spx::launch_plan(descs, n_pairs, P.tile, P.fused, plan, L, check, blur_w, ticket,
+    e = spx::launch_plan(descs, n_pairs, P.T.rule, P.fused, plan, L, check, blur_w, ticket,
                          mode == Mode::Render ? reinterpret_cast<uint32_t *>(ws + L.count) : nullptr, st);
     if (e != cudaSuccess) return fail(SYNTHPIX_ECUDA, "plan launch: %s", cudaGetErrorString(e));
     if (ev && ev[1]) cudaEventRecord(ev[1], st);
@@ -335,7 +468,8 @@ static int run(Mode mode, const synthpix_batch_desc *batch, const synthpix_pair_
     a.tiled = (mode == Mode::Render && !x.particles_in && !P.ext && !(batch->flags & SYNTHPIX_FLAG_GATHER_ADVECT))
                   ? 1 : 0;
     a.ticket = ticket;
-    a.rec_buf_bytes = spx::rec_buf_bytes_for(P.tile);
+    a.rec_buf_bytes = P.T.rec_buf;
+    a.reg_epilogue = P.T.reg_epi;
     a.blur_w = blur_w;
     a.inter_dtype = batch->inter_dtype;
     a.inter = ws + L.inter;
@@ -374,9 +508,33 @@ static int run(Mode mode, const synthpix_batch_desc *batch, const synthpix_pair_
 
 static int render_impl(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
                        const synthpix_pair_desc *pairs_dev, int32_t n_pairs, const float *flows, void *images,
-                       void *workspace, size_t workspace_bytes, void *stream, cudaEvent_t const *ev) {
+                       void *workspace, size_t workspace_bytes, void *stream, cudaEvent_t const *ev,
+                       const Tuning *tuning = nullptr) {
     return run(Mode::Render, batch, pairs, pairs_dev, n_pairs, flows, images, workspace, workspace_bytes, stream, ev,
-               Extra());
+               Extra(), tuning);
+}
+
+// Mean time (ms) of `reps` renders with tuning T after one warm-up render, on
+// `stream` (blocks the host).  SYNTHPIX_EUNSUPPORTED: the tuning does not fit
+// the batch (shared memory); other errors as the render's.
+static int time_renders(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
+                        const synthpix_pair_desc *pairs_dev, int32_t n_pairs, const float *flows, void *images,
+                        void *workspace, size_t workspace_bytes, void *stream, int32_t reps, const Tuning &T,
+                        cudaEvent_t e0, cudaEvent_t e1, float *ms) {
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int rc = render_impl(batch, pairs, pairs_dev, n_pairs, flows, images, workspace, workspace_bytes, stream, nullptr,
+                         &T);
+    if (rc) return rc;
+    cudaEventRecord(e0, st);
+    for (int k = 0; k < reps && !rc; ++k)
+        rc = render_impl(batch, pairs, pairs_dev, n_pairs, flows, images, workspace, workspace_bytes, stream, nullptr,
+                         &T);
+    cudaEventRecord(e1, st);
+    if (rc) return rc;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(ms, e0, e1) != cudaSuccess)
+        return fail(SYNTHPIX_ECUDA, "autotune: event timing failed");
+    *ms /= (float)reps;
+    return SYNTHPIX_OK;
 }
 
 extern "C" {
@@ -396,35 +554,22 @@ int synthpix_autotune_tile(const synthpix_batch_desc *batch, const synthpix_pair
     Plan P;
     int rc = make_plan(batch, pairs, n_pairs, P);
     if (rc) return rc;
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         if (e0) cudaEventDestroy(e0);
         return fail(SYNTHPIX_ECUDA, "autotune: cudaEventCreate failed");
     }
-    synthpix_batch_desc b = *batch;
     float best = -1.0f;
     int best_t = 0;
     for (int t : kTileCandidates) {
-        b.tile = t;
-        rc = render_impl(&b, pairs, pairs_dev, n_pairs, flows, images, workspace, workspace_bytes, stream, nullptr);
+        float ms = 0.0f;
+        rc = time_renders(batch, pairs, pairs_dev, n_pairs, flows, images, workspace, workspace_bytes, stream, reps,
+                          default_tuning(uniform_rule(t)), e0, e1, &ms);
         if (rc == SYNTHPIX_EUNSUPPORTED) {  // this edge does not fit the blur radius on chip: try the others
             rc = SYNTHPIX_OK;
             continue;
         }
-        if (rc) break;  // warm-up; also validates the workspace for this tile
-        cudaEventRecord(e0, st);
-        for (int k = 0; k < reps && !rc; ++k)
-            rc = render_impl(&b, pairs, pairs_dev, n_pairs, flows, images, workspace, workspace_bytes, stream,
-                             nullptr);
-        cudaEventRecord(e1, st);
         if (rc) break;
-        float ms = 0.0f;
-        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-            rc = fail(SYNTHPIX_ECUDA, "autotune: event timing failed");
-            break;
-        }
-        ms /= (float)reps;
         if (best < 0.0f || ms < best) {
             best = ms;
             best_t = t;
@@ -438,6 +583,143 @@ int synthpix_autotune_tile(const synthpix_batch_desc *batch, const synthpix_pair
     if (best_ms) *best_ms = best;
     g_err[0] = 0;
     return SYNTHPIX_OK;
+}
+
+static void to_public(const Tuning &T, const ClassInfo &c, float ms, synthpix_tuning *out) {
+    for (int k = 0; k < spx::kSizeClasses; ++k) out->tile[k] = c.present[k] ? T.rule.edge[k] : 0;
+    out->records_per_stage = spx::rec_cap(T.rec_buf);
+    out->register_epilogue = T.reg_epi;
+    out->ms = ms;
+    out->reserved[0] = out->reserved[1] = 0;
+}
+
+int synthpix_autotune(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
+                      const synthpix_pair_desc *pairs_dev, int32_t n_pairs, const float *flows, void *images,
+                      void *workspace, size_t workspace_bytes, void *stream, int32_t reps, synthpix_tuning *out) {
+    if (!batch) return fail(SYNTHPIX_EINVAL, "batch is NULL");
+    if (batch->tile != 0) return fail(SYNTHPIX_EINVAL, "autotune needs batch->tile = 0");
+    if (reps < 1 || reps > 1000) return fail(SYNTHPIX_EINVAL, "reps %d outside 1..1000", reps);
+    Plan P;
+    int rc = make_plan(batch, pairs, n_pairs, P);
+    if (rc) return rc;
+    if (n_pairs == 0) return fail(SYNTHPIX_EINVAL, "autotune needs at least one pair");
+    const ClassInfo c = batch_classes(batch, pairs, n_pairs);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return fail(SYNTHPIX_ECUDA, "autotune: cudaEventCreate failed");
+    }
+    // coordinate descent from the defaults: each class's edge (largest class
+    // first), then the records per stage, then the epilogue variant
+    Tuning best = default_tuning(kDefaultRule);
+    float best_ms = -1.0f;
+    auto trial = [&](Tuning T) -> int {
+        float ms = 0.0f;
+        const int r = time_renders(batch, pairs, pairs_dev, n_pairs, flows, images, workspace, workspace_bytes,
+                                   stream, reps, T, e0, e1, &ms);
+        if (r == SYNTHPIX_EUNSUPPORTED) return SYNTHPIX_OK;  // does not fit on chip: not a candidate
+        if (r) return r;
+        if (best_ms < 0.0f || ms < best_ms) {
+            best_ms = ms;
+            best = T;
+        }
+        return SYNTHPIX_OK;
+    };
+    int order[spx::kSizeClasses], n_order = 0;
+    order[n_order++] = c.largest;
+    for (int k = spx::kSizeClasses - 1; k >= 0; --k)
+        if (c.present[k] && k != c.largest) order[n_order++] = k;
+    rc = trial(best);
+    for (int q = 0; q < n_order && !rc; ++q) {
+        const Tuning base = best;
+        for (int t : kTileCandidates) {
+            if (t == base.rule.edge[order[q]]) continue;
+            Tuning T = base;
+            T.rule.edge[order[q]] = t;
+            rc = trial(T);
+            if (rc) break;
+        }
+    }
+    if (!rc) {
+        const Tuning base = best;
+        for (int rb : kRecBufCandidates) {
+            Plan Q;
+            if (make_plan_tuned(batch, pairs, n_pairs, base, Q) != SYNTHPIX_OK) break;
+            if (rb == Q.T.rec_buf) continue;
+            Tuning T = base;
+            T.rec_buf = rb;
+            rc = trial(T);
+            if (rc) break;
+        }
+    }
+    if (!rc) {
+        Tuning T = best;
+        T.reg_epi = 1 - best.reg_epi;
+        rc = trial(T);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (best_ms < 0.0f) return fail(SYNTHPIX_EUNSUPPORTED, "autotune: no tuning fits the batch on chip");
+    {
+        Plan Q;
+        if (make_plan_tuned(batch, pairs, n_pairs, best, Q) == SYNTHPIX_OK) best.rec_buf = Q.T.rec_buf;
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        for (int k = 0; k < spx::kSizeClasses; ++k)
+            if (c.present[k]) g_tune[c.key[k]] = TuneEntry{best.rule.edge[k], best.rec_buf, best.reg_epi};
+    }
+    if (out) to_public(best, c, best_ms, out);
+    g_err[0] = 0;
+    return SYNTHPIX_OK;
+}
+
+int synthpix_tuning_lookup(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs, int32_t n_pairs,
+                           synthpix_tuning *out) {
+    if (!out) return fail(SYNTHPIX_EINVAL, "out is NULL");
+    Plan P;
+    const int rc = make_plan(batch, pairs, n_pairs, P);
+    if (rc) return rc;
+    to_public(P.T, batch_classes(batch, pairs, n_pairs), 0.0f, out);
+    g_err[0] = 0;
+    return SYNTHPIX_OK;
+}
+
+int synthpix_tuning_set(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs, int32_t n_pairs,
+                        const synthpix_tuning *t) {
+    if (!t) return fail(SYNTHPIX_EINVAL, "tuning is NULL");
+    if (!batch) return fail(SYNTHPIX_EINVAL, "batch is NULL");
+    if (batch->tile != 0) return fail(SYNTHPIX_EINVAL, "the table serves batches with tile = 0");
+    int rc = check_counts(batch, pairs, n_pairs);
+    if (rc) return rc;
+    if (t->register_epilogue != 0 && t->register_epilogue != 1)
+        return fail(SYNTHPIX_EINVAL, "register_epilogue must be 0 or 1");
+    if (t->records_per_stage < 1 || t->records_per_stage > 4096)
+        return fail(SYNTHPIX_EINVAL, "records_per_stage %d outside 1..4096", t->records_per_stage);
+    const ClassInfo c = batch_classes(batch, pairs, n_pairs);
+    Tuning T = default_tuning(kDefaultRule);
+    for (int k = 0; k < spx::kSizeClasses; ++k) {
+        if (!c.present[k]) continue;
+        const int e = t->tile[k];
+        if (e != 16 && e != 32 && e != 64 && e != 128)
+            return fail(SYNTHPIX_EINVAL, "tile[%d] = %d is not 16, 32, 64 or 128", k, e);
+        T.rule.edge[k] = e;
+    }
+    // the staged-buffer bytes that hold records_per_stage 24-byte records
+    T.rec_buf = (spx::kStageHeader + 32 + 24 * t->records_per_stage + 15) & ~15;
+    T.reg_epi = t->register_epilogue;
+    Plan P;
+    rc = make_plan_tuned(batch, pairs, n_pairs, T, P);  // validates the buffer against the largest edge
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (int k = 0; k < spx::kSizeClasses; ++k)
+        if (c.present[k]) g_tune[c.key[k]] = TuneEntry{T.rule.edge[k], T.rec_buf, T.reg_epi};
+    g_err[0] = 0;
+    return SYNTHPIX_OK;
+}
+
+void synthpix_tuning_clear(void) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune.clear();
 }
 
 int synthpix_render_pairs_from(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,

@@ -26,9 +26,26 @@ struct PairPlan {
     int32_t blur_r;      // ceil(3 * blur_sigma), 0 without blur
     int32_t halo;        // pixels a tile's bins extend beyond the tile (blur_r or 0)
     int32_t chunk_base;  // first particle chunk (kChunk particles) of the pair
-    int32_t pad;
+    int32_t tile;        // screen tile edge of the pair (16, 32, 64 or 128)
 };
 static_assert(sizeof(PairPlan) == 64, "PairPlan layout");
+
+// Screen tile edges by frame size class: a batch may render its small and
+// large frames with different tile edges in one launch sequence.  The class
+// of a pair is that of its frame area: < 2^15 pixels (up to about 181^2),
+// < 2^17 (362^2), < 2^19 (724^2), larger.  Host and device resolve a pair's
+// edge from the same rule (passed by value to the plan kernel).
+constexpr int kSizeClasses = 4;
+struct TileRule {
+    int32_t edge[kSizeClasses];
+};
+__host__ __device__ inline int size_class(int32_t height, int32_t width) {
+    const int64_t a = (int64_t)height * width;
+    return a < (1 << 15) ? 0 : (a < (1 << 17) ? 1 : (a < (1 << 19) ? 2 : 3));
+}
+__host__ __device__ inline int32_t rule_tile(const TileRule &r, const synthpix_pair_desc &d) {
+    return r.edge[size_class(d.height, d.width)];
+}
 
 // Screen tile edge and per-pair quantities shared by host and device.
 struct PairGeom {

@@ -12,7 +12,7 @@ struct KernelArgs {
     const PairPlan *plan;             // device plan (k_plan)
     const int32_t *check;             // 1 when the device plan matches the host's
     int32_t n_pairs;
-    int32_t tile;
+    int32_t tile;                     // largest tile edge of the batch's pairs (launch shapes, shared memory)
     int64_t n_part;                   // particles of all pairs
     int64_t n_tiles;                  // (pair, frame, tile) work items
     int64_t n_chunks;                 // particle chunks (kChunk particles of one pair)
@@ -43,7 +43,8 @@ struct KernelArgs {
     int32_t smem_edge;                // capacity edge of the on-chip tile (tile + 2 max radius)
     int32_t warp_scratch;             // floats of per-warp window scratch
     const float *blur_w;              // [n_pairs][kBlurStride] normalised taps w[|k|]
-    int32_t rec_buf_bytes;            // bytes of each staged-records buffer
+    int32_t rec_buf_bytes;            // bytes of each staged-records buffer (at most rec_buf_bytes_for(tile))
+    int32_t reg_epilogue;             // 1: full 128 x 128 tiles finish with the register blur
     int32_t inter_dtype;              // SYNTHPIX_F32: fused; F16 / BF16: intermediate frames
     void *inter;                      // 16-bit intermediate frames (non-fused path)
     const float *particles_in;        // NULL or [n_part][3] (x0, y0, d) replacing the seeded values
@@ -96,7 +97,7 @@ __host__ __device__ constexpr int rec_buf_bytes_for(int tile) { return tile >= 1
 constexpr size_t kMaxSmemBytes = 227 * 1024;  // dynamic shared memory of one CTA
 
 // count: NULL, or the per-(pair, frame, tile) bin counts, zeroed by the plan launch
-cudaError_t launch_plan(const synthpix_pair_desc *descs, int32_t n_pairs, int32_t tile, int32_t fused,
+cudaError_t launch_plan(const synthpix_pair_desc *descs, int32_t n_pairs, const TileRule &rule, int32_t fused,
                         PairPlan *plan, const Layout &L, int32_t *check, float *blur_w, uint32_t *ticket,
                         uint32_t *count, cudaStream_t st);
 // ev: NULL or kStageEvents events recorded at the stage boundaries.

@@ -36,7 +36,7 @@ constexpr int kPlanZeroWords = 16384;
 constexpr int kPlanTapPairs = 32;
 
 __global__ void __launch_bounds__(1024) k_plan(const synthpix_pair_desc *__restrict__ descs, int32_t n_pairs,
-                                               int32_t tile, int32_t fused, PairPlan *__restrict__ plan,
+                                               TileRule rule, int32_t fused, PairPlan *__restrict__ plan,
                                                int64_t want_part, int64_t want_tiles, int64_t want_list,
                                                int64_t want_inter, int64_t want_chunks, int32_t *__restrict__ check,
                                                float *__restrict__ blur_w, uint32_t *__restrict__ ticket,
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(1024) k_plan(const synthpix_pair_desc *__restr
     long long v[5] = {0, 0, 0, 0, 0};  // particles, tiles, bin slots, intermediate elements, chunks
     for (int b = b0; b < b1; ++b) {
         const synthpix_pair_desc d = descs[b];
-        const PairGeom g = pair_geom(d, tile, fused != 0);
+        const PairGeom g = pair_geom(d, rule_tile(rule, d), fused != 0);
         v[0] += d.n_particles;
         v[1] += 2LL * g.ntiles;
         v[2] += 2LL * g.list_cap;
@@ -111,6 +111,7 @@ __global__ void __launch_bounds__(1024) k_plan(const synthpix_pair_desc *__restr
     long long bc = s_w[4][warp] + inc[4] - v[4];
     for (int b = b0; b < b1; ++b) {
         const synthpix_pair_desc d = descs[b];
+        const int32_t tile = rule_tile(rule, d);
         const PairGeom g = pair_geom(d, tile, fused != 0);
         PairPlan p;
         p.part_base = bp;
@@ -124,7 +125,7 @@ __global__ void __launch_bounds__(1024) k_plan(const synthpix_pair_desc *__restr
         p.blur_r = g.blur_r;
         p.halo = g.halo;
         p.chunk_base = (int32_t)bc;
-        p.pad = 0;
+        p.tile = tile;
         plan[b] = p;
         bp += d.n_particles;
         bt += 2LL * g.ntiles;
@@ -180,7 +181,7 @@ __device__ __forceinline__ void count_window(const KernelArgs &a, const ChunkCtx
                                              uint32_t *hist) {
     if (w.j0 > w.j1 || w.i0 > w.i1) return;
     int32_t tx0, tx1, ty0, ty1;
-    window_tiles(w, c.pl.halo, a.tile, c.d.width, c.d.height, tx0, tx1, ty0, ty1);
+    window_tiles(w, c.pl.halo, c.pl.tile, c.d.width, c.d.height, tx0, tx1, ty0, ty1);
     const int32_t k0 = f * c.pl.ntiles;
     for (int32_t ty = ty0; ty <= ty1; ++ty)
         for (int32_t tx = tx0; tx <= tx1; ++tx) {
@@ -348,7 +349,7 @@ __device__ __forceinline__ void chunk_windows(const KernelArgs &a, const ChunkCt
                                               6.0f * sh.y, c.d.width, c.d.height);
             if (w.j0 > w.j1 || w.i0 > w.i1) continue;
             int32_t tx0, tx1, ty0, ty1;
-            window_tiles(w, c.pl.halo, a.tile, c.d.width, c.d.height, tx0, tx1, ty0, ty1);
+            window_tiles(w, c.pl.halo, c.pl.tile, c.d.width, c.d.height, tx0, tx1, ty0, ty1);
             for (int32_t ty = ty0; ty <= ty1; ++ty)
                 for (int32_t tx = tx0; tx <= tx1; ++tx) put(f, f * c.pl.ntiles + ty * c.pl.tiles_x + tx, p, sh);
         }
@@ -440,10 +441,10 @@ __device__ __forceinline__ TileCtx frame1_tile(const KernelArgs &a, const PairPl
     c.t = (int32_t)(gt - (pl.tile_base >> 1));
     c.ty = c.t / pl.tiles_x;
     c.tx = c.t - c.ty * pl.tiles_x;
-    c.x0 = c.tx * a.tile;
-    c.y0 = c.ty * a.tile;
-    c.x1 = min(c.x0 + a.tile, W);
-    c.y1 = min(c.y0 + a.tile, H);
+    c.x0 = c.tx * pl.tile;
+    c.y0 = c.ty * pl.tile;
+    c.x1 = min(c.x0 + pl.tile, W);
+    c.y1 = min(c.y0 + pl.tile, H);
     c.it = a.items[pl.tile_base + c.t];
     c.adv0 = c.it.rec0 - (pl.list_base >> 1);
     return c;
@@ -461,7 +462,7 @@ __device__ __forceinline__ void frame2_tiles(const KernelArgs &a, const PairPlan
     const Window w = particle_window(r.ix, r.fx, r.iy, r.fy, 6.0f * r.sigma, W, H);
     if (w.j0 > w.j1 || w.i0 > w.i1) return;
     int32_t tx0, tx1, ty0, ty1;
-    window_tiles(w, pl.halo, a.tile, W, H, tx0, tx1, ty0, ty1);
+    window_tiles(w, pl.halo, pl.tile, W, H, tx0, tx1, ty0, ty1);
     for (int32_t ty = ty0; ty <= ty1; ++ty)
         for (int32_t tx = tx0; tx <= tx1; ++tx) {
             const int32_t dy = ty - c.ty + kNbr, dx = tx - c.tx + kNbr;
@@ -487,7 +488,7 @@ __global__ void __launch_bounds__(NT) k_advect(KernelArgs a) {
     const int W = D.width, H = D.height;
     const TileCtx c = frame1_tile(a, pl, b, W, H, gt);
     // this CTA's home rows [hy0, hy1): its band of the tile
-    const int bh = (a.tile + NB - 1) / NB;
+    const int bh = (pl.tile + NB - 1) / NB;
     const int hy0 = min(c.y0 + band * bh, c.y1), hy1 = min(hy0 + bh, c.y1);
     const Flow F = pair_flow(a, D);
     // grid nodes under [x0 - M, x1 + M) x [hy0 - M, hy1 + M), bilinear neighbours included
@@ -644,14 +645,14 @@ __global__ void __launch_bounds__(kAdvThreads) k_scatter2(KernelArgs a) {
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
-cudaError_t launch_plan(const synthpix_pair_desc *descs, int32_t n_pairs, int32_t tile, int32_t fused,
+cudaError_t launch_plan(const synthpix_pair_desc *descs, int32_t n_pairs, const TileRule &rule, int32_t fused,
                         PairPlan *plan, const Layout &L, int32_t *check, float *blur_w, uint32_t *ticket,
                         uint32_t *count, cudaStream_t st) {
     const int64_t n_count = count ? L.n_tiles : 0;
     const int32_t zero_ctas = (int32_t)((n_count + kPlanZeroWords - 1) / kPlanZeroWords);
     const int32_t tap_ctas = (n_pairs + kPlanTapPairs - 1) / kPlanTapPairs;
     const unsigned grid = 1u + (unsigned)zero_ctas + (unsigned)tap_ctas;
-    return launch_kernel(k_plan, grid, 1024, 0, st, descs, n_pairs, tile, fused, plan, L.n_part, L.n_tiles, L.n_list,
+    return launch_kernel(k_plan, grid, 1024, 0, st, descs, n_pairs, rule, fused, plan, L.n_part, L.n_tiles, L.n_list,
                           L.n_inter, L.n_chunks, check, blur_w, ticket, count, n_count, zero_ctas);
 }
 

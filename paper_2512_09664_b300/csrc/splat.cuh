@@ -1625,7 +1625,7 @@ __device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo
     const synthpix_pair_desc &D = *reinterpret_cast<const synthpix_pair_desc *>(buf);
     const PairPlan &pl = *reinterpret_cast<const PairPlan *>(buf + kStageDesc);
     const float *wtab = reinterpret_cast<const float *>(buf + kStagePlan);
-    const Geo g = make_geo(D, pl, a.tile, it.tile, pl.halo);
+    const Geo g = make_geo(D, pl, pl.tile, it.tile, pl.halo);
     const bool fused = a.inter_dtype == SYNTHPIX_F32;
     const float imax = D.i_max > 0.0f ? D.i_max : 1.0f;
     const float unit = imax * kFixedUnit;
@@ -1677,7 +1677,7 @@ __device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo
         }
         return;  // the caller's loop ends with a barrier
     }
-    if (NT == 512 && fast_finish_ok(g)) {
+    if (NT == 512 && a.reg_epilogue && fast_finish_ok(g)) {
         finish_fast_r<T>(a, g, D, wtab, it.frame, K, s, src);
         return;
     }
@@ -1841,7 +1841,7 @@ __global__ void __launch_bounds__(kSplatThreads) k_finish(KernelArgs a) {
     const synthpix_pair_desc &D = a.descs[it.pair];
     const PairPlan pl = a.plan[it.pair];
     if (threadIdx.x < kBlurStride) wtab[threadIdx.x] = a.blur_w[(int64_t)it.pair * kBlurStride + threadIdx.x];
-    const Geo g = make_geo(D, pl, a.tile, it.tile, pl.blur_r);
+    const Geo g = make_geo(D, pl, pl.tile, it.tile, pl.blur_r);
     const EpiK K = epi_consts(D, it.frame, 1.0f);  // the intermediate frames hold S at full scale
     illum_factors(g, D, K, s);
     __syncthreads();
