@@ -39,7 +39,6 @@ METRIC = "PIV image pairs/s at 512², ppp 0.05 (batched/FP16 vs plain FP32); % r
 UNIT = "pairs/s"
 N_PAIRS = 64
 HBM_PEAK_FALLBACK = 6400.0  # GB/s, used only when MEASURED_PEAKS.json is absent
-SM_COUNT = 148
 FP32_LANES_PER_SM = 128
 
 # ncu DRAM traffic of k_splat per launch (bytes), with the sha256 of the
@@ -61,8 +60,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--pairs", type=int, default=N_PAIRS, help="pairs per step (profiling a smaller case)")
     ap.add_argument("--workload", default="batch64_512_u8",
-                    choices=("batch64_512_u8", "uneven256", "diff32_256", "large_mixed", "shapes64_512",
-                             "ablations", "stream512"),
+                    choices=("batch64_512_u8", "single256", "uneven256", "diff32_256", "large_mixed",
+                             "shapes64_512", "ablations", "stream512"),
                     help="the headline workload (default) or one of the other workloads, measured on their own")
     ap.add_argument("--quick", action="store_true",
                     help="timed steps only (no autotune, graph, FP16, e2e, per-pair or CPU legs): for profilers")
@@ -300,17 +299,186 @@ def splat_source_hash():
         return hashlib.sha256(f.read()).hexdigest()
 
 
+def device_alu_peak(dev, peaks):
+    """FP32 lane-op peak (T/s) of the device: SMs (queried) x 128 lanes x the max SM clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = float(peaks.get("sm_max_mhz", 2032.0))
+    return sms * FP32_LANES_PER_SM * mhz * 1e6 / 1e12, f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {mhz:.0f} MHz"
+
+
+def step_roofline(wl, ms, peaks, alu_peak):
+    """The method's step roofline: t_roof = max(algorithmic bytes / HBM peak,
+    algorithmic lane-ops / FP32 peak); frac = t_roof / measured step time."""
+    alg_bytes, alg_ops = algorithmic(wl)
+    t_hbm = alg_bytes / (float(peaks["hbm_gbs"]) * 1e9) * 1e6
+    t_alu = alg_ops / (alu_peak * 1e12) * 1e6
+    t_roof = max(t_hbm, t_alu)
+    return {"t_hbm_us": t_hbm, "t_alu_us": t_alu, "t_roof_us": t_roof, "t_step_us": ms * 1e3,
+            "frac": t_roof / (ms * 1e3), "bound": "hbm" if t_hbm >= t_alu else "alu",
+            "algorithmic_bytes": alg_bytes, "algorithmic_lane_ops": alg_ops}
+
+
+def _events(n):
+    import torch
+    return [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+
+
+def _timed(fn, steps, flush, stream, flush_l2=True):
+    """Per-call device times (ms) of fn on stream, CUDA events around each call."""
+    import torch
+    ev = _events(steps)
+    torch.cuda.synchronize()
+    for k in range(steps):
+        if flush_l2:
+            flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        fn()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def leg_single_pair(flush, stream, peaks, alu_peak, steps):
+    """Config 1: one 256^2 pair (Lamb-Oseen, FP32 output): a latency-bound render."""
+    import statistics
+
+    from paper_2512_09664_b300 import workloads as W
+    from paper_2512_09664_b300.binding import Renderer
+    wl = W.single_pair_256(seed=0)
+    r = Renderer(wl)
+    for _ in range(3):
+        r.render()
+    eager = statistics.median(_timed(r.render, steps, flush, stream))
+    r.capture()
+    for _ in range(3):
+        r.replay()
+    graph = statistics.median(_timed(r.replay, steps, flush, stream))
+    return {"config": wl.description, "eager_ms": eager, "graph_ms": graph, "value": 1.0 / (graph / 1e3),
+            "unit": UNIT, "mpx_per_s": 2 * 256 * 256 / (graph / 1e3) / 1e6,
+            "step_roofline": step_roofline(wl, graph, peaks, alu_peak),
+            "note": "median over the timed renders; one pair is bound by launch and dependency latency"}
+
+
+def leg_uneven(flush, stream, peaks, alu_peak, steps):
+    """Config 3: 256 pairs of uneven sizes in one persistent, graph-captured
+    launch sequence with autotuned per-size-class parameters, against one
+    autotuned edge for the whole batch and against per-pair launches."""
+    import statistics
+
+    import torch
+
+    from paper_2512_09664_b300 import workloads as W
+    from paper_2512_09664_b300.binding import Renderer
+    wl = W.uneven_batch(n_pairs=256, seed=2)
+    r = Renderer(wl)
+    tuned = r.tune(reps=2)
+    r.capture()
+    for _ in range(2):
+        r.replay()
+    g_ms = statistics.median(_timed(r.replay, steps, flush, stream))
+    one = Renderer(wl)
+    edge, _ = one.autotune(reps=2)
+    one.capture()
+    for _ in range(2):
+        one.replay()
+    one_ms = statistics.median(_timed(one.replay, steps, flush, stream))
+    del one
+    per = [Renderer(wl.subset([b])) for b in range(wl.n_pairs)]  # tile 0: the tuned table
+    for p in per:
+        p.render()
+
+    def per_pair():
+        for p in per:
+            p.render()
+    p_ms = statistics.median(_timed(per_pair, max(3, steps // 5), flush, stream))
+    del per
+    torch.cuda.empty_cache()
+    return {"config": wl.description, "tuned": tuned, "graph_persistent_ms": g_ms,
+            "value": wl.n_pairs / (g_ms / 1e3), "unit": UNIT, "mpx_per_s": wl.image_elems() / (g_ms / 1e3) / 1e6,
+            "single_edge": {"tile": edge, "graph_ms": one_ms, "value": wl.n_pairs / (one_ms / 1e3)},
+            "per_pair_launches": {"ms": p_ms, "value": wl.n_pairs / (p_ms / 1e3)},
+            "speedup_over_per_pair": p_ms / g_ms, "speedup_over_single_edge": one_ms / g_ms,
+            "particles": sum(p.n_particles for p in wl.pairs),
+            "step_roofline": step_roofline(wl, g_ms, peaks, alu_peak)}
+
+
+def leg_differentiable(flush, stream, peaks, alu_peak, steps):
+    """Config 4: 32 pairs 256^2 from a 32^2 control grid: forward render from
+    the seeded particles and the adjoint (gradients w.r.t. flow, x0, y0, d)."""
+    import statistics
+
+    import numpy as np
+    import torch
+
+    from paper_2512_09664_b300 import workloads as W
+    from paper_2512_09664_b300.binding import Renderer
+    wl = W.differentiable_batch(n_pairs=32)
+    ctrl = torch.tensor(np.stack(wl.meta["control"]), dtype=torch.float32)
+    up = torch.nn.functional.interpolate(ctrl.permute(0, 3, 1, 2), size=(256, 256), mode="bilinear",
+                                         align_corners=False).permute(0, 2, 3, 1).contiguous()
+    wl.flows = [f.numpy() for f in up]
+    r = Renderer(wl)
+    G = torch.randn(r.images.shape, device=r.images.device)
+    gf = torch.zeros_like(r.flows)
+    gp = torch.empty((sum(p.n_particles for p in wl.pairs), 3), device=r.images.device)
+    for _ in range(3):
+        r.render_from()
+        r.backward(G, grad_flows=gf, grad_particles=gp)
+    f_ms = statistics.median(_timed(r.render_from, steps, flush, stream))
+    b_ms = statistics.median(_timed(lambda: r.backward(G, grad_flows=gf, grad_particles=gp), steps, flush, stream))
+    n_part = sum(p.n_particles for p in wl.pairs)
+    # backward bytes: dL/dimages read once (FP32), flows read, flow gradients written, particle gradients written
+    b_bytes = r.images.numel() * 4 + 2 * r.flows.numel() * 4 + n_part * 12
+    hbm = float(peaks["hbm_gbs"]) * 1e9
+    return {"config": wl.description, "forward_ms": f_ms, "backward_ms": b_ms,
+            "value": wl.n_pairs / ((f_ms + b_ms) / 1e3), "unit": UNIT,
+            "forward_value": wl.n_pairs / (f_ms / 1e3),
+            "forward_step_roofline": step_roofline(wl, f_ms, peaks, alu_peak),
+            "backward_roofline_hbm": {"algorithmic_bytes": b_bytes, "t_hbm_us": b_bytes / hbm * 1e6,
+                                      "frac": (b_bytes / hbm * 1e3) / b_ms}}
+
+
+def leg_large_mixed(flush, stream, peaks, alu_peak, steps):
+    """Config 5: 16 x 2048^2 + 16 x 1920x1080, 16-bit output; FP32 (fused, on
+    chip) vs FP16 and BF16 intermediate frames in HBM, each autotuned."""
+    import statistics
+
+    import torch
+
+    from paper_2512_09664_b300 import workloads as W
+    from paper_2512_09664_b300.binding import Renderer
+    wl = W.large_mixed_batch()
+    res = {}
+    for inter in ("f32", "f16", "bf16"):
+        r = Renderer(wl, inter_dtype=inter)
+        tuned = r.tune(reps=1)
+        for _ in range(2):
+            r.render()
+        ms = statistics.median(_timed(r.render, steps, flush, stream))
+        res[inter] = {"ms_per_step": ms, "value": wl.n_pairs / (ms / 1e3), "tuned": tuned,
+                      "mpx_per_s": wl.image_elems() / (ms / 1e3) / 1e6,
+                      "step_roofline": step_roofline(wl, ms, peaks, alu_peak)}
+        del r
+        torch.cuda.empty_cache()
+    return {"config": wl.description, "paths": res, "value": res["f16"]["value"], "unit": UNIT,
+            "f16_speedup_over_f32": res["f32"]["ms_per_step"] / res["f16"]["ms_per_step"]}
+
+
 def run_ours(args, rank, world, dist):
+    import statistics
+
     import torch
 
     from paper_2512_09664_b300.binding import Renderer
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     wl = workload(rank, args.pairs)
-    r = Renderer(wl, device=dev, tile=args.tile)  # 0: the library's default edge, autotuned below
+    r = Renderer(wl, device=dev, tile=args.tile)  # 0: per-size-class edges (defaults, then autotuned)
     stream = torch.cuda.current_stream()
+    tuned = None
     if args.tile == 0 and not args.quick:
-        r.autotune(reps=2)
+        tuned = r.tune(reps=2)
 
     def barrier():
         if dist is not None:
@@ -328,7 +496,7 @@ def run_ours(args, rank, world, dist):
         r.render()
     torch.cuda.synchronize()
     # timed steps: one event pair around each render (nothing between its launches)
-    events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    events = _events(args.steps)
     with ClockSampler(dev.index) as clk:
         barrier()
         torch.cuda.synchronize()
@@ -364,38 +532,17 @@ def run_ours(args, rank, world, dist):
     r.capture()
     for _ in range(2):
         r.replay()
-    torch.cuda.synchronize()
-    g_ms = 0.0
-    for k in range(min(args.steps, 50)):
-        flush.fill_(k & 0xFF)
-        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        g0.record(stream)
-        r.replay()
-        g1.record(stream)
-        g1.synchronize()
-        g_ms += g0.elapsed_time(g1)
-    graph_ms = g_ms / min(args.steps, 50)
+    graph_ms = statistics.mean(_timed(r.replay, min(args.steps, 50), flush, stream))
 
     # the batched path with FP16 intermediate frames (splat, then a separate
     # finishing kernel reading the 16-bit frames)
     r16 = Renderer(wl, device=dev, tile=args.tile, inter_dtype="f16")
     if args.tile == 0:
-        r16.autotune(reps=2)
+        r16.tune(reps=2)
     for _ in range(3):
         r16.render()
-    torch.cuda.synchronize()
-    f_ms = 0.0
-    nf = min(args.steps, 50)
-    for k in range(nf):
-        flush.fill_(k & 0xFF)
-        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        h0.record(stream)
-        r16.render()
-        h1.record(stream)
-        h1.synchronize()
-        f_ms += h0.elapsed_time(h1)
-    f16_ms = f_ms / nf
-    f16_tile = r16.pk.batch.tile
+    f16_ms = statistics.mean(_timed(r16.render, min(args.steps, 50), flush, stream))
+    f16_tuning = r16.tuning()
     del r16
 
     # end to end through the same C ABI: every step copies its flows in from
@@ -423,13 +570,9 @@ def run_ours(args, rank, world, dist):
     d2h = img_host[0].numel() * img_host[0].element_size()
     e2e_serial_ms = _e2e_serial_ms(r, flows_host, img_host[0], stream, e2e_steps)
 
-    # plain FP32 per-pair path: one launch sequence per pair, FP32 output
-    from paper_2512_09664_b300 import workloads as W
-    plain = [Renderer(wl.subset([b]), device=dev, tile=args.tile, out_dtype="f32") for b in range(wl.n_pairs)]
-    if args.tile == 0:  # the single-pair path at its own best tile edge
-        t_one, _ = plain[0].autotune(reps=3)
-        for p in plain:
-            p.pk.batch.tile = t_one
+    # plain per-pair path at the same accuracy: one launch sequence per pair,
+    # the same u8 output and epilogue, FP32 throughout
+    plain = [Renderer(wl.subset([b]), device=dev, tile=args.tile) for b in range(wl.n_pairs)]
     for p in plain:
         p.render()
     torch.cuda.synchronize()
@@ -442,12 +585,13 @@ def run_ours(args, rank, world, dist):
     p1.record(stream)
     torch.cuda.synchronize()
     plain_pairs_s = reps * wl.n_pairs / (p0.elapsed_time(p1) / 1e3)
+    plain_tuning = plain[0].tuning()
+    del plain
 
     peaks, peak_kind = measured_peaks()
+    alu_peak, alu_src = device_alu_peak(dev, peaks)
     alg_bytes, alg_ops = algorithmic(wl)
     splat_ms = stage_ms["splat_epilogue"]
-    sm_mhz = float(peaks.get("sm_max_mhz", 2032.0))
-    alu_peak = SM_COUNT * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12  # T lane-op/s
     # the epilogue and splat work run in the splat kernel; seeding/advection
     # arithmetic is not counted there
     achieved = alg_ops / (splat_ms / 1e3) / 1e12
@@ -457,38 +601,54 @@ def run_ours(args, rank, world, dist):
     hbm_peak = float(peaks["hbm_gbs"])
     step_gbs = alg_bytes / (ms_per_step / 1e3) / 1e9
     probes = alu_probes(stream)
+    legs = {}
+    if rank == 0 and world == 1:  # the other configurations, on one GPU
+        legs["single_pair_256"] = leg_single_pair(flush, stream, peaks, alu_peak, max(args.steps, 20))
+        legs["uneven256"] = leg_uneven(flush, stream, peaks, alu_peak, min(args.steps, 20))
+        legs["diff32_256"] = leg_differentiable(flush, stream, peaks, alu_peak, min(args.steps, 20))
+        legs["large_mixed"] = leg_large_mixed(flush, stream, peaks, alu_peak, min(args.steps, 10))
     # k_plan, k_seed_advect, k_scan (frame 1), k_scatter, k_advect, k_scan (frame 2), k_scatter2, k_splat
     launches_per_step = 8
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_config(wl, {"tile": r.pk.batch.tile, "tile_choice": "autotuned" if args.tile == 0
+        "config": workload_config(wl, {"tuning": r.tuning(), "tuning_choice": "autotuned" if args.tile == 0
                                        else "fixed", "path": "fused FP32 splat + epilogue (on-chip intermediate)",
                                        "parallelism": f"replicas x{world}"}),
         "mpx_per_s": value * 2 * 512 * 512 / 1e6,
         "stage_ms": stage_ms,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tlane-op/s",
                      "frac": achieved / alu_peak, "traffic": traffic, "kernel": "k_splat",
-                     "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_mhz:.0f} MHz",
+                     "peak_source": alu_src,
                      "measured_fma_peak": probes["fma"], "frac_of_measured_fma": achieved / probes["fma"]},
         "alu_probes": {"unit": "T op/s", **probes,
-                       "source": "synthpix_alu_probe, best of 3 launches of one full wave after the timed steps"},
+                       "source": "synthpix_alu_probe (measurement library), best of 3 launches of one full wave "
+                                 "after the timed steps"},
+        "step_roofline": step_roofline(wl, ms_per_step, peaks, alu_peak),
         "step_roofline_hbm": {"achieved_gbs": step_gbs, "peak_gbs": hbm_peak, "frac": step_gbs / hbm_peak,
                               "peak_source": peak_kind, "algorithmic_bytes_per_step": alg_bytes},
         "plain_fp32_per_pair": {"value": plain_pairs_s, "unit": UNIT, "speedup": value / world / plain_pairs_s,
-                                "tile": plain[0].pk.batch.tile if plain else None},
-        "batched_f16_intermediate": {"value": wl.n_pairs / (f16_ms / 1e3), "unit": UNIT, "ms_per_step": f16_ms,
-                                     "tile": f16_tile},
+                                "output": "u8 with the same illumination, noise, blur and quantisation",
+                                "tuning": plain_tuning},
+        "batched_f16_intermediate": {
+            "value": wl.n_pairs / (f16_ms / 1e3), "unit": UNIT, "ms_per_step": f16_ms, "tuning": f16_tuning,
+            "speedup_over_fused_f32": (ms_per_step / world) / f16_ms,
+            "why": "at 512x512 the fused FP32 path keeps the splatted frame on chip and writes each output "
+                   "pixel once, so 16-bit intermediate frames only add an HBM round trip and a second kernel; "
+                   "they pay where a frame's tile cannot be finished on chip (see large_mixed)"},
         "graph_replay": {"ms_per_step": graph_ms, "value": world * wl.n_pairs / (graph_ms / 1e3), "unit": UNIT},
         "e2e": {"value": world * wl.n_pairs / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
                 "path": "HostPipeline: pinned flows in, render, pinned images out; two device buffer sets, "
                         "copies of neighbouring steps overlap the render",
                 "serial_value": world * wl.n_pairs / (e2e_serial_ms / 1e3)},
+        "workloads": legs,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
     }
+    if tuned is not None:
+        line["config"]["autotune"] = tuned
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
     if rank == 0:
@@ -659,44 +819,14 @@ def run_other(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     line = {"workload": args.workload, "steps": args.steps, "warmup": args.warmup, "unit": UNIT}
+    peaks, peak_kind = measured_peaks()
+    alu_peak, alu_src = device_alu_peak(torch.device("cuda", 0), peaks)
     if args.workload == "uneven256":
-        wl = W.uneven_batch(n_pairs=256, seed=2)
-        r = Renderer(wl)
-        tile, _ = r.autotune(reps=2)
-        r.capture()
-        for _ in range(args.warmup):
-            r.replay()
-        g_ms = _time_device(r.replay, args.steps, flush, stream)
-        per = [Renderer(wl.subset([b]), tile=tile) for b in range(wl.n_pairs)]
-        for p in per:
-            p.render()
-
-        def per_pair():
-            for p in per:
-                p.render()
-        p_ms = _time_device(per_pair, max(2, args.steps // 10), flush, stream)
-        line.update({"config": wl.description, "tile": tile, "graph_persistent_ms": g_ms,
-                     "value": wl.n_pairs / (g_ms / 1e3), "per_pair_launches_ms": p_ms,
-                     "per_pair_value": wl.n_pairs / (p_ms / 1e3), "speedup": p_ms / g_ms,
-                     "mpx_per_s": wl.image_elems() / (g_ms / 1e3) / 1e6,
-                     "particles": sum(p.n_particles for p in wl.pairs)})
+        line.update(leg_uneven(flush, stream, peaks, alu_peak, args.steps))
     elif args.workload == "diff32_256":
-        wl = W.differentiable_batch(n_pairs=32)
-        ctrl = torch.tensor(np.stack(wl.meta["control"]), dtype=torch.float32)
-        up = torch.nn.functional.interpolate(ctrl.permute(0, 3, 1, 2), size=(256, 256), mode="bilinear",
-                                             align_corners=False).permute(0, 2, 3, 1).contiguous()
-        wl.flows = [f.numpy() for f in up]
-        r = Renderer(wl)
-        G = torch.randn(r.images.shape, device="cuda")
-        gf = torch.zeros_like(r.flows)
-        gp = torch.empty((sum(p.n_particles for p in wl.pairs), 3), device="cuda")
-        for _ in range(args.warmup):
-            r.render_from()
-            r.backward(G, grad_flows=gf, grad_particles=gp)
-        f_ms = _time_device(r.render_from, args.steps, flush, stream)
-        b_ms = _time_device(lambda: r.backward(G, grad_flows=gf, grad_particles=gp), args.steps, flush, stream)
-        line.update({"config": wl.description, "forward_ms": f_ms, "backward_ms": b_ms,
-                     "value": wl.n_pairs / ((f_ms + b_ms) / 1e3), "forward_value": wl.n_pairs / (f_ms / 1e3)})
+        line.update(leg_differentiable(flush, stream, peaks, alu_peak, args.steps))
+    elif args.workload == "single256":
+        line.update(leg_single_pair(flush, stream, peaks, alu_peak, args.steps))
     elif args.workload == "shapes64_512":
         # Eq. 1 shape options: elliptical axis-misaligned particles with frame-2
         # variation and hiding (general-shape splat), and round particles with
@@ -707,26 +837,23 @@ def run_other(args):
             wl = W.focus_batch(n_pairs=64) if kind == "focus" else W.shapes_batch(n_pairs=64,
                                                                                  general=kind == "general")
             r = Renderer(wl)
-            tile, _ = r.autotune(reps=1)
+            tuned = r.tune(reps=1)
             for _ in range(args.warmup):
                 flush.fill_(1)
                 r.render()
             with ClockSampler(0) as clk:
                 ms = _time_device(r.render, args.steps, flush, stream)
             st = _stage_ms(r, min(args.steps, 20), flush, stream)
-            res[kind] = {"ms_per_step": ms, "value": wl.n_pairs / (ms / 1e3), "tile": tile, "stage_ms": st,
+            res[kind] = {"ms_per_step": ms, "value": wl.n_pairs / (ms / 1e3), "tuning": tuned, "stage_ms": st,
                          "config": wl.description, "clocks": clk.summary()}
             if kind == "general":
-                peaks, peak_kind = measured_peaks()
-                sm_mhz = float(peaks.get("sm_max_mhz", 2032.0))
-                alu_peak = SM_COUNT * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
                 achieved = shapes_algorithmic(wl) / (st["splat_epilogue"] / 1e3) / 1e12
                 alg_bytes, _ = algorithmic(wl)
                 step_gbs = alg_bytes / (ms / 1e3) / 1e9
                 res[kind]["roofline"] = {
                     "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tlane-op/s",
                     "frac": achieved / alu_peak, "traffic": None, "kernel": "k_splat (general shapes)",
-                    "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_mhz:.0f} MHz"}
+                    "peak_source": alu_src}
                 res[kind]["step_roofline_hbm"] = {"achieved_gbs": step_gbs, "peak_gbs": float(peaks["hbm_gbs"]),
                                                   "frac": step_gbs / float(peaks["hbm_gbs"]),
                                                   "peak_source": peak_kind}
@@ -772,7 +899,6 @@ def run_other(args):
         # 64 Fourier fields of 512^2 with 64 modes (FP32: a product and three FMAs,
         # 7 flops, per node and mode)
         from paper_2512_09664_b300 import binding as Bn
-        peaks, peak_kind = measured_peaks()
         wlh = W.batch_512_u8(n_pairs=64, seed=1)
         r = Renderer(wlh)
         r.render()
@@ -800,7 +926,7 @@ def run_other(args):
         torch.cuda.synchronize()
         f_ms = e0.elapsed_time(e1) / n
         f_flop = 64 * 512 * 512 * 64 * 7.0
-        fp32_peak = SM_COUNT * FP32_LANES_PER_SM * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 * 2 / 1e12
+        fp32_peak = 2 * alu_peak
         line.update({"config": "streaming sampler, 64 pairs 512x512 u8 per batch (the headline recipe), "
                                "Fourier flows rms 3 generated on the device", "paths": res,
                      "value": res["F64_R1"]["value"],
@@ -811,21 +937,9 @@ def run_other(args):
                      "flow_generation_64x512": {"ms": f_ms, "roofline": {
                          "bound": "alu", "achieved": f_flop / (f_ms / 1e3) / 1e12, "peak": fp32_peak,
                          "unit": "TFLOP/s (FP32)", "frac": f_flop / (f_ms / 1e3) / 1e12 / fp32_peak,
-                         "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 flops x max clock"}}})
+                         "peak_source": alu_src + " x 2 flops"}}})
     else:  # large_mixed
-        wl = W.large_mixed_batch()
-        res = {}
-        for inter in ("f32", "f16", "bf16"):
-            r = Renderer(wl, inter_dtype=inter)
-            tile, _ = r.autotune(reps=1)
-            for _ in range(args.warmup):
-                r.render()
-            ms = _time_device(r.render, args.steps, flush, stream)
-            res[inter] = {"ms_per_step": ms, "value": wl.n_pairs / (ms / 1e3), "tile": tile}
-            del r
-            torch.cuda.empty_cache()
-        line.update({"config": wl.description, "paths": res, "value": res["f16"]["value"],
-                     "f16_speedup_over_f32": res["f32"]["ms_per_step"] / res["f16"]["ms_per_step"]})
+        line.update(leg_large_mixed(flush, stream, peaks, alu_peak, args.steps))
     print(json.dumps(line), flush=True)
 
 
