@@ -263,7 +263,8 @@ int synthpix_advect_particles(const synthpix_batch_desc *batch, const synthpix_p
  * Adjoint of the render (not in the paper; its differentiable use): given
  * grad_images = dL/d(images) (FP32, same packing as the images), computes
  *   grad_flows      dL/d(flows), ADDED to the caller's array (same layout as
- *                   flows; several pairs sharing a grid sum into it), or NULL;
+ *                   flows, 8-byte aligned; several pairs sharing a grid sum
+ *                   into it), or NULL;
  *   grad_particles  [sum of n_particles][3] dL/d(x0, y0, d), overwritten, or NULL;
  * for the frames B = L * S + noise (the splat of Eq. 1 integrated per pixel,
  * times the illumination field).  Requires out_dtype F32 (quantisation has no

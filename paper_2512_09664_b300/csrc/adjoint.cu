@@ -12,20 +12,25 @@
 #include "common.cuh"
 #include "kernels.cuh"
 #include "particle.cuh"
+#include "phi.cuh"
 
 namespace spx {
 
-__device__ __forceinline__ float gauss_pdf(float t) { return 0.39894228040143267794f * expf(-0.5f * t * t); }
+// Standard normal density (the hardware exponential: relative error ~1e-7,
+// far below the gradient's FP32 tolerance).
+__device__ __forceinline__ float gauss_pdf(float t) { return 0.39894228040143267794f * __expf(-0.5f * t * t); }
 
 // Pixel mass of column j for a particle at i + f (split), and its derivatives
 // with respect to the centre and to sigma:
 //   m = Phi(b) - Phi(a), dm/dc = (pdf(a) - pdf(b)) / sigma,
 //   dm/dsigma = (a pdf(a) - b pdf(b)) / sigma,  a = (j - c)/sigma, b = (j + 1 - c)/sigma.
-__device__ __forceinline__ void axis_terms(int32_t ic, float fc, int32_t j, float inv, float &m, float &dm,
-                                           float &ds) {
+// The masses use the forward splat's tabulated tail (tab: the table in
+// shared memory), so the gradient is that of the rendered values.
+__device__ __forceinline__ void axis_terms(int32_t ic, float fc, int32_t j, float inv, uint32_t tab, float &m,
+                                           float &dm, float &ds) {
     const float da = (float)(j - ic) - fc, db = (float)(j + 1 - ic) - fc;
     const float ta = da * inv, tb = db * inv;
-    m = pixel_mass(edge_value(ta), edge_value(tb), da > 0.0f, db > 0.0f);
+    m = edge_mass(edge_value_tab(da, inv, tab), edge_value_tab(db, inv, tab));
     const float pa = gauss_pdf(ta), pb = gauss_pdf(tb);
     dm = (pa - pb) * inv;
     ds = (ta * pa - tb * pb) * inv;
@@ -34,6 +39,10 @@ __device__ __forceinline__ void axis_terms(int32_t ic, float fc, int32_t j, floa
 __global__ void __launch_bounds__(256) k_adj_splat(KernelArgs a) {
     if (*a.check != 1) return;
     extern __shared__ float scr[];
+    __shared__ __align__(16) float s_phi[(kPhiDegree + 1) * kPhiPieces];
+    for (int k = threadIdx.x; k < (kPhiDegree + 1) * kPhiPieces; k += blockDim.x) s_phi[k] = kPhiTable[k];
+    __syncthreads();
+    const uint32_t tab = sh_addr(s_phi);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t wg = (int64_t)blockIdx.x * 8 + warp;
     if (wg >= 2 * a.n_part) return;  // whole warp
@@ -58,12 +67,12 @@ __global__ void __launch_bounds__(256) k_adj_splat(KernelArgs a) {
     const float inv = __frcp_rn(sig);
     const bool illum = D.illum_min != 1.0f || D.illum_max != 1.0f;
     for (int e = lane; e < nx; e += 32) {
-        axis_terms(ix, p.x, w.j0 + e, inv, ex[e], dex[e], dsx[e]);
+        axis_terms(ix, p.x, w.j0 + e, inv, tab, ex[e], dex[e], dsx[e]);
         const float sv = sinpif(((float)(w.j0 + e) + 0.5f) / (float)W);
         lx[e] = sv * sv;
     }
     for (int e = lane; e < ny; e += 32) {
-        axis_terms(iy, p.y, w.i0 + e, inv, ey[e], dey[e], dsy[e]);
+        axis_terms(iy, p.y, w.i0 + e, inv, tab, ey[e], dey[e], dsy[e]);
         const float sv = sinpif(((float)(w.i0 + e) + 0.5f) / (float)H);
         ly[e] = sv * sv;
     }
@@ -120,15 +129,19 @@ __device__ __forceinline__ float2 velocity_jac(const Flow &F, int32_t ix, float 
     return make_float2(fmaf(ty, bu - tu, tu), fmaf(ty, bv - tv, tv));
 }
 
+// dL/dflow of one stage at its four stencil nodes: one vector reduction per
+// node adds (u, v) (each component atomically, as two atomicAdds would).
 __device__ __forceinline__ void scatter_flow(float *gf, const int node[4], const float wgt[4], float lx, float ly) {
     if (!gf) return;
 #pragma unroll
-    for (int n = 0; n < 4; ++n) {
-        atomicAdd(gf + 2 * node[n], wgt[n] * lx);
-        atomicAdd(gf + 2 * node[n] + 1, wgt[n] * ly);
-    }
+    for (int n = 0; n < 4; ++n)
+        asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(gf + 2 * node[n]), "f"(wgt[n] * lx),
+                     "f"(wgt[n] * ly) : "memory");
 }
 
+// NMAX: capacity of the substep arrays (n_substeps <= NMAX); with a small
+// NMAX the loops unroll and the arrays live in registers.
+template <int NMAX>
 __global__ void __launch_bounds__(128) k_adj_advect(KernelArgs a) {
     if (*a.check != 1) return;
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -144,17 +157,22 @@ __global__ void __launch_bounds__(128) k_adj_advect(KernelArgs a) {
     const int n = a.n_substeps;
     const float h = a.dt / (float)n;
     const float hh = 0.5f * h, h6 = h / 6.0f;
-    // forward, keeping the start of every substep (n <= kMaxAdjointSubsteps)
-    int32_t si[kMaxAdjointSubsteps], sj[kMaxAdjointSubsteps];
-    float sfx[kMaxAdjointSubsteps], sfy[kMaxAdjointSubsteps];
+    // forward, keeping the start of every substep (n <= NMAX)
+    int32_t si[NMAX], sj[NMAX];
+    float sfx[NMAX], sfy[NMAX];
     int32_t jx = P.ix, jy = P.iy;
     float fx = P.fx, fy = P.fy;
-    for (int s = 0; s < n; ++s) {
-        si[s] = jx; sj[s] = jy; sfx[s] = fx; sfy[s] = fy;
-        advect_split(F, h, 1, a.integrator, jx, fx, jy, fy);
+#pragma unroll(NMAX <= 8 ? NMAX : 1)
+    for (int s = 0; s < NMAX; ++s) {
+        if (s < n) {
+            si[s] = jx; sj[s] = jy; sfx[s] = fx; sfy[s] = fy;
+            advect_split(F, h, 1, a.integrator, jx, fx, jy, fy);
+        }
     }
     float lx = g2.x, ly = g2.y;  // dL / d(frame-2 position)
-    for (int s = n - 1; s >= 0; --s) {
+#pragma unroll(NMAX <= 8 ? NMAX : 1)
+    for (int s = NMAX - 1; s >= 0; --s) {
+        if (s >= n) continue;
         const int32_t px = si[s], py = sj[s];
         const float ux = sfx[s], uy = sfy[s];
         float J1[4], w1[4];
@@ -205,7 +223,10 @@ cudaError_t launch_adjoint(const KernelArgs &a, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(k_adj_splat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_adj_splat<<<(unsigned)((2 * a.n_part + 7) / 8), 256, smem, st>>>(a);
-    k_adj_advect<<<(unsigned)((a.n_part + 127) / 128), 128, 0, st>>>(a);
+    const unsigned grid = (unsigned)((a.n_part + 127) / 128);
+    if (a.n_substeps <= 4) k_adj_advect<4><<<grid, 128, 0, st>>>(a);
+    else if (a.n_substeps <= 8) k_adj_advect<8><<<grid, 128, 0, st>>>(a);
+    else k_adj_advect<kMaxAdjointSubsteps><<<grid, 128, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -396,8 +396,8 @@ static int run(Mode mode, const synthpix_batch_desc *batch, const synthpix_pair_
     if (mode == Mode::Backward) {
         if (!x.grad_images || ((uintptr_t)x.grad_images & 3))
             return fail(SYNTHPIX_EINVAL, "grad_images is NULL or not 4-byte aligned");
-        if ((x.grad_flows && ((uintptr_t)x.grad_flows & 3)) || (x.grad_particles && ((uintptr_t)x.grad_particles & 3)))
-            return fail(SYNTHPIX_EINVAL, "gradient outputs must be 4-byte aligned");
+        if ((x.grad_flows && ((uintptr_t)x.grad_flows & 7)) || (x.grad_particles && ((uintptr_t)x.grad_particles & 3)))
+            return fail(SYNTHPIX_EINVAL, "grad_flows must be 8-byte and grad_particles 4-byte aligned");
         if (batch->out_dtype != SYNTHPIX_F32)
             return fail(SYNTHPIX_EUNSUPPORTED, "the adjoint needs out_dtype F32 (quantisation has no gradient)");
         if (batch->n_substeps > spx::kMaxAdjointSubsteps)

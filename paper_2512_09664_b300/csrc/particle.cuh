@@ -336,8 +336,17 @@ __device__ __forceinline__ void advect_split_z(const Flow &F, const float *w, fl
 // velocity(), so the result is identical.
 struct FlowWindow {
     const float2 *s;
+    uint32_t sa;  // .shared address of s
     int32_t gx0, gy0, nw, nh;
 };
+
+// One node of the staged window by its .shared address (explicit state
+// space: no generic-address handling per load).
+__device__ __forceinline__ float2 window_node(uint32_t a) {
+    float2 v;
+    asm("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
+    return v;
+}
 
 __device__ __forceinline__ float2 velocity_windowed(const Flow &F, const FlowWindow &Wn, int32_t ix, float fx,
                                                     int32_t iy, float fy) {
@@ -377,8 +386,8 @@ __device__ __forceinline__ float2 velocity_tile(const Flow &F, const FlowWindow 
     const int32_t v = iy - Wn.gy0 + (__float_as_int(fly + 12582912.0f) - 0x4B400000);
     const unsigned lx = Wn.nw > 1 ? (unsigned)(Wn.nw - 1) : 0u, ly = Wn.nh > 1 ? (unsigned)(Wn.nh - 1) : 0u;
     if ((unsigned)u < lx && (unsigned)v < ly) {
-        const float2 *p = Wn.s + v * Wn.nw + u;
-        const float2 a = p[0], b = p[1], c = p[Wn.nw], d = p[Wn.nw + 1];
+        const uint32_t p = Wn.sa + 8u * (uint32_t)(v * Wn.nw + u), q = p + 8u * (uint32_t)Wn.nw;
+        const float2 a = window_node(p), b = window_node(p + 8u), c = window_node(q), d = window_node(q + 8u);
         const float tu = fmaf(tx, b.x - a.x, a.x), tv = fmaf(tx, b.y - a.y, a.y);
         const float bu = fmaf(tx, d.x - c.x, c.x), bv = fmaf(tx, d.y - c.y, c.y);
         return make_float2(fmaf(ty, bu - tu, tu), fmaf(ty, bv - tv, tv));

@@ -500,6 +500,7 @@ __global__ void __launch_bounds__(NT) k_advect(KernelArgs a) {
     grid_coord(hy1 + kAdvMargin, 0.0f, F.gh, F.H, k1, t_);
     FlowWindow Wn;
     Wn.s = s_flow;
+    Wn.sa = (uint32_t)__cvta_generic_to_shared(s_flow);
     Wn.gx0 = min(max(l0, 0), F.gw - 1);
     Wn.gy0 = min(max(k0, 0), F.gh - 1);
     Wn.nw = min(max(l1 + 1, 0), F.gw - 1) - Wn.gx0 + 1;

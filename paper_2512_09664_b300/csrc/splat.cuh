@@ -21,7 +21,7 @@
 #include "common.cuh"
 #include "kernels.cuh"
 #include "particle.cuh"
-#include "phi_table.cuh"
+#include "phi.cuh"
 
 namespace spx {
 
@@ -65,27 +65,6 @@ template <int RS>
 __device__ __forceinline__ int record_lead(int64_t first) { return (int)((first * (int64_t)RS) & 15); }
 
 // ---------------------------------------------------------------------------
-// shared-memory accesses by 32-bit .shared addresses: immediate offsets fold
-// into the instruction and no access needs generic-address handling
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t sh_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-template <int OFF>
-__device__ __forceinline__ void sh_red_add(uint32_t a, uint32_t v) {
-    asm volatile("red.shared.add.u32 [%0+%2], %1;" ::"r"(a), "r"(v), "n"(OFF));
-}
-__device__ __forceinline__ uint32_t sh_atom_add(uint32_t a, uint32_t v) {
-    uint32_t old;
-    asm volatile("atom.shared.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(a), "r"(v));
-    return old;
-}
-// a read of data that stays constant while the kernel runs (the tail table)
-__device__ __forceinline__ float4 sh_ld_const4(uint32_t a) {
-    float4 v;
-    asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
-    return v;
-}
-
-// ---------------------------------------------------------------------------
 // exact fixed-point accumulation
 // ---------------------------------------------------------------------------
 // A pixel sums integer contributions in units q = i_max 2^-26 in a 32-bit
@@ -108,8 +87,6 @@ __device__ __forceinline__ float4 sh_ld_const4(uint32_t a) {
 // and the adds go unchecked.  Otherwise the chunk takes the checked path:
 // the thread whose add wraps a word adds 1 to the pixel's carry word (worth
 // 2^32 units), so no sum is ever lost.
-constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
-constexpr int32_t kMagicBits = 0x4B400000;
 constexpr float kFixedScale = 67108864.0f;      // 2^26 units per i_max
 constexpr float kFixedUnit = 1.0f / 67108864.0f;
 constexpr float kWrapValue = 4294967296.0f;     // 2^32: the weight of a carry
@@ -193,40 +170,6 @@ template <int N>
 struct RowAdds<N, N> {
     static __device__ __forceinline__ void run(uint32_t, const uint32_t (&)[N], uint32_t) {}
 };
-
-// ---------------------------------------------------------------------------
-// pixel integration of Eq. 1
-// ---------------------------------------------------------------------------
-// Upper normal tail Q(a) = erfc(a / sqrt 2) / 2 for a >= 0 from the cubic
-// table (one float4 per piece, staged in shared memory at .shared address
-// tab).  a is clamped to the table's end (Q(8) = 6e-16); the piece is
-// k = rint(16 a), so s = a - k / 16 is exact and |s| <= 1/32.
-__device__ __forceinline__ float phi_tail(float a, uint32_t tab) {
-    a = fminf(a, kPhiTMax);
-    const float kf = fmaf(a, kPhiPerUnit, kMagic);
-    const int k = __float_as_int(kf) - kMagicBits;
-    const float s = fmaf(__fsub_rn(kf, kMagic), -1.0f / kPhiPerUnit, a);
-    const float4 c = sh_ld_const4(tab + 16u * (uint32_t)k);
-    return fmaf(fmaf(fmaf(c.w, s, c.z), s, c.y), s, c.x);
-}
-
-// Edge value of a pixel edge at offset dd = edge - particle centre (pixels):
-// the lower tail Phi(t), t = dd / sigma, for dd < 0, and minus the upper tail
-// -(1 - Phi(t)) for dd >= +0, so both tails keep their absolute accuracy.
-// Q never reaches 0 on the table (Q(8) > 0), so the sign bit of the value
-// tells the side of the centre.
-__device__ __forceinline__ float edge_value_tab(float dd, float inv, uint32_t tab) {
-    const float q = phi_tail(fabsf(__fmul_rn(dd, inv)), tab);
-    return __int_as_float(__float_as_int(q) ^ (~__float_as_int(dd) & (int)0x80000000));
-}
-
-// Mass of the unit Gaussian between two pixel edges from their edge values:
-// Phi(b) - Phi(a) = sb - sa, plus 1 when the centre lies between them (sa on
-// the lower side, sb on the upper side).
-__device__ __forceinline__ float edge_mass(float sa, float sb) {
-    const int across = (__float_as_int(sb) & ~__float_as_int(sa)) >> 31;  // -1 or 0
-    return fmaxf(__fadd_rn(__fsub_rn(sb, sa), __int_as_float(across & 0x3F800000)), 0.0f);
-}
 
 // One particle's visit of a tile, set up for the splat (same size as a
 // Record, written over the staged records it comes from).
@@ -1082,6 +1025,21 @@ __device__ __forceinline__ void store_group(T *o, float *v, int nvalid, float M)
     }
 }
 
+// Store 4 consecutive outputs of a row at a 4-element aligned address
+// (quantised when M > 0): the store_group arithmetic without its checks.
+template <typename T>
+__device__ __forceinline__ void store_quad(T *o, const float *v, float M) {
+    if constexpr (IsCode<T>::value) {
+        uint32_t q[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) q[j] = quant_code(v[j], M);
+        if (sizeof(T) == 1) *reinterpret_cast<uint32_t *>(o) = q[0] | (q[1] << 8) | (q[2] << 16) | (q[3] << 24);
+        else *reinterpret_cast<uint2 *>(o) = make_uint2(q[0] | (q[1] << 16), q[2] | (q[3] << 16));
+    } else {
+        Out<T>::store4(o, v);
+    }
+}
+
 // Horizontal pass (rows of the full halo rectangle, tile columns) and
 // vertical pass with store; taps w[|k|], k = -R..R, replicate border already
 // materialised in A.  R is a compile-time radius (0 < R <= 6).  Tiles start
@@ -1522,8 +1480,7 @@ __device__ __forceinline__ void finish_fast(const KernelArgs &a, const Geo &g, c
         const float4 v4 = a_quad(a, K, S, Lu, (uint32_t)(((g.fy0 + r) * g.W + g.afx0 + cl) >> 2));
         const float v[4] = {v4.x, v4.y, v4.z, v4.w};
         if constexpr (R == 0) {
-            float o[4] = {v[0], v[1], v[2], v[3]};
-            store_group<T>(out + (r - rlo) * g.W + 4 * lane, o, 4, M);
+            store_quad<T>(out + (r - rlo) * g.W + 4 * lane, v, M);
         } else {
             // x[m], m = -R .. 3 + R: the row's A around this lane's 4 pixels
             float x[4 + 2 * R];
@@ -1577,8 +1534,8 @@ __device__ __forceinline__ void finish_fast(const KernelArgs &a, const Geo &g, c
                 p1 = f2_fma(wp[k], f2_add(hv[o + R - k][1], hv[o + R + k][1]), p1);
             }
             const float2 a0 = f2_unpack(p0), a1 = f2_unpack(p1);
-            float ov[4] = {a0.x, a0.y, a1.x, a1.y};
-            store_group<T>(out + (t0 + o) * g.W + 4 * lane, ov, 4, M);
+            const float ov[4] = {a0.x, a0.y, a1.x, a1.y};
+            store_quad<T>(out + (t0 + o) * g.W + 4 * lane, ov, M);
         }
     }
     __syncthreads();
@@ -1588,9 +1545,11 @@ __device__ __forceinline__ void finish_fast(const KernelArgs &a, const Geo &g, c
 }
 
 // The fast finishing path applies: a full 128 x 128 tile, W a multiple of 4
-// (aligned noise quads), blur radius at most 4.
-__device__ __forceinline__ bool fast_finish_ok(const Geo &g) {
-    return g.x1 - g.x0 == 128 && g.y1 - g.y0 == 128 && (g.W & 3) == 0 && g.R <= 4;
+// (aligned noise quads), blur radius at most 4, outputs of the pair starting
+// on a 4-element boundary of a 16-byte aligned buffer (aligned quad stores).
+__device__ __forceinline__ bool fast_finish_ok(const Geo &g, const synthpix_pair_desc &D, const void *images) {
+    return g.x1 - g.x0 == 128 && g.y1 - g.y0 == 128 && (g.W & 3) == 0 && g.R <= 4 && (D.image_offset & 3) == 0 &&
+           (reinterpret_cast<uintptr_t>(images) & 15) == 0;
 }
 
 template <typename T>
@@ -1677,7 +1636,7 @@ __device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo
         }
         return;  // the caller's loop ends with a barrier
     }
-    if (NT == 512 && a.reg_epilogue && fast_finish_ok(g)) {
+    if (NT == 512 && a.reg_epilogue && fast_finish_ok(g, D, a.images)) {
         finish_fast_r<T>(a, g, D, wtab, it.frame, K, s, src);
         return;
     }
