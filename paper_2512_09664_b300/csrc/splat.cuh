@@ -94,6 +94,7 @@ constexpr float kMassScale = 2147483648.0f;     // 2^31: x masses as integers
 constexpr uint32_t kSafeVisits = 63;            // visits per block that cannot wrap a word
 constexpr int kBlkShift = 3;                    // 8 x 8 pixel blocks
 constexpr int kBlkSide = 24;                    // blocks per side of the counter grid (row pitch <= 192)
+constexpr int kBlkPitch = kBlkSide + 1;         // counter rows padded: a lane per row hits its own bank
 
 // Tile geometry of one work item.  The accumulator and the finishing buffer A
 // share memory: the full halo rectangle [x0 - R, x1 + R) x [y0 - R, y1 + R)
@@ -127,10 +128,47 @@ static __shared__ uint32_t sh_cnt[kBuckets];              // visits of the chunk
 static __shared__ uint32_t sh_off[kBuckets + 1];          // their exclusive offsets
 static __shared__ uint32_t sh_next;                       // warp-slot ticket of the chunk's render
 static __shared__ uint32_t sh_slot_end[kWideClass + 1];   // slots of the classes, widest first: cumulative ends
-static __shared__ uint32_t sh_blk[kBlkSide * kBlkSide];  // visits of the item so far per 8 x 8 block
+// The visits of the item so far per 8 x 8 block, as a difference array
+// along each block row: a visit whose window meets blocks [bx0, bx1] of rows
+// [by0, by1] adds +1 at bx0 and -1 at bx1 + 1 of each of those rows (two
+// adds per row, at most three rows for windows up to 17 px); the counts are
+// the rows' prefix sums (blocks_checked).  Column kBlkSide holds the end
+// marks of windows reaching the last block.
+static __shared__ uint32_t sh_blk[kBlkPitch * kBlkSide];
 static __shared__ int sh_checked;                         // the chunk takes the checked path
 static __shared__ int sh_carry_clean;                     // the item's carry words are zero
 static __shared__ int sh_wrap;                            // a checked add wrapped a word in this item
+
+// Count a visit whose clipped window is [j0, j1] x [i0, i1] (frame pixels)
+// in the blocks it meets.
+__device__ __forceinline__ void count_blocks(const Geo &g, int32_t j0, int32_t j1, int32_t i0, int32_t i1) {
+    const int bx0 = (j0 - g.afx0) >> kBlkShift, bx1 = ((j1 - g.afx0) >> kBlkShift) + 1;
+    const int by0 = (i0 - g.fy0) >> kBlkShift, by1 = (i1 - g.fy0) >> kBlkShift;
+    for (int by = by0; by <= by1; ++by) {
+        atomicAdd(sh_blk + by * kBlkPitch + bx0, 1u);
+        atomicAdd(sh_blk + by * kBlkPitch + bx1, 0xFFFFFFFFu);
+    }
+}
+
+// Warp 0, after the counts of a chunk: true when some block has been met by
+// more than kSafeVisits visits of the item (a lane per block row sums its
+// row's differences).
+__device__ __forceinline__ bool blocks_checked() {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    uint32_t mx = 0;
+    if (lane < kBlkSide) {
+        uint32_t run = 0;
+#pragma unroll 8
+        for (int c = 0; c < kBlkSide; ++c) {
+            run += sh_blk[lane * kBlkPitch + c];
+            mx = max(mx, run);
+        }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) mx = max(mx, __shfl_xor_sync(FULL, mx, d));
+    return mx > kSafeVisits;
+}
 
 // The tile's accumulator as the splat sees it.
 struct Acc {
@@ -413,10 +451,7 @@ __device__ __forceinline__ void splat_chunk(const unsigned char *recs, unsigned 
                 const int cls = m > kNarrowMax ? kWideClass : (m - 1) >> 1;
                 key[q] = cls * 32 + (v[q].base & 31);
                 slot[q] = atomicAdd(sh_cnt + key[q], 1u);
-                const int bx0 = (j0 - g.afx0) >> kBlkShift, bx1 = (j1 - g.afx0) >> kBlkShift;
-                const int by0 = (i0 - g.fy0) >> kBlkShift, by1 = (i1 - g.fy0) >> kBlkShift;
-                for (int by = by0; by <= by1; ++by)
-                    for (int bx = bx0; bx <= bx1; ++bx) atomicAdd(sh_blk + by * kBlkSide + bx, 1u);
+                count_blocks(g, j0, j1, i0, i1);
             }
         }
     }
@@ -459,12 +494,8 @@ __device__ __forceinline__ void splat_chunk(const unsigned char *recs, unsigned 
             if (lane >= d) nsl += t;
         }
         if (lane <= kWideClass) sh_slot_end[lane] = nsl;
-        uint32_t mx = 0;
-#pragma unroll
-        for (int j = 0; j < kBlkSide * kBlkSide / 32; ++j) mx = max(mx, sh_blk[lane + 32 * j]);
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) mx = max(mx, __shfl_xor_sync(FULL, mx, d));
-        if (lane == 0) sh_checked = mx > kSafeVisits ? 1 : 0;
+        const bool ck = blocks_checked();
+        if (lane == 0) sh_checked = ck ? 1 : 0;
     }
     __syncthreads();
     float2 *o8 = reinterpret_cast<float2 *>(out);  // 16-byte aligned; a Visit is three 8-byte words
@@ -820,20 +851,13 @@ __device__ __forceinline__ void splat_chunk_general(const unsigned char *recs, u
         int32_t j0, j1, i0, i1;
         general_window(R[k], g, j0, j1, i0, i1);
         if (j0 > j1 || i0 > i1) continue;
-        const int bx0 = (j0 - g.afx0) >> kBlkShift, bx1 = (j1 - g.afx0) >> kBlkShift;
-        const int by0 = (i0 - g.fy0) >> kBlkShift, by1 = (i1 - g.fy0) >> kBlkShift;
-        for (int by = by0; by <= by1; ++by)
-            for (int bx = bx0; bx <= bx1; ++bx) atomicAdd(sh_blk + by * kBlkSide + bx, 1u);
+        count_blocks(g, j0, j1, i0, i1);
     }
     __syncthreads();
     if (threadIdx.x < 32) {
-        uint32_t mx = 0;
-#pragma unroll
-        for (int j = 0; j < kBlkSide * kBlkSide / 32; ++j) mx = max(mx, sh_blk[lane + 32 * j]);
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) mx = max(mx, __shfl_xor_sync(FULL, mx, d));
+        const bool ck = blocks_checked();
         if (lane == 0) {
-            sh_checked = mx > kSafeVisits ? 1 : 0;
+            sh_checked = ck ? 1 : 0;
             sh_next = 0;
         }
     }
@@ -1613,7 +1637,7 @@ __device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo
     }
     if (it.count == 0) __syncthreads();  // illumination factors
     // block counts of the next item start from zero (its first count comes after a barrier)
-    for (int k = threadIdx.x; k < kBlkSide * kBlkSide; k += blockDim.x) sh_blk[k] = 0u;
+    for (int k = threadIdx.x; k < kBlkPitch * kBlkSide; k += blockDim.x) sh_blk[k] = 0u;
     if (threadIdx.x == 0) {
         if ((int64_t)t2 < a.n_tiles) after = a.items[t2];
         else after.pair = -1;
@@ -1699,7 +1723,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_splat(KernelArgs a) {
     for (int k = threadIdx.x; k < (kPhiDegree + 1) * kPhiPieces; k += blockDim.x) phi[k] = kPhiTable[k];
     s.phi = sh_addr(phi);
     for (int k = threadIdx.x; k < kBuckets; k += blockDim.x) sh_cnt[k] = 0;
-    for (int k = threadIdx.x; k < kBlkSide * kBlkSide; k += blockDim.x) sh_blk[k] = 0;
+    for (int k = threadIdx.x; k < kBlkPitch * kBlkSide; k += blockDim.x) sh_blk[k] = 0;
     s.BP = (a.tile + 3) & ~3;
     unsigned char *bufs = smem + L.bufs;
     const uint32_t cap = (uint32_t)rec_cap(a.rec_buf_bytes, RS);
