@@ -42,10 +42,10 @@ HBM_PEAK_FALLBACK = 6400.0  # GB/s, used only when MEASURED_PEAKS.json is absent
 FP32_LANES_PER_SM = 128
 
 # ncu DRAM traffic of k_splat per launch (bytes), with the sha256 of the
-# kernel source (splat.cuh) it was taken on; reported only while the source is
-# unchanged.
-SPLAT_TRAFFIC = {"sha256": "e92f3479fde2cebde48a920373d5551e09ca782b859075574e646ca456048203",
-                 "bytes_per_launch": 49466368 + 7684608,
+# kernel sources (splat.cuh, then phi.cuh) it was taken on; reported only
+# while they are unchanged.
+SPLAT_TRAFFIC = {"sha256": "2bce081d45c00368c82a9f42287247a5bf21dd8203e67f8759fcf6ea83fc62e2",
+                 "bytes_per_launch": 50682112 + 8084736,
                  "capture": "profiles/k_splat_batch64_512_u8.md"}
 
 
@@ -295,8 +295,11 @@ def run_reference(args, rank, world):
 # ----------------------------------------------------------------------------
 
 def splat_source_hash():
-    with open(os.path.join(ROOT, "paper_2512_09664_b300", "csrc", "splat.cuh"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()
+    data = b""
+    for name in ("splat.cuh", "phi.cuh"):
+        with open(os.path.join(ROOT, "paper_2512_09664_b300", "csrc", name), "rb") as f:
+            data += f.read()
+    return hashlib.sha256(data).hexdigest()
 
 
 def device_alu_peak(dev, peaks):
