@@ -6,6 +6,11 @@
   the C ABI of ``include/synthpix.h``.
 * ``paper_2512_09664_b300/libsynthpix_probe.so``: the ALU throughput probes
   of ``measure/`` (measurement support for the benchmark only).
+* ``paper_2512_09664_b300/libsynthpix_smallbins.so``: the renderer with fixed
+  bins too small for their records (``SPX_SMALL_FIXED_BINS``), so that the
+  tests can run the exact rebinning after an overflow, which the product
+  library's bin capacities make all but impossible to reach.  Only the units
+  that size the bins are compiled again.
 
 nvcc cross-compiles for sm_103a without a GPU.  Each translation unit is
 compiled to an object of its own (in parallel, into ``_build/``; a unit is
@@ -28,6 +33,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libsynthpix.so")
 PROBE_LIB = os.path.join(PKG, "libsynthpix_probe.so")
+SMALLBINS_LIB = os.path.join(PKG, "libsynthpix_smallbins.so")
+SMALLBINS_UNITS = ("prep.cu", "api.cu")  # the units that size the fixed bins
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -54,7 +61,8 @@ def _newer(paths, t):
 
 
 def _stale() -> bool:
-    for lib, srcs, folder in ((LIB, sources(), CSRC), (PROBE_LIB, probe_sources(), MEASURE)):
+    for lib, srcs, folder in ((LIB, sources(), CSRC), (PROBE_LIB, probe_sources(), MEASURE),
+                              (SMALLBINS_LIB, sources(), CSRC)):
         if not os.path.exists(lib) or _newer(srcs + _headers(folder), os.path.getmtime(lib)):
             return True
     return False
@@ -73,19 +81,28 @@ def _compile(src, obj, inc, extra, verbose):
     return obj
 
 
-def _build_lib(lib, srcs, folder, tag, force, verbose, extra):
+def _build_lib(lib, srcs, folder, tag, force, verbose, extra, variant=None):
+    """variant: None, or (tag, units, flags): those units compiled again with the flags
+    (objects tagged `tag`), the others shared with the main build."""
     os.makedirs(BUILD, exist_ok=True)
     hdr_t = max([os.path.getmtime(h) for h in _headers(folder)] or [0.0])
+
+    def obj_of(s):
+        if variant and os.path.basename(s) in variant[1]:
+            return _obj(s, variant[0])
+        return _obj(s, tag)
+
     jobs = []
     for s in srcs:
-        o = _obj(s, tag)
+        o = obj_of(s)
         if force or not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), hdr_t):
-            jobs.append((s, o))
+            flags = list(extra) + (list(variant[2]) if variant and o != _obj(s, tag) else [])
+            jobs.append((s, o, flags))
     with ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 1))) as ex:
-        for f in [ex.submit(_compile, s, o, folder, extra, verbose) for s, o in jobs]:
+        for f in [ex.submit(_compile, s, o, folder, fl, verbose) for s, o, fl in jobs]:
             f.result()
     tmp = lib + f".tmp{os.getpid()}"
-    cmd = [NVCC, *ARCH_FLAGS, *LINK_FLAGS, *[_obj(s, tag) for s in srcs], "-o", tmp]
+    cmd = [NVCC, *ARCH_FLAGS, *LINK_FLAGS, *[obj_of(s) for s in srcs], "-o", tmp]
     if verbose:
         print(" ".join(cmd), flush=True)
     subprocess.check_call(cmd)
@@ -98,6 +115,8 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         return LIB
     _build_lib(LIB, sources(), CSRC, "spx", force, verbose, list(extra))
     _build_lib(PROBE_LIB, probe_sources(), MEASURE, "probe", force, verbose, list(extra))
+    _build_lib(SMALLBINS_LIB, sources(), CSRC, "spx", force, verbose, list(extra),
+               variant=("smallbins", SMALLBINS_UNITS, ["-DSPX_SMALL_FIXED_BINS"]))
     return LIB
 
 
@@ -106,3 +125,4 @@ if __name__ == "__main__":
           extra=["-Xptxas", "-v"] if "--ptxas-v" in sys.argv else [])
     print(LIB)
     print(PROBE_LIB)
+    print(SMALLBINS_LIB)

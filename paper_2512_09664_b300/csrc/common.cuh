@@ -90,6 +90,30 @@ __host__ __device__ inline PairGeom pair_geom(const synthpix_pair_desc &d, int t
     return g;
 }
 
+// Records per bin of the fixed bin layout of seeded renders (each producer
+// places its records directly, without a counting pass).  A bin of an
+// interior tile collects the particles whose centres lie within the tile
+// widened by the halo and a window on each side: E = N side_x side_y / (W H)
+// expected for uniform positions.  Frame 1 gets E + E/4 + 64 (more than 9
+// standard deviations of the binomial count for E >= 100), frame 2, whose
+// density the flow changes, E + E/2 + 64.  A bin that overflows sets a flag
+// and the frame is binned again exactly (k_rebin).  Integer arithmetic, so
+// host and device agree.
+__host__ __device__ inline void fixed_caps(const synthpix_pair_desc &d, int32_t tile, int32_t halo, int64_t &cap1,
+                                           int64_t &cap2) {
+    const int64_t W = d.width, H = d.height;
+    const int64_t reach = (int64_t)tile + 2LL * halo + window_max(pair_max_diameter(d));
+    const int64_t sx = reach < W ? reach : W, sy = reach < H ? reach : H;
+    const int64_t e = ((int64_t)d.n_particles * sx * sy + W * H - 1) / (W * H);
+#ifdef SPX_SMALL_FIXED_BINS  // the overflow test library: nearly every bin overflows (k_rebin rebins)
+    cap1 = e / 2 + 1;
+    cap2 = e / 2 + 1;
+#else
+    cap1 = e + e / 4 + 64;
+    cap2 = e + e / 2 + 64;
+#endif
+}
+
 // A particle as binned for one frame: split position, sigma, amplitude.
 struct Record {
     float fx, fy;      // fractions of the split position

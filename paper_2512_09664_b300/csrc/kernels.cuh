@@ -39,6 +39,9 @@ struct KernelArgs {
     Record *rec;                      // bins
     Record *adv;                      // tiled advection: frame-2 records by frame-1 bin slot (sigma < 0: none)
     int32_t tiled;                    // 1: frame 2 comes from the tiled advection (k_advect), not k_seed_advect
+    int32_t fixed;                    // 1 (tiled renders whose fixed bins fit the bin segments): k_seed_place
+                                      // and k_advect place records into fixed-capacity bins (fixed_caps)
+    uint32_t *ovf;                    // [2]: a fixed bin of frame 1 / frame 2 overflowed (zeroed by k_plan)
     uint32_t *ticket;                 // work-queue counter of the persistent splat
     int32_t smem_edge;                // capacity edge of the on-chip tile (tile + 2 max radius)
     int32_t warp_scratch;             // floats of per-warp window scratch
@@ -56,6 +59,19 @@ struct KernelArgs {
     float *grad_particles;            // NULL or [n_part][3] dL/d(x0, y0, d)
     float4 *grad_frames;              // [n_part][2]: dL/d(x, y, sigma) of each frame's splat
 };
+
+// The splat's work item t (t = tile_base + frame ntiles + tile).  With fixed
+// bins the item holds the bin's capacity and the count is the bin's counter
+// (records were placed at slots 0 .. min(counter, capacity) - 1), unless the
+// frame was binned again exactly after an overflow (k_rebin wrote the item).
+__device__ __forceinline__ ItemInfo work_item(const KernelArgs &a, int64_t t) {
+    ItemInfo it = a.items[t];
+    if (a.fixed) {  // the three loads are independent of the item's
+        const uint32_t n = a.count[t], o0 = a.ovf[0], o1 = a.ovf[1];
+        if ((it.frame ? o1 : o0) == 0u) it.count = min(it.count, n);
+    }
+    return it;
+}
 
 constexpr int kStageEvents = 6;
 
@@ -97,6 +113,7 @@ __host__ __device__ constexpr int rec_buf_bytes_for(int tile) { return tile >= 1
 constexpr size_t kMaxSmemBytes = 227 * 1024;  // dynamic shared memory of one CTA
 
 // count: NULL, or the per-(pair, frame, tile) bin counts, zeroed by the plan launch
+// ticket: the splat's work-queue counter, followed by the two overflow flags of the fixed bins.
 cudaError_t launch_plan(const synthpix_pair_desc *descs, int32_t n_pairs, const TileRule &rule, int32_t fused,
                         PairPlan *plan, const Layout &L, int32_t *check, float *blur_w, uint32_t *ticket,
                         uint32_t *count, cudaStream_t st);

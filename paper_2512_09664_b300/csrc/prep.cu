@@ -134,7 +134,9 @@ __global__ void __launch_bounds__(1024) k_plan(const synthpix_pair_desc *__restr
         bc += g.chunks;
     }
     if (t == 1023) {
-        *ticket = 0u;
+        ticket[0] = 0u;  // the splat's work queue
+        ticket[1] = 0u;  // overflow flags of the fixed bins (frames 1, 2)
+        ticket[2] = 0u;
         const bool ok = s_tot[0] == want_part && s_tot[1] == want_tiles && s_tot[2] == want_list &&
                         s_tot[3] == want_inter && s_tot[4] == want_chunks;
         *check = ok ? 1 : 0;
@@ -263,14 +265,118 @@ __global__ void __launch_bounds__(kPrepThreads, 5) k_seed_advect(KernelArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// k_seed_place (seeded renders with fixed bins): k_seed_advect's seeding
+// with frame 1 binned in the same pass.  A CTA counts its chunk's records per
+// tile on chip, reserves each tile's range of the tile's fixed bin with one
+// global atomic (the bin counters count every record), and places its
+// records from registers.  Records past a bin's capacity are dropped and
+// flag the frame for k_rebin.  The split positions and sigma / amplitude
+// are still written (k_rebin's input).  The first chunk of each pair writes
+// the pair's work items of the fixed layout.
+// ---------------------------------------------------------------------------
+// Record r at slot `slot` of the fixed bin of tile k of frame f of a pair
+// (bin capacity cap), or the frame's overflow flag.
+__device__ __forceinline__ void place_fixed(const KernelArgs &a, const PairPlan &pl, int f, int32_t k, int64_t cap,
+                                            uint32_t slot, const Record &r) {
+    if ((int64_t)slot >= cap) {
+        a.ovf[f] = 1u;
+        return;
+    }
+    float2 *o = reinterpret_cast<float2 *>(a.rec + pl.list_base + (int64_t)f * pl.list_cap + (int64_t)k * cap + slot);
+    o[0] = make_float2(r.fx, r.fy);
+    o[1] = make_float2(__int_as_float(r.ix), __int_as_float(r.iy));
+    o[2] = make_float2(r.sigma, r.amp);
+}
+
+__global__ void __launch_bounds__(kPrepThreads, 4) k_seed_place(KernelArgs a) {
+    if (*a.check != 1) return;
+    __shared__ __align__(16) ChunkCtx c;
+    __shared__ uint32_t cnt[kHistMax], base[kHistMax];
+    load_chunk(a, c);
+    const int nk = c.pl.ntiles;
+    const bool local = nk <= kHistMax;
+    int64_t cap1, cap2;
+    fixed_caps(c.d, c.pl.tile, c.pl.halo, cap1, cap2);
+    if ((int64_t)blockIdx.x == c.pl.chunk_base) {  // the pair's work items (fixed layout)
+        for (int k = threadIdx.x; k < 2 * nk; k += kPrepThreads) {
+            ItemInfo it;
+            it.pair = c.pair;
+            it.frame = k >= nk ? 1 : 0;
+            it.tile = k - it.frame * nk;
+            const int64_t cap = it.frame ? cap2 : cap1;
+            it.count = (uint32_t)cap;
+            it.rec0 = c.pl.list_base + (int64_t)it.frame * c.pl.list_cap + (int64_t)it.tile * cap;
+            a.items[c.pl.tile_base + k] = it;
+        }
+    }
+    if (local) {
+        for (int k = threadIdx.x; k < nk; k += kPrepThreads) cnt[k] = 0u;
+        __syncthreads();
+    }
+    uint32_t *cnt1 = a.count + c.pl.tile_base;
+    const int W = c.d.width, H = c.d.height;
+    auto tiles_of = [&](const Record &r, int32_t &tx0, int32_t &tx1, int32_t &ty0, int32_t &ty1) {
+        const Window w = particle_window(r.ix, r.fx, r.iy, r.fy, 6.0f * r.sigma, W, H);
+        if (w.j0 > w.j1 || w.i0 > w.i1) return false;
+        window_tiles(w, c.pl.halo, c.pl.tile, W, H, tx0, tx1, ty0, ty1);
+        return true;
+    };
+    constexpr int U = kChunk / kPrepThreads;
+    Record r[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int q = threadIdx.x + u * kPrepThreads;
+        r[u].sigma = -1.0f;
+        if (q >= c.n) continue;
+        const uint32_t i = (uint32_t)(c.first + q);
+        const int64_t g = c.pl.part_base + i;
+        const Seeded P = seed_particle(a, c.d, i, g);
+        a.sa[g] = make_float2(P.sigma, P.amp);
+        a.pos0[g] = make_float4(P.fx, P.fy, __int_as_float(P.ix), __int_as_float(P.iy));
+        r[u].fx = P.fx;
+        r[u].fy = P.fy;
+        r[u].ix = P.ix;
+        r[u].iy = P.iy;
+        r[u].sigma = P.sigma;
+        r[u].amp = P.amp;
+        int32_t tx0, tx1, ty0, ty1;
+        if (!tiles_of(r[u], tx0, tx1, ty0, ty1)) continue;
+        for (int32_t ty = ty0; ty <= ty1; ++ty)
+            for (int32_t tx = tx0; tx <= tx1; ++tx) {
+                const int32_t k = ty * c.pl.tiles_x + tx;
+                if (local) atomicAdd(cnt + k, 1u);
+                else place_fixed(a, c.pl, 0, k, cap1, atomicAdd(cnt1 + k, 1u), r[u]);
+            }
+    }
+    if (!local) return;
+    __syncthreads();
+    for (int k = threadIdx.x; k < nk; k += kPrepThreads) {
+        const uint32_t n = cnt[k];
+        base[k] = n ? atomicAdd(cnt1 + k, n) : 0u;
+        cnt[k] = 0u;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        if (r[u].sigma < 0.0f) continue;
+        int32_t tx0, tx1, ty0, ty1;
+        if (!tiles_of(r[u], tx0, tx1, ty0, ty1)) continue;
+        for (int32_t ty = ty0; ty <= ty1; ++ty)
+            for (int32_t tx = tx0; tx <= tx1; ++tx) {
+                const int32_t k = ty * c.pl.tiles_x + tx;
+                place_fixed(a, c.pl, 0, k, cap1, base[k] + atomicAdd(cnt + k, 1u), r[u]);
+            }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // k_scan: exclusive scan of the bin counts of one (pair, frame) per CTA
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_scan(KernelArgs a, int frame) {
-    if (*a.check != 1) return;
+// Offsets, cursors and work items of the bins of pair b, frame f, by the
+// 1024 threads of a CTA.  Contains barriers.
+__device__ __forceinline__ void scan_pair(const KernelArgs &a, int b, int f) {
     __shared__ uint32_t s[1024];
     __shared__ uint32_t carry;
-    const int b = frame < 0 ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
-    const int f = frame < 0 ? (int)(blockIdx.x & 1) : frame;
     const PairPlan pl = a.plan[b];
     const int64_t base = pl.tile_base + (int64_t)f * pl.ntiles;
     if (threadIdx.x == 0) carry = 0;
@@ -306,6 +412,13 @@ __global__ void __launch_bounds__(1024) k_scan(KernelArgs a, int frame) {
     }
 }
 
+__global__ void __launch_bounds__(1024) k_scan(KernelArgs a, int frame) {
+    if (*a.check != 1) return;
+    const int b = frame < 0 ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+    const int f = frame < 0 ? (int)(blockIdx.x & 1) : frame;
+    scan_pair(a, b, f);
+}
+
 // ---------------------------------------------------------------------------
 // k_scatter: particle records into their tiles' bins (order within a bin is
 // free: the splat accumulates in exact fixed point, so sums are
@@ -316,42 +429,44 @@ __global__ void __launch_bounds__(1024) k_scan(KernelArgs a, int frame) {
 // (sigma_x, sigma_y, rho, amplitude) of the frame (hidden particles skipped).
 template <typename Put>
 __device__ __forceinline__ void chunk_windows(const KernelArgs &a, const ChunkCtx &c, int nf, Put put) {
-    static_assert(kChunk == 2 * kPrepThreads, "two particles of the chunk per thread");
-    // both particles' loads are issued before either is binned (two requests in flight)
-    const int64_t g0 = c.pl.part_base + c.first + threadIdx.x, g1 = g0 + kPrepThreads;
-    const bool v0 = (int)threadIdx.x < c.n, v1 = (int)threadIdx.x + kPrepThreads < c.n;
-    float4 s0 = make_float4(-1.0f, 0.0f, 0.0f, 0.0f), s1 = s0;
-    if (!a.ext) {
-        if (v0) {
-            const float2 sa = a.sa[g0];
-            s0 = make_float4(sa.x, sa.x, 0.0f, sa.y);
-        }
-        if (v1) {
-            const float2 sa = a.sa[g1];
-            s1 = make_float4(sa.x, sa.x, 0.0f, sa.y);
+    constexpr int U = kChunk / kPrepThreads;  // particles of the chunk per thread
+    static_assert(U * kPrepThreads == kChunk, "whole particles per thread");
+    // every particle's loads are issued before any is binned (U requests in flight)
+    int64_t g[U];
+    bool v[U];
+    float4 sh[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        g[u] = c.pl.part_base + c.first + threadIdx.x + u * kPrepThreads;
+        v[u] = (int)threadIdx.x + u * kPrepThreads < c.n;
+        sh[u] = make_float4(-1.0f, 0.0f, 0.0f, 0.0f);
+        if (!a.ext && v[u]) {
+            const float2 sa = a.sa[g[u]];
+            sh[u] = make_float4(sa.x, sa.x, 0.0f, sa.y);
         }
     }
     for (int f = 0; f < nf; ++f) {
         const float4 *pos = f ? a.pos1 : a.pos0;
-        float4 p0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), p1 = p0;
-        if (a.ext) {
-            s0.x = s1.x = -1.0f;
-            if (v0) s0 = a.shape[f * a.n_part + g0];
-            if (v1) s1 = a.shape[f * a.n_part + g1];
-        }
-        if (v0) p0 = pos[g0];
-        if (v1) p1 = pos[g1];
+        float4 p[U];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const float4 &p = u ? p1 : p0, &sh = u ? s1 : s0;
-            if (sh.x < 0.0f) continue;  // outside the chunk, or hidden from this frame
-            const Window w = particle_window2(__float_as_int(p.z), p.x, __float_as_int(p.w), p.y, 6.0f * sh.x,
-                                              6.0f * sh.y, c.d.width, c.d.height);
+        for (int u = 0; u < U; ++u) {
+            if (a.ext) {
+                sh[u].x = -1.0f;
+                if (v[u]) sh[u] = a.shape[f * a.n_part + g[u]];
+            }
+            p[u] = v[u] ? pos[g[u]] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (sh[u].x < 0.0f) continue;  // outside the chunk, or hidden from this frame
+            const Window w = particle_window2(__float_as_int(p[u].z), p[u].x, __float_as_int(p[u].w), p[u].y,
+                                              6.0f * sh[u].x, 6.0f * sh[u].y, c.d.width, c.d.height);
             if (w.j0 > w.j1 || w.i0 > w.i1) continue;
             int32_t tx0, tx1, ty0, ty1;
             window_tiles(w, c.pl.halo, c.pl.tile, c.d.width, c.d.height, tx0, tx1, ty0, ty1);
             for (int32_t ty = ty0; ty <= ty1; ++ty)
-                for (int32_t tx = tx0; tx <= tx1; ++tx) put(f, f * c.pl.ntiles + ty * c.pl.tiles_x + tx, p, sh);
+                for (int32_t tx = tx0; tx <= tx1; ++tx)
+                    put(f, f * c.pl.ntiles + ty * c.pl.tiles_x + tx, p[u], sh[u]);
         }
     }
 }
@@ -445,7 +560,7 @@ __device__ __forceinline__ TileCtx frame1_tile(const KernelArgs &a, const PairPl
     c.y0 = c.ty * pl.tile;
     c.x1 = min(c.x0 + pl.tile, W);
     c.y1 = min(c.y0 + pl.tile, H);
-    c.it = a.items[pl.tile_base + c.t];
+    c.it = work_item(a, pl.tile_base + c.t);  // the fixed layout's count, or the exact item
     c.adv0 = c.it.rec0 - (pl.list_base >> 1);
     return c;
 }
@@ -474,10 +589,10 @@ __device__ __forceinline__ void frame2_tiles(const KernelArgs &a, const PairPlan
 // NT threads: 256, or 1024 at tile 128 (one CTA per SM with its larger window).
 // NT threads per CTA, NB row bands per tile (blockIdx.x = NB tile + band).
 template <int NT, int NB>
-__global__ void __launch_bounds__(NT) k_advect(KernelArgs a) {
+__global__ void __launch_bounds__(NT, 1024 / NT) k_advect(KernelArgs a) {
     if (*a.check != 1) return;
     extern __shared__ __align__(16) float2 s_flow[];
-    __shared__ uint32_t s_nb[kNbrSide * kNbrSide];
+    __shared__ uint32_t s_nb[kNbrSide * kNbrSide], s_base[kNbrSide * kNbrSide];
     __shared__ uint16_t s_home[kAdvBatch];
     __shared__ uint32_t s_nhome;
     const int64_t gt = (int64_t)(blockIdx.x / NB);
@@ -519,6 +634,11 @@ __global__ void __launch_bounds__(NT) k_advect(KernelArgs a) {
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     uint32_t *cnt2 = a.count + pl.tile_base + pl.ntiles;
     const bool same_res = F.gw == F.W && F.gh == F.H;
+    // fixed bins: each batch's frame-2 records are placed here (ranges of the
+    // neighbourhood's bins reserved per batch, farther bins record by record)
+    int64_t cap1 = 0, cap2 = 0;  // frame 1's capacity is not needed here
+    if (a.fixed) fixed_caps(D, pl.tile, pl.halo, cap1, cap2);
+    auto nb_tile = [&](int i) { return (c.ty + i / kNbrSide - kNbr) * pl.tiles_x + (c.tx + i % kNbrSide - kNbr); };
     for (uint32_t base = 0; base < c.it.count; base += kAdvBatch) {
         // compact this batch's home particles (integer position inside the band); particles
         // outside the tile are advected by their own home tile and marked here (by every
@@ -559,12 +679,39 @@ __global__ void __launch_bounds__(NT) k_advect(KernelArgs a) {
             o[2] = make_float2(r.sigma, r.amp);
             frame2_tiles(a, pl, c, r, W, H, [&](int kk, int32_t tile) {
                 if (kk >= 0) atomicAdd(s_nb + kk, 1u);
+                else if (a.fixed) place_fixed(a, pl, 1, tile, cap2, atomicAdd(cnt2 + tile, 1u), r);
                 else atomicAdd(cnt2 + tile, 1u);
             });
         }
         __syncthreads();
+        if (a.fixed) {  // reserve the neighbourhood's ranges, then place this batch's records there
+            for (int i = threadIdx.x; i < kNbrSide * kNbrSide; i += NT) {
+                const uint32_t n = s_nb[i];
+                s_base[i] = n ? atomicAdd(cnt2 + nb_tile(i), n) : 0u;
+                s_nb[i] = 0u;
+            }
+            __syncthreads();
+            for (uint32_t h = threadIdx.x; h < s_nhome; h += NT) {
+                // the record this thread advected above (read back: fewer registers across the integration)
+                const uint32_t k = base + s_home[h];
+                const float2 *rp = reinterpret_cast<const float2 *>(a.adv + c.adv0 + k);
+                const float2 p0 = rp[0], p1 = rp[1], p2 = rp[2];
+                Record r;
+                r.fx = p0.x;
+                r.fy = p0.y;
+                r.ix = __float_as_int(p1.x);
+                r.iy = __float_as_int(p1.y);
+                r.sigma = p2.x;
+                r.amp = p2.y;
+                frame2_tiles(a, pl, c, r, W, H, [&](int kk, int32_t tile) {
+                    if (kk >= 0) place_fixed(a, pl, 1, tile, cap2, s_base[kk] + atomicAdd(s_nb + kk, 1u), r);
+                });
+            }
+            __syncthreads();
+        }
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");  // an empty bin never waited for the window
+    if (a.fixed) return;  // every count was added by the reservations
     for (int i = threadIdx.x; i < kNbrSide * kNbrSide; i += NT) {
         if (!s_nb[i]) continue;
         const int ty = c.ty + i / kNbrSide - kNbr, tx = c.tx + i % kNbrSide - kNbr;
@@ -644,6 +791,76 @@ __global__ void __launch_bounds__(kAdvThreads) k_scatter2(KernelArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// k_rebin: after an overflow of a fixed bin of frame f (a.ovf[f]), the
+// frame's bins are rebuilt in the exact layout, one CTA per pair: the scan
+// of the bin counters (which counted every record), then every record placed
+// at its bin's cursor.  Frame 1 from the seeded positions, frame 2 from the
+// advected records of the frame-1 bins.  Without an overflow every CTA
+// returns at once.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_rebin(KernelArgs a, int f) {
+    if (*a.check != 1 || a.ovf[f] == 0u) return;
+    const int b = (int)blockIdx.x;
+    scan_pair(a, b, f);
+    __syncthreads();  // the cursors written by this CTA
+    const PairPlan pl = a.plan[b];
+    const synthpix_pair_desc &D = a.descs[b];
+    const int W = D.width, H = D.height;
+    uint32_t *cursor = a.cursor + pl.tile_base + (int64_t)f * pl.ntiles;
+    Record *seg = a.rec + pl.list_base + (int64_t)f * pl.list_cap;
+    auto place = [&](int32_t tile, const Record &r) {
+        const uint32_t slot = atomicAdd(cursor + tile, 1u);
+        if ((int64_t)slot < pl.list_cap) {
+            float2 *o = reinterpret_cast<float2 *>(seg + slot);
+            o[0] = make_float2(r.fx, r.fy);
+            o[1] = make_float2(__int_as_float(r.ix), __int_as_float(r.iy));
+            o[2] = make_float2(r.sigma, r.amp);
+        }
+    };
+    auto place_all = [&](const Record &r) {
+        const Window w = particle_window(r.ix, r.fx, r.iy, r.fy, 6.0f * r.sigma, W, H);
+        if (w.j0 > w.j1 || w.i0 > w.i1) return;
+        int32_t tx0, tx1, ty0, ty1;
+        window_tiles(w, pl.halo, pl.tile, W, H, tx0, tx1, ty0, ty1);
+        for (int32_t ty = ty0; ty <= ty1; ++ty)
+            for (int32_t tx = tx0; tx <= tx1; ++tx) place(ty * pl.tiles_x + tx, r);
+    };
+    if (f == 0) {
+        for (uint32_t q = threadIdx.x; q < D.n_particles; q += blockDim.x) {
+            const int64_t g = pl.part_base + q;
+            const float4 p = a.pos0[g];
+            const float2 sa = a.sa[g];
+            Record r;
+            r.fx = p.x;
+            r.fy = p.y;
+            r.ix = __float_as_int(p.z);
+            r.iy = __float_as_int(p.w);
+            r.sigma = sa.x;
+            r.amp = sa.y;
+            place_all(r);
+        }
+        return;
+    }
+    for (int32_t t = 0; t < pl.ntiles; ++t) {  // the advected records of each frame-1 bin
+        const ItemInfo it = work_item(a, pl.tile_base + t);
+        const Record *adv = a.adv + (it.rec0 - (pl.list_base >> 1));
+        for (uint32_t k = threadIdx.x; k < it.count; k += blockDim.x) {
+            const float2 *rp = reinterpret_cast<const float2 *>(adv + k);
+            const float2 p0 = rp[0], p1 = rp[1], p2 = rp[2];
+            if (p2.x < 0.0f) continue;  // advected by another tile
+            Record r;
+            r.fx = p0.x;
+            r.fy = p0.y;
+            r.ix = __float_as_int(p1.x);
+            r.iy = __float_as_int(p1.y);
+            r.sigma = p2.x;
+            r.amp = p2.y;
+            place_all(r);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
 cudaError_t launch_plan(const synthpix_pair_desc *descs, int32_t n_pairs, const TileRule &rule, int32_t fused,
@@ -682,14 +899,25 @@ cudaError_t launch_prep(const KernelArgs &a, cudaStream_t st, cudaEvent_t const 
     ok(big ? cudaFuncSetAttribute(k_advect<512, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adv_smem)
            : cudaFuncSetAttribute(k_advect<256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adv_smem));
     if (e != cudaSuccess) return e;
-    if (nb > 0) ok(launch_kernel(k_seed_advect, nb, kPrepThreads, 0, st, a));
-    ok(launch_kernel(k_scan, (unsigned)a.n_pairs, 1024, 0, st, a, 0));
-    if (nb > 0) ok(launch_kernel(k_scatter, nb, kPrepThreads, 0, st, a));
+    if (a.fixed) {  // frame 1 placed while seeding; the exact rebinning runs only after an overflow
+        if (nb > 0) ok(launch_kernel(k_seed_place, nb, kPrepThreads, 0, st, a));
+        ok(launch_kernel(k_rebin, (unsigned)a.n_pairs, 1024, 0, st, a, 0));
+    } else {
+        if (nb > 0) ok(launch_kernel(k_seed_advect, nb, kPrepThreads, 0, st, a));
+        ok(launch_kernel(k_scan, (unsigned)a.n_pairs, 1024, 0, st, a, 0));
+        if (nb > 0) ok(launch_kernel(k_scatter, nb, kPrepThreads, 0, st, a));
+    }
     if (nt1 > 0) {
         if (big) ok(launch_kernel(k_advect<512, 2>, 2 * nt1, 512, adv_smem, st, a));
         else ok(launch_kernel(k_advect<256, 1>, nt1, 256, adv_smem, st, a));
     }
     mark(2);
+    if (a.fixed) {  // frame 2 placed by k_advect
+        mark(3);
+        ok(launch_kernel(k_rebin, (unsigned)a.n_pairs, 1024, 0, st, a, 1));
+        mark(4);
+        return e;
+    }
     ok(launch_kernel(k_scan, (unsigned)a.n_pairs, 1024, 0, st, a, 1));
     mark(3);
     if (nt1 > 0) ok(launch_kernel(k_scatter2, nt1, kAdvThreads, 0, st, a));

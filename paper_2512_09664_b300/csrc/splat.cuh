@@ -1639,7 +1639,7 @@ __device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo
     // block counts of the next item start from zero (its first count comes after a barrier)
     for (int k = threadIdx.x; k < kBlkPitch * kBlkSide; k += blockDim.x) sh_blk[k] = 0u;
     if (threadIdx.x == 0) {
-        if ((int64_t)t2 < a.n_tiles) after = a.items[t2];
+        if ((int64_t)t2 < a.n_tiles) after = work_item(a, t2);
         else after.pair = -1;
     }
 
@@ -1737,7 +1737,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_splat(KernelArgs a) {
         for (int q = 0; q < 2; ++q) {
             const uint32_t t = atomicAdd(a.ticket, 1u);
             ItemInfo it;
-            if ((int64_t)t < a.n_tiles) it = a.items[t];
+            if ((int64_t)t < a.n_tiles) it = work_item(a, t);
             else it.pair = -1;
             s_item[q] = it;
         }

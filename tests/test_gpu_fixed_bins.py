@@ -1,0 +1,107 @@
+"""Fixed-capacity bins of seeded renders and the exact rebinning after an
+overflow, on the GPU.
+
+Seeded renders place each record straight into a bin of fixed capacity
+while seeding (frame 1) and advecting (frame 2).  A bin that overflows
+flags its frame, and k_rebin then bins the frame again exactly.  The splat
+sums in exact fixed point, so the record order in a bin does not matter and
+both layouts must give bit-identical frames:
+
+* libsynthpix_smallbins.so is built from the same sources with bins of half
+  the expected count, so nearly every bin of both frames overflows there;
+  its renders must equal the product library's bit for bit;
+* a converging flow overflows frame 2 in the product library itself (the
+  count it piles into the centre tile, from the oracle's positions, exceeds
+  the bin capacity); that render must match the oracle.
+"""
+import contextlib
+import os
+
+import numpy as np
+import pytest
+
+from paper_2512_09664_b300 import workloads as W
+
+from parity import compare, gpu_render, oracle_render
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("CUDA device required")
+
+
+@contextlib.contextmanager
+def _library(path):
+    """Route the binding's calls to another build of the library."""
+    from paper_2512_09664_b300 import binding as B
+    saved = (B.LIB_PATH, B._lib)
+    B.LIB_PATH, B._lib = path, None
+    try:
+        yield
+    finally:
+        B.LIB_PATH, B._lib = saved
+
+
+def _smallbins_path():
+    from paper_2512_09664_b300 import build
+    if not os.path.exists(build.SMALLBINS_LIB):
+        pytest.fail(f"{build.SMALLBINS_LIB} is missing: python -m paper_2512_09664_b300.build")
+    return build.SMALLBINS_LIB
+
+
+def _window_max(d_max):
+    return int(np.floor(3.0 * float(d_max))) + 5
+
+
+def _cap2(p, tile, halo):
+    """The frame-2 bin capacity of the library's fixed layout (integer arithmetic)."""
+    reach = tile + 2 * halo + _window_max(max(p.d_max, p.dy_max))
+    sx, sy = min(reach, p.width), min(reach, p.height)
+    e = (p.n_particles * sx * sy + p.width * p.height - 1) // (p.width * p.height)
+    return e + e // 2 + 64
+
+
+@pytest.mark.parametrize("out,tile", [("u8", 128), ("u8", 64), ("f32", 128)])
+def test_overflowing_bins_render_the_same_bits(out, tile):
+    import torch
+
+    from paper_2512_09664_b300.binding import Renderer
+    wl = W.batch_512_u8(n_pairs=3)
+    if out == "f32":
+        wl.out_dtype, wl.quant_bits = "f32", 0
+    ref = Renderer(wl, tile=tile).render().clone()
+    torch.cuda.synchronize()
+    with _library(_smallbins_path()):
+        got = Renderer(wl, tile=tile).render().clone()
+        torch.cuda.synchronize()
+    assert torch.equal(got, ref)
+    assert int((ref != 0).sum()) > 0
+
+
+def test_converging_flow_overflows_frame2_and_matches_the_oracle():
+    import oracle
+
+    h = w = 256
+    tile = 64
+    # (u, v) = -(p - c), c the middle of tile (2, 2): RK4 over dt = 1 contracts distances to c by
+    # about e^-1, so the tile receives the particles of a 174 px square around it (up to 100 px away)
+    c = 2.5 * tile
+    flow = W.linear_flow(h, w, h, w, [[-1.0, 0.0], [0.0, -1.0]], (c, c))
+    pair = W.PairSpec(height=h, width=w, n_particles=W.n_particles_for(0.05, h, w), pair_id=7,
+                      d_dist=0, d_min=1.0, d_max=3.0, noise_sigma=0.02, blur_sigma=0.7,
+                      illum_min=0.8, illum_max=1.0)
+    wl = W.Workload(name="converging_256", seed=11, pairs=[pair], flows=[flow], out_dtype="u8", quant_bits=8)
+    # the precondition: the centre tile's frame-2 bin holds more records than fit
+    parts = oracle.particles(oracle.pair_from_workload(wl, 0), flow)
+    x1, y1 = parts[:, 6], parts[:, 7]
+    t0 = 2 * tile
+    inside = int(((x1 >= t0) & (x1 < t0 + tile) & (y1 >= t0) & (y1 < t0 + tile)).sum())
+    halo = int(np.ceil(3.0 * float(pair.blur_sigma)))
+    assert inside > _cap2(pair, tile, halo), (inside, _cap2(pair, tile, halo))
+    st = compare(wl, gpu_render(wl, tile=tile), oracle_render(wl))
+    print("converging", st)
+    assert st["pixels"] == 2 * h * w
