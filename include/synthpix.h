@@ -287,8 +287,19 @@ int synthpix_render_backward(const synthpix_batch_desc *batch, const synthpix_pa
  * are recorded on `stream` at the stage boundaries, so the caller can time
  * each kernel with cudaEventElapsedTime after synchronising:
  *   [0] before the plan kernel, [1] after the plan and the bin reset,
- *   [2] after seeding + advection, [3] after the bin scan,
- *   [4] after the bin scatter, [5] after the splat + epilogue kernel.
+ *   [2] after everything up to the advection: seeding and advection, and
+ *       the binning done with them.  Seeded renders of round particles bin
+ *       the records into fixed-capacity bins while seeding (frame 1) and
+ *       advecting (frame 2) when those bins fit the bin segments (tile
+ *       edges of 64 and up, in practice); other seeded renders count,
+ *       scan and scatter frame 1 here; renders from given particles or
+ *       with per-frame shapes only seed and advect here,
+ *   [3] after the scan of the remaining bin counts (nothing with fixed
+ *       bins),
+ *   [4] after the scatter of the remaining records (with fixed bins: the
+ *       exact rebinning of frame 2, which does work only if a bin
+ *       overflowed),
+ *   [5] after the splat + epilogue kernel.
  * The paper has no counterpart; it exists for measurement.  Same arguments,
  * errors and asynchrony as synthpix_render_pairs; no synchronisation.
  */
