@@ -193,23 +193,29 @@ ClassInfo batch_classes(const synthpix_batch_desc *batch, const synthpix_pair_de
 
 // The tuning a render runs with: batch->tile for every class when it is
 // set; otherwise the cached entries of the batch's classes, default edges
-// where none is cached.
+// where none is cached.  A cached record-buffer size was tuned with the
+// largest edge of the tuned batch; it is clamped to what this batch's
+// largest edge allows (the chunking changes, the rendered bits do not).
 Tuning resolve_tuning(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs, int32_t n_pairs) {
     if (batch->tile != 0) return default_tuning(uniform_rule(batch->tile));
     Tuning T = default_tuning(kDefaultRule);
     if (n_pairs <= 0 || !pairs) return T;
     const ClassInfo c = batch_classes(batch, pairs, n_pairs);
     std::lock_guard<std::mutex> lock(g_tune_mu);
+    int32_t emax = 0;
     for (int k = 0; k < spx::kSizeClasses; ++k) {
         if (!c.present[k]) continue;
         const auto it = g_tune.find(c.key[k]);
-        if (it == g_tune.end()) continue;
-        T.rule.edge[k] = it->second.tile;
-        if (k == c.largest) {
-            T.rec_buf = it->second.rec_buf;
-            T.reg_epi = it->second.reg_epi;
+        if (it != g_tune.end()) {
+            T.rule.edge[k] = it->second.tile;
+            if (k == c.largest) {
+                T.rec_buf = it->second.rec_buf;
+                T.reg_epi = it->second.reg_epi;
+            }
         }
+        emax = std::max(emax, T.rule.edge[k]);
     }
+    if (T.rec_buf > spx::rec_buf_bytes_for(emax)) T.rec_buf = spx::rec_buf_bytes_for(emax);
     return T;
 }
 

@@ -96,9 +96,10 @@ __host__ __device__ inline PairGeom pair_geom(const synthpix_pair_desc &d, int t
 // widened by the halo and a window on each side: E = N side_x side_y / (W H)
 // expected for uniform positions.  Frame 1 gets E + E/4 + 64 (more than 9
 // standard deviations of the binomial count for E >= 100), frame 2, whose
-// density the flow changes, E + E/2 + 64.  A bin that overflows sets a flag
-// and the frame is binned again exactly (k_rebin).  Integer arithmetic, so
-// host and device agree.
+// density the flow changes, E + E/2 + 64; both at most N (a bin receives a
+// particle at most once, so a frame of one tile never overflows).  A bin
+// that overflows sets a flag and the frame is binned again exactly
+// (k_rebin).  Integer arithmetic, so host and device agree.
 __host__ __device__ inline void fixed_caps(const synthpix_pair_desc &d, int32_t tile, int32_t halo, int64_t &cap1,
                                            int64_t &cap2) {
     const int64_t W = d.width, H = d.height;
@@ -109,8 +110,12 @@ __host__ __device__ inline void fixed_caps(const synthpix_pair_desc &d, int32_t 
     cap1 = e / 2 + 1;
     cap2 = e / 2 + 1;
 #else
+    // a bin receives each particle at most once: N records always fit
+    const int64_t n = (int64_t)d.n_particles;
     cap1 = e + e / 4 + 64;
     cap2 = e + e / 2 + 64;
+    cap1 = cap1 < n ? cap1 : n;
+    cap2 = cap2 < n ? cap2 : n;
 #endif
 }
 
