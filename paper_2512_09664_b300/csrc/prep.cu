@@ -708,6 +708,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_advect(KernelArgs a) {
                 });
             }
             __syncthreads();
+            // the next batch counts from zero (the barrier after its compaction orders this first)
+            for (int i = threadIdx.x; i < kNbrSide * kNbrSide; i += NT) s_nb[i] = 0u;
         }
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");  // an empty bin never waited for the window

@@ -12,7 +12,10 @@ both layouts must give bit-identical frames:
   its renders must equal the product library's bit for bit;
 * a converging flow overflows frame 2 in the product library itself (the
   count it piles into the centre tile, from the oracle's positions, exceeds
-  the bin capacity); that render must match the oracle.
+  the bin capacity); that render must match the oracle;
+* frame-1 bins of more records than the advection examines per pass (a
+  dense 1024^2 pair at tile 128) place frame 2 over several passes; the
+  render must equal the undersized-bin library's exact rebinning.
 """
 import contextlib
 import os
@@ -105,3 +108,23 @@ def test_converging_flow_overflows_frame2_and_matches_the_oracle():
     st = compare(wl, gpu_render(wl, tile=tile), oracle_render(wl))
     print("converging", st)
     assert st["pixels"] == 2 * h * w
+
+
+def test_dense_bins_placed_over_several_passes_render_the_same_bits():
+    import torch
+
+    from paper_2512_09664_b300.binding import Renderer
+    h = w = 1024
+    flow = W.fourier_flow(h, w, h, w, rms=3.0, seed=2251)
+    pair = W.PairSpec(height=h, width=w, n_particles=W.n_particles_for(0.099, h, w), pair_id=251,
+                      d_dist=0, d_min=1.0, d_max=5.0, illum_min=0.7, illum_max=1.0, noise_sigma=0.02,
+                      blur_sigma=0.7)
+    wl = W.Workload(name="dense_1024", seed=2, pairs=[pair], flows=[flow], out_dtype="u16", quant_bits=12)
+    # a frame-1 bin of tile 128 holds about 2300 records: more than one pass of 2048
+    ref = Renderer(wl, tile=128).render().clone()
+    torch.cuda.synchronize()
+    with _library(_smallbins_path()):
+        got = Renderer(wl, tile=128).render().clone()
+        torch.cuda.synchronize()
+    assert torch.equal(got, ref)
+
