@@ -3,7 +3,7 @@
 // gradient of a loss with dL/dB given, with respect to the flow grids, the
 // frame-1 particle positions and the particle diameters.
 //
-//   k_adj_splat   one warp per (particle, frame): gathers
+//   k_adj_splat   a group of 8, 16 or 32 lanes per (particle, frame): gathers
 //                 sum_ij dL/dB(i,j) L(i,j) dS(i,j)/d(x, y, sigma) over the
 //                 particle's window (a per-particle reduction, no pixel atomics)
 //   k_adj_advect  one thread per particle: recomputes the RK4 / Euler
@@ -36,71 +36,100 @@ __device__ __forceinline__ void axis_terms(int32_t ic, float fc, int32_t j, floa
     ds = (ta * pa - tb * pb) * inv;
 }
 
+// GS lanes per (particle, frame): 32 / GS of them per warp, so that lanes
+// are not left idle on windows much narrower than a warp.
+template <int GS>
 __global__ void __launch_bounds__(256) k_adj_splat(KernelArgs a) {
+    static_assert(GS == 8 || GS == 16 || GS == 32, "lane groups within a warp");
     if (*a.check != 1) return;
     extern __shared__ float scr[];
     __shared__ __align__(16) float s_phi[(kPhiDegree + 1) * kPhiPieces];
     for (int k = threadIdx.x; k < (kPhiDegree + 1) * kPhiPieces; k += blockDim.x) s_phi[k] = kPhiTable[k];
     __syncthreads();
     const uint32_t tab = sh_addr(s_phi);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t wg = (int64_t)blockIdx.x * 8 + warp;
-    if (wg >= 2 * a.n_part) return;  // whole warp
-    const int64_t g = wg >> 1;
+    const int lane = threadIdx.x & 31, j = lane & (GS - 1);
+    const int grp = (int)(threadIdx.x / GS);  // group of the CTA
+    const int64_t wg = (int64_t)blockIdx.x * (256 / GS) + grp;
+    const bool valid = wg < 2 * a.n_part;
+    const int64_t g = valid ? wg >> 1 : 0;
     const int f = (int)(wg & 1);
-    const int b = upper_find(a.n_pairs, g, [&](int m) { return a.plan[m].part_base; });
-    const synthpix_pair_desc &D = a.descs[b];
-    const int32_t H = D.height, W = D.width;
-    const float4 p = f ? a.pos1[g] : a.pos0[g];
-    const float2 q = a.sa[g];
-    const int32_t ix = __float_as_int(p.z), iy = __float_as_int(p.w);
-    const float sig = q.x, amp = q.y;
-    const Window w = particle_window(ix, p.x, iy, p.y, 6.0f * sig, W, H);
-    if (w.j0 > w.j1 || w.i0 > w.i1) {
-        if (lane == 0) a.grad_frames[2 * g + f] = make_float4(0.f, 0.f, 0.f, 0.f);
-        return;
+    float sx = 0.f, sy = 0.f, ss = 0.f, sm = 0.f, amp = 0.f, inv = 0.f;
+    // the group's particle and window (any: a non-empty window)
+    bool any = false, illum = false;
+    int32_t H = 0, W = 0, ix = 0, iy = 0, nx = 0, ny = 0;
+    float px = 0.f, py = 0.f, dl = 0.f, lmin = 0.f;
+    Window w;
+    w.j0 = w.i0 = 0;
+    int64_t img = 0;
+    if (valid) {
+        const int b = upper_find(a.n_pairs, g, [&](int m) { return a.plan[m].part_base; });
+        const synthpix_pair_desc &D = a.descs[b];
+        H = D.height;
+        W = D.width;
+        const float4 p = f ? a.pos1[g] : a.pos0[g];
+        const float2 q = a.sa[g];
+        ix = __float_as_int(p.z);
+        iy = __float_as_int(p.w);
+        px = p.x;
+        py = p.y;
+        const float sig = q.x;
+        amp = q.y;
+        inv = __frcp_rn(sig);
+        w = particle_window(ix, px, iy, py, 6.0f * sig, W, H);
+        any = w.j0 <= w.j1 && w.i0 <= w.i1;
+        nx = w.j1 - w.j0 + 1;
+        ny = w.i1 - w.i0 + 1;
+        illum = D.illum_min != 1.0f || D.illum_max != 1.0f;
+        dl = D.illum_max - D.illum_min;
+        lmin = D.illum_min;
+        img = D.image_offset + (int64_t)f * H * W;
     }
-    const int nx = w.j1 - w.j0 + 1, ny = w.i1 - w.i0 + 1;
     const int wq = a.warp_scratch;  // floats per array
-    float *ex = scr + warp * 8 * wq, *dex = ex + wq, *dsx = dex + wq, *lx = dsx + wq;
+    float *ex = scr + grp * 8 * wq, *dex = ex + wq, *dsx = dex + wq, *lx = dsx + wq;
     float *ey = lx + wq, *dey = ey + wq, *dsy = dey + wq, *ly = dsy + wq;
-    const float inv = __frcp_rn(sig);
-    const bool illum = D.illum_min != 1.0f || D.illum_max != 1.0f;
-    for (int e = lane; e < nx; e += 32) {
-        axis_terms(ix, p.x, w.j0 + e, inv, tab, ex[e], dex[e], dsx[e]);
-        const float sv = sinpif(((float)(w.j0 + e) + 0.5f) / (float)W);
-        lx[e] = sv * sv;
+    if (any) {
+        for (int e = j; e < nx; e += GS) {
+            axis_terms(ix, px, w.j0 + e, inv, tab, ex[e], dex[e], dsx[e]);
+            if (illum) {
+                const float sv = sinpif(((float)(w.j0 + e) + 0.5f) / (float)W);
+                lx[e] = sv * sv;
+            }
+        }
+        for (int e = j; e < ny; e += GS) {
+            axis_terms(iy, py, w.i0 + e, inv, tab, ey[e], dey[e], dsy[e]);
+            if (illum) {
+                const float sv = sinpif(((float)(w.i0 + e) + 0.5f) / (float)H);
+                ly[e] = sv * sv;
+            }
+        }
     }
-    for (int e = lane; e < ny; e += 32) {
-        axis_terms(iy, p.y, w.i0 + e, inv, tab, ey[e], dey[e], dsy[e]);
-        const float sv = sinpif(((float)(w.i0 + e) + 0.5f) / (float)H);
-        ly[e] = sv * sv;
-    }
-    __syncwarp();
-    const float *G = a.grad_images + D.image_offset + (int64_t)f * H * W;
-    const float dl = D.illum_max - D.illum_min;
-    const float invx = 1.0f / (float)nx;
-    float sx = 0.f, sy = 0.f, ss = 0.f, sm = 0.f;
-    for (int m = lane; m < nx * ny; m += 32) {
-        const int r = min((int)(((float)m + 0.5f) * invx), ny - 1);
-        const int c = m - r * nx;
-        if ((unsigned)c >= (unsigned)nx) continue;
-        float gv = G[(int64_t)(w.i0 + r) * W + (w.j0 + c)];
-        if (illum) gv *= fmaf(dl, lx[c] * ly[r], D.illum_min);
-        sx = fmaf(gv * dex[c], ey[r], sx);
-        sy = fmaf(gv * ex[c], dey[r], sy);
-        ss = fmaf(gv, fmaf(dsx[c], ey[r], ex[c] * dsy[r]), ss);
-        sm = fmaf(gv * ex[c], ey[r], sm);
+    __syncwarp();  // every lane of the warp: the group's terms are visible to the group
+    if (any) {
+        const float *G = a.grad_images + img;
+        const float invx = 1.0f / (float)nx;
+        for (int m = j; m < nx * ny; m += GS) {
+            const int r = min((int)(((float)m + 0.5f) * invx), ny - 1);
+            const int c = m - r * nx;
+            if ((unsigned)c >= (unsigned)nx) continue;
+            float gv = G[(int64_t)(w.i0 + r) * W + (w.j0 + c)];
+            if (illum) gv *= fmaf(dl, lx[c] * ly[r], lmin);
+            sx = fmaf(gv * dex[c], ey[r], sx);
+            sy = fmaf(gv * ex[c], dey[r], sy);
+            ss = fmaf(gv, fmaf(dsx[c], ey[r], ex[c] * dsy[r]), ss);
+            sm = fmaf(gv * ex[c], ey[r], sm);
+        }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
+    for (int o = GS / 2; o > 0; o >>= 1) {  // within the group (xor offsets below GS stay in it)
         sx += __shfl_xor_sync(0xffffffffu, sx, o);
         sy += __shfl_xor_sync(0xffffffffu, sy, o);
         ss += __shfl_xor_sync(0xffffffffu, ss, o);
         sm += __shfl_xor_sync(0xffffffffu, sm, o);
     }
     // S = amp Ex Ey with amp = Ieff 2 pi sigma^2: d amp / d sigma = 2 amp / sigma
-    if (lane == 0) a.grad_frames[2 * g + f] = make_float4(amp * sx, amp * sy, amp * ss + 2.0f * amp * inv * sm, 0.f);
+    if (valid && j == 0)
+        a.grad_frames[2 * g + f] =
+            any ? make_float4(amp * sx, amp * sy, amp * ss + 2.0f * amp * inv * sm, 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // Velocity at i + f (split) with its Jacobian (J = du/dx, du/dy, dv/dx, dv/dy)
@@ -217,16 +246,29 @@ __global__ void __launch_bounds__(128) k_adj_advect(KernelArgs a) {
     }
 }
 
+// Lanes per (particle, frame) of k_adj_splat for windows of at most wmax
+// pixels a side: the narrowest group whose lanes take at most two columns
+// (or rows) each.
+__host__ __device__ inline int adj_group(int wmax) { return wmax <= 16 ? 8 : (wmax <= 32 ? 16 : 32); }
+
 cudaError_t launch_adjoint(const KernelArgs &a, cudaStream_t st) {
     if (a.n_part == 0) return cudaGetLastError();
-    const size_t smem = (size_t)8 * 8 * a.warp_scratch * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(k_adj_splat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int gs = adj_group(a.warp_scratch - 2);
+    const int per_cta = 256 / gs;  // (particle, frame) groups of a CTA
+    const size_t smem = (size_t)per_cta * 8 * a.warp_scratch * sizeof(float);
+    const unsigned grid = (unsigned)((2 * a.n_part + per_cta - 1) / per_cta);
+    auto go = [&](auto kern) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<grid, 256, smem, st>>>(a);
+        return cudaGetLastError();
+    };
+    cudaError_t e = gs == 8 ? go(k_adj_splat<8>) : (gs == 16 ? go(k_adj_splat<16>) : go(k_adj_splat<32>));
     if (e != cudaSuccess) return e;
-    k_adj_splat<<<(unsigned)((2 * a.n_part + 7) / 8), 256, smem, st>>>(a);
-    const unsigned grid = (unsigned)((a.n_part + 127) / 128);
-    if (a.n_substeps <= 4) k_adj_advect<4><<<grid, 128, 0, st>>>(a);
-    else if (a.n_substeps <= 8) k_adj_advect<8><<<grid, 128, 0, st>>>(a);
-    else k_adj_advect<kMaxAdjointSubsteps><<<grid, 128, 0, st>>>(a);
+    const unsigned agrid = (unsigned)((a.n_part + 127) / 128);
+    if (a.n_substeps <= 4) k_adj_advect<4><<<agrid, 128, 0, st>>>(a);
+    else if (a.n_substeps <= 8) k_adj_advect<8><<<agrid, 128, 0, st>>>(a);
+    else k_adj_advect<kMaxAdjointSubsteps><<<agrid, 128, 0, st>>>(a);
     return cudaGetLastError();
 }
 
