@@ -481,6 +481,14 @@ int synthpix_match_histogram(const synthpix_batch_desc *batch, const synthpix_pa
 /* SYNTHPIX_ABI_VERSION of the loaded library. */
 int synthpix_version(void);
 
+/*
+ * Kernel launches the library has issued in this process so far (all
+ * threads and devices; a launch that returned an error is not counted).  For
+ * measurement: the difference around a loop of calls is the number of the
+ * library's kernels those calls launched.  The paper has no counterpart.
+ */
+uint64_t synthpix_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,7 +28,8 @@ _EXPORTS = ("synthpix_workspace_bytes", "synthpix_render_pairs", "synthpix_rende
             "synthpix_render_backward", "synthpix_autotune_tile", "synthpix_autotune", "synthpix_tuning_lookup",
             "synthpix_tuning_set", "synthpix_tuning_clear", "synthpix_render_pairs_noalloc",
             "synthpix_fourier_flows", "synthpix_fourier_flows_workspace_bytes", "synthpix_match_histogram",
-            "synthpix_match_histogram_workspace_bytes", "synthpix_last_error", "synthpix_version")
+            "synthpix_match_histogram_workspace_bytes", "synthpix_last_error", "synthpix_version",
+            "synthpix_launch_count")
 STAGES = ("plan", "seed_advect", "bin_scan", "bin_scatter", "splat_epilogue")
 
 
@@ -133,8 +134,15 @@ def lib():
         L.synthpix_last_error.restype = C.c_char_p
         L.synthpix_version.argtypes = []
         L.synthpix_version.restype = C.c_int
+        L.synthpix_launch_count.argtypes = []
+        L.synthpix_launch_count.restype = C.c_uint64
         _lib = L
     return _lib
+
+
+def launch_count() -> int:
+    """Kernel launches the library has issued in this process (synthpix_launch_count)."""
+    return int(lib().synthpix_launch_count())
 
 
 def exported_symbols() -> List[str]:

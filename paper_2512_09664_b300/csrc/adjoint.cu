@@ -260,16 +260,14 @@ cudaError_t launch_adjoint(const KernelArgs &a, cudaStream_t st) {
     auto go = [&](auto kern) -> cudaError_t {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        kern<<<grid, 256, smem, st>>>(a);
-        return cudaGetLastError();
+        return launch_kernel(kern, grid, 256, smem, st, a);
     };
     cudaError_t e = gs == 8 ? go(k_adj_splat<8>) : (gs == 16 ? go(k_adj_splat<16>) : go(k_adj_splat<32>));
     if (e != cudaSuccess) return e;
     const unsigned agrid = (unsigned)((a.n_part + 127) / 128);
-    if (a.n_substeps <= 4) k_adj_advect<4><<<agrid, 128, 0, st>>>(a);
-    else if (a.n_substeps <= 8) k_adj_advect<8><<<agrid, 128, 0, st>>>(a);
-    else k_adj_advect<kMaxAdjointSubsteps><<<agrid, 128, 0, st>>>(a);
-    return cudaGetLastError();
+    if (a.n_substeps <= 4) return launch_kernel(k_adj_advect<4>, agrid, 128, 0, st, a);
+    if (a.n_substeps <= 8) return launch_kernel(k_adj_advect<8>, agrid, 128, 0, st, a);
+    return launch_kernel(k_adj_advect<kMaxAdjointSubsteps>, agrid, 128, 0, st, a);
 }
 
 }  // namespace spx

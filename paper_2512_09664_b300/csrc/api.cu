@@ -2,6 +2,7 @@
 // validation, workspace layout and the launch sequence.  Nothing here touches
 // the device before every argument has been checked.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -347,6 +348,12 @@ size_t elem_size(int32_t dt) {
 
 }  // namespace
 
+namespace spx {
+static std::atomic<uint64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+uint64_t launch_total() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace spx
+
 static_assert(sizeof(synthpix_pair_desc) == 160, "pair descriptor ABI");
 static_assert(sizeof(synthpix_batch_desc) == 64, "batch descriptor ABI");
 
@@ -355,6 +362,8 @@ extern "C" {
 const char *synthpix_last_error(void) { return g_err; }
 
 int synthpix_version(void) { return SYNTHPIX_ABI_VERSION; }
+
+uint64_t synthpix_launch_count(void) { return spx::launch_total(); }
 
 size_t synthpix_workspace_bytes(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
                                 int32_t n_pairs) {

@@ -75,14 +75,21 @@ __device__ __forceinline__ ItemInfo work_item(const KernelArgs &a, int64_t t) {
 
 constexpr int kStageEvents = 6;
 
-// Launch a kernel of the render sequence; returns the launch's error.
+// Counts the library's kernel launches (synthpix_launch_count); every launch
+// of the library goes through launch_kernel, which calls it.
+void count_launch();
+uint64_t launch_total();
+
+// Launch a kernel of the library; returns the launch's error.
 // (Programmatic dependent launch was measured: a replayed render took 12 us
 // longer with it, so the kernels are launched plainly.)
 template <typename... P, typename... A>
 inline cudaError_t launch_kernel(void (*kernel)(P...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
                                   A &&...args) {
     kernel<<<grid, block, smem, st>>>(static_cast<A &&>(args)...);
-    return cudaGetLastError();
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) count_launch();
+    return e;
 }
 constexpr int kSplatThreads = 256;      // k_splat below tile 128, k_finish
 constexpr int kSplatMaxThreads = 1024;  // k_splat at tile 128 (one CTA per SM)

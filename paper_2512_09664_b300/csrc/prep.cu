@@ -932,7 +932,7 @@ cudaError_t launch_prep(const KernelArgs &a, cudaStream_t st, cudaEvent_t const 
 namespace spx {
 
 cudaError_t launch_seed_only(const KernelArgs &a, cudaStream_t st) {
-    if (a.n_chunks > 0) k_seed_advect<<<(unsigned)a.n_chunks, kPrepThreads, 0, st>>>(a);
+    if (a.n_chunks > 0) return launch_kernel(k_seed_advect, (unsigned)a.n_chunks, kPrepThreads, 0, st, a);
     return cudaGetLastError();
 }
 

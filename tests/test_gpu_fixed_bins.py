@@ -128,3 +128,29 @@ def test_dense_bins_placed_over_several_passes_render_the_same_bits():
         torch.cuda.synchronize()
     assert torch.equal(got, ref)
 
+
+
+def test_launch_count_of_each_binning_mode():
+    import torch
+
+    from paper_2512_09664_b300.binding import Renderer, launch_count
+    wl = W.batch_512_u8(n_pairs=2)
+
+    def launches(r):
+        r.render()
+        torch.cuda.synchronize()
+        n0 = launch_count()
+        r.render()
+        torch.cuda.synchronize()
+        return launch_count() - n0
+
+    # fixed bins: plan, seeding + frame-1 placement, rebin check, advection + frame-2 placement,
+    # rebin check, splat
+    assert launches(Renderer(wl, tile=128)) == 6
+    # counting sort (bins of 32-pixel tiles do not fit fixed capacities): plan, seed, scan,
+    # scatter, advection, scan, scatter, splat
+    assert launches(Renderer(wl, tile=32)) == 8
+    # per-particle advection (hiding): plan, seed + advect, scan, scatter, splat
+    hidden = W.batch_512_u8(n_pairs=2)
+    hidden.hide_prob = np.float32(0.1)
+    assert launches(Renderer(hidden, tile=128)) == 5
