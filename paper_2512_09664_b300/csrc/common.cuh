@@ -72,24 +72,6 @@ __host__ __device__ inline bool pair_general_shape(const synthpix_pair_desc &d) 
     return d.dy_min != 0.0f || d.dy_max != 0.0f || d.rho_min != 0.0f || d.rho_max != 0.0f;
 }
 
-__host__ __device__ inline PairGeom pair_geom(const synthpix_pair_desc &d, int tile, bool fused) {
-    PairGeom g;
-    g.tiles_x = (d.width + tile - 1) / tile;
-    g.tiles_y = (d.height + tile - 1) / tile;
-    g.ntiles = g.tiles_x * g.tiles_y;
-    g.blur_r = blur_radius_of(d.blur_sigma);
-    g.halo = fused ? g.blur_r : 0;
-    // pixels of a clipped particle window: <= floor(3 d_max) + 2, plus margin
-    // for FP32 rounding of d and x +- 1.5 d; widened by the halo on both sides
-    int32_t ext = window_max(pair_max_diameter(d)) + 2 * g.halo;
-    g.span = (ext - 1) / tile + 2;
-    int32_t sx = g.span < g.tiles_x ? g.span : g.tiles_x;
-    int32_t sy = g.span < g.tiles_y ? g.span : g.tiles_y;
-    g.list_cap = (int64_t)d.n_particles * (int64_t)sx * (int64_t)sy;
-    g.chunks = ((int64_t)d.n_particles + kChunk - 1) / kChunk;
-    return g;
-}
-
 // Records per bin of the fixed bin layout of seeded renders (each producer
 // places its records directly, without a counting pass).  A bin of an
 // interior tile collects the particles whose centres lie within the tile
@@ -117,6 +99,29 @@ __host__ __device__ inline void fixed_caps(const synthpix_pair_desc &d, int32_t 
     cap1 = cap1 < n ? cap1 : n;
     cap2 = cap2 < n ? cap2 : n;
 #endif
+}
+
+__host__ __device__ inline PairGeom pair_geom(const synthpix_pair_desc &d, int tile, bool fused) {
+    PairGeom g;
+    g.tiles_x = (d.width + tile - 1) / tile;
+    g.tiles_y = (d.height + tile - 1) / tile;
+    g.ntiles = g.tiles_x * g.tiles_y;
+    g.blur_r = blur_radius_of(d.blur_sigma);
+    g.halo = fused ? g.blur_r : 0;
+    // pixels of a clipped particle window: <= floor(3 d_max) + 2, plus margin
+    // for FP32 rounding of d and x +- 1.5 d; widened by the halo on both sides
+    int32_t ext = window_max(pair_max_diameter(d)) + 2 * g.halo;
+    g.span = (ext - 1) / tile + 2;
+    int32_t sx = g.span < g.tiles_x ? g.span : g.tiles_x;
+    int32_t sy = g.span < g.tiles_y ? g.span : g.tiles_y;
+    g.list_cap = (int64_t)d.n_particles * (int64_t)sx * (int64_t)sy;
+    // room for the fixed bins too (sparse pairs of many tiles need more than the bound above)
+    int64_t cap1, cap2;
+    fixed_caps(d, tile, g.halo, cap1, cap2);
+    const int64_t fixed = (int64_t)g.ntiles * (cap1 > cap2 ? cap1 : cap2);
+    if (fixed > g.list_cap) g.list_cap = fixed;
+    g.chunks = ((int64_t)d.n_particles + kChunk - 1) / kChunk;
+    return g;
 }
 
 // A particle as binned for one frame: split position, sigma, amplitude.

@@ -147,9 +147,12 @@ def test_launch_count_of_each_binning_mode():
     # fixed bins: plan, seeding + frame-1 placement, rebin check, advection + frame-2 placement,
     # rebin check, splat
     assert launches(Renderer(wl, tile=128)) == 6
-    # counting sort (bins of 32-pixel tiles do not fit fixed capacities): plan, seed, scan,
-    # scatter, advection, scan, scatter, splat
-    assert launches(Renderer(wl, tile=32)) == 8
+    assert launches(Renderer(wl, tile=32)) == 6
+    # counting sort (a batch with an empty pair): plan, seed, scan, scatter, advection, scan,
+    # scatter, splat
+    empty = W.batch_512_u8(n_pairs=2)
+    empty.pairs[1].n_particles = 0
+    assert launches(Renderer(empty, tile=128)) == 8
     # per-particle advection (hiding): plan, seed + advect, scan, scatter, splat
     hidden = W.batch_512_u8(n_pairs=2)
     hidden.hide_prob = np.float32(0.1)
