@@ -157,3 +157,17 @@ def test_launch_count_of_each_binning_mode():
     hidden = W.batch_512_u8(n_pairs=2)
     hidden.hide_prob = np.float32(0.1)
     assert launches(Renderer(hidden, tile=128)) == 5
+
+
+def test_counting_sort_path_of_a_batch_with_an_empty_pair_matches_the_oracle():
+    # an empty pair keeps the counting-sort bins (k_scan, k_scatter, the tiled advection's
+    # marks and k_scatter2): the other pairs must render as the oracle does
+    h = w = 256
+    flows = [W.fourier_flow(h, w, h, w, rms=3.0, seed=1500 + b) for b in range(3)]
+    pairs = [W.PairSpec(height=h, width=w, n_particles=W.n_particles_for(0.05, h, w) if b != 1 else 0,
+                        pair_id=b, flow_index=b, d_min=1.0, d_max=4.0, illum_min=0.7, illum_max=1.0,
+                        noise_sigma=0.02, blur_sigma=0.7) for b in range(3)]
+    wl = W.Workload(name="empty_pair", seed=5, pairs=pairs, flows=flows, out_dtype="u8", quant_bits=8)
+    for tile in (64, 128):
+        st = compare(wl, gpu_render(wl, tile=tile), oracle_render(wl))
+        assert st["pixels"] == 3 * 2 * h * w
