@@ -1,17 +1,22 @@
 // sm_103a kernels of the PIV image-pair renderer (SynthPix, arXiv 2512.09664,
 // Section 2) that prepare the splat.  One batch is rendered by a fixed
-// sequence of launches:
+// sequence of launches.  Seeded renders of round particles, with
+// fixed-capacity bins (every pair seeded with at least one particle):
 //
 //   k_plan         per-pair prefix sums of particles, tiles and bin slots,
-//                  blur taps, the work-queue ticket
-//   k_seed_advect  Philox attributes of every particle, advection through the
-//                  flow grid (RK4 / Euler substeps), split positions and
-//                  per-(frame, tile) counts
-//   k_scan         exclusive scan of the counts of each (pair, frame), and the
-//                  splat's work items
-//   k_scatter      particle records into the bins of every tile their (halo-
-//                  widened) window meets
-//   k_splat        (splat.cu) persistent CTAs over the work items
+//                  blur taps, the work-queue ticket; clears the bin counters
+//   k_seed_place   Philox attributes of every particle, split positions, and
+//                  the frame-1 records placed into the fixed bins
+//   k_rebin (f 1)  only after a frame-1 bin overflowed: the exact binning
+//   k_advect       tiled advection of each frame-1 tile's home particles from
+//                  a flow window in shared memory; frame-2 records placed
+//   k_rebin (f 2)  only after a frame-2 bin overflowed
+//   k_splat        (splat.cuh) persistent CTAs over the work items
+//
+// Otherwise the bins come from a counting sort: k_seed_advect (which also
+// advects per particle when the render needs each particle's index: given
+// particles, per-frame shapes), k_scan (offsets and work items), k_scatter,
+// and for seeded renders k_advect, k_scan, k_scatter2 for frame 2.
 //
 // No kernel waits on another CTA, spins, traps or asserts.
 #include <cuda_bf16.h>
