@@ -105,18 +105,21 @@ __global__ void __launch_bounds__(256) k_adj_splat(KernelArgs a) {
     }
     __syncwarp();  // every lane of the warp: the group's terms are visible to the group
     if (any) {
-        const float *G = a.grad_images + img;
-        const float invx = 1.0f / (float)nx;
-        for (int m = j; m < nx * ny; m += GS) {
-            const int r = min((int)(((float)m + 0.5f) * invx), ny - 1);
-            const int c = m - r * nx;
-            if ((unsigned)c >= (unsigned)nx) continue;
-            float gv = G[(int64_t)(w.i0 + r) * W + (w.j0 + c)];
-            if (illum) gv *= fmaf(dl, lx[c] * ly[r], lmin);
-            sx = fmaf(gv * dex[c], ey[r], sx);
-            sy = fmaf(gv * ex[c], dey[r], sy);
-            ss = fmaf(gv, fmaf(dsx[c], ey[r], ex[c] * dsy[r]), ss);
-            sm = fmaf(gv * ex[c], ey[r], sm);
+        // lane j walks the rows of columns j, j + GS, ...: the column terms stay in registers, the
+        // row terms are read once per pixel (the same word for all lanes), dL/dB a row at a time
+        const float *G = a.grad_images + img + (int64_t)w.i0 * W + w.j0;
+        for (int c = j; c < nx; c += GS) {
+            const float exc = ex[c], dexc = dex[c], dsxc = dsx[c], lxc = illum ? lx[c] : 0.0f;
+            const float *gc = G + c;
+            for (int r = 0; r < ny; ++r) {
+                float gv = gc[(int64_t)r * W];
+                const float eyr = ey[r];
+                if (illum) gv *= fmaf(dl, lxc * ly[r], lmin);
+                sx = fmaf(gv * dexc, eyr, sx);
+                sy = fmaf(gv * exc, dey[r], sy);
+                ss = fmaf(gv, fmaf(dsxc, eyr, exc * dsy[r]), ss);
+                sm = fmaf(gv * exc, eyr, sm);
+            }
         }
     }
 #pragma unroll
