@@ -45,7 +45,6 @@ struct Plan {
     float max_d;
     int32_t ext;      // per-frame shapes: general shapes, frame-2 variation or hiding
     int32_t general;  // general-shape splat (32-byte records)
-    int32_t fixed_ok; // every pair's fixed bins (spx::fixed_caps) fit its bin segments
 };
 
 int check_batch(const synthpix_batch_desc *b) {
@@ -251,7 +250,6 @@ int make_plan_any(const synthpix_batch_desc *batch, const synthpix_pair_desc *pa
     P.max_d = 0.0f;
     P.ext = (batch->hide_prob > 0.0f || (batch->flags & SYNTHPIX_FLAG_OUT_OF_PLANE)) ? 1 : 0;
     P.general = 0;
-    P.fixed_ok = 1;
     spx::Layout &L = P.L;
     L.n_part = L.n_tiles = L.n_list = L.n_inter = L.n_chunks = 0;
     for (int32_t b = 0; b < n_pairs; ++b) {
@@ -268,13 +266,6 @@ int make_plan_any(const synthpix_batch_desc *batch, const synthpix_pair_desc *pa
                 g.ntiles = std::max(g.ntiles, h.ntiles);
                 g.list_cap = std::max(g.list_cap, h.list_cap);
             }
-        {
-            int64_t cap1, cap2;
-            spx::fixed_caps(pairs[b], t, g.halo, cap1, cap2);
-            if (pairs[b].n_particles == 0 || (int64_t)g.ntiles * std::max(cap1, cap2) > g.list_cap ||
-                std::max(cap1, cap2) > 0x7FFFFFFFLL)
-                P.fixed_ok = 0;
-        }
         L.n_part += pairs[b].n_particles;
         L.n_tiles += 2LL * g.ntiles;
         L.n_list += 2LL * g.list_cap;
@@ -493,7 +484,6 @@ static int run(Mode mode, const synthpix_batch_desc *batch, const synthpix_pair_
                   ? 1 : 0;
     a.ticket = ticket;
     a.ovf = ticket + 1;
-    a.fixed = a.tiled && P.fixed_ok ? 1 : 0;
     a.rec_buf_bytes = P.T.rec_buf;
     a.reg_epilogue = P.T.reg_epi;
     a.blur_w = blur_w;

@@ -51,7 +51,7 @@ __host__ __device__ inline int32_t rule_tile(const TileRule &r, const synthpix_p
 struct PairGeom {
     int32_t tiles_x, tiles_y, ntiles, blur_r, halo, span;
     int64_t list_cap;
-    int64_t chunks;  // ceil(n_particles / kChunk)
+    int64_t chunks;  // ceil(n_particles / kChunk), at least 1 (the first chunk of a pair writes its work items)
 };
 
 __host__ __device__ inline int32_t blur_radius_of(float blur_sigma) {
@@ -120,7 +120,7 @@ __host__ __device__ inline PairGeom pair_geom(const synthpix_pair_desc &d, int t
     fixed_caps(d, tile, g.halo, cap1, cap2);
     const int64_t fixed = (int64_t)g.ntiles * (cap1 > cap2 ? cap1 : cap2);
     if (fixed > g.list_cap) g.list_cap = fixed;
-    g.chunks = ((int64_t)d.n_particles + kChunk - 1) / kChunk;
+    g.chunks = max((int64_t)1, ((int64_t)d.n_particles + kChunk - 1) / kChunk);  // an empty pair: one empty chunk
     return g;
 }
 

@@ -38,9 +38,9 @@ struct KernelArgs {
     ItemInfo *items;                  // per (pair, frame, tile): the splat's work items
     Record *rec;                      // bins
     Record *adv;                      // tiled advection: frame-2 records by frame-1 bin slot (sigma < 0: none)
-    int32_t tiled;                    // 1: frame 2 comes from the tiled advection (k_advect), not k_seed_advect
-    int32_t fixed;                    // 1 (tiled renders whose fixed bins fit the bin segments): k_seed_place
-                                      // and k_advect place records into fixed-capacity bins (fixed_caps)
+    int32_t tiled;                    // 1 (seeded renders): frame 2 comes from the tiled advection (k_advect),
+                                      // and k_seed_place and k_advect place the records into fixed-capacity
+                                      // bins (fixed_caps); 0: k_seed_advect and a counting sort
     uint32_t *ovf;                    // [2]: a fixed bin of frame 1 / frame 2 overflowed (zeroed by k_plan)
     uint32_t *ticket;                 // work-queue counter of the persistent splat
     int32_t smem_edge;                // capacity edge of the on-chip tile (tile + 2 max radius)
@@ -66,7 +66,7 @@ struct KernelArgs {
 // frame was binned again exactly after an overflow (k_rebin wrote the item).
 __device__ __forceinline__ ItemInfo work_item(const KernelArgs &a, int64_t t) {
     ItemInfo it = a.items[t];
-    if (a.fixed) {  // the three loads are independent of the item's
+    if (a.tiled) {  // the three loads are independent of the item's
         const uint32_t n = a.count[t], o0 = a.ovf[0], o1 = a.ovf[1];
         if ((it.frame ? o1 : o0) == 0u) it.count = min(it.count, n);
     }

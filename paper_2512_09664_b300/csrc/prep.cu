@@ -1,7 +1,7 @@
 // sm_103a kernels of the PIV image-pair renderer (SynthPix, arXiv 2512.09664,
 // Section 2) that prepare the splat.  One batch is rendered by a fixed
 // sequence of launches.  Seeded renders of round particles, with
-// fixed-capacity bins (every pair seeded with at least one particle):
+// fixed-capacity bins:
 //
 //   k_plan         per-pair prefix sums of particles, tiles and bin slots,
 //                  blur taps, the work-queue ticket; clears the bin counters
@@ -13,10 +13,10 @@
 //   k_rebin (f 2)  only after a frame-2 bin overflowed
 //   k_splat        (splat.cuh) persistent CTAs over the work items
 //
-// Otherwise the bins come from a counting sort: k_seed_advect (which also
-// advects per particle when the render needs each particle's index: given
-// particles, per-frame shapes), k_scan (offsets and work items), k_scatter,
-// and for seeded renders k_advect, k_scan, k_scatter2 for frame 2.
+// Renders that need each particle's index when its frame-2 record is made
+// (given particles, per-frame shapes) advect per particle and bin both frames
+// by a counting sort: k_plan, k_seed_advect (attributes, advection, counts),
+// k_scan (offsets and work items), k_scatter, k_splat.
 //
 // No kernel waits on another CTA, spins, traps or asserts.
 #include <cuda_bf16.h>
@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_scatter(KernelArgs a) {
     __shared__ __align__(16) ChunkCtx c;
     __shared__ uint32_t cnt[kHistMax], base[kHistMax];
     load_chunk(a, c);
-    const int nf = a.tiled ? 1 : 2;  // tiled: frame 2 is placed by k_scatter2
+    const int nf = 2;  // (renders without the tiled advection) both frames
     const int nk = nf * c.pl.ntiles;
     uint32_t *cursor = a.cursor + c.pl.tile_base;
     if (nk > kHistMax) {
@@ -530,10 +530,9 @@ __global__ void __launch_bounds__(kPrepThreads) k_scatter(KernelArgs a) {
 // coalesced 8-byte loads; the tile's home particles (integer position inside
 // the tile, so each particle once) are advected from it, lookups that leave
 // the window read global memory.  Frame-2 records go to adv (by frame-1 bin
-// slot) and frame-2 bin counts are aggregated on chip for tiles near the
-// home tile.  k_scatter2 places them once the frame-2 bins are scanned.
+// slot: k_rebin's input after an overflow) and, counted on chip for the tiles
+// near the home tile, into those tiles' fixed frame-2 bins.
 // ---------------------------------------------------------------------------
-constexpr int kAdvThreads = 256;
 constexpr int kAdvMargin = 2;  // image pixels of flow staged beyond the tile on each side (measured best)
 constexpr int kNbr = 3;        // on-chip counters for frame-2 tiles within +-kNbr of the home tile
 constexpr int kNbrSide = 2 * kNbr + 1;
@@ -641,8 +640,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_advect(KernelArgs a) {
     const bool same_res = F.gw == F.W && F.gh == F.H;
     // fixed bins: each batch's frame-2 records are placed here (ranges of the
     // neighbourhood's bins reserved per batch, farther bins record by record)
-    int64_t cap1 = 0, cap2 = 0;  // frame 1's capacity is not needed here
-    if (a.fixed) fixed_caps(D, pl.tile, pl.halo, cap1, cap2);
+    int64_t cap1, cap2;  // frame 1's capacity is not needed here
+    fixed_caps(D, pl.tile, pl.halo, cap1, cap2);
     auto nb_tile = [&](int i) { return (c.ty + i / kNbrSide - kNbr) * pl.tiles_x + (c.tx + i % kNbrSide - kNbr); };
     for (uint32_t base = 0; base < c.it.count; base += kAdvBatch) {
         // compact this batch's home particles (integer position inside the band); particles
@@ -684,12 +683,11 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_advect(KernelArgs a) {
             o[2] = make_float2(r.sigma, r.amp);
             frame2_tiles(a, pl, c, r, W, H, [&](int kk, int32_t tile) {
                 if (kk >= 0) atomicAdd(s_nb + kk, 1u);
-                else if (a.fixed) place_fixed(a, pl, 1, tile, cap2, atomicAdd(cnt2 + tile, 1u), r);
-                else atomicAdd(cnt2 + tile, 1u);
+                else place_fixed(a, pl, 1, tile, cap2, atomicAdd(cnt2 + tile, 1u), r);
             });
         }
         __syncthreads();
-        if (a.fixed) {  // reserve the neighbourhood's ranges, then place this batch's records there
+        {  // reserve the neighbourhood's ranges, then place this batch's records there
             for (int i = threadIdx.x; i < kNbrSide * kNbrSide; i += NT) {
                 const uint32_t n = s_nb[i];
                 s_base[i] = n ? atomicAdd(cnt2 + nb_tile(i), n) : 0u;
@@ -718,83 +716,6 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_advect(KernelArgs a) {
         }
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");  // an empty bin never waited for the window
-    if (a.fixed) return;  // every count was added by the reservations
-    for (int i = threadIdx.x; i < kNbrSide * kNbrSide; i += NT) {
-        if (!s_nb[i]) continue;
-        const int ty = c.ty + i / kNbrSide - kNbr, tx = c.tx + i % kNbrSide - kNbr;
-        atomicAdd(cnt2 + ty * pl.tiles_x + tx, s_nb[i]);
-    }
-}
-
-// Frame-2 records of the tiled advection into their bins: count per nearby
-// tile on chip, reserve each tile's range with one global atomic, place.
-__global__ void __launch_bounds__(kAdvThreads) k_scatter2(KernelArgs a) {
-    if (*a.check != 1) return;
-    __shared__ uint32_t s_cnt[kNbrSide * kNbrSide], s_base[kNbrSide * kNbrSide];
-    const int b = frame1_pair(a, (int64_t)blockIdx.x);
-    const PairPlan pl = a.plan[b];
-    const int W = a.descs[b].width, H = a.descs[b].height;
-    const TileCtx c = frame1_tile(a, pl, b, W, H, (int64_t)blockIdx.x);
-    uint32_t *cur2 = a.cursor + pl.tile_base + pl.ntiles;
-    Record *seg = a.rec + pl.list_base + pl.list_cap;
-    for (int i = threadIdx.x; i < kNbrSide * kNbrSide; i += kAdvThreads) s_cnt[i] = 0u;
-    __syncthreads();
-    constexpr int U = 4;  // records per thread and pass, loaded together
-    auto load = [&](uint32_t k, Record &r) {
-        if (k >= c.it.count) {
-            r.sigma = -1.0f;
-            return;
-        }
-        const float2 *rp = reinterpret_cast<const float2 *>(a.adv + c.adv0 + k);
-        const float2 p0 = rp[0], p1 = rp[1], p2 = rp[2];
-        r.fx = p0.x;
-        r.fy = p0.y;
-        r.ix = __float_as_int(p1.x);
-        r.iy = __float_as_int(p1.y);
-        r.sigma = p2.x;  // negative: advected by another tile
-        r.amp = p2.y;
-    };
-    auto place = [&](uint32_t slot, const Record &r) {
-        if ((int64_t)slot < pl.list_cap) {
-            float2 *o = reinterpret_cast<float2 *>(seg + slot);
-            o[0] = make_float2(r.fx, r.fy);
-            o[1] = make_float2(__int_as_float(r.ix), __int_as_float(r.iy));
-            o[2] = make_float2(r.sigma, r.amp);
-        }
-    };
-    for (uint32_t k0 = threadIdx.x; k0 < c.it.count; k0 += U * kAdvThreads) {
-        Record r[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) load(k0 + u * kAdvThreads, r[u]);
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (r[u].sigma < 0.0f) continue;
-            frame2_tiles(a, pl, c, r[u], W, H, [&](int kk, int32_t tile) {
-                if (kk >= 0) atomicAdd(s_cnt + kk, 1u);
-                else place(atomicAdd(cur2 + tile, 1u), r[u]);
-            });
-        }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < kNbrSide * kNbrSide; i += kAdvThreads) {
-        const uint32_t n = s_cnt[i];
-        const int ty = c.ty + i / kNbrSide - kNbr, tx = c.tx + i % kNbrSide - kNbr;
-        s_base[i] = n ? atomicAdd(cur2 + ty * pl.tiles_x + tx, n) : 0u;
-        s_cnt[i] = 0u;
-    }
-    __syncthreads();
-    for (uint32_t k0 = threadIdx.x; k0 < c.it.count; k0 += U * kAdvThreads) {
-        Record r[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) load(k0 + u * kAdvThreads, r[u]);
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (r[u].sigma < 0.0f) continue;
-            frame2_tiles(a, pl, c, r[u], W, H, [&](int kk, int32_t) {
-                if (kk >= 0) place(s_base[kk] + atomicAdd(s_cnt + kk, 1u), r[u]);
-            });
-        }
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -899,35 +820,22 @@ cudaError_t launch_prep(const KernelArgs &a, cudaStream_t st, cudaEvent_t const 
         mark(4);
         return e;
     }
-    // seeded render: seed + frame-1 bins, tiled advection, frame-2 bins
+    // seeded render: seeding with the frame-1 placement, tiled advection with the frame-2 placement
     const unsigned nt1 = (unsigned)(a.n_tiles / 2);
     const size_t adv_smem = (size_t)adv_window_nodes(a.tile) * sizeof(float2);
     const bool big = a.tile >= 128;  // two row bands per tile, 512 threads each
     ok(big ? cudaFuncSetAttribute(k_advect<512, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adv_smem)
            : cudaFuncSetAttribute(k_advect<256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adv_smem));
     if (e != cudaSuccess) return e;
-    if (a.fixed) {  // frame 1 placed while seeding; the exact rebinning runs only after an overflow
-        if (nb > 0) ok(launch_kernel(k_seed_place, nb, kPrepThreads, 0, st, a));
-        ok(launch_kernel(k_rebin, (unsigned)a.n_pairs, 1024, 0, st, a, 0));
-    } else {
-        if (nb > 0) ok(launch_kernel(k_seed_advect, nb, kPrepThreads, 0, st, a));
-        ok(launch_kernel(k_scan, (unsigned)a.n_pairs, 1024, 0, st, a, 0));
-        if (nb > 0) ok(launch_kernel(k_scatter, nb, kPrepThreads, 0, st, a));
-    }
+    if (nb > 0) ok(launch_kernel(k_seed_place, nb, kPrepThreads, 0, st, a));
+    ok(launch_kernel(k_rebin, (unsigned)a.n_pairs, 1024, 0, st, a, 0));  // returns at once unless a bin overflowed
     if (nt1 > 0) {
         if (big) ok(launch_kernel(k_advect<512, 2>, 2 * nt1, 512, adv_smem, st, a));
         else ok(launch_kernel(k_advect<256, 1>, nt1, 256, adv_smem, st, a));
     }
     mark(2);
-    if (a.fixed) {  // frame 2 placed by k_advect
-        mark(3);
-        ok(launch_kernel(k_rebin, (unsigned)a.n_pairs, 1024, 0, st, a, 1));
-        mark(4);
-        return e;
-    }
-    ok(launch_kernel(k_scan, (unsigned)a.n_pairs, 1024, 0, st, a, 1));
     mark(3);
-    if (nt1 > 0) ok(launch_kernel(k_scatter2, nt1, kAdvThreads, 0, st, a));
+    ok(launch_kernel(k_rebin, (unsigned)a.n_pairs, 1024, 0, st, a, 1));
     mark(4);
     return e;
 }

@@ -148,20 +148,18 @@ def test_launch_count_of_each_binning_mode():
     # rebin check, splat
     assert launches(Renderer(wl, tile=128)) == 6
     assert launches(Renderer(wl, tile=32)) == 6
-    # counting sort (a batch with an empty pair): plan, seed, scan, scatter, advection, scan,
-    # scatter, splat
-    empty = W.batch_512_u8(n_pairs=2)
+    empty = W.batch_512_u8(n_pairs=2)  # an empty pair: one empty chunk writes its work items
     empty.pairs[1].n_particles = 0
-    assert launches(Renderer(empty, tile=128)) == 8
+    assert launches(Renderer(empty, tile=128)) == 6
     # per-particle advection (hiding): plan, seed + advect, scan, scatter, splat
     hidden = W.batch_512_u8(n_pairs=2)
     hidden.hide_prob = np.float32(0.1)
     assert launches(Renderer(hidden, tile=128)) == 5
 
 
-def test_counting_sort_path_of_a_batch_with_an_empty_pair_matches_the_oracle():
-    # an empty pair keeps the counting-sort bins (k_scan, k_scatter, the tiled advection's
-    # marks and k_scatter2): the other pairs must render as the oracle does
+def test_a_batch_with_an_empty_pair_matches_the_oracle():
+    # the empty pair has bins of capacity 0 and one empty seeding chunk, which writes its work
+    # items; its frames hold noise only, the other pairs render as the oracle does
     h = w = 256
     flows = [W.fourier_flow(h, w, h, w, rms=3.0, seed=1500 + b) for b in range(3)]
     pairs = [W.PairSpec(height=h, width=w, n_particles=W.n_particles_for(0.05, h, w) if b != 1 else 0,
