@@ -290,14 +290,12 @@ int synthpix_render_backward(const synthpix_batch_desc *batch, const synthpix_pa
  *   [2] after everything up to the advection: seeding and advection, and
  *       the binning done with them.  Seeded renders of round particles bin
  *       the records into fixed-capacity bins while seeding (frame 1) and
- *       advecting (frame 2) when those bins fit the bin segments (tile
- *       edges of 64 and up, in practice); other seeded renders count,
- *       scan and scatter frame 1 here; renders from given particles or
- *       with per-frame shapes only seed and advect here,
- *   [3] after the scan of the remaining bin counts (nothing with fixed
- *       bins),
- *   [4] after the scatter of the remaining records (with fixed bins: the
- *       exact rebinning of frame 2, which does work only if a bin
+ *       advecting (frame 2); renders from given particles or with
+ *       per-frame shapes only seed and advect here,
+ *   [3] after the scan of the bin counts (renders from given particles or
+ *       with per-frame shapes; nothing for seeded renders),
+ *   [4] after the scatter of the records into the bins (seeded renders:
+ *       the exact rebinning of frame 2, which does work only if a bin
  *       overflowed),
  *   [5] after the splat + epilogue kernel.
  * The paper has no counterpart; it exists for measurement.  Same arguments,
