@@ -183,22 +183,33 @@ __global__ void __launch_bounds__(128) k_adj_advect(KernelArgs a) {
     const synthpix_pair_desc &D = a.descs[b];
     const uint32_t i = (uint32_t)(g - pl.part_base);
     const float4 g1 = a.grad_frames[2 * g], g2 = a.grad_frames[2 * g + 1];
-    const Seeded P = seed_particle(a, D, i, g);
     const Flow F = pair_flow(a, D);
     float *gf = a.grad_flows ? a.grad_flows + D.flow_offset : nullptr;
     const int n = a.n_substeps;
     const float h = a.dt / (float)n;
     const float hh = 0.5f * h, h6 = h / 6.0f;
-    // forward, keeping the start of every substep (n <= NMAX)
+    // the start of every substep (n <= NMAX): kept by the forward advection, or recomputed
     int32_t si[NMAX], sj[NMAX];
     float sfx[NMAX], sfy[NMAX];
-    int32_t jx = P.ix, jy = P.iy;
-    float fx = P.fx, fy = P.fy;
+    if (a.states) {
+        const float4 *sp = a.states + g * n;
 #pragma unroll(NMAX <= 8 ? NMAX : 1)
-    for (int s = 0; s < NMAX; ++s) {
-        if (s < n) {
-            si[s] = jx; sj[s] = jy; sfx[s] = fx; sfy[s] = fy;
-            advect_split(F, h, 1, a.integrator, jx, fx, jy, fy);
+        for (int s = 0; s < NMAX; ++s) {
+            if (s < n) {
+                const float4 q = sp[s];
+                sfx[s] = q.x; sfy[s] = q.y; si[s] = __float_as_int(q.z); sj[s] = __float_as_int(q.w);
+            }
+        }
+    } else {
+        const Seeded P = seed_particle(a, D, i, g);
+        int32_t jx = P.ix, jy = P.iy;
+        float fx = P.fx, fy = P.fy;
+#pragma unroll(NMAX <= 8 ? NMAX : 1)
+        for (int s = 0; s < NMAX; ++s) {
+            if (s < n) {
+                si[s] = jx; sj[s] = jy; sfx[s] = fx; sfy[s] = fy;
+                advect_split(F, h, 1, a.integrator, jx, fx, jy, fy);
+            }
         }
     }
     float lx = g2.x, ly = g2.y;  // dL / d(frame-2 position)

@@ -496,6 +496,7 @@ static int run(Mode mode, const synthpix_batch_desc *batch, const synthpix_pair_
     a.grad_flows = x.grad_flows;
     a.grad_particles = x.grad_particles;
     a.grad_frames = reinterpret_cast<float4 *>(ws + L.gfr);
+    a.states = nullptr;
     a.carry = reinterpret_cast<uint32_t *>(ws + L.carry);
     a.carry_stride = L.carry_stride;
     a.smem_edge = P.tile + 2 * P.max_r;
@@ -506,6 +507,11 @@ static int run(Mode mode, const synthpix_batch_desc *batch, const synthpix_pair_
         if (e != cudaSuccess) return fail(SYNTHPIX_ECUDA, "seeding launch: %s", cudaGetErrorString(e));
     } else if (mode == Mode::Backward) {
         a.warp_scratch = spx::window_max(P.max_d) + 2;  // floats per scratch array of the adjoint splat
+        // the substep starts of the advection go to the bin records' region (no bins in the adjoint)
+        // when they fit there; otherwise the adjoint recomputes them
+        const size_t states = (size_t)L.n_part * (size_t)batch->n_substeps * sizeof(float4);
+        if (states <= (size_t)L.n_list * (P.general ? sizeof(spx::RecordG) : sizeof(spx::Record)))
+            a.states = reinterpret_cast<float4 *>(ws + L.rec);
         e = spx::launch_seed_only(a, st);                // positions of both frames
         if (e == cudaSuccess) e = spx::launch_adjoint(a, st);
         if (e != cudaSuccess) return fail(SYNTHPIX_ECUDA, "adjoint launch: %s", cudaGetErrorString(e));

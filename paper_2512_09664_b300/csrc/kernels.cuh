@@ -58,6 +58,9 @@ struct KernelArgs {
     float *grad_flows;                // NULL or dL/d(flows), accumulated
     float *grad_particles;            // NULL or [n_part][3] dL/d(x0, y0, d)
     float4 *grad_frames;              // [n_part][2]: dL/d(x, y, sigma) of each frame's splat
+    float4 *states;                   // NULL, or [n_part][n_substeps]: the split position (fx, fy, ix, iy) at
+                                      // the start of each substep, written by the per-particle advection for
+                                      // the adjoint (which then does not recompute them)
 };
 
 // The splat's work item t (t = tile_base + frame ntiles + tile).  With fixed

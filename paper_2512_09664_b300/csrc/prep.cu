@@ -239,8 +239,16 @@ __global__ void __launch_bounds__(kPrepThreads, 5) k_seed_advect(KernelArgs a) {
             if (a.out_of_plane)
                 advect_split_z(F, a.flows + c.d.flow_offset + 2LL * c.d.flow_h * c.d.flow_w, a.dt, a.n_substeps,
                                a.integrator, jx, gx, jy, gy, z2);
-            else
+            else if (a.states) {  // each substep's start kept for the adjoint (the same arithmetic)
+                float4 *sp = a.states + g * a.n_substeps;
+                const float h = a.dt / (float)a.n_substeps;
+                for (int s = 0; s < a.n_substeps; ++s) {
+                    sp[s] = make_float4(gx, gy, __int_as_float(jx), __int_as_float(jy));
+                    advect_split(F, h, 1, a.integrator, jx, gx, jy, gy);
+                }
+            } else {
                 advect_split(F, a.dt, a.n_substeps, a.integrator, jx, gx, jy, gy);
+            }
             a.pos1[g] = make_float4(gx, gy, __int_as_float(jx), __int_as_float(jy));
         }
         // window half-extents 1.5 d (x) and 1.5 d_y (y) of each frame; < 0: hidden
