@@ -34,11 +34,13 @@ namespace spx {
 
 // ---------------------------------------------------------------------------
 // k_plan: per-pair prefix sums (CTA 0, 1024 threads); the next CTAs clear
-// the bin counts of a render; the last ones form the FP64 blur taps, 32
-// pairs each (FP64 is slow on this part: spread over SMs, off CTA 0's path)
+// the bin counts of a render; the last ones form the FP64 blur taps, four
+// pairs each, a tap per lane (FP64 is slow on this part: spread over SMs and
+// lanes, off CTA 0's path)
 // ---------------------------------------------------------------------------
 constexpr int kPlanZeroWords = 16384;
-constexpr int kPlanTapPairs = 32;
+constexpr int kTapLanes = 8;                  // lanes per pair of the blur-tap CTAs
+constexpr int kPlanTapPairs = 32 / kTapLanes;  // pairs per blur-tap CTA (one warp each: FP64 spread over SMs)
 
 __global__ void __launch_bounds__(1024) k_plan(const synthpix_pair_desc *__restrict__ descs, int32_t n_pairs,
                                                TileRule rule, int32_t fused, PairPlan *__restrict__ plan,
@@ -52,19 +54,32 @@ __global__ void __launch_bounds__(1024) k_plan(const synthpix_pair_desc *__restr
         for (int64_t k = threadIdx.x; k < n; k += blockDim.x) count[k0 + k] = 0u;
         return;
     }
-    if (blockIdx.x > 0) {  // normalised blur taps w[|k|], k = -R..R (FP64, stored FP32), a pair per thread
-        const int b = ((int)blockIdx.x - 1 - zero_ctas) * kPlanTapPairs + (int)threadIdx.x;
-        if (threadIdx.x >= kPlanTapPairs || b >= n_pairs) return;
-        const float bs = descs[b].blur_sigma;
-        const int32_t R = blur_radius_of(bs);
-        if (R > 0) {
-            double w[kMaxBlurRadius + 1], sum = 0.0;
-            const double sb = (double)bs;
-            for (int k = 0; k <= R; ++k) {
-                w[k] = exp(-(double)(k * k) / (2.0 * sb * sb));
-                sum += k ? 2.0 * w[k] : w[k];
+    if (blockIdx.x > 0) {  // normalised blur taps w[|k|], k = -R..R (FP64, stored FP32)
+        // kPlanTapPairs pairs per CTA, a group of kTapLanes lanes of warp 0 per pair: lane k
+        // evaluates w[k] (R < kTapLanes; larger radii: the group's first lane evaluates them in
+        // turn), every lane of the group sums them in the order k = 0..R
+        if (threadIdx.x >= 32) return;
+        const int q = (int)threadIdx.x / kTapLanes, k = (int)threadIdx.x % kTapLanes;
+        const int b = ((int)blockIdx.x - 1 - zero_ctas) * kPlanTapPairs + q;
+        const int32_t R = b < n_pairs ? blur_radius_of(descs[b].blur_sigma) : 0;
+        const unsigned grp = ((1u << kTapLanes) - 1u) << (q * kTapLanes);
+        if (R == 0) return;  // the whole group
+        const double sb = (double)descs[b].blur_sigma;
+        if (R < kTapLanes) {
+            const double wk = k <= R ? exp(-(double)(k * k) / (2.0 * sb * sb)) : 0.0;
+            double sum = 0.0;
+            for (int j = 0; j <= R; ++j) {
+                const double v = __shfl_sync(grp, wk, q * kTapLanes + j);
+                sum += j ? 2.0 * v : v;
             }
-            for (int k = 0; k <= R; ++k) blur_w[b * kBlurStride + k] = (float)(w[k] / sum);
+            if (k <= R) blur_w[b * kBlurStride + k] = (float)(wk / sum);
+        } else if (k == 0) {
+            double w[kMaxBlurRadius + 1], sum = 0.0;
+            for (int j = 0; j <= R; ++j) {
+                w[j] = exp(-(double)(j * j) / (2.0 * sb * sb));
+                sum += j ? 2.0 * w[j] : w[j];
+            }
+            for (int j = 0; j <= R; ++j) blur_w[b * kBlurStride + j] = (float)(w[j] / sum);
         }
         return;
     }
