@@ -613,8 +613,9 @@ __device__ __forceinline__ void frame2_tiles(const KernelArgs &a, const PairPlan
         }
 }
 
-// NT threads: 256, or 1024 at tile 128 (one CTA per SM with its larger window).
-// NT threads per CTA, NB row bands per tile (blockIdx.x = NB tile + band).
+// NT threads per CTA (256, or 512 at tile 128 with two 64-row bands: two CTAs
+// per SM, the launch bounds keeping 64 registers), NB row bands per tile
+// (blockIdx.x = NB tile + band).
 template <int NT, int NB>
 __global__ void __launch_bounds__(NT, 1024 / NT) k_advect(KernelArgs a) {
     if (*a.check != 1) return;
