@@ -296,7 +296,7 @@ int synthpix_render_backward(const synthpix_batch_desc *batch, const synthpix_pa
  *       with per-frame shapes; nothing for seeded renders),
  *   [4] after the scatter of the records into the bins (seeded renders:
  *       the exact rebinning of frame 2, which does work only if a bin
- *       overflowed),
+ *       overflowed, and is not launched when no pair's bins can overflow),
  *   [5] after the splat + epilogue kernel.
  * The paper has no counterpart; it exists for measurement.  Same arguments,
  * errors and asynchrony as synthpix_render_pairs; no synchronisation.

@@ -45,6 +45,7 @@ struct Plan {
     float max_d;
     int32_t ext;      // per-frame shapes: general shapes, frame-2 variation or hiding
     int32_t general;  // general-shape splat (32-byte records)
+    int32_t rebin;    // some pair's fixed bins could overflow: the rebinning launches are needed
 };
 
 int check_batch(const synthpix_batch_desc *b) {
@@ -250,6 +251,7 @@ int make_plan_any(const synthpix_batch_desc *batch, const synthpix_pair_desc *pa
     P.max_d = 0.0f;
     P.ext = (batch->hide_prob > 0.0f || (batch->flags & SYNTHPIX_FLAG_OUT_OF_PLANE)) ? 1 : 0;
     P.general = 0;
+    P.rebin = 0;
     spx::Layout &L = P.L;
     L.n_part = L.n_tiles = L.n_list = L.n_inter = L.n_chunks = 0;
     for (int32_t b = 0; b < n_pairs; ++b) {
@@ -266,6 +268,7 @@ int make_plan_any(const synthpix_batch_desc *batch, const synthpix_pair_desc *pa
                 g.ntiles = std::max(g.ntiles, h.ntiles);
                 g.list_cap = std::max(g.list_cap, h.list_cap);
             }
+        if (!spx::fixed_exact(pairs[b], t, g.halo)) P.rebin = 1;
         L.n_part += pairs[b].n_particles;
         L.n_tiles += 2LL * g.ntiles;
         L.n_list += 2LL * g.list_cap;
@@ -484,6 +487,7 @@ static int run(Mode mode, const synthpix_batch_desc *batch, const synthpix_pair_
                   ? 1 : 0;
     a.ticket = ticket;
     a.ovf = ticket + 1;
+    a.rebin = P.rebin;
     a.rec_buf_bytes = P.T.rec_buf;
     a.reg_epilogue = P.T.reg_epi;
     a.blur_w = blur_w;

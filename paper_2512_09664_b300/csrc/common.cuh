@@ -72,6 +72,8 @@ __host__ __device__ inline bool pair_general_shape(const synthpix_pair_desc &d) 
     return d.dy_min != 0.0f || d.dy_max != 0.0f || d.rho_min != 0.0f || d.rho_max != 0.0f;
 }
 
+constexpr int64_t kExactBinRecords = 1 << 16;  // see fixed_caps
+
 // Records per bin of the fixed bin layout of seeded renders (each producer
 // places its records directly, without a counting pass).  A bin of an
 // interior tile collects the particles whose centres lie within the tile
@@ -79,9 +81,11 @@ __host__ __device__ inline bool pair_general_shape(const synthpix_pair_desc &d) 
 // expected for uniform positions.  Frame 1 gets E + E/4 + 64 (more than 9
 // standard deviations of the binomial count for E >= 100), frame 2, whose
 // density the flow changes, E + E/2 + 64; both at most N (a bin receives a
-// particle at most once, so a frame of one tile never overflows).  A bin
-// that overflows sets a flag and the frame is binned again exactly
-// (k_rebin).  Integer arithmetic, so host and device agree.
+// particle at most once, so a frame of one tile never overflows), and N for
+// pairs whose N x tiles is at most kExactBinRecords (no overflow, and a
+// render of such pairs alone needs no rebinning launch).  A bin that
+// overflows sets a flag and the frame is binned again exactly (k_rebin).
+// Integer arithmetic, so host and device agree.
 __host__ __device__ inline void fixed_caps(const synthpix_pair_desc &d, int32_t tile, int32_t halo, int64_t &cap1,
                                            int64_t &cap2) {
     const int64_t W = d.width, H = d.height;
@@ -92,13 +96,21 @@ __host__ __device__ inline void fixed_caps(const synthpix_pair_desc &d, int32_t 
     cap1 = e / 2 + 1;
     cap2 = e / 2 + 1;
 #else
-    // a bin receives each particle at most once: N records always fit
+    // a bin receives each particle at most once: N records always fit; small pairs (at most
+    // kExactBinRecords records over all their bins of a frame) take N, so they never overflow
     const int64_t n = (int64_t)d.n_particles;
+    const int64_t ntiles = ((W + tile - 1) / tile) * ((H + tile - 1) / tile);
     cap1 = e + e / 4 + 64;
     cap2 = e + e / 2 + 64;
-    cap1 = cap1 < n ? cap1 : n;
-    cap2 = cap2 < n ? cap2 : n;
+    if (cap1 > n || n * ntiles <= kExactBinRecords) cap1 = n;
+    if (cap2 > n || n * ntiles <= kExactBinRecords) cap2 = n;
 #endif
+}
+// The pair's fixed bins cannot overflow (both capacities are N).
+__host__ __device__ inline bool fixed_exact(const synthpix_pair_desc &d, int32_t tile, int32_t halo) {
+    int64_t cap1, cap2;
+    fixed_caps(d, tile, halo, cap1, cap2);
+    return cap1 == (int64_t)d.n_particles && cap2 == (int64_t)d.n_particles;
 }
 
 __host__ __device__ inline PairGeom pair_geom(const synthpix_pair_desc &d, int tile, bool fused) {

@@ -42,6 +42,7 @@ struct KernelArgs {
                                       // and k_seed_place and k_advect place the records into fixed-capacity
                                       // bins (fixed_caps); 0: k_seed_advect and a counting sort
     uint32_t *ovf;                    // [2]: a fixed bin of frame 1 / frame 2 overflowed (zeroed by k_plan)
+    int32_t rebin;                    // 1: launch k_rebin after each placement (0: no bin can overflow)
     uint32_t *ticket;                 // work-queue counter of the persistent splat
     int32_t smem_edge;                // capacity edge of the on-chip tile (tile + 2 max radius)
     int32_t warp_scratch;             // floats of per-warp window scratch

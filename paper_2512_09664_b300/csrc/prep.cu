@@ -852,14 +852,14 @@ cudaError_t launch_prep(const KernelArgs &a, cudaStream_t st, cudaEvent_t const 
            : cudaFuncSetAttribute(k_advect<256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adv_smem));
     if (e != cudaSuccess) return e;
     if (nb > 0) ok(launch_kernel(k_seed_place, nb, kPrepThreads, 0, st, a));
-    ok(launch_kernel(k_rebin, (unsigned)a.n_pairs, 1024, 0, st, a, 0));  // returns at once unless a bin overflowed
+    if (a.rebin) ok(launch_kernel(k_rebin, (unsigned)a.n_pairs, 1024, 0, st, a, 0));  // at once unless overflowed
     if (nt1 > 0) {
         if (big) ok(launch_kernel(k_advect<512, 2>, 2 * nt1, 512, adv_smem, st, a));
         else ok(launch_kernel(k_advect<256, 1>, nt1, 256, adv_smem, st, a));
     }
     mark(2);
     mark(3);
-    ok(launch_kernel(k_rebin, (unsigned)a.n_pairs, 1024, 0, st, a, 1));
+    if (a.rebin) ok(launch_kernel(k_rebin, (unsigned)a.n_pairs, 1024, 0, st, a, 1));
     mark(4);
     return e;
 }

@@ -65,7 +65,10 @@ def _cap2(p, tile, halo):
     reach = tile + 2 * halo + _window_max(max(p.d_max, p.dy_max))
     sx, sy = min(reach, p.width), min(reach, p.height)
     e = (p.n_particles * sx * sy + p.width * p.height - 1) // (p.width * p.height)
-    return e + e // 2 + 64
+    ntiles = -(-p.width // tile) * -(-p.height // tile)
+    if p.n_particles * ntiles <= 1 << 16:  # small pairs: capacity N, no overflow
+        return p.n_particles
+    return min(e + e // 2 + 64, p.n_particles)
 
 
 @pytest.mark.parametrize("out,tile", [("u8", 128), ("u8", 64), ("f32", 128)])
@@ -94,7 +97,7 @@ def test_converging_flow_overflows_frame2_and_matches_the_oracle():
     # about e^-1, so the tile receives the particles of a 174 px square around it (up to 100 px away)
     c = 2.5 * tile
     flow = W.linear_flow(h, w, h, w, [[-1.0, 0.0], [0.0, -1.0]], (c, c))
-    pair = W.PairSpec(height=h, width=w, n_particles=W.n_particles_for(0.05, h, w), pair_id=7,
+    pair = W.PairSpec(height=h, width=w, n_particles=W.n_particles_for(0.08, h, w), pair_id=7,
                       d_dist=0, d_min=1.0, d_max=3.0, noise_sigma=0.02, blur_sigma=0.7,
                       illum_min=0.8, illum_max=1.0)
     wl = W.Workload(name="converging_256", seed=11, pairs=[pair], flows=[flow], out_dtype="u8", quant_bits=8)
@@ -155,6 +158,8 @@ def test_launch_count_of_each_binning_mode():
     hidden = W.batch_512_u8(n_pairs=2)
     hidden.hide_prob = np.float32(0.1)
     assert launches(Renderer(hidden, tile=128)) == 5
+    # a small pair (N x tiles <= 2^16): bins of capacity N cannot overflow, no rebinning launches
+    assert launches(Renderer(W.single_pair_256(seed=0), tile=64)) == 4
 
 
 def test_a_batch_with_an_empty_pair_matches_the_oracle():
