@@ -408,8 +408,8 @@ __device__ __forceinline__ void splat_coop(const Visit &v, bool valid, const Acc
 //   A. each thread sets up its records' visits (window clipped to the halo
 //      rectangle), takes a slot in its (class, bank) bucket and counts the
 //      visit in the 8 x 8 blocks its window meets;
-//   B. warp 0 scans the bucket counts and decides from the block counts
-//      whether the chunk's adds must be checked for wrapping;
+//   B. warp 0 scans the bucket counts, and warp 1 decides from the block
+//      counts whether the chunk's adds must be checked for wrapping;
 //   C. the visits are written in key order over the staged records (out);
 //   D. warps claim slots of 32 visits, widest class first, and render them
 //      (checked: every visit by a whole warp, with checked adds).
@@ -494,6 +494,7 @@ __device__ __forceinline__ void splat_chunk(const unsigned char *recs, unsigned 
             if (lane >= d) nsl += t;
         }
         if (lane <= kWideClass) sh_slot_end[lane] = nsl;
+    } else if (threadIdx.x < 64) {  // warp 1: the wrap guard's block counts, beside warp 0's scan
         const bool ck = blocks_checked();
         if (lane == 0) sh_checked = ck ? 1 : 0;
     }
@@ -917,12 +918,21 @@ __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float sn, f
     n1 = -r * s;
 }
 
-// Quantised code clamp(rint(v M), 0, M): v clamped to [0, 1] first, then the
-// product rounded half to even by one FMA with 1.5 2^23 (exact for products
-// below 2^22; M <= 65535).  NaN gives 0.
-__device__ __forceinline__ uint32_t quant_code(float v, float M) {
-    const float t = fmaf(fminf(fmaxf(v, 0.0f), 1.0f), M, kMagic);
-    return (uint32_t)(__float_as_int(t) - kMagicBits);
+// Quantised code clamp(rint(v M), 0, M): v saturated to [0, 1] first (NaN
+// gives 0), then the product rounded half to even by one FMA with 1.5 2^23
+// (exact for products below 2^22; M <= 65535).  quant_raw returns the bit
+// pattern of that sum, 0x4B400000 + code: its low 16 bits are the code.
+__device__ __forceinline__ uint32_t quant_raw(float v, float M) {
+    return __float_as_uint(fmaf(__saturatef(v), M, kMagic));
+}
+__device__ __forceinline__ uint32_t quant_code(float v, float M) { return quant_raw(v, M) - (uint32_t)kMagicBits; }
+
+// Four codes packed from their raw patterns: bytes (8-bit codes) or 16-bit halves.
+__device__ __forceinline__ uint32_t pack_u8(uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3) {
+    return __byte_perm(__byte_perm(r0, r1, 0x0040), __byte_perm(r2, r3, 0x0040), 0x5410);
+}
+__device__ __forceinline__ uint2 pack_u16(uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3) {
+    return make_uint2(__byte_perm(r0, r1, 0x5410), __byte_perm(r2, r3, 0x5410));
 }
 
 // Packed FP32 pairs (two lanes of one 64-bit register; each lane rounds as
@@ -1022,16 +1032,14 @@ __device__ __forceinline__ void store_group(T *o, float *v, int nvalid, float M)
             // Q = clamp(rint(B M), 0, M)
             uint32_t q[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) q[j] = quant_code(v[j], M);
+            for (int j = 0; j < 4; ++j) q[j] = quant_raw(v[j], M);
             if (nvalid == 4 && (reinterpret_cast<uintptr_t>(o) % (4 * sizeof(T))) == 0) {
-                if (sizeof(T) == 1)
-                    *reinterpret_cast<uint32_t *>(o) = q[0] | (q[1] << 8) | (q[2] << 16) | (q[3] << 24);
-                else
-                    *reinterpret_cast<uint2 *>(o) = make_uint2(q[0] | (q[1] << 16), q[2] | (q[3] << 16));
+                if (sizeof(T) == 1) *reinterpret_cast<uint32_t *>(o) = pack_u8(q[0], q[1], q[2], q[3]);
+                else *reinterpret_cast<uint2 *>(o) = pack_u16(q[0], q[1], q[2], q[3]);
             } else {
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
-                    if (j < nvalid) o[j] = (T)q[j];
+                    if (j < nvalid) o[j] = (T)(q[j] - (uint32_t)kMagicBits);
             }
             return;
         }
@@ -1056,9 +1064,9 @@ __device__ __forceinline__ void store_quad(T *o, const float *v, float M) {
     if constexpr (IsCode<T>::value) {
         uint32_t q[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) q[j] = quant_code(v[j], M);
-        if (sizeof(T) == 1) *reinterpret_cast<uint32_t *>(o) = q[0] | (q[1] << 8) | (q[2] << 16) | (q[3] << 24);
-        else *reinterpret_cast<uint2 *>(o) = make_uint2(q[0] | (q[1] << 16), q[2] | (q[3] << 16));
+        for (int j = 0; j < 4; ++j) q[j] = quant_raw(v[j], M);
+        if (sizeof(T) == 1) *reinterpret_cast<uint32_t *>(o) = pack_u8(q[0], q[1], q[2], q[3]);
+        else *reinterpret_cast<uint2 *>(o) = pack_u16(q[0], q[1], q[2], q[3]);
     } else {
         Out<T>::store4(o, v);
     }
@@ -1727,21 +1735,25 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_splat(KernelArgs a) {
     s.BP = (a.tile + 3) & ~3;
     unsigned char *bufs = smem + L.bufs;
     const uint32_t cap = (uint32_t)rec_cap(a.rec_buf_bytes, RS);
-    for (int k = threadIdx.x; k < words; k += blockDim.x) s.acc[k] = 0u;
+    for (int k = threadIdx.x; k < (words >> 2); k += blockDim.x)
+        reinterpret_cast<uint4 *>(s.acc)[k] = make_uint4(0u, 0u, 0u, 0u);
     // work queue: the current item, the next one (staged while the current
     // one renders) and the ticket of the one after (its item read during
-    // the current item); tickets only grow, so a CTA never drops a valid one
+    // the current item); tickets only grow, so a CTA never drops a valid one.
+    // The first two tickets of CTA b are b and grid + b; the counter hands
+    // out the rest from 2 grid (one atomic per CTA at the start, not three
+    // on one address).
     uint32_t t_pending = 0;
     if (threadIdx.x == 0) {
         sh_wrap = 0;
         for (int q = 0; q < 2; ++q) {
-            const uint32_t t = atomicAdd(a.ticket, 1u);
+            const uint32_t t = blockIdx.x + (uint32_t)q * gridDim.x;
             ItemInfo it;
             if ((int64_t)t < a.n_tiles) it = work_item(a, t);
             else it.pair = -1;
             s_item[q] = it;
         }
-        t_pending = atomicAdd(a.ticket, 1u);
+        t_pending = 2u * gridDim.x + atomicAdd(a.ticket, 1u);
     }
     __syncthreads();
     if (s_item[0].pair < 0) return;
@@ -1767,7 +1779,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_splat(KernelArgs a) {
         }
         cp_async_commit();
         const uint32_t t2 = t_pending;
-        if (threadIdx.x == 0) t_pending = atomicAdd(a.ticket, 1u);  // returns while this item renders
+        if (threadIdx.x == 0) t_pending = 2u * gridDim.x + atomicAdd(a.ticket, 1u);  // returns while this item renders
         ItemInfo after;
         process_item<T, NT, RS>(a, it, bufs + cur * a.rec_buf_bytes, cap, s, t2, after);
         if (threadIdx.x == 0) s_item[cur] = after;
