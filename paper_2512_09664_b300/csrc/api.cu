@@ -31,7 +31,7 @@ bool finite(float v) { return std::isfinite(v); }
 // depend on them).
 struct Tuning {
     spx::TileRule rule;  // tile edge per frame size class
-    int32_t rec_buf;     // bytes of each staged-records buffer of the splat
+    int32_t rec_buf;     // bytes of the splat's staged-record region
     int32_t reg_epi;     // 1: full 128 x 128 tiles finish with the register blur
 };
 
@@ -124,7 +124,7 @@ int check_pair(const synthpix_pair_desc &d, int b) {
 // borders, fewer work items).
 constexpr spx::TileRule kDefaultRule = {{32, 64, 128, 128}};
 constexpr int kTileCandidates[4] = {16, 32, 64, 128};
-constexpr int kRecBufCandidates[3] = {8192, 10240, spx::kRecBufBytesLarge};
+constexpr int kRecBufCandidates[3] = {2 * 8192 - 2 * spx::kStageHeader, spx::kRecBufBytes, spx::kRecBufBytesLarge};
 
 spx::TileRule uniform_rule(int t) { return spx::TileRule{{t, t, t, t}}; }
 
@@ -319,7 +319,7 @@ int make_plan_any(const synthpix_batch_desc *batch, const synthpix_pair_desc *pa
     }
     if (P.T.rec_buf == 0) P.T.rec_buf = spx::rec_buf_bytes_for(P.tile);
     // at least one record of either size; at most what the splat's per-thread slots cover
-    if (P.T.rec_buf < spx::kStageHeader + 32 + (int)sizeof(spx::RecordG) ||
+    if (P.T.rec_buf < 32 + (int)sizeof(spx::RecordG) ||
         P.T.rec_buf > spx::rec_buf_bytes_for(P.tile) || (P.T.rec_buf & 15))
         return fail(SYNTHPIX_EUNSUPPORTED, "%d-byte record buffers do not fit tile edge %d", P.T.rec_buf, P.tile);
     L.gfr = take((size_t)L.n_part * 2 * sizeof(float4));
@@ -730,8 +730,8 @@ int synthpix_tuning_set(const synthpix_batch_desc *batch, const synthpix_pair_de
             return fail(SYNTHPIX_EINVAL, "tile[%d] = %d is not 16, 32, 64 or 128", k, e);
         T.rule.edge[k] = e;
     }
-    // the staged-buffer bytes that hold records_per_stage 24-byte records
-    T.rec_buf = (spx::kStageHeader + 32 + 24 * t->records_per_stage + 15) & ~15;
+    // the staged-record region that holds records_per_stage 24-byte records
+    T.rec_buf = (32 + 24 * t->records_per_stage + 15) & ~15;
     T.reg_epi = t->register_epilogue;
     Plan P;
     rc = make_plan_tuned(batch, pairs, n_pairs, T, P);  // validates the buffer against the largest edge

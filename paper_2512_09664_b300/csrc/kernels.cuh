@@ -47,7 +47,7 @@ struct KernelArgs {
     int32_t smem_edge;                // capacity edge of the on-chip tile (tile + 2 max radius)
     int32_t warp_scratch;             // floats of per-warp window scratch
     const float *blur_w;              // [n_pairs][kBlurStride] normalised taps w[|k|]
-    int32_t rec_buf_bytes;            // bytes of each staged-records buffer (at most rec_buf_bytes_for(tile))
+    int32_t rec_buf_bytes;            // bytes of the staged-record region (at most rec_buf_bytes_for(tile))
     int32_t reg_epilogue;             // 1: full 128 x 128 tiles finish with the register blur
     int32_t inter_dtype;              // SYNTHPIX_F32: fused; F16 / BF16: intermediate frames
     void *inter;                      // 16-bit intermediate frames (non-fused path)
@@ -100,12 +100,15 @@ constexpr int kSplatMaxThreads = 1024;  // k_splat at tile 128 (one CTA per SM)
 constexpr int kStageDesc = (int)sizeof(synthpix_pair_desc);  // staged header: descriptor (160),
 constexpr int kStagePlan = kStageDesc + (int)sizeof(PairPlan);  // plan (64),
 constexpr int kStageHeader = kStagePlan + 128;                  // blur taps (128)
-constexpr int kRecBufBytes = 10240;     // each staged-records buffer of k_splat (tiles up to 64)
-constexpr int kRecBufBytesLarge = 13312;  // the same at tile 128 (two CTAs per SM: 2 chunks for most items)
-// records of rec_bytes bytes per staged chunk of a buffer
-__host__ __device__ constexpr int rec_cap(int buf_bytes, int rec_bytes = 24) {
-    return (buf_bytes - kStageHeader - 32) / rec_bytes;
-}
+// k_splat stages two headers (the current and the next item's) and one
+// region of binned records: the next item's records are copied in once the
+// current item's are splatted, behind its finishing steps.
+constexpr int kRecBufBytes = 2 * 10240 - 2 * kStageHeader;       // the record region (tiles up to 64)
+constexpr int kRecBufBytesLarge = 2 * 13312 - 2 * kStageHeader;  // the same at tile 128 (two CTAs per SM; one
+                                                                  // chunk for most items of 512 x 512 frames)
+constexpr int kSplatRpt = 3;  // records per thread of one chunk of round particles (splat_chunk)
+// records of rec_bytes bytes per staged chunk of a record region
+__host__ __device__ constexpr int rec_cap(int buf_bytes, int rec_bytes = 24) { return (buf_bytes - 32) / rec_bytes; }
 // threads of a k_splat CTA at a tile edge: 512 at tile 128 (two CTAs per
 // SM), else 256 (several CTAs per SM hide each other's barriers)
 __host__ __device__ constexpr int splat_threads(int tile) { return tile >= 128 ? 512 : 256; }

@@ -5,9 +5,11 @@
 // blur) and quantisation.
 //
 // k_splat is persistent: each CTA takes (pair, frame, tile) work items from a
-// ticket counter (atomicAdd, no waiting on other CTAs) and, while it renders
-// one item, stages the next item's descriptor, plan, blur taps and binned
-// particle records into shared memory with cp.async.  An item renders the
+// ticket counter (atomicAdd, no waiting on other CTAs) and stages the next
+// item's descriptor, plan and blur taps while it renders one item, and the
+// next item's binned particle records while it finishes one (they take the
+// record region the splatted records leave), into shared memory with
+// cp.async.  An item renders the
 // tile plus the blur halo into an on-chip fixed-point accumulator, finishes
 // it, and writes every output pixel of the tile once.
 //
@@ -417,7 +419,7 @@ template <int NT>
 __device__ __forceinline__ void splat_chunk(const unsigned char *recs, unsigned char *out, uint32_t n, const Geo &g,
                                             float scale, const Acc &acc, float *scr,
                                             int wq, uint32_t tab) {
-    constexpr int RPT = (rec_cap(NT >= 512 ? kRecBufBytesLarge : kRecBufBytes) + NT - 1) / NT;
+    constexpr int RPT = kSplatRpt;  // n <= RPT NT (k_splat caps its chunks)
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
     Visit v[RPT];
@@ -1609,13 +1611,16 @@ __device__ __forceinline__ __nv_bfloat16 to_inter<__nv_bfloat16>(float v) { retu
 // store S in 16 bits to the intermediate frames; k_finish does the rest.
 // Thread 0 reads the work item of ticket t2 into `after` once the splat is
 // done (the ticket was taken an item earlier), so the read's latency hides
-// behind the finishing steps.
+// behind the finishing steps.  hdr: the item's staged header; rec: the
+// record region, which receives the first chunk of the next item nx as soon
+// as the item's own records are splatted (the copy runs behind the finishing).
 template <typename T, int NT, int RS>
-__device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo &it, unsigned char *buf,
-                                             uint32_t cap, const Smem &s, uint32_t t2, ItemInfo &after) {
-    const synthpix_pair_desc &D = *reinterpret_cast<const synthpix_pair_desc *>(buf);
-    const PairPlan &pl = *reinterpret_cast<const PairPlan *>(buf + kStageDesc);
-    const float *wtab = reinterpret_cast<const float *>(buf + kStagePlan);
+__device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo &it, const ItemInfo &nx,
+                                             const unsigned char *hdr, unsigned char *rec, uint32_t cap,
+                                             const Smem &s, uint32_t t2, ItemInfo &after) {
+    const synthpix_pair_desc &D = *reinterpret_cast<const synthpix_pair_desc *>(hdr);
+    const PairPlan &pl = *reinterpret_cast<const PairPlan *>(hdr + kStageDesc);
+    const float *wtab = reinterpret_cast<const float *>(hdr + kStagePlan);
     const Geo g = make_geo(D, pl, pl.tile, it.tile, pl.halo);
     const bool fused = a.inter_dtype == SYNTHPIX_F32;
     const float imax = D.i_max > 0.0f ? D.i_max : 1.0f;
@@ -1630,20 +1635,23 @@ __device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo
     while (done < it.count) {
         const uint32_t n = min(it.count - done, cap);
         if constexpr (RS == (int)sizeof(RecordG))
-            splat_chunk_general(buf + kStageHeader + record_lead<RS>(it.rec0 + done), n, g, scale, acc, s.phi);
+            splat_chunk_general(rec + record_lead<RS>(it.rec0 + done), n, g, scale, acc, s.phi);
         else
-            splat_chunk<NT>(buf + kStageHeader + record_lead<RS>(it.rec0 + done), buf + kStageHeader, n, g, scale,
-                            acc, s.scr + (threadIdx.x >> 5) * a.warp_scratch, a.warp_scratch >> 2, s.phi);
+            splat_chunk<NT>(rec + record_lead<RS>(it.rec0 + done), rec, n, g, scale, acc,
+                            s.scr + (threadIdx.x >> 5) * a.warp_scratch, a.warp_scratch >> 2, s.phi);
         done += n;
         __syncthreads();
         if (done < it.count) {  // more records: stage the next chunk
-            stage_records<RS>(a, it.rec0 + done, min(it.count - done, cap), buf + kStageHeader);
+            stage_records<RS>(a, it.rec0 + done, min(it.count - done, cap), rec);
             cp_async_commit();
             cp_async_wait_all();
             __syncthreads();
         }
     }
     if (it.count == 0) __syncthreads();  // illumination factors
+    // every warp is past the last chunk: the record region takes the next item's first chunk
+    if (nx.pair >= 0) stage_records<RS>(a, nx.rec0, min(nx.count, cap), rec);
+    cp_async_commit();
     // block counts of the next item start from zero (its first count comes after a barrier)
     for (int k = threadIdx.x; k < kBlkPitch * kBlkSide; k += blockDim.x) sh_blk[k] = 0u;
     if (threadIdx.x == 0) {
@@ -1686,9 +1694,9 @@ struct SmemLayout {
 
 // The accumulator words, which hold the finishing buffer A after the first
 // finishing pass (+ padding read by the last row's blur loads); illumination
-// factors; per-warp window scratch; the normal-tail table; two
-// staged-record buffers; the horizontal-blur buffer Bh of the blur for radii
-// above 6 (the others blur rows in place).
+// factors; per-warp window scratch; the normal-tail table; two staged
+// headers and the staged-record region; the horizontal-blur buffer Bh of the
+// blur for radii above 6 (the others blur rows in place).
 __host__ __device__ inline SmemLayout smem_layout(int E, int tile, int warp_scratch, int rec_buf_bytes) {
     SmemLayout L;
     const int BP = (tile + 3) & ~3;
@@ -1704,7 +1712,7 @@ __host__ __device__ inline SmemLayout smem_layout(int E, int tile, int warp_scra
     L.sy2 = take((size_t)E * 4);
     L.scr = take((size_t)(splat_threads(tile) / 32) * warp_scratch * 4);
     L.phi = take((size_t)(kPhiDegree + 1) * kPhiPieces * 4);
-    L.bufs = take(2 * (size_t)rec_buf_bytes);
+    L.bufs = take(2 * (size_t)kStageHeader + (size_t)rec_buf_bytes);  // two headers, one record region
     const bool need_bh = (E - tile) / 2 > 6;  // only the blur of radii above 6 uses Bh
     L.Bh = need_bh ? take((size_t)E * BP * 4) : L.acc;
     L.total = o;
@@ -1733,8 +1741,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_splat(KernelArgs a) {
     for (int k = threadIdx.x; k < kBuckets; k += blockDim.x) sh_cnt[k] = 0;
     for (int k = threadIdx.x; k < kBlkPitch * kBlkSide; k += blockDim.x) sh_blk[k] = 0;
     s.BP = (a.tile + 3) & ~3;
-    unsigned char *bufs = smem + L.bufs;
-    const uint32_t cap = (uint32_t)rec_cap(a.rec_buf_bytes, RS);
+    unsigned char *bufs = smem + L.bufs;  // headers [0, 2 kStageHeader), then the record region
+    unsigned char *rec = bufs + 2 * kStageHeader;
+    const uint32_t cap = (uint32_t)(RS == (int)sizeof(RecordG) ? rec_cap(a.rec_buf_bytes, RS)
+                                                               : min(rec_cap(a.rec_buf_bytes, RS), kSplatRpt * NT));
     for (int k = threadIdx.x; k < (words >> 2); k += blockDim.x)
         reinterpret_cast<uint4 *>(s.acc)[k] = make_uint4(0u, 0u, 0u, 0u);
     // work queue: the current item, the next one (staged while the current
@@ -1758,30 +1768,26 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_splat(KernelArgs a) {
     __syncthreads();
     if (s_item[0].pair < 0) return;
     stage_header(a, s_item[0].pair, bufs);
-    stage_records<RS>(a, s_item[0].rec0, min(s_item[0].count, cap), bufs + kStageHeader);
+    stage_records<RS>(a, s_item[0].rec0, min(s_item[0].count, cap), rec);
     cp_async_commit();
     int cur = 0;
     for (;;) {
         const ItemInfo it = s_item[cur];
         const ItemInfo nx = s_item[cur ^ 1];
         cp_async_wait_all();
-        __syncthreads();  // staged data of `it` visible; the other buffer is free; the wrap flag is read
+        __syncthreads();  // staged header and records of `it` visible; the other header slot is free; the wrap flag is read
         if (it.pair < 0) break;
         // the splat's first add comes after a barrier inside splat_chunk
         if (threadIdx.x == 0) {
             sh_wrap = 0;
             sh_carry_clean = 0;
         }
-        unsigned char *bnext = bufs + (cur ^ 1) * a.rec_buf_bytes;
-        if (nx.pair >= 0) {
-            stage_header(a, nx.pair, bnext);
-            stage_records<RS>(a, nx.rec0, min(nx.count, cap), bnext + kStageHeader);
-        }
+        if (nx.pair >= 0) stage_header(a, nx.pair, bufs + (cur ^ 1) * kStageHeader);  // its records: after the splat
         cp_async_commit();
         const uint32_t t2 = t_pending;
         if (threadIdx.x == 0) t_pending = 2u * gridDim.x + atomicAdd(a.ticket, 1u);  // returns while this item renders
         ItemInfo after;
-        process_item<T, NT, RS>(a, it, bufs + cur * a.rec_buf_bytes, cap, s, t2, after);
+        process_item<T, NT, RS>(a, it, nx, bufs + cur * kStageHeader, rec, cap, s, t2, after);
         if (threadIdx.x == 0) s_item[cur] = after;
         cur ^= 1;
         __syncthreads();

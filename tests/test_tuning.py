@@ -77,19 +77,20 @@ def test_tile0_workspace_covers_every_uniform_edge():
 
 
 def test_cached_record_buffers_fit_a_batch_of_smaller_edges():
-    # records per stage tuned with 128-pixel tiles (13 KB buffers) for a batch of two
-    # classes; a batch holding only the class cached with edge 32 (10 KB at most)
-    # resolves the same entry with its buffers clamped, not rejected
+    # records per stage tuned with 128-pixel tiles (a 25 KB record region, 1078
+    # records) for a batch of two classes; a batch holding only the class cached
+    # with edge 32 (19 KB at most, 822 records) resolves the same entry with its
+    # record region clamped, not rejected
     wl = W.uneven_batch(n_pairs=12, sizes=(128, 512))
     pk = B.pack(wl)
     c_small, c_big = B.size_class(128, 128), B.size_class(512, 512)
     tile = [0, 0, 0, 0]
     tile[c_small], tile[c_big] = 32, 128
-    assert _set(pk, tile, 538, 1) == B.OK
+    assert _set(pk, tile, 1000, 1) == B.OK
     big = _lookup(pk)
-    assert big["tile"][c_big] == 128 and big["records_per_stage"] == 538
+    assert big["tile"][c_big] == 128 and big["records_per_stage"] == 1000
     small = B.pack(wl.subset([b for b, p in enumerate(wl.pairs) if p.height == 128][:1]))
     got = _lookup(small)
-    assert got["tile"][c_small] == 32 and 0 < got["records_per_stage"] < 538
+    assert got["tile"][c_small] == 32 and 0 < got["records_per_stage"] < 1000
     assert B.workspace_bytes(small) > 0
 
