@@ -140,6 +140,44 @@ static __shared__ uint32_t sh_blk[kBlkPitch * kBlkSide];
 static __shared__ int sh_checked;                         // the chunk takes the checked path
 static __shared__ int sh_carry_clean;                     // the item's carry words are zero
 static __shared__ int sh_wrap;                            // a checked add wrapped a word in this item
+// The next work item's raw fields, copied in by cp.async while the current
+// item renders: ItemInfo (24 bytes), the bin's counter, the overflow flags.
+static __shared__ __align__(16) uint32_t sh_raw[10];
+static __shared__ uint32_t sh_tk;  // its ticket
+
+__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gsrc) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem_dst, const void *gsrc) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+// Thread 0: copy the fields of work item t into sh_raw (nothing past the queue).
+__device__ __forceinline__ void fetch_item(const KernelArgs &a, uint32_t t) {
+    sh_tk = t;
+    if ((int64_t)t >= a.n_tiles) return;
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(a.items + t);
+    for (int k = 0; k < 3; ++k) cp_async8(sh_raw + 2 * k, src + 2 * k);
+    if (a.tiled) {
+        cp_async4(sh_raw + 6, a.count + t);
+        cp_async4(sh_raw + 7, a.ovf);
+        cp_async4(sh_raw + 8, a.ovf + 1);
+    }
+    cp_async_commit();
+}
+// Thread 0, once its copies are complete: the fetched work item (work_item's rule).
+__device__ __forceinline__ ItemInfo fetched_item(const KernelArgs &a) {
+    const uint32_t t = sh_tk;
+    ItemInfo it;
+    if ((int64_t)t >= a.n_tiles) {
+        it.pair = -1;
+        return it;
+    }
+    it = *reinterpret_cast<const ItemInfo *>(sh_raw);
+    if (a.tiled && (it.frame ? sh_raw[8] : sh_raw[7]) == 0u) it.count = min(it.count, sh_raw[6]);
+    return it;
+}
 
 // Count a visit whose clipped window is [j0, j1] x [i0, i1] (frame pixels)
 // in the blocks it meets.
@@ -415,10 +453,12 @@ __device__ __forceinline__ void splat_coop(const Visit &v, bool valid, const Acc
 //   C. the visits are written in key order over the staged records (out);
 //   D. warps claim slots of 32 visits, widest class first, and render them
 //      (checked: every visit by a whole warp, with checked adds).
+// fetch_t: thread 0 starts the copy of work item fetch_t (fetch_item) after
+// the first barrier (~0u: none).
 template <int NT>
 __device__ __forceinline__ void splat_chunk(const unsigned char *recs, unsigned char *out, uint32_t n, const Geo &g,
                                             float scale, const Acc &acc, float *scr,
-                                            int wq, uint32_t tab) {
+                                            int wq, uint32_t tab, const KernelArgs &a, uint32_t fetch_t) {
     constexpr int RPT = kSplatRpt;  // n <= RPT NT (k_splat caps its chunks)
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
@@ -458,6 +498,7 @@ __device__ __forceinline__ void splat_chunk(const unsigned char *recs, unsigned 
         }
     }
     __syncthreads();
+    if (threadIdx.x == 0 && fetch_t != ~0u) fetch_item(a, fetch_t);
     if (threadIdx.x < 32) {
         constexpr int PER = kBuckets / 32;
         uint32_t c[PER], sum = 0;
@@ -846,7 +887,8 @@ __device__ __forceinline__ void general_window(const RecordG &r, const Geo &g, i
 //   B. warp 0 decides whether the chunk's adds must be checked for wrapping;
 //   C. warps take records from a shared counter, a warp per record.
 __device__ __forceinline__ void splat_chunk_general(const unsigned char *recs, uint32_t n, const Geo &g, float scale,
-                                                    const Acc &acc, uint32_t tab) {
+                                                    const Acc &acc, uint32_t tab, const KernelArgs &a,
+                                                    uint32_t fetch_t) {
     const RecordG *R = reinterpret_cast<const RecordG *>(recs);
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -857,6 +899,7 @@ __device__ __forceinline__ void splat_chunk_general(const unsigned char *recs, u
         count_blocks(g, j0, j1, i0, i1);
     }
     __syncthreads();
+    if (threadIdx.x == 0 && fetch_t != ~0u) fetch_item(a, fetch_t);
     if (threadIdx.x < 32) {
         const bool ck = blocks_checked();
         if (lane == 0) {
@@ -910,10 +953,12 @@ __device__ __forceinline__ float neg2_log_uo24(uint32_t w) {
 
 // Box-Muller pair from two Philox words, times the noise sigma sn:
 // r = sqrt(-2 ln u), theta = 2 pi v, evaluated as -(sn r) (cos, sin)(theta - pi)
-// so the fast sine and cosine work on [-pi, pi).
+// so the fast sine and cosine work on [-pi, pi).  sqrt(x) = x rsqrt(x), with
+// x raised to at least 1e-30 inside the rsqrt so that x = 0 (u = 1) gives 0
+// (the smallest positive x, -2 ln(1 - 2^-24), is far above it).
 __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float sn, float &n0, float &n1) {
     const float x = neg2_log_uo24(wa);
-    const float r = sn * (x > 0.0f ? x * rsqrtf(x) : 0.0f);
+    const float r = sn * (x * rsqrtf(fmaxf(x, 1e-30f)));
     float s, c;
     __sincosf(6.28318530717958647692f * (u24f(wb) - 0.5f), &s, &c);
     n0 = -r * c;
@@ -1609,15 +1654,16 @@ __device__ __forceinline__ __nv_bfloat16 to_inter<__nv_bfloat16>(float v) { retu
 // One work item of k_splat.  Fused (inter_dtype F32): splat the tile plus
 // its blur halo and finish it on chip.  Otherwise splat the tile alone and
 // store S in 16 bits to the intermediate frames; k_finish does the rest.
-// Thread 0 reads the work item of ticket t2 into `after` once the splat is
-// done (the ticket was taken an item earlier), so the read's latency hides
-// behind the finishing steps.  hdr: the item's staged header; rec: the
-// record region, which receives the first chunk of the next item nx as soon
-// as the item's own records are splatted (the copy runs behind the finishing).
+// The next work item is ticket tk (taken as the previous item ended): thread
+// 0 copies its fields in while the first chunk renders (fetch_item) and
+// publishes it in *next at the last chunk's barrier.  hdr: the item's staged
+// header; hdr_next: the next item's header slot; rec: the record region,
+// which receives the next item's header and first chunk as soon as the
+// item's own records are splatted (the copies run behind the finishing).
 template <typename T, int NT, int RS>
-__device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo &it, const ItemInfo &nx,
-                                             const unsigned char *hdr, unsigned char *rec, uint32_t cap,
-                                             const Smem &s, uint32_t t2, ItemInfo &after) {
+__device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo &it, uint32_t tk,
+                                             const unsigned char *hdr, unsigned char *hdr_next, unsigned char *rec,
+                                             uint32_t cap, const Smem &s, ItemInfo *next) {
     const synthpix_pair_desc &D = *reinterpret_cast<const synthpix_pair_desc *>(hdr);
     const PairPlan &pl = *reinterpret_cast<const PairPlan *>(hdr + kStageDesc);
     const float *wtab = reinterpret_cast<const float *>(hdr + kStagePlan);
@@ -1631,15 +1677,21 @@ __device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo
     // splat, chunk by chunk of staged records
     const float scale = kFixedScale / imax;
     const Acc acc{sh_addr(s.acc), s.carry, g.AP};
+    if (it.count == 0 && threadIdx.x == 0) fetch_item(a, tk);  // no chunk to start the copy in
     uint32_t done = 0;
     while (done < it.count) {
         const uint32_t n = min(it.count - done, cap);
+        const uint32_t ft = done == 0 ? tk : ~0u;
         if constexpr (RS == (int)sizeof(RecordG))
-            splat_chunk_general(rec + record_lead<RS>(it.rec0 + done), n, g, scale, acc, s.phi);
+            splat_chunk_general(rec + record_lead<RS>(it.rec0 + done), n, g, scale, acc, s.phi, a, ft);
         else
             splat_chunk<NT>(rec + record_lead<RS>(it.rec0 + done), rec, n, g, scale, acc,
-                            s.scr + (threadIdx.x >> 5) * a.warp_scratch, a.warp_scratch >> 2, s.phi);
+                            s.scr + (threadIdx.x >> 5) * a.warp_scratch, a.warp_scratch >> 2, s.phi, a, ft);
         done += n;
+        if (done >= it.count && threadIdx.x == 0) {
+            cp_async_wait_all();  // the next item's fields (copied while this item rendered)
+            *next = fetched_item(a);
+        }
         __syncthreads();
         if (done < it.count) {  // more records: stage the next chunk
             stage_records<RS>(a, it.rec0 + done, min(it.count - done, cap), rec);
@@ -1648,16 +1700,22 @@ __device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo
             __syncthreads();
         }
     }
-    if (it.count == 0) __syncthreads();  // illumination factors
-    // every warp is past the last chunk: the record region takes the next item's first chunk
-    if (nx.pair >= 0) stage_records<RS>(a, nx.rec0, min(nx.count, cap), rec);
+    if (it.count == 0) {  // no records: the barrier also shows the illumination factors
+        if (threadIdx.x == 0) {
+            cp_async_wait_all();
+            *next = fetched_item(a);
+        }
+        __syncthreads();
+    }
+    // every warp is past the last chunk: the next item's header and first chunk are staged
+    const ItemInfo nx = *next;
+    if (nx.pair >= 0) {
+        stage_header(a, nx.pair, hdr_next);
+        stage_records<RS>(a, nx.rec0, min(nx.count, cap), rec);
+    }
     cp_async_commit();
     // block counts of the next item start from zero (its first count comes after a barrier)
     for (int k = threadIdx.x; k < kBlkPitch * kBlkSide; k += blockDim.x) sh_blk[k] = 0u;
-    if (threadIdx.x == 0) {
-        if ((int64_t)t2 < a.n_tiles) after = work_item(a, t2);
-        else after.pair = -1;
-    }
 
     const bool wrapped = sh_wrap != 0;
     if (wrapped) wrapped_to_float(s, g);
@@ -1747,23 +1805,20 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_splat(KernelArgs a) {
                                                                : min(rec_cap(a.rec_buf_bytes, RS), kSplatRpt * NT));
     for (int k = threadIdx.x; k < (words >> 2); k += blockDim.x)
         reinterpret_cast<uint4 *>(s.acc)[k] = make_uint4(0u, 0u, 0u, 0u);
-    // work queue: the current item, the next one (staged while the current
-    // one renders) and the ticket of the one after (its item read during
-    // the current item); tickets only grow, so a CTA never drops a valid one.
-    // The first two tickets of CTA b are b and grid + b; the counter hands
-    // out the rest from 2 grid (one atomic per CTA at the start, not three
-    // on one address).
-    uint32_t t_pending = 0;
+    // work queue: the current item and the ticket tk of the next one, whose
+    // fields are copied in while the current item renders (process_item).  A
+    // CTA holds one ticket beyond the item it works on, so when the queue
+    // runs dry the CTAs stop within about one item of each other.  Tickets
+    // only grow, so a CTA never drops a valid one.  The first two tickets of
+    // CTA b are b and grid + b; the counter hands out the rest from 2 grid,
+    // each taken as an item ends (it has the next item's set-up to return).
+    uint32_t tk = gridDim.x + blockIdx.x;
     if (threadIdx.x == 0) {
         sh_wrap = 0;
-        for (int q = 0; q < 2; ++q) {
-            const uint32_t t = blockIdx.x + (uint32_t)q * gridDim.x;
-            ItemInfo it;
-            if ((int64_t)t < a.n_tiles) it = work_item(a, t);
-            else it.pair = -1;
-            s_item[q] = it;
-        }
-        t_pending = 2u * gridDim.x + atomicAdd(a.ticket, 1u);
+        ItemInfo it;
+        if ((int64_t)blockIdx.x < a.n_tiles) it = work_item(a, blockIdx.x);
+        else it.pair = -1;
+        s_item[0] = it;
     }
     __syncthreads();
     if (s_item[0].pair < 0) return;
@@ -1773,7 +1828,6 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_splat(KernelArgs a) {
     int cur = 0;
     for (;;) {
         const ItemInfo it = s_item[cur];
-        const ItemInfo nx = s_item[cur ^ 1];
         cp_async_wait_all();
         __syncthreads();  // staged header and records of `it` visible; the other header slot is free; the wrap flag is read
         if (it.pair < 0) break;
@@ -1782,13 +1836,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_splat(KernelArgs a) {
             sh_wrap = 0;
             sh_carry_clean = 0;
         }
-        if (nx.pair >= 0) stage_header(a, nx.pair, bufs + (cur ^ 1) * kStageHeader);  // its records: after the splat
-        cp_async_commit();
-        const uint32_t t2 = t_pending;
-        if (threadIdx.x == 0) t_pending = 2u * gridDim.x + atomicAdd(a.ticket, 1u);  // returns while this item renders
-        ItemInfo after;
-        process_item<T, NT, RS>(a, it, nx, bufs + cur * kStageHeader, rec, cap, s, t2, after);
-        if (threadIdx.x == 0) s_item[cur] = after;
+        process_item<T, NT, RS>(a, it, tk, bufs + cur * kStageHeader, bufs + (cur ^ 1) * kStageHeader, rec, cap, s,
+                                &s_item[cur ^ 1]);
+        if (threadIdx.x == 0) tk = 2u * gridDim.x + atomicAdd(a.ticket, 1u);  // the item after the next
         cur ^= 1;
         __syncthreads();
     }
