@@ -695,9 +695,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_advect(KernelArgs a) {
             r.sigma = p2.x;
             r.amp = p2.y;
             if (same_res)
-                advect_split_with(
-                    [&](int32_t ix, float fx, int32_t iy, float fy) { return velocity_tile(F, Wn, ix, fx, iy, fy); },
-                    a.dt, a.n_substeps, a.integrator, r.ix, r.fx, r.iy, r.fy);
+                advect_split_with(TileVelocity(F, Wn), a.dt, a.n_substeps, a.integrator, r.ix, r.fx, r.iy, r.fy);
             else
                 advect_split_with(
                     [&](int32_t ix, float fx, int32_t iy, float fy) { return velocity_windowed(F, Wn, ix, fx, iy, fy); },
