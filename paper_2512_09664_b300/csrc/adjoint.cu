@@ -135,18 +135,34 @@ __global__ void __launch_bounds__(256) k_adj_splat(KernelArgs a) {
             any ? make_float4(amp * sx, amp * sy, amp * ss + 2.0f * amp * inv * sm, 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
+// The four nodes of the last grid cell (l, k) a thread's Jacobians read: the
+// third stage of an RK4 substep nearly always samples the cell of the second,
+// so its gathers (and their latency in the thread's dependent chain) are
+// skipped.  Same nodes, same arithmetic.
+struct CellCache {
+    int32_t l, k;  // the cell before clamping; l = INT32_MIN: none
+    float2 A, B, C, D;
+};
+
 // Velocity at i + f (split) with its Jacobian (J = du/dx, du/dy, dv/dx, dv/dy)
 // and the four stencil nodes (flat index k * gw + l) with their weights.
 __device__ __forceinline__ float2 velocity_jac(const Flow &F, int32_t ix, float fx, int32_t iy, float fy, float J[4],
-                                               int node[4], float wgt[4]) {
+                                               int node[4], float wgt[4], CellCache &cc) {
     int32_t l, k;
     float tx, ty;
     grid_coord(ix, fx, F.gw, F.W, l, tx);
     grid_coord(iy, fy, F.gh, F.H, k, ty);
     const int32_t l0 = min(max(l, 0), F.gw - 1), l1 = min(max(l + 1, 0), F.gw - 1);
     const int32_t k0 = min(max(k, 0), F.gh - 1), k1 = min(max(k + 1, 0), F.gh - 1);
-    const float2 A = __ldg(F.f + (size_t)k0 * F.gw + l0), B = __ldg(F.f + (size_t)k0 * F.gw + l1);
-    const float2 C = __ldg(F.f + (size_t)k1 * F.gw + l0), D = __ldg(F.f + (size_t)k1 * F.gw + l1);
+    if (l != cc.l || k != cc.k) {
+        cc.l = l;
+        cc.k = k;
+        cc.A = __ldg(F.f + (size_t)k0 * F.gw + l0);
+        cc.B = __ldg(F.f + (size_t)k0 * F.gw + l1);
+        cc.C = __ldg(F.f + (size_t)k1 * F.gw + l0);
+        cc.D = __ldg(F.f + (size_t)k1 * F.gw + l1);
+    }
+    const float2 A = cc.A, B = cc.B, C = cc.C, D = cc.D;
     const float tu = fmaf(tx, B.x - A.x, A.x), tv = fmaf(tx, B.y - A.y, A.y);
     const float bu = fmaf(tx, D.x - C.x, C.x), bv = fmaf(tx, D.y - C.y, C.y);
     const float sxg = (float)F.gw / (float)F.W, syg = (float)F.gh / (float)F.H;
@@ -213,6 +229,9 @@ __global__ void __launch_bounds__(128) k_adj_advect(KernelArgs a) {
         }
     }
     float lx = g2.x, ly = g2.y;  // dL / d(frame-2 position)
+    CellCache cc;
+    cc.l = INT32_MIN;
+    cc.k = 0;
 #pragma unroll(NMAX <= 8 ? NMAX : 1)
     for (int s = NMAX - 1; s >= 0; --s) {
         if (s >= n) continue;
@@ -220,7 +239,7 @@ __global__ void __launch_bounds__(128) k_adj_advect(KernelArgs a) {
         const float ux = sfx[s], uy = sfy[s];
         float J1[4], w1[4];
         int n1[4];
-        const float2 k1 = velocity_jac(F, px, ux, py, uy, J1, n1, w1);
+        const float2 k1 = velocity_jac(F, px, ux, py, uy, J1, n1, w1, cc);
         if (a.integrator == SYNTHPIX_EULER) {
             scatter_flow(gf, n1, w1, h * lx, h * ly);
             const float ax = lx + h * (J1[0] * lx + J1[2] * ly);
@@ -231,9 +250,9 @@ __global__ void __launch_bounds__(128) k_adj_advect(KernelArgs a) {
         }
         float J2[4], w2[4], J3[4], w3[4], J4[4], w4[4];
         int n2[4], n3[4], n4[4];
-        const float2 k2 = velocity_jac(F, px, fmaf(hh, k1.x, ux), py, fmaf(hh, k1.y, uy), J2, n2, w2);
-        const float2 k3 = velocity_jac(F, px, fmaf(hh, k2.x, ux), py, fmaf(hh, k2.y, uy), J3, n3, w3);
-        velocity_jac(F, px, fmaf(h, k3.x, ux), py, fmaf(h, k3.y, uy), J4, n4, w4);
+        const float2 k2 = velocity_jac(F, px, fmaf(hh, k1.x, ux), py, fmaf(hh, k1.y, uy), J2, n2, w2, cc);
+        const float2 k3 = velocity_jac(F, px, fmaf(hh, k2.x, ux), py, fmaf(hh, k2.y, uy), J3, n3, w3, cc);
+        velocity_jac(F, px, fmaf(h, k3.x, ux), py, fmaf(h, k3.y, uy), J4, n4, w4, cc);
         // p+ = p + h/6 (k1 + 2 k2 + 2 k3 + k4), k_m = U(q_m): adjoints of the stages
         const float k4x = h6 * lx, k4y = h6 * ly;
         const float k3x = 2.0f * h6 * lx + h * (J4[0] * k4x + J4[2] * k4y);
