@@ -80,6 +80,37 @@ __device__ __forceinline__ float2 velocity(const Flow &F, int32_t ix, float fx, 
     return make_float2(fmaf(ty, bu - tu, tu), fmaf(ty, bv - tv, tv));
 }
 
+// velocity() with the four nodes of the last grid cell (l, k) kept in
+// registers: consecutive RK4 stages mostly sample the same cell (the third
+// stage that of the second, a substep's first that of the previous fourth),
+// and a lane reloads the nodes from the grid only when its cell changes.
+// Same nodes, same arithmetic: the result is identical.
+struct GridVelocity {
+    const Flow &F;
+    int32_t cl, ck;  // the cached cell (l, k) before clamping; cl = INT32_MIN: none
+    float2 a, b, c, d;
+    __device__ explicit GridVelocity(const Flow &f) : F(f), cl(INT32_MIN), ck(0) {}
+    __device__ __forceinline__ float2 operator()(int32_t ix, float fx, int32_t iy, float fy) {
+        int32_t l, k;
+        float tx, ty;
+        grid_coord(ix, fx, F.gw, F.W, l, tx);
+        grid_coord(iy, fy, F.gh, F.H, k, ty);
+        if (l != cl || k != ck) {
+            cl = l;
+            ck = k;
+            const int32_t l0 = min(max(l, 0), F.gw - 1), l1 = min(max(l + 1, 0), F.gw - 1);
+            const int32_t k0 = min(max(k, 0), F.gh - 1), k1 = min(max(k + 1, 0), F.gh - 1);
+            a = __ldg(F.f + (size_t)k0 * F.gw + l0);
+            b = __ldg(F.f + (size_t)k0 * F.gw + l1);
+            c = __ldg(F.f + (size_t)k1 * F.gw + l0);
+            d = __ldg(F.f + (size_t)k1 * F.gw + l1);
+        }
+        const float tu = fmaf(tx, b.x - a.x, a.x), tv = fmaf(tx, b.y - a.y, a.y);
+        const float bu = fmaf(tx, d.x - c.x, c.x), bv = fmaf(tx, d.y - c.y, c.y);
+        return make_float2(fmaf(ty, bu - tu, tu), fmaf(ty, bv - tv, tv));
+    }
+};
+
 // Clipped pixel window [j0, j1] x [i0, i1] of a particle (empty: j0 > j1).
 struct Window {
     int32_t j0, j1, i0, i1;
@@ -259,7 +290,7 @@ __device__ __forceinline__ Flow pair_flow(const KernelArgs &a, const synthpix_pa
 // Frame-2 position: n substeps of RK4 (or Euler) over dt, on split
 // coordinates; vel(ix, fx, iy, fy) is the bilinear velocity.
 template <typename Vel>
-__device__ __forceinline__ void advect_split_with(Vel vel, float dt, int n_substeps, int integrator, int32_t &jx,
+__device__ __forceinline__ void advect_split_with(Vel &&vel, float dt, int n_substeps, int integrator, int32_t &jx,
                                                   float &gx, int32_t &jy, float &gy) {
     const float h = dt / (float)n_substeps;
     const float hh = 0.5f * h, h6 = h / 6.0f;

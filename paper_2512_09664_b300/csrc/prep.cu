@@ -218,7 +218,11 @@ __device__ __forceinline__ void count_window(const KernelArgs &a, const ChunkCtx
 // split positions and bin counts (export only: writes (x, y, d) of frame 1
 // or, advected, of frame 2)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kPrepThreads, 5) k_seed_advect(KernelArgs a) {
+// CACHE (the adjoint's positions, a.states set): the substeps' flow lookups
+// keep the last grid cell's nodes in registers (GridVelocity), with the
+// register room of two CTAs per SM; the render paths keep five.
+template <bool CACHE>
+__global__ void __launch_bounds__(kPrepThreads, CACHE ? 2 : 5) k_seed_advect(KernelArgs a) {
     if (*a.check != 1) return;
     __shared__ __align__(16) ChunkCtx c;
     __shared__ uint32_t hist[kHistMax];
@@ -257,9 +261,17 @@ __global__ void __launch_bounds__(kPrepThreads, 5) k_seed_advect(KernelArgs a) {
             else if (a.states) {  // each substep's start kept for the adjoint (the same arithmetic)
                 float4 *sp = a.states + g * a.n_substeps;
                 const float h = a.dt / (float)a.n_substeps;
-                for (int s = 0; s < a.n_substeps; ++s) {
-                    sp[s] = make_float4(gx, gy, __int_as_float(jx), __int_as_float(jy));
-                    advect_split(F, h, 1, a.integrator, jx, gx, jy, gy);
+                if constexpr (CACHE) {
+                    GridVelocity vel(F);  // its cached cell carries over the substeps
+                    for (int s = 0; s < a.n_substeps; ++s) {
+                        sp[s] = make_float4(gx, gy, __int_as_float(jx), __int_as_float(jy));
+                        advect_split_with(vel, h, 1, a.integrator, jx, gx, jy, gy);
+                    }
+                } else {
+                    for (int s = 0; s < a.n_substeps; ++s) {
+                        sp[s] = make_float4(gx, gy, __int_as_float(jx), __int_as_float(jy));
+                        advect_split(F, h, 1, a.integrator, jx, gx, jy, gy);
+                    }
                 }
             } else {
                 advect_split(F, a.dt, a.n_substeps, a.integrator, jx, gx, jy, gy);
@@ -834,7 +846,7 @@ cudaError_t launch_prep(const KernelArgs &a, cudaStream_t st, cudaEvent_t const 
         if (e == cudaSuccess) e = r;
     };
     if (!a.tiled) {
-        if (nb > 0) ok(launch_kernel(k_seed_advect, nb, kPrepThreads, 0, st, a));
+        if (nb > 0) ok(launch_kernel(k_seed_advect<false>, nb, kPrepThreads, 0, st, a));
         mark(2);
         ok(launch_kernel(k_scan, 2u * (unsigned)a.n_pairs, 1024, 0, st, a, -1));
         mark(3);
@@ -867,7 +879,10 @@ cudaError_t launch_prep(const KernelArgs &a, cudaStream_t st, cudaEvent_t const 
 namespace spx {
 
 cudaError_t launch_seed_only(const KernelArgs &a, cudaStream_t st) {
-    if (a.n_chunks > 0) return launch_kernel(k_seed_advect, (unsigned)a.n_chunks, kPrepThreads, 0, st, a);
+    if (a.n_chunks > 0) {
+        if (a.states) return launch_kernel(k_seed_advect<true>, (unsigned)a.n_chunks, kPrepThreads, 0, st, a);
+        return launch_kernel(k_seed_advect<false>, (unsigned)a.n_chunks, kPrepThreads, 0, st, a);
+    }
     return cudaGetLastError();
 }
 
