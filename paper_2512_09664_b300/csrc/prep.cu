@@ -218,11 +218,13 @@ __device__ __forceinline__ void count_window(const KernelArgs &a, const ChunkCtx
 // split positions and bin counts (export only: writes (x, y, d) of frame 1
 // or, advected, of frame 2)
 // ---------------------------------------------------------------------------
-// CACHE (the adjoint's positions, a.states set): the substeps' flow lookups
-// keep the last grid cell's nodes in registers (GridVelocity), with the
-// register room of two CTAs per SM; the render paths keep five.
+// CACHE: the flow lookups of the per-particle advection keep the last grid
+// cell's nodes in registers (GridVelocity), with the register room of three
+// CTAs per SM (at five per SM the cache spilled).  Used by the renders that
+// advect per particle and by the adjoint's positions; the export of
+// particle positions keeps the five-CTA variant.
 template <bool CACHE>
-__global__ void __launch_bounds__(kPrepThreads, CACHE ? 2 : 5) k_seed_advect(KernelArgs a) {
+__global__ void __launch_bounds__(kPrepThreads, CACHE ? 3 : 5) k_seed_advect(KernelArgs a) {
     if (*a.check != 1) return;
     __shared__ __align__(16) ChunkCtx c;
     __shared__ uint32_t hist[kHistMax];
@@ -274,7 +276,8 @@ __global__ void __launch_bounds__(kPrepThreads, CACHE ? 2 : 5) k_seed_advect(Ker
                     }
                 }
             } else {
-                advect_split(F, a.dt, a.n_substeps, a.integrator, jx, gx, jy, gy);
+                if constexpr (CACHE) advect_split_with(GridVelocity(F), a.dt, a.n_substeps, a.integrator, jx, gx, jy, gy);
+                else advect_split(F, a.dt, a.n_substeps, a.integrator, jx, gx, jy, gy);
             }
             a.pos1[g] = make_float4(gx, gy, __int_as_float(jx), __int_as_float(jy));
         }
@@ -846,7 +849,7 @@ cudaError_t launch_prep(const KernelArgs &a, cudaStream_t st, cudaEvent_t const 
         if (e == cudaSuccess) e = r;
     };
     if (!a.tiled) {
-        if (nb > 0) ok(launch_kernel(k_seed_advect<false>, nb, kPrepThreads, 0, st, a));
+        if (nb > 0) ok(launch_kernel(k_seed_advect<true>, nb, kPrepThreads, 0, st, a));
         mark(2);
         ok(launch_kernel(k_scan, 2u * (unsigned)a.n_pairs, 1024, 0, st, a, -1));
         mark(3);
