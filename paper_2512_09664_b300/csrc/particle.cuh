@@ -404,34 +404,14 @@ __device__ __forceinline__ float2 velocity_windowed(const Flow &F, const FlowWin
 // common case: the node below the position is (ix + floor(fx - 1/2),
 // iy + floor(fy - 1/2)).  When it and its three neighbours lie in the staged
 // window, they are read from shared memory with one row offset; otherwise
-// (window edge, grid border clamping) velocity() reads the grid.  The
-// nodes and the arithmetic are those of velocity(), so the result is
-// identical.
-__device__ __forceinline__ float2 velocity_tile(const Flow &F, const FlowWindow &Wn, int32_t ix, float fx,
-                                                int32_t iy, float fy) {
-    const float gx = fx - 0.5f, gy = fy - 0.5f;
-    const float flx = floorf(gx), fly = floorf(gy);
-    const float tx = gx - flx, ty = gy - fly;
-    // small integral floats to int without the conversion unit (|fl| < 2^22)
-    const int32_t u = ix - Wn.gx0 + (__float_as_int(flx + 12582912.0f) - 0x4B400000);
-    const int32_t v = iy - Wn.gy0 + (__float_as_int(fly + 12582912.0f) - 0x4B400000);
-    const unsigned lx = Wn.nw > 1 ? (unsigned)(Wn.nw - 1) : 0u, ly = Wn.nh > 1 ? (unsigned)(Wn.nh - 1) : 0u;
-    if ((unsigned)u < lx && (unsigned)v < ly) {
-        const uint32_t p = Wn.sa + 8u * (uint32_t)(v * Wn.nw + u), q = p + 8u * (uint32_t)Wn.nw;
-        const float2 a = window_node(p), b = window_node(p + 8u), c = window_node(q), d = window_node(q + 8u);
-        const float tu = fmaf(tx, b.x - a.x, a.x), tv = fmaf(tx, b.y - a.y, a.y);
-        const float bu = fmaf(tx, d.x - c.x, c.x), bv = fmaf(tx, d.y - c.y, c.y);
-        return make_float2(fmaf(ty, bu - tu, tu), fmaf(ty, bv - tv, tv));
-    }
-    return velocity(F, ix, fx, iy, fy);
-}
-
-// velocity_tile with the four nodes of the last cell kept in registers: the
-// stages of an RK4 substep mostly sample the cell of the stage before (the
-// third stage that of the second, the next substep's first that of the
-// fourth), so a lane reloads the nodes only when its cell changes and the
-// window's shared-memory loads (random gathers, bank-conflicted) are issued
-// by fewer lanes.  Same nodes, same arithmetic: the result is identical.
+// (window edge, grid border clamping) velocity() reads the grid.  The four
+// nodes of the last cell are kept in registers: the stages of an RK4
+// substep mostly sample the cell of the stage before (the third stage that
+// of the second, the next substep's first that of the fourth), so a lane
+// reloads the nodes only when its cell changes and the window's
+// shared-memory loads (random gathers, bank-conflicted) are issued by fewer
+// lanes.  The nodes and the arithmetic are those of velocity(), so the
+// result is identical.
 struct TileVelocity {
     const Flow &F;
     const FlowWindow &Wn;
