@@ -415,9 +415,10 @@ int synthpix_tuning_lookup(const synthpix_batch_desc *batch, const synthpix_pair
  * Writes parameters into the autotuner's table for this batch's classes
  * (tile = 0 batches), e.g. ones saved from an earlier process: the tile
  * edges of the classes present (others ignored), records_per_stage
- * (1..4096; larger than the splat's staging buffers hold for the largest
- * edge gives SYNTHPIX_EUNSUPPORTED) and register_epilogue (0 or 1); ms is
- * ignored.  No device call.
+ * (1..4096; more than the splat's staged-record region holds for the
+ * largest edge, 1078 records at edge 128 and 822 below, gives
+ * SYNTHPIX_EUNSUPPORTED) and register_epilogue (0 or 1); ms is ignored.  No
+ * device call.
  */
 int synthpix_tuning_set(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs, int32_t n_pairs,
                         const synthpix_tuning *tuning);
