@@ -69,7 +69,11 @@ extern "C" {
 
 /* batch flags */
 #define SYNTHPIX_FLAG_GATHER_ADVECT 1  /* advect every particle by direct flow-grid gathers
-                                          instead of the tiled advection (same result)  */
+                                          and bin both frames by a counting sort instead
+                                          of the fixed-capacity bins (same result)       */
+#define SYNTHPIX_FLAG_TILED_ADVECT  4  /* advect tile by tile from flow windows staged on
+                                          chip instead of per particle while seeding
+                                          (same result); excludes GATHER_ADVECT          */
 #define SYNTHPIX_FLAG_OUT_OF_PLANE  2  /* out-of-plane motion (Remark "out-of-focus": a
                                           three-dimensional flow): each pair's flow grid
                                           is followed in `flows`, at flow_offset +
@@ -162,12 +166,16 @@ typedef struct synthpix_batch_desc {
                                     128 fails with SYNTHPIX_EUNSUPPORTED when the
                                     largest blur radius needs more shared memory than a
                                     CTA has.                                           */
-    int32_t  flags;              /* 0 or SYNTHPIX_FLAG_GATHER_ADVECT.  By default a
-                                    seeded render advects the particles tile by tile:
-                                    the flow nodes under each frame-1 tile are staged
-                                    on chip with coalesced loads.  Renders from given
-                                    particles and the adjoint always gather per
-                                    particle.  Both give the same positions.          */
+    int32_t  flags;              /* 0 or an OR of SYNTHPIX_FLAG_*.  By default a
+                                    seeded render advects each particle where it is
+                                    seeded, by flow-grid gathers that keep the last
+                                    grid cell's nodes in registers, and places both
+                                    frames' records into fixed-capacity bins in the
+                                    same pass.  TILED_ADVECT advects tile by tile from
+                                    flow windows staged on chip; GATHER_ADVECT bins by
+                                    a counting sort.  Renders from given particles and
+                                    the adjoint always gather per particle.  All give
+                                    the same positions and images.                    */
     float    hide_prob;          /* probability, 0..1, that a particle is left out of a
                                     frame, independently per frame (Section 2,
                                     aggregation of the particle contributions)         */

@@ -19,8 +19,9 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libsynthpix.so")
 
 OK, EINVAL, EWORKSPACE, ECUDA, EUNSUPPORTED = 0, -1, -2, -3, -4
-FLAG_GATHER_ADVECT = 1  # advect per particle by direct flow gathers (default: tiled advection)
+FLAG_GATHER_ADVECT = 1  # advect per particle by direct flow gathers, bin by a counting sort
 FLAG_OUT_OF_PLANE = 2   # a w grid follows each flow grid; particles move in z (set by pack for flows_w)
+FLAG_TILED_ADVECT = 4   # advect tile by tile from on-chip flow windows (default: per particle while seeding)
 DTYPE_CODE = {"f32": 0, "f16": 1, "bf16": 2, "u8": 3, "u16": 4}
 INTEGRATOR_CODE = {"rk4": 0, "euler": 1}
 _EXPORTS = ("synthpix_workspace_bytes", "synthpix_render_pairs", "synthpix_render_pairs_staged",

@@ -67,8 +67,10 @@ int check_batch(const synthpix_batch_desc *b) {
     if (!finite(b->dt) || std::fabs(b->dt) > 64.0f) return fail(SYNTHPIX_EINVAL, "dt must be finite with |dt| <= 64");
     if (b->tile != 0 && b->tile != 16 && b->tile != 32 && b->tile != 64 && b->tile != 128)
         return fail(SYNTHPIX_EINVAL, "tile %d is not 0, 16, 32, 64 or 128", b->tile);
-    if (b->flags & ~(SYNTHPIX_FLAG_GATHER_ADVECT | SYNTHPIX_FLAG_OUT_OF_PLANE))
+    if (b->flags & ~(SYNTHPIX_FLAG_GATHER_ADVECT | SYNTHPIX_FLAG_OUT_OF_PLANE | SYNTHPIX_FLAG_TILED_ADVECT))
         return fail(SYNTHPIX_EUNSUPPORTED, "unknown flags 0x%x", b->flags);
+    if ((b->flags & SYNTHPIX_FLAG_GATHER_ADVECT) && (b->flags & SYNTHPIX_FLAG_TILED_ADVECT))
+        return fail(SYNTHPIX_EINVAL, "flags GATHER_ADVECT and TILED_ADVECT exclude each other");
     if (!finite(b->hide_prob) || b->hide_prob < 0.0f || b->hide_prob > 1.0f)
         return fail(SYNTHPIX_EINVAL, "hide_prob must lie in [0, 1]");
     for (int k = 0; k < 5; ++k)
@@ -483,8 +485,10 @@ static int run(Mode mode, const synthpix_batch_desc *batch, const synthpix_pair_
     a.rec = reinterpret_cast<spx::Record *>(ws + L.rec);
     a.adv = reinterpret_cast<spx::Record *>(ws + L.adv);
     // per-frame shapes need each particle's index: those renders advect per particle
-    a.tiled = (mode == Mode::Render && !x.particles_in && !P.ext && !(batch->flags & SYNTHPIX_FLAG_GATHER_ADVECT))
-                  ? 1 : 0;
+    if (mode == Mode::Render && !x.particles_in && !P.ext && !(batch->flags & SYNTHPIX_FLAG_GATHER_ADVECT))
+        a.tiled = (batch->flags & SYNTHPIX_FLAG_TILED_ADVECT) ? 1 : 2;
+    else
+        a.tiled = 0;
     a.ticket = ticket;
     a.ovf = ticket + 1;
     a.rebin = P.rebin;

@@ -38,9 +38,10 @@ struct KernelArgs {
     ItemInfo *items;                  // per (pair, frame, tile): the splat's work items
     Record *rec;                      // bins
     Record *adv;                      // tiled advection: frame-2 records by frame-1 bin slot (sigma < 0: none)
-    int32_t tiled;                    // 1 (seeded renders): frame 2 comes from the tiled advection (k_advect),
-                                      // and k_seed_place and k_advect place the records into fixed-capacity
-                                      // bins (fixed_caps); 0: k_seed_advect and a counting sort
+    int32_t tiled;                    // seeded renders, records placed into fixed-capacity bins (fixed_caps):
+                                      // 2: k_seed_place advects each particle and places both frames;
+                                      // 1: k_seed_place places frame 1, the tiled advection (k_advect)
+                                      // makes and places frame 2; 0: k_seed_advect and a counting sort
     uint32_t *ovf;                    // [2]: a fixed bin of frame 1 / frame 2 overflowed (zeroed by k_plan)
     int32_t rebin;                    // 1: launch k_rebin after each placement (0: no bin can overflow)
     uint32_t *ticket;                 // work-queue counter of the persistent splat

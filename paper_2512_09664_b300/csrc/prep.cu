@@ -331,13 +331,20 @@ __device__ __forceinline__ void place_fixed(const KernelArgs &a, const PairPlan 
     o[2] = make_float2(r.sigma, r.amp);
 }
 
-__global__ void __launch_bounds__(kPrepThreads, 4) k_seed_place(KernelArgs a) {
+// ADV (a.tiled == 2): each particle is also advected here, through the
+// flow grid with the last cell's nodes in registers (GridVelocity), and
+// both frames' records are placed: frame 2 follows frame 1 on the counters
+// and bins; the frame-2 positions go to pos1 (the exact rebinning's input).
+// Three CTAs per SM leave room for the advection's registers.
+template <bool ADV>
+__global__ void __launch_bounds__(kPrepThreads, ADV ? 3 : 4) k_seed_place(KernelArgs a) {
     if (*a.check != 1) return;
     __shared__ __align__(16) ChunkCtx c;
     __shared__ uint32_t cnt[kHistMax], base[kHistMax];
     load_chunk(a, c);
     const int nk = c.pl.ntiles;
-    const bool local = nk <= kHistMax;
+    constexpr int NF = ADV ? 2 : 1;  // frames placed here
+    const bool local = NF * nk <= kHistMax;
     int64_t cap1, cap2;
     fixed_caps(c.d, c.pl.tile, c.pl.halo, cap1, cap2);
     if ((int64_t)blockIdx.x == c.pl.chunk_base) {  // the pair's work items (fixed layout)
@@ -353,10 +360,10 @@ __global__ void __launch_bounds__(kPrepThreads, 4) k_seed_place(KernelArgs a) {
         }
     }
     if (local) {
-        for (int k = threadIdx.x; k < nk; k += kPrepThreads) cnt[k] = 0u;
+        for (int k = threadIdx.x; k < NF * nk; k += kPrepThreads) cnt[k] = 0u;
         __syncthreads();
     }
-    uint32_t *cnt1 = a.count + c.pl.tile_base;
+    uint32_t *cnt1 = a.count + c.pl.tile_base;  // frame f's counter of tile k at f nk + k
     const int W = c.d.width, H = c.d.height;
     auto tiles_of = [&](const Record &r, int32_t &tx0, int32_t &tx1, int32_t &ty0, int32_t &ty1) {
         const Window w = particle_window(r.ix, r.fx, r.iy, r.fy, 6.0f * r.sigma, W, H);
@@ -365,35 +372,42 @@ __global__ void __launch_bounds__(kPrepThreads, 4) k_seed_place(KernelArgs a) {
         return true;
     };
     constexpr int U = kChunk / kPrepThreads;
-    Record r[U];
+    Record r[NF][U];  // the particle's record of each frame placed here (sigma < 0: none)
+    const Flow F = pair_flow(a, c.d);
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         const int q = threadIdx.x + u * kPrepThreads;
-        r[u].sigma = -1.0f;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) r[f][u].sigma = -1.0f;
         if (q >= c.n) continue;
         const uint32_t i = (uint32_t)(c.first + q);
         const int64_t g = c.pl.part_base + i;
         const Seeded P = seed_particle(a, c.d, i, g);
         a.sa[g] = make_float2(P.sigma, P.amp);
         a.pos0[g] = make_float4(P.fx, P.fy, __int_as_float(P.ix), __int_as_float(P.iy));
-        r[u].fx = P.fx;
-        r[u].fy = P.fy;
-        r[u].ix = P.ix;
-        r[u].iy = P.iy;
-        r[u].sigma = P.sigma;
-        r[u].amp = P.amp;
-        int32_t tx0, tx1, ty0, ty1;
-        if (!tiles_of(r[u], tx0, tx1, ty0, ty1)) continue;
-        for (int32_t ty = ty0; ty <= ty1; ++ty)
-            for (int32_t tx = tx0; tx <= tx1; ++tx) {
-                const int32_t k = ty * c.pl.tiles_x + tx;
-                if (local) atomicAdd(cnt + k, 1u);
-                else place_fixed(a, c.pl, 0, k, cap1, atomicAdd(cnt1 + k, 1u), r[u]);
-            }
+        r[0][u] = Record{P.fx, P.fy, P.ix, P.iy, P.sigma, P.amp};
+        if constexpr (ADV) {
+            int32_t jx = P.ix, jy = P.iy;
+            float gx = P.fx, gy = P.fy;
+            advect_split_with(GridVelocity(F), a.dt, a.n_substeps, a.integrator, jx, gx, jy, gy);
+            a.pos1[g] = make_float4(gx, gy, __int_as_float(jx), __int_as_float(jy));
+            r[NF - 1][u] = Record{gx, gy, jx, jy, P.sigma, P.amp};
+        }
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            int32_t tx0, tx1, ty0, ty1;
+            if (!tiles_of(r[f][u], tx0, tx1, ty0, ty1)) continue;
+            for (int32_t ty = ty0; ty <= ty1; ++ty)
+                for (int32_t tx = tx0; tx <= tx1; ++tx) {
+                    const int32_t k = f * nk + ty * c.pl.tiles_x + tx;
+                    if (local) atomicAdd(cnt + k, 1u);
+                    else place_fixed(a, c.pl, f, k - f * nk, f ? cap2 : cap1, atomicAdd(cnt1 + k, 1u), r[f][u]);
+                }
+        }
     }
     if (!local) return;
     __syncthreads();
-    for (int k = threadIdx.x; k < nk; k += kPrepThreads) {
+    for (int k = threadIdx.x; k < NF * nk; k += kPrepThreads) {
         const uint32_t n = cnt[k];
         base[k] = n ? atomicAdd(cnt1 + k, n) : 0u;
         cnt[k] = 0u;
@@ -401,14 +415,17 @@ __global__ void __launch_bounds__(kPrepThreads, 4) k_seed_place(KernelArgs a) {
     __syncthreads();
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        if (r[u].sigma < 0.0f) continue;
-        int32_t tx0, tx1, ty0, ty1;
-        if (!tiles_of(r[u], tx0, tx1, ty0, ty1)) continue;
-        for (int32_t ty = ty0; ty <= ty1; ++ty)
-            for (int32_t tx = tx0; tx <= tx1; ++tx) {
-                const int32_t k = ty * c.pl.tiles_x + tx;
-                place_fixed(a, c.pl, 0, k, cap1, base[k] + atomicAdd(cnt + k, 1u), r[u]);
-            }
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            if (r[f][u].sigma < 0.0f) continue;
+            int32_t tx0, tx1, ty0, ty1;
+            if (!tiles_of(r[f][u], tx0, tx1, ty0, ty1)) continue;
+            for (int32_t ty = ty0; ty <= ty1; ++ty)
+                for (int32_t tx = tx0; tx <= tx1; ++tx) {
+                    const int32_t k = f * nk + ty * c.pl.tiles_x + tx;
+                    place_fixed(a, c.pl, f, k - f * nk, f ? cap2 : cap1, base[k] + atomicAdd(cnt + k, 1u), r[f][u]);
+                }
+        }
     }
 }
 
@@ -760,8 +777,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_advect(KernelArgs a) {
 // frame's bins are rebuilt in the exact layout, one CTA per pair: the scan
 // of the bin counters (which counted every record), then every record placed
 // at its bin's cursor.  Frame 1 from the seeded positions, frame 2 from the
-// advected records of the frame-1 bins.  Without an overflow every CTA
-// returns at once.
+// advected records of the frame-1 bins (tiled advection) or from the
+// advected positions (advection in k_seed_place).  Without an overflow every
+// CTA returns at once.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_rebin(KernelArgs a, int f) {
     if (*a.check != 1 || a.ovf[f] == 0u) return;
@@ -790,10 +808,11 @@ __global__ void __launch_bounds__(1024) k_rebin(KernelArgs a, int f) {
         for (int32_t ty = ty0; ty <= ty1; ++ty)
             for (int32_t tx = tx0; tx <= tx1; ++tx) place(ty * pl.tiles_x + tx, r);
     };
-    if (f == 0) {
+    if (f == 0 || a.tiled == 2) {
+        const float4 *pos = f ? a.pos1 : a.pos0;
         for (uint32_t q = threadIdx.x; q < D.n_particles; q += blockDim.x) {
             const int64_t g = pl.part_base + q;
-            const float4 p = a.pos0[g];
+            const float4 p = pos[g];
             const float2 sa = a.sa[g];
             Record r;
             r.fx = p.x;
@@ -857,6 +876,15 @@ cudaError_t launch_prep(const KernelArgs &a, cudaStream_t st, cudaEvent_t const 
         mark(4);
         return e;
     }
+    if (a.tiled == 2) {  // seeded render: seeding, advection and both frames' placement in one pass
+        if (nb > 0) ok(launch_kernel(k_seed_place<true>, nb, kPrepThreads, 0, st, a));
+        mark(2);
+        if (a.rebin) ok(launch_kernel(k_rebin, (unsigned)a.n_pairs, 1024, 0, st, a, 0));  // at once unless overflowed
+        mark(3);
+        if (a.rebin) ok(launch_kernel(k_rebin, (unsigned)a.n_pairs, 1024, 0, st, a, 1));
+        mark(4);
+        return e;
+    }
     // seeded render: seeding with the frame-1 placement, tiled advection with the frame-2 placement
     const unsigned nt1 = (unsigned)(a.n_tiles / 2);
     const size_t adv_smem = (size_t)adv_window_nodes(a.tile) * sizeof(float2);
@@ -864,7 +892,7 @@ cudaError_t launch_prep(const KernelArgs &a, cudaStream_t st, cudaEvent_t const 
     ok(big ? cudaFuncSetAttribute(k_advect<512, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adv_smem)
            : cudaFuncSetAttribute(k_advect<256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adv_smem));
     if (e != cudaSuccess) return e;
-    if (nb > 0) ok(launch_kernel(k_seed_place, nb, kPrepThreads, 0, st, a));
+    if (nb > 0) ok(launch_kernel(k_seed_place<false>, nb, kPrepThreads, 0, st, a));
     if (a.rebin) ok(launch_kernel(k_rebin, (unsigned)a.n_pairs, 1024, 0, st, a, 0));  // at once unless overflowed
     if (nt1 > 0) {
         if (big) ok(launch_kernel(k_advect<512, 2>, 2 * nt1, 512, adv_smem, st, a));

@@ -67,7 +67,7 @@ def test_bad_pair_fields_are_rejected(field, value):
 
 def test_reserved_fields_and_flags_unsupported():
     pk = _packed()
-    pk.batch.flags = 4
+    pk.batch.flags = 8  # the first bit no flag uses
     assert _render(pk) == B.EUNSUPPORTED
     pk = _packed()
     pk.batch.reserved[0] = 1
@@ -120,6 +120,15 @@ def test_gather_advection_flag_accepted():
     pk = _packed()
     pk.batch.flags = B.FLAG_GATHER_ADVECT
     assert B.workspace_bytes(pk) > 0
+
+
+def test_tiled_advection_flag_accepted_and_exclusive():
+    pk = _packed()
+    pk.batch.flags = B.FLAG_TILED_ADVECT
+    assert B.workspace_bytes(pk) > 0
+    pk.batch.flags = B.FLAG_TILED_ADVECT | B.FLAG_GATHER_ADVECT
+    with pytest.raises(B.SynthpixError, match="exclude each other"):
+        B.workspace_bytes(pk)
 
 
 def test_advect_particles_rejects_missing_buffers():

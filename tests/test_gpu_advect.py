@@ -1,6 +1,8 @@
-"""The tiled advection (flow nodes under each frame-1 tile staged on chip)
-against the per-particle gather advection: the lookups use the same nodes
-and arithmetic, so whole batches must render bit-identically, including
+"""The three advection and binning paths of a seeded render: per particle
+while seeding with fixed-capacity bins (the default), tile by tile from flow
+nodes staged on chip (TILED_ADVECT), and per particle with a counting sort
+(GATHER_ADVECT).  The lookups use the same nodes and arithmetic and the
+splat's sums are exact, so whole batches must render bit-identically, including
 flows coarser and finer than the image, displacements that leave the
 staged window and the frame-2 tile neighbourhood, Euler and RK4, and all
 tile edges.  One case is also compared with the FP64 oracle."""
@@ -22,12 +24,15 @@ def _need_cuda():
 
 
 def _both(wl, tile):
+    """The default render and the gather render; the tiled render must equal the default."""
     import torch
 
-    from paper_2512_09664_b300.binding import FLAG_GATHER_ADVECT, Renderer
+    from paper_2512_09664_b300.binding import FLAG_GATHER_ADVECT, FLAG_TILED_ADVECT, Renderer
     a = Renderer(wl, tile=tile).render().clone()
+    t = Renderer(wl, tile=tile, flags=FLAG_TILED_ADVECT).render().clone()
     b = Renderer(wl, tile=tile, flags=FLAG_GATHER_ADVECT).render().clone()
     torch.cuda.synchronize()
+    assert torch.equal(a, t), ("tiled", wl.pairs[0].height, tile)
     return a, b
 
 

@@ -2,7 +2,8 @@
 overflow, on the GPU.
 
 Seeded renders place each record straight into a bin of fixed capacity
-while seeding (frame 1) and advecting (frame 2).  A bin that overflows
+while seeding and advecting each particle (both frames; with TILED_ADVECT,
+frame 1 while seeding and frame 2 in the tiled advection).  A bin that overflows
 flags its frame, and k_rebin then bins the frame again exactly.  The splat
 sums in exact fixed point, so the record order in a bin does not matter and
 both layouts must give bit-identical frames:
@@ -13,8 +14,8 @@ both layouts must give bit-identical frames:
 * a converging flow overflows frame 2 in the product library itself (the
   count it piles into the centre tile, from the oracle's positions, exceeds
   the bin capacity); that render must match the oracle;
-* frame-1 bins of more records than the advection examines per pass (a
-  dense 1024^2 pair at tile 128) place frame 2 over several passes; the
+* frame-1 bins of more records than the tiled advection examines per pass
+  (a dense 1024^2 pair at tile 128) place frame 2 over several passes; the
   render must equal the undersized-bin library's exact rebinning.
 """
 import contextlib
@@ -71,18 +72,20 @@ def _cap2(p, tile, halo):
     return min(e + e // 2 + 64, p.n_particles)
 
 
-@pytest.mark.parametrize("out,tile", [("u8", 128), ("u8", 64), ("f32", 128)])
-def test_overflowing_bins_render_the_same_bits(out, tile):
+@pytest.mark.parametrize("out,tile,tiled", [("u8", 128, False), ("u8", 64, False), ("f32", 128, False),
+                                            ("u8", 128, True), ("u8", 32, True)])
+def test_overflowing_bins_render_the_same_bits(out, tile, tiled):
     import torch
 
-    from paper_2512_09664_b300.binding import Renderer
+    from paper_2512_09664_b300.binding import FLAG_TILED_ADVECT, Renderer
     wl = W.batch_512_u8(n_pairs=3)
     if out == "f32":
         wl.out_dtype, wl.quant_bits = "f32", 0
-    ref = Renderer(wl, tile=tile).render().clone()
+    flags = FLAG_TILED_ADVECT if tiled else 0
+    ref = Renderer(wl, tile=tile, flags=flags).render().clone()
     torch.cuda.synchronize()
     with _library(_smallbins_path()):
-        got = Renderer(wl, tile=tile).render().clone()
+        got = Renderer(wl, tile=tile, flags=flags).render().clone()
         torch.cuda.synchronize()
     assert torch.equal(got, ref)
     assert int((ref != 0).sum()) > 0
@@ -108,15 +111,18 @@ def test_converging_flow_overflows_frame2_and_matches_the_oracle():
     inside = int(((x1 >= t0) & (x1 < t0 + tile) & (y1 >= t0) & (y1 < t0 + tile)).sum())
     halo = int(np.ceil(3.0 * float(pair.blur_sigma)))
     assert inside > _cap2(pair, tile, halo), (inside, _cap2(pair, tile, halo))
-    st = compare(wl, gpu_render(wl, tile=tile), oracle_render(wl))
-    print("converging", st)
-    assert st["pixels"] == 2 * h * w
+    from paper_2512_09664_b300.binding import FLAG_TILED_ADVECT, Renderer
+    ref = oracle_render(wl)
+    for flags in (0, FLAG_TILED_ADVECT):
+        st = compare(wl, gpu_render(wl, renderer=Renderer(wl, tile=tile, flags=flags)), ref)
+        print("converging", flags, st)
+        assert st["pixels"] == 2 * h * w
 
 
 def test_dense_bins_placed_over_several_passes_render_the_same_bits():
     import torch
 
-    from paper_2512_09664_b300.binding import Renderer
+    from paper_2512_09664_b300.binding import FLAG_TILED_ADVECT, Renderer
     h = w = 1024
     flow = W.fourier_flow(h, w, h, w, rms=3.0, seed=2251)
     pair = W.PairSpec(height=h, width=w, n_particles=W.n_particles_for(0.099, h, w), pair_id=251,
@@ -124,19 +130,20 @@ def test_dense_bins_placed_over_several_passes_render_the_same_bits():
                       blur_sigma=0.7)
     wl = W.Workload(name="dense_1024", seed=2, pairs=[pair], flows=[flow], out_dtype="u16", quant_bits=12)
     # a frame-1 bin of tile 128 holds about 2300 records: more than one pass of 2048
-    ref = Renderer(wl, tile=128).render().clone()
+    ref = Renderer(wl, tile=128, flags=FLAG_TILED_ADVECT).render().clone()
     torch.cuda.synchronize()
     with _library(_smallbins_path()):
-        got = Renderer(wl, tile=128).render().clone()
+        got = Renderer(wl, tile=128, flags=FLAG_TILED_ADVECT).render().clone()
         torch.cuda.synchronize()
     assert torch.equal(got, ref)
+    assert torch.equal(Renderer(wl, tile=128).render(), ref)  # advected while seeding
 
 
 
 def test_launch_count_of_each_binning_mode():
     import torch
 
-    from paper_2512_09664_b300.binding import Renderer, launch_count
+    from paper_2512_09664_b300.binding import FLAG_TILED_ADVECT, Renderer, launch_count
     wl = W.batch_512_u8(n_pairs=2)
 
     def launches(r):
@@ -147,19 +154,23 @@ def test_launch_count_of_each_binning_mode():
         torch.cuda.synchronize()
         return launch_count() - n0
 
-    # fixed bins: plan, seeding + frame-1 placement, rebin check, advection + frame-2 placement,
-    # rebin check, splat
-    assert launches(Renderer(wl, tile=128)) == 6
-    assert launches(Renderer(wl, tile=32)) == 6
+    # fixed bins: plan, seeding + advection + both frames' placement, two rebin checks, splat
+    assert launches(Renderer(wl, tile=128)) == 5
+    assert launches(Renderer(wl, tile=32)) == 5
     empty = W.batch_512_u8(n_pairs=2)  # an empty pair: one empty chunk writes its work items
     empty.pairs[1].n_particles = 0
-    assert launches(Renderer(empty, tile=128)) == 6
+    assert launches(Renderer(empty, tile=128)) == 5
+    # tiled advection: plan, seeding + frame-1 placement, rebin check, advection + frame-2
+    # placement, rebin check, splat
+    assert launches(Renderer(wl, tile=128, flags=FLAG_TILED_ADVECT)) == 6
+    assert launches(Renderer(empty, tile=32, flags=FLAG_TILED_ADVECT)) == 6
     # per-particle advection (hiding): plan, seed + advect, scan, scatter, splat
     hidden = W.batch_512_u8(n_pairs=2)
     hidden.hide_prob = np.float32(0.1)
     assert launches(Renderer(hidden, tile=128)) == 5
     # a small pair (N x tiles <= 2^16): bins of capacity N cannot overflow, no rebinning launches
-    assert launches(Renderer(W.single_pair_256(seed=0), tile=64)) == 4
+    assert launches(Renderer(W.single_pair_256(seed=0), tile=64)) == 3
+    assert launches(Renderer(W.single_pair_256(seed=0), tile=64, flags=FLAG_TILED_ADVECT)) == 4
 
 
 def test_a_batch_with_an_empty_pair_matches_the_oracle():
