@@ -5,13 +5,16 @@
 //
 //   k_plan         per-pair prefix sums of particles, tiles and bin slots,
 //                  blur taps, the work-queue ticket; clears the bin counters
-//   k_seed_place   Philox attributes of every particle, split positions, and
-//                  the frame-1 records placed into the fixed bins
+//   k_seed_place   Philox attributes of every particle, split positions, the
+//                  per-particle advection, and both frames' records placed
+//                  into the fixed bins
 //   k_rebin (f 1)  only after a frame-1 bin overflowed: the exact binning
-//   k_advect       tiled advection of each frame-1 tile's home particles from
-//                  a flow window in shared memory; frame-2 records placed
 //   k_rebin (f 2)  only after a frame-2 bin overflowed
 //   k_splat        (splat.cuh) persistent CTAs over the work items
+//
+// With SYNTHPIX_FLAG_TILED_ADVECT, k_seed_place places frame 1 only and
+// k_advect (after k_rebin (f 1)) advects each frame-1 tile's home particles
+// from a flow window in shared memory and places the frame-2 records.
 //
 // Renders that need each particle's index when its frame-2 record is made
 // (given particles, per-frame shapes) advect per particle and bin both frames
@@ -309,10 +312,10 @@ __global__ void __launch_bounds__(kPrepThreads, CACHE ? 3 : 5) k_seed_advect(Ker
 
 // ---------------------------------------------------------------------------
 // k_seed_place (seeded renders with fixed bins): k_seed_advect's seeding
-// with frame 1 binned in the same pass.  A CTA counts its chunk's records per
-// tile on chip, reserves each tile's range of the tile's fixed bin with one
-// global atomic (the bin counters count every record), and places its
-// records from registers.  Records past a bin's capacity are dropped and
+// with the records binned in the same pass (frame 1, or both frames with the
+// advection).  A CTA counts its chunk's records per tile on chip, reserves
+// each tile's range of the tile's fixed bin with one global atomic (the bin
+// counters count every record), and places its records.  Records past a bin's capacity are dropped and
 // flag the frame for k_rebin.  The split positions and sigma / amplitude
 // are still written (k_rebin's input).  The first chunk of each pair writes
 // the pair's work items of the fixed layout.
@@ -335,9 +338,11 @@ __device__ __forceinline__ void place_fixed(const KernelArgs &a, const PairPlan 
 // flow grid with the last cell's nodes in registers (GridVelocity), and
 // both frames' records are placed: frame 2 follows frame 1 on the counters
 // and bins; the frame-2 positions go to pos1 (the exact rebinning's input).
-// Three CTAs per SM leave room for the advection's registers.
+// The advection waits on flow gathers: four CTAs per SM (measured: 100 us
+// for the 64-pair 512 x 512 batch against 117 us at three; five and six
+// gained nothing).
 template <bool ADV>
-__global__ void __launch_bounds__(kPrepThreads, ADV ? 3 : 4) k_seed_place(KernelArgs a) {
+__global__ void __launch_bounds__(kPrepThreads, 4) k_seed_place(KernelArgs a) {
     if (*a.check != 1) return;
     __shared__ __align__(16) ChunkCtx c;
     __shared__ uint32_t cnt[kHistMax], base[kHistMax];
@@ -372,37 +377,43 @@ __global__ void __launch_bounds__(kPrepThreads, ADV ? 3 : 4) k_seed_place(Kernel
         return true;
     };
     constexpr int U = kChunk / kPrepThreads;
-    Record r[NF][U];  // the particle's record of each frame placed here (sigma < 0: none)
+    // without the advection the records stay in registers between the count
+    // and the placement; with it they are read back from pos0 / pos1 / sa
+    // (written just before by the same thread), which frees the registers
+    // across the advection for more resident CTAs
+    constexpr int UK = ADV ? 1 : U;
+    Record rk[UK];
     const Flow F = pair_flow(a, c.d);
-#pragma unroll
+    auto count_or_place = [&](int f, const Record &r, bool place, const uint32_t *at) {
+        int32_t tx0, tx1, ty0, ty1;
+        if (!tiles_of(r, tx0, tx1, ty0, ty1)) return;
+        for (int32_t ty = ty0; ty <= ty1; ++ty)
+            for (int32_t tx = tx0; tx <= tx1; ++tx) {
+                const int32_t k = f * nk + ty * c.pl.tiles_x + tx;
+                if (!place) atomicAdd(cnt + k, 1u);
+                else place_fixed(a, c.pl, f, k - f * nk, f ? cap2 : cap1,
+                                 (at ? at[k] + atomicAdd(cnt + k, 1u) : atomicAdd(cnt1 + k, 1u)), r);
+            }
+    };
+#pragma unroll (ADV ? 1 : U)
     for (int u = 0; u < U; ++u) {
         const int q = threadIdx.x + u * kPrepThreads;
-#pragma unroll
-        for (int f = 0; f < NF; ++f) r[f][u].sigma = -1.0f;
+        if constexpr (!ADV) rk[u].sigma = -1.0f;
         if (q >= c.n) continue;
         const uint32_t i = (uint32_t)(c.first + q);
         const int64_t g = c.pl.part_base + i;
         const Seeded P = seed_particle(a, c.d, i, g);
         a.sa[g] = make_float2(P.sigma, P.amp);
         a.pos0[g] = make_float4(P.fx, P.fy, __int_as_float(P.ix), __int_as_float(P.iy));
-        r[0][u] = Record{P.fx, P.fy, P.ix, P.iy, P.sigma, P.amp};
+        const Record r0{P.fx, P.fy, P.ix, P.iy, P.sigma, P.amp};
+        if constexpr (!ADV) rk[u] = r0;
+        count_or_place(0, r0, !local, nullptr);
         if constexpr (ADV) {
             int32_t jx = P.ix, jy = P.iy;
             float gx = P.fx, gy = P.fy;
             advect_split_with(GridVelocity(F), a.dt, a.n_substeps, a.integrator, jx, gx, jy, gy);
             a.pos1[g] = make_float4(gx, gy, __int_as_float(jx), __int_as_float(jy));
-            r[NF - 1][u] = Record{gx, gy, jx, jy, P.sigma, P.amp};
-        }
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            int32_t tx0, tx1, ty0, ty1;
-            if (!tiles_of(r[f][u], tx0, tx1, ty0, ty1)) continue;
-            for (int32_t ty = ty0; ty <= ty1; ++ty)
-                for (int32_t tx = tx0; tx <= tx1; ++tx) {
-                    const int32_t k = f * nk + ty * c.pl.tiles_x + tx;
-                    if (local) atomicAdd(cnt + k, 1u);
-                    else place_fixed(a, c.pl, f, k - f * nk, f ? cap2 : cap1, atomicAdd(cnt1 + k, 1u), r[f][u]);
-                }
+            count_or_place(1, Record{gx, gy, jx, jy, P.sigma, P.amp}, !local, nullptr);
         }
     }
     if (!local) return;
@@ -415,16 +426,17 @@ __global__ void __launch_bounds__(kPrepThreads, ADV ? 3 : 4) k_seed_place(Kernel
     __syncthreads();
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            if (r[f][u].sigma < 0.0f) continue;
-            int32_t tx0, tx1, ty0, ty1;
-            if (!tiles_of(r[f][u], tx0, tx1, ty0, ty1)) continue;
-            for (int32_t ty = ty0; ty <= ty1; ++ty)
-                for (int32_t tx = tx0; tx <= tx1; ++tx) {
-                    const int32_t k = f * nk + ty * c.pl.tiles_x + tx;
-                    place_fixed(a, c.pl, f, k - f * nk, f ? cap2 : cap1, base[k] + atomicAdd(cnt + k, 1u), r[f][u]);
-                }
+        if constexpr (ADV) {
+            const int q = threadIdx.x + u * kPrepThreads;
+            if (q >= c.n) continue;
+            const int64_t g = c.pl.part_base + (uint32_t)(c.first + q);
+            const float2 sa = a.sa[g];
+            const float4 p0 = a.pos0[g], p1 = a.pos1[g];
+            count_or_place(0, Record{p0.x, p0.y, __float_as_int(p0.z), __float_as_int(p0.w), sa.x, sa.y}, true, base);
+            count_or_place(1, Record{p1.x, p1.y, __float_as_int(p1.z), __float_as_int(p1.w), sa.x, sa.y}, true, base);
+        } else {
+            if (rk[u].sigma < 0.0f) continue;
+            count_or_place(0, rk[u], true, base);
         }
     }
 }
