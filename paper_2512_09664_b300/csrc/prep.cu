@@ -338,11 +338,15 @@ __device__ __forceinline__ void place_fixed(const KernelArgs &a, const PairPlan 
 // flow grid with the last cell's nodes in registers (GridVelocity), and
 // both frames' records are placed: frame 2 follows frame 1 on the counters
 // and bins; the frame-2 positions go to pos1 (the exact rebinning's input).
-// The advection waits on flow gathers: four CTAs per SM (measured: 100 us
-// for the 64-pair 512 x 512 batch against 117 us at three; five and six
-// gained nothing).
-template <bool ADV>
-__global__ void __launch_bounds__(kPrepThreads, 4) k_seed_place(KernelArgs a) {
+// The advection waits on flow gathers.  NT = 256 (two particles a thread,
+// four CTAs per SM) for batches of more chunks than fill the GPU in one
+// wave (measured: 100 us for the 64-pair 512 x 512 batch, against 117 us at
+// three CTAs per SM and 114 us with NT = 512; five and six CTAs per SM
+// gained nothing); NT = 512 (a particle a thread: half the dependent lookups
+// of a lane) for smaller batches (the single 256 x 256 pair 45.1 -> 37.1 us).
+template <bool ADV, int NT>
+__global__ void __launch_bounds__(NT, NT == 512 ? 2 : 4) k_seed_place(KernelArgs a) {
+    static_assert(kChunk % NT == 0, "whole particles per thread");
     if (*a.check != 1) return;
     __shared__ __align__(16) ChunkCtx c;
     __shared__ uint32_t cnt[kHistMax], base[kHistMax];
@@ -353,7 +357,7 @@ __global__ void __launch_bounds__(kPrepThreads, 4) k_seed_place(KernelArgs a) {
     int64_t cap1, cap2;
     fixed_caps(c.d, c.pl.tile, c.pl.halo, cap1, cap2);
     if ((int64_t)blockIdx.x == c.pl.chunk_base) {  // the pair's work items (fixed layout)
-        for (int k = threadIdx.x; k < 2 * nk; k += kPrepThreads) {
+        for (int k = threadIdx.x; k < 2 * nk; k += NT) {
             ItemInfo it;
             it.pair = c.pair;
             it.frame = k >= nk ? 1 : 0;
@@ -365,7 +369,7 @@ __global__ void __launch_bounds__(kPrepThreads, 4) k_seed_place(KernelArgs a) {
         }
     }
     if (local) {
-        for (int k = threadIdx.x; k < NF * nk; k += kPrepThreads) cnt[k] = 0u;
+        for (int k = threadIdx.x; k < NF * nk; k += NT) cnt[k] = 0u;
         __syncthreads();
     }
     uint32_t *cnt1 = a.count + c.pl.tile_base;  // frame f's counter of tile k at f nk + k
@@ -376,7 +380,7 @@ __global__ void __launch_bounds__(kPrepThreads, 4) k_seed_place(KernelArgs a) {
         window_tiles(w, c.pl.halo, c.pl.tile, W, H, tx0, tx1, ty0, ty1);
         return true;
     };
-    constexpr int U = kChunk / kPrepThreads;
+    constexpr int U = kChunk / NT;
     // without the advection the records stay in registers between the count
     // and the placement; with it they are read back from pos0 / pos1 / sa
     // (written just before by the same thread), which frees the registers
@@ -397,7 +401,7 @@ __global__ void __launch_bounds__(kPrepThreads, 4) k_seed_place(KernelArgs a) {
     };
 #pragma unroll (ADV ? 1 : U)
     for (int u = 0; u < U; ++u) {
-        const int q = threadIdx.x + u * kPrepThreads;
+        const int q = threadIdx.x + u * NT;
         if constexpr (!ADV) rk[u].sigma = -1.0f;
         if (q >= c.n) continue;
         const uint32_t i = (uint32_t)(c.first + q);
@@ -418,7 +422,7 @@ __global__ void __launch_bounds__(kPrepThreads, 4) k_seed_place(KernelArgs a) {
     }
     if (!local) return;
     __syncthreads();
-    for (int k = threadIdx.x; k < NF * nk; k += kPrepThreads) {
+    for (int k = threadIdx.x; k < NF * nk; k += NT) {
         const uint32_t n = cnt[k];
         base[k] = n ? atomicAdd(cnt1 + k, n) : 0u;
         cnt[k] = 0u;
@@ -427,7 +431,7 @@ __global__ void __launch_bounds__(kPrepThreads, 4) k_seed_place(KernelArgs a) {
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         if constexpr (ADV) {
-            const int q = threadIdx.x + u * kPrepThreads;
+            const int q = threadIdx.x + u * NT;
             if (q >= c.n) continue;
             const int64_t g = c.pl.part_base + (uint32_t)(c.first + q);
             const float2 sa = a.sa[g];
@@ -889,7 +893,12 @@ cudaError_t launch_prep(const KernelArgs &a, cudaStream_t st, cudaEvent_t const 
         return e;
     }
     if (a.tiled == 2) {  // seeded render: seeding, advection and both frames' placement in one pass
-        if (nb > 0) ok(launch_kernel(k_seed_place<true>, nb, kPrepThreads, 0, st, a));
+        int dev = 0, nsm = 0;
+        ok(cudaGetDevice(&dev));
+        ok(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        if (e != cudaSuccess) return e;
+        if (nb > 2u * (unsigned)nsm) ok(launch_kernel(k_seed_place<true, 256>, nb, 256, 0, st, a));
+        else if (nb > 0) ok(launch_kernel(k_seed_place<true, 512>, nb, 512, 0, st, a));
         mark(2);
         if (a.rebin) ok(launch_kernel(k_rebin, (unsigned)a.n_pairs, 1024, 0, st, a, 0));  // at once unless overflowed
         mark(3);
@@ -904,7 +913,7 @@ cudaError_t launch_prep(const KernelArgs &a, cudaStream_t st, cudaEvent_t const 
     ok(big ? cudaFuncSetAttribute(k_advect<512, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adv_smem)
            : cudaFuncSetAttribute(k_advect<256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adv_smem));
     if (e != cudaSuccess) return e;
-    if (nb > 0) ok(launch_kernel(k_seed_place<false>, nb, kPrepThreads, 0, st, a));
+    if (nb > 0) ok(launch_kernel(k_seed_place<false, kPrepThreads>, nb, kPrepThreads, 0, st, a));
     if (a.rebin) ok(launch_kernel(k_rebin, (unsigned)a.n_pairs, 1024, 0, st, a, 0));  // at once unless overflowed
     if (nt1 > 0) {
         if (big) ok(launch_kernel(k_advect<512, 2>, 2 * nt1, 512, adv_smem, st, a));

@@ -65,3 +65,14 @@ def test_tiled_advection_batch_512_u8_identical_and_matches_oracle():
     a, b = _both(wl, 64)
     assert torch.equal(a, b)
     compare(wl, gpu_render(wl), oracle_render(wl))
+
+
+def test_batch_of_more_chunks_than_one_wave_renders_identically():
+    # 12 pairs of 13 107 particles: 312 chunks of 512, more than two per SM, so
+    # the seeding kernel runs two particles a thread (one a thread below that)
+    import torch
+    wl = W.batch_512_u8(n_pairs=12)
+    n_chunks = sum(-(-p.n_particles // 512) for p in wl.pairs)
+    assert n_chunks > 2 * torch.cuda.get_device_properties(0).multi_processor_count
+    a, b = _both(wl, 128)
+    assert torch.equal(a, b)

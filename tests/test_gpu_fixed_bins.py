@@ -72,13 +72,15 @@ def _cap2(p, tile, halo):
     return min(e + e // 2 + 64, p.n_particles)
 
 
-@pytest.mark.parametrize("out,tile,tiled", [("u8", 128, False), ("u8", 64, False), ("f32", 128, False),
-                                            ("u8", 128, True), ("u8", 32, True)])
-def test_overflowing_bins_render_the_same_bits(out, tile, tiled):
+@pytest.mark.parametrize("out,tile,tiled,n_pairs", [("u8", 128, False, 3), ("u8", 64, False, 3),
+                                                    ("f32", 128, False, 3), ("u8", 128, False, 12),
+                                                    ("u8", 128, True, 3), ("u8", 32, True, 3)])
+def test_overflowing_bins_render_the_same_bits(out, tile, tiled, n_pairs):
+    # 12 pairs: more seeding chunks than one wave (two particles a thread)
     import torch
 
     from paper_2512_09664_b300.binding import FLAG_TILED_ADVECT, Renderer
-    wl = W.batch_512_u8(n_pairs=3)
+    wl = W.batch_512_u8(n_pairs=n_pairs)
     if out == "f32":
         wl.out_dtype, wl.quant_bits = "f32", 0
     flags = FLAG_TILED_ADVECT if tiled else 0
