@@ -63,6 +63,9 @@ def parse():
                     choices=("batch64_512_u8", "single256", "uneven256", "diff32_256", "large_mixed",
                              "shapes64_512", "ablations", "stream512"),
                     help="the headline workload (default) or one of the other workloads, measured on their own")
+    ap.add_argument("--advect", choices=("seed", "tiled", "gather"), default="seed",
+                    help="headline workload: advect per particle while seeding (default), tile by tile "
+                         "from on-chip flow windows, or per particle with a counting sort")
     ap.add_argument("--quick", action="store_true",
                     help="timed steps only (no autotune, graph, FP16, e2e, per-pair or CPU legs): for profilers")
     return ap.parse_args()
@@ -477,7 +480,10 @@ def run_ours(args, rank, world, dist):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     wl = workload(rank, args.pairs)
-    r = Renderer(wl, device=dev, tile=args.tile)  # 0: per-size-class edges (defaults, then autotuned)
+    from paper_2512_09664_b300.binding import FLAG_GATHER_ADVECT, FLAG_TILED_ADVECT
+    adv_flags = {"seed": 0, "tiled": FLAG_TILED_ADVECT, "gather": FLAG_GATHER_ADVECT}[args.advect]
+    # tile 0: per-size-class edges (defaults, then autotuned)
+    r = Renderer(wl, device=dev, tile=args.tile, flags=adv_flags)
     stream = torch.cuda.current_stream()
     tuned = None
     if args.tile == 0 and not args.quick:
@@ -542,7 +548,7 @@ def run_ours(args, rank, world, dist):
 
     # the batched path with FP16 intermediate frames (splat, then a separate
     # finishing kernel reading the 16-bit frames)
-    r16 = Renderer(wl, device=dev, tile=args.tile, inter_dtype="f16")
+    r16 = Renderer(wl, device=dev, tile=args.tile, inter_dtype="f16", flags=adv_flags)
     if args.tile == 0:
         r16.tune(reps=2)
     for _ in range(3):
@@ -578,7 +584,7 @@ def run_ours(args, rank, world, dist):
 
     # plain per-pair path at the same accuracy: one launch sequence per pair,
     # the same u8 output and epilogue, FP32 throughout
-    plain = [Renderer(wl.subset([b]), device=dev, tile=args.tile) for b in range(wl.n_pairs)]
+    plain = [Renderer(wl.subset([b]), device=dev, tile=args.tile, flags=adv_flags) for b in range(wl.n_pairs)]
     for p in plain:
         p.render()
     torch.cuda.synchronize()
@@ -619,6 +625,9 @@ def run_ours(args, rank, world, dist):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(wl, {"tuning": r.tuning(), "tuning_choice": "autotuned" if args.tile == 0
                                        else "fixed", "path": "fused FP32 splat + epilogue (on-chip intermediate)",
+                                       "advection": {"seed": "per particle while seeding, fixed bins",
+                                                     "tiled": "tile by tile from on-chip flow windows, fixed bins",
+                                                     "gather": "per particle, counting-sort bins"}[args.advect],
                                        "parallelism": f"replicas x{world}"}),
         "mpx_per_s": value * 2 * 512 * 512 / 1e6,
         "stage_ms": stage_ms,
