@@ -8,13 +8,14 @@
 //   k_seed_place   Philox attributes of every particle, split positions, the
 //                  per-particle advection, and both frames' records placed
 //                  into the fixed bins
-//   k_rebin (f 1)  only after a frame-1 bin overflowed: the exact binning
-//   k_rebin (f 2)  only after a frame-2 bin overflowed
+//   k_rebin        a CTA per (pair, frame); only after a bin of that frame
+//                  overflowed: the exact binning
 //   k_splat        (splat.cuh) persistent CTAs over the work items
 //
-// With SYNTHPIX_FLAG_TILED_ADVECT, k_seed_place places frame 1 only and
-// k_advect (after k_rebin (f 1)) advects each frame-1 tile's home particles
-// from a flow window in shared memory and places the frame-2 records.
+// With SYNTHPIX_FLAG_TILED_ADVECT, k_seed_place places frame 1 only, then
+// k_rebin (frame 1), k_advect (advects each frame-1 tile's home particles
+// from a flow window in shared memory and places the frame-2 records) and
+// k_rebin (frame 2).
 //
 // Renders that need each particle's index when its frame-2 record is made
 // (given particles, per-frame shapes) advect per particle and bin both frames
@@ -797,9 +798,15 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_advect(KernelArgs a) {
 // advected positions (advection in k_seed_place).  Without an overflow every
 // CTA returns at once.
 // ---------------------------------------------------------------------------
+// f < 0: both frames in one launch, CTA f n_pairs + b (frame 2 independent
+// of frame 1's bins: the advection inside the seeding kernel).
 __global__ void __launch_bounds__(1024) k_rebin(KernelArgs a, int f) {
+    int b = (int)blockIdx.x;
+    if (f < 0) {
+        f = b >= a.n_pairs ? 1 : 0;
+        b -= f * a.n_pairs;
+    }
     if (*a.check != 1 || a.ovf[f] == 0u) return;
-    const int b = (int)blockIdx.x;
     scan_pair(a, b, f);
     __syncthreads();  // the cursors written by this CTA
     const PairPlan pl = a.plan[b];
@@ -900,9 +907,9 @@ cudaError_t launch_prep(const KernelArgs &a, cudaStream_t st, cudaEvent_t const 
         if (nb > 2u * (unsigned)nsm) ok(launch_kernel(k_seed_place<true, 256>, nb, 256, 0, st, a));
         else if (nb > 0) ok(launch_kernel(k_seed_place<true, 512>, nb, 512, 0, st, a));
         mark(2);
-        if (a.rebin) ok(launch_kernel(k_rebin, (unsigned)a.n_pairs, 1024, 0, st, a, 0));  // at once unless overflowed
+        // both frames' checks in one launch (each CTA returns at once unless its frame overflowed)
+        if (a.rebin) ok(launch_kernel(k_rebin, 2u * (unsigned)a.n_pairs, 1024, 0, st, a, -1));
         mark(3);
-        if (a.rebin) ok(launch_kernel(k_rebin, (unsigned)a.n_pairs, 1024, 0, st, a, 1));
         mark(4);
         return e;
     }

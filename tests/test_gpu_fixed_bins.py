@@ -156,12 +156,13 @@ def test_launch_count_of_each_binning_mode():
         torch.cuda.synchronize()
         return launch_count() - n0
 
-    # fixed bins: plan, seeding + advection + both frames' placement, two rebin checks, splat
-    assert launches(Renderer(wl, tile=128)) == 5
-    assert launches(Renderer(wl, tile=32)) == 5
+    # fixed bins: plan, seeding + advection + both frames' placement, one rebin check of both
+    # frames, splat
+    assert launches(Renderer(wl, tile=128)) == 4
+    assert launches(Renderer(wl, tile=32)) == 4
     empty = W.batch_512_u8(n_pairs=2)  # an empty pair: one empty chunk writes its work items
     empty.pairs[1].n_particles = 0
-    assert launches(Renderer(empty, tile=128)) == 5
+    assert launches(Renderer(empty, tile=128)) == 4
     # tiled advection: plan, seeding + frame-1 placement, rebin check, advection + frame-2
     # placement, rebin check, splat
     assert launches(Renderer(wl, tile=128, flags=FLAG_TILED_ADVECT)) == 6
