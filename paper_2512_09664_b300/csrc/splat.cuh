@@ -1654,14 +1654,14 @@ __device__ __forceinline__ __nv_bfloat16 to_inter<__nv_bfloat16>(float v) { retu
 // One work item of k_splat.  Fused (inter_dtype F32): splat the tile plus
 // its blur halo and finish it on chip.  Otherwise splat the tile alone and
 // store S in 16 bits to the intermediate frames; k_finish does the rest.
-// The next work item is ticket tk (taken as the previous item ended): thread
+// The next work item is ticket tk (taken during the previous item): thread
 // 0 copies its fields in while the first chunk renders (fetch_item) and
 // publishes it in *next at the last chunk's barrier.  hdr: the item's staged
 // header; hdr_next: the next item's header slot; rec: the record region,
 // which receives the next item's header and first chunk as soon as the
 // item's own records are splatted (the copies run behind the finishing).
 template <typename T, int NT, int RS>
-__device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo &it, uint32_t tk,
+__device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo &it, uint32_t &tk,
                                              const unsigned char *hdr, unsigned char *hdr_next, unsigned char *rec,
                                              uint32_t cap, const Smem &s, ItemInfo *next) {
     const synthpix_pair_desc &D = *reinterpret_cast<const synthpix_pair_desc *>(hdr);
@@ -1714,6 +1714,10 @@ __device__ __forceinline__ void process_item(const KernelArgs &a, const ItemInfo
         stage_records<RS>(a, nx.rec0, min(nx.count, cap), rec);
     }
     cp_async_commit();
+    // the ticket of the item after the next (thread 0 alone uses tk): taken
+    // here, ahead of the finishing, so that the atomic's round trip overlaps
+    // the finishing instead of holding the item-end barrier
+    if (threadIdx.x == 0) tk = 2u * gridDim.x + atomicAdd(a.ticket, 1u);
     // block counts of the next item start from zero (its first count comes after a barrier)
     for (int k = threadIdx.x; k < kBlkPitch * kBlkSide; k += blockDim.x) sh_blk[k] = 0u;
 
@@ -1807,11 +1811,12 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_splat(KernelArgs a) {
         reinterpret_cast<uint4 *>(s.acc)[k] = make_uint4(0u, 0u, 0u, 0u);
     // work queue: the current item and the ticket tk of the next one, whose
     // fields are copied in while the current item renders (process_item).  A
-    // CTA holds one ticket beyond the item it works on, so when the queue
-    // runs dry the CTAs stop within about one item of each other.  Tickets
+    // CTA holds one ticket beyond the item it renders (two while it finishes
+    // one), so when the queue runs dry the CTAs stop within about one item of
+    // each other.  Tickets
     // only grow, so a CTA never drops a valid one.  The first two tickets of
     // CTA b are b and grid + b; the counter hands out the rest from 2 grid,
-    // each taken as an item ends (it has the next item's set-up to return).
+    // each taken once an item's records are splatted, ahead of its finishing.
     uint32_t tk = gridDim.x + blockIdx.x;
     if (threadIdx.x == 0) {
         sh_wrap = 0;
@@ -1837,8 +1842,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_splat(KernelArgs a) {
             sh_carry_clean = 0;
         }
         process_item<T, NT, RS>(a, it, tk, bufs + cur * kStageHeader, bufs + (cur ^ 1) * kStageHeader, rec, cap, s,
-                                &s_item[cur ^ 1]);
-        if (threadIdx.x == 0) tk = 2u * gridDim.x + atomicAdd(a.ticket, 1u);  // the item after the next
+                                &s_item[cur ^ 1]);  // takes the ticket of the item after the next
         cur ^= 1;
         __syncthreads();
     }
