@@ -447,9 +447,16 @@ static int run(Mode mode, const synthpix_batch_desc *batch, const synthpix_pair_
     int32_t *check = reinterpret_cast<int32_t *>(ws + L.check);
     uint32_t *ticket = reinterpret_cast<uint32_t *>(ws + L.check + 16);
     float *blur_w = reinterpret_cast<float *>(ws + L.blur);
+    // flow grids of at most a quarter of L2 in all: the plan launch has them
+    // fetched into L2 ahead of the advection's dependent gathers
+    const int32_t planes = (batch->flags & SYNTHPIX_FLAG_OUT_OF_PLANE) ? 3 : 2;
+    int64_t flow_bytes = 0;
+    for (int32_t b = 0; b < n_pairs; ++b) flow_bytes += 4LL * planes * pairs[b].flow_h * pairs[b].flow_w;
+    const float *pf_flows = mode != Mode::Seed && flow_bytes <= spx::kPrefetchMaxBytes ? flows : nullptr;
     if (ev && ev[0]) cudaEventRecord(ev[0], st);
     e = spx::launch_plan(descs, n_pairs, P.T.rule, P.fused, plan, L, check, blur_w, ticket,
-                         mode == Mode::Render ? reinterpret_cast<uint32_t *>(ws + L.count) : nullptr, st);
+                         mode == Mode::Render ? reinterpret_cast<uint32_t *>(ws + L.count) : nullptr, pf_flows,
+                         planes, st);
     if (e != cudaSuccess) return fail(SYNTHPIX_ECUDA, "plan launch: %s", cudaGetErrorString(e));
     if (ev && ev[1]) cudaEventRecord(ev[1], st);
 

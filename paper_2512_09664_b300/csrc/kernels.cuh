@@ -129,9 +129,15 @@ constexpr size_t kMaxSmemBytes = 227 * 1024;  // dynamic shared memory of one CT
 
 // count: NULL, or the per-(pair, frame, tile) bin counts, zeroed by the plan launch
 // ticket: the splat's work-queue counter, followed by the two overflow flags of the fixed bins.
+// pf_flows: NULL, or the flows of a batch whose flow grids take at most
+// kPrefetchMaxBytes in all (pf_planes floats per node: 2, or 3 with the
+// out-of-plane grid); a CTA per pair of the plan launch then asks the L2 to
+// fetch the pair's grid, so that the flow gathers of the next kernels hit L2.
+constexpr int64_t kPrefetchMaxBytes = 32LL << 20;    // a quarter of the 126 MB L2
+constexpr int64_t kPrefetchPieceBytes = 64LL << 10;  // per bulk-prefetch instruction (one lane)
 cudaError_t launch_plan(const synthpix_pair_desc *descs, int32_t n_pairs, const TileRule &rule, int32_t fused,
                         PairPlan *plan, const Layout &L, int32_t *check, float *blur_w, uint32_t *ticket,
-                        uint32_t *count, cudaStream_t st);
+                        uint32_t *count, const float *pf_flows, int32_t pf_planes, cudaStream_t st);
 // ev: NULL or kStageEvents events recorded at the stage boundaries.
 cudaError_t launch_prep(const KernelArgs &a, cudaStream_t st, cudaEvent_t const *ev);
 cudaError_t launch_splat(const KernelArgs &a, int32_t out_dtype, cudaStream_t st, cudaEvent_t const *ev);

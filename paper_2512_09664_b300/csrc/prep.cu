@@ -38,9 +38,12 @@ namespace spx {
 
 // ---------------------------------------------------------------------------
 // k_plan: per-pair prefix sums (CTA 0, 1024 threads); the next CTAs clear
-// the bin counts of a render; the last ones form the FP64 blur taps, four
+// the bin counts of a render; then CTAs that form the FP64 blur taps, four
 // pairs each, a tap per lane (FP64 is slow on this part: spread over SMs and
-// lanes, off CTA 0's path)
+// lanes, off CTA 0's path); the last ones, when the batch's flow grids are
+// small enough to stay in L2 (single pairs, small batches), ask the L2 to
+// fetch them with bulk prefetches, so that the dependent flow gathers of the
+// per-particle advection that follows hit L2 instead of waiting on DRAM.
 // ---------------------------------------------------------------------------
 constexpr int kPlanZeroWords = 16384;
 constexpr int kTapLanes = 8;                  // lanes per pair of the blur-tap CTAs
@@ -51,7 +54,23 @@ __global__ void __launch_bounds__(1024) k_plan(const synthpix_pair_desc *__restr
                                                int64_t want_part, int64_t want_tiles, int64_t want_list,
                                                int64_t want_inter, int64_t want_chunks, int32_t *__restrict__ check,
                                                float *__restrict__ blur_w, uint32_t *__restrict__ ticket,
-                                               uint32_t *__restrict__ count, int64_t n_count, int32_t zero_ctas) {
+                                               uint32_t *__restrict__ count, int64_t n_count, int32_t zero_ctas,
+                                               const float *__restrict__ pf_flows, int32_t pf_planes) {
+    const int tap_ctas = (n_pairs + kPlanTapPairs - 1) / kPlanTapPairs;
+    if ((int)blockIdx.x > zero_ctas + tap_ctas) {  // L2 prefetch of pair b's flow grid
+        const int b = (int)blockIdx.x - 1 - zero_ctas - tap_ctas;
+        const synthpix_pair_desc &d = descs[b];
+        // the grid's bytes from its first 16-byte boundary to its last one
+        const uintptr_t p0 = ((uintptr_t)(pf_flows + d.flow_offset) + 15) & ~(uintptr_t)15;
+        const uintptr_t p1 = (uintptr_t)(pf_flows + d.flow_offset + (int64_t)pf_planes * d.flow_h * d.flow_w) &
+                             ~(uintptr_t)15;
+        for (uintptr_t p = p0 + (uintptr_t)threadIdx.x * kPrefetchPieceBytes; p < p1;
+             p += (uintptr_t)blockDim.x * kPrefetchPieceBytes) {
+            const uint32_t n = (uint32_t)min((uintptr_t)kPrefetchPieceBytes, p1 - p);  // a multiple of 16
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(n) : "memory");
+        }
+        return;
+    }
     if (blockIdx.x > 0 && (int)blockIdx.x <= zero_ctas) {  // clear the bin counts, 16 Ki words per CTA
         const int64_t k0 = ((int64_t)blockIdx.x - 1) * kPlanZeroWords;
         const int64_t n = min((int64_t)kPlanZeroWords, n_count - k0);
@@ -872,13 +891,14 @@ __global__ void __launch_bounds__(1024) k_rebin(KernelArgs a, int f) {
 // ---------------------------------------------------------------------------
 cudaError_t launch_plan(const synthpix_pair_desc *descs, int32_t n_pairs, const TileRule &rule, int32_t fused,
                         PairPlan *plan, const Layout &L, int32_t *check, float *blur_w, uint32_t *ticket,
-                        uint32_t *count, cudaStream_t st) {
+                        uint32_t *count, const float *pf_flows, int32_t pf_planes, cudaStream_t st) {
     const int64_t n_count = count ? L.n_tiles : 0;
     const int32_t zero_ctas = (int32_t)((n_count + kPlanZeroWords - 1) / kPlanZeroWords);
     const int32_t tap_ctas = (n_pairs + kPlanTapPairs - 1) / kPlanTapPairs;
-    const unsigned grid = 1u + (unsigned)zero_ctas + (unsigned)tap_ctas;
+    const int32_t pf_ctas = pf_flows ? n_pairs : 0;
+    const unsigned grid = 1u + (unsigned)zero_ctas + (unsigned)tap_ctas + (unsigned)pf_ctas;
     return launch_kernel(k_plan, grid, 1024, 0, st, descs, n_pairs, rule, fused, plan, L.n_part, L.n_tiles, L.n_list,
-                          L.n_inter, L.n_chunks, check, blur_w, ticket, count, n_count, zero_ctas);
+                          L.n_inter, L.n_chunks, check, blur_w, ticket, count, n_count, zero_ctas, pf_flows, pf_planes);
 }
 
 cudaError_t launch_prep(const KernelArgs &a, cudaStream_t st, cudaEvent_t const *ev) {
