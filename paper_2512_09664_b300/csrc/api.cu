@@ -348,7 +348,133 @@ namespace spx {
 static std::atomic<uint64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 uint64_t launch_total() { return g_launches.load(std::memory_order_relaxed); }
+thread_local std::vector<RecordedLaunch> *t_recording = nullptr;
 }  // namespace spx
+
+namespace {
+
+// A render's launch sequence (plan, seeding and binning, splat) submitted as
+// one CUDA graph: the GPU starts each kernel of a graph sooner after the
+// previous one than it starts stream launches.  Sequences are keyed by the
+// device and by each launch's kernel and shape; a sequence met for the first
+// time is launched kernel by kernel, the second time it is instantiated as a
+// graph (a chain of kernel nodes), and from then on each render sets the
+// nodes' arguments and launches the graph.  Graph launches of one sequence
+// are ordered behind one another, whatever their streams.  Not used while
+// the stream is being captured (the caller's graph records the kernels
+// themselves), for staged renders (events between the stages), or where the
+// library must not allocate (t_direct).
+struct SeqKey {
+    int device;
+    std::vector<std::tuple<const void *, unsigned, unsigned, size_t>> shape;
+    bool operator<(const SeqKey &o) const { return std::tie(device, shape) < std::tie(o.device, o.shape); }
+};
+struct SeqGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaGraphNode_t> nodes;
+};
+constexpr size_t kMaxSeqGraphs = 32;  // instantiated sequences kept (then new ones run kernel by kernel)
+constexpr size_t kMaxSeqSeen = 1024;  // sequences remembered as met once
+std::mutex g_seq_mu;
+std::map<SeqKey, SeqGraph> g_seq_graphs;
+std::map<SeqKey, int> g_seq_seen;
+thread_local bool t_direct = false;
+
+cudaKernelNodeParams node_params(const spx::RecordedLaunch &r) {
+    cudaKernelNodeParams p{};
+    p.func = const_cast<void *>(r.func);
+    p.gridDim = dim3(r.grid);
+    p.blockDim = dim3(r.block);
+    p.sharedMemBytes = (unsigned)r.smem;
+    p.kernelParams = const_cast<void **>(r.params.data());
+    p.extra = nullptr;
+    return p;
+}
+
+cudaError_t launch_direct(const std::vector<spx::RecordedLaunch> &seq, cudaStream_t st) {
+    for (const spx::RecordedLaunch &r : seq) {
+        const cudaError_t e = cudaLaunchKernel(r.func, dim3(r.grid), dim3(r.block),
+                                               const_cast<void **>(r.params.data()), r.smem, st);
+        if (e != cudaSuccess) return e;
+        spx::count_launch();
+    }
+    return cudaSuccess;
+}
+
+void destroy(SeqGraph &g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+    g = SeqGraph();
+}
+
+cudaError_t build(const std::vector<spx::RecordedLaunch> &seq, SeqGraph &g) {
+    cudaError_t e = cudaGraphCreate(&g.graph, 0);
+    for (size_t i = 0; e == cudaSuccess && i < seq.size(); ++i) {
+        const cudaKernelNodeParams p = node_params(seq[i]);
+        cudaGraphNode_t n = nullptr;
+        e = cudaGraphAddKernelNode(&n, g.graph, i ? &g.nodes.back() : nullptr, i ? 1 : 0, &p);
+        if (e == cudaSuccess) g.nodes.push_back(n);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, g.graph, 0);
+    if (e != cudaSuccess) destroy(g);
+    return e;
+}
+
+cudaError_t submit(const std::vector<spx::RecordedLaunch> &seq, cudaStream_t st) {
+    if (seq.empty()) return cudaSuccess;
+    SeqKey key;
+    cudaError_t e = cudaGetDevice(&key.device);
+    if (e != cudaSuccess) return e;
+    for (const spx::RecordedLaunch &r : seq) key.shape.emplace_back(r.func, r.grid, r.block, r.smem);
+    std::lock_guard<std::mutex> lock(g_seq_mu);
+    auto it = g_seq_graphs.find(key);
+    if (it == g_seq_graphs.end()) {
+        if (g_seq_graphs.size() >= kMaxSeqGraphs) return launch_direct(seq, st);
+        if (g_seq_seen.size() >= kMaxSeqSeen) g_seq_seen.clear();
+        if (g_seq_seen[key]++ == 0) return launch_direct(seq, st);
+        SeqGraph g;
+        if (build(seq, g) != cudaSuccess) {
+            cudaGetLastError();  // the sequence still runs, kernel by kernel
+            return launch_direct(seq, st);
+        }
+        g_seq_seen.erase(key);
+        it = g_seq_graphs.emplace(std::move(key), g).first;
+    } else {
+        for (size_t i = 0; i < seq.size(); ++i) {
+            const cudaKernelNodeParams p = node_params(seq[i]);
+            e = cudaGraphExecKernelNodeSetParams(it->second.exec, it->second.nodes[i], &p);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    e = cudaGraphLaunch(it->second.exec, st);
+    if (e == cudaSuccess)
+        for (size_t i = 0; i < seq.size(); ++i) spx::count_launch();
+    return e;
+}
+
+// Records the launches of its scope on this thread (see launch_kernel).
+struct Recording {
+    std::vector<spx::RecordedLaunch> seq;
+    bool on;
+    explicit Recording(bool enable) : on(enable) {
+        if (on) spx::t_recording = &seq;
+    }
+    ~Recording() {
+        if (on) spx::t_recording = nullptr;
+    }
+};
+
+bool stream_capturing(cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return true;  // unknown: launch kernel by kernel
+    }
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+}  // namespace
 
 static_assert(sizeof(synthpix_pair_desc) == 160, "pair descriptor ABI");
 static_assert(sizeof(synthpix_batch_desc) == 64, "batch descriptor ABI");
@@ -453,6 +579,8 @@ static int run(Mode mode, const synthpix_batch_desc *batch, const synthpix_pair_
     int64_t flow_bytes = 0;
     for (int32_t b = 0; b < n_pairs; ++b) flow_bytes += 4LL * planes * pairs[b].flow_h * pairs[b].flow_w;
     const float *pf_flows = mode != Mode::Seed && flow_bytes <= spx::kPrefetchMaxBytes ? flows : nullptr;
+    // renders without stage events: the launch sequence goes to the GPU as one graph
+    Recording rec(mode == Mode::Render && !ev && !t_direct && !stream_capturing(st));
     if (ev && ev[0]) cudaEventRecord(ev[0], st);
     e = spx::launch_plan(descs, n_pairs, P.T.rule, P.fused, plan, L, check, blur_w, ticket,
                          mode == Mode::Render ? reinterpret_cast<uint32_t *>(ws + L.count) : nullptr, pf_flows,
@@ -538,6 +666,11 @@ static int run(Mode mode, const synthpix_batch_desc *batch, const synthpix_pair_
         if (e != cudaSuccess) return fail(SYNTHPIX_ECUDA, "seeding/binning launch: %s", cudaGetErrorString(e));
         e = spx::launch_splat(a, batch->out_dtype, st, ev);
         if (e != cudaSuccess) return fail(SYNTHPIX_ECUDA, "splat launch: %s", cudaGetErrorString(e));
+        if (rec.on) {
+            spx::t_recording = nullptr;
+            e = submit(rec.seq, st);
+            if (e != cudaSuccess) return fail(SYNTHPIX_ECUDA, "render launch: %s", cudaGetErrorString(e));
+        }
     }
     g_err[0] = 0;
     return SYNTHPIX_OK;
@@ -830,6 +963,23 @@ int render_workspace_need(const synthpix_batch_desc *batch, const synthpix_pair_
     if (rc) return rc;
     *need = n_pairs > 0 ? P.L.total : 0;
     return SYNTHPIX_OK;
+}
+
+}  // namespace spx
+
+namespace spx {
+
+// synthpix_render_pairs with its kernels launched one by one: no CUDA graph
+// is instantiated (which may allocate), for callers that cannot have the
+// library allocate device memory.
+int render_pairs_direct(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
+                        const synthpix_pair_desc *pairs_dev, int32_t n_pairs, const float *flows, void *images,
+                        void *workspace, size_t workspace_bytes, void *stream) {
+    t_direct = true;
+    const int rc =
+        synthpix_render_pairs(batch, pairs, pairs_dev, n_pairs, flows, images, workspace, workspace_bytes, stream);
+    t_direct = false;
+    return rc;
 }
 
 }  // namespace spx

@@ -2,6 +2,10 @@
 // (prep.cu: plan, seeding + advection, binning; splat.cu: the splat).
 #pragma once
 
+#include <memory>
+#include <tuple>
+#include <vector>
+
 #include "common.cuh"
 
 namespace spx {
@@ -85,12 +89,40 @@ constexpr int kStageEvents = 6;
 void count_launch();
 uint64_t launch_total();
 
-// Launch a kernel of the library; returns the launch's error.
-// (Programmatic dependent launch was measured: a replayed render took 12 us
-// longer with it, so the kernels are launched plainly.)
+// A kernel launch held back for a CUDA graph: the kernel, its shape and a
+// copy of its arguments (params points into `args`).
+struct RecordedLaunch {
+    const void *func;
+    unsigned grid, block;
+    size_t smem;
+    std::shared_ptr<void> args;
+    std::vector<void *> params;
+};
+// While a render's launch sequence is recorded on this thread, launch_kernel
+// appends to it instead of launching (api.cu submits the sequence as one
+// CUDA graph).
+extern thread_local std::vector<RecordedLaunch> *t_recording;
+
+// Launch a kernel of the library (or record it, see t_recording); returns
+// the launch's error.  (Programmatic dependent launch was measured: a
+// replayed render took 12 us longer with it, so the kernels are launched
+// plainly.)
 template <typename... P, typename... A>
 inline cudaError_t launch_kernel(void (*kernel)(P...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
                                   A &&...args) {
+    if (t_recording) {
+        using Tuple = std::tuple<P...>;
+        auto tup = std::make_shared<Tuple>(static_cast<A &&>(args)...);
+        RecordedLaunch r;
+        r.func = reinterpret_cast<const void *>(kernel);
+        r.grid = grid;
+        r.block = block;
+        r.smem = smem;
+        r.params = std::apply([](auto &...e) { return std::vector<void *>{static_cast<void *>(&e)...}; }, *tup);
+        r.args = std::move(tup);
+        t_recording->push_back(std::move(r));
+        return cudaSuccess;
+    }
     kernel<<<grid, block, smem, st>>>(static_cast<A &&>(args)...);
     const cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) count_launch();

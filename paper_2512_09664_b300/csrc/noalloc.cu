@@ -18,6 +18,11 @@ namespace spx {
 int set_error(int code, const char *msg);
 int render_workspace_need(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs, int32_t n_pairs,
                           size_t *need);
+// synthpix_render_pairs with the kernels launched one by one (no CUDA graph,
+// whose instantiation may allocate)
+int render_pairs_direct(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
+                        const synthpix_pair_desc *pairs_dev, int32_t n_pairs, const float *flows, void *images,
+                        void *workspace, size_t workspace_bytes, void *stream);
 }
 
 namespace {
@@ -79,6 +84,6 @@ extern "C" int synthpix_render_pairs_noalloc(const synthpix_batch_desc *batch, c
     if (rc != SYNTHPIX_OK) return rc;
     // the render clears what must start at zero (its bin counters) itself;
     // everything else in the scratch is written before it is read
-    return synthpix_render_pairs(batch, pairs, pairs_dev, n_pairs, flows, images, scratch,
-                                 (size_t)SYNTHPIX_NOALLOC_SCRATCH_BYTES, stream);
+    return spx::render_pairs_direct(batch, pairs, pairs_dev, n_pairs, flows, images, scratch,
+                                    (size_t)SYNTHPIX_NOALLOC_SCRATCH_BYTES, stream);
 }
