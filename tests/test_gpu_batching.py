@@ -49,6 +49,35 @@ def test_graph_replay_matches_eager():
         assert torch.equal(r.images, eager)
 
 
+def test_renders_submitted_as_graphs_match_kernel_by_kernel_launches():
+    """From a launch sequence's second use on, a render goes to the GPU as one
+    CUDA graph whose nodes' arguments are set for each render; a render with
+    an events array launches kernel by kernel.  Both give the same bits, seed
+    after seed, and a second renderer of the same shapes (other buffers)
+    reuses the graph with its own arguments."""
+    import torch
+
+    from paper_2512_09664_b300.binding import Renderer, launch_count
+    wl = W.batch_512_u8(n_pairs=3)
+    r = Renderer(wl, tile=64)
+    first = {}
+    for seed in (11, 12, 13, 11):
+        r.pk.batch.seed = seed
+        n0 = launch_count()
+        via_graph = r.render().clone()
+        torch.cuda.synchronize()
+        assert launch_count() - n0 == 4
+        r.images.zero_()
+        direct = r.render_staged([None] * 6).clone()
+        torch.cuda.synchronize()
+        assert torch.equal(via_graph, direct)
+        first.setdefault(seed, via_graph)
+    assert torch.equal(first[11], via_graph) and not torch.equal(first[11], first[12])
+    r2 = Renderer(wl, tile=64)
+    r2.pk.batch.seed = 12
+    assert torch.equal(r2.render(), first[12])
+
+
 def test_uneven_batch_full_size_mix_sampled_against_oracle():
     # the uneven workload's size mix (128..1024) with fewer pairs; every pair
     # of the batch is compared in full
