@@ -214,6 +214,16 @@ size_t synthpix_workspace_bytes(const synthpix_batch_desc *batch,
  *              synthpix_workspace_bytes(...) bytes; contents on entry ignored.
  *   stream     cudaStream_t.
  *
+ * Launches: the render's kernels (plan, seeding and binning, splat) run in
+ * stream order on `stream`.  Unless the stream is being captured, the
+ * library submits them as one CUDA graph from the second render of the same
+ * launch shapes on a device on (the first render of a shape launches kernel
+ * by kernel; the second instantiates the graph, which may allocate device
+ * memory; later renders set its arguments and launch it).  Graph launches of
+ * one shape are ordered behind one another even on different streams.  The
+ * cached graphs belong to the device's context: a cudaDeviceReset after such
+ * a render is not supported.
+ *
  * Returns SYNTHPIX_OK or a negative status (nothing is launched on error).
  */
 int synthpix_render_pairs(const synthpix_batch_desc *batch, const synthpix_pair_desc *pairs,
