@@ -336,7 +336,8 @@ int synthpix_render_pairs_staged(const synthpix_batch_desc *batch, const synthpi
  * static __device__ array of SYNTHPIX_NOALLOC_SCRATCH_BYTES (32 MiB) compiled
  * into the library; every GPU that loads the library holds it until the
  * process exits.  This call allocates nothing (no cudaMalloc / cudaFree, no
- * allocating library routine).
+ * allocating library routine); its kernels are launched one by one, never
+ * submitted as a CUDA graph (graph instantiation may allocate).
  *  - A batch that needs more scratch than the array holds (compare
  *    synthpix_workspace_bytes) is rejected with SYNTHPIX_EWORKSPACE and a
  *    message, before anything is launched.
